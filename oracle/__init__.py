@@ -1,0 +1,16 @@
+"""FP64 CPU oracle for batched adaptive Dormand-Prince 5(4).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+bench's CPU-baseline leg use it.  The product path never imports it.
+"""
+from .oracle import (  # noqa: F401
+    build,
+    default_opts,
+    field_eval,
+    dense_weights,
+    solve,
+    replay,
+    adjoint,
+    tableau_doubles,
+    STATUS,
+)

@@ -1,0 +1,857 @@
+/*
+ * tode_oracle.c -- plain, slow FP64 CPU oracle for batched adaptive
+ * Dormand-Prince 5(4) with fully independent per-instance solver state.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the package's smoke check and the bench's
+ * CPU-baseline leg do.  It shares no code, header, table or helper with the
+ * CUDA path: every constant below is written out here independently.
+ *
+ * What it follows (torchode paper):
+ *   - Sec. 3 "Design & Features": every instance of the batch keeps its own
+ *     initial condition, integration bounds, step size, tolerances and
+ *     accept/reject decisions; nothing couples instances.
+ *   - Sec. 3, paragraph "What makes torchode fast?": FSAL/SSAL reuse of stage
+ *     values, dense output polynomials evaluated by Horner's rule.
+ *   - Sec. 3, paragraph "What slows torchode down?": every instance passes its
+ *     own evaluation points at its own pace.
+ *   - App. A: dopri5 (Dormand & Prince 1980) with an integral controller.
+ *   - App. C "Impact of PID Control": the controller is a filter over the
+ *     last error estimates (Soderlind 2002/2003); the PI subset is used here.
+ *   - App. A, FEN benchmark: gradients by backpropagation through the solver
+ *     (discretize-then-optimize) -> the discrete adjoint of the fixed-mesh map.
+ *
+ * Readings of passages the paper leaves open (it prints no tableau, norm,
+ * controller constants, starting-step rule or interpolant):
+ *   - tableau: Dormand & Prince 1980, "A family of embedded Runge-Kutta
+ *     formulae", the 5(4) pair with FSAL;
+ *   - dense output: the 4th-order continuous extension of that pair given by
+ *     Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.6, expanded into one
+ *     quartic polynomial b_i(theta) per stage and evaluated by Horner's rule;
+ *   - error norm: the weighted RMS norm of HNW Sec. II.4, per instance;
+ *   - controller: factor = safety * err^-beta1 * err_prev^beta2, clamped;
+ *   - starting step: the heuristic of HNW Sec. II.4 ("starting step size").
+ *     PARITY UNPINNED: the paper gives no starting-step rule and no worked
+ *     example of it; only the other parts below are pinned by tests.
+ *
+ * Arithmetic: double everywhere, built with -O2 -ffp-contract=off and no
+ * fast-math, sums taken left to right in the order written.
+ */
+#define _GNU_SOURCE
+#include <math.h>
+#include <pthread.h>
+#include <sched.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+/* ------------------------------------------------------------------------ */
+/* Dormand-Prince 5(4) tableau (Dormand & Prince 1980; dopri5 in App. A).    */
+/* ------------------------------------------------------------------------ */
+#define NS 7
+
+static const double DP_C[NS] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
+
+static const double DP_A[NS][NS] = {
+    {0, 0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0, 0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0, 0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0, 0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0, 0},
+    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0}};
+
+/* 5th-order weights: identical to the last stage row (FSAL/SSAL, Sec. 3). */
+static const double DP_B[NS] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0,
+                                -2187.0 / 6784.0, 11.0 / 84.0, 0.0};
+/* embedded 4th-order weights */
+static const double DP_BHAT[NS] = {5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0,
+                                   -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0};
+
+/* Dense output: b_i(theta) = theta*(q0 + theta*(q1 + theta*(q2 + theta*q3))).
+ * These are the expanded coefficients of the HNW Sec. II.6 continuous
+ * extension of the pair above, one exact rational each. */
+static const double DP_Q[NS][4] = {
+    {1.0, -8048581381.0 / 2820520608.0, 8663915743.0 / 2820520608.0,
+     -12715105075.0 / 11282082432.0},
+    {0.0, 0.0, 0.0, 0.0},
+    {0.0, 131558114200.0 / 32700410799.0, -68118460800.0 / 10900136933.0,
+     87487479700.0 / 32700410799.0},
+    {0.0, -1754552775.0 / 470086768.0, 14199869525.0 / 1410260304.0,
+     -10690763975.0 / 1880347072.0},
+    {0.0, 127303824393.0 / 49829197408.0, -318862633887.0 / 49829197408.0,
+     701980252875.0 / 199316789632.0},
+    {0.0, -282668133.0 / 205662961.0, 2019193451.0 / 616988883.0,
+     -1453857185.0 / 822651844.0},
+    {0.0, 40617522.0 / 29380423.0, -110615467.0 / 29380423.0, 69997945.0 / 29380423.0}};
+
+/* Lets tests compare these doubles with an exact rational table. */
+void orc_tableau(double *c, double *a, double *b, double *bhat, double *q) {
+  for (int i = 0; i < NS; ++i) {
+    c[i] = DP_C[i];
+    b[i] = DP_B[i];
+    bhat[i] = DP_BHAT[i];
+    for (int j = 0; j < NS; ++j) a[i * NS + j] = DP_A[i][j];
+    for (int j = 0; j < 4; ++j) q[i * 4 + j] = DP_Q[i][j];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Problem description.                                                      */
+/* ------------------------------------------------------------------------ */
+enum { ORC_VDP = 1, ORC_LINEAR = 2, ORC_MLP = 3 };
+enum { ST_SUCCESS = 0, ST_MAX_STEPS = 1, ST_DT_UNDERFLOW = 2, ST_NONFINITE = 3,
+       ST_INVALID_INPUT = 4, ST_RUNNING = -1 };
+
+#define MLP_MAX_LAYERS 8
+
+typedef struct {
+  int kind;
+  int D;
+  const double *mu;          /* Van der Pol: [B] damping */
+  const double *A;           /* linear: [B][D][D] row-major */
+  int n_layers;              /* MLP: number of weight matrices */
+  const int *widths;         /* MLP: [n_layers+1]; widths[0]=D+1, widths[n_layers]=D */
+  const double *const *W;    /* MLP: W[l] is [widths[l+1]][widths[l]] row-major */
+  const double *const *bias; /* MLP: bias[l] is [widths[l+1]] */
+} orc_field;
+
+typedef struct {
+  double rtol, atol;
+  const double *rtol_b, *atol_b; /* optional per-instance tolerances [B], NULL = scalar */
+  double safety, fac_min, fac_max, beta1, beta2;
+  double h0;                     /* > 0: first step given; 0: starting-step heuristic */
+  int max_steps;                 /* attempted steps per instance */
+} orc_opts;
+
+typedef struct {
+  int cap;          /* attempts recorded per instance */
+  double *t, *h, *err;
+  int32_t *accepted; /* all [B][cap] */
+  int32_t *len;      /* [B]: attempts recorded */
+} orc_trace;
+
+static int mlp_max_width(const orc_field *F) {
+  int m = 0;
+  for (int l = 0; l <= F->n_layers; ++l)
+    if (F->widths[l] > m) m = F->widths[l];
+  return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vector fields f(t, y) for instance i.                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Van der Pol, Eq. 1 written as a first-order system:
+ * y1' = y2,  y2' = mu (1 - y1^2) y2 - y1. */
+static void f_vdp(double mu, const double *y, double *out) {
+  out[0] = y[1];
+  out[1] = mu * (1.0 - y[0] * y[0]) * y[1] - y[0];
+}
+
+/* y' = A_i y, A_i row-major. */
+static void f_linear(const double *A, int D, const double *y, double *out) {
+  for (int r = 0; r < D; ++r) {
+    double s = 0.0;
+    for (int c = 0; c < D; ++c) s = s + A[r * D + c] * y[c];
+    out[r] = s;
+  }
+}
+
+/* MLP field f(t,y) = W_L tanh( ... tanh(W_1 [y; t] + b_1) ... ) + b_L.
+ * act (optional) receives the input of every layer: act[l] has widths[l]
+ * entries, act[0] = [y; t]; it needs sum(widths) doubles. */
+static void f_mlp(const orc_field *F, double t, const double *y, double *out, double *act) {
+  const int L = F->n_layers, D = F->D;
+  double *a = act; /* act[0] */
+  for (int j = 0; j < D; ++j) a[j] = y[j];
+  a[D] = t;
+  for (int l = 0; l < L; ++l) {
+    const int nin = F->widths[l], nout = F->widths[l + 1];
+    const double *W = F->W[l], *bv = F->bias[l];
+    double *next = (l + 1 < L) ? a + nin : out;
+    for (int r = 0; r < nout; ++r) {
+      double s = 0.0;
+      for (int c = 0; c < nin; ++c) s = s + W[r * nin + c] * a[c];
+      s = s + bv[r];
+      next[r] = (l + 1 < L) ? tanh(s) : s;
+    }
+    a = next;
+  }
+}
+
+typedef struct {
+  const orc_field *F;
+  int i;        /* instance index */
+  double *act;  /* MLP scratch */
+  long nfe;     /* evaluations */
+} fctx;
+
+static void feval(fctx *c, double t, const double *y, double *out) {
+  const orc_field *F = c->F;
+  c->nfe++;
+  if (F->kind == ORC_VDP) {
+    f_vdp(F->mu[c->i], y, out);
+  } else if (F->kind == ORC_LINEAR) {
+    f_linear(F->A + (size_t)c->i * F->D * F->D, F->D, y, out);
+  } else {
+    f_mlp(F, t, y, out, c->act);
+  }
+}
+
+/* Exported single evaluation (tests pin the fields with it). */
+void orc_field_eval(const orc_field *F, int i, double t, const double *y, double *out) {
+  fctx c = {F, i, NULL, 0};
+  double *act = NULL;
+  if (F->kind == ORC_MLP) {
+    int tot = 0;
+    for (int l = 0; l <= F->n_layers; ++l) tot += F->widths[l];
+    act = (double *)malloc(sizeof(double) * tot);
+    c.act = act;
+  }
+  feval(&c, t, y, out);
+  free(act);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Norm, starting step, controller.                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Weighted RMS norm of v with weights sc (HNW Sec. II.4), taken per instance
+ * (Sec. 3 / Sec. 4.1: never across the batch). */
+static double rms(const double *v, const double *sc, int D) {
+  double s = 0.0;
+  for (int j = 0; j < D; ++j) {
+    double q = v[j] / sc[j];
+    s = s + q * q;
+  }
+  return sqrt(s / (double)D);
+}
+
+static double dmax(double a, double b) { return (a > b) ? a : b; }
+static double dmin(double a, double b) { return (b < a) ? b : a; }
+
+/* Starting step size, HNW Sec. II.4 (PARITY UNPINNED, see header).  f0 =
+ * f(t0, y0) is supplied and reused as the first step's k1 (FSAL). */
+static double starting_step(fctx *c, double t0, double t1, const double *y0, const double *f0,
+                            int D, double rtol, double atol, double *w1, double *w2, double *sc) {
+  for (int j = 0; j < D; ++j) sc[j] = atol + rtol * fabs(y0[j]);
+  double d0 = rms(y0, sc, D);
+  double d1 = rms(f0, sc, D);
+  double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * (d0 / d1);
+  for (int j = 0; j < D; ++j) w1[j] = y0[j] + h0 * f0[j];
+  feval(c, t0 + h0, w1, w2);
+  for (int j = 0; j < D; ++j) w2[j] = w2[j] - f0[j];
+  double d2 = rms(w2, sc, D) / h0;
+  double m = (d1 > d2) ? d1 : d2;
+  double h1 = (m <= 1e-15) ? dmax(1e-6, h0 * 1e-3) : pow(0.01 / m, 1.0 / 5.0);
+  double h = dmin(100.0 * h0, h1);
+  h = dmin(h, t1 - t0);
+  if (!(h > 0.0 && isfinite(h))) h = t1 - t0;
+  return h;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One Dormand-Prince step from (t, y) with step h; k[0] holds f(t, y)       */
+/* on entry (FSAL).  Fills k[1..6], Y (stage inputs, Y[6] = y1 by SSAL).     */
+/* ------------------------------------------------------------------------ */
+static void dp_stages(fctx *c, double t, double h, const double *y, int D, double *k /*[7][D]*/,
+                      double *Y /*[7][D]*/) {
+  for (int j = 0; j < D; ++j) Y[j] = y[j];
+  for (int i = 1; i < NS; ++i) {
+    double *Yi = Y + i * D;
+    for (int j = 0; j < D; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < i; ++l) s = s + DP_A[i][l] * k[l * D + j];
+      Yi[j] = y[j] + h * s;
+    }
+    feval(c, t + DP_C[i] * h, Yi, k + i * D);
+  }
+}
+
+/* Embedded error e = h * sum_i (b_i - bhat_i) k_i, then its weighted RMS norm
+ * against sc = atol + rtol * max(|y|, |y1|). */
+static double dp_error(double h, const double *y, const double *y1, const double *k, int D,
+                       double rtol, double atol, double *e, double *sc) {
+  for (int j = 0; j < D; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < NS; ++i) s = s + (DP_B[i] - DP_BHAT[i]) * k[i * D + j];
+    e[j] = h * s;
+    sc[j] = atol + rtol * dmax(fabs(y[j]), fabs(y1[j]));
+  }
+  return rms(e, sc, D);
+}
+
+/* Dense output at theta in [0,1): y + h * sum_i b_i(theta) k_i, each b_i by
+ * Horner's rule (Sec. 3, "What makes torchode fast?"). */
+static void dp_dense(double theta, double h, const double *y, const double *k, int D,
+                     double *out) {
+  double bt[NS];
+  for (int i = 0; i < NS; ++i) {
+    const double *q = DP_Q[i];
+    bt[i] = theta * (q[0] + theta * (q[1] + theta * (q[2] + theta * q[3])));
+  }
+  for (int j = 0; j < D; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < NS; ++i) s = s + bt[i] * k[i * D + j];
+    out[j] = y[j] + h * s;
+  }
+}
+
+/* Exported: dense-output weights b_i(theta), for the tests. */
+void orc_dense_weights(double theta, double *bt) {
+  for (int i = 0; i < NS; ++i) {
+    const double *q = DP_Q[i];
+    bt[i] = theta * (q[0] + theta * (q[1] + theta * (q[2] + theta * q[3])));
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Input checks (Sec. 3: per-instance bounds and evaluation points).         */
+/* ------------------------------------------------------------------------ */
+static int instance_inputs_valid(double t0, double t1, const double *te, int K) {
+  if (!isfinite(t0) || !isfinite(t1) || t1 < t0) return 0;
+  for (int q = 0; q < K; ++q) {
+    if (!isfinite(te[q]) || te[q] < t0 || te[q] > t1) return 0;
+    if (q > 0 && te[q] < te[q - 1]) return 0;
+  }
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adaptive solve of one instance (Sec. 3; App. A: dopri5 + I controller).   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_field *F;
+  const orc_opts *O;
+  int B, K;
+  const double *y0, *t0, *t1, *t_eval;
+  double *y_eval, *y_final;
+  int32_t *n_acc, *n_rej, *n_feval, *status;
+  const orc_trace *trace;
+  /* replay / adjoint */
+  const double *mesh_t, *mesh_h;
+  const int32_t *mesh_n;
+  int mesh_cap;
+  const double *gy_eval, *gy_final;
+  double *gy0, *gparam; /* gparam: VdP [B], linear [B][D][D] */
+  double **gW_part, **gb_part; /* MLP per-thread partial sums */
+  /* threading */
+  int nthreads;
+} job;
+
+static void fill_nan(double *p, size_t n) {
+  for (size_t j = 0; j < n; ++j) p[j] = NAN;
+}
+
+static void solve_one(const job *J, int i, double *work, double *act) {
+  const orc_field *F = J->F;
+  const orc_opts *O = J->O;
+  const int D = F->D, K = J->K;
+  const double rtol = O->rtol_b ? O->rtol_b[i] : O->rtol;
+  const double atol = O->atol_b ? O->atol_b[i] : O->atol;
+  const double t0 = J->t0[i], t1 = J->t1[i];
+  const double *te = J->t_eval + (size_t)i * K;
+  double *ye = J->y_eval + (size_t)i * K * D;
+  double *yf = J->y_final + (size_t)i * D;
+  double *y = work, *y1 = y + D, *k = y1 + D, *Y = k + NS * D, *e = Y + NS * D, *sc = e + D,
+         *w1 = sc + D, *w2 = w1 + D;
+  fctx c = {F, i, act, 0};
+  int n_acc = 0, n_rej = 0, st = ST_RUNNING, tr = 0;
+
+  fill_nan(ye, (size_t)K * D);
+  if (!instance_inputs_valid(t0, t1, te, K)) {
+    fill_nan(yf, D);
+    J->n_acc[i] = J->n_rej[i] = J->n_feval[i] = 0;
+    J->status[i] = ST_INVALID_INPUT;
+    if (J->trace) J->trace->len[i] = 0;
+    return;
+  }
+  for (int j = 0; j < D; ++j) y[j] = J->y0[(size_t)i * D + j];
+
+  /* evaluation points at t0 take y0 itself */
+  int cur = 0;
+  while (cur < K && te[cur] == t0) {
+    for (int j = 0; j < D; ++j) ye[(size_t)cur * D + j] = y[j];
+    cur++;
+  }
+  if (t1 == t0) {
+    for (int j = 0; j < D; ++j) yf[j] = y[j];
+    J->n_acc[i] = J->n_rej[i] = J->n_feval[i] = 0;
+    J->status[i] = ST_SUCCESS;
+    if (J->trace) J->trace->len[i] = 0;
+    return;
+  }
+
+  double t = t0;
+  feval(&c, t, y, k); /* k1 = f(t0, y0) */
+  double h = (O->h0 > 0.0) ? O->h0
+                           : starting_step(&c, t0, t1, y, k, D, rtol, atol, w1, w2, sc);
+  double err_prev = 1.0;
+  int prev_rejected = 0;
+
+  while (st == ST_RUNNING) {
+    int last = 0;
+    if (t + h >= t1) {
+      h = t1 - t;
+      last = 1;
+    }
+    dp_stages(&c, t, h, y, D, k, Y);
+    for (int j = 0; j < D; ++j) y1[j] = Y[6 * D + j]; /* SSAL: y1 is the last stage input */
+    double err = dp_error(h, y, y1, k, D, rtol, atol, e, sc);
+    int finite = isfinite(err);
+    for (int j = 0; j < D; ++j) finite = finite && isfinite(y1[j]);
+    int accept = finite && err <= 1.0;
+
+    if (J->trace && tr < J->trace->cap) {
+      size_t o = (size_t)i * J->trace->cap + tr;
+      J->trace->t[o] = t;
+      J->trace->h[o] = h;
+      J->trace->err[o] = err;
+      J->trace->accepted[o] = accept;
+      tr++;
+    }
+
+    double h_next;
+    if (accept) {
+      double t_next = last ? t1 : t + h;
+      /* dense output for every evaluation point in (t, t_next] */
+      while (cur < K && te[cur] <= t_next) {
+        double *o = ye + (size_t)cur * D;
+        if (te[cur] == t_next) {
+          for (int j = 0; j < D; ++j) o[j] = y1[j];
+        } else {
+          dp_dense((te[cur] - t) / h, h, y, k, D, o);
+        }
+        cur++;
+      }
+      /* controller: factor = safety * err^-beta1 * err_prev^beta2 */
+      double fac;
+      if (err == 0.0) {
+        fac = O->fac_max;
+      } else {
+        fac = O->safety * pow(err, -O->beta1);
+        if (O->beta2 != 0.0) fac = fac * pow(err_prev, O->beta2);
+      }
+      fac = dmin(dmax(fac, O->fac_min), O->fac_max);
+      if (prev_rejected) fac = dmin(fac, 1.0);
+      h_next = h * fac;
+      err_prev = dmax(err, 1e-4);
+      prev_rejected = 0;
+      n_acc++;
+      t = t_next;
+      for (int j = 0; j < D; ++j) {
+        y[j] = y1[j];
+        k[j] = k[6 * D + j]; /* FSAL */
+      }
+      if (last) st = ST_SUCCESS;
+    } else {
+      double fac = finite ? dmin(dmax(O->safety * pow(err, -O->beta1), O->fac_min), 1.0)
+                          : O->fac_min;
+      h_next = h * fac;
+      prev_rejected = 1;
+      n_rej++;
+    }
+    h = h_next;
+    if (st == ST_RUNNING) {
+      double scale = dmax(fabs(t), fabs(t1));
+      if (t + h == t || h < 1e-14 * scale || !(h > 0.0))
+        st = finite ? ST_DT_UNDERFLOW : ST_NONFINITE;
+      else if (n_acc + n_rej >= O->max_steps)
+        st = ST_MAX_STEPS;
+    }
+  }
+  for (int j = 0; j < D; ++j) yf[j] = y[j];
+  J->n_acc[i] = n_acc;
+  J->n_rej[i] = n_rej;
+  J->n_feval[i] = (int32_t)c.nfe;
+  J->status[i] = st;
+  if (J->trace) J->trace->len[i] = tr;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fixed-mesh replay (no controller): the map whose discrete adjoint the     */
+/* gradient is.  mesh_t[i][n], mesh_h[i][n] for n < mesh_n[i]; the last step */
+/* ends at t1[i].  Also returns every step-start state when ys != NULL.      */
+/* ------------------------------------------------------------------------ */
+static double mesh_end(const job *J, int i, int n) {
+  const int N = J->mesh_n[i];
+  return (n + 1 < N) ? J->mesh_t[(size_t)i * J->mesh_cap + n + 1] : J->t1[i];
+}
+
+static void replay_one(const job *J, int i, double *work, double *act, double *ys /*[N+1][D]*/) {
+  const orc_field *F = J->F;
+  const int D = F->D, K = J->K, N = J->mesh_n[i];
+  const double t0 = J->t0[i];
+  const double *te = J->t_eval + (size_t)i * K;
+  double *ye = J->y_eval + (size_t)i * K * D;
+  double *y = work, *k = y + D, *Y = k + NS * D;
+  fctx c = {F, i, act, 0};
+  for (int j = 0; j < D; ++j) y[j] = J->y0[(size_t)i * D + j];
+  fill_nan(ye, (size_t)K * D);
+  int cur = 0;
+  while (cur < K && te[cur] == t0) {
+    for (int j = 0; j < D; ++j) ye[(size_t)cur * D + j] = y[j];
+    cur++;
+  }
+  if (ys)
+    for (int j = 0; j < D; ++j) ys[j] = y[j];
+  for (int n = 0; n < N; ++n) {
+    const double t = J->mesh_t[(size_t)i * J->mesh_cap + n];
+    const double h = J->mesh_h[(size_t)i * J->mesh_cap + n];
+    const double t_next = mesh_end(J, i, n);
+    feval(&c, t, y, k);
+    dp_stages(&c, t, h, y, D, k, Y);
+    const double *y1 = Y + 6 * D;
+    while (cur < K && te[cur] <= t_next) {
+      double *o = ye + (size_t)cur * D;
+      if (te[cur] == t_next) {
+        for (int j = 0; j < D; ++j) o[j] = y1[j];
+      } else {
+        dp_dense((te[cur] - t) / h, h, y, k, D, o);
+      }
+      cur++;
+    }
+    for (int j = 0; j < D; ++j) y[j] = y1[j];
+    if (ys)
+      for (int j = 0; j < D; ++j) ys[(size_t)(n + 1) * D + j] = y[j];
+  }
+  for (int j = 0; j < D; ++j) J->y_final[(size_t)i * D + j] = y[j];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vector-Jacobian products of the fields: gy += J_f(y)^T v, and the         */
+/* parameter cotangents.                                                     */
+/* ------------------------------------------------------------------------ */
+static void vjp(const job *J, int i, double t, const double *y, const double *v, double *gy,
+                double *gparam_i, double *gW, double *gb, double *act, double *dscr) {
+  const orc_field *F = J->F;
+  const int D = F->D;
+  if (F->kind == ORC_VDP) {
+    /* J = [[0, 1], [-2 mu y1 y2 - 1, mu (1 - y1^2)]] */
+    const double mu = F->mu[i];
+    gy[0] = gy[0] + v[1] * (-2.0 * mu * y[0] * y[1] - 1.0);
+    gy[1] = gy[1] + (v[0] + v[1] * (mu * (1.0 - y[0] * y[0])));
+    gparam_i[0] = gparam_i[0] + v[1] * ((1.0 - y[0] * y[0]) * y[1]);
+  } else if (F->kind == ORC_LINEAR) {
+    const double *A = F->A + (size_t)i * D * D;
+    for (int cidx = 0; cidx < D; ++cidx) {
+      double s = 0.0;
+      for (int r = 0; r < D; ++r) s = s + A[r * D + cidx] * v[r];
+      gy[cidx] = gy[cidx] + s;
+    }
+    for (int r = 0; r < D; ++r)
+      for (int cidx = 0; cidx < D; ++cidx)
+        gparam_i[r * D + cidx] = gparam_i[r * D + cidx] + v[r] * y[cidx];
+  } else {
+    /* forward pass storing every layer input, then backpropagation */
+    const int L = F->n_layers;
+    double out_dummy[256];
+    double *outp = (D <= 256) ? out_dummy : NULL;
+    f_mlp(F, t, y, outp, act);
+    int off[MLP_MAX_LAYERS + 1];
+    off[0] = 0;
+    for (int l = 0; l < L; ++l) off[l + 1] = off[l] + F->widths[l];
+    int maxw = mlp_max_width(F);
+    double *delta = dscr, *ga = dscr + maxw;
+    for (int r = 0; r < D; ++r) delta[r] = v[r];
+    size_t woff = 0, boff = 0;
+    size_t wstart[MLP_MAX_LAYERS], bstart[MLP_MAX_LAYERS];
+    for (int l = 0; l < L; ++l) {
+      wstart[l] = woff;
+      bstart[l] = boff;
+      woff += (size_t)F->widths[l] * F->widths[l + 1];
+      boff += F->widths[l + 1];
+    }
+    for (int l = L - 1; l >= 0; --l) {
+      const int nin = F->widths[l], nout = F->widths[l + 1];
+      const double *a = act + off[l];
+      const double *W = F->W[l];
+      double *gWl = gW + wstart[l], *gbl = gb + bstart[l];
+      for (int r = 0; r < nout; ++r) {
+        gbl[r] = gbl[r] + delta[r];
+        for (int cidx = 0; cidx < nin; ++cidx)
+          gWl[(size_t)r * nin + cidx] = gWl[(size_t)r * nin + cidx] + delta[r] * a[cidx];
+      }
+      for (int cidx = 0; cidx < nin; ++cidx) {
+        double s = 0.0;
+        for (int r = 0; r < nout; ++r) s = s + W[(size_t)r * nin + cidx] * delta[r];
+        ga[cidx] = s;
+      }
+      if (l > 0) {
+        for (int cidx = 0; cidx < nin; ++cidx) delta[cidx] = ga[cidx] * (1.0 - a[cidx] * a[cidx]);
+      } else {
+        for (int r = 0; r < D; ++r) gy[r] = gy[r] + ga[r]; /* drop the t input */
+      }
+    }
+  }
+}
+
+/* Discrete adjoint of one instance over its fixed mesh (the reverse of
+ * replay_one).  For step n with stages Y_i, k_i = f(t_n + c_i h, Y_i):
+ *   kbar_i = h b_i ybar_{n+1} + sum_{tau in step} h b_i(theta_tau) ybar_tau
+ *   for i = 7..1: g_i = J_f(Y_i)^T kbar_i, kbar_j += h a_ij g_i (j < i)
+ *   ybar_n = ybar_{n+1} + sum_tau ybar_tau + sum_i g_i. */
+static void adjoint_one(const job *J, int i, double *work, double *act, double *dscr,
+                        double *gW, double *gb) {
+  const orc_field *F = J->F;
+  const int D = F->D, K = J->K, N = J->mesh_n[i];
+  const double t0 = J->t0[i];
+  const double *te = J->t_eval + (size_t)i * K;
+  const double *gye = J->gy_eval ? J->gy_eval + (size_t)i * K * D : NULL;
+  double *ys = (double *)malloc(sizeof(double) * (size_t)(N + 1) * D);
+  double *yb = work, *k = yb + D, *Y = k + NS * D, *kb = Y + NS * D, *g = kb + NS * D;
+  double *scratch = g + D;
+  double *gp = NULL;
+  if (F->kind == ORC_VDP) gp = J->gparam + i;
+  if (F->kind == ORC_LINEAR) gp = J->gparam + (size_t)i * D * D;
+  if (gp) {
+    int np = (F->kind == ORC_VDP) ? 1 : D * D;
+    for (int p = 0; p < np; ++p) gp[p] = 0.0;
+  }
+
+  /* forward replay to recover the step-start states */
+  replay_one(J, i, scratch, act, ys);
+  fctx c = {F, i, act, 0};
+
+  for (int j = 0; j < D; ++j) yb[j] = J->gy_final ? J->gy_final[(size_t)i * D + j] : 0.0;
+  int cur = K - 1;
+  for (int n = N - 1; n >= 0; --n) {
+    const double t = J->mesh_t[(size_t)i * J->mesh_cap + n];
+    const double h = J->mesh_h[(size_t)i * J->mesh_cap + n];
+    const double t_next = mesh_end(J, i, n);
+    const double *y = ys + (size_t)n * D;
+    feval(&c, t, y, k);
+    dp_stages(&c, t, h, y, D, k, Y);
+    /* cotangents of the stage values */
+    for (int s = 0; s < NS; ++s)
+      for (int j = 0; j < D; ++j) kb[s * D + j] = h * DP_B[s] * yb[j];
+    while (cur >= 0 && te[cur] > t) {
+      if (gye) {
+        const double *gq = gye + (size_t)cur * D;
+        if (te[cur] == t_next) {
+          /* this output is y_{n+1} itself: y_{n+1} = y_n + h sum b_i k_i */
+          for (int s = 0; s < NS; ++s)
+            for (int j = 0; j < D; ++j) kb[s * D + j] = kb[s * D + j] + h * DP_B[s] * gq[j];
+        } else {
+          double bt[NS];
+          orc_dense_weights((te[cur] - t) / h, bt);
+          for (int s = 0; s < NS; ++s)
+            for (int j = 0; j < D; ++j) kb[s * D + j] = kb[s * D + j] + h * bt[s] * gq[j];
+        }
+        for (int j = 0; j < D; ++j) yb[j] = yb[j] + gq[j];
+      }
+      cur--;
+    }
+    for (int s = NS - 1; s >= 0; --s) {
+      for (int j = 0; j < D; ++j) g[j] = 0.0;
+      vjp(J, i, t + DP_C[s] * h, Y + s * D, kb + s * D, g, gp, gW, gb, act, dscr);
+      for (int l = 0; l < s; ++l)
+        for (int j = 0; j < D; ++j) kb[l * D + j] = kb[l * D + j] + h * DP_A[s][l] * g[j];
+      for (int j = 0; j < D; ++j) yb[j] = yb[j] + g[j];
+    }
+  }
+  /* evaluation points at t0 are y0 itself */
+  while (cur >= 0) {
+    if (gye && te[cur] == t0)
+      for (int j = 0; j < D; ++j) yb[j] = yb[j] + gye[(size_t)cur * D + j];
+    cur--;
+  }
+  for (int j = 0; j < D; ++j) J->gy0[(size_t)i * D + j] = yb[j];
+  free(ys);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Threading over instances (independent by construction, Sec. 3).          */
+/* ------------------------------------------------------------------------ */
+enum { MODE_SOLVE = 0, MODE_REPLAY = 1, MODE_ADJOINT = 2 };
+
+typedef struct {
+  const job *J;
+  int mode, tid, lo, hi;
+} worker_arg;
+
+static size_t mlp_params(const orc_field *F, size_t *nb) {
+  size_t w = 0, b = 0;
+  for (int l = 0; l < F->n_layers; ++l) {
+    w += (size_t)F->widths[l] * F->widths[l + 1];
+    b += F->widths[l + 1];
+  }
+  if (nb) *nb = b;
+  return w;
+}
+
+static void *worker(void *p) {
+  worker_arg *a = (worker_arg *)p;
+  const job *J = a->J;
+  const int D = J->F->D;
+  int acts = 0, maxw = 8;
+  if (J->F->kind == ORC_MLP) {
+    for (int l = 0; l <= J->F->n_layers; ++l) acts += J->F->widths[l];
+    maxw = mlp_max_width(J->F);
+  }
+  double *work = (double *)malloc(sizeof(double) * (size_t)(40 * D + 64));
+  double *act = (double *)malloc(sizeof(double) * (size_t)(acts + 8));
+  double *dscr = (double *)malloc(sizeof(double) * (size_t)(2 * maxw + 8));
+  for (int i = a->lo; i < a->hi; ++i) {
+    if (a->mode == MODE_SOLVE) solve_one(J, i, work, act);
+    else if (a->mode == MODE_REPLAY) replay_one(J, i, work, act, NULL);
+    else {
+      double *gW = J->gW_part ? J->gW_part[a->tid] : NULL;
+      double *gb = J->gb_part ? J->gb_part[a->tid] : NULL;
+      adjoint_one(J, i, work, act, dscr, gW, gb);
+    }
+  }
+  free(work);
+  free(act);
+  free(dscr);
+  return NULL;
+}
+
+static int default_threads(void) {
+  cpu_set_t s;
+  if (sched_getaffinity(0, sizeof(s), &s) == 0) return CPU_COUNT(&s);
+  long n = sysconf(_SC_NPROCESSORS_ONLN);
+  return n > 0 ? (int)n : 1;
+}
+
+static int run(job *J, int mode, int nthreads) {
+  if (nthreads <= 0) nthreads = default_threads();
+  if (nthreads > J->B) nthreads = J->B > 0 ? J->B : 1;
+  J->nthreads = nthreads;
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
+  worker_arg *args = (worker_arg *)malloc(sizeof(worker_arg) * nthreads);
+  for (int k = 0; k < nthreads; ++k) {
+    args[k].J = J;
+    args[k].mode = mode;
+    args[k].tid = k;
+    args[k].lo = (int)((long)J->B * k / nthreads);
+    args[k].hi = (int)((long)J->B * (k + 1) / nthreads);
+  }
+  for (int k = 1; k < nthreads; ++k) pthread_create(&th[k], NULL, worker, &args[k]);
+  if (nthreads > 0) worker(&args[0]);
+  for (int k = 1; k < nthreads; ++k) pthread_join(th[k], NULL);
+  free(th);
+  free(args);
+  return nthreads;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported entry points.  All arrays are host arrays, instance-major.       */
+/* Return value: the number of threads used.                                 */
+/* ------------------------------------------------------------------------ */
+int orc_solve(const orc_field *F, const orc_opts *O, int B, const double *y0, const double *t0,
+              const double *t1, const double *t_eval, int K, double *y_eval, double *y_final,
+              int32_t *n_acc, int32_t *n_rej, int32_t *n_feval, int32_t *status,
+              const orc_trace *trace, int nthreads) {
+  job J;
+  memset(&J, 0, sizeof(J));
+  J.F = F;
+  J.O = O;
+  J.B = B;
+  J.K = K;
+  J.y0 = y0;
+  J.t0 = t0;
+  J.t1 = t1;
+  J.t_eval = t_eval;
+  J.y_eval = y_eval;
+  J.y_final = y_final;
+  J.n_acc = n_acc;
+  J.n_rej = n_rej;
+  J.n_feval = n_feval;
+  J.status = status;
+  J.trace = trace;
+  return run(&J, MODE_SOLVE, nthreads);
+}
+
+int orc_replay(const orc_field *F, int B, const double *y0, const double *t0, const double *t1,
+               const double *mesh_t, const double *mesh_h, const int32_t *mesh_n, int mesh_cap,
+               const double *t_eval, int K, double *y_eval, double *y_final, int nthreads) {
+  job J;
+  memset(&J, 0, sizeof(J));
+  J.F = F;
+  J.B = B;
+  J.K = K;
+  J.y0 = y0;
+  J.t0 = t0;
+  J.t1 = t1;
+  J.t_eval = t_eval;
+  J.y_eval = y_eval;
+  J.y_final = y_final;
+  J.mesh_t = mesh_t;
+  J.mesh_h = mesh_h;
+  J.mesh_n = mesh_n;
+  J.mesh_cap = mesh_cap;
+  return run(&J, MODE_REPLAY, nthreads);
+}
+
+/* gparam: VdP [B] (d/dmu), linear [B][D][D] (d/dA); MLP: gW[l], gb[l] summed
+ * over the batch (per-thread partials added in thread order). */
+int orc_adjoint(const orc_field *F, int B, const double *y0, const double *t0, const double *t1,
+                const double *mesh_t, const double *mesh_h, const int32_t *mesh_n, int mesh_cap,
+                const double *t_eval, int K, const double *gy_eval, const double *gy_final,
+                double *gy0, double *gparam, double *const *gW, double *const *gb,
+                int nthreads) {
+  job J;
+  memset(&J, 0, sizeof(J));
+  J.F = F;
+  J.B = B;
+  J.K = K;
+  J.y0 = y0;
+  J.t0 = t0;
+  J.t1 = t1;
+  J.t_eval = t_eval;
+  J.mesh_t = mesh_t;
+  J.mesh_h = mesh_h;
+  J.mesh_n = mesh_n;
+  J.mesh_cap = mesh_cap;
+  J.gy_eval = gy_eval;
+  J.gy_final = gy_final;
+  J.gy0 = gy0;
+  J.gparam = gparam;
+  double *ye_dummy = (double *)malloc(sizeof(double) * ((size_t)B * K * F->D + 1));
+  double *yf_dummy = (double *)malloc(sizeof(double) * ((size_t)B * F->D + 1));
+  J.y_eval = ye_dummy;
+  J.y_final = yf_dummy;
+  int T = nthreads <= 0 ? default_threads() : nthreads;
+  if (T > B) T = B > 0 ? B : 1;
+  size_t nb = 0, nw = 0;
+  if (F->kind == ORC_MLP) {
+    nw = mlp_params(F, &nb);
+    J.gW_part = (double **)malloc(sizeof(double *) * T);
+    J.gb_part = (double **)malloc(sizeof(double *) * T);
+    for (int k = 0; k < T; ++k) {
+      J.gW_part[k] = (double *)calloc(nw, sizeof(double));
+      J.gb_part[k] = (double *)calloc(nb, sizeof(double));
+    }
+  }
+  int used = run(&J, MODE_ADJOINT, T);
+  if (F->kind == ORC_MLP) {
+    size_t wo = 0, bo = 0;
+    for (int l = 0; l < F->n_layers; ++l) {
+      size_t nwl = (size_t)F->widths[l] * F->widths[l + 1], nbl = F->widths[l + 1];
+      for (size_t p = 0; p < nwl; ++p) {
+        double s = 0.0;
+        for (int k = 0; k < used; ++k) s = s + J.gW_part[k][wo + p];
+        gW[l][p] = s;
+      }
+      for (size_t p = 0; p < nbl; ++p) {
+        double s = 0.0;
+        for (int k = 0; k < used; ++k) s = s + J.gb_part[k][bo + p];
+        gb[l][p] = s;
+      }
+      wo += nwl;
+      bo += nbl;
+    }
+    for (int k = 0; k < T; ++k) {
+      free(J.gW_part[k]);
+      free(J.gb_part[k]);
+    }
+    free(J.gW_part);
+    free(J.gb_part);
+  }
+  free(ye_dummy);
+  free(yf_dummy);
+  return used;
+}

@@ -1,0 +1,419 @@
+"""Pins of the FP64 oracle against what mathematics fixes: closed forms,
+observed convergence order, brute force on tiny inputs, the controller's
+steady state, the first-step error estimate of the linear test equation,
+statuses and independence (Sec. 3, Sec. 4.1, App. A, App. C)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import sympy as sp
+
+import oracle
+import rk_exact as rk
+from oracle.oracle import mesh_from_trace
+from paper_2210_12375_b300 import workloads
+
+
+# ---------------------------------------------------------------- helpers
+def rk4_reference(f, y0, t_end, n):
+    """Classical RK4 with n uniform steps (independent of the oracle)."""
+    y = np.array(y0, dtype=np.float64)
+    h = t_end / n
+    for _ in range(n):
+        k1 = f(y)
+        k2 = f(y + 0.5 * h * k1)
+        k3 = f(y + 0.5 * h * k2)
+        k4 = f(y + h * k3)
+        y = y + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+    return y
+
+
+def vdp_rhs(mu):
+    def f(y):
+        return np.stack([y[:, 1], mu * (1 - y[:, 0] ** 2) * y[:, 1] - y[:, 0]], axis=1)
+    return f
+
+
+def linear_exact(w, t):
+    """Q diag(exp(-lambda t)) Q^T y0 for every instance and time."""
+    Q, lam, y0 = w["field"]["Q"], w["field"]["lam"], w["y0"]
+    c = np.einsum("bji,bj->bi", Q, y0)  # Q^T y0
+    ex = np.exp(-lam[:, None, :] * t[:, :, None])  # [B,K,D]
+    return np.einsum("bij,bkj->bki", Q, ex * c[:, None, :])
+
+
+def uniform_mesh(B, t1, N):
+    mt = np.zeros((B, N))
+    mh = np.zeros((B, N))
+    for i in range(B):
+        h = t1[i] / N
+        mt[i] = np.arange(N) * h
+        mh[i] = h
+    return mt, mh, np.full(B, N, np.int32)
+
+
+# ---------------------------------------------------------------- closed forms
+def test_linear_closed_form_tight_tolerance():
+    w = workloads.make(2, B=24)
+    r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], w["t_eval"],
+                     dict(rtol=1e-11, atol=1e-11))
+    assert (r["status"] == 0).all()
+    ex = linear_exact(w, w["t_eval"])
+    err = np.abs(r["y_eval"] - ex).max()
+    assert err < 1e-9, err
+    # the last evaluation point is t1 and must equal y_final exactly
+    assert np.array_equal(r["y_eval"][:, -1], r["y_final"])
+    # t_eval == t0 gives y0 exactly
+    assert np.array_equal(r["y_eval"][:, 0], w["y0"])
+
+
+def test_linear_closed_form_config_tolerance_band():
+    w = workloads.make(2, B=64)
+    r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], w["t_eval"],
+                     dict(rtol=w["rtol"], atol=w["atol"]))
+    ex = linear_exact(w, w["t_eval"])
+    band = 10 * (w["atol"] + w["rtol"] * np.abs(ex))
+    assert (np.abs(r["y_eval"] - ex) <= band).all()
+
+
+def test_mlp_scalar_closed_form():
+    """D=1, one hidden unit: y' = v tanh(w y) has sinh(w y(t)) = sinh(w y0)
+    exp(w v t); pins the MLP wiring ([y; t] input, tanh hidden, linear out)
+    and the solver on a nonlinear field."""
+    w_, v_ = 0.8, -1.3
+    field = {"kind": "mlp", "W": [np.array([[w_, 0.0]]), np.array([[v_]])],
+             "b": [np.zeros(1), np.zeros(1)]}
+    B = 5
+    y0 = np.linspace(-1.5, 2.0, B)[:, None]
+    t0 = np.zeros(B)
+    t1 = np.full(B, 3.0)
+    te = np.linspace(0, 3.0, 7)[None, :].repeat(B, 0)
+    r = oracle.solve(field, y0, t0, t1, te, dict(rtol=1e-11, atol=1e-11))
+    ex = np.arcsinh(np.sinh(w_ * y0) * np.exp(w_ * v_ * te)) / w_
+    assert np.abs(r["y_eval"][..., 0] - ex).max() < 1e-9
+
+
+def test_mlp_field_known_values():
+    a = math.atanh(0.5)
+    # column 0 is y, column 1 is t; bias of the hidden layer, linear output
+    f_y = {"kind": "mlp", "W": [np.array([[a, 0.0]]), np.array([[3.0]])],
+           "b": [np.zeros(1), np.array([0.25])]}
+    assert abs(oracle.field_eval(f_y, 0, 7.0, [1.0])[0] - (1.5 + 0.25)) < 1e-15
+    f_t = {"kind": "mlp", "W": [np.array([[0.0, a]]), np.array([[3.0]])],
+           "b": [np.zeros(1), np.zeros(1)]}
+    assert abs(oracle.field_eval(f_t, 0, 1.0, [5.0])[0] - 1.5) < 1e-15
+    f_b = {"kind": "mlp", "W": [np.array([[0.0, 0.0]]), np.array([[-2.0]])],
+           "b": [np.array([a]), np.zeros(1)]}
+    assert abs(oracle.field_eval(f_b, 0, 0.0, [0.0])[0] + 1.0) < 1e-15
+    # two hidden layers: tanh(tanh(.)) composition
+    f_2 = {"kind": "mlp", "W": [np.array([[0.3, 0.0]]), np.array([[0.5]]), np.array([[1.0]])],
+           "b": [np.zeros(1), np.zeros(1), np.zeros(1)]}
+    assert abs(oracle.field_eval(f_2, 0, 0.0, [1.0])[0] - math.tanh(0.5 * math.tanh(0.3))) < 1e-15
+
+
+def test_mlp_odd_symmetry_bitwise():
+    """With zero biases and no t input the MLP is odd, so the solution from
+    -y0 is exactly the negated solution from y0."""
+    w = workloads.make(4, B=4)
+    W = [x.copy() for x in w["field"]["W"]]
+    W[0][:, -1] = 0.0
+    field = {"kind": "mlp", "W": W, "b": w["field"]["b"]}
+    y0 = w["y0"]
+    y0s = np.concatenate([y0, -y0])
+    t0 = np.zeros(8)
+    t1 = np.ones(8)
+    te = np.concatenate([w["t_eval"], w["t_eval"]])
+    r = oracle.solve(field, y0s, t0, t1, te, dict(rtol=1e-6, atol=1e-6))
+    assert np.array_equal(r["y_eval"][:4], -r["y_eval"][4:])
+    assert np.array_equal(r["n_acc"][:4], r["n_acc"][4:])
+
+
+# ---------------------------------------------------------------- convergence
+def test_observed_order_five_fixed_step_vdp():
+    B = 3
+    mu = np.array([0.5, 1.0, 2.0])
+    y0 = np.array([[2.0, 0.0], [1.0, -1.0], [-0.5, 1.5]])
+    T = 2.0
+    ref = rk4_reference(vdp_rhs(mu), y0, T, 20000)
+    errs = []
+    for N in (20, 40, 80):
+        mt, mh, mn = uniform_mesh(B, np.full(B, T), N)
+        r = oracle.replay({"kind": "vdp", "mu": mu}, y0, np.zeros(B), np.full(B, T), mt, mh, mn)
+        errs.append(np.abs(r["y_final"] - ref).max(axis=1))
+    errs = np.array(errs)
+    # order >= 5: halving h divides the error by at least ~2^5 (dopri5's
+    # small principal error constant makes the pre-asymptotic ratio larger)
+    for k in range(2):
+        ratio = errs[k] / errs[k + 1]
+        assert (ratio > 26).all(), ratio
+
+
+def test_dense_output_order_fixed_step():
+    """Mid-step dense output converges with order >= 4 (HNW Sec. II.6)."""
+    B = 2
+    mu = np.array([1.0, 1.5])
+    y0 = np.array([[2.0, 0.0], [0.5, 0.5]])
+    T = 2.0
+    errs = []
+    for N in (16, 32, 64):
+        mt, mh, mn = uniform_mesh(B, np.full(B, T), N)
+        # evaluation points in the middle of steps that are common to all N
+        te = np.array([[0.3 * T / 16 + j * T / 16 for j in range(16)]] * B)
+        r = oracle.replay({"kind": "vdp", "mu": mu}, y0, np.zeros(B), np.full(B, T), mt, mh, mn,
+                          te)
+        ref = np.stack([rk4_reference(vdp_rhs(mu), y0, tj, 8000) for tj in te[0]], axis=1)
+        errs.append(np.abs(r["y_eval"] - ref).max())
+    assert errs[0] / errs[1] > 14 and errs[1] / errs[2] > 14, errs
+
+
+def test_adaptive_vdp_vs_brute_force():
+    w = workloads.make(1, B=4)
+    T = 3.0
+    t1 = np.full(4, T)
+    r = oracle.solve(w["field"], w["y0"], w["t0"], t1, None, dict(rtol=1e-12, atol=1e-12))
+    ref = rk4_reference(vdp_rhs(w["field"]["mu"]), w["y0"], T, 30000)
+    assert np.abs(r["y_final"] - ref).max() < 1e-9
+
+
+def test_tolerance_proportionality_vdp():
+    """Global error falls roughly in proportion to the tolerance (a controller
+    that does not track err <= 1 fails this)."""
+    w = workloads.make(1, B=16)
+    ref = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], w["t_eval"],
+                       dict(rtol=1e-13, atol=1e-13))
+    e = []
+    for tol in (1e-5, 1e-7, 1e-9):
+        r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], w["t_eval"],
+                         dict(rtol=tol, atol=tol))
+        e.append(np.abs(r["y_eval"] - ref["y_eval"]).max())
+    assert 10 < e[0] / e[1] < 1000 and 10 < e[1] / e[2] < 1000, e
+
+
+# ---------------------------------------------------------------- controller
+@pytest.mark.parametrize("beta1,beta2", [(0.2, 0.0), (0.14, 0.08)])
+def test_controller_steady_state(beta1, beta2):
+    """For a smooth problem in the asymptotic regime (err ~ C h^p) the
+    controller factor safety*err^-b1*err_prev^b2 drives accepted errors to
+    the fixed point err* = safety^(1/(b1-b2)), whatever p is (App. C: the
+    PI(D) family; App. A: I controller, b2 = 0)."""
+    field = {"kind": "linear", "A": np.array([[[1.0]]])}
+    r = oracle.solve(field, np.ones((1, 1)), np.zeros(1), np.array([12.0]), None,
+                     dict(rtol=1e-10, atol=0.0, beta1=beta1, beta2=beta2), trace_cap=10000)
+    L = r["trace_len"][0]
+    acc = r["trace_accepted"][0, :L].astype(bool)
+    errs = r["trace_err"][0, :L][acc][:-1]  # drop the clipped last step
+    target = 0.9 ** (1.0 / (beta1 - beta2))
+    tail = errs[len(errs) // 2:]
+    assert np.abs(tail / target - 1).max() < 0.03, (tail.min(), tail.max(), target)
+
+
+def test_controller_clamps_and_no_growth_after_reject():
+    w = workloads.make(1, B=8)
+    # tiny first step: err ~ 0 -> factor clamped to fac_max exactly
+    r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], None,
+                     dict(rtol=1e-7, atol=1e-7, h0=1e-9), trace_cap=5000)
+    assert np.allclose(r["trace_h"][:, 1], 1e-8, rtol=0, atol=0)
+    # huge first step: rejected; every step right after a rejection does not grow
+    r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], None,
+                     dict(rtol=1e-7, atol=1e-7, h0=2.0), trace_cap=5000)
+    seen = 0
+    for i in range(8):
+        L = r["trace_len"][i]
+        acc = r["trace_accepted"][i, :L]
+        h = r["trace_h"][i, :L]
+        assert acc[0] == 0
+        for n in range(1, L - 1):
+            if acc[n - 1] == 0:
+                assert h[n] <= h[n - 1] * (1 + 1e-15)  # reject shrinks
+                if acc[n] == 1 and n + 1 < L:
+                    assert h[n + 1] <= h[n] * (1 + 1e-15) or n + 1 == L - 1
+                    seen += 1
+    assert seen > 0
+
+
+def test_first_step_error_estimate_matches_exact_polynomial():
+    """y' = diag(l1, l2) y: the first attempt's error estimate is
+    e_j = E(h l_j) y0_j with E the embedded error polynomial, exact from the
+    tableau; the norm is the per-instance weighted RMS."""
+    z, Rz, Ez = rk.linear_step_polys()
+    lams = (-3.0, 0.7)
+    A = np.array([[[lams[0], 0.0], [0.0, lams[1]]]])
+    y0 = np.array([[1.3, -0.4]])
+    h = 0.05
+    rtol, atol = 1e-6, 1e-9
+    r = oracle.solve({"kind": "linear", "A": A}, y0, np.zeros(1), np.array([1.0]), None,
+                     dict(rtol=rtol, atol=atol, h0=h), trace_cap=4)
+    q = []
+    for j in range(2):
+        zz = sp.Float(h * lams[j], 30)
+        e = float(Ez.subs(z, zz)) * y0[0, j]
+        y1 = float(Rz.subs(z, zz)) * y0[0, j]
+        sc = atol + rtol * max(abs(y0[0, j]), abs(y1))
+        q.append(e / sc)
+    expect = math.sqrt((q[0] ** 2 + q[1] ** 2) / 2)
+    assert abs(r["trace_err"][0, 0] / expect - 1) < 1e-9
+    # and with D = 1 the norm reduces to |e|/sc
+    r1 = oracle.solve({"kind": "linear", "A": A[:, :1, :1]}, y0[:, :1], np.zeros(1),
+                      np.array([1.0]), None, dict(rtol=rtol, atol=atol, h0=h), trace_cap=4)
+    assert abs(r1["trace_err"][0, 0] / abs(q[0]) - 1) < 1e-9
+
+
+# ---------------------------------------------------------------- statuses
+def test_statuses_and_counters():
+    w = workloads.make(1, B=8)
+    f, y0, t0, t1, te = w["field"], w["y0"].copy(), w["t0"].copy(), w["t1"].copy(), \
+        w["t_eval"].copy()
+    te[1, 3], te[1, 4] = te[1, 4], te[1, 3]  # decreasing
+    te[2, 5] = t1[2] + 1.0                   # outside [t0, t1]
+    t1[3] = -1.0                             # t1 < t0
+    y0[4, 0] = np.nan                        # non-finite state
+    t1[5] = t0[5]                            # empty range
+    te[5] = t0[5]
+    r = oracle.solve(f, y0, t0, t1, te, dict(rtol=1e-7, atol=1e-7))
+    st = r["status"]
+    assert list(st[[1, 2, 3]]) == [4, 4, 4]
+    assert st[4] == 3
+    assert st[5] == 0 and r["n_acc"][5] == 0 and r["n_feval"][5] == 0
+    assert np.array_equal(r["y_eval"][5], np.repeat(y0[5:6], te.shape[1], 0))
+    for i in (0, 6, 7):
+        assert st[i] == 0
+        assert r["n_feval"][i] == 2 + 6 * (r["n_acc"][i] + r["n_rej"][i])
+    assert np.isnan(r["y_eval"][1]).all() and np.isnan(r["y_final"][1]).all()
+    # max_steps
+    r = oracle.solve(f, w["y0"], w["t0"], w["t1"], None, dict(rtol=1e-7, atol=1e-7,
+                                                               max_steps=5))
+    assert (r["status"] == 1).all() and ((r["n_acc"] + r["n_rej"]) == 5).all()
+    # given first step: one evaluation for k1, none for the heuristic
+    r = oracle.solve(f, w["y0"], w["t0"], w["t1"], None, dict(rtol=1e-7, atol=1e-7, h0=1e-3))
+    assert (r["n_feval"] == 1 + 6 * (r["n_acc"] + r["n_rej"])).all()
+
+
+def test_instances_are_independent_bitwise():
+    """Sec. 3 / Sec. 4.1: an instance's result does not depend on its batch."""
+    w = workloads.make(1, B=12)
+    full = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], w["t_eval"],
+                        dict(rtol=1e-7, atol=1e-7))
+    perm = np.random.default_rng(3).permutation(12)
+    fp = {"kind": "vdp", "mu": w["field"]["mu"][perm]}
+    sh = oracle.solve(fp, w["y0"][perm], w["t0"][perm], w["t1"][perm], w["t_eval"][perm],
+                      dict(rtol=1e-7, atol=1e-7), nthreads=3)
+    for k in ("y_eval", "y_final", "n_acc", "n_rej", "status"):
+        assert np.array_equal(full[k][perm], sh[k])
+    one = oracle.solve({"kind": "vdp", "mu": w["field"]["mu"][5:6]}, w["y0"][5:6],
+                       w["t0"][5:6], w["t1"][5:6], w["t_eval"][5:6], dict(rtol=1e-7, atol=1e-7))
+    assert np.array_equal(one["y_eval"][0], full["y_eval"][5])
+
+
+# ---------------------------------------------------------------- adjoint
+def _loss_replay(field, w, mt, mh, mn, gy_eval):
+    r = oracle.replay(field, w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"])
+    return float((gy_eval * r["y_eval"]).sum())
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_adjoint_vs_central_fd_frozen_mesh(cfg):
+    w = workloads.make(cfg, B=3)
+    tol = 1e-6
+    r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], w["t_eval"],
+                     dict(rtol=tol, atol=tol), trace_cap=20000)
+    mt, mh, mn = mesh_from_trace(r)
+    rng = np.random.default_rng(11)
+    gye = rng.standard_normal(r["y_eval"].shape)
+    adj = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"], gye)
+    D = w["y0"].shape[1]
+    num = np.zeros_like(w["y0"])
+    for i in range(3):
+        for j in range(D):
+            eps = 1e-6 * max(1.0, abs(w["y0"][i, j]))
+            wp = dict(w, y0=w["y0"].copy())
+            wp["y0"][i, j] += eps
+            lp = _loss_replay(w["field"], wp, mt, mh, mn, gye)
+            wp["y0"][i, j] -= 2 * eps
+            lm = _loss_replay(w["field"], wp, mt, mh, mn, gye)
+            num[i, j] = (lp - lm) / (2 * eps)
+    rel = np.linalg.norm(num - adj["gy0"]) / np.linalg.norm(adj["gy0"])
+    assert rel < 1e-6, rel
+    # parameter cotangent
+    if cfg == 1:
+        mu = w["field"]["mu"]
+        for i in range(3):
+            eps = 1e-6 * max(1, abs(mu[i]))
+            fp = {"kind": "vdp", "mu": mu.copy()}
+            fp["mu"][i] += eps
+            lp = _loss_replay(fp, w, mt, mh, mn, gye)
+            fp["mu"][i] -= 2 * eps
+            lm = _loss_replay(fp, w, mt, mh, mn, gye)
+            g = (lp - lm) / (2 * eps)
+            assert abs(g - adj["gmu"][i]) <= 1e-6 * max(1.0, abs(g))
+    else:
+        A = w["field"]["A"]
+        for (i, a, b) in [(0, 0, 0), (1, 3, 7), (2, 15, 2)]:
+            eps = 1e-6
+            fp = {"kind": "linear", "A": A.copy()}
+            fp["A"][i, a, b] += eps
+            lp = _loss_replay(fp, w, mt, mh, mn, gye)
+            fp["A"][i, a, b] -= 2 * eps
+            lm = _loss_replay(fp, w, mt, mh, mn, gye)
+            g = (lp - lm) / (2 * eps)
+            assert abs(g - adj["gA"][i, a, b]) <= 1e-6 * max(1.0, abs(g))
+
+
+def test_adjoint_mlp_vs_fd():
+    w = workloads.make(4, B=2)
+    tol = 1e-5
+    r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], w["t_eval"],
+                     dict(rtol=tol, atol=tol), trace_cap=5000)
+    mt, mh, mn = mesh_from_trace(r)
+    gye = 2.0 * r["y_eval"]  # L = sum y(t_eval)^2
+    adj = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"], gye)
+
+    def loss(field, y0):
+        rr = oracle.replay(field, y0, w["t0"], w["t1"], mt, mh, mn, w["t_eval"])
+        return float((rr["y_eval"] ** 2).sum())
+
+    for (i, j) in [(0, 0), (1, 17), (1, 31)]:
+        eps = 1e-6
+        y = w["y0"].copy()
+        y[i, j] += eps
+        lp = loss(w["field"], y)
+        y[i, j] -= 2 * eps
+        lm = loss(w["field"], y)
+        g = (lp - lm) / (2 * eps)
+        assert abs(g - adj["gy0"][i, j]) <= 1e-6 * max(1.0, abs(g))
+    for (l, a, b) in [(0, 5, 32), (1, 100, 7), (2, 31, 127), (0, 0, 0)]:
+        eps = 1e-6
+        Wp = [x.copy() for x in w["field"]["W"]]
+        Wp[l][a, b] += eps
+        lp = loss({"kind": "mlp", "W": Wp, "b": w["field"]["b"]}, w["y0"])
+        Wp[l][a, b] -= 2 * eps
+        lm = loss({"kind": "mlp", "W": Wp, "b": w["field"]["b"]}, w["y0"])
+        g = (lp - lm) / (2 * eps)
+        assert abs(g - adj["gW"][l][a, b]) <= 1e-6 * max(1.0, abs(g)), (l, a, b)
+    for (l, a) in [(0, 3), (2, 9)]:
+        eps = 1e-6
+        bp = [x.copy() for x in w["field"]["b"]]
+        bp[l][a] += eps
+        lp = loss({"kind": "mlp", "W": w["field"]["W"], "b": bp}, w["y0"])
+        bp[l][a] -= 2 * eps
+        lm = loss({"kind": "mlp", "W": w["field"]["W"], "b": bp}, w["y0"])
+        g = (lp - lm) / (2 * eps)
+        assert abs(g - adj["gb"][l][a]) <= 1e-6 * max(1.0, abs(g))
+
+
+def test_adjoint_linear_closed_form_jacobian():
+    """For y' = A y, d y(T) / d y0 = expm(A T) (up to discretisation error)."""
+    w = workloads.make(2, B=2)
+    r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], None,
+                     dict(rtol=1e-11, atol=1e-11), trace_cap=50000)
+    mt, mh, mn = mesh_from_trace(r)
+    D = 16
+    for i in range(2):
+        M = sla.expm(w["field"]["A"][i] * w["t1"][i])
+        for col in (0, 9):
+            gyf = np.zeros((2, D))
+            gyf[i, col] = 1.0
+            adj = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, None, None,
+                                 gyf)
+            # row `col` of M: d y_col(T) / d y0
+            assert np.abs(adj["gy0"][i] - M[col]).max() < 1e-8
