@@ -30,6 +30,8 @@
  *     quartic polynomial b_i(theta) per stage and evaluated by Horner's rule;
  *   - error norm: the weighted RMS norm of HNW Sec. II.4, per instance;
  *   - controller: factor = safety * err^-beta1 * err_prev^beta2, clamped;
+ *   - powers err^-beta: a fixed exp/log procedure (orc_pow) so that every
+ *     IEEE machine running it reproduces the controller's step sizes;
  *   - starting step: the heuristic of HNW Sec. II.4 ("starting step size").
  *     PARITY UNPINNED: the paper gives no starting-step rule and no worked
  *     example of it; only the other parts below are pinned by tests.
@@ -232,6 +234,92 @@ static double rms(const double *v, const double *sc, int D) {
 static double dmax(double a, double b) { return (a > b) ? a : b; }
 static double dmin(double a, double b) { return (b < a) ? b : a; }
 
+/* x^y for the step-size controller and the starting step, evaluated as
+ * exp(y ln x) by a fully specified sequence of IEEE-754 double operations:
+ *   ln x: x = 2^e m with m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1),
+ *         ln m = 2 (s + s^3/3 + ... + s^23/23) (Horner in s^2),
+ *         ln x = e ln2_hi + (e ln2_lo + ln m)  (ln 2 split after 32 bits);
+ *   exp z: k = floor(z / ln2 + 1/2), r = (z - k ln2_hi) - k ln2_lo,
+ *         exp r = sum_{j<=14} r^j / j! (Horner), times 2^k exactly.
+ * Platform pow implementations may differ by an ulp, and the embedded error
+ * estimate (a difference of nearly equal stage sums) amplifies such a
+ * difference about 1e4-fold; with this procedure any IEEE machine that runs
+ * the same operations in the same order gets the same bits. */
+static const double CTL_LN2_HI = 0x1.62e42fee00000p-1;
+static const double CTL_LN2_LO = 0x1.a39ef35793c76p-33;
+static const double CTL_INV_LN2 = 0x1.71547652b82fep+0;
+static const double CTL_SQRT2 = 0x1.6a09e667f3bcdp+0;
+
+static double ctl_ln(double x) {
+  uint64_t u;
+  memcpy(&u, &x, 8);
+  int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0) { /* subnormal: scale by 2^54 exactly */
+    x = x * 18014398509481984.0;
+    memcpy(&u, &x, 8);
+    e = (int)((u >> 52) & 0x7ff) - 54;
+  }
+  e -= 1023;
+  u = (u & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
+  double m;
+  memcpy(&m, &u, 8);
+  if (m > CTL_SQRT2) {
+    m = m * 0.5;
+    e = e + 1;
+  }
+  double s = (m - 1.0) / (m + 1.0);
+  double w = s * s;
+  double p = 1.0 / 23.0;
+  p = 1.0 / 21.0 + w * p;
+  p = 1.0 / 19.0 + w * p;
+  p = 1.0 / 17.0 + w * p;
+  p = 1.0 / 15.0 + w * p;
+  p = 1.0 / 13.0 + w * p;
+  p = 1.0 / 11.0 + w * p;
+  p = 1.0 / 9.0 + w * p;
+  p = 1.0 / 7.0 + w * p;
+  p = 1.0 / 5.0 + w * p;
+  p = 1.0 / 3.0 + w * p;
+  p = 1.0 + w * p;
+  double lnm = 2.0 * (s * p);
+  double de = (double)e;
+  return de * CTL_LN2_HI + (de * CTL_LN2_LO + lnm);
+}
+
+static double ctl_exp(double z) {
+  if (z > 700.0) return INFINITY;
+  if (z < -700.0) return 0.0;
+  double k = floor(z * CTL_INV_LN2 + 0.5);
+  double r = (z - k * CTL_LN2_HI) - k * CTL_LN2_LO;
+  double p = 1.0 / 87178291200.0;           /* 1/14! */
+  p = 1.0 / 6227020800.0 + r * p;           /* 1/13! */
+  p = 1.0 / 479001600.0 + r * p;
+  p = 1.0 / 39916800.0 + r * p;
+  p = 1.0 / 3628800.0 + r * p;
+  p = 1.0 / 362880.0 + r * p;
+  p = 1.0 / 40320.0 + r * p;
+  p = 1.0 / 5040.0 + r * p;
+  p = 1.0 / 720.0 + r * p;
+  p = 1.0 / 120.0 + r * p;
+  p = 1.0 / 24.0 + r * p;
+  p = 1.0 / 6.0 + r * p;
+  p = 0.5 + r * p;
+  p = 1.0 + r * p;
+  p = 1.0 + r * p;
+  uint64_t b = (uint64_t)((int64_t)k + 1023) << 52;
+  double two_k;
+  memcpy(&two_k, &b, 8);
+  return p * two_k;
+}
+
+double orc_pow(double x, double y) {
+  if (x != x || y != y || x < 0.0) return NAN;
+  if (x == 0.0) return (y > 0.0) ? 0.0 : INFINITY;
+  if (isinf(x)) return (y > 0.0) ? INFINITY : 0.0;
+  if (x == 1.0 || y == 0.0) return 1.0;
+  return ctl_exp(y * ctl_ln(x));
+}
+
 /* Starting step size, HNW Sec. II.4 (PARITY UNPINNED, see header).  f0 =
  * f(t0, y0) is supplied and reused as the first step's k1 (FSAL). */
 static double starting_step(fctx *c, double t0, double t1, const double *y0, const double *f0,
@@ -245,7 +333,7 @@ static double starting_step(fctx *c, double t0, double t1, const double *y0, con
   for (int j = 0; j < D; ++j) w2[j] = w2[j] - f0[j];
   double d2 = rms(w2, sc, D) / h0;
   double m = (d1 > d2) ? d1 : d2;
-  double h1 = (m <= 1e-15) ? dmax(1e-6, h0 * 1e-3) : pow(0.01 / m, 1.0 / 5.0);
+  double h1 = (m <= 1e-15) ? dmax(1e-6, h0 * 1e-3) : orc_pow(0.01 / m, 1.0 / 5.0);
   double h = dmin(100.0 * h0, h1);
   h = dmin(h, t1 - t0);
   if (!(h > 0.0 && isfinite(h))) h = t1 - t0;
@@ -431,8 +519,8 @@ static void solve_one(const job *J, int i, double *work, double *act) {
       if (err == 0.0) {
         fac = O->fac_max;
       } else {
-        fac = O->safety * pow(err, -O->beta1);
-        if (O->beta2 != 0.0) fac = fac * pow(err_prev, O->beta2);
+        fac = O->safety * orc_pow(err, -O->beta1);
+        if (O->beta2 != 0.0) fac = fac * orc_pow(err_prev, O->beta2);
       }
       fac = dmin(dmax(fac, O->fac_min), O->fac_max);
       if (prev_rejected) fac = dmin(fac, 1.0);
@@ -447,7 +535,7 @@ static void solve_one(const job *J, int i, double *work, double *act) {
       }
       if (last) st = ST_SUCCESS;
     } else {
-      double fac = finite ? dmin(dmax(O->safety * pow(err, -O->beta1), O->fac_min), 1.0)
+      double fac = finite ? dmin(dmax(O->safety * orc_pow(err, -O->beta1), O->fac_min), 1.0)
                           : O->fac_min;
       h_next = h * fac;
       prev_rejected = 1;

@@ -191,6 +191,35 @@ def test_tolerance_proportionality_vdp():
 
 
 # ---------------------------------------------------------------- controller
+def test_controller_power_function_accuracy():
+    """The controller's x^y (a fixed exp/log procedure, identical on every
+    IEEE machine) agrees with the platform pow within the error bound of
+    exp(y ln x): a few ulps plus the absolute error of y ln x."""
+    import ctypes as C
+    from oracle import oracle as O
+    lib = C.CDLL(O.build())
+    lib.orc_pow.restype = C.c_double
+    lib.orc_pow.argtypes = [C.c_double, C.c_double]
+    xs = np.concatenate([10.0 ** np.linspace(-300, 300, 2001), np.linspace(0.01, 3.0, 3001),
+                         [5e-324, 2.2e-308, 1.0 - 2 ** -53, 1.0 + 2 ** -52]])
+    worst = 0.0
+    for y in (-0.2, 0.2, -0.14, 0.08, 0.5, -1.0):
+        for x in xs:
+            try:
+                ref = math.pow(x, y)
+            except OverflowError:
+                continue
+            if ref == 0.0 or math.isinf(ref) or ref > 1e300 or ref < 1e-300:
+                continue
+            v = lib.orc_pow(x, y)
+            bound = 2.3e-16 * (8.0 + 2.0 * abs(y * math.log(x)))
+            worst = max(worst, abs(v - ref) / ref / bound)
+    assert worst < 1.0, worst
+    assert lib.orc_pow(1.0, -0.2) == 1.0 and lib.orc_pow(0.0, 0.2) == 0.0
+    assert math.isinf(lib.orc_pow(0.0, -0.2)) and math.isnan(lib.orc_pow(-1.0, 0.2))
+    assert math.isnan(lib.orc_pow(float("nan"), 0.2))
+
+
 @pytest.mark.parametrize("beta1,beta2", [(0.2, 0.0), (0.14, 0.08)])
 def test_controller_steady_state(beta1, beta2):
     """For a smooth problem in the asymptotic regime (err ~ C h^p) the
