@@ -1,0 +1,206 @@
+/*
+ * tode.h -- C ABI of the B300 batched adaptive Dormand-Prince 5(4) solver.
+ *
+ * The library solves B independent initial value problems y' = f(t, y),
+ * each with its own initial state, integration range, step size, error
+ * estimate, accept/reject decisions and evaluation times (torchode, Sec. 3:
+ * the solver keeps a separate state per instance; Sec. 4.1 shows why
+ * instances must not share a step size).  The method is dopri5 (App. A) with
+ * FSAL/SSAL and Horner dense output (Sec. 3, "What makes torchode fast?"),
+ * a PI step-size controller of Soderlind's family (Sec. 3, App. C) and per-
+ * instance statistics and status (Sec. 3; App. B).
+ *
+ * Conventions for every entry point:
+ *  - Pointers are DEVICE pointers unless marked "host".  The caller owns and
+ *    allocates every buffer (inputs, outputs, workspace, tape, scratch); the
+ *    library never allocates or frees device memory.
+ *  - Calls enqueue work on `stream` (a cudaStream_t, NULL = legacy default)
+ *    and return.  Outputs are valid once the stream has synchronised.  The
+ *    plain form (TODE_PLAIN) additionally synchronises `stream` every
+ *    `poll_every` steps to read its "any instance still running" flag.
+ *  - Argument and launch errors are returned as tode_err before or at launch
+ *    and leave outputs unspecified.  Numerical failures never abort the
+ *    batch: they are reported per instance in status[].
+ *  - Times (t0, t1, t_eval) are always FP64.  The state dtype (y0, y_eval,
+ *    y_final, mu, A, gradients) follows tode_options.prec: double for
+ *    TODE_F64, float for TODE_F32 and TODE_BF16W.
+ *  - Layouts are row-major, instance-major: y0 [B][D], y_eval [B][K][D],
+ *    t_eval [B][K], A [B][D][D].
+ */
+#ifndef TODE_H
+#define TODE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TODE_VERSION 1
+
+typedef enum {
+  TODE_OK = 0,
+  TODE_EINVAL = 1,        /* bad argument (null pointer, size, option) */
+  TODE_EWORKSPACE = 2,    /* workspace / tape / scratch too small or misaligned */
+  TODE_ECUDA = 3,         /* a CUDA runtime call failed */
+  TODE_EUNSUPPORTED = 4,  /* combination not built (field, D, precision) */
+  TODE_ETIMEOUT = 5       /* a bounded host wait gave up */
+} tode_err;
+
+typedef enum { TODE_VDP = 1, TODE_LINEAR = 2, TODE_MLP = 3 } tode_field_kind;
+
+/* TODE_F64: FP64 state and arithmetic.  TODE_F32: FP32 state (compensated
+ * summation of the state updates), FP64 time.  TODE_BF16W (MLP only): BF16
+ * weights on tensor cores, FP32 accumulation, FP32 state, FP64 time. */
+typedef enum { TODE_F64 = 0, TODE_F32 = 1, TODE_BF16W = 2 } tode_prec;
+
+/* TODE_PLAIN: one kernel launch per step over the whole masked batch.
+ * TODE_FUSED: one persistent launch; every worker integrates its instance to
+ * the end and then takes the next one (work stealing). */
+typedef enum { TODE_PLAIN = 0, TODE_FUSED = 1 } tode_form;
+
+/* Per-instance status[] values. */
+enum {
+  TODE_S_SUCCESS = 0,       /* reached t1 */
+  TODE_S_MAX_STEPS = 1,     /* max_steps attempted steps without reaching t1 */
+  TODE_S_DT_UNDERFLOW = 2,  /* step size underflowed with finite errors */
+  TODE_S_NONFINITE = 3,     /* step size underflowed while the state was non-finite */
+  TODE_S_INVALID_INPUT = 4  /* t0/t1/t_eval not finite, t1 < t0, t_eval unsorted or outside [t0,t1] */
+};
+
+/* The vector field f(t, y) (built-in kinds only).
+ *  TODE_VDP:    Van der Pol, Eq. 1 as a first-order system, D = 2:
+ *               f = (y2, mu_i (1 - y1^2) y2 - y1).  mu: [B] state dtype.
+ *  TODE_LINEAR: f = A_i y.  A: [B][D][D] state dtype; D in {1,2,4,8,16,32}.
+ *  TODE_MLP:    f = W_L tanh(... tanh(W_1 [y; t] + b_1) ...) + b_L.
+ *               n_layers weight matrices, widths (host) [n_layers+1] with
+ *               widths[0] = D + 1 and widths[n_layers] = D; W (host array of
+ *               device pointers) W[l] is [widths[l+1]][widths[l]] BF16
+ *               (uint16 bit patterns); b (host array of device pointers)
+ *               b[l] is [widths[l+1]] float. */
+typedef struct {
+  tode_field_kind kind;
+  int B;
+  int D;
+  const void* mu;
+  const void* A;
+  int n_layers;
+  const int* widths;
+  const void* const* W;
+  const float* const* b;
+} tode_field_desc;
+
+typedef struct {
+  double rtol, atol;          /* scalar tolerances */
+  const double* rtol_b;       /* optional per-instance tolerances [B] (device), NULL = scalar */
+  const double* atol_b;
+  /* controller: factor = safety * err^-beta1 * err_prev^beta2, clamped to
+   * [fac_min, fac_max]; beta2 = 0 is the integral controller of App. A. */
+  double safety, fac_min, fac_max, beta1, beta2;
+  double h0;                  /* > 0: first step size; 0: starting-step heuristic */
+  int max_steps;              /* attempted steps per instance (>= 1) */
+  tode_prec prec;
+  tode_form form;
+  /* launch tuning (0 = default / autotuned) */
+  int group;                  /* lanes per instance (linear field, D = 16: 4, 8 or 16) */
+  int block;                  /* threads per block (multiple of 32, <= 256) */
+  int ctas_per_sm;            /* fused form: resident CTAs per SM */
+  int poll_every;             /* plain form: steps between host polls */
+} tode_options;
+
+/* Checkpoint tape written by tode_solve for tode_adjoint.  Slot j of
+ * instance i holds the solver state at the start of accepted step j*stride
+ * (state y, its FSAL stage k1, time t, proposed step h, previous error,
+ * flags), from which tode_adjoint re-runs the forward bit for bit.
+ * Instance i needs ceil(n_acc[i] / stride) slots; tode_solve never writes
+ * past `slots`, and tode_adjoint reports instances that needed more through
+ * its `overflow` output. */
+typedef struct {
+  int slots;
+  int stride;
+  void* y;          /* [slots][B][D] state dtype */
+  void* y_lo;       /* [slots][B][D] float: compensation term of an FP32 state
+                       (TODE_F32 / TODE_BF16W); ignored for TODE_F64 (may be NULL) */
+  void* k1;         /* [slots][B][D] state dtype: f(t, y) carried by FSAL */
+  double* t;        /* [slots][B] */
+  void* h;          /* [slots][B] state dtype */
+  void* err_prev;   /* [slots][B] state dtype */
+  int32_t* flags;   /* [slots][B] */
+} tode_tape;
+
+/* Per-attempt trace (testing and diagnostics): for instance i, attempt n <
+ * cap: step start t, step size h, error norm err, accepted flag; len[i] =
+ * min(attempts, cap).  All [B][cap] except len [B]. */
+typedef struct {
+  int cap;
+  double* t;
+  double* h;
+  double* err;
+  int32_t* accepted;
+  int32_t* len;
+} tode_trace;
+
+/* Fills *o with the defaults: rtol = atol = 1e-6, safety 0.9, fac_min 0.2,
+ * fac_max 10, beta1 0.2, beta2 0 (integral controller), h0 = 0 (heuristic),
+ * max_steps 100000, TODE_F32, TODE_FUSED, tuning fields 0. */
+void tode_default_options(tode_options* o);
+
+/* Bytes of device workspace tode_solve needs for this problem (the base
+ * pointer must be 256-byte aligned).  Returns 0 for an unsupported or
+ * invalid combination. */
+size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int K);
+
+/* Solve all B instances (Sec. 3: independent parallel solving).
+ *  y0 [B][D], t0 [B], t1 [B], t_eval [B][K] (K >= 0; NULL when K == 0).
+ *  Outputs: y_eval [B][K][D] (NULL when K == 0), y_final [B][D] (state at
+ *  the last accepted step), n_acc, n_rej, n_feval, status [B] int32.
+ *  Evaluation points not reached (failed instance) are NaN; instances with
+ *  TODE_S_INVALID_INPUT get NaN outputs and zero counters.
+ *  tape: NULL or a checkpoint tape to fill for tode_adjoint.
+ *  trace: NULL or a per-attempt trace to fill.
+ *  workspace: >= tode_workspace_size bytes, 256-byte aligned. */
+tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void* y0,
+                    const double* t0, const double* t1, const double* t_eval, int K,
+                    void* y_eval, void* y_final, int32_t* n_acc, int32_t* n_rej,
+                    int32_t* n_feval, int32_t* status, const tode_tape* tape,
+                    const tode_trace* trace, void* workspace, size_t ws_bytes, void* stream);
+
+/* Bytes of device scratch tode_adjoint needs (256-byte aligned base). */
+size_t tode_adjoint_scratch_size(const tode_field_desc* f, const tode_options* o,
+                                 const tode_tape* tape);
+
+/* Discrete adjoint of the fixed-mesh map of a previous tode_solve with the
+ * same f, o, inputs and a filled tape (App. A: gradients by backpropagation
+ * through the solver).  The mesh (accepted t_n, h_n) is a constant.  For
+ * every instance it reverses the accepted steps, recomputing the stages
+ * from the checkpoints, and writes
+ *   gy0 [B][D]       = dL/dy0
+ *   gparam           = VDP: dL/dmu [B]; LINEAR: dL/dA [B][D][D] (state
+ *                      dtype, per instance); MLP: unused (NULL)
+ *   gW, gb           = MLP only (host arrays of device pointers): dL/dW_l
+ *                      [widths[l+1]][widths[l]] and dL/db_l [widths[l+1]],
+ *                      float, summed over the batch in a fixed order
+ *                      (deterministic); overwritten, not accumulated
+ * from gy_eval [B][K][D] = dL/dy_eval (NULL = 0) and gy_final [B][D] =
+ * dL/dy_final (NULL = 0).  n_acc and status are the forward's outputs;
+ * instances whose status is not TODE_S_SUCCESS get NaN gradients.
+ * overflow (int32, device) is set to 1 when some instance needed more tape
+ * slots than the forward had (that instance's gradients are NaN). */
+tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const double* t0,
+                      const double* t1, const double* t_eval, int K, const int32_t* n_acc,
+                      const int32_t* status, const tode_tape* tape, const void* gy_eval,
+                      const void* gy_final, void* gy0, void* gparam, float* const* gW,
+                      float* const* gb, int32_t* overflow, void* scratch, size_t scratch_bytes,
+                      void* stream);
+
+/* Static text for an error code. */
+const char* tode_strerror(tode_err e);
+
+/* TODE_VERSION of the loaded library. */
+int tode_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TODE_H */

@@ -1,0 +1,12 @@
+"""B300-native batched adaptive Dormand-Prince 5(4) (torchode's method).
+
+Every instance of a batch is solved independently with its own step size,
+accept/reject decisions and evaluation points (torchode, Sec. 3).  The
+solver is the C-ABI library ``libtode.so`` (hand-written CUDA for sm_103a);
+this package only marshals torch tensors into it.
+"""
+from . import _abi  # noqa: F401
+from .api import MLP, Linear, Solution, TapeBuffers, VdP, adjoint, make_options, solve  # noqa: F401
+
+__all__ = ["VdP", "Linear", "MLP", "solve", "adjoint", "TapeBuffers", "Solution",
+           "make_options"]

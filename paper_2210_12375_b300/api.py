@@ -1,0 +1,262 @@
+"""Python binding of the C ABI (include/tode.h) on torch CUDA tensors.
+
+torch provides device memory and streams; every step of the solver runs in
+libtode's kernels.  Names follow the paper: a batch of independent initial
+value problems y' = f(t, y), one state, step size, accept/reject sequence and
+set of evaluation points per instance (torchode, Sec. 3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field as dc_field
+from typing import Optional
+
+import torch
+
+from . import _abi
+
+
+# ------------------------------------------------------------------ fields
+class VdP:
+    """Van der Pol, Eq. 1 as a first-order system (D = 2); mu: [B]."""
+    kind = _abi.TODE_VDP
+
+    def __init__(self, mu: torch.Tensor):
+        self.mu = mu
+
+    def desc(self, B: int, D: int, keep: list) -> _abi.FieldDesc:
+        f = _abi.FieldDesc()
+        f.kind, f.B, f.D = self.kind, B, D
+        f.mu = self.mu.data_ptr()
+        return f
+
+    def params(self):
+        return self.mu
+
+
+class Linear:
+    """y' = A_i y; A: [B, D, D] row-major."""
+    kind = _abi.TODE_LINEAR
+
+    def __init__(self, A: torch.Tensor):
+        self.A = A
+
+    def desc(self, B: int, D: int, keep: list) -> _abi.FieldDesc:
+        f = _abi.FieldDesc()
+        f.kind, f.B, f.D = self.kind, B, D
+        f.A = self.A.data_ptr()
+        return f
+
+    def params(self):
+        return self.A
+
+
+class MLP:
+    """f(t, y) = W_L tanh(... tanh(W_1 [y; t] + b_1) ...) + b_L with BF16
+    weights W_l [out, in] and float biases b_l [out]."""
+    kind = _abi.TODE_MLP
+
+    def __init__(self, weights, biases):
+        self.W = list(weights)
+        self.b = list(biases)
+
+    @property
+    def widths(self):
+        return [self.W[0].shape[1]] + [w.shape[0] for w in self.W]
+
+    def desc(self, B: int, D: int, keep: list) -> _abi.FieldDesc:
+        f = _abi.FieldDesc()
+        f.kind, f.B, f.D = self.kind, B, D
+        wd = self.widths
+        wa = (C.c_int * len(wd))(*wd)
+        Wp = (C.c_void_p * len(self.W))(*[w.data_ptr() for w in self.W])
+        bp = (C.c_void_p * len(self.b))(*[b.data_ptr() for b in self.b])
+        keep += [wa, Wp, bp]
+        f.n_layers = len(self.W)
+        f.widths = wa
+        f.W = Wp
+        f.b = bp
+        return f
+
+    def params(self):
+        return None
+
+
+# ------------------------------------------------------------------ options
+def _prec_of(field, y0: torch.Tensor) -> int:
+    if isinstance(field, MLP):
+        return _abi.TODE_BF16W
+    if y0.dtype == torch.float64:
+        return _abi.TODE_F64
+    if y0.dtype == torch.float32:
+        return _abi.TODE_F32
+    raise TypeError(f"state dtype {y0.dtype} not supported")
+
+
+def make_options(*, rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, fac_min=0.2,
+                 fac_max=10.0, beta1=0.2, beta2=0.0, h0=0.0, max_steps=100000,
+                 prec=_abi.TODE_F32, form="fused", group=0, block=0, ctas_per_sm=0,
+                 poll_every=0) -> _abi.Options:
+    o = _abi.Options()
+    o.rtol, o.atol = float(rtol), float(atol)
+    o.rtol_b = rtol_b.data_ptr() if rtol_b is not None else None
+    o.atol_b = atol_b.data_ptr() if atol_b is not None else None
+    o.safety, o.fac_min, o.fac_max = float(safety), float(fac_min), float(fac_max)
+    o.beta1, o.beta2, o.h0 = float(beta1), float(beta2), float(h0)
+    o.max_steps = int(max_steps)
+    o.prec = int(prec)
+    o.form = {"plain": _abi.TODE_PLAIN, "fused": _abi.TODE_FUSED}[form] \
+        if isinstance(form, str) else int(form)
+    o.group, o.block, o.ctas_per_sm, o.poll_every = int(group), int(block), int(ctas_per_sm), \
+        int(poll_every)
+    return o
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ tape / trace
+@dataclass
+class TapeBuffers:
+    """Checkpoint tape for the adjoint: slot j = solver state at the start of
+    accepted step j*stride (state, FSAL stage, time, step, controller)."""
+    slots: int
+    stride: int
+    y: torch.Tensor
+    y_lo: torch.Tensor
+    k1: torch.Tensor
+    t: torch.Tensor
+    h: torch.Tensor
+    err_prev: torch.Tensor
+    flags: torch.Tensor
+
+    @staticmethod
+    def allocate(B, D, dtype, slots, stride, device):
+        comp = (slots, B, D) if dtype != torch.float64 else (1,)
+        return TapeBuffers(slots, stride,
+                           torch.empty((slots, B, D), dtype=dtype, device=device),
+                           torch.empty(comp, dtype=dtype, device=device),
+                           torch.empty((slots, B, D), dtype=dtype, device=device),
+                           torch.empty((slots, B), dtype=torch.float64, device=device),
+                           torch.empty((slots, B), dtype=dtype, device=device),
+                           torch.empty((slots, B), dtype=dtype, device=device),
+                           torch.empty((slots, B), dtype=torch.int32, device=device))
+
+    @staticmethod
+    def bytes_per_slot(B, D, itemsize):
+        comp = D * itemsize if itemsize == 4 else 0
+        return B * (2 * D * itemsize + comp + 8 + 2 * itemsize + 4)
+
+    def c(self) -> _abi.Tape:
+        tp = _abi.Tape()
+        tp.slots, tp.stride = self.slots, self.stride
+        tp.y, tp.y_lo, tp.k1 = self.y.data_ptr(), self.y_lo.data_ptr(), self.k1.data_ptr()
+        tp.t, tp.h = self.t.data_ptr(), self.h.data_ptr()
+        tp.err_prev, tp.flags = self.err_prev.data_ptr(), self.flags.data_ptr()
+        return tp
+
+
+@dataclass
+class Solution:
+    y_eval: torch.Tensor
+    y_final: torch.Tensor
+    n_acc: torch.Tensor
+    n_rej: torch.Tensor
+    n_feval: torch.Tensor
+    status: torch.Tensor
+    trace: Optional[dict] = None
+    extra: dict = dc_field(default_factory=dict)
+
+
+def solve(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
+          t_eval: Optional[torch.Tensor] = None, *, tape: Optional[TapeBuffers] = None,
+          trace_cap: int = 0, stream: Optional[torch.cuda.Stream] = None,
+          out: Optional[Solution] = None, workspace: Optional[torch.Tensor] = None,
+          **opt_kw) -> Solution:
+    """Solve every instance of the batch independently (Sec. 3).
+
+    y0 [B, D] (float64 or float32; MLP: float32), t0/t1 [B] float64,
+    t_eval [B, K] float64.  Keyword options as in ``make_options``.
+    """
+    lib = _abi.load()
+    B, D = y0.shape
+    K = 0 if t_eval is None else t_eval.shape[1]
+    dev = y0.device
+    prec = _prec_of(field, y0)
+    opts = make_options(prec=prec, **opt_kw)
+    keep = []
+    fd = field.desc(B, D, keep)
+    if out is None:
+        out = Solution(
+            y_eval=torch.empty((B, K, D), dtype=y0.dtype, device=dev),
+            y_final=torch.empty((B, D), dtype=y0.dtype, device=dev),
+            n_acc=torch.empty(B, dtype=torch.int32, device=dev),
+            n_rej=torch.empty(B, dtype=torch.int32, device=dev),
+            n_feval=torch.empty(B, dtype=torch.int32, device=dev),
+            status=torch.empty(B, dtype=torch.int32, device=dev))
+    trace_c = None
+    if trace_cap > 0:
+        tr = dict(t=torch.zeros((B, trace_cap), dtype=torch.float64, device=dev),
+                  h=torch.zeros((B, trace_cap), dtype=torch.float64, device=dev),
+                  err=torch.zeros((B, trace_cap), dtype=torch.float64, device=dev),
+                  accepted=torch.zeros((B, trace_cap), dtype=torch.int32, device=dev),
+                  len=torch.zeros(B, dtype=torch.int32, device=dev))
+        trace_c = _abi.Trace(trace_cap, tr["t"].data_ptr(), tr["h"].data_ptr(),
+                             tr["err"].data_ptr(), tr["accepted"].data_ptr(),
+                             tr["len"].data_ptr())
+        out.trace = tr
+    ws_bytes = lib.tode_workspace_size(C.byref(fd), C.byref(opts), int(K))
+    if ws_bytes == 0 and B > 0:
+        raise _abi.TodeError(_abi.TODE_EUNSUPPORTED, "tode_workspace_size")
+    if workspace is None or workspace.numel() < ws_bytes:
+        workspace = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
+    tape_c = tape.c() if tape is not None else None
+    code = lib.tode_solve(
+        C.byref(fd), C.byref(opts), _ptr(y0), _ptr(t0), _ptr(t1),
+        _ptr(t_eval) if K > 0 else None, int(K), _ptr(out.y_eval) if K > 0 else None,
+        _ptr(out.y_final), _ptr(out.n_acc), _ptr(out.n_rej), _ptr(out.n_feval), _ptr(out.status),
+        C.byref(tape_c) if tape_c is not None else None,
+        C.byref(trace_c) if trace_c is not None else None,
+        _ptr(workspace), C.c_size_t(workspace.numel()), _stream_handle(stream))
+    _abi.check(code, "tode_solve")
+    out.extra["workspace"] = workspace
+    return out
+
+
+def adjoint(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=None,
+            gy_final=None, *, stream=None, scratch: Optional[torch.Tensor] = None, **opt_kw):
+    """Discrete adjoint of the forward solve that filled ``tape`` (App. A:
+    backpropagation through the solver on the frozen mesh).  Returns
+    (gy0, gparam, overflow)."""
+    lib = _abi.load()
+    B, D = sol.y_final.shape
+    K = 0 if t_eval is None else t_eval.shape[1]
+    dev = sol.y_final.device
+    dtype = sol.y_final.dtype
+    prec = _prec_of(field, sol.y_final)
+    opts = make_options(prec=prec, **opt_kw)
+    keep = []
+    fd = field.desc(B, D, keep)
+    tape_c = tape.c()
+    nb = lib.tode_adjoint_scratch_size(C.byref(fd), C.byref(opts), C.byref(tape_c))
+    if nb == 0 and B > 0:
+        raise _abi.TodeError(_abi.TODE_EUNSUPPORTED, "tode_adjoint_scratch_size")
+    if scratch is None or scratch.numel() < nb:
+        scratch = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+    gy0 = torch.empty((B, D), dtype=dtype, device=dev)
+    params = field.params()
+    gparam = torch.empty_like(params) if params is not None else None
+    overflow = torch.zeros(1, dtype=torch.int32, device=dev)
+    code = lib.tode_adjoint(
+        C.byref(fd), C.byref(opts), _ptr(t0), _ptr(t1), _ptr(t_eval) if K > 0 else None,
+        int(K), _ptr(sol.n_acc), _ptr(sol.status), C.byref(tape_c), _ptr(gy_eval),
+        _ptr(gy_final), _ptr(gy0), _ptr(gparam), None, None, _ptr(overflow), _ptr(scratch),
+        C.c_size_t(scratch.numel()), _stream_handle(stream))
+    _abi.check(code, "tode_adjoint")
+    return gy0, gparam, overflow

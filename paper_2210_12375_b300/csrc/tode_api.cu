@@ -1,0 +1,205 @@
+// tode_api.cu -- the C ABI (include/tode.h): argument validation, workspace
+// sizing and dispatch to the per-precision launchers.  No entry point
+// allocates device memory.
+#include <cmath>
+#include <cstring>
+
+#include "tode_internal.h"
+
+namespace tode {
+
+bool simt_supported(int kind, int D) {
+  if (kind == TODE_VDP) return D == 2;
+  if (kind == TODE_LINEAR) return D == 1 || D == 2 || D == 4 || D == 8 || D == 16 || D == 32;
+  return false;
+}
+
+static bool opts_ok(const tode_options* o) {
+  if (!o) return false;
+  if (!(o->rtol >= 0.0) || !(o->atol >= 0.0) || !std::isfinite(o->rtol) ||
+      !std::isfinite(o->atol))
+    return false;
+  if (!o->rtol_b && !o->atol_b && !(o->rtol + o->atol > 0.0)) return false;
+  if (!(o->safety > 0.0) || !(o->fac_min > 0.0) || !(o->fac_min <= 1.0) || !(o->fac_max >= 1.0))
+    return false;
+  if (!(o->beta1 > 0.0) || !std::isfinite(o->beta1) || !std::isfinite(o->beta2)) return false;
+  if (!(o->h0 >= 0.0) || !std::isfinite(o->h0)) return false;
+  if (o->max_steps < 1) return false;
+  if (o->form != TODE_PLAIN && o->form != TODE_FUSED) return false;
+  if (o->block < 0 || o->group < 0 || o->ctas_per_sm < 0 || o->poll_every < 0) return false;
+  return true;
+}
+
+static size_t state_size(const tode_options* o) { return o->prec == TODE_F64 ? 8 : 4; }
+
+static tode_err field_ok(const tode_field_desc* f, const tode_options* o) {
+  if (!f || !o) return TODE_EINVAL;
+  if (f->B < 0 || f->D < 1) return TODE_EINVAL;
+  if (f->kind == TODE_VDP || f->kind == TODE_LINEAR) {
+    if (o->prec != TODE_F64 && o->prec != TODE_F32) return TODE_EUNSUPPORTED;
+    if (!simt_supported(f->kind, f->D)) return TODE_EUNSUPPORTED;
+    if (f->B > 0 && f->kind == TODE_VDP && !f->mu) return TODE_EINVAL;
+    if (f->B > 0 && f->kind == TODE_LINEAR && !f->A) return TODE_EINVAL;
+    return TODE_OK;
+  }
+  if (f->kind == TODE_MLP) return TODE_EUNSUPPORTED;
+  return TODE_EINVAL;
+}
+
+static bool tape_ok(const tode_tape* tp, const tode_options* o) {
+  return tp->slots >= 1 && tp->stride >= 1 && tp->y && tp->k1 && tp->t && tp->h &&
+         tp->err_prev && tp->flags && (o->prec == TODE_F64 || tp->y_lo);
+}
+
+static tode_err device_sms(int* sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TODE_ECUDA;
+  }
+  if (cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TODE_ECUDA;
+  }
+  return TODE_OK;
+}
+
+static bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+
+}  // namespace tode
+
+using namespace tode;
+
+extern "C" {
+
+int tode_version(void) { return TODE_VERSION; }
+
+const char* tode_strerror(tode_err e) {
+  switch (e) {
+    case TODE_OK: return "ok";
+    case TODE_EINVAL: return "invalid argument";
+    case TODE_EWORKSPACE: return "workspace, tape or scratch too small or misaligned";
+    case TODE_ECUDA: return "CUDA runtime error";
+    case TODE_EUNSUPPORTED: return "unsupported field / dimension / precision combination";
+    case TODE_ETIMEOUT: return "bounded wait gave up";
+  }
+  return "unknown error";
+}
+
+void tode_default_options(tode_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->rtol = 1e-6;
+  o->atol = 1e-6;
+  o->safety = 0.9;
+  o->fac_min = 0.2;
+  o->fac_max = 10.0;
+  o->beta1 = 0.2;
+  o->beta2 = 0.0;
+  o->h0 = 0.0;
+  o->max_steps = 100000;
+  o->prec = TODE_F32;
+  o->form = TODE_FUSED;
+}
+
+size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int K) {
+  if (K < 0 || !opts_ok(o) || field_ok(f, o) != TODE_OK) return 0;
+  return simt_workspace_bytes(f->B, f->D, state_size(o), o->form);
+}
+
+tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void* y0,
+                    const double* t0, const double* t1, const double* t_eval, int K,
+                    void* y_eval, void* y_final, int32_t* n_acc, int32_t* n_rej,
+                    int32_t* n_feval, int32_t* status, const tode_tape* tape,
+                    const tode_trace* trace, void* workspace, size_t ws_bytes, void* stream) {
+  if (!opts_ok(o) || K < 0) return TODE_EINVAL;
+  tode_err e = field_ok(f, o);
+  if (e != TODE_OK) return e;
+  if (f->B == 0) return TODE_OK;
+  if (!y0 || !t0 || !t1 || !y_final || !n_acc || !n_rej || !n_feval || !status)
+    return TODE_EINVAL;
+  if (K > 0 && (!t_eval || !y_eval)) return TODE_EINVAL;
+  if (tape && !tape_ok(tape, o)) return TODE_EINVAL;
+  if (trace) {
+    if (trace->cap < 0) return TODE_EINVAL;
+    if (trace->cap > 0 &&
+        (!trace->t || !trace->h || !trace->err || !trace->accepted || !trace->len))
+      return TODE_EINVAL;
+  }
+  const size_t need = tode_workspace_size(f, o, K);
+  if (!workspace || !aligned256(workspace) || ws_bytes < need) return TODE_EWORKSPACE;
+  SolveReq r{};
+  r.f = f;
+  r.o = o;
+  r.B = f->B;
+  r.D = f->D;
+  r.K = K;
+  r.y0 = y0;
+  r.t0 = t0;
+  r.t1 = t1;
+  r.te = t_eval;
+  r.ye = y_eval;
+  r.yf = y_final;
+  r.n_acc = n_acc;
+  r.n_rej = n_rej;
+  r.n_fe = n_feval;
+  r.status = status;
+  r.tape = tape;
+  r.trace = trace;
+  r.ws = (char*)workspace;
+  r.ws_bytes = ws_bytes;
+  r.stream = (cudaStream_t)stream;
+  e = device_sms(&r.num_sms);
+  if (e != TODE_OK) return e;
+  return o->prec == TODE_F64 ? simt_solve_f64(r) : simt_solve_f32(r);
+}
+
+size_t tode_adjoint_scratch_size(const tode_field_desc* f, const tode_options* o,
+                                 const tode_tape* tape) {
+  if (!opts_ok(o) || field_ok(f, o) != TODE_OK || !tape || tape->stride < 1) return 0;
+  return simt_adjoint_scratch_bytes(f->B, f->D, state_size(o), tape->stride);
+}
+
+tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const double* t0,
+                      const double* t1, const double* t_eval, int K, const int32_t* n_acc,
+                      const int32_t* status, const tode_tape* tape, const void* gy_eval,
+                      const void* gy_final, void* gy0, void* gparam, float* const* gW,
+                      float* const* gb, int32_t* overflow, void* scratch, size_t scratch_bytes,
+                      void* stream) {
+  if (!opts_ok(o) || K < 0) return TODE_EINVAL;
+  tode_err e = field_ok(f, o);
+  if (e != TODE_OK) return e;
+  if (f->B == 0) return TODE_OK;
+  if (!t0 || !t1 || !n_acc || !status || !tape || !gy0 || !overflow) return TODE_EINVAL;
+  if (K > 0 && !t_eval) return TODE_EINVAL;
+  if (!tape_ok(tape, o)) return TODE_EINVAL;
+  const size_t need = tode_adjoint_scratch_size(f, o, tape);
+  if (!scratch || !aligned256(scratch) || scratch_bytes < need) return TODE_EWORKSPACE;
+  AdjReq r{};
+  r.f = f;
+  r.o = o;
+  r.B = f->B;
+  r.D = f->D;
+  r.K = K;
+  r.t0 = t0;
+  r.t1 = t1;
+  r.te = t_eval;
+  r.n_acc = n_acc;
+  r.status = status;
+  r.tape = tape;
+  r.gye = gy_eval;
+  r.gyf = gy_final;
+  r.gy0 = gy0;
+  r.gparam = gparam;
+  r.gW = gW;
+  r.gb = gb;
+  r.overflow = overflow;
+  r.scratch = (char*)scratch;
+  r.scratch_bytes = scratch_bytes;
+  r.stream = (cudaStream_t)stream;
+  e = device_sms(&r.num_sms);
+  if (e != TODE_OK) return e;
+  return o->prec == TODE_F64 ? simt_adjoint_f64(r) : simt_adjoint_f32(r);
+}
+
+}  // extern "C"

@@ -1,0 +1,594 @@
+// tode_core.cuh -- device-side Dormand-Prince 5(4) step routine shared by the
+// plain (one launch per step) and fused (persistent, work-stealing) forms.
+//
+// One instance is owned by a group of G adjacent lanes; lane g of the group
+// holds components g*R .. g*R+R-1 of the state (D = G*R).  Every decision
+// (accept/reject, step size, dense-output cursor) is computed identically on
+// all lanes of the group, so the group's control flow is uniform and the
+// plain and fused forms run bit-identical arithmetic.
+//
+// Method (torchode): independent per-instance state (Sec. 3), dopri5 with
+// FSAL/SSAL and Horner dense output (Sec. 3, App. A), PI controller of
+// Soderlind's family (Sec. 3, App. C), per-instance status (App. B).
+// Tableau: Dormand & Prince 1980; dense output: the continuous extension of
+// Hairer-Norsett-Wanner Sec. II.6 expanded into quartic weights b_i(theta);
+// starting step: HNW Sec. II.4.
+//
+// FP64 instantiations are compiled with -fmad=false and evaluate every sum
+// left to right, so their accept/reject sequences are reproducible bit for bit
+// by any IEEE-754 implementation that follows the same order.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tode {
+
+// ---------------------------------------------------------------- tableau
+struct DP5 {
+  static constexpr double c2 = 1.0 / 5.0, c3 = 3.0 / 10.0, c4 = 4.0 / 5.0, c5 = 8.0 / 9.0;
+  static constexpr double a21 = 1.0 / 5.0;
+  static constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+  static constexpr double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+  static constexpr double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0,
+                          a53 = 64448.0 / 6561.0, a54 = -212.0 / 729.0;
+  static constexpr double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0,
+                          a64 = 49.0 / 176.0, a65 = -5103.0 / 18656.0;
+  // 5th-order weights = last stage row (FSAL/SSAL)
+  static constexpr double b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0,
+                          b5 = -2187.0 / 6784.0, b6 = 11.0 / 84.0;
+  // embedded 4th-order weights
+  static constexpr double bh1 = 5179.0 / 57600.0, bh3 = 7571.0 / 16695.0, bh4 = 393.0 / 640.0,
+                          bh5 = -92097.0 / 339200.0, bh6 = 187.0 / 2100.0, bh7 = 1.0 / 40.0;
+  // error weights, formed in double arithmetic from the two weight rows
+  static constexpr double e1 = b1 - bh1, e3 = b3 - bh3, e4 = b4 - bh4, e5 = b5 - bh5,
+                          e6 = b6 - bh6, e7 = 0.0 - bh7;
+  // dense output b_i(theta) = theta*(q_i0 + theta*(q_i1 + theta*(q_i2 + theta*q_i3)))
+  static constexpr double q10 = 1.0, q11 = -8048581381.0 / 2820520608.0,
+                          q12 = 8663915743.0 / 2820520608.0,
+                          q13 = -12715105075.0 / 11282082432.0;
+  static constexpr double q31 = 131558114200.0 / 32700410799.0,
+                          q32 = -68118460800.0 / 10900136933.0,
+                          q33 = 87487479700.0 / 32700410799.0;
+  static constexpr double q41 = -1754552775.0 / 470086768.0,
+                          q42 = 14199869525.0 / 1410260304.0,
+                          q43 = -10690763975.0 / 1880347072.0;
+  static constexpr double q51 = 127303824393.0 / 49829197408.0,
+                          q52 = -318862633887.0 / 49829197408.0,
+                          q53 = 701980252875.0 / 199316789632.0;
+  static constexpr double q61 = -282668133.0 / 205662961.0, q62 = 2019193451.0 / 616988883.0,
+                          q63 = -1453857185.0 / 822651844.0;
+  static constexpr double q71 = 40617522.0 / 29380423.0, q72 = -110615467.0 / 29380423.0,
+                          q73 = 69997945.0 / 29380423.0;
+};
+
+enum : int { ST_SUCCESS = 0, ST_MAX_STEPS = 1, ST_DT_UNDERFLOW = 2, ST_NONFINITE = 3,
+             ST_INVALID = 4, ST_RUNNING = -1 };
+enum : int { FL_PREV_REJ = 1 };
+
+// ---------------------------------------------------------------- scalar helpers
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return (a > b) ? a : b; }
+template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return (b < a) ? b : a; }
+__device__ __forceinline__ bool finite_(double x) { return isfinite(x); }
+__device__ __forceinline__ bool finite_(float x) { return isfinite(x); }
+__device__ __forceinline__ double nan_(double) { return __longlong_as_double(0x7ff8000000000000LL); }
+__device__ __forceinline__ float nan_(float) { return __int_as_float(0x7fc00000); }
+
+// FP64 x^y of the controller and the starting step: exp(y ln x) through one
+// fixed sequence of IEEE-754 double operations, so that the FP64 path's step
+// sizes are reproducible bit for bit on any IEEE machine running the same
+// sequence (a platform pow may differ by an ulp, and the embedded error
+// estimate amplifies such a difference about 1e4-fold through cancellation).
+//   ln x : x = 2^e m, m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1),
+//          ln m = 2 s (1 + s^2/3 + ... + s^22/23)   (Horner in s^2),
+//          ln x = e ln2_hi + (e ln2_lo + ln m)       (ln 2 split after 32 bits)
+//   exp z: k = floor(z/ln2 + 1/2), r = (z - k ln2_hi) - k ln2_lo,
+//          exp r = sum_{j<=14} r^j/j! (Horner), scaled by 2^k exactly.
+// Only the -fmad=false translation unit for FP64 calls it.
+__device__ __forceinline__ double spec_ln(double x) {
+  const double ln2_hi = 0x1.62e42fee00000p-1, ln2_lo = 0x1.a39ef35793c76p-33;
+  long long u = __double_as_longlong(x);
+  int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0) {
+    x = x * 18014398509481984.0;  // 2^54
+    u = __double_as_longlong(x);
+    e = (int)((u >> 52) & 0x7ff) - 54;
+  }
+  e -= 1023;
+  double m = __longlong_as_double((u & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  if (m > 0x1.6a09e667f3bcdp+0) {
+    m = m * 0.5;
+    e = e + 1;
+  }
+  const double s = (m - 1.0) / (m + 1.0);
+  const double w = s * s;
+  double p = 1.0 / 23.0;
+  p = 1.0 / 21.0 + w * p;
+  p = 1.0 / 19.0 + w * p;
+  p = 1.0 / 17.0 + w * p;
+  p = 1.0 / 15.0 + w * p;
+  p = 1.0 / 13.0 + w * p;
+  p = 1.0 / 11.0 + w * p;
+  p = 1.0 / 9.0 + w * p;
+  p = 1.0 / 7.0 + w * p;
+  p = 1.0 / 5.0 + w * p;
+  p = 1.0 / 3.0 + w * p;
+  p = 1.0 + w * p;
+  const double lnm = 2.0 * (s * p);
+  const double de = (double)e;
+  return de * ln2_hi + (de * ln2_lo + lnm);
+}
+__device__ __forceinline__ double spec_exp(double z) {
+  const double ln2_hi = 0x1.62e42fee00000p-1, ln2_lo = 0x1.a39ef35793c76p-33;
+  if (z > 700.0) return __longlong_as_double(0x7ff0000000000000LL);
+  if (z < -700.0) return 0.0;
+  const double k = floor(z * 0x1.71547652b82fep+0 + 0.5);
+  const double r = (z - k * ln2_hi) - k * ln2_lo;
+  double p = 1.0 / 87178291200.0;
+  p = 1.0 / 6227020800.0 + r * p;
+  p = 1.0 / 479001600.0 + r * p;
+  p = 1.0 / 39916800.0 + r * p;
+  p = 1.0 / 3628800.0 + r * p;
+  p = 1.0 / 362880.0 + r * p;
+  p = 1.0 / 40320.0 + r * p;
+  p = 1.0 / 5040.0 + r * p;
+  p = 1.0 / 720.0 + r * p;
+  p = 1.0 / 120.0 + r * p;
+  p = 1.0 / 24.0 + r * p;
+  p = 1.0 / 6.0 + r * p;
+  p = 0.5 + r * p;
+  p = 1.0 + r * p;
+  p = 1.0 + r * p;
+  return p * __longlong_as_double((long long)((int)k + 1023) << 52);
+}
+__device__ __forceinline__ double ctl_pow(double x, double y) {
+  if (x != x || y != y || x < 0.0) return __longlong_as_double(0x7ff8000000000000LL);
+  if (x == 0.0) return (y > 0.0) ? 0.0 : __longlong_as_double(0x7ff0000000000000LL);
+  if (isinf(x)) return (y > 0.0) ? __longlong_as_double(0x7ff0000000000000LL) : 0.0;
+  if (x == 1.0 || y == 0.0) return 1.0;
+  return spec_exp(y * spec_ln(x));
+}
+// FP32 controller power: no cross-machine reproducibility is asked of FP32.
+__device__ __forceinline__ float ctl_pow(float x, float e) { return exp2f(e * __log2f(x)); }
+
+// ---------------------------------------------------------------- group ops
+// Group of G lanes (G divides 32).  mask() is the group's lane mask.
+template <int G> struct Grp {
+  __device__ __forceinline__ static unsigned mask() {
+    if constexpr (G == 32) return 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    return ((1u << G) - 1u) << (lane - (lane % G));
+  }
+  __device__ __forceinline__ static int rank() { return (threadIdx.x & 31) % G; }
+  template <typename T> __device__ __forceinline__ static T bcast(T v, int src) {
+    if constexpr (G == 1) return v;
+    else return __shfl_sync(mask(), v, src, G);
+  }
+};
+
+// Sum over the D = G*R components in index order 0..D-1 (FP64: the exact
+// left-to-right order; FP32: per-lane partial sums then a butterfly, which
+// gives the same bits on every lane because IEEE addition commutes).
+template <typename T, int R, int G>
+__device__ __forceinline__ T group_sum(const T (&v)[R]) {
+  if constexpr (sizeof(T) == 8) {
+    T s = T(0);
+    if constexpr (G == 1) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) s = s + v[r];
+    } else {
+#pragma unroll
+      for (int j = 0; j < G * R; ++j) s = s + Grp<G>::bcast(v[j % R], j / R);
+    }
+    return s;
+  } else {
+    T s = T(0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) s = s + v[r];
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) s = s + __shfl_xor_sync(Grp<G>::mask(), s, off, G);
+    return s;
+  }
+}
+
+// Weighted RMS norm sqrt(sum_j (v_j / sc_j)^2 / D), per instance (HNW II.4).
+template <typename T, int R, int G>
+__device__ __forceinline__ T rms_norm(const T (&v)[R], const T (&sc)[R]) {
+  T q2[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T q = v[r] / sc[r];
+    q2[r] = q * q;
+  }
+  return sqrt(group_sum<T, R, G>(q2) / T(G * R));
+}
+
+// ---------------------------------------------------------------- per-instance state
+// FP32 state is accumulated with compensated (Kahan) summation: the state is
+// y + ylo with |ylo| <= ulp(y)/2, so thousands of FP32 steps do not lose the
+// rounding of every state update.  FP64 state is summed plainly.
+template <typename T> struct Comp {
+  static constexpr bool on = sizeof(T) == 4;
+};
+
+template <typename T, int R> struct Inst {
+  T y[R];
+  T ylo[R];      // compensation term (FP32 only; 0 in FP64)
+  T k1[R];       // FSAL stage
+  double t, t0, t1;
+  T h;           // step size proposed for the next attempt
+  T err_prev;
+  T rtol, atol;
+  int n_acc, n_rej, cursor, status, flags;
+};
+
+struct SolveOpts {
+  double safety, fac_min, fac_max, beta1, beta2, h0;
+  int max_steps;
+};
+
+// Output pointers for one instance.
+template <typename T> struct InstOut {
+  const double* te;  // [K]
+  T* ye;             // [K][D]
+  int K;
+};
+
+// Dense output of one evaluation point:  y + h * sum_i b_i(theta) k_i
+// (+ the state's compensation term in FP32).
+template <typename T, int R>
+__device__ __forceinline__ void dense_point(T theta, T h, const T (&y)[R], const T (&ylo)[R],
+                                            const T (&k1)[R], const T (&k3)[R], const T (&k4)[R],
+                                            const T (&k5)[R], const T (&k6)[R], const T (&k7)[R],
+                                            T (&out)[R]) {
+  using C = DP5;
+  const T w1 = theta * (T(C::q10) + theta * (T(C::q11) + theta * (T(C::q12) + theta * T(C::q13))));
+  const T w3 = theta * (T(0) + theta * (T(C::q31) + theta * (T(C::q32) + theta * T(C::q33))));
+  const T w4 = theta * (T(0) + theta * (T(C::q41) + theta * (T(C::q42) + theta * T(C::q43))));
+  const T w5 = theta * (T(0) + theta * (T(C::q51) + theta * (T(C::q52) + theta * T(C::q53))));
+  const T w6 = theta * (T(0) + theta * (T(C::q61) + theta * (T(C::q62) + theta * T(C::q63))));
+  const T w7 = theta * (T(0) + theta * (T(C::q71) + theta * (T(C::q72) + theta * T(C::q73))));
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T s = w1 * k1[r];
+    s = s + w3 * k3[r];
+    s = s + w4 * k4[r];
+    s = s + w5 * k5[r];
+    s = s + w6 * k6[r];
+    s = s + w7 * k7[r];
+    if constexpr (Comp<T>::on) out[r] = y[r] + (ylo[r] + h * s);
+    else out[r] = y[r] + h * s;
+  }
+}
+
+// Write one evaluation point's R components of lane `g`.
+template <typename T, int R, int G>
+__device__ __forceinline__ void store_point(T* dst, const T (&v)[R]) {
+  const int g = Grp<G>::rank();
+#pragma unroll
+  for (int r = 0; r < R; ++r) dst[g * R + r] = v[r];
+}
+
+// ---------------------------------------------------------------- tape / trace
+template <typename T> struct TapeDev {
+  int slots, stride, B, D;
+  T* y;
+  T* ylo;  // FP32 only
+  T* k1;   // FSAL stage at the slot
+  double* t;
+  T* h;
+  T* err_prev;
+  int32_t* flags;
+};
+struct TraceDev {
+  int cap;
+  double* t;
+  double* h;
+  double* err;
+  int32_t* acc;
+  int32_t* len;
+};
+
+template <typename T, int R, int G>
+__device__ __forceinline__ void tape_store(const TapeDev<T>& tp, int i, const Inst<T, R>& s) {
+  if (tp.slots == 0 || (s.n_acc % tp.stride) != 0) return;
+  const int j = s.n_acc / tp.stride;
+  if (j >= tp.slots) return;
+  const size_t o = (size_t)j * tp.B + i;
+  const int g = Grp<G>::rank();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    tp.y[o * tp.D + g * R + r] = s.y[r];
+    tp.k1[o * tp.D + g * R + r] = s.k1[r];
+  }
+  if constexpr (Comp<T>::on) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) tp.ylo[o * tp.D + g * R + r] = s.ylo[r];
+  }
+  if (g == 0) {
+    tp.t[o] = s.t;
+    tp.h[o] = s.h;
+    tp.err_prev[o] = s.err_prev;
+    tp.flags[o] = s.flags;
+  }
+}
+
+// ---------------------------------------------------------------- init (a1, a2)
+// Loads the instance, validates its times, writes evaluation points at t0,
+// evaluates k1 = f(t0, y0) and picks the first step (given h0 or the HNW
+// Sec. II.4 heuristic, which costs one more evaluation).  Returns false if
+// the instance is already finished (invalid input or t1 == t0).
+template <class Field, typename T, int R, int G>
+__device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int i, int D,
+                          const T* y0, const double* t0p, const double* t1p, double rtol,
+                          double atol, const InstOut<T>& out) {
+  const int g = Grp<G>::rank();
+  s.t0 = t0p[i];
+  s.t1 = t1p[i];
+  s.t = s.t0;
+  s.rtol = T(rtol);
+  s.atol = T(atol);
+  s.n_acc = s.n_rej = 0;
+  s.cursor = 0;
+  s.flags = 0;
+  s.err_prev = T(1);
+  s.h = T(0);
+  s.status = ST_RUNNING;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    s.y[r] = y0[(size_t)i * D + g * R + r];
+    s.ylo[r] = T(0);
+    s.k1[r] = T(0);
+  }
+  // validity of the time arguments (Sec. 3: per-instance bounds and points)
+  bool ok = isfinite(s.t0) && isfinite(s.t1) && !(s.t1 < s.t0);
+  double prev = s.t0;
+  for (int q = 0; q < out.K && ok; ++q) {
+    const double v = out.te[q];
+    ok = isfinite(v) && !(v < prev) && !(v > s.t1);
+    prev = v;
+  }
+  if (!ok) {
+    s.status = ST_INVALID;
+    T nanv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) nanv[r] = nan_(T(0));
+    for (int q = 0; q < out.K; ++q) store_point<T, R, G>(out.ye + (size_t)q * D, nanv);
+    return false;
+  }
+  while (s.cursor < out.K && out.te[s.cursor] == s.t0) {
+    store_point<T, R, G>(out.ye + (size_t)s.cursor * D, s.y);
+    s.cursor++;
+  }
+  if (s.t1 == s.t0) {
+    s.status = ST_SUCCESS;
+    return false;
+  }
+  F.eval(s.t, s.y, s.k1);
+  if (o.h0 > 0.0) {
+    s.h = T(o.h0);
+    return true;
+  }
+  // starting step size, HNW Sec. II.4
+  T sc[R], w[R], f1[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) sc[r] = s.atol + s.rtol * fabs(s.y[r]);
+  const T d0 = rms_norm<T, R, G>(s.y, sc);
+  const T d1 = rms_norm<T, R, G>(s.k1, sc);
+  const T h0 = (d0 < T(1e-5) || d1 < T(1e-5)) ? T(1e-6) : T(0.01) * (d0 / d1);
+#pragma unroll
+  for (int r = 0; r < R; ++r) w[r] = s.y[r] + h0 * s.k1[r];
+  F.eval(s.t + (double)h0, w, f1);
+#pragma unroll
+  for (int r = 0; r < R; ++r) f1[r] = f1[r] - s.k1[r];
+  const T d2 = rms_norm<T, R, G>(f1, sc) / h0;
+  const T m = (d1 > d2) ? d1 : d2;
+  const T h1 = (m <= T(1e-15)) ? tmax(T(1e-6), h0 * T(1e-3)) : ctl_pow(T(0.01) / m, T(1.0 / 5.0));
+  T h = tmin(T(100) * h0, h1);
+  h = tmin(h, T(s.t1 - s.t0));
+  if (!(h > T(0) && finite_(h))) h = T(s.t1 - s.t0);
+  s.h = h;
+  return true;
+}
+
+// ---------------------------------------------------------------- one attempt (a3..a9)
+// Returns true while the instance is still running.
+template <class Field, typename T, int R, int G>
+__device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, int i, int D,
+                             const InstOut<T>& out, const TraceDev& tr) {
+  using C = DP5;
+  T h = s.h;
+  bool last = false;
+  if (s.t + (double)h >= s.t1) {
+    h = T(s.t1 - s.t);
+    last = true;
+  }
+  const double hd = (double)h;
+  T k2[R], k3[R], k4[R], k5[R], k6[R], k7[R], Y[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) Y[r] = s.y[r] + h * (T(C::a21) * s.k1[r]);
+  F.eval(s.t + C::c2 * hd, Y, k2);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::a31) * s.k1[r];
+    a = a + T(C::a32) * k2[r];
+    Y[r] = s.y[r] + h * a;
+  }
+  F.eval(s.t + C::c3 * hd, Y, k3);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::a41) * s.k1[r];
+    a = a + T(C::a42) * k2[r];
+    a = a + T(C::a43) * k3[r];
+    Y[r] = s.y[r] + h * a;
+  }
+  F.eval(s.t + C::c4 * hd, Y, k4);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::a51) * s.k1[r];
+    a = a + T(C::a52) * k2[r];
+    a = a + T(C::a53) * k3[r];
+    a = a + T(C::a54) * k4[r];
+    Y[r] = s.y[r] + h * a;
+  }
+  F.eval(s.t + C::c5 * hd, Y, k5);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::a61) * s.k1[r];
+    a = a + T(C::a62) * k2[r];
+    a = a + T(C::a63) * k3[r];
+    a = a + T(C::a64) * k4[r];
+    a = a + T(C::a65) * k5[r];
+    Y[r] = s.y[r] + h * a;
+  }
+  F.eval(s.t + hd, Y, k6);
+  T y1[R], inc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::b1) * s.k1[r];
+    a = a + T(C::b3) * k3[r];
+    a = a + T(C::b4) * k4[r];
+    a = a + T(C::b5) * k5[r];
+    a = a + T(C::b6) * k6[r];
+    inc[r] = h * a;
+    y1[r] = s.y[r] + inc[r];  // SSAL: the 7th stage input is the new solution
+  }
+  F.eval(s.t + hd, y1, k7);
+  // embedded error estimate and its norm
+  T ev[R], sc[R];
+  bool fin_local = true;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::e1) * s.k1[r];
+    a = a + T(C::e3) * k3[r];
+    a = a + T(C::e4) * k4[r];
+    a = a + T(C::e5) * k5[r];
+    a = a + T(C::e6) * k6[r];
+    a = a + T(C::e7) * k7[r];
+    ev[r] = h * a;
+    sc[r] = s.atol + s.rtol * tmax(fabs(s.y[r]), fabs(y1[r]));
+    fin_local = fin_local && finite_(y1[r]);
+  }
+  const T err = rms_norm<T, R, G>(ev, sc);
+  bool finite = finite_(err);
+  if constexpr (G > 1) finite = finite && (__all_sync(Grp<G>::mask(), fin_local) != 0);
+  else finite = finite && fin_local;
+  const bool accept = finite && err <= T(1);
+
+  const int att = s.n_acc + s.n_rej;
+  if (tr.cap > 0 && att < tr.cap && Grp<G>::rank() == 0) {
+    const size_t q = (size_t)i * tr.cap + att;
+    tr.t[q] = s.t;
+    tr.h[q] = hd;
+    tr.err[q] = (double)err;
+    tr.acc[q] = accept ? 1 : 0;
+  }
+
+  T h_next;
+  if (accept) {
+    const double t_next = last ? s.t1 : s.t + hd;
+    // new state (FP32: compensated sum y + (inc + ylo))
+    T yn[R], ylon[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if constexpr (Comp<T>::on) {
+        const T u = inc[r] + s.ylo[r];
+        yn[r] = s.y[r] + u;
+        ylon[r] = (s.y[r] - yn[r]) + u;
+      } else {
+        yn[r] = y1[r];
+        ylon[r] = T(0);
+      }
+    }
+    while (s.cursor < out.K) {
+      const double tq = out.te[s.cursor];
+      if (!(tq <= t_next)) break;
+      T* dst = out.ye + (size_t)s.cursor * D;
+      if (tq == t_next) {
+        store_point<T, R, G>(dst, yn);
+      } else {
+        T v[R];
+        dense_point<T, R>(T((tq - s.t) / hd), h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
+        store_point<T, R, G>(dst, v);
+      }
+      s.cursor++;
+    }
+    T fac;
+    if (err == T(0)) {
+      fac = T(o.fac_max);
+    } else {
+      fac = T(o.safety) * ctl_pow(err, T(-o.beta1));
+      if (o.beta2 != 0.0) fac = fac * ctl_pow(s.err_prev, T(o.beta2));
+    }
+    fac = tmin(tmax(fac, T(o.fac_min)), T(o.fac_max));
+    if (s.flags & FL_PREV_REJ) fac = tmin(fac, T(1));
+    h_next = h * fac;
+    s.err_prev = tmax(err, T(1e-4));
+    s.flags &= ~FL_PREV_REJ;
+    s.n_acc++;
+    s.t = t_next;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      s.y[r] = yn[r];
+      s.ylo[r] = ylon[r];
+      s.k1[r] = k7[r];  // FSAL
+    }
+    if (last) s.status = ST_SUCCESS;
+  } else {
+    const T fac = finite ? tmin(tmax(T(o.safety) * ctl_pow(err, T(-o.beta1)), T(o.fac_min)), T(1))
+                         : T(o.fac_min);
+    h_next = h * fac;
+    s.flags |= FL_PREV_REJ;
+    s.n_rej++;
+  }
+  s.h = h_next;
+  if (s.status == ST_RUNNING) {
+    const double scale = tmax(fabs(s.t), fabs(s.t1));
+    const double hn = (double)h_next;
+    if (s.t + hn == s.t || hn < 1e-14 * scale || !(h_next > T(0)))
+      s.status = finite ? ST_DT_UNDERFLOW : ST_NONFINITE;
+    else if (s.n_acc + s.n_rej >= o.max_steps)
+      s.status = ST_MAX_STEPS;
+  }
+  return s.status == ST_RUNNING;
+}
+
+// ---------------------------------------------------------------- finalize
+template <typename T, int R, int G>
+__device__ void inst_finalize(const Inst<T, R>& s, const SolveOpts& o, int i, int D,
+                              T* y_final, int32_t* n_acc, int32_t* n_rej, int32_t* n_fe,
+                              int32_t* status, const TraceDev& tr) {
+  const int g = Grp<G>::rank();
+  const bool invalid = s.status == ST_INVALID;
+#pragma unroll
+  for (int r = 0; r < R; ++r) y_final[(size_t)i * D + g * R + r] = invalid ? nan_(T(0)) : s.y[r];
+  if (g == 0) {
+    const int att = s.n_acc + s.n_rej;
+    n_acc[i] = s.n_acc;
+    n_rej[i] = s.n_rej;
+    const bool stepped = !invalid && s.t1 != s.t0;
+    n_fe[i] = stepped ? ((o.h0 > 0.0 ? 1 : 2) + 6 * att) : 0;
+    status[i] = s.status;
+    if (tr.cap > 0) tr.len[i] = att < tr.cap ? att : tr.cap;
+  }
+}
+
+// ---------------------------------------------------------------- work stealing
+// Hands the next instance index to every group of the calling lanes with one
+// atomic per warp (lanes of a group always arrive together).
+template <int G>
+__device__ __forceinline__ int grab_instance(int32_t* counter, int first_wave) {
+  if constexpr (G > 1) __syncwarp(Grp<G>::mask());
+  const unsigned active = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = lane - (lane % G);
+  const unsigned want = __ballot_sync(active, (lane % G) == 0);
+  const int first = __ffs(want) - 1;
+  int base = 0;
+  if (lane == first) base = atomicAdd(counter, __popc(want));
+  base = __shfl_sync(active, base, first < 0 ? 0 : first);
+  int mine = first_wave + base + __popc(want & ((1u << leader) - 1u));
+  if constexpr (G > 1) mine = __shfl_sync(Grp<G>::mask(), mine, 0, G);
+  return mine;
+}
+
+}  // namespace tode

@@ -1,0 +1,77 @@
+// tode_fields.cuh -- built-in SIMT vector fields evaluated by a lane group.
+//
+// Each field object is bound to one instance (its parameters are loaded into
+// registers once) and evaluates f(t, Y) for the group's R components.
+#pragma once
+#include "tode_core.cuh"
+
+namespace tode {
+
+// Van der Pol, Eq. 1 written as a first-order system (D = 2, G = 1, R = 2):
+//   y1' = y2,  y2' = mu (1 - y1^2) y2 - y1.
+template <typename T> struct VdpField {
+  T mu;
+  __device__ __forceinline__ void load(const T* mu_all, int i) { mu = mu_all[i]; }
+  __device__ __forceinline__ void eval(double, const T (&y)[2], T (&f)[2]) const {
+    f[0] = y[1];
+    f[1] = mu * (T(1) - y[0] * y[0]) * y[1] - y[0];
+  }
+};
+
+// y' = A_i y, D = G*R; lane g owns rows g*R .. g*R+R-1 of A_i and gathers
+// the whole state from its group with shuffles.
+template <typename T, int R, int G> struct LinearField {
+  static constexpr int D = G * R;
+  T a[R][D];
+  __device__ __forceinline__ void load(const T* A_all, int i) {
+    const int g = Grp<G>::rank();
+    const T* A = A_all + (size_t)i * D * D + (size_t)g * R * D;
+    if constexpr (sizeof(T) == 4 && (D % 4) == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < D; c += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(A + r * D + c);
+          a[r][c] = v.x;
+          a[r][c + 1] = v.y;
+          a[r][c + 2] = v.z;
+          a[r][c + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) a[r][c] = A[r * D + c];
+    }
+  }
+  __device__ __forceinline__ void gather(const T (&y)[R], T (&yall)[D]) const {
+#pragma unroll
+    for (int j = 0; j < D; ++j) yall[j] = Grp<G>::bcast(y[j % R], j / R);
+  }
+  __device__ __forceinline__ void eval(double, const T (&y)[R], T (&f)[R]) const {
+    T yall[D];
+    gather(y, yall);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if constexpr (sizeof(T) == 8 || D < 8) {
+        // FP64: left-to-right sum (reproducible); small D: nothing to split
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) s = s + a[r][c] * yall[c];
+        f[r] = s;
+      } else {
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+        for (int c = 0; c < D; c += 4) {
+          s0 = fmaf(a[r][c], yall[c], s0);
+          s1 = fmaf(a[r][c + 1], yall[c + 1], s1);
+          s2 = fmaf(a[r][c + 2], yall[c + 2], s2);
+          s3 = fmaf(a[r][c + 3], yall[c + 3], s3);
+        }
+        f[r] = (s0 + s1) + (s2 + s3);
+      }
+    }
+  }
+};
+
+}  // namespace tode

@@ -1,0 +1,92 @@
+// tode_internal.h -- host-side requests passed from the C-ABI layer
+// (tode_api.cu) to the per-precision launchers (tode_simt_f64.cu,
+// tode_simt_f32.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/tode.h"
+
+namespace tode {
+
+struct SolveReq {
+  const tode_field_desc* f;
+  const tode_options* o;
+  int B, D, K;
+  const void* y0;
+  const double* t0;
+  const double* t1;
+  const double* te;
+  void* ye;
+  void* yf;
+  int32_t *n_acc, *n_rej, *n_fe, *status;
+  const tode_tape* tape;    // may be NULL
+  const tode_trace* trace;  // may be NULL
+  char* ws;                 // carved by the launcher
+  size_t ws_bytes;
+  cudaStream_t stream;
+  int num_sms;
+};
+
+struct AdjReq {
+  const tode_field_desc* f;
+  const tode_options* o;
+  int B, D, K;
+  const double* t0;
+  const double* t1;
+  const double* te;
+  const int32_t* n_acc;
+  const int32_t* status;
+  const tode_tape* tape;
+  const void* gye;
+  const void* gyf;
+  void* gy0;
+  void* gparam;
+  float* const* gW;
+  float* const* gb;
+  int32_t* overflow;
+  char* scratch;
+  size_t scratch_bytes;
+  cudaStream_t stream;
+  int num_sms;
+};
+
+#define TODE_CUDA_TRY(x)        \
+  do {                          \
+    if ((x) != cudaSuccess) {   \
+      (void)cudaGetLastError(); \
+      return TODE_ECUDA;        \
+    }                           \
+  } while (0)
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Workspace bytes of the SIMT solver for state dtype size `ts`.
+inline size_t simt_workspace_bytes(int B, int D, size_t ts, int form) {
+  size_t s = 0;
+  s += align256(256);  // any-active flag + work counter
+  if (form == TODE_PLAIN) {
+    s += 3 * align256((size_t)B * D * ts);  // y, y_lo, k1
+    s += align256((size_t)B * 8);           // t
+    s += 2 * align256((size_t)B * ts);      // h, err_prev
+    s += 2 * align256((size_t)B * 4);       // cursor, flags
+  }
+  return s;
+}
+
+// Scratch bytes of the SIMT adjoint: one segment of `stride` step-start
+// states per instance (y, t, h) plus the work counter.
+inline size_t simt_adjoint_scratch_bytes(int B, int D, size_t ts, int stride) {
+  return align256(256) + align256((size_t)stride * B * D * ts) +
+         align256((size_t)stride * B * 8) + align256((size_t)stride * B * ts);
+}
+
+tode_err simt_solve_f64(const SolveReq& r);
+tode_err simt_solve_f32(const SolveReq& r);
+tode_err simt_adjoint_f64(const AdjReq& r);
+tode_err simt_adjoint_f32(const AdjReq& r);
+
+bool simt_supported(int kind, int D);
+
+}  // namespace tode

@@ -1,0 +1,400 @@
+// tode_simt_adjoint.cuh -- discrete adjoint of the fixed-mesh dopri5 map for
+// the SIMT fields (torchode App. A: gradients by backpropagation through the
+// solver, i.e. discretize-then-optimize).
+//
+// Per instance, in reverse over its accepted steps n with (t_n, h_n) frozen:
+//   kbar_i = h b_i ybar_{n+1} + sum_{tau in (t_n, t_n+1]} h b_i(theta_tau) ybar_tau
+//   for i = 7..1:  g_i = J_f(Y_i)^T kbar_i,  dtheta += (df/dtheta)^T kbar_i,
+//                  kbar_j += h a_ij g_i  (j < i)
+//   ybar_n = ybar_{n+1} + sum_tau ybar_tau + sum_i g_i.
+// Step-start states come from the checkpoint tape: slot j holds the solver
+// state (including its FSAL stage) at the start of accepted step j*stride;
+// the segment up to the next slot is re-run with the forward routine (a
+// bit-identical mesh), its step-start states parked in scratch, then
+// reversed.
+#pragma once
+#include "tode_simt.cuh"
+
+namespace tode {
+
+// ---------------------------------------------------------------- adjoint fields
+template <typename T> struct VdpAdj {
+  static constexpr int R = 2, G = 1;
+  VdpField<T> f;
+  T gmu;
+  __device__ __forceinline__ void load(const T* p, int i) {
+    f.load(p, i);
+    gmu = T(0);
+  }
+  __device__ __forceinline__ void eval(double t, const T (&y)[2], T (&o)[2]) const {
+    f.eval(t, y, o);
+  }
+  // gy = J^T v with J = [[0, 1], [-2 mu y1 y2 - 1, mu (1 - y1^2)]]
+  __device__ __forceinline__ void vjp(const T (&y)[2], const T (&v)[2], T (&gy)[2]) {
+    const T mu = f.mu;
+    gy[0] = v[1] * (T(-2) * mu * y[0] * y[1] - T(1));
+    gy[1] = v[0] + v[1] * (mu * (T(1) - y[0] * y[0]));
+    gmu = gmu + v[1] * ((T(1) - y[0] * y[0]) * y[1]);
+  }
+  __device__ __forceinline__ void store_param(T* gp, int i, bool bad) const {
+    gp[i] = bad ? nan_(T(0)) : gmu;
+  }
+};
+
+template <typename T, int R_, int G_> struct LinearAdj {
+  static constexpr int R = R_, G = G_, D = R_ * G_;
+  LinearField<T, R, G> f;
+  T acol[R][D];  // columns g*R+r of A_i: acol[r][j] = A[j][g*R + r]
+  T gA[R][D];    // rows g*R+r of dL/dA_i
+  __device__ __forceinline__ void load(const T* p, int i) {
+    f.load(p, i);
+    const int g = Grp<G>::rank();
+    const T* A = p + (size_t)i * D * D;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        acol[r][j] = A[(size_t)j * D + g * R + r];
+        gA[r][j] = T(0);
+      }
+  }
+  __device__ __forceinline__ void eval(double t, const T (&y)[R], T (&o)[R]) const {
+    f.eval(t, y, o);
+  }
+  // gy = A^T v,  dL/dA += v Y^T
+  __device__ __forceinline__ void vjp(const T (&y)[R], const T (&v)[R], T (&gy)[R]) {
+    T vall[D], yall[D];
+    f.gather(v, vall);
+    f.gather(y, yall);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < D; ++j) s = s + acol[r][j] * vall[j];
+      gy[r] = s;
+#pragma unroll
+      for (int c = 0; c < D; ++c) gA[r][c] = gA[r][c] + v[r] * yall[c];
+    }
+  }
+  __device__ __forceinline__ void store_param(T* gp, int i, bool bad) const {
+    const int g = Grp<G>::rank();
+    T* dst = gp + (size_t)i * D * D + (size_t)g * R * D;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) dst[r * D + c] = bad ? nan_(T(0)) : gA[r][c];
+  }
+};
+
+template <typename T> struct AdjArgs {
+  int B, D, K;
+  const double* t0;
+  const double* t1;
+  const double* te;
+  const double* rtol_b;
+  const double* atol_b;
+  double rtol, atol;
+  const int32_t* n_acc;
+  const int32_t* status;
+  TapeDev<T> tape;
+  SolveOpts o;
+  const T* gye;
+  const T* gyf;
+  T* gy0;
+  T* gparam;
+  const T* fparam;
+  int32_t* overflow;
+  int32_t* counter;
+  T* sy;        // [stride][B][D]
+  double* st;   // [stride][B]
+  T* sh;        // [stride][B]
+};
+
+// Reverse one accepted step.  y: step-start state, yb: running cotangent,
+// q: cursor over the instance's evaluation points, from the last backwards.
+template <class AF, typename T, int R, int G>
+__device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, int D, double t,
+                                             T h, double t_next, const T (&y)[R], T (&yb)[R],
+                                             int& q) {
+  using C = DP5;
+  T Y[7][R], k[7][R];
+  const double hd = (double)h;
+#pragma unroll
+  for (int r = 0; r < R; ++r) Y[0][r] = y[r];
+  F.eval(t, Y[0], k[0]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) Y[1][r] = y[r] + h * (T(C::a21) * k[0][r]);
+  F.eval(t + C::c2 * hd, Y[1], k[1]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T s = T(C::a31) * k[0][r];
+    s = s + T(C::a32) * k[1][r];
+    Y[2][r] = y[r] + h * s;
+  }
+  F.eval(t + C::c3 * hd, Y[2], k[2]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T s = T(C::a41) * k[0][r];
+    s = s + T(C::a42) * k[1][r];
+    s = s + T(C::a43) * k[2][r];
+    Y[3][r] = y[r] + h * s;
+  }
+  F.eval(t + C::c4 * hd, Y[3], k[3]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T s = T(C::a51) * k[0][r];
+    s = s + T(C::a52) * k[1][r];
+    s = s + T(C::a53) * k[2][r];
+    s = s + T(C::a54) * k[3][r];
+    Y[4][r] = y[r] + h * s;
+  }
+  F.eval(t + C::c5 * hd, Y[4], k[4]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T s = T(C::a61) * k[0][r];
+    s = s + T(C::a62) * k[1][r];
+    s = s + T(C::a63) * k[2][r];
+    s = s + T(C::a64) * k[3][r];
+    s = s + T(C::a65) * k[4][r];
+    Y[5][r] = y[r] + h * s;
+  }
+  F.eval(t + hd, Y[5], k[5]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T s = T(C::b1) * k[0][r];
+    s = s + T(C::b3) * k[2][r];
+    s = s + T(C::b4) * k[3][r];
+    s = s + T(C::b5) * k[4][r];
+    s = s + T(C::b6) * k[5][r];
+    Y[6][r] = y[r] + h * s;
+  }
+  F.eval(t + hd, Y[6], k[6]);
+
+  // cotangents of the stage derivatives
+  const T bw[7] = {T(C::b1), T(0), T(C::b3), T(C::b4), T(C::b5), T(C::b6), T(0)};
+  T kb[7][R];
+#pragma unroll
+  for (int s = 0; s < 7; ++s)
+#pragma unroll
+    for (int r = 0; r < R; ++r) kb[s][r] = h * bw[s] * yb[r];
+  bool dense7 = false;
+  const int g = Grp<G>::rank();
+  while (q >= 0) {
+    const double tq = a.te[(size_t)i * a.K + q];
+    if (!(tq > t)) break;
+    if (a.gye) {
+      T gq[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + g * R + r];
+      T w[7];
+      if (tq == t_next) {
+#pragma unroll
+        for (int s = 0; s < 7; ++s) w[s] = bw[s];
+      } else {
+        const T th = T((tq - t) / hd);
+        w[0] = th * (T(C::q10) + th * (T(C::q11) + th * (T(C::q12) + th * T(C::q13))));
+        w[1] = T(0);
+        w[2] = th * (T(0) + th * (T(C::q31) + th * (T(C::q32) + th * T(C::q33))));
+        w[3] = th * (T(0) + th * (T(C::q41) + th * (T(C::q42) + th * T(C::q43))));
+        w[4] = th * (T(0) + th * (T(C::q51) + th * (T(C::q52) + th * T(C::q53))));
+        w[5] = th * (T(0) + th * (T(C::q61) + th * (T(C::q62) + th * T(C::q63))));
+        w[6] = th * (T(0) + th * (T(C::q71) + th * (T(C::q72) + th * T(C::q73))));
+        dense7 = true;
+      }
+#pragma unroll
+      for (int s = 0; s < 7; ++s)
+#pragma unroll
+        for (int r = 0; r < R; ++r) kb[s][r] = kb[s][r] + h * w[s] * gq[r];
+#pragma unroll
+      for (int r = 0; r < R; ++r) yb[r] = yb[r] + gq[r];
+    }
+    q--;
+  }
+  // reverse stage sweep
+  const T A[7][6] = {{T(0), T(0), T(0), T(0), T(0), T(0)},
+                     {T(C::a21), T(0), T(0), T(0), T(0), T(0)},
+                     {T(C::a31), T(C::a32), T(0), T(0), T(0), T(0)},
+                     {T(C::a41), T(C::a42), T(C::a43), T(0), T(0), T(0)},
+                     {T(C::a51), T(C::a52), T(C::a53), T(C::a54), T(0), T(0)},
+                     {T(C::a61), T(C::a62), T(C::a63), T(C::a64), T(C::a65), T(0)},
+                     {T(C::b1), T(0), T(C::b3), T(C::b4), T(C::b5), T(C::b6)}};
+#pragma unroll
+  for (int s = 6; s >= 0; --s) {
+    if (s == 6 && !dense7) continue;  // kbar_7 = 0 without interior dense points
+    T gs[R];
+    F.vjp(Y[s], kb[s], gs);
+#pragma unroll
+    for (int l = 0; l < s; ++l)
+#pragma unroll
+      for (int r = 0; r < R; ++r) kb[l][r] = kb[l][r] + h * A[s][l] * gs[r];
+#pragma unroll
+    for (int r = 0; r < R; ++r) yb[r] = yb[r] + gs[r];
+  }
+}
+
+template <class AF, typename T>
+__global__ void __launch_bounds__(256) k_adjoint(AdjArgs<T> a) {
+  constexpr int R = AF::R, G = AF::G;
+  const int D = a.D;
+  const int groups_total = (int)((gridDim.x * (size_t)blockDim.x) / G);
+  int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
+  const int g = Grp<G>::rank();
+  SolveOpts ro = a.o;
+  ro.max_steps = 0x7fffffff;  // the re-run never stops on a step count
+  TraceDev no_trace{};
+  no_trace.cap = 0;
+  InstOut<T> no_out{};
+  no_out.K = 0;
+  while (i < a.B) {
+    AF F;
+    F.load(a.fparam, i);
+    const int N = a.n_acc[i];
+    const int m = a.tape.stride;
+    const int nseg = (N + m - 1) / m;
+    bool bad = a.status[i] != ST_SUCCESS;
+    if (!bad && nseg > a.tape.slots) {
+      bad = true;
+      if (g == 0) *a.overflow = 1;
+    }
+    T yb[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
+    int q = a.K - 1;
+    const double t1 = a.t1[i];
+    for (int j = nseg - 1; j >= 0 && !bad; --j) {
+      const int n0 = j * m;
+      const int n1 = (n0 + m < N) ? n0 + m : N;
+      // restore the slot and re-run the forward over the segment
+      Inst<T, R> s;
+      const size_t o = (size_t)j * a.B + i;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        s.y[r] = a.tape.y[o * D + g * R + r];
+        s.ylo[r] = Comp<T>::on ? a.tape.ylo[o * D + g * R + r] : T(0);
+        s.k1[r] = a.tape.k1[o * D + g * R + r];
+      }
+      s.t = a.tape.t[o];
+      s.h = a.tape.h[o];
+      s.err_prev = a.tape.err_prev[o];
+      s.flags = a.tape.flags[o];
+      s.t0 = a.t0[i];
+      s.t1 = t1;
+      s.rtol = T(a.rtol_b ? a.rtol_b[i] : a.rtol);
+      s.atol = T(a.atol_b ? a.atol_b[i] : a.atol);
+      s.n_acc = n0;
+      s.n_rej = 0;
+      s.cursor = 0;
+      s.status = ST_RUNNING;
+      while (s.n_acc < n1 && s.status == ST_RUNNING) {
+        const int before = s.n_acc;
+        const double tb = s.t;
+        T hb = s.h;
+        if (tb + (double)hb >= t1) hb = T(t1 - tb);
+        T ys[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) ys[r] = s.y[r];
+        inst_attempt<AF, T, R, G>(F, s, ro, i, D, no_out, no_trace);
+        if (s.n_acc != before) {
+          const size_t p = (size_t)(before - n0) * a.B + i;
+#pragma unroll
+          for (int r = 0; r < R; ++r) a.sy[p * D + g * R + r] = ys[r];
+          if (g == 0) {
+            a.st[p] = tb;
+            a.sh[p] = hb;
+          }
+        }
+      }
+      if (s.n_acc < n1) {  // the re-run left the forward's mesh: cannot happen
+        bad = true;
+        break;
+      }
+      if constexpr (G > 1) __syncwarp(Grp<G>::mask());
+      for (int n = n1 - 1; n >= n0; --n) {
+        const size_t p = (size_t)(n - n0) * a.B + i;
+        T y[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) y[r] = a.sy[p * D + g * R + r];
+        const double t = a.st[p];
+        const T h = a.sh[p];
+        const double t_next = (n == N - 1) ? t1 : t + (double)h;
+        reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, yb, q);
+      }
+      if constexpr (G > 1) __syncwarp(Grp<G>::mask());
+    }
+    // evaluation points at t0 are y0 itself
+    if (!bad && a.gye) {
+      const double t0 = a.t0[i];
+      for (; q >= 0; --q) {
+        if (a.te[(size_t)i * a.K + q] == t0) {
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            yb[r] = yb[r] + a.gye[((size_t)i * a.K + q) * D + g * R + r];
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) a.gy0[(size_t)i * D + g * R + r] = bad ? nan_(T(0)) : yb[r];
+    if (a.gparam) F.store_param(a.gparam, i, bad);
+    i = grab_instance<G>(a.counter, groups_total);
+  }
+}
+
+template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
+  AdjArgs<T> a{};
+  a.B = r.B;
+  a.D = r.D;
+  a.K = r.K;
+  a.t0 = r.t0;
+  a.t1 = r.t1;
+  a.te = r.te;
+  a.rtol_b = r.o->rtol_b;
+  a.atol_b = r.o->atol_b;
+  a.rtol = r.o->rtol;
+  a.atol = r.o->atol;
+  a.n_acc = r.n_acc;
+  a.status = r.status;
+  a.tape = make_tape<T>(r.tape, r.B, r.D);
+  a.o = make_opts(r.o);
+  a.gye = (const T*)r.gye;
+  a.gyf = (const T*)r.gyf;
+  a.gy0 = (T*)r.gy0;
+  a.gparam = (T*)r.gparam;
+  a.fparam = (const T*)(r.f->kind == TODE_VDP ? r.f->mu : r.f->A);
+  a.overflow = r.overflow;
+  char* p = r.scratch;
+  a.counter = (int32_t*)p;
+  p += align256(256);
+  const int m = r.tape->stride;
+  a.sy = (T*)p;
+  p += align256((size_t)m * r.B * r.D * sizeof(T));
+  a.st = (double*)p;
+  p += align256((size_t)m * r.B * 8);
+  a.sh = (T*)p;
+  const int block = 256;
+  int per_sm = 0;
+  TODE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<AF, T>, block, 0));
+  if (per_sm < 1) per_sm = 1;
+  long long grid = (long long)r.num_sms * per_sm;
+  const long long need = ((long long)r.B * AF::G + block - 1) / block;
+  if (grid > need) grid = need;
+  if (grid == 0) return TODE_OK;
+  TODE_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int32_t), r.stream));
+  k_adjoint<AF, T><<<(int)grid, block, 0, r.stream>>>(a);
+  TODE_CUDA_TRY(cudaGetLastError());
+  return TODE_OK;
+}
+
+template <typename T> tode_err simt_adjoint(const AdjReq& r) {
+  if (r.f->kind == TODE_VDP) return launch_adjoint<VdpAdj<T>, T>(r);
+  switch (r.D) {
+    case 1: return launch_adjoint<LinearAdj<T, 1, 1>, T>(r);
+    case 2: return launch_adjoint<LinearAdj<T, 1, 2>, T>(r);
+    case 4: return launch_adjoint<LinearAdj<T, 1, 4>, T>(r);
+    case 8: return launch_adjoint<LinearAdj<T, 1, 8>, T>(r);
+    case 16: return launch_adjoint<LinearAdj<T, 1, 16>, T>(r);
+    case 32: return launch_adjoint<LinearAdj<T, 2, 16>, T>(r);
+    default: return TODE_EUNSUPPORTED;
+  }
+}
+
+}  // namespace tode

@@ -1,0 +1,7 @@
+// FP32-state instantiation of the SIMT solver (time stays FP64).
+#include "tode_simt_adjoint.cuh"
+
+namespace tode {
+tode_err simt_solve_f32(const SolveReq& r) { return simt_solve<float>(r); }
+tode_err simt_adjoint_f32(const AdjReq& r) { return simt_adjoint<float>(r); }
+}  // namespace tode

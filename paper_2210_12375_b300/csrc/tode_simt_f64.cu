@@ -1,0 +1,9 @@
+// FP64 instantiation of the SIMT solver.  Built with -fmad=false so that no
+// multiply-add is contracted and every sum is taken left to right: the FP64
+// path's accept/reject decisions are reproducible on any IEEE-754 machine.
+#include "tode_simt_adjoint.cuh"
+
+namespace tode {
+tode_err simt_solve_f64(const SolveReq& r) { return simt_solve<double>(r); }
+tode_err simt_adjoint_f64(const AdjReq& r) { return simt_adjoint<double>(r); }
+}  // namespace tode

@@ -1,0 +1,147 @@
+"""The C-ABI library loads without a GPU, exports every entry point that
+include/tode.h declares, and rejects bad arguments before touching a device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2210_12375_b300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(tode_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _abi.load()
+    declared = _declared()
+    assert declared, "no declarations found"
+    out = subprocess.run(["nm", "-D", "--defined-only", _abi.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (tode_[a-z0-9_]+)", out))
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+    for n in declared:
+        getattr(lib, n)
+    assert set(_abi.EXPORTS) <= set(declared)
+    assert lib.tode_version() == 1
+
+
+def test_default_options_and_strerror():
+    lib = _abi.load()
+    o = _abi.Options()
+    lib.tode_default_options(C.byref(o))
+    assert (o.rtol, o.atol, o.safety, o.fac_min, o.fac_max, o.beta1, o.beta2) == \
+        (1e-6, 1e-6, 0.9, 0.2, 10.0, 0.2, 0.0)
+    assert o.max_steps == 100000 and o.form == _abi.TODE_FUSED and o.prec == _abi.TODE_F32
+    for code in range(6):
+        assert lib.tode_strerror(code)
+
+
+def _desc(kind, B, D):
+    f = _abi.FieldDesc()
+    f.kind, f.B, f.D = kind, B, D
+    f.mu = 0x1000
+    f.A = 0x1000
+    return f
+
+
+def _opts(**kw):
+    lib = _abi.load()
+    o = _abi.Options()
+    lib.tode_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def test_workspace_size_rules():
+    lib = _abi.load()
+    o = _opts(prec=_abi.TODE_F64, form=_abi.TODE_PLAIN)
+    n = lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 1000, 2)), C.byref(o), 16)
+    assert n > 1000 * 2 * 8 * 3 and n % 256 == 0
+    o2 = _opts(prec=_abi.TODE_F64, form=_abi.TODE_FUSED)
+    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 1000, 2)), C.byref(o2), 16) == 256
+    # unsupported or invalid combinations report 0
+    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 10, 3)), C.byref(o), 1) == 0
+    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_LINEAR, 10, 5)), C.byref(o), 1) == 0
+    bad = _opts(fac_min=2.0)
+    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 10, 2)), C.byref(bad), 1) == 0
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (dict(rtol=-1.0), _abi.TODE_EINVAL),
+    (dict(max_steps=0), _abi.TODE_EINVAL),
+    (dict(form=7), _abi.TODE_EINVAL),
+    (dict(beta1=0.0), _abi.TODE_EINVAL),
+    (dict(prec=_abi.TODE_BF16W), _abi.TODE_EUNSUPPORTED),
+])
+def test_solve_rejects_bad_options_before_launch(mutate, code):
+    lib = _abi.load()
+    o = _opts(**mutate)
+    f = _desc(_abi.TODE_VDP, 4, 2)
+    p = C.c_void_p(0x1000)
+    rc = lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, None, None, p,
+                        C.c_size_t(1 << 20), None)
+    assert rc == code
+
+
+def test_solve_rejects_null_pointers_and_small_workspace():
+    lib = _abi.load()
+    o = _opts(prec=_abi.TODE_F64)
+    f = _desc(_abi.TODE_VDP, 4, 2)
+    p = C.c_void_p(0x1000)
+    # null y0
+    assert lib.tode_solve(C.byref(f), C.byref(o), None, p, p, p, 2, p, p, p, p, p, p, None, None,
+                          p, C.c_size_t(1 << 20), None) == _abi.TODE_EINVAL
+    # K > 0 without t_eval
+    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, None, 2, p, p, p, p, p, p, None, None,
+                          p, C.c_size_t(1 << 20), None) == _abi.TODE_EINVAL
+    # workspace too small / misaligned
+    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, None, None,
+                          p, C.c_size_t(8), None) == _abi.TODE_EWORKSPACE
+    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, None, None,
+                          C.c_void_p(0x1008), C.c_size_t(1 << 20), None) == _abi.TODE_EWORKSPACE
+    # empty batch is a no-op
+    f0 = _desc(_abi.TODE_VDP, 0, 2)
+    assert lib.tode_solve(C.byref(f0), C.byref(o), None, None, None, None, 0, None, None, None,
+                          None, None, None, None, None, None, C.c_size_t(0), None) == _abi.TODE_OK
+    # bad tape: no slots, or an FP32 tape without its compensation buffer
+    tp = _abi.Tape()
+    tp.slots, tp.stride = 0, 1
+    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, C.byref(tp),
+                          None, p, C.c_size_t(1 << 20), None) == _abi.TODE_EINVAL
+    tp.slots = 2
+    tp.y = tp.t = tp.h = tp.err_prev = tp.flags = tp.k1 = 0x1000
+    o32 = _opts(prec=_abi.TODE_F32)
+    assert lib.tode_solve(C.byref(f), C.byref(o32), p, p, p, p, 2, p, p, p, p, p, p, C.byref(tp),
+                          None, p, C.c_size_t(1 << 20), None) == _abi.TODE_EINVAL
+
+
+def test_adjoint_rejects_bad_arguments():
+    lib = _abi.load()
+    o = _opts(prec=_abi.TODE_F64)
+    f = _desc(_abi.TODE_VDP, 4, 2)
+    p = C.c_void_p(0x1000)
+    tp = _abi.Tape()
+    tp.slots, tp.stride = 2, 1
+    tp.y = tp.t = tp.h = tp.err_prev = tp.flags = tp.k1 = tp.y_lo = 0x1000
+    need = lib.tode_adjoint_scratch_size(C.byref(f), C.byref(o), C.byref(tp))
+    assert need > 0 and need % 256 == 0
+    # null gy0
+    assert lib.tode_adjoint(C.byref(f), C.byref(o), p, p, p, 2, p, p, C.byref(tp), p, p, None,
+                            p, None, None, p, p, C.c_size_t(need), None) == _abi.TODE_EINVAL
+    # scratch one byte short
+    assert lib.tode_adjoint(C.byref(f), C.byref(o), p, p, p, 2, p, p, C.byref(tp), p, p, p,
+                            p, None, None, p, p, C.c_size_t(need - 1), None) == \
+        _abi.TODE_EWORKSPACE

@@ -1,0 +1,106 @@
+"""GPU discrete adjoint (App. A: backpropagation through the solver on the
+frozen mesh) against the FP64 oracle adjoint on the GPU's own mesh, against
+central finite differences, and checkpoint-stride invariance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2210_12375_b300 as tode
+from gpu_helpers import gpu_solve, make
+from oracle.oracle import mesh_from_trace
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(w, dtype, form, stride, slots=None, gy_seed=1, **kw):
+    B, D = w["y0"].shape
+    probe = gpu_solve(w, dtype, form, trace_cap=20000, **kw)
+    N = int(probe["n_acc"].max())
+    if slots is None:
+        slots = max(1, -(-N // stride))
+    tape = tode.TapeBuffers.allocate(B, D, dtype, slots, stride, "cuda")
+    g = gpu_solve(w, dtype, form, tape=tape, **kw)
+    rng = np.random.default_rng(gy_seed)
+    gye = rng.standard_normal(g["y_eval"].shape)
+    gyf = rng.standard_normal(g["y_final"].shape)
+    dev = g["_dev"]
+    gy0, gp, ovf = tode.adjoint(dev["field"], dev["t0"], dev["t1"], dev["te"], g["_sol"], tape,
+                                torch.tensor(gye, dtype=dtype, device="cuda"),
+                                torch.tensor(gyf, dtype=dtype, device="cuda"),
+                                rtol=kw.get("rtol", w["rtol"]), atol=kw.get("atol", w["atol"]),
+                                **{k: v for k, v in kw.items() if k not in ("rtol", "atol")})
+    torch.cuda.synchronize()
+    return dict(probe=probe, fwd=g, gy0=gy0.double().cpu().numpy(),
+                gp=gp.double().cpu().numpy(), ovf=int(ovf.item()), gye=gye, gyf=gyf)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+@pytest.mark.parametrize("form", ["plain", "fused"])
+def test_adjoint_f64_vs_oracle_adjoint(cfg, form):
+    w = make(cfg, B=64 if cfg == 2 else 256)
+    r = _run(w, torch.float64, form, stride=1)
+    assert r["ovf"] == 0
+    mt, mh, mn = mesh_from_trace(r["probe"])
+    ref = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"],
+                         r["gye"], r["gyf"])
+    assert _rel(r["gy0"], ref["gy0"]) <= 1e-10
+    key = "gmu" if cfg == 1 else "gA"
+    assert _rel(r["gp"], ref[key]) <= 1e-10
+    for i in range(0, w["B"], 7):
+        assert _rel(r["gy0"][i], ref["gy0"][i]) <= 1e-10
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_adjoint_recompute_stride_is_bitwise(cfg):
+    """A small checkpoint budget (one slot every m accepted steps, segments
+    recomputed) gives gradients bitwise equal to full storage."""
+    w = make(cfg, B=200)
+    dtype = torch.float64 if cfg == 1 else torch.float32
+    a = _run(w, dtype, "fused", stride=1)
+    for m in (3, 8):
+        b = _run(w, dtype, "fused", stride=m)
+        assert np.array_equal(a["gy0"], b["gy0"])
+        assert np.array_equal(a["gp"], b["gp"])
+
+
+def test_adjoint_overflow_is_reported():
+    w = make(1, B=32)
+    r = _run(w, torch.float64, "fused", stride=1, slots=3)
+    assert r["ovf"] == 1
+    assert np.isnan(r["gy0"]).all()
+
+
+def test_adjoint_f64_vs_central_fd():
+    w = make(1, B=4)
+    r = _run(w, torch.float64, "fused", stride=1)
+    mt, mh, mn = mesh_from_trace(r["probe"])
+
+    def loss(y0):
+        rr = oracle.replay(w["field"], y0, w["t0"], w["t1"], mt, mh, mn, w["t_eval"])
+        return float((r["gye"] * rr["y_eval"]).sum() + (r["gyf"] * rr["y_final"]).sum())
+
+    num = np.zeros_like(w["y0"])
+    for i in range(4):
+        for j in range(2):
+            eps = 1e-6 * max(1.0, abs(w["y0"][i, j]))
+            yp = w["y0"].copy()
+            yp[i, j] += eps
+            ym = w["y0"].copy()
+            ym[i, j] -= eps
+            num[i, j] = (loss(yp) - loss(ym)) / (2 * eps)
+    assert _rel(r["gy0"], num) <= 1e-6
+
+
+def test_adjoint_f32_linear_vs_oracle():
+    w = make(2, B=512)
+    r = _run(w, torch.float32, "fused", stride=1)
+    mt, mh, mn = mesh_from_trace(r["probe"])
+    ref = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"],
+                         r["gye"], r["gyf"])
+    assert _rel(r["gy0"], ref["gy0"]) <= 1e-4
+    assert _rel(r["gp"], ref["gA"]) <= 1e-4
