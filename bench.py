@@ -1,0 +1,429 @@
+"""Benchmark: batched adaptive dopri5 instance-steps/s, forward + discrete
+adjoint, fused persistent form vs plain per-step form, on one B300.
+
+Default workload: linear y' = A_i y, D = 16, FP32 state / FP64 time,
+B = 8192, 32 t_eval, rtol = atol = 1e-5 (A_i = Q diag(-lambda) Q^T).  One
+"step" is one pass of the whole solver path over the batch: the fused
+forward solve (stages, error norm, PI control, dense output, checkpoint
+tape) followed by the discrete adjoint of L = <c, y(t_eval)> + <d, y(t1)>
+for fixed seeded cotangents c, d.  An instance-step is one attempted step
+of a live instance.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--workload 2|3|1]
+Under torchrun (N > 1) every rank solves its own copy of the batch (weak
+scaling, no data-path collective) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2210_12375_b300 import workloads  # noqa: E402
+
+METRIC = "instance-steps/s, dopri5 fwd and fwd+adjoint, fused vs plain form at matched error"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="tode", choices=["tode", "reference"])
+    p.add_argument("--workload", type=int, default=2)
+    p.add_argument("--plain-steps", type=int, default=30)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+            "sm_max_mhz": 2032.0}, "fallback"
+
+
+def flops_per_attempt(kind: str, D: int) -> float:
+    """Algorithmic FLOPs of one attempted dopri5 step (FMA = 2 FLOPs): six
+    field evaluations, the 20 stage-combination terms plus 6 state updates per
+    component, the 6-term error estimate and its weighted norm."""
+    f_eval = 2 * D * D if kind == "linear" else 6
+    comb = 2 * (20 + 6 + 7) * D + 6 * D
+    return 6 * f_eval + comb
+
+
+def adjoint_flops_per_step(kind: str, D: int) -> float:
+    """Algorithmic FLOPs of reversing one accepted step: 7 stage
+    re-evaluations, 6 transposed-Jacobian products with their parameter outer
+    products, and the stage-cotangent combinations."""
+    if kind == "linear":
+        f_eval, vjp = 2 * D * D, 4 * D * D
+    else:
+        f_eval, vjp = 6, 12
+    return 7 * f_eval + 6 * vjp + 2 * (26 + 21) * D
+
+
+def _events(torch, n):
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(n)]
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_tode(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2210_12375_b300 as tode
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    w = workloads.make(args.workload)
+    kind = w["field"]["kind"]
+    dtype = torch.float64 if w["prec"] == "f64" else torch.float32
+    B, D = w["y0"].shape
+    K = w["t_eval"].shape[1]
+    if kind == "linear":
+        field = tode.Linear(torch.tensor(w["field"]["A"], dtype=dtype, device=dev).contiguous())
+    else:
+        field = tode.VdP(torch.tensor(w["field"]["mu"], dtype=dtype, device=dev))
+    y0 = torch.tensor(w["y0"], dtype=dtype, device=dev)
+    t0 = torch.tensor(w["t0"], dtype=torch.float64, device=dev)
+    t1 = torch.tensor(w["t1"], dtype=torch.float64, device=dev)
+    te = torch.tensor(w["t_eval"], dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(20221022)
+    gye = torch.tensor(rng.standard_normal((B, K, D)), dtype=dtype, device=dev)
+    gyf = torch.tensor(rng.standard_normal((B, D)), dtype=dtype, device=dev)
+    opt = dict(rtol=w["rtol"], atol=w["atol"])
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # probe: step counts (identical every pass) and the tape size
+    probe = tode.solve(field, y0, t0, t1, te, form="fused", **opt)
+    torch.cuda.synchronize()
+    assert int((probe.status != 0).sum().item()) == 0, "benchmark workload must solve cleanly"
+    n_att = int((probe.n_acc.long() + probe.n_rej.long()).sum().item())
+    n_acc_total = int(probe.n_acc.long().sum().item())
+    n_acc_max = int(probe.n_acc.max().item())
+    tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev)
+
+    def fwd(form, sol=None, ws=None):
+        return tode.solve(field, y0, t0, t1, te, form=form, tape=tape, out=sol, workspace=ws,
+                          **opt)
+
+    def step(form, sol=None, ws=None, scratch=None):
+        s = fwd(form, sol, ws)
+        return s, tode.adjoint(field, t0, t1, te, s, tape, gye, gyf, scratch=scratch, **opt)
+
+    # matched error: both forms against the exact solution of the same batch
+    sol_f = fwd("fused")
+    sol_p = fwd("plain")
+    torch.cuda.synchronize()
+    same = bool(torch.equal(sol_f.y_eval, sol_p.y_eval))
+    err = None
+    if kind == "linear":
+        Q, lam = w["field"]["Q"], w["field"]["lam"]
+        c = np.einsum("bji,bj->bi", Q, w["y0"])
+        ex = np.exp(-lam[:, None, :] * w["t_eval"][:, :, None])
+        exact = np.einsum("bij,bkj->bki", Q, ex * c[:, None, :])
+        ye = sol_f.y_eval.double().cpu().numpy()
+        err = float(np.max(np.abs(ye - exact) / (w["atol"] + w["rtol"] * np.abs(exact))))
+
+    def timed(form, nsteps, with_adj=True):
+        sol = fwd(form)
+        ws = sol.extra["workspace"]
+        for _ in range(args.warmup):
+            if with_adj:
+                step(form, sol, ws)
+            else:
+                fwd(form, sol, ws)
+        torch.cuda.synchronize()
+        ev = _events(torch, nsteps)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for k in range(nsteps):
+            flush.zero_()  # L2 flush, outside the timed events
+            ev[k][0].record(stream)
+            if with_adj:
+                step(form, sol, ws)
+            else:
+                fwd(form, sol, ws)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+        ms = float(sum(a.elapsed_time(b) for a, b in ev))
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms, wall
+
+    def kernel_ms(nrep, adjoint_only):
+        sol = fwd("fused")
+        ws = sol.extra["workspace"]
+        torch.cuda.synchronize()
+        ev = _events(torch, nrep)
+        for k in range(nrep):
+            flush.zero_()
+            ev[k][0].record(stream)
+            if adjoint_only:
+                tode.adjoint(field, t0, t1, te, sol, tape, gye, gyf, **opt)
+            else:
+                fwd("fused", sol, ws)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    nk = max(20, args.steps // 4)
+    with ClockSampler(local) as clk:
+        ms_fused, wall_fused = timed("fused", args.steps, True)
+        k_fwd_ms = kernel_ms(nk, False)
+        k_adj_ms = kernel_ms(nk, True)
+    clocks = clk.summary()
+    ms_fused_fwd, _ = timed("fused", nk, False)
+    ms_plain, _ = timed("plain", args.plain_steps, True)
+    ms_plain_fwd, _ = timed("plain", args.plain_steps, False)
+
+    per_step = ms_fused / args.steps
+    value = world * n_att / (per_step * 1e-3)
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {k: v.cpu().pin_memory() for k, v in dict(
+            y0=y0, t0=t0, t1=t1, te=te, gye=gye, gyf=gyf, P=field.params()).items()}
+        dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+        field_e2e = tode.Linear(dev_in["P"]) if kind == "linear" else tode.VdP(dev_in["P"])
+        sol = fwd("fused")
+        out_h = {}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+
+        def e2e_step():
+            for k, v in host.items():
+                dev_in[k].copy_(v, non_blocking=True)
+            s = tode.solve(field_e2e, dev_in["y0"], dev_in["t0"], dev_in["t1"], dev_in["te"],
+                           form="fused", tape=tape, out=sol, workspace=sol.extra["workspace"],
+                           **opt)
+            g0, gp, _ = tode.adjoint(field_e2e, dev_in["t0"], dev_in["t1"], dev_in["te"], s,
+                                     tape, dev_in["gye"], dev_in["gyf"], **opt)
+            res = dict(y_eval=s.y_eval, y_final=s.y_final, n_acc=s.n_acc, n_rej=s.n_rej,
+                       n_feval=s.n_feval, status=s.status, gy0=g0, gp=gp)
+            for k, v in res.items():
+                if k not in out_h:
+                    out_h[k] = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+                out_h[k].copy_(v, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        d2h = sum(v.numel() * v.element_size() for v in out_h.values())
+        ev = _events(torch, nk)
+        for k in range(nk):
+            flush.zero_()
+            ev[k][0].record(stream)
+            e2e_step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = float(sum(a.elapsed_time(b) for a, b in ev)) / nk
+        if world > 1:
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": world * n_att / (ms_e2e * 1e-3), "unit": "instance-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": ms_e2e}
+
+    peaks, src = _peaks()
+    clk_mhz = peaks.get("sm_max_mhz", 2032.0)
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sms * 128 * 2 * clk_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 FLOPs
+    achieved = flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "k_fused<LinearField<float,1,16>> (fused forward)",
+                "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {clk_mhz:.0f} MHz",
+                "kernel_ms": k_fwd_ms}
+    breakdown = {
+        "fused_fwd_adj": value,
+        "fused_fwd": world * n_att / (ms_fused_fwd / nk * 1e-3),
+        "plain_fwd_adj": world * n_att / (ms_plain / args.plain_steps * 1e-3),
+        "plain_fwd": world * n_att / (ms_plain_fwd / args.plain_steps * 1e-3),
+        "fused_over_plain_fwd_adj": (ms_plain / args.plain_steps) / per_step,
+        "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
+        "adjoint_kernel_ms": k_adj_ms,
+        "adjoint_achieved_tflops": adjoint_flops_per_step(kind, D) * n_acc_total
+        / (k_adj_ms * 1e-3) / 1e12,
+        "max_err_over_tol_vs_closed_form": err,
+        "fused_equals_plain_bitwise": same,
+        "instance_steps_per_pass": n_att,
+    }
+    result = {
+        "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded, shaped like the paper's workloads)",
+        "config": {"workload": w["name"], "B": B, "D": D, "K": K, "rtol": w["rtol"],
+                   "atol": w["atol"], "form": "fused", "pass": "fwd+adjoint",
+                   "state": "f32 (compensated), time f64", "controller": "I (beta1=0.2)",
+                   "l2": "flushed between timed steps (256 MiB write outside the events)",
+                   "parallelism": f"dp{world} (independent replicas of the batch)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks, "e2e": e2e, "roofline": roofline, "breakdown": breakdown,
+        "wall_s_timed_region": wall_fused,
+    }
+    if rank == 0 and not args.no_cpu and world == 1:
+        result["cpu_baseline"] = cpu_baseline(w, budget_s=12.0)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_baseline(w, budget_s=12.0, nthreads=0):
+    """The FP64 oracle as it stands, forward + adjoint, on a seeded prefix of
+    the same workload sized to take roughly `budget_s` seconds."""
+    import oracle
+    from oracle.oracle import mesh_from_trace
+
+    def run(n):
+        ws = workloads.make(w["cfg"], n)
+        t = time.perf_counter()
+        r = oracle.solve(ws["field"], ws["y0"], ws["t0"], ws["t1"], ws["t_eval"],
+                         dict(rtol=ws["rtol"], atol=ws["atol"]), trace_cap=8192,
+                         nthreads=nthreads)
+        mt, mh, mn = mesh_from_trace(r)
+        K, D = ws["t_eval"].shape[1], ws["y0"].shape[1]
+        rng = np.random.default_rng(1)
+        oracle.adjoint(ws["field"], ws["y0"], ws["t0"], ws["t1"], mt, mh, mn, ws["t_eval"],
+                       rng.standard_normal((n, K, D)), rng.standard_normal((n, D)),
+                       nthreads=nthreads)
+        dt = time.perf_counter() - t
+        return int((r["n_acc"] + r["n_rej"]).sum()), dt, r["threads"]
+
+    n = 64
+    att, dt, thr = run(n)
+    while dt < budget_s / 4 and n < w["B"]:
+        n = min(w["B"], int(n * max(2.0, budget_s / max(dt, 1e-3) * 0.8)))
+        att, dt, thr = run(n)
+    return {"value": att / dt, "unit": "instance-steps/s", "cores": thr, "kind": "oracle",
+            "sample": f"first {n} of {w['B']} instances of {w['name']}, fwd+adjoint, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    w = workloads.make(args.workload)
+    for _ in range(args.warmup):
+        cpu_baseline(w, budget_s=0.3)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(w, budget_s=min(2.0, 120.0 / max(args.steps, 1)))
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "instance-steps/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall / max(args.steps, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded, shaped like the paper's workloads)",
+        "config": {"workload": w["name"], "B": w["B"], "pass": "fwd+adjoint",
+                   "form": "oracle (scalar C, one thread per core)"},
+        "cpu_baseline": {"value": v, "unit": "instance-steps/s", "cores": last["cores"],
+                         "kind": "oracle", "sample": last["sample"]},
+        "e2e": {"value": v, "unit": "instance-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_tode(a)
