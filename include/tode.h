@@ -194,6 +194,35 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
                       float* const* gb, int32_t* overflow, void* scratch, size_t scratch_bytes,
                       void* stream);
 
+/* Size of the device scratch that tode_adjoint_static keeps inside the
+ * library (32 MiB on every GPU that loads it). */
+#define TODE_STATIC_ADJOINT_SCRATCH_BYTES (32u << 20)
+
+/* tode_adjoint without a scratch argument, for callers that cannot allocate
+ * device memory: code that only receives its input and output buffers from a
+ * host framework (a plugin interface, for instance) and has no allocator of
+ * its own, or code that must not call cudaMalloc in a latency-critical loop
+ * because it can synchronise the device.  The paper has no counterpart; this
+ * is a deployment convenience.
+ *  - Arguments, outputs and errors are those of tode_adjoint minus scratch.
+ *    The scratch is a library-owned device array of
+ *    TODE_STATIC_ADJOINT_SCRATCH_BYTES; a problem whose
+ *    tode_adjoint_scratch_size exceeds it is rejected with TODE_EWORKSPACE
+ *    before any device work (lower tape->stride or split the batch).
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current (cudaGetSymbolAddress) and caches it; make that
+ *    first call before any stream capture.
+ *  - All calls on a device share the one array, which keeps the last call's
+ *    contents (the work counter is cleared on `stream` at every call).  Calls
+ *    that can overlap on the GPU (different streams, or several host
+ *    threads) race on it: serialise them. */
+tode_err tode_adjoint_static(const tode_field_desc* f, const tode_options* o, const double* t0,
+                             const double* t1, const double* t_eval, int K, const int32_t* n_acc,
+                             const int32_t* status, const tode_tape* tape, const void* gy_eval,
+                             const void* gy_final, void* gy0, void* gparam, float* const* gW,
+                             float* const* gb, int32_t* overflow, void* stream);
+
 /* Static text for an error code. */
 const char* tode_strerror(tode_err e);
 

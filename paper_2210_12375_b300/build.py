@@ -26,6 +26,7 @@ UNITS = {
     "tode_api.cu": [],
     "tode_simt_f64.cu": ["-fmad=false"],
     "tode_simt_f32.cu": [],
+    "tode_static.cu": [],
 }
 
 
