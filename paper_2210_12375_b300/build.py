@@ -25,7 +25,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
 UNITS = {
     "tode_api.cu": [],
     "tode_simt_f64.cu": ["-fmad=false"],
-    "tode_simt_f32.cu": [],
+    "tode_simt_f32.cu": ["-fmad=false"],
     "tode_static.cu": [],
 }
 

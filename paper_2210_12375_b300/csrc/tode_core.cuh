@@ -66,12 +66,31 @@ enum : int { ST_SUCCESS = 0, ST_MAX_STEPS = 1, ST_DT_UNDERFLOW = 2, ST_NONFINITE
 enum : int { FL_PREV_REJ = 1 };
 
 // ---------------------------------------------------------------- scalar helpers
+// a*b + c.  Both translation units are built with -fmad=false, so nothing is
+// contracted behind the source's back: FP32 multiply-adds are written as
+// explicit fused operations (identical in every kernel that inlines this
+// routine), FP64 keeps a separate multiply and add (the oracle's arithmetic).
+__device__ __forceinline__ float madd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double madd(double a, double b, double c) { return a * b + c; }
+
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return (a > b) ? a : b; }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return (b < a) ? b : a; }
 __device__ __forceinline__ bool finite_(double x) { return isfinite(x); }
 __device__ __forceinline__ bool finite_(float x) { return isfinite(x); }
 __device__ __forceinline__ double nan_(double) { return __longlong_as_double(0x7ff8000000000000LL); }
 __device__ __forceinline__ float nan_(float) { return __int_as_float(0x7fc00000); }
+
+// Times are compared through order-preserving integer keys of their FP64
+// bit patterns (integer ALU instead of the narrow FP64 pipe): for finite x, y
+// key(x) < key(y) iff x < y and key(x) == key(y) iff x == y (-0 maps to +0).
+__device__ __forceinline__ long long tkey(double x) {
+  long long b = __double_as_longlong(x);
+  if (b == (long long)0x8000000000000000ULL) b = 0;
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool tfinite(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
 
 // FP64 x^y of the controller and the starting step: exp(y ln x) through one
 // fixed sequence of IEEE-754 double operations, so that the FP64 path's step
@@ -216,6 +235,9 @@ template <typename T, int R> struct Inst {
   T k1[R];       // FSAL stage
   double t, t0, t1;
   T h;           // step size proposed for the next attempt
+  T h_last;      // step size the last attempt used (clipped at t1)
+  T rem;         // FP32 state: t1 - t rounded down to float (last-step test)
+  T hmin;        // FP32 state: step-size underflow threshold 1e-14 max(|t0|,|t1|)
   T err_prev;
   T rtol, atol;
   int n_acc, n_rej, cursor, status, flags;
@@ -233,6 +255,18 @@ template <typename T> struct InstOut {
   int K;
 };
 
+// Dense-output weights b_i(theta), each by Horner's rule (w[1] = 0).
+template <typename T> __device__ __forceinline__ void dense_weights(T th, T (&w)[7]) {
+  using C = DP5;
+  w[0] = th * madd(th, madd(th, madd(th, T(C::q13), T(C::q12)), T(C::q11)), T(C::q10));
+  w[1] = T(0);
+  w[2] = th * madd(th, madd(th, madd(th, T(C::q33), T(C::q32)), T(C::q31)), T(0));
+  w[3] = th * madd(th, madd(th, madd(th, T(C::q43), T(C::q42)), T(C::q41)), T(0));
+  w[4] = th * madd(th, madd(th, madd(th, T(C::q53), T(C::q52)), T(C::q51)), T(0));
+  w[5] = th * madd(th, madd(th, madd(th, T(C::q63), T(C::q62)), T(C::q61)), T(0));
+  w[6] = th * madd(th, madd(th, madd(th, T(C::q73), T(C::q72)), T(C::q71)), T(0));
+}
+
 // Dense output of one evaluation point:  y + h * sum_i b_i(theta) k_i
 // (+ the state's compensation term in FP32).
 template <typename T, int R>
@@ -241,22 +275,18 @@ __device__ __forceinline__ void dense_point(T theta, T h, const T (&y)[R], const
                                             const T (&k5)[R], const T (&k6)[R], const T (&k7)[R],
                                             T (&out)[R]) {
   using C = DP5;
-  const T w1 = theta * (T(C::q10) + theta * (T(C::q11) + theta * (T(C::q12) + theta * T(C::q13))));
-  const T w3 = theta * (T(0) + theta * (T(C::q31) + theta * (T(C::q32) + theta * T(C::q33))));
-  const T w4 = theta * (T(0) + theta * (T(C::q41) + theta * (T(C::q42) + theta * T(C::q43))));
-  const T w5 = theta * (T(0) + theta * (T(C::q51) + theta * (T(C::q52) + theta * T(C::q53))));
-  const T w6 = theta * (T(0) + theta * (T(C::q61) + theta * (T(C::q62) + theta * T(C::q63))));
-  const T w7 = theta * (T(0) + theta * (T(C::q71) + theta * (T(C::q72) + theta * T(C::q73))));
+  T w[7];
+  dense_weights<T>(theta, w);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    T s = w1 * k1[r];
-    s = s + w3 * k3[r];
-    s = s + w4 * k4[r];
-    s = s + w5 * k5[r];
-    s = s + w6 * k6[r];
-    s = s + w7 * k7[r];
-    if constexpr (Comp<T>::on) out[r] = y[r] + (ylo[r] + h * s);
-    else out[r] = y[r] + h * s;
+    T s = w[0] * k1[r];
+    s = madd(w[2], k3[r], s);
+    s = madd(w[3], k4[r], s);
+    s = madd(w[4], k5[r], s);
+    s = madd(w[5], k6[r], s);
+    s = madd(w[6], k7[r], s);
+    if constexpr (Comp<T>::on) out[r] = y[r] + madd(h, s, ylo[r]);
+    else out[r] = madd(h, s, y[r]);
   }
 }
 
@@ -332,6 +362,9 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
   s.flags = 0;
   s.err_prev = T(1);
   s.h = T(0);
+  s.h_last = T(0);
+  s.rem = T(0);
+  s.hmin = T(0);
   s.status = ST_RUNNING;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -340,12 +373,14 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
     s.k1[r] = T(0);
   }
   // validity of the time arguments (Sec. 3: per-instance bounds and points)
-  bool ok = isfinite(s.t0) && isfinite(s.t1) && !(s.t1 < s.t0);
-  double prev = s.t0;
+  bool ok = tfinite(s.t0) && tfinite(s.t1) && !(s.t1 < s.t0);
+  const long long k0 = tkey(s.t0), k1 = tkey(s.t1);
+  long long kprev = k0;
   for (int q = 0; q < out.K && ok; ++q) {
     const double v = out.te[q];
-    ok = isfinite(v) && !(v < prev) && !(v > s.t1);
-    prev = v;
+    const long long kv = tkey(v);
+    ok = tfinite(v) && kv >= kprev && kv <= k1;
+    kprev = kv;
   }
   if (!ok) {
     s.status = ST_INVALID;
@@ -355,13 +390,17 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
     for (int q = 0; q < out.K; ++q) store_point<T, R, G>(out.ye + (size_t)q * D, nanv);
     return false;
   }
-  while (s.cursor < out.K && out.te[s.cursor] == s.t0) {
+  while (s.cursor < out.K && tkey(out.te[s.cursor]) == k0) {
     store_point<T, R, G>(out.ye + (size_t)s.cursor * D, s.y);
     s.cursor++;
   }
-  if (s.t1 == s.t0) {
+  if (k1 == k0) {
     s.status = ST_SUCCESS;
     return false;
+  }
+  if constexpr (Comp<T>::on) {
+    s.rem = __double2float_rd(s.t1 - s.t0);
+    s.hmin = T(1e-14 * tmax(fabs(s.t0), fabs(s.t1)));
   }
   F.eval(s.t, s.y, s.k1);
   if (o.h0 > 0.0) {
@@ -371,12 +410,12 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
   // starting step size, HNW Sec. II.4
   T sc[R], w[R], f1[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) sc[r] = s.atol + s.rtol * fabs(s.y[r]);
+  for (int r = 0; r < R; ++r) sc[r] = madd(s.rtol, T(fabs(s.y[r])), s.atol);
   const T d0 = rms_norm<T, R, G>(s.y, sc);
   const T d1 = rms_norm<T, R, G>(s.k1, sc);
   const T h0 = (d0 < T(1e-5) || d1 < T(1e-5)) ? T(1e-6) : T(0.01) * (d0 / d1);
 #pragma unroll
-  for (int r = 0; r < R; ++r) w[r] = s.y[r] + h0 * s.k1[r];
+  for (int r = 0; r < R; ++r) w[r] = madd(h0, s.k1[r], s.y[r]);
   F.eval(s.t + (double)h0, w, f1);
 #pragma unroll
   for (int r = 0; r < R; ++r) f1[r] = f1[r] - s.k1[r];
@@ -398,57 +437,65 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
   using C = DP5;
   T h = s.h;
   bool last = false;
-  if (s.t + (double)h >= s.t1) {
+  if constexpr (Comp<T>::on) {
+    // FP32 state: compare with t1 - t rounded down, so a step that is not
+    // flagged last never passes t1 by more than FP64 rounding
+    if (h >= s.rem) {
+      h = s.rem;
+      last = true;
+    }
+  } else if (s.t + (double)h >= s.t1) {
     h = T(s.t1 - s.t);
     last = true;
   }
+  s.h_last = h;
   const double hd = (double)h;
   T k2[R], k3[R], k4[R], k5[R], k6[R], k7[R], Y[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) Y[r] = s.y[r] + h * (T(C::a21) * s.k1[r]);
+  for (int r = 0; r < R; ++r) Y[r] = madd(h, T(C::a21) * s.k1[r], s.y[r]);
   F.eval(s.t + C::c2 * hd, Y, k2);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T a = T(C::a31) * s.k1[r];
-    a = a + T(C::a32) * k2[r];
-    Y[r] = s.y[r] + h * a;
+    a = madd(T(C::a32), k2[r], a);
+    Y[r] = madd(h, a, s.y[r]);
   }
   F.eval(s.t + C::c3 * hd, Y, k3);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T a = T(C::a41) * s.k1[r];
-    a = a + T(C::a42) * k2[r];
-    a = a + T(C::a43) * k3[r];
-    Y[r] = s.y[r] + h * a;
+    a = madd(T(C::a42), k2[r], a);
+    a = madd(T(C::a43), k3[r], a);
+    Y[r] = madd(h, a, s.y[r]);
   }
   F.eval(s.t + C::c4 * hd, Y, k4);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T a = T(C::a51) * s.k1[r];
-    a = a + T(C::a52) * k2[r];
-    a = a + T(C::a53) * k3[r];
-    a = a + T(C::a54) * k4[r];
-    Y[r] = s.y[r] + h * a;
+    a = madd(T(C::a52), k2[r], a);
+    a = madd(T(C::a53), k3[r], a);
+    a = madd(T(C::a54), k4[r], a);
+    Y[r] = madd(h, a, s.y[r]);
   }
   F.eval(s.t + C::c5 * hd, Y, k5);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T a = T(C::a61) * s.k1[r];
-    a = a + T(C::a62) * k2[r];
-    a = a + T(C::a63) * k3[r];
-    a = a + T(C::a64) * k4[r];
-    a = a + T(C::a65) * k5[r];
-    Y[r] = s.y[r] + h * a;
+    a = madd(T(C::a62), k2[r], a);
+    a = madd(T(C::a63), k3[r], a);
+    a = madd(T(C::a64), k4[r], a);
+    a = madd(T(C::a65), k5[r], a);
+    Y[r] = madd(h, a, s.y[r]);
   }
   F.eval(s.t + hd, Y, k6);
   T y1[R], inc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T a = T(C::b1) * s.k1[r];
-    a = a + T(C::b3) * k3[r];
-    a = a + T(C::b4) * k4[r];
-    a = a + T(C::b5) * k5[r];
-    a = a + T(C::b6) * k6[r];
+    a = madd(T(C::b3), k3[r], a);
+    a = madd(T(C::b4), k4[r], a);
+    a = madd(T(C::b5), k5[r], a);
+    a = madd(T(C::b6), k6[r], a);
     inc[r] = h * a;
     y1[r] = s.y[r] + inc[r];  // SSAL: the 7th stage input is the new solution
   }
@@ -459,13 +506,13 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T a = T(C::e1) * s.k1[r];
-    a = a + T(C::e3) * k3[r];
-    a = a + T(C::e4) * k4[r];
-    a = a + T(C::e5) * k5[r];
-    a = a + T(C::e6) * k6[r];
-    a = a + T(C::e7) * k7[r];
+    a = madd(T(C::e3), k3[r], a);
+    a = madd(T(C::e4), k4[r], a);
+    a = madd(T(C::e5), k5[r], a);
+    a = madd(T(C::e6), k6[r], a);
+    a = madd(T(C::e7), k7[r], a);
     ev[r] = h * a;
-    sc[r] = s.atol + s.rtol * tmax(fabs(s.y[r]), fabs(y1[r]));
+    sc[r] = madd(s.rtol, T(tmax(fabs(s.y[r]), fabs(y1[r]))), s.atol);
     fin_local = fin_local && finite_(y1[r]);
   }
   const T err = rms_norm<T, R, G>(ev, sc);
@@ -485,7 +532,14 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
 
   T h_next;
   if (accept) {
-    const double t_next = last ? s.t1 : s.t + hd;
+    double t_next = last ? s.t1 : s.t + hd;
+    if constexpr (Comp<T>::on) {
+      if (!last && tkey(t_next) >= tkey(s.t1)) {  // landed on t1 by rounding
+        last = true;
+        t_next = s.t1;
+      }
+    }
+    const long long kn = tkey(t_next);
     // new state (FP32: compensated sum y + (inc + ylo))
     T yn[R], ylon[R];
 #pragma unroll
@@ -501,13 +555,18 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     }
     while (s.cursor < out.K) {
       const double tq = out.te[s.cursor];
-      if (!(tq <= t_next)) break;
+      const long long kq = tkey(tq);
+      if (kq > kn) break;
       T* dst = out.ye + (size_t)s.cursor * D;
-      if (tq == t_next) {
+      if (kq == kn) {
         store_point<T, R, G>(dst, yn);
       } else {
+        // abscissa: the difference tq - t in FP64, the ratio in the state type
+        T theta;
+        if constexpr (Comp<T>::on) theta = T(tq - s.t) / h;
+        else theta = T((tq - s.t) / hd);
         T v[R];
-        dense_point<T, R>(T((tq - s.t) / hd), h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
+        dense_point<T, R>(theta, h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
         store_point<T, R, G>(dst, v);
       }
       s.cursor++;
@@ -526,6 +585,9 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     s.flags &= ~FL_PREV_REJ;
     s.n_acc++;
     s.t = t_next;
+    if constexpr (Comp<T>::on) {
+      if (!last) s.rem = __double2float_rd(s.t1 - s.t);
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       s.y[r] = yn[r];
@@ -542,9 +604,17 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
   }
   s.h = h_next;
   if (s.status == ST_RUNNING) {
-    const double scale = tmax(fabs(s.t), fabs(s.t1));
-    const double hn = (double)h_next;
-    if (s.t + hn == s.t || hn < 1e-14 * scale || !(h_next > T(0)))
+    bool under;
+    if constexpr (Comp<T>::on) {
+      // FP32 state: 1e-14 max(|t0|,|t1|) bounds 1e-14 max(|t|,|t1|) and lies
+      // above the FP64 spacing of t, so "t + h == t" cannot occur first
+      under = !(h_next >= s.hmin) || !(h_next > T(0));
+    } else {
+      const double scale = tmax(fabs(s.t), fabs(s.t1));
+      const double hn = (double)h_next;
+      under = s.t + hn == s.t || hn < 1e-14 * scale || !(h_next > T(0));
+    }
+    if (under)
       s.status = finite ? ST_DT_UNDERFLOW : ST_NONFINITE;
     else if (s.n_acc + s.n_rej >= o.max_steps)
       s.status = ST_MAX_STEPS;
@@ -565,7 +635,7 @@ __device__ void inst_finalize(const Inst<T, R>& s, const SolveOpts& o, int i, in
     const int att = s.n_acc + s.n_rej;
     n_acc[i] = s.n_acc;
     n_rej[i] = s.n_rej;
-    const bool stepped = !invalid && s.t1 != s.t0;
+    const bool stepped = !invalid && tkey(s.t1) != tkey(s.t0);
     n_fe[i] = stepped ? ((o.h0 > 0.0 ? 1 : 2) + 6 * att) : 0;
     status[i] = s.status;
     if (tr.cap > 0) tr.len[i] = att < tr.cap ? att : tr.cap;

@@ -14,7 +14,8 @@ template <typename T> struct VdpField {
   __device__ __forceinline__ void load(const T* mu_all, int i) { mu = mu_all[i]; }
   __device__ __forceinline__ void eval(double, const T (&y)[2], T (&f)[2]) const {
     f[0] = y[1];
-    f[1] = mu * (T(1) - y[0] * y[0]) * y[1] - y[0];
+    // mu (1 - y1^2) y2 - y1 (FP64: the same operations as written out)
+    f[1] = madd(mu * madd(-y[0], y[0], T(1)), y[1], -y[0]);
   }
 };
 
@@ -54,19 +55,19 @@ template <typename T, int R, int G> struct LinearField {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if constexpr (sizeof(T) == 8 || D < 8) {
-        // FP64: left-to-right sum (reproducible); small D: nothing to split
+        // FP64: left-to-right sum (the oracle's order); small D: one chain
         T s = T(0);
 #pragma unroll
-        for (int c = 0; c < D; ++c) s = s + a[r][c] * yall[c];
+        for (int c = 0; c < D; ++c) s = madd(a[r][c], yall[c], s);
         f[r] = s;
       } else {
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
         for (int c = 0; c < D; c += 4) {
-          s0 = fmaf(a[r][c], yall[c], s0);
-          s1 = fmaf(a[r][c + 1], yall[c + 1], s1);
-          s2 = fmaf(a[r][c + 2], yall[c + 2], s2);
-          s3 = fmaf(a[r][c + 3], yall[c + 3], s3);
+          s0 = madd(a[r][c], yall[c], s0);
+          s1 = madd(a[r][c + 1], yall[c + 1], s1);
+          s2 = madd(a[r][c + 2], yall[c + 2], s2);
+          s3 = madd(a[r][c + 3], yall[c + 3], s3);
         }
         f[r] = (s0 + s1) + (s2 + s3);
       }

@@ -98,6 +98,10 @@ __device__ __forceinline__ void plain_load(const SolveArgs<T>& a, int i, Inst<T,
   s.status = a.status[i];
   s.rtol = T(rtol_of(a, i));
   s.atol = T(atol_of(a, i));
+  if constexpr (Comp<T>::on) {  // functions of (t, t0, t1), as in the fused form
+    s.rem = __double2float_rd(s.t1 - s.t);
+    s.hmin = T(1e-14 * tmax(fabs(s.t0), fabs(s.t1)));
+  }
 }
 
 // ---------------------------------------------------------------- plain form

@@ -32,9 +32,10 @@ template <typename T> struct VdpAdj {
   // gy = J^T v with J = [[0, 1], [-2 mu y1 y2 - 1, mu (1 - y1^2)]]
   __device__ __forceinline__ void vjp(const T (&y)[2], const T (&v)[2], T (&gy)[2]) {
     const T mu = f.mu;
-    gy[0] = v[1] * (T(-2) * mu * y[0] * y[1] - T(1));
-    gy[1] = v[0] + v[1] * (mu * (T(1) - y[0] * y[0]));
-    gmu = gmu + v[1] * ((T(1) - y[0] * y[0]) * y[1]);
+    const T one_m = madd(-y[0], y[0], T(1));  // 1 - y1^2
+    gy[0] = v[1] * madd(T(-2) * mu * y[0], y[1], T(-1));
+    gy[1] = madd(v[1], mu * one_m, v[0]);
+    gmu = madd(v[1], one_m * y[1], gmu);
   }
   __device__ __forceinline__ void store_param(T* gp, int i, bool bad) const {
     gp[i] = bad ? nan_(T(0)) : gmu;
@@ -70,10 +71,10 @@ template <typename T, int R_, int G_> struct LinearAdj {
     for (int r = 0; r < R; ++r) {
       T s = T(0);
 #pragma unroll
-      for (int j = 0; j < D; ++j) s = s + acol[r][j] * vall[j];
+      for (int j = 0; j < D; ++j) s = madd(acol[r][j], vall[j], s);
       gy[r] = s;
 #pragma unroll
-      for (int c = 0; c < D; ++c) gA[r][c] = gA[r][c] + v[r] * yall[c];
+      for (int c = 0; c < D; ++c) gA[r][c] = madd(v[r], yall[c], gA[r][c]);
     }
   }
   __device__ __forceinline__ void store_param(T* gp, int i, bool bad) const {
@@ -123,50 +124,50 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
   for (int r = 0; r < R; ++r) Y[0][r] = y[r];
   F.eval(t, Y[0], k[0]);
 #pragma unroll
-  for (int r = 0; r < R; ++r) Y[1][r] = y[r] + h * (T(C::a21) * k[0][r]);
+  for (int r = 0; r < R; ++r) Y[1][r] = madd(h, T(C::a21) * k[0][r], y[r]);
   F.eval(t + C::c2 * hd, Y[1], k[1]);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T s = T(C::a31) * k[0][r];
-    s = s + T(C::a32) * k[1][r];
-    Y[2][r] = y[r] + h * s;
+    s = madd(T(C::a32), k[1][r], s);
+    Y[2][r] = madd(h, s, y[r]);
   }
   F.eval(t + C::c3 * hd, Y[2], k[2]);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T s = T(C::a41) * k[0][r];
-    s = s + T(C::a42) * k[1][r];
-    s = s + T(C::a43) * k[2][r];
-    Y[3][r] = y[r] + h * s;
+    s = madd(T(C::a42), k[1][r], s);
+    s = madd(T(C::a43), k[2][r], s);
+    Y[3][r] = madd(h, s, y[r]);
   }
   F.eval(t + C::c4 * hd, Y[3], k[3]);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T s = T(C::a51) * k[0][r];
-    s = s + T(C::a52) * k[1][r];
-    s = s + T(C::a53) * k[2][r];
-    s = s + T(C::a54) * k[3][r];
-    Y[4][r] = y[r] + h * s;
+    s = madd(T(C::a52), k[1][r], s);
+    s = madd(T(C::a53), k[2][r], s);
+    s = madd(T(C::a54), k[3][r], s);
+    Y[4][r] = madd(h, s, y[r]);
   }
   F.eval(t + C::c5 * hd, Y[4], k[4]);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T s = T(C::a61) * k[0][r];
-    s = s + T(C::a62) * k[1][r];
-    s = s + T(C::a63) * k[2][r];
-    s = s + T(C::a64) * k[3][r];
-    s = s + T(C::a65) * k[4][r];
-    Y[5][r] = y[r] + h * s;
+    s = madd(T(C::a62), k[1][r], s);
+    s = madd(T(C::a63), k[2][r], s);
+    s = madd(T(C::a64), k[3][r], s);
+    s = madd(T(C::a65), k[4][r], s);
+    Y[5][r] = madd(h, s, y[r]);
   }
   F.eval(t + hd, Y[5], k[5]);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T s = T(C::b1) * k[0][r];
-    s = s + T(C::b3) * k[2][r];
-    s = s + T(C::b4) * k[3][r];
-    s = s + T(C::b5) * k[4][r];
-    s = s + T(C::b6) * k[5][r];
-    Y[6][r] = y[r] + h * s;
+    s = madd(T(C::b3), k[2][r], s);
+    s = madd(T(C::b4), k[3][r], s);
+    s = madd(T(C::b5), k[4][r], s);
+    s = madd(T(C::b6), k[5][r], s);
+    Y[6][r] = madd(h, s, y[r]);
   }
   F.eval(t + hd, Y[6], k[6]);
 
@@ -179,32 +180,30 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
     for (int r = 0; r < R; ++r) kb[s][r] = h * bw[s] * yb[r];
   bool dense7 = false;
   const int g = Grp<G>::rank();
+  const long long kt = tkey(t), kn = tkey(t_next);
   while (q >= 0) {
     const double tq = a.te[(size_t)i * a.K + q];
-    if (!(tq > t)) break;
+    const long long kq = tkey(tq);
+    if (!(kq > kt)) break;
     if (a.gye) {
       T gq[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + g * R + r];
       T w[7];
-      if (tq == t_next) {
+      if (kq == kn) {
 #pragma unroll
         for (int s = 0; s < 7; ++s) w[s] = bw[s];
       } else {
-        const T th = T((tq - t) / hd);
-        w[0] = th * (T(C::q10) + th * (T(C::q11) + th * (T(C::q12) + th * T(C::q13))));
-        w[1] = T(0);
-        w[2] = th * (T(0) + th * (T(C::q31) + th * (T(C::q32) + th * T(C::q33))));
-        w[3] = th * (T(0) + th * (T(C::q41) + th * (T(C::q42) + th * T(C::q43))));
-        w[4] = th * (T(0) + th * (T(C::q51) + th * (T(C::q52) + th * T(C::q53))));
-        w[5] = th * (T(0) + th * (T(C::q61) + th * (T(C::q62) + th * T(C::q63))));
-        w[6] = th * (T(0) + th * (T(C::q71) + th * (T(C::q72) + th * T(C::q73))));
+        T th;
+        if constexpr (Comp<T>::on) th = T(tq - t) / h;
+        else th = T((tq - t) / hd);
+        dense_weights<T>(th, w);
         dense7 = true;
       }
 #pragma unroll
       for (int s = 0; s < 7; ++s)
 #pragma unroll
-        for (int r = 0; r < R; ++r) kb[s][r] = kb[s][r] + h * w[s] * gq[r];
+        for (int r = 0; r < R; ++r) kb[s][r] = madd(h * w[s], gq[r], kb[s][r]);
 #pragma unroll
       for (int r = 0; r < R; ++r) yb[r] = yb[r] + gq[r];
     }
@@ -226,7 +225,7 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
 #pragma unroll
     for (int l = 0; l < s; ++l)
 #pragma unroll
-      for (int r = 0; r < R; ++r) kb[l][r] = kb[l][r] + h * A[s][l] * gs[r];
+      for (int r = 0; r < R; ++r) kb[l][r] = madd(h * A[s][l], gs[r], kb[l][r]);
 #pragma unroll
     for (int r = 0; r < R; ++r) yb[r] = yb[r] + gs[r];
   }
@@ -285,15 +284,18 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs<T> a) {
       s.n_rej = 0;
       s.cursor = 0;
       s.status = ST_RUNNING;
+      if constexpr (Comp<T>::on) {  // functions of (t, t0, t1), as in the forward
+        s.rem = __double2float_rd(s.t1 - s.t);
+        s.hmin = T(1e-14 * tmax(fabs(s.t0), fabs(s.t1)));
+      }
       while (s.n_acc < n1 && s.status == ST_RUNNING) {
         const int before = s.n_acc;
         const double tb = s.t;
-        T hb = s.h;
-        if (tb + (double)hb >= t1) hb = T(t1 - tb);
         T ys[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) ys[r] = s.y[r];
         inst_attempt<AF, T, R, G>(F, s, ro, i, D, no_out, no_trace);
+        const T hb = s.h_last;
         if (s.n_acc != before) {
           const size_t p = (size_t)(before - n0) * a.B + i;
 #pragma unroll
@@ -323,9 +325,9 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs<T> a) {
     }
     // evaluation points at t0 are y0 itself
     if (!bad && a.gye) {
-      const double t0 = a.t0[i];
+      const long long k0 = tkey(a.t0[i]);
       for (; q >= 0; --q) {
-        if (a.te[(size_t)i * a.K + q] == t0) {
+        if (tkey(a.te[(size_t)i * a.K + q]) == k0) {
 #pragma unroll
           for (int r = 0; r < R; ++r)
             yb[r] = yb[r] + a.gye[((size_t)i * a.K + q) * D + g * R + r];

@@ -1,4 +1,6 @@
-// FP32-state instantiation of the SIMT solver (time stays FP64).
+// FP32-state instantiation of the SIMT solver (time stays FP64).  Built with
+// -fmad=false: every multiply-add it performs is an explicit fused operation
+// (madd), so the plain and fused kernels round identically.
 #include "tode_simt_adjoint.cuh"
 
 namespace tode {
