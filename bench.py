@@ -320,7 +320,7 @@ def run_tode(args):
     achieved = flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
-                "kernel": "k_fused<LinearField<float,1,16>> (fused forward)",
+                "kernel": "k_fused<LinearField<float,2,8>> (fused forward)",
                 "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {clk_mhz:.0f} MHz",
                 "kernel_ms": k_fwd_ms}
     breakdown = {

@@ -386,15 +386,20 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   return TODE_OK;
 }
 
+// The adjoint re-runs the forward's attempts, so it must use the forward's
+// lane grouping (linear_group): the FP32 error norm's butterfly order, and
+// with it the recomputed mesh, depends on the group size.
 template <typename T> tode_err simt_adjoint(const AdjReq& r) {
   if (r.f->kind == TODE_VDP) return launch_adjoint<VdpAdj<T>, T>(r);
-  switch (r.D) {
+  switch (linear_group(r.D, r.o->group)) {
     case 1: return launch_adjoint<LinearAdj<T, 1, 1>, T>(r);
     case 2: return launch_adjoint<LinearAdj<T, 1, 2>, T>(r);
-    case 4: return launch_adjoint<LinearAdj<T, 1, 4>, T>(r);
-    case 8: return launch_adjoint<LinearAdj<T, 1, 8>, T>(r);
-    case 16: return launch_adjoint<LinearAdj<T, 1, 16>, T>(r);
-    case 32: return launch_adjoint<LinearAdj<T, 2, 16>, T>(r);
+    case 4: return r.D == 4 ? launch_adjoint<LinearAdj<T, 1, 4>, T>(r)
+                            : launch_adjoint<LinearAdj<T, 4, 4>, T>(r);
+    case 8: return r.D == 8 ? launch_adjoint<LinearAdj<T, 1, 8>, T>(r)
+                            : launch_adjoint<LinearAdj<T, 2, 8>, T>(r);
+    case 16: return r.D == 16 ? launch_adjoint<LinearAdj<T, 1, 16>, T>(r)
+                              : launch_adjoint<LinearAdj<T, 2, 16>, T>(r);
     default: return TODE_EUNSUPPORTED;
   }
 }
