@@ -27,6 +27,7 @@ UNITS = {
     "tode_simt_f64.cu": ["-fmad=false"],
     "tode_simt_f32.cu": ["-fmad=false"],
     "tode_static.cu": [],
+    "tode_tc_gemm.cu": [],
 }
 
 

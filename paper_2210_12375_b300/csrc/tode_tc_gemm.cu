@@ -1,0 +1,89 @@
+// tode_tc_gemm.cu -- tode_tc_gemm: the MLP field's tensor-core building block
+// on its own (C = A * B^T, BF16 inputs, FP32 accumulation in tensor memory),
+// so that the operand layout, descriptors and tensor-memory conventions can be
+// checked against a plain matrix product.
+#include "tode_internal.h"
+#include "tode_tc.cuh"
+
+namespace tode {
+
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, float* C, int N,
+              int K, int32_t* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  unsigned char* sA = smem;                       // 128 x K
+  unsigned char* sB = smem + (size_t)128 * K * 2;  // N x K
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // operands into the core-matrix layout
+  for (int e = tid; e < 128 * K; e += 128) {
+    const int row = e / K, k = e % K;
+    *reinterpret_cast<uint16_t*>(sA + tc::cm_offset(row, k, K)) = A[e];
+  }
+  for (int e = tid; e < N * K; e += 128) {
+    const int row = e / K, k = e % K;
+    *reinterpret_cast<uint16_t*>(sB + tc::cm_offset(row, k, K)) = B[e];
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const uint32_t ncols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, ncols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tmem_base;
+
+  if (tid == 0) {
+    const uint32_t idesc = tc::idesc_bf16_f32(128, N);
+    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+    for (int kk = 0; kk < K / 16; ++kk) {
+      const uint64_t da = tc::smem_desc(a0 + kk * 256, 128, K * 16);
+      const uint64_t db = tc::smem_desc(b0 + kk * 256, 128, K * 16);
+      tc::mma_bf16(tbase, da, db, idesc, kk > 0);
+    }
+    tc::mma_commit(&mbar);
+  }
+  const bool ok = tc::mbar_wait(&mbar, 0);
+  if (!ok && lane == 0) atomicExch(err, 1);
+  tc::fence_after_sync();
+  if (ok) {
+    const int row = warp * 32 + lane;
+    for (int c = 0; c < N; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) C[(size_t)row * N + c + j] = v[j];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, ncols);
+}
+
+}  // namespace tode
+
+extern "C" tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, int N, int K,
+                                 int32_t* err, void* stream) {
+  if (!A || !B || !C || !err) return TODE_EINVAL;
+  if (M != 128 || N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16) return TODE_EINVAL;
+  const size_t smem = (size_t)(128 + N) * K * 2;
+  cudaError_t e = cudaFuncSetAttribute(tode::k_tc_gemm,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TODE_ECUDA;
+  }
+  tode::k_tc_gemm<<<1, 128, smem, (cudaStream_t)stream>>>((const uint16_t*)A, (const uint16_t*)B,
+                                                          C, N, K, err);
+  if (cudaGetLastError() != cudaSuccess) return TODE_ECUDA;
+  return TODE_OK;
+}

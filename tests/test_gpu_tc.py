@@ -1,0 +1,37 @@
+"""The MLP field's tensor-core building block (tcgen05.mma, BF16 x BF16 ->
+FP32 in tensor memory, core-matrix operand layout) against a plain FP32
+product of the same BF16 values."""
+import ctypes as C
+
+import pytest
+import torch
+
+from paper_2210_12375_b300 import _abi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("N,K", [(16, 16), (32, 48), (128, 48), (128, 128), (32, 128),
+                                 (256, 64), (64, 256)])
+def test_tc_gemm_matches_fp32_product(N, K):
+    lib = _abi.load()
+    g = torch.Generator(device="cpu").manual_seed(N * 1000 + K)
+    A = torch.randn(128, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    Cm = torch.full((128, N), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.tode_tc_gemm(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
+                          C.c_void_p(Cm.data_ptr()), 128, N, K, C.c_void_p(err.data_ptr()),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == 0 and int(err.item()) == 0
+    ref = A.double() @ B.double().T
+    assert torch.isfinite(Cm).all()
+    assert (Cm.double() - ref).abs().max().item() <= 1e-5 * max(1.0, ref.abs().max().item())
+
+
+def test_tc_gemm_rejects_bad_shapes():
+    lib = _abi.load()
+    p = C.c_void_p(0x1000)
+    for (M, N, K) in [(64, 16, 16), (128, 8, 16), (128, 16, 8), (128, 272, 16)]:
+        assert lib.tode_tc_gemm(p, p, p, M, N, K, p, None) == _abi.TODE_EINVAL
