@@ -52,8 +52,12 @@ typedef enum { TODE_VDP = 1, TODE_LINEAR = 2, TODE_MLP = 3 } tode_field_kind;
 
 /* TODE_F64: FP64 state and arithmetic.  TODE_F32: FP32 state (compensated
  * summation of the state updates), FP64 time.  TODE_BF16W (MLP only): BF16
- * weights on tensor cores, FP32 accumulation, FP32 state, FP64 time. */
-typedef enum { TODE_F64 = 0, TODE_F32 = 1, TODE_BF16W = 2 } tode_prec;
+ * weights on tensor cores, FP32 accumulation, FP32 state, FP64 time; the
+ * field's input [y; t] enters as two BF16 terms (hi + lo), hidden
+ * activations are rounded to BF16.  TODE_BF16W_SPLIT: as TODE_BF16W but the
+ * hidden activations are also carried as two BF16 terms (twice the tensor
+ * work, ~16 significant bits instead of 8). */
+typedef enum { TODE_F64 = 0, TODE_F32 = 1, TODE_BF16W = 2, TODE_BF16W_SPLIT = 3 } tode_prec;
 
 /* TODE_PLAIN: one kernel launch per step over the whole masked batch.
  * TODE_FUSED: one persistent launch; every worker integrates its instance to
@@ -78,7 +82,8 @@ enum {
  *               widths[0] = D + 1 and widths[n_layers] = D; W (host array of
  *               device pointers) W[l] is [widths[l+1]][widths[l]] BF16
  *               (uint16 bit patterns); b (host array of device pointers)
- *               b[l] is [widths[l+1]] float. */
+ *               b[l] is [widths[l+1]] float (NULL = zero).  Built shape:
+ *               widths {33, 128, 128, 32}; fused form only; no tape yet. */
 typedef struct {
   tode_field_kind kind;
   int B;

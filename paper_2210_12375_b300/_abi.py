@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libtode.so")
 # enums
 TODE_OK, TODE_EINVAL, TODE_EWORKSPACE, TODE_ECUDA, TODE_EUNSUPPORTED, TODE_ETIMEOUT = range(6)
 TODE_VDP, TODE_LINEAR, TODE_MLP = 1, 2, 3
-TODE_F64, TODE_F32, TODE_BF16W = 0, 1, 2
+TODE_F64, TODE_F32, TODE_BF16W, TODE_BF16W_SPLIT = 0, 1, 2, 3
 TODE_PLAIN, TODE_FUSED = 0, 1
 STATUS = {"SUCCESS": 0, "MAX_STEPS": 1, "DT_UNDERFLOW": 2, "NONFINITE": 3, "INVALID_INPUT": 4}
 

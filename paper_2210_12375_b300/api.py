@@ -56,9 +56,10 @@ class MLP:
     weights W_l [out, in] and float biases b_l [out]."""
     kind = _abi.TODE_MLP
 
-    def __init__(self, weights, biases):
+    def __init__(self, weights, biases, split: bool = False):
         self.W = list(weights)
         self.b = list(biases)
+        self.split = split
 
     @property
     def widths(self):
@@ -85,7 +86,7 @@ class MLP:
 # ------------------------------------------------------------------ options
 def _prec_of(field, y0: torch.Tensor) -> int:
     if isinstance(field, MLP):
-        return _abi.TODE_BF16W
+        return _abi.TODE_BF16W_SPLIT if field.split else _abi.TODE_BF16W
     if y0.dtype == torch.float64:
         return _abi.TODE_F64
     if y0.dtype == torch.float32:

@@ -28,6 +28,7 @@ UNITS = {
     "tode_simt_f32.cu": ["-fmad=false"],
     "tode_static.cu": [],
     "tode_tc_gemm.cu": [],
+    "tode_mlp.cu": ["-fmad=false"],
 }
 
 

@@ -42,7 +42,15 @@ static tode_err field_ok(const tode_field_desc* f, const tode_options* o) {
     if (f->B > 0 && f->kind == TODE_LINEAR && !f->A) return TODE_EINVAL;
     return TODE_OK;
   }
-  if (f->kind == TODE_MLP) return TODE_EUNSUPPORTED;
+  if (f->kind == TODE_MLP) {
+    if (o->prec != TODE_BF16W && o->prec != TODE_BF16W_SPLIT) return TODE_EUNSUPPORTED;
+    if (!f->widths || !f->W || !f->b) return TODE_EINVAL;
+    if (!mlp_supported(f)) return TODE_EUNSUPPORTED;
+    if (f->B > 0)
+      for (int l = 0; l < f->n_layers; ++l)
+        if (!f->W[l]) return TODE_EINVAL;
+    return TODE_OK;
+  }
   return TODE_EINVAL;
 }
 
@@ -104,6 +112,7 @@ void tode_default_options(tode_options* o) {
 
 size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int K) {
   if (K < 0 || !opts_ok(o) || field_ok(f, o) != TODE_OK) return 0;
+  if (f->kind == TODE_MLP) return mlp_workspace_bytes(f);
   return simt_workspace_bytes(f->B, f->D, state_size(o), o->form);
 }
 
@@ -151,12 +160,14 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
   r.stream = (cudaStream_t)stream;
   e = device_sms(&r.num_sms);
   if (e != TODE_OK) return e;
+  if (f->kind == TODE_MLP) return mlp_solve(r, o->prec == TODE_BF16W_SPLIT);
   return o->prec == TODE_F64 ? simt_solve_f64(r) : simt_solve_f32(r);
 }
 
 size_t tode_adjoint_scratch_size(const tode_field_desc* f, const tode_options* o,
                                  const tode_tape* tape) {
   if (!opts_ok(o) || field_ok(f, o) != TODE_OK || !tape || tape->stride < 1) return 0;
+  if (f->kind == TODE_MLP) return 0;  // not built yet
   return simt_adjoint_scratch_bytes(f->B, f->D, state_size(o), tape->stride);
 }
 
@@ -169,6 +180,7 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
   if (!opts_ok(o) || K < 0) return TODE_EINVAL;
   tode_err e = field_ok(f, o);
   if (e != TODE_OK) return e;
+  if (f->kind == TODE_MLP) return TODE_EUNSUPPORTED;  // not built yet
   if (f->B == 0) return TODE_OK;
   if (!t0 || !t1 || !n_acc || !status || !tape || !gy0 || !overflow) return TODE_EINVAL;
   if (K > 0 && !t_eval) return TODE_EINVAL;

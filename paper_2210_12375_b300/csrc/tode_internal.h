@@ -89,4 +89,8 @@ tode_err simt_adjoint_f32(const AdjReq& r);
 
 bool simt_supported(int kind, int D);
 
+bool mlp_supported(const tode_field_desc* f);
+size_t mlp_workspace_bytes(const tode_field_desc* f);
+tode_err mlp_solve(const SolveReq& r, bool split);
+
 }  // namespace tode

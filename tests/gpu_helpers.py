@@ -17,6 +17,11 @@ def device_field(w, dtype, dev="cuda"):
         return tode.VdP(torch.tensor(f["mu"], dtype=dtype, device=dev))
     if f["kind"] == "linear":
         return tode.Linear(torch.tensor(f["A"], dtype=dtype, device=dev).contiguous())
+    if f["kind"] == "mlp":  # BF16 weights (exactly the oracle's values), float biases
+        W = [torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(dev).contiguous()
+             for x in f["W"]]
+        b = [torch.tensor(x, dtype=torch.float32, device=dev) for x in f["b"]]
+        return tode.MLP(W, b, split=w.get("split", True))
     raise ValueError(f["kind"])
 
 

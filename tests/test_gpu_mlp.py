@@ -1,0 +1,82 @@
+"""The MLP field on the tensor cores (tcgen05, BF16 weights, FP32
+accumulation; input [y; t] as two BF16 terms) against the FP64 oracle run
+with the same BF16 weights.  Tolerance: 10 (atol + rtol |y|) of a
+1e-12-tolerance oracle solution."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import gpu_solve, make, oracle_solve, subset
+
+pytestmark = pytest.mark.gpu
+
+
+def _band_ratio(g, ref, w):
+    band = 10 * (w["atol"] + w["rtol"] * np.abs(ref["y_eval"]))
+    return np.abs(g["y_eval"] - ref["y_eval"]) / band
+
+
+def test_mlp_split_matches_oracle_full_size_sampled():
+    w = dict(make(4), split=True)
+    g = gpu_solve(w, torch.float32, "fused")
+    assert (g["status"] == 0).all()
+    assert (g["n_feval"] == 2 + 6 * (g["n_acc"] + g["n_rej"])).all()
+    idx = np.arange(0, w["B"], 61)
+    ws = subset(w, idx)
+    ref = oracle_solve(ws, rtol=1e-12, atol=1e-12)
+    r = _band_ratio({"y_eval": g["y_eval"][idx]}, ref, w)
+    assert np.isfinite(r).all() and r.max() <= 1.0, r.max()
+    # matched steps: the same accepted-step counts as the FP64 oracle at the
+    # workload tolerance on nearly every instance
+    cfg = oracle_solve(ws)
+    assert (g["n_acc"][idx] == cfg["n_acc"]).mean() > 0.95
+
+
+def test_mlp_bf16_activations_error_is_reported():
+    """Hidden activations rounded to BF16: f carries ~1e-3 relative noise;
+    the solution stays within a few bands (reported, not the default)."""
+    w = dict(make(4, B=2048), split=False)
+    g = gpu_solve(w, torch.float32, "fused")
+    assert (g["status"] == 0).all()
+    ref = oracle_solve(subset(w, np.arange(256)), rtol=1e-12, atol=1e-12)
+    r = _band_ratio({"y_eval": g["y_eval"][:256]}, ref, w)
+    assert r.max() <= 3.0 and (r <= 1.0).mean() > 0.99
+
+
+def test_mlp_batch_invariance_bitwise():
+    w = dict(make(4, B=700), split=True)
+    full = gpu_solve(w, torch.float32, "fused")
+    perm = np.random.default_rng(9).permutation(w["B"])
+    sh = gpu_solve(subset(w, perm), torch.float32, "fused")
+    for k in ("y_eval", "y_final", "n_acc", "n_rej", "status"):
+        assert np.array_equal(full[k][perm], sh[k]), k
+    one = gpu_solve(subset(w, [123]), torch.float32, "fused")
+    assert np.array_equal(one["y_eval"][0], full["y_eval"][123])
+
+
+def test_mlp_edge_cases():
+    w = dict(make(4, B=200), split=True)
+    y0, t0, t1, te = w["y0"].copy(), w["t0"].copy(), w["t1"].copy(), w["t_eval"].copy()
+    te[1, 3], te[1, 4] = te[1, 4], te[1, 3]
+    t1[2] = -1.0
+    t1[3] = t0[3]
+    te[3] = t0[3]
+    y0[4, 7] = np.nan
+    w2 = dict(w, y0=y0, t1=t1, t_eval=te)
+    g = gpu_solve(w2, torch.float32, "fused")
+    o = oracle_solve(w2)
+    assert list(g["status"][[1, 2]]) == [4, 4]
+    assert g["status"][3] == 0 and g["n_acc"][3] == 0
+    assert np.array_equal(g["y_eval"][3], np.repeat(y0[3:4].astype(np.float32), 8, 0))
+    assert g["status"][4] == 3 and o["status"][4] == 3
+    assert (g["status"][5:] == 0).all()
+    # the healthy rows of the same tiles are unaffected
+    ref = gpu_solve(subset(w, np.arange(5, 200)), torch.float32, "fused")
+    assert np.array_equal(ref["y_eval"], g["y_eval"][5:])
+
+
+def test_mlp_unsupported_requests_fail_loudly():
+    import paper_2210_12375_b300 as tode
+    w = dict(make(4, B=64), split=True)
+    with pytest.raises(tode._abi.TodeError):
+        gpu_solve(w, torch.float32, "plain")
