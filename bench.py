@@ -161,8 +161,14 @@ def run_tode(args):
     dtype = torch.float64 if w["prec"] == "f64" else torch.float32
     B, D = w["y0"].shape
     K = w["t_eval"].shape[1]
+    mlp = kind == "mlp"
     if kind == "linear":
         field = tode.Linear(torch.tensor(w["field"]["A"], dtype=dtype, device=dev).contiguous())
+    elif mlp:
+        field = tode.MLP([torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(dev)
+                          .contiguous() for x in w["field"]["W"]],
+                         [torch.tensor(x, dtype=torch.float32, device=dev)
+                          for x in w["field"]["b"]], split=True)
     else:
         field = tode.VdP(torch.tensor(w["field"]["mu"], dtype=dtype, device=dev))
     y0 = torch.tensor(w["y0"], dtype=dtype, device=dev)
@@ -182,7 +188,10 @@ def run_tode(args):
     n_att = int((probe.n_acc.long() + probe.n_rej.long()).sum().item())
     n_acc_total = int(probe.n_acc.long().sum().item())
     n_acc_max = int(probe.n_acc.max().item())
-    tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev)
+    # the MLP field has no adjoint and no plain form yet: forward, fused
+    with_adjoint = not mlp
+    tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev) \
+        if with_adjoint else None
 
     def fwd(form, sol=None, ws=None):
         return tode.solve(field, y0, t0, t1, te, form=form, tape=tape, out=sol, workspace=ws,
@@ -194,9 +203,9 @@ def run_tode(args):
 
     # matched error: both forms against the exact solution of the same batch
     sol_f = fwd("fused")
-    sol_p = fwd("plain")
+    sol_p = fwd("plain") if not mlp else None
     torch.cuda.synchronize()
-    same = bool(torch.equal(sol_f.y_eval, sol_p.y_eval))
+    same = bool(torch.equal(sol_f.y_eval, sol_p.y_eval)) if sol_p is not None else None
     err = None
     if kind == "linear":
         Q, lam = w["field"]["Q"], w["field"]["lam"]
@@ -256,13 +265,14 @@ def run_tode(args):
 
     nk = max(20, args.steps // 4)
     with ClockSampler(local) as clk:
-        ms_fused, wall_fused = timed("fused", args.steps, True)
+        ms_fused, wall_fused = timed("fused", args.steps, with_adjoint)
         k_fwd_ms = kernel_ms(nk, False)
-        k_adj_ms = kernel_ms(nk, True)
+        k_adj_ms = kernel_ms(nk, True) if with_adjoint else None
     clocks = clk.summary()
     ms_fused_fwd, _ = timed("fused", nk, False)
-    ms_plain, _ = timed("plain", args.plain_steps, True)
-    ms_plain_fwd, _ = timed("plain", args.plain_steps, False)
+    if not mlp:
+        ms_plain, _ = timed("plain", args.plain_steps, True)
+        ms_plain_fwd, _ = timed("plain", args.plain_steps, False)
 
     per_step = ms_fused / args.steps
     value = world * n_att / (per_step * 1e-3)
@@ -270,10 +280,20 @@ def run_tode(args):
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        host = {k: v.cpu().pin_memory() for k, v in dict(
-            y0=y0, t0=t0, t1=t1, te=te, gye=gye, gyf=gyf, P=field.params()).items()}
+        src = dict(y0=y0, t0=t0, t1=t1, te=te)
+        if with_adjoint:
+            src.update(gye=gye, gyf=gyf, P=field.params())
+        else:
+            src.update({f"W{l}": x for l, x in enumerate(field.W)})
+        host = {k: v.cpu().pin_memory() for k, v in src.items()}
         dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-        field_e2e = tode.Linear(dev_in["P"]) if kind == "linear" else tode.VdP(dev_in["P"])
+        if kind == "linear":
+            field_e2e = tode.Linear(dev_in["P"])
+        elif mlp:
+            field_e2e = tode.MLP([dev_in[f"W{l}"] for l in range(len(field.W))], field.b,
+                                 split=True)
+        else:
+            field_e2e = tode.VdP(dev_in["P"])
         sol = fwd("fused")
         out_h = {}
         h2d = sum(v.numel() * v.element_size() for v in host.values())
@@ -284,10 +304,12 @@ def run_tode(args):
             s = tode.solve(field_e2e, dev_in["y0"], dev_in["t0"], dev_in["t1"], dev_in["te"],
                            form="fused", tape=tape, out=sol, workspace=sol.extra["workspace"],
                            **opt)
-            g0, gp, _ = tode.adjoint(field_e2e, dev_in["t0"], dev_in["t1"], dev_in["te"], s,
-                                     tape, dev_in["gye"], dev_in["gyf"], **opt)
             res = dict(y_eval=s.y_eval, y_final=s.y_final, n_acc=s.n_acc, n_rej=s.n_rej,
-                       n_feval=s.n_feval, status=s.status, gy0=g0, gp=gp)
+                       n_feval=s.n_feval, status=s.status)
+            if with_adjoint:
+                g0, gp, _ = tode.adjoint(field_e2e, dev_in["t0"], dev_in["t1"], dev_in["te"],
+                                         s, tape, dev_in["gye"], dev_in["gyf"], **opt)
+                res.update(gy0=g0, gp=gp)
             for k, v in res.items():
                 if k not in out_h:
                     out_h[k] = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
@@ -316,43 +338,61 @@ def run_tode(args):
     peaks, src = _peaks()
     clk_mhz = peaks.get("sm_max_mhz", 2032.0)
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = n_sms * 128 * 2 * clk_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 FLOPs
-    achieved = flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
-                "kernel": "k_fused<LinearField<float,2,8>> (fused forward)",
-                "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {clk_mhz:.0f} MHz",
-                "kernel_ms": k_fwd_ms}
+    if mlp:
+        # tensor-bound: algorithmic field FLOPs, 6 evaluations per attempt
+        wd = [x.shape[1] for x in w["field"]["W"]] + [w["field"]["W"][-1].shape[0]]
+        f_flops = 2 * sum(wd[l] * wd[l + 1] for l in range(len(wd) - 1))
+        achieved = 6 * f_flops * n_att / (k_fwd_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops"]
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_mlp_fused<D=32,H=128,3 layers,split>",
+                    "peak_source": f"bf16 burst, {src} (MEASURED_PEAKS.json)",
+                    "kernel_ms": k_fwd_ms}
+    else:
+        fp32_peak = n_sms * 128 * 2 * clk_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 FLOPs
+        achieved = flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak, "traffic": None,
+                    "kernel": "k_fused<LinearField<float,2,8>> (fused forward)",
+                    "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x "
+                                   f"{clk_mhz:.0f} MHz",
+                    "kernel_ms": k_fwd_ms}
     breakdown = {
-        "fused_fwd_adj": value,
         "fused_fwd": world * n_att / (ms_fused_fwd / nk * 1e-3),
-        "plain_fwd_adj": world * n_att / (ms_plain / args.plain_steps * 1e-3),
-        "plain_fwd": world * n_att / (ms_plain_fwd / args.plain_steps * 1e-3),
-        "fused_over_plain_fwd_adj": (ms_plain / args.plain_steps) / per_step,
-        "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
-        "adjoint_kernel_ms": k_adj_ms,
-        "adjoint_achieved_tflops": adjoint_flops_per_step(kind, D) * n_acc_total
-        / (k_adj_ms * 1e-3) / 1e12,
         "max_err_over_tol_vs_closed_form": err,
         "fused_equals_plain_bitwise": same,
         "instance_steps_per_pass": n_att,
     }
+    if with_adjoint:
+        breakdown.update({
+            "fused_fwd_adj": value,
+            "plain_fwd_adj": world * n_att / (ms_plain / args.plain_steps * 1e-3),
+            "plain_fwd": world * n_att / (ms_plain_fwd / args.plain_steps * 1e-3),
+            "fused_over_plain_fwd_adj": (ms_plain / args.plain_steps) / per_step,
+            "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
+            "adjoint_kernel_ms": k_adj_ms,
+            "adjoint_achieved_tflops": adjoint_flops_per_step(kind, D) * n_acc_total
+            / (k_adj_ms * 1e-3) / 1e12,
+        })
     result = {
         "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 (field, split activations) / f32 state" if mlp else "f32",
         "data": "synthetic (seeded, shaped like the paper's workloads)",
         "config": {"workload": w["name"], "B": B, "D": D, "K": K, "rtol": w["rtol"],
-                   "atol": w["atol"], "form": "fused", "pass": "fwd+adjoint",
+                   "atol": w["atol"], "form": "fused",
+                   "pass": "fwd+adjoint" if with_adjoint else "fwd",
                    "state": "f32 (compensated), time f64", "controller": "I (beta1=0.2)",
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
                    "parallelism": f"dp{world} (independent replicas of the batch)"},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (2 if with_adjoint else 1 + len(w["field"].get("W", []))) * args.steps,
         "clocks": clocks, "e2e": e2e, "roofline": roofline, "breakdown": breakdown,
         "wall_s_timed_region": wall_fused,
     }
     if rank == 0 and not args.no_cpu and world == 1:
-        result["cpu_baseline"] = cpu_baseline(w, budget_s=12.0)
+        result["cpu_baseline"] = cpu_baseline(w, budget_s=12.0, with_adjoint=with_adjoint)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -360,9 +400,10 @@ def run_tode(args):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_baseline(w, budget_s=12.0, nthreads=0):
-    """The FP64 oracle as it stands, forward + adjoint, on a seeded prefix of
-    the same workload sized to take roughly `budget_s` seconds."""
+def cpu_baseline(w, budget_s=12.0, nthreads=0, with_adjoint=True):
+    """The FP64 oracle as it stands (forward, + adjoint when the GPU pass has
+    one) on a seeded prefix of the same workload, sized to take roughly
+    `budget_s` seconds."""
     import oracle
     from oracle.oracle import mesh_from_trace
 
@@ -372,12 +413,13 @@ def cpu_baseline(w, budget_s=12.0, nthreads=0):
         r = oracle.solve(ws["field"], ws["y0"], ws["t0"], ws["t1"], ws["t_eval"],
                          dict(rtol=ws["rtol"], atol=ws["atol"]), trace_cap=8192,
                          nthreads=nthreads)
-        mt, mh, mn = mesh_from_trace(r)
-        K, D = ws["t_eval"].shape[1], ws["y0"].shape[1]
-        rng = np.random.default_rng(1)
-        oracle.adjoint(ws["field"], ws["y0"], ws["t0"], ws["t1"], mt, mh, mn, ws["t_eval"],
-                       rng.standard_normal((n, K, D)), rng.standard_normal((n, D)),
-                       nthreads=nthreads)
+        if with_adjoint:
+            mt, mh, mn = mesh_from_trace(r)
+            K, D = ws["t_eval"].shape[1], ws["y0"].shape[1]
+            rng = np.random.default_rng(1)
+            oracle.adjoint(ws["field"], ws["y0"], ws["t0"], ws["t1"], mt, mh, mn, ws["t_eval"],
+                           rng.standard_normal((n, K, D)), rng.standard_normal((n, D)),
+                           nthreads=nthreads)
         dt = time.perf_counter() - t
         return int((r["n_acc"] + r["n_rej"]).sum()), dt, r["threads"]
 
@@ -387,8 +429,8 @@ def cpu_baseline(w, budget_s=12.0, nthreads=0):
         n = min(w["B"], int(n * max(2.0, budget_s / max(dt, 1e-3) * 0.8)))
         att, dt, thr = run(n)
     return {"value": att / dt, "unit": "instance-steps/s", "cores": thr, "kind": "oracle",
-            "sample": f"first {n} of {w['B']} instances of {w['name']}, fwd+adjoint, "
-                      f"{dt:.1f} s"}
+            "sample": f"first {n} of {w['B']} instances of {w['name']}, "
+                      f"{'fwd+adjoint' if with_adjoint else 'fwd'}, {dt:.1f} s"}
 
 
 def run_reference(args):

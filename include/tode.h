@@ -229,14 +229,18 @@ tode_err tode_adjoint_static(const tode_field_desc* f, const tode_options* o, co
                              float* const* gb, int32_t* overflow, void* stream);
 
 /* The MLP field's tensor-core building block on its own, for checking the
- * operand layout and tensor-memory conventions against a plain product:
- * C[M][N] = A[M][K] * B[N][K]^T with A, B BF16 (uint16 bit patterns)
- * row-major and C float row-major, on one CTA with tcgen05.mma and FP32
- * accumulation in tensor memory.  M = 128; N, K multiples of 16 in
- * [16, 256].  err (device int32) is set to 1 if the tensor cores did not
- * signal completion within about a second (C is then left unwritten). */
-tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, int N, int K, int32_t* err,
-                      void* stream);
+ * operand layouts and tensor-memory conventions against a plain product:
+ * C[M][N] = sum_k A(m,k) B(n,k) with A, B BF16 (uint16 bit patterns) and C
+ * float row-major, on one CTA with tcgen05.mma and FP32 accumulation in
+ * tensor memory.  A is [M][K] row-major (K-major operand) or, with flags bit
+ * 0, [K][M] row-major (MN-major operand); likewise B is [N][K] or, with bit
+ * 1, [K][N].  Bit 2 swaps the two stride fields of MN-major descriptors.
+ * M = 128; N, K multiples of 16 in [16, 256] (K <= 128 and N <= 144 when
+ * any flag is set).  err (device int32) is set to
+ * 1 if the tensor cores did not signal completion within about a second (C
+ * is then left unwritten). */
+tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, int N, int K, int flags,
+                      int32_t* err, void* stream);
 
 /* Static text for an error code. */
 const char* tode_strerror(tode_err e);

@@ -129,7 +129,7 @@ def load(path: str = LIB_PATH):
                                         C.c_int, _vp, _vp, C.POINTER(Tape), _vp, _vp, _vp, _vp,
                                         C.POINTER(_vp), C.POINTER(_vp), _vp, _vp]
     lib.tode_tc_gemm.restype = C.c_int
-    lib.tode_tc_gemm.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]
+    lib.tode_tc_gemm.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp]
     _lib = lib
     return lib
 

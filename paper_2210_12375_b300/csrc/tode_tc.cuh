@@ -37,11 +37,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;                // base offset 0, layout SWIZZLE_NONE (0)
 }
 
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N/8 and M/16 fields.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// Descriptor of an MN-major operand stored as a core-matrix tile whose rows
+// are the K index (a [K][MN] tile): the leading-dimension field takes the
+// stride between groups of 8 K-rows (MN*16 bytes), the stride field the
+// 128-byte step between 8-element MN chunks (measured on sm_103a; the other
+// assignment gives wrong products).
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t saddr, uint32_t k8_stride,
+                                                 uint32_t mn8_stride = 128) {
+  return smem_desc(saddr, k8_stride, mn8_stride);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, N/8
+// and M/16 fields; a_mn / b_mn select the MN-major operand layout (the
+// operand's M or N index runs along the 16-byte rows of its core matrices).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool a_mn = false,
+                                                      bool b_mn = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // ---------------------------------------------------------------- TMEM

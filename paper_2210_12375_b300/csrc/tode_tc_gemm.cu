@@ -7,24 +7,42 @@
 
 namespace tode {
 
+// flags bit 0: A given as [K][M] row-major and fed MN-major; bit 1: the same
+// for B ([K][N]); bit 2: swap the two core-matrix strides of MN-major
+// operands (which descriptor field is which is what this probe checks).
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, float* C, int N,
-              int K, int32_t* err) {
+              int K, int flags, int32_t* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  unsigned char* sA = smem;                       // 128 x K
-  unsigned char* sB = smem + (size_t)128 * K * 2;  // N x K
+  // MN-major probes keep A and B 100 KB apart so that either reading of the
+  // descriptor's two stride fields stays inside this CTA's allocation
+  unsigned char* sA = smem;  // 128 x K
+  unsigned char* sB = smem + (flags ? (size_t)102400 : (size_t)128 * K * 2);  // N x K
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // operands into the core-matrix layout
+  const bool a_mn = flags & 1, b_mn = flags & 2, swap = flags & 4;
+  // operands into the core-matrix layout: K-major tiles are [rows][K]; an
+  // MN-major operand is stored as the [K][rows] tile it was given, i.e. its
+  // M (or N) index runs along the core matrices' 16-byte rows
   for (int e = tid; e < 128 * K; e += 128) {
-    const int row = e / K, k = e % K;
-    *reinterpret_cast<uint16_t*>(sA + tc::cm_offset(row, k, K)) = A[e];
+    if (a_mn) {
+      const int k = e / 128, m = e % 128;
+      *reinterpret_cast<uint16_t*>(sA + tc::cm_offset(k, m, 128)) = A[e];
+    } else {
+      const int row = e / K, k = e % K;
+      *reinterpret_cast<uint16_t*>(sA + tc::cm_offset(row, k, K)) = A[e];
+    }
   }
   for (int e = tid; e < N * K; e += 128) {
-    const int row = e / K, k = e % K;
-    *reinterpret_cast<uint16_t*>(sB + tc::cm_offset(row, k, K)) = B[e];
+    if (b_mn) {
+      const int k = e / N, n = e % N;
+      *reinterpret_cast<uint16_t*>(sB + tc::cm_offset(k, n, N)) = B[e];
+    } else {
+      const int row = e / K, k = e % K;
+      *reinterpret_cast<uint16_t*>(sB + tc::cm_offset(row, k, K)) = B[e];
+    }
   }
   if (tid == 0) {
     tc::mbar_init(&mbar, 1);
@@ -42,11 +60,26 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tbase = tmem_base;
 
   if (tid == 0) {
-    const uint32_t idesc = tc::idesc_bf16_f32(128, N);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, N, a_mn, b_mn);
     const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
     for (int kk = 0; kk < K / 16; ++kk) {
-      const uint64_t da = tc::smem_desc(a0 + kk * 256, 128, K * 16);
-      const uint64_t db = tc::smem_desc(b0 + kk * 256, 128, K * 16);
+      // K-major: next K slice is 2 core matrices (256 B) along K.  MN-major:
+      // 2 groups of 8 K-rows, each MN*16 bytes.
+      uint64_t da, db;
+      if (a_mn) {
+        const uint32_t kst = 128 * 16, mst = 128;
+        da = swap ? tc::smem_desc(a0 + kk * 2 * kst, kst, mst)
+                  : tc::smem_desc(a0 + kk * 2 * kst, mst, kst);
+      } else {
+        da = tc::smem_desc(a0 + kk * 256, 128, K * 16);
+      }
+      if (b_mn) {
+        const uint32_t kst = (uint32_t)N * 16, nst = 128;
+        db = swap ? tc::smem_desc(b0 + kk * 2 * kst, kst, nst)
+                  : tc::smem_desc(b0 + kk * 2 * kst, nst, kst);
+      } else {
+        db = tc::smem_desc(b0 + kk * 256, 128, K * 16);
+      }
       tc::mma_bf16(tbase, da, db, idesc, kk > 0);
     }
     tc::mma_commit(&mbar);
@@ -72,10 +105,12 @@ __global__ void __launch_bounds__(128, 1)
 }  // namespace tode
 
 extern "C" tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, int N, int K,
-                                 int32_t* err, void* stream) {
+                                 int flags, int32_t* err, void* stream) {
   if (!A || !B || !C || !err) return TODE_EINVAL;
   if (M != 128 || N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16) return TODE_EINVAL;
-  const size_t smem = (size_t)(128 + N) * K * 2;
+  if (flags & ~7) return TODE_EINVAL;
+  if (flags && (K > 128 || N > 144)) return TODE_EINVAL;
+  const size_t smem = flags ? (size_t)215040 : (size_t)(128 + N) * K * 2;
   cudaError_t e = cudaFuncSetAttribute(tode::k_tc_gemm,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) {
@@ -83,7 +118,7 @@ extern "C" tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, 
     return TODE_ECUDA;
   }
   tode::k_tc_gemm<<<1, 128, smem, (cudaStream_t)stream>>>((const uint16_t*)A, (const uint16_t*)B,
-                                                          C, N, K, err);
+                                                          C, N, K, flags, err);
   if (cudaGetLastError() != cudaSuccess) return TODE_ECUDA;
   return TODE_OK;
 }

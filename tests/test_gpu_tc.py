@@ -21,7 +21,7 @@ def test_tc_gemm_matches_fp32_product(N, K):
     Cm = torch.full((128, N), float("nan"), device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     rc = lib.tode_tc_gemm(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
-                          C.c_void_p(Cm.data_ptr()), 128, N, K, C.c_void_p(err.data_ptr()),
+                          C.c_void_p(Cm.data_ptr()), 128, N, K, 0, C.c_void_p(err.data_ptr()),
                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
     torch.cuda.synchronize()
     assert rc == 0 and int(err.item()) == 0
@@ -34,4 +34,29 @@ def test_tc_gemm_rejects_bad_shapes():
     lib = _abi.load()
     p = C.c_void_p(0x1000)
     for (M, N, K) in [(64, 16, 16), (128, 8, 16), (128, 16, 8), (128, 272, 16)]:
-        assert lib.tode_tc_gemm(p, p, p, M, N, K, p, None) == _abi.TODE_EINVAL
+        assert lib.tode_tc_gemm(p, p, p, M, N, K, 0, p, None) == _abi.TODE_EINVAL
+    assert lib.tode_tc_gemm(p, p, p, 128, 16, 16, 8, p, None) == _abi.TODE_EINVAL
+
+
+@pytest.mark.parametrize("flags", [5, 6, 7])
+@pytest.mark.parametrize("N", [32, 48, 128, 144])
+def test_tc_gemm_mn_major_operands(flags, N):
+    """Transposed (MN-major) operands, as the adjoint's weight-gradient GEMMs
+    use them: A given as [K][M] (flags bit 0) and/or B as [K][N] (bit 1),
+    with the stride fields the primitives use (bit 2)."""
+    lib = _abi.load()
+    K = 128
+    g = torch.Generator(device="cpu").manual_seed(flags * 100 + N)
+    A = torch.randn(128, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    Ain = (A.T.contiguous() if flags & 1 else A).cuda()
+    Bin = (B.T.contiguous() if flags & 2 else B).cuda()
+    Cm = torch.full((128, N), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.tode_tc_gemm(C.c_void_p(Ain.data_ptr()), C.c_void_p(Bin.data_ptr()),
+                          C.c_void_p(Cm.data_ptr()), 128, N, K, flags, C.c_void_p(err.data_ptr()),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == 0 and int(err.item()) == 0
+    ref = (A.double() @ B.double().T).cuda()
+    assert (Cm.double() - ref).abs().max().item() <= 1e-5 * max(1.0, ref.abs().max().item())
