@@ -83,7 +83,7 @@ enum {
  *               device pointers) W[l] is [widths[l+1]][widths[l]] BF16
  *               (uint16 bit patterns); b (host array of device pointers)
  *               b[l] is [widths[l+1]] float (NULL = zero).  Built shape:
- *               widths {33, 128, 128, 32}; fused form only; no tape yet. */
+ *               widths {33, 128, 128, 32}; fused form only. */
 typedef struct {
   tode_field_kind kind;
   int B;
@@ -120,7 +120,9 @@ typedef struct {
  * flags), from which tode_adjoint re-runs the forward bit for bit.
  * Instance i needs ceil(n_acc[i] / stride) slots; tode_solve never writes
  * past `slots`, and tode_adjoint reports instances that needed more through
- * its `overflow` output. */
+ * its `overflow` output.
+ * MLP field: stride must be 1 and only y, k1, t and h_acc are used (every
+ * accepted step is recorded; no re-run is needed). */
 typedef struct {
   int slots;
   int stride;
@@ -129,9 +131,12 @@ typedef struct {
                        (TODE_F32 / TODE_BF16W); ignored for TODE_F64 (may be NULL) */
   void* k1;         /* [slots][B][D] state dtype: f(t, y) carried by FSAL */
   double* t;        /* [slots][B] */
-  void* h;          /* [slots][B] state dtype */
+  void* h;          /* [slots][B] state dtype: step proposed for the next attempt */
   void* err_prev;   /* [slots][B] state dtype */
   int32_t* flags;   /* [slots][B] */
+  void* h_acc;      /* [slots][B] state dtype: size of the accepted step that
+                       starts at the slot (written when that step is accepted;
+                       required for the MLP field, optional otherwise) */
 } tode_tape;
 
 /* Per-attempt trace (testing and diagnostics): for instance i, attempt n <

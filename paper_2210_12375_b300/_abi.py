@@ -73,6 +73,7 @@ class Tape(C.Structure):
         ("h", _vp),
         ("err_prev", _vp),
         ("flags", _vp),
+        ("h_acc", _vp),
     ]
 
 

@@ -136,6 +136,7 @@ class TapeBuffers:
     h: torch.Tensor
     err_prev: torch.Tensor
     flags: torch.Tensor
+    h_acc: torch.Tensor
 
     @staticmethod
     def allocate(B, D, dtype, slots, stride, device):
@@ -147,12 +148,13 @@ class TapeBuffers:
                            torch.empty((slots, B), dtype=torch.float64, device=device),
                            torch.empty((slots, B), dtype=dtype, device=device),
                            torch.empty((slots, B), dtype=dtype, device=device),
-                           torch.empty((slots, B), dtype=torch.int32, device=device))
+                           torch.empty((slots, B), dtype=torch.int32, device=device),
+                           torch.empty((slots, B), dtype=dtype, device=device))
 
     @staticmethod
     def bytes_per_slot(B, D, itemsize):
         comp = D * itemsize if itemsize == 4 else 0
-        return B * (2 * D * itemsize + comp + 8 + 2 * itemsize + 4)
+        return B * (2 * D * itemsize + comp + 8 + 3 * itemsize + 4)
 
     def c(self) -> _abi.Tape:
         tp = _abi.Tape()
@@ -160,6 +162,7 @@ class TapeBuffers:
         tp.y, tp.y_lo, tp.k1 = self.y.data_ptr(), self.y_lo.data_ptr(), self.k1.data_ptr()
         tp.t, tp.h = self.t.data_ptr(), self.h.data_ptr()
         tp.err_prev, tp.flags = self.err_prev.data_ptr(), self.flags.data_ptr()
+        tp.h_acc = self.h_acc.data_ptr()
         return tp
 
 
@@ -253,11 +256,19 @@ def adjoint(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=Non
     gy0 = torch.empty((B, D), dtype=dtype, device=dev)
     params = field.params()
     gparam = torch.empty_like(params) if params is not None else None
+    gW_arr = gb_arr = None
+    if isinstance(field, MLP):
+        # float gradients of the weights and biases, summed over the batch
+        gW = [torch.empty(w.shape, dtype=torch.float32, device=dev) for w in field.W]
+        gb = [torch.empty(b.shape, dtype=torch.float32, device=dev) for b in field.b]
+        gW_arr = (C.c_void_p * len(gW))(*[g.data_ptr() for g in gW])
+        gb_arr = (C.c_void_p * len(gb))(*[g.data_ptr() for g in gb])
+        gparam = (gW, gb)
     overflow = torch.zeros(1, dtype=torch.int32, device=dev)
     code = lib.tode_adjoint(
         C.byref(fd), C.byref(opts), _ptr(t0), _ptr(t1), _ptr(t_eval) if K > 0 else None,
         int(K), _ptr(sol.n_acc), _ptr(sol.status), C.byref(tape_c), _ptr(gy_eval),
-        _ptr(gy_final), _ptr(gy0), _ptr(gparam), None, None, _ptr(overflow), _ptr(scratch),
-        C.c_size_t(scratch.numel()), _stream_handle(stream))
+        _ptr(gy_final), _ptr(gy0), _ptr(gparam) if params is not None else None, gW_arr, gb_arr,
+        _ptr(overflow), _ptr(scratch), C.c_size_t(scratch.numel()), _stream_handle(stream))
     _abi.check(code, "tode_adjoint")
     return gy0, gparam, overflow

@@ -54,9 +54,21 @@ static tode_err field_ok(const tode_field_desc* f, const tode_options* o) {
   return TODE_EINVAL;
 }
 
-static bool tape_ok(const tode_tape* tp, const tode_options* o) {
+static bool tape_ok(const tode_tape* tp, const tode_options* o, const tode_field_desc* f) {
+  if (f->kind == TODE_MLP)
+    return tp->slots >= 1 && tp->stride == 1 && tp->y && tp->k1 && tp->t && tp->h_acc;
   return tp->slots >= 1 && tp->stride >= 1 && tp->y && tp->k1 && tp->t && tp->h &&
          tp->err_prev && tp->flags && (o->prec == TODE_F64 || tp->y_lo);
+}
+
+static int sm_count_or_zero() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return sms;
 }
 
 static tode_err device_sms(int* sms) {
@@ -128,7 +140,7 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
   if (!y0 || !t0 || !t1 || !y_final || !n_acc || !n_rej || !n_feval || !status)
     return TODE_EINVAL;
   if (K > 0 && (!t_eval || !y_eval)) return TODE_EINVAL;
-  if (tape && !tape_ok(tape, o)) return TODE_EINVAL;
+  if (tape && !tape_ok(tape, o, f)) return TODE_EINVAL;
   if (trace) {
     if (trace->cap < 0) return TODE_EINVAL;
     if (trace->cap > 0 &&
@@ -167,7 +179,13 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
 size_t tode_adjoint_scratch_size(const tode_field_desc* f, const tode_options* o,
                                  const tode_tape* tape) {
   if (!opts_ok(o) || field_ok(f, o) != TODE_OK || !tape || tape->stride < 1) return 0;
-  if (f->kind == TODE_MLP) return 0;  // not built yet
+  if (f->kind == TODE_MLP) {
+    // sized for one CTA per SM of the current device (at least one SM)
+    const int sms = sm_count_or_zero();
+    return (tape->stride == 1 && o->prec == TODE_BF16W_SPLIT)
+               ? mlp_adjoint_scratch_bytes(f->B, sms > 0 ? sms : 1)
+               : 0;
+  }
   return simt_adjoint_scratch_bytes(f->B, f->D, state_size(o), tape->stride);
 }
 
@@ -180,11 +198,11 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
   if (!opts_ok(o) || K < 0) return TODE_EINVAL;
   tode_err e = field_ok(f, o);
   if (e != TODE_OK) return e;
-  if (f->kind == TODE_MLP) return TODE_EUNSUPPORTED;  // not built yet
+  if (f->kind == TODE_MLP && o->prec != TODE_BF16W_SPLIT) return TODE_EUNSUPPORTED;
   if (f->B == 0) return TODE_OK;
   if (!t0 || !t1 || !n_acc || !status || !tape || !gy0 || !overflow) return TODE_EINVAL;
   if (K > 0 && !t_eval) return TODE_EINVAL;
-  if (!tape_ok(tape, o)) return TODE_EINVAL;
+  if (!tape_ok(tape, o, f)) return TODE_EINVAL;
   const size_t need = tode_adjoint_scratch_size(f, o, tape);
   if (!scratch || !aligned256(scratch) || scratch_bytes < need) return TODE_EWORKSPACE;
   AdjReq r{};
@@ -211,6 +229,7 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
   r.stream = (cudaStream_t)stream;
   e = device_sms(&r.num_sms);
   if (e != TODE_OK) return e;
+  if (f->kind == TODE_MLP) return mlp_adjoint(r);
   return o->prec == TODE_F64 ? simt_adjoint_f64(r) : simt_adjoint_f32(r);
 }
 

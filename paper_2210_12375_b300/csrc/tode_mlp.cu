@@ -28,6 +28,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace tode {
 
 constexpr int MLP_MAX_LAYERS = 4;
@@ -50,6 +52,12 @@ struct MlpArgs {
   const float* bias[MLP_MAX_LAYERS];
   int32_t* counter;
   int32_t* err;
+  // checkpoint tape (every accepted step; slots == 0: none)
+  int slots;
+  float* tp_y;
+  float* tp_k1;
+  double* tp_t;
+  float* tp_h;
 };
 
 template <int D_, int H_, int NL_, bool SPLIT_> struct MlpCfg {
@@ -542,6 +550,18 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
           t_next = s.t1;
         }
         const long long kn = tkey(t_next);
+        if (s.n_acc < a.slots) {  // tape: the state this accepted step started from
+          const size_t o = (size_t)s.n_acc * a.B + i;
+#pragma unroll
+          for (int r = 0; r < C; ++r) {
+            a.tp_y[o * D + coff + r] = y[r];
+            a.tp_k1[o * D + coff + r] = k[0][r];
+          }
+          if (half == 0) {
+            a.tp_t[o] = s.t;
+            a.tp_h[o] = h;
+          }
+        }
         float yn[16], ylon[16];
 #pragma unroll
         for (int r = 0; r < C; ++r) {
@@ -649,6 +669,668 @@ __global__ void k_mlp_weight_image(const uint16_t* __restrict__ W, int N, int Ki
   *reinterpret_cast<uint16_t*>(img + tc::cm_offset(n, kk, Kp)) = v;
 }
 
+// ======================================================================
+// Discrete adjoint of the MLP-field solve (torchode App. A: gradients by
+// backpropagation through the solver), on the frozen mesh the forward
+// recorded (every accepted step: y_n, FSAL k1, t_n, h_n).
+//
+// Rows of a 128-row tile reverse their own instances (assigned statically,
+// row r of CTA c takes instances c*128 + r, c*128 + r + 128*grid, ..., so the
+// weight gradients are summed in a fixed order).  Each round runs, for the
+// whole tile, the forward layers at a stage input [Y; t] (the output layer's
+// f serves rows that are recomputing stages) and the backward chain for a
+// stage cotangent kbar (rows that are in the reverse sweep; the others send
+// kbar = 0 and contribute nothing):
+//   gh2 = kbar W3        dW3^T += h2^T kbar          (h2: split BF16 tile)
+//   delta2 = gh2 (1 - h2^2)
+//   gh1 = delta2 W2      dW2 += delta2^T h1, db2 += delta2^T 1
+//   delta1 = gh1 (1 - h1^2)
+//   gx = delta1 W1       dW1 += delta1^T [X | 1]     (the 1 column gives db1)
+// Transposed operands are the same shared-memory tiles read MN-major; dW
+// accumulates in tensor memory over the whole kernel and is written once
+// per CTA as a partial, which k_mlp_grad_reduce sums over CTAs in order.
+// ======================================================================
+template <class Cfg> struct MlpAdjLayout {
+  static constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0;
+  static_assert(Cfg::NL == 3 && Cfg::SPLIT, "adjoint built for two hidden layers, split");
+  static constexpr int S_W = 0;
+  static constexpr int S_XH = ((Cfg::WIMG_BYTES + 1023) / 1024) * 1024;
+  static constexpr int S_XL = S_XH + 128 * K0 * 2;
+  static constexpr int S_H1H = S_XL + 128 * K0 * 2;
+  static constexpr int S_H1L = S_H1H + 128 * H * 2;
+  static constexpr int S_H2H = S_H1L + 128 * H * 2;
+  static constexpr int S_H2L = S_H2H + 128 * H * 2;
+  static constexpr int S_D3H = S_H2L + 128 * H * 2;
+  static constexpr int S_D3L = S_D3H + 128 * D * 2;
+  static constexpr int S_ONES = S_D3L + 128 * D * 2;
+  static constexpr int S_BIAS = S_ONES + 128 * 16 * 2;
+  static constexpr int S_END = S_BIAS + Cfg::BIAS_FLOATS * 4;
+  static_assert(S_END <= 232448, "shared memory");
+  // tensor memory columns (accumulators start on 32-column boundaries)
+  static constexpr uint32_t T_R = 0, T_D0 = 128, T_D1 = T_D0 + ((K0 + 31) / 32) * 32,
+                            T_DB = T_D1 + H, T_D2 = T_DB + 32, T_COLS = 512;
+  static_assert(T_D2 + D <= T_COLS, "tensor memory");
+  // per-CTA partial gradient block (floats)
+  static constexpr int P_W0 = 0;                 // [H][K0]  (col D: t weight, col D+1: db1)
+  static constexpr int P_W1 = P_W0 + H * K0;     // [H][H]
+  static constexpr int P_B1 = P_W1 + H * H;      // [H]
+  static constexpr int P_W2T = P_B1 + H;         // [H][D]   (dW3 transposed)
+  static constexpr int P_B2 = P_W2T + H * D;     // [D]
+  static constexpr int P_FLOATS = P_B2 + D;
+};
+
+struct MlpAdjArgs {
+  int B, K;
+  const double* t0;
+  const double* t1;
+  const double* te;
+  const int32_t* n_acc;
+  const int32_t* status;
+  int slots;
+  const float* tp_y;
+  const float* tp_k1;
+  const double* tp_t;
+  const float* tp_h;
+  const float* gye;
+  const float* gyf;
+  float* gy0;
+  const unsigned char* wimg;
+  const float* bias[MLP_MAX_LAYERS];
+  float* kscr;   // [grid][128][7][D] stage derivatives of the step being reversed
+  float* part;   // [grid][P_FLOATS]
+  int32_t* overflow;
+  int32_t* err;
+};
+
+// adjoint row phases: 0 idle, 1..6 recompute stage s = phase + 1,
+// 7..13 reverse stage s = 14 - phase
+enum : int { AP_IDLE = 0, AP_A = 1, AP_C = 7 };
+
+template <class Cfg>
+__global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
+  using L = MlpAdjLayout<Cfg>;
+  using Cc = DP5;
+  constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, HC = Cfg::HC;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar_mma, mbar_w;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  unsigned char* sW = sm + L::S_W;
+  unsigned char* sXh = sm + L::S_XH;
+  unsigned char* sXl = sm + L::S_XL;
+  unsigned char* sH1h = sm + L::S_H1H;
+  unsigned char* sH1l = sm + L::S_H1L;
+  unsigned char* sH2h = sm + L::S_H2H;
+  unsigned char* sH2l = sm + L::S_H2L;
+  unsigned char* sD3h = sm + L::S_D3H;
+  unsigned char* sD3l = sm + L::S_D3L;
+  unsigned char* sOnes = sm + L::S_ONES;
+  float* sBias = reinterpret_cast<float*>(sm + L::S_BIAS);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & 127, half = tid >> 7;
+  const int coff = half * C;
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const int grid = gridDim.x;
+
+  if (tid == 0) {
+    tc::mbar_init(&mbar_mma, 1);
+    tc::mbar_init(&mbar_w, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    tc::mbar_expect_tx(&mbar_w, (uint32_t)Cfg::WIMG_BYTES);
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      tc::bulk_g2s(sW + Cfg::W_off(l), a.wimg + Cfg::W_off(l), (uint32_t)Cfg::W_bytes(l), &mbar_w);
+  }
+  {
+    int o = 0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const int n = Cfg::N_of(l);
+      for (int j = tid; j < n; j += 256) sBias[o + j] = a.bias[l] ? a.bias[l][j] : 0.0f;
+      o += n;
+    }
+  }
+  // input tiles: zero, with a constant 1 in column D+1 (hi) for db1
+  for (int j = tid; j < 128 * K0 * 2 / 16; j += 256) {
+    reinterpret_cast<uint4*>(sXh)[j] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(sXl)[j] = make_uint4(0, 0, 0, 0);
+  }
+  // ones operand for db2: [K = 128 rows][N = 16], column 0 = 1
+  for (int j = tid; j < 128 * 16; j += 256) {
+    const int r = j / 16, c = j % 16;
+    *reinterpret_cast<__nv_bfloat16*>(sOnes + tc::cm_offset(r, c, 16)) =
+        __float2bfloat16_rn(c == 0 ? 1.0f : 0.0f);
+  }
+  __syncthreads();
+  if (tid < 128)
+    *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(tid, D + 1, K0)) =
+        __float2bfloat16_rn(1.0f);
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base_s, L::T_COLS);
+    tc::tmem_relinquish();
+  }
+  if (!tc::mbar_wait(&mbar_w, 0)) atomicExch(&abort_s, 1);
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tmem_base_s;
+  uint32_t parity = 0;
+  bool first_round = true;
+
+  // ---- per-row reverse state
+  int inst = blockIdx.x * 128 + row;  // static assignment (fixed summation order)
+  int ph = AP_IDLE, n = -1, N = 0, q = -1;
+  bool bad = false, dense7 = false;
+  double tn = 0.0, tnext = 0.0;
+  float h = 0.0f;
+  float yn[16], yb[16], db3[16], kb[7][16];
+#pragma unroll
+  for (int r = 0; r < C; ++r) {
+    yn[r] = yb[r] = db3[r] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) kb[j][r] = 0.0f;
+  }
+  float* kslot = a.kscr + ((size_t)blockIdx.x * 128 + row) * 7 * D + coff;
+  const float bw[7] = {float(Cc::b1), 0.0f, float(Cc::b3), float(Cc::b4), float(Cc::b5),
+                       float(Cc::b6), 0.0f};
+
+  auto load_step = [&](int i) {  // step n of instance i: recompute its stages next
+    const size_t o = (size_t)n * a.B + i;
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      yn[r] = a.tp_y[o * D + coff + r];
+      kslot[r] = a.tp_k1[o * D + coff + r];  // k1 (FSAL stage)
+    }
+    tn = a.tp_t[o];
+    h = a.tp_h[o];
+    tnext = (n == N - 1) ? a.t1[i] : tn + (double)h;
+    ph = AP_A;  // stage 2
+  };
+  // advance through instances until this row has a step to work on (or none)
+  auto next_work = [&](bool finishing) {
+    while (true) {
+      if (finishing) {
+        const int i = inst;
+        if (!bad && a.gye) {
+          const long long k0 = tkey(a.t0[i]);
+          for (; q >= 0; --q)
+            if (tkey(a.te[(size_t)i * a.K + q]) == k0)
+#pragma unroll
+              for (int r = 0; r < C; ++r) yb[r] += a.gye[((size_t)i * a.K + q) * D + coff + r];
+        }
+#pragma unroll
+        for (int r = 0; r < C; ++r) a.gy0[(size_t)i * D + coff + r] = bad ? nan_(0.0f) : yb[r];
+        inst += grid * 128;
+        finishing = false;
+      }
+      if (inst >= a.B) {
+        ph = AP_IDLE;
+        return;
+      }
+      const int i = inst;
+      N = a.n_acc[i];
+      bad = a.status[i] != ST_SUCCESS;
+      if (!bad && N > a.slots) {
+        bad = true;
+        if (half == 0) atomicExch(a.overflow, 1);
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + coff + r] : 0.0f;
+      q = a.K - 1;
+      n = N - 1;
+      if (bad || n < 0) {
+        finishing = true;
+        continue;
+      }
+      load_step(i);
+      return;
+    }
+  };
+  next_work(false);
+
+  const uint32_t idH = tc::idesc_bf16_f32(128, H);
+  while (true) {
+    const bool any = __syncthreads_or(ph != AP_IDLE) != 0;
+    if (!any || abort_s) break;
+
+    // ---- stage input [Y_s; t_s] and stage cotangent of this row
+    const int s = (ph >= AP_C) ? 14 - ph : ph + 1;  // stage 1..7 (idle: 0)
+    float Y[16], d3[16];
+    float tin = 0.0f;
+    if (ph == AP_IDLE) {
+#pragma unroll
+      for (int r = 0; r < C; ++r) Y[r] = d3[r] = 0.0f;
+    } else {
+      // Y_s = y_n + h sum_{j<s} a_sj k_j (the forward's formulas; Y_7 = y_{n+1})
+#pragma unroll
+      for (int r = 0; r < C; ++r) Y[r] = 0.0f;
+      if (s >= 2) {
+        float kj[16];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          if (j >= s - 1) break;
+          float c;
+          switch (s) {
+            case 2: c = float(Cc::a21); break;
+            case 3: c = j == 0 ? float(Cc::a31) : float(Cc::a32); break;
+            case 4: c = j == 0 ? float(Cc::a41) : j == 1 ? float(Cc::a42) : float(Cc::a43); break;
+            case 5: c = j == 0 ? float(Cc::a51) : j == 1 ? float(Cc::a52) : j == 2 ? float(Cc::a53)
+                                                                             : float(Cc::a54);
+                    break;
+            case 6: c = j == 0 ? float(Cc::a61) : j == 1 ? float(Cc::a62) : j == 2 ? float(Cc::a63)
+                      : j == 3 ? float(Cc::a64) : float(Cc::a65);
+                    break;
+            default: c = bw[j]; break;
+          }
+#pragma unroll
+          for (int r = 0; r < C; ++r) kj[r] = kslot[j * D + r];
+#pragma unroll
+          for (int r = 0; r < C; ++r) Y[r] = (j == 0) ? c * kj[r] : madd(c, kj[r], Y[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) Y[r] = (s == 7) ? yn[r] + h * Y[r] : madd(h, Y[r], yn[r]);
+      double cs = 0.0;
+      switch (s) {
+        case 2: cs = Cc::c2; break;
+        case 3: cs = Cc::c3; break;
+        case 4: cs = Cc::c4; break;
+        case 5: cs = Cc::c5; break;
+        case 6: case 7: cs = 1.0; break;
+        default: cs = 0.0; break;
+      }
+      tin = (float)(tn + cs * (double)h);
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        float v = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+          if (ph >= AP_C && j == s - 1) v = kb[j][r];
+        d3[r] = v;
+      }
+    }
+    store_row16<true>(sXh, sXl, row, coff, K0, Y);
+    store_row16<true>(sD3h, sD3l, row, coff, D, d3);
+    if (half == 1) {
+      const __nv_bfloat16 th = __float2bfloat16_rn(tin);
+      const __nv_bfloat16 tl = __float2bfloat16_rn(tin - __bfloat162float(th));
+      *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(row, D, K0)) = th;
+      *reinterpret_cast<__nv_bfloat16*>(sXl + tc::cm_offset(row, D, K0)) = tl;
+    }
+    auto barrier = [&]() {
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    };
+    auto wait_mma = [&]() {
+      if (!tc::mbar_wait(&mbar_mma, parity)) atomicExch(&abort_s, 1);
+      parity ^= 1u;
+      tc::fence_after_sync();
+    };
+    // hidden epilogue: h = tanh(acc + b) into a split tile
+    auto hidden_epi = [&](const float* bl, unsigned char* th, unsigned char* tl) {
+#pragma unroll
+      for (int c = 0; c < HC; c += 16) {
+        const int col = half * HC + c;
+        float v[16];
+        tc::tmem_ld16(tbase + lane_base + L::T_R + col, v);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = tanh_acc(v[j] + bl[col + j]);
+        store_row16<true>(th, tl, row, col, H, v);
+      }
+    };
+    // backward epilogue: delta = acc (1 - h^2), h = hi + lo of the tile; the
+    // split delta replaces h in place (row-local; the tile's other readers
+    // are done)
+    auto delta_epi = [&](unsigned char* th, unsigned char* tl) {
+#pragma unroll
+      for (int c = 0; c < HC; c += 16) {
+        const int col = half * HC + c;
+        float v[16];
+        tc::tmem_ld16(tbase + lane_base + L::T_R + col, v);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t off = tc::cm_offset(row, col + j, H);
+          const float hv = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(th + off)) +
+                           __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tl + off));
+          v[j] = v[j] * madd(-hv, hv, 1.0f);
+        }
+        store_row16<true>(th, tl, row, col, H, v);
+      }
+    };
+    barrier();
+
+    // F0: acc = X W1^T (hi + lo)
+    if (tid == 0) {
+      const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(0));
+      for (int kk = 0; kk < K0 / 16; ++kk) {
+        const uint64_t db = tc::smem_desc(wa + kk * 256, 128, K0 * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sXh) + kk * 256, 128, K0 * 16), db,
+                     idH, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sXl) + kk * 256, 128, K0 * 16), db,
+                     idH, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    hidden_epi(sBias, sH1h, sH1l);
+    barrier();
+    // F1: acc = h1 W2^T
+    if (tid == 0) {
+      const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(1));
+      for (int kk = 0; kk < H / 16; ++kk) {
+        const uint64_t db = tc::smem_desc(wa + kk * 256, 128, H * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH1h) + kk * 256, 128, H * 16), db,
+                     idH, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH1l) + kk * 256, 128, H * 16), db,
+                     idH, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    hidden_epi(sBias + H, sH2h, sH2l);
+    barrier();
+    // L2: acc[0:D] = h2 W3^T  (f for rows recomputing stages)
+    if (tid == 0) {
+      const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(2));
+      const uint32_t idD = tc::idesc_bf16_f32(128, D);
+      for (int kk = 0; kk < H / 16; ++kk) {
+        const uint64_t db = tc::smem_desc(wa + kk * 256, 128, H * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2h) + kk * 256, 128, H * 16), db,
+                     idD, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2l) + kk * 256, 128, H * 16), db,
+                     idD, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    float f[16];
+    {
+      float v[16];
+      tc::tmem_ld16(tbase + lane_base + L::T_R + coff, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int r = 0; r < C; ++r) f[r] = v[r] + sBias[2 * H + coff + r];
+    }
+    barrier();
+    // B2: acc = kbar W3;  dW3^T += h2^T kbar  (split operands: hi*hi + lo*hi + hi*lo)
+    if (tid == 0) {
+      const uint32_t w3 = tc::smem_u32(sW + Cfg::W_off(2));
+      const uint32_t dh = tc::smem_u32(sD3h), dl = tc::smem_u32(sD3l);
+      const uint32_t idR = tc::idesc_bf16_f32(128, H, false, true);
+      for (int kk = 0; kk < D / 16; ++kk) {
+        const uint64_t db = tc::smem_desc_mn(w3 + kk * 2 * (H * 16), H * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, D * 16), db, idR, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, D * 16), db, idR, true);
+      }
+      const uint32_t idT = tc::idesc_bf16_f32(128, D, true, true);
+      const uint32_t hh = tc::smem_u32(sH2h), hl = tc::smem_u32(sH2l);
+      for (int kk = 0; kk < 128 / 16; ++kk) {
+        const uint64_t bh = tc::smem_desc_mn(dh + kk * 2 * (D * 16), D * 16);
+        const uint64_t bl = tc::smem_desc_mn(dl + kk * 2 * (D * 16), D * 16);
+        const uint64_t ah = tc::smem_desc_mn(hh + kk * 2 * (H * 16), H * 16);
+        const uint64_t al = tc::smem_desc_mn(hl + kk * 2 * (H * 16), H * 16);
+        tc::mma_bf16(tbase + L::T_D2, ah, bh, idT, !(first_round && kk == 0));
+        tc::mma_bf16(tbase + L::T_D2, al, bh, idT, true);
+        tc::mma_bf16(tbase + L::T_D2, ah, bl, idT, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    delta_epi(sH2h, sH2l);  // delta2 replaces h2
+    barrier();
+    // B1: acc = delta2 W2;  dW2 += delta2^T h1;  db2 += delta2^T 1
+    if (tid == 0) {
+      const uint32_t w2 = tc::smem_u32(sW + Cfg::W_off(1));
+      const uint32_t dh = tc::smem_u32(sH2h), dl = tc::smem_u32(sH2l);
+      const uint32_t idR = tc::idesc_bf16_f32(128, H, false, true);
+      for (int kk = 0; kk < H / 16; ++kk) {
+        const uint64_t db = tc::smem_desc_mn(w2 + kk * 2 * (H * 16), H * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, H * 16), db, idR, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, H * 16), db, idR, true);
+      }
+      const uint32_t idT = tc::idesc_bf16_f32(128, H, true, true);
+      const uint32_t idB = tc::idesc_bf16_f32(128, 16, true, true);
+      const uint32_t hh = tc::smem_u32(sH1h), hl = tc::smem_u32(sH1l);
+      for (int kk = 0; kk < 128 / 16; ++kk) {
+        const uint64_t ah = tc::smem_desc_mn(dh + kk * 2 * (H * 16), H * 16);
+        const uint64_t al = tc::smem_desc_mn(dl + kk * 2 * (H * 16), H * 16);
+        const uint64_t bh = tc::smem_desc_mn(hh + kk * 2 * (H * 16), H * 16);
+        const uint64_t bl = tc::smem_desc_mn(hl + kk * 2 * (H * 16), H * 16);
+        const uint64_t b1 = tc::smem_desc_mn(tc::smem_u32(sOnes) + kk * 2 * (16 * 16), 16 * 16);
+        const bool acc = !(first_round && kk == 0);
+        tc::mma_bf16(tbase + L::T_D1, ah, bh, idT, acc);
+        tc::mma_bf16(tbase + L::T_D1, al, bh, idT, true);
+        tc::mma_bf16(tbase + L::T_D1, ah, bl, idT, true);
+        tc::mma_bf16(tbase + L::T_DB, ah, b1, idB, acc);
+        tc::mma_bf16(tbase + L::T_DB, al, b1, idB, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    delta_epi(sH1h, sH1l);  // delta1 replaces h1
+    barrier();
+    // B0: acc = delta1 W1;  dW1 += delta1^T [X | 1]
+    if (tid == 0) {
+      const uint32_t w1 = tc::smem_u32(sW + Cfg::W_off(0));
+      const uint32_t dh = tc::smem_u32(sH1h), dl = tc::smem_u32(sH1l);
+      const uint32_t idR = tc::idesc_bf16_f32(128, K0, false, true);
+      for (int kk = 0; kk < H / 16; ++kk) {
+        const uint64_t db = tc::smem_desc_mn(w1 + kk * 2 * (K0 * 16), K0 * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, H * 16), db, idR, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, H * 16), db, idR, true);
+      }
+      const uint32_t idT = tc::idesc_bf16_f32(128, K0, true, true);
+      const uint32_t xh = tc::smem_u32(sXh), xl = tc::smem_u32(sXl);
+      for (int kk = 0; kk < 128 / 16; ++kk) {
+        const uint64_t ah = tc::smem_desc_mn(dh + kk * 2 * (H * 16), H * 16);
+        const uint64_t al = tc::smem_desc_mn(dl + kk * 2 * (H * 16), H * 16);
+        const uint64_t bh = tc::smem_desc_mn(xh + kk * 2 * (K0 * 16), K0 * 16);
+        const uint64_t bl = tc::smem_desc_mn(xl + kk * 2 * (K0 * 16), K0 * 16);
+        const bool acc = !(first_round && kk == 0);
+        tc::mma_bf16(tbase + L::T_D0, ah, bh, idT, acc);
+        tc::mma_bf16(tbase + L::T_D0, al, bh, idT, true);
+        tc::mma_bf16(tbase + L::T_D0, ah, bl, idT, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    float g[16];
+    {
+      float v[16];
+      tc::tmem_ld16(tbase + lane_base + L::T_R + coff, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int r = 0; r < C; ++r) g[r] = v[r];
+    }
+    first_round = false;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
+    // ---- consume
+    if (ph == AP_IDLE) continue;
+    const int i = inst;
+    if (ph < AP_C) {
+      // recomputed stage s: store k_s
+#pragma unroll
+      for (int r = 0; r < C; ++r) kslot[(s - 1) * D + r] = f[r];
+      if (s < 7) {
+        ph += 1;
+      } else {
+        // stage cotangents from ybar_{n+1} and the step's dense outputs
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+#pragma unroll
+          for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
+        dense7 = false;
+        const long long kt = tkey(tn), kn = tkey(tnext);
+        while (q >= 0) {
+          const double tq = a.te[(size_t)i * a.K + q];
+          const long long kq = tkey(tq);
+          if (!(kq > kt)) break;
+          if (a.gye) {
+            float gq[16], w[7];
+#pragma unroll
+            for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + coff + r];
+            if (kq == kn) {
+#pragma unroll
+              for (int j = 0; j < 7; ++j) w[j] = bw[j];
+            } else {
+              dense_weights<float>(float(tq - tn) / h, w);
+              dense7 = true;
+            }
+#pragma unroll
+            for (int j = 0; j < 7; ++j)
+#pragma unroll
+              for (int r = 0; r < C; ++r) kb[j][r] = madd(h * w[j], gq[r], kb[j][r]);
+#pragma unroll
+            for (int r = 0; r < C; ++r) yb[r] += gq[r];
+          }
+          q--;
+        }
+        ph = dense7 ? AP_C : AP_C + 1;  // reverse from stage 7 (or 6: kbar_7 = 0)
+      }
+    } else {
+      // reversed stage s: g = J_f(Y_s)^T kbar_s
+#pragma unroll
+      for (int r = 0; r < C; ++r) db3[r] += (s == 7) ? kb[6][r] : 0.0f;
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int r = 0; r < C; ++r)
+          if (j == s - 1) db3[r] += kb[j][r];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j >= s - 1) break;
+        float c;
+        switch (s) {
+          case 2: c = float(Cc::a21); break;
+          case 3: c = j == 0 ? float(Cc::a31) : float(Cc::a32); break;
+          case 4: c = j == 0 ? float(Cc::a41) : j == 1 ? float(Cc::a42) : float(Cc::a43); break;
+          case 5: c = j == 0 ? float(Cc::a51) : j == 1 ? float(Cc::a52) : j == 2 ? float(Cc::a53)
+                                                                           : float(Cc::a54);
+                  break;
+          case 6: c = j == 0 ? float(Cc::a61) : j == 1 ? float(Cc::a62) : j == 2 ? float(Cc::a63)
+                    : j == 3 ? float(Cc::a64) : float(Cc::a65);
+                  break;
+          default: c = bw[j]; break;
+        }
+#pragma unroll
+        for (int r = 0; r < C; ++r) kb[j][r] = madd(h * c, g[r], kb[j][r]);
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) yb[r] += g[r];
+      if (s > 1) {
+        ph += 1;
+      } else {
+        n -= 1;  // step n reversed
+        if (n >= 0) load_step(i);
+        else next_work(true);
+      }
+    }
+  }
+
+  // ---- per-CTA partial gradients: tensor-memory accumulators, db3 over rows
+  float* P = a.part + (size_t)blockIdx.x * L::P_FLOATS;
+  tc::fence_after_sync();
+  {
+    const uint32_t lb = tbase + lane_base;
+    float v[16];
+    // dW1 (and its t and bias columns): lane = output unit of layer 1
+    for (int c = half * 32; c < (half ? K0 : 32); c += 16) {
+      tc::tmem_ld16(lb + L::T_D0 + c, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) P[L::P_W0 + row * K0 + c + j] = v[j];
+    }
+#pragma unroll
+    for (int c = 0; c < HC; c += 16) {
+      const int col = half * HC + c;
+      tc::tmem_ld16(lb + L::T_D1 + col, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) P[L::P_W1 + row * H + col + j] = v[j];
+    }
+    tc::tmem_ld16(lb + L::T_DB, v);
+    tc::tmem_wait_ld();
+    if (half == 0) P[L::P_B1 + row] = v[0];
+    tc::tmem_ld16(lb + L::T_D2 + coff, v);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) P[L::P_W2T + row * D + coff + j] = v[j];
+  }
+  // db3: sum the rows' accumulators in a fixed order (reuses the h2 tile)
+  float* sDb = reinterpret_cast<float*>(sH2h);
+  tc::fence_before_sync();
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < C; ++r) sDb[row * D + coff + r] = db3[r];
+  __syncthreads();
+  if (tid < D) {
+    float acc = 0.0f;
+    for (int rr = 0; rr < 128; ++rr) acc += sDb[rr * D + tid];
+    P[L::P_B2 + tid] = acc;
+  }
+  if (abort_s && tid == 0) atomicExch(a.err, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, L::T_COLS);
+}
+
+// Sums the per-CTA partials in CTA order into the caller's gradients
+// (layouts of the weights: W_l [out][in], b_l [out]).
+template <class Cfg>
+__global__ void k_mlp_grad_reduce(const float* part, int grid, float* gW0, float* gb0, float* gW1,
+                                  float* gb1, float* gW2, float* gb2) {
+  using L = MlpAdjLayout<Cfg>;
+  constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, IN = D + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  auto sum = [&](int off) {
+    float acc = 0.0f;
+    for (int c = 0; c < grid; ++c) acc += part[(size_t)c * L::P_FLOATS + off];
+    return acc;
+  };
+  int k = e;
+  if (k < H * IN) {
+    const int o = k / IN, j = k % IN;
+    gW0[k] = sum(L::P_W0 + o * K0 + j);
+    return;
+  }
+  k -= H * IN;
+  if (k < H) {
+    if (gb0) gb0[k] = sum(L::P_W0 + k * K0 + IN);
+    return;
+  }
+  k -= H;
+  if (k < H * H) {
+    gW1[k] = sum(L::P_W1 + k);
+    return;
+  }
+  k -= H * H;
+  if (k < H) {
+    if (gb1) gb1[k] = sum(L::P_B1 + k);
+    return;
+  }
+  k -= H;
+  if (k < D * H) {
+    const int o = k / H, j = k % H;  // W3 [out = D][in = H]
+    gW2[k] = sum(L::P_W2T + j * D + o);
+    return;
+  }
+  k -= D * H;
+  if (k < D && gb2) gb2[k] = sum(L::P_B2 + k);
+}
+
 // ---------------------------------------------------------------- host side
 using Cfg32 = MlpCfg<32, 128, 3, false>;
 using Cfg32s = MlpCfg<32, 128, 3, true>;
@@ -689,6 +1371,15 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   a.o.beta2 = r.o->beta2;
   a.o.h0 = r.o->h0;
   a.o.max_steps = r.o->max_steps;
+  if (r.tape) {
+    a.slots = r.tape->slots;
+    a.tp_y = (float*)r.tape->y;
+    a.tp_k1 = (float*)r.tape->k1;
+    a.tp_t = r.tape->t;
+    a.tp_h = (float*)r.tape->h_acc;
+  } else {
+    a.slots = 0;
+  }
   if (r.trace) {
     a.trace.cap = r.trace->cap;
     a.trace.t = r.trace->t;
@@ -726,8 +1417,71 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
 
 tode_err mlp_solve(const SolveReq& r, bool split) {
   if (r.o->form != TODE_FUSED) return TODE_EUNSUPPORTED;
-  if (r.tape) return TODE_EUNSUPPORTED;
+  if (r.tape && r.tape->stride != 1) return TODE_EUNSUPPORTED;
   return split ? launch_mlp<Cfg32s>(r) : launch_mlp<Cfg32>(r);
+}
+
+size_t mlp_adjoint_scratch_bytes(int B, int num_sms) {
+  using L = MlpAdjLayout<Cfg32s>;
+  const long long grid = std::min<long long>((B + 127) / 128, num_sms);
+  return align256(256) + align256((size_t)Cfg32s::WIMG_BYTES) +
+         align256((size_t)grid * 128 * 7 * Cfg32s::D * 4) +
+         align256((size_t)grid * L::P_FLOATS * 4);
+}
+
+tode_err mlp_adjoint(const AdjReq& r) {
+  using Cfg = Cfg32s;
+  using L = MlpAdjLayout<Cfg>;
+  if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->k1 || !r.tape->y || !r.tape->t)
+    return TODE_EINVAL;
+  if (!r.gW || !r.gW[0] || !r.gW[1] || !r.gW[2]) return TODE_EINVAL;
+  const cudaStream_t st = r.stream;
+  const long long grid = std::min<long long>((r.B + 127) / 128, r.num_sms);
+  MlpAdjArgs a{};
+  a.B = r.B;
+  a.K = r.K;
+  a.t0 = r.t0;
+  a.t1 = r.t1;
+  a.te = r.te;
+  a.n_acc = r.n_acc;
+  a.status = r.status;
+  a.slots = r.tape->slots;
+  a.tp_y = (const float*)r.tape->y;
+  a.tp_k1 = (const float*)r.tape->k1;
+  a.tp_t = r.tape->t;
+  a.tp_h = (const float*)r.tape->h_acc;
+  a.gye = (const float*)r.gye;
+  a.gyf = (const float*)r.gyf;
+  a.gy0 = (float*)r.gy0;
+  for (int l = 0; l < MLP_MAX_LAYERS; ++l) a.bias[l] = l < 3 ? r.f->b[l] : nullptr;
+  char* p = r.scratch;
+  a.err = (int32_t*)(p + 128);
+  p += align256(256);
+  unsigned char* img = (unsigned char*)p;
+  a.wimg = img;
+  p += align256((size_t)Cfg::WIMG_BYTES);
+  a.kscr = (float*)p;
+  p += align256((size_t)grid * 128 * 7 * Cfg::D * 4);
+  a.part = (float*)p;
+  a.overflow = r.overflow;
+  for (int l = 0; l < 3; ++l) {
+    const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
+    k_mlp_weight_image<<<(N * Kp + 255) / 256, 256, 0, st>>>((const uint16_t*)r.f->W[l], N, Kin,
+                                                             Kp, img + Cfg::W_off(l));
+  }
+  TODE_CUDA_TRY(cudaGetLastError());
+  TODE_CUDA_TRY(cudaMemsetAsync(r.scratch, 0, 256, st));
+  TODE_CUDA_TRY(cudaFuncSetAttribute(k_mlp_adjoint<Cfg>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::S_END));
+  k_mlp_adjoint<Cfg><<<(int)grid, 256, L::S_END, st>>>(a);
+  TODE_CUDA_TRY(cudaGetLastError());
+  const int total = Cfg::H * (Cfg::D + 1) + Cfg::H + Cfg::H * Cfg::H + Cfg::H +
+                    Cfg::D * Cfg::H + Cfg::D;
+  k_mlp_grad_reduce<Cfg><<<(total + 255) / 256, 256, 0, st>>>(
+      a.part, (int)grid, r.gW[0], r.gb ? r.gb[0] : nullptr, r.gW[1], r.gb ? r.gb[1] : nullptr,
+      r.gW[2], r.gb ? r.gb[2] : nullptr);
+  TODE_CUDA_TRY(cudaGetLastError());
+  return TODE_OK;
 }
 
 }  // namespace tode
