@@ -10,7 +10,7 @@ for fixed seeded cotangents c, d.  An instance-step is one attempted step
 of a live instance.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-       [--workload 2|3|1]
+       [--workload 2|3|1|4]
 Under torchrun (N > 1) every rank solves its own copy of the batch (weak
 scaling, no data-path collective) and rank 0 prints one JSON line.
 """
@@ -188,10 +188,9 @@ def run_tode(args):
     n_att = int((probe.n_acc.long() + probe.n_rej.long()).sum().item())
     n_acc_total = int(probe.n_acc.long().sum().item())
     n_acc_max = int(probe.n_acc.max().item())
-    # the MLP field has no adjoint and no plain form yet: forward, fused
-    with_adjoint = not mlp
-    tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev) \
-        if with_adjoint else None
+    # every field has the adjoint; the MLP field has no plain form yet
+    with_adjoint = True
+    tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev)
 
     def fwd(form, sol=None, ws=None):
         return tode.solve(field, y0, t0, t1, te, form=form, tape=tape, out=sol, workspace=ws,
@@ -281,10 +280,11 @@ def run_tode(args):
     e2e = None
     if not args.no_e2e:
         src = dict(y0=y0, t0=t0, t1=t1, te=te)
-        if with_adjoint:
-            src.update(gye=gye, gyf=gyf, P=field.params())
-        else:
+        src.update(gye=gye, gyf=gyf)
+        if mlp:
             src.update({f"W{l}": x for l, x in enumerate(field.W)})
+        else:
+            src.update(P=field.params())
         host = {k: v.cpu().pin_memory() for k, v in src.items()}
         dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
         if kind == "linear":
@@ -309,7 +309,12 @@ def run_tode(args):
             if with_adjoint:
                 g0, gp, _ = tode.adjoint(field_e2e, dev_in["t0"], dev_in["t1"], dev_in["te"],
                                          s, tape, dev_in["gye"], dev_in["gyf"], **opt)
-                res.update(gy0=g0, gp=gp)
+                res["gy0"] = g0
+                if mlp:  # (gW, gb) lists of the MLP field
+                    res.update({f"gW{l}": x for l, x in enumerate(gp[0])})
+                    res.update({f"gb{l}": x for l, x in enumerate(gp[1])})
+                else:
+                    res["gp"] = gp
             for k, v in res.items():
                 if k not in out_h:
                     out_h[k] = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
@@ -338,43 +343,56 @@ def run_tode(args):
     peaks, src = _peaks()
     clk_mhz = peaks.get("sm_max_mhz", 2032.0)
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sms * 128 * 2 * clk_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 FLOPs
     if mlp:
-        # tensor-bound: algorithmic field FLOPs, 6 evaluations per attempt
+        # tensor-bound: algorithmic FLOPs of the field and of its VJP
         wd = [x.shape[1] for x in w["field"]["W"]] + [w["field"]["W"][-1].shape[0]]
-        f_flops = 2 * sum(wd[l] * wd[l + 1] for l in range(len(wd) - 1))
-        achieved = 6 * f_flops * n_att / (k_fwd_ms * 1e-3) / 1e12
+        S = sum(wd[l] * wd[l + 1] for l in range(len(wd) - 1))  # MACs of one evaluation
         peak = peaks["bf16_tflops"]
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": "k_mlp_fused<D=32,H=128,3 layers,split>",
-                    "peak_source": f"bf16 burst, {src} (MEASURED_PEAKS.json)",
-                    "kernel_ms": k_fwd_ms}
+        kf = {"achieved": 6 * 2 * S * n_att / (k_fwd_ms * 1e-3) / 1e12,
+              "kernel": "k_mlp_fused<D=32,H=128,3 layers,split> (fused forward)",
+              "kernel_ms": k_fwd_ms}
+        # per accepted step: 7 evaluations (stages recomputed, activations at
+        # every stage input) and 6 transposed products dX + dW (2 x 2S MACs)
+        ka = {"achieved": (7 * 2 * S + 6 * 4 * S) * n_acc_total / (k_adj_ms * 1e-3) / 1e12,
+              "kernel": "k_mlp_adjoint<D=32,H=128,3 layers,split>", "kernel_ms": k_adj_ms}
+        for r in (kf, ka):
+            r.update(bound="tensor", peak=peak, unit="TFLOP/s", frac=r["achieved"] / peak,
+                     traffic=None, peak_source=f"bf16 burst, {src} (MEASURED_PEAKS.json)")
     else:
-        fp32_peak = n_sms * 128 * 2 * clk_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 FLOPs
-        achieved = flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp32_peak, "traffic": None,
-                    "kernel": "k_fused<LinearField<float,2,8>> (fused forward)",
-                    "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x "
-                                   f"{clk_mhz:.0f} MHz",
-                    "kernel_ms": k_fwd_ms}
+        psrc = f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {clk_mhz:.0f} MHz"
+        kf = {"achieved": flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12,
+              "kernel": "k_fused<LinearField<float,2,8>> (fused forward)", "kernel_ms": k_fwd_ms}
+        ka = {"achieved": adjoint_flops_per_step(kind, D) * n_acc_total / (k_adj_ms * 1e-3)
+              / 1e12, "kernel": "k_adjoint<LinearAdj<float,2,8>>", "kernel_ms": k_adj_ms}
+        for r in (kf, ka):
+            r.update(bound="alu", peak=fp32_peak, unit="TFLOP/s",
+                     frac=r["achieved"] / fp32_peak, traffic=None, peak_source=psrc)
+    # the dominant kernel of the timed step (forward + adjoint) is the roofline line
+    roofline, other = (ka, kf) if k_adj_ms >= k_fwd_ms else (kf, ka)
     breakdown = {
         "fused_fwd": world * n_att / (ms_fused_fwd / nk * 1e-3),
         "max_err_over_tol_vs_closed_form": err,
         "fused_equals_plain_bitwise": same,
         "instance_steps_per_pass": n_att,
+        "other_kernel_roofline": other,
     }
     if with_adjoint:
         breakdown.update({
             "fused_fwd_adj": value,
+            "adjoint_kernel_ms": k_adj_ms,
+            "accepted_steps_per_pass": n_acc_total,
+        })
+    if not mlp:
+        breakdown.update({
             "plain_fwd_adj": world * n_att / (ms_plain / args.plain_steps * 1e-3),
             "plain_fwd": world * n_att / (ms_plain_fwd / args.plain_steps * 1e-3),
             "fused_over_plain_fwd_adj": (ms_plain / args.plain_steps) / per_step,
             "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
-            "adjoint_kernel_ms": k_adj_ms,
-            "adjoint_achieved_tflops": adjoint_flops_per_step(kind, D) * n_acc_total
-            / (k_adj_ms * 1e-3) / 1e12,
         })
+    # our kernels per timed step: fused forward (+3 weight-image builds for the
+    # MLP) and the adjoint (+3 image builds and the ordered dW reduction)
+    gpu_launches = 4 + 5 if mlp else 2
     result = {
         "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
@@ -387,7 +405,7 @@ def run_tode(args):
                    "state": "f32 (compensated), time f64", "controller": "I (beta1=0.2)",
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
                    "parallelism": f"dp{world} (independent replicas of the batch)"},
-        "gpu_launches": (2 if with_adjoint else 1 + len(w["field"].get("W", []))) * args.steps,
+        "gpu_launches": gpu_launches * args.steps,
         "clocks": clocks, "e2e": e2e, "roofline": roofline, "breakdown": breakdown,
         "wall_s_timed_region": wall_fused,
     }
