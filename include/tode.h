@@ -121,8 +121,10 @@ typedef struct {
  * Instance i needs ceil(n_acc[i] / stride) slots; tode_solve never writes
  * past `slots`, and tode_adjoint reports instances that needed more through
  * its `overflow` output.
- * MLP field: stride must be 1 and only y, k1, t and h_acc are used (every
- * accepted step is recorded; no re-run is needed). */
+ * With stride 1 and h_acc given (the same tape struct for both calls), every
+ * accepted step is on the tape with its size and tode_adjoint reverses it
+ * directly, without re-running the forward's attempts.
+ * MLP field: stride must be 1 and only y, k1, t and h_acc are used. */
 typedef struct {
   int slots;
   int stride;

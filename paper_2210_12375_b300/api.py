@@ -136,7 +136,7 @@ class TapeBuffers:
     h: torch.Tensor
     err_prev: torch.Tensor
     flags: torch.Tensor
-    h_acc: torch.Tensor
+    h_acc: Optional[torch.Tensor]  # None: the adjoint re-runs each segment's attempts
 
     @staticmethod
     def allocate(B, D, dtype, slots, stride, device):
@@ -162,7 +162,7 @@ class TapeBuffers:
         tp.y, tp.y_lo, tp.k1 = self.y.data_ptr(), self.y_lo.data_ptr(), self.k1.data_ptr()
         tp.t, tp.h = self.t.data_ptr(), self.h.data_ptr()
         tp.err_prev, tp.flags = self.err_prev.data_ptr(), self.flags.data_ptr()
-        tp.h_acc = self.h_acc.data_ptr()
+        tp.h_acc = self.h_acc.data_ptr() if self.h_acc is not None else None
         return tp
 
 

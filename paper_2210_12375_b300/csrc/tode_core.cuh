@@ -308,6 +308,7 @@ template <typename T> struct TapeDev {
   T* h;
   T* err_prev;
   int32_t* flags;
+  T* h_acc;  // optional: size of the accepted step that starts at the slot
 };
 struct TraceDev {
   int cap;
@@ -340,6 +341,17 @@ __device__ __forceinline__ void tape_store(const TapeDev<T>& tp, int i, const In
     tp.err_prev[o] = s.err_prev;
     tp.flags[o] = s.flags;
   }
+}
+
+// After an accepted attempt: the size of that step (n = n_acc - 1) into its
+// slot, so that a stride-1 adjoint can reverse straight from the tape.
+template <typename T, int R, int G>
+__device__ __forceinline__ void tape_store_hacc(const TapeDev<T>& tp, int i, const Inst<T, R>& s) {
+  const int n = s.n_acc - 1;
+  if (tp.slots == 0 || !tp.h_acc || (n % tp.stride) != 0) return;
+  const int j = n / tp.stride;
+  if (j >= tp.slots) return;
+  if (Grp<G>::rank() == 0) tp.h_acc[(size_t)j * tp.B + i] = s.h_last;
 }
 
 // ---------------------------------------------------------------- init (a1, a2)

@@ -676,11 +676,12 @@ __global__ void k_mlp_weight_image(const uint16_t* __restrict__ W, int N, int Ki
 //
 // Rows of a 128-row tile reverse their own instances (assigned statically,
 // row r of CTA c takes instances c*128 + r, c*128 + r + 128*grid, ..., so the
-// weight gradients are summed in a fixed order).  Each round runs, for the
-// whole tile, the forward layers at a stage input [Y; t] (the output layer's
-// f serves rows that are recomputing stages) and the backward chain for a
-// stage cotangent kbar (rows that are in the reverse sweep; the others send
-// kbar = 0 and contribute nothing):
+// weight gradients are summed in a fixed order).  Reversing one accepted step
+// takes 12 rounds for every row, so all rows of a tile stay in step:
+//   rounds 0..4   recompute stages 2..6: forward layers at Y_s, f = k_s
+//   rounds 5..11  reverse stages 7..1: hidden layers at Y_s, then the
+//                 backward chain for the stage cotangent kbar_s
+// A reverse round, for the whole tile:
 //   gh2 = kbar W3        dW3^T += h2^T kbar          (h2: split BF16 tile)
 //   delta2 = gh2 (1 - h2^2)
 //   gh1 = delta2 W2      dW2 += delta2^T h1, db2 += delta2^T 1
@@ -689,10 +690,14 @@ __global__ void k_mlp_weight_image(const uint16_t* __restrict__ W, int N, int Ki
 // Transposed operands are the same shared-memory tiles read MN-major; dW
 // accumulates in tensor memory over the whole kernel and is written once
 // per CTA as a partial, which k_mlp_grad_reduce sums over CTAs in order.
+// The stage inputs Y_2..Y_6 of the step being reversed wait in tensor memory
+// between the recompute and the reverse rounds; Y_7 comes from the stage
+// sums still in registers, Y_1 is the step's start.
 // ======================================================================
 template <class Cfg> struct MlpAdjLayout {
   static constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0;
   static_assert(Cfg::NL == 3 && Cfg::SPLIT, "adjoint built for two hidden layers, split");
+  static_assert(D == 32 && H == 128 && K0 == 48, "tensor-memory plan below");
   static constexpr int S_W = 0;
   static constexpr int S_XH = ((Cfg::WIMG_BYTES + 1023) / 1024) * 1024;
   static constexpr int S_XL = S_XH + 128 * K0 * 2;
@@ -705,11 +710,16 @@ template <class Cfg> struct MlpAdjLayout {
   static constexpr int S_ONES = S_D3L + 128 * D * 2;
   static constexpr int S_BIAS = S_ONES + 128 * 16 * 2;
   static constexpr int S_END = S_BIAS + Cfg::BIAS_FLOATS * 4;
-  static_assert(S_END <= 232448, "shared memory");
-  // tensor memory columns (accumulators start on 32-column boundaries)
-  static constexpr uint32_t T_R = 0, T_D0 = 128, T_D1 = T_D0 + ((K0 + 31) / 32) * 32,
-                            T_DB = T_D1 + H, T_D2 = T_DB + 32, T_COLS = 512;
-  static_assert(T_D2 + D <= T_COLS, "tensor memory");
+  static_assert(S_END <= 232448 - 1024, "shared memory");
+  // tensor memory columns: accumulators on 32-column boundaries
+  //   R [0,128)  D1 [128,256)  D0 [256,304)  DB [320,336)  D2 [352,384)
+  // and ten 16-column halves of the stage inputs Y_2..Y_6 in the gaps
+  static constexpr uint32_t T_R = 0, T_D1 = 128, T_D0 = 256, T_DB = 320, T_D2 = 352,
+                            T_COLS = 512;
+  __device__ static uint32_t y_col(int s, int half) {
+    const int u = (s - 2) * 2 + half;  // 0..9
+    return u == 0 ? 304u : (u == 1 ? 336u : 384u + 16u * (uint32_t)(u - 2));
+  }
   // per-CTA partial gradient block (floats)
   static constexpr int P_W0 = 0;                 // [H][K0]  (col D: t weight, col D+1: db1)
   static constexpr int P_W1 = P_W0 + H * K0;     // [H][H]
@@ -736,21 +746,62 @@ struct MlpAdjArgs {
   float* gy0;
   const unsigned char* wimg;
   const float* bias[MLP_MAX_LAYERS];
-  float* kscr;   // [grid][128][7][D] stage derivatives of the step being reversed
   float* part;   // [grid][P_FLOATS]
   int32_t* overflow;
   int32_t* err;
 };
 
-// adjoint row phases: 0 idle, 1..6 recompute stage s = phase + 1,
-// 7..13 reverse stage s = 14 - phase
-enum : int { AP_IDLE = 0, AP_A = 1, AP_C = 7 };
+constexpr int ADJ_ROUNDS = 12;
+
+// a_{s,j} of the tableau (stage 7 row = b), as float; s = 2..7, j = 1..6
+__device__ __forceinline__ float dp_a(int s, int j) {
+  using C = DP5;
+  switch (s * 8 + j) {
+    case 17: return float(C::a21);
+    case 25: return float(C::a31);
+    case 26: return float(C::a32);
+    case 33: return float(C::a41);
+    case 34: return float(C::a42);
+    case 35: return float(C::a43);
+    case 41: return float(C::a51);
+    case 42: return float(C::a52);
+    case 43: return float(C::a53);
+    case 44: return float(C::a54);
+    case 49: return float(C::a61);
+    case 50: return float(C::a62);
+    case 51: return float(C::a63);
+    case 52: return float(C::a64);
+    case 53: return float(C::a65);
+    case 57: return float(C::b1);
+    case 59: return float(C::b3);
+    case 60: return float(C::b4);
+    case 61: return float(C::b5);
+    case 62: return float(C::b6);
+    default: return 0.0f;
+  }
+}
+__device__ __forceinline__ double dp_c(int s) {
+  using C = DP5;
+  return s == 2 ? C::c2 : s == 3 ? C::c3 : s == 4 ? C::c4 : s == 5 ? C::c5 : s >= 6 ? 1.0 : 0.0;
+}
+// o = k[j] for a runtime j (selects; keeps k in registers)
+__device__ __forceinline__ void pick7(const float (&k)[7][16], int j, float (&o)[16]) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) o[r] = k[0][r];
+#pragma unroll
+  for (int u = 1; u < 7; ++u)
+    if (u == j) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) o[r] = k[u][r];
+    }
+}
 
 template <class Cfg>
 __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   using L = MlpAdjLayout<Cfg>;
   using Cc = DP5;
   constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, HC = Cfg::HC;
+  static_assert(C == 16, "16 state components per thread");
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar_mma, mbar_w;
   __shared__ uint32_t tmem_base_s;
@@ -820,13 +871,15 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = tmem_base_s;
+  const uint32_t tl = tbase + lane_base;  // this warp's lane quarter
   uint32_t parity = 0;
-  bool first_round = true;
+  bool dw_first = true;  // the next backward round starts the dW accumulators
 
   // ---- per-row reverse state
-  int inst = blockIdx.x * 128 + row;  // static assignment (fixed summation order)
-  int ph = AP_IDLE, n = -1, N = 0, q = -1;
-  bool bad = false, dense7 = false;
+  int inst = blockIdx.x * 128 + row;
+  bool act = false;
+  int n = -1, N = 0, q = -1;
+  bool bad = false;
   double tn = 0.0, tnext = 0.0;
   float h = 0.0f;
   float yn[16], yb[16], db3[16], kb[7][16];
@@ -836,23 +889,31 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 #pragma unroll
     for (int j = 0; j < 7; ++j) kb[j][r] = 0.0f;
   }
-  float* kslot = a.kscr + ((size_t)blockIdx.x * 128 + row) * 7 * D + coff;
-  const float bw[7] = {float(Cc::b1), 0.0f, float(Cc::b3), float(Cc::b4), float(Cc::b5),
-                       float(Cc::b6), 0.0f};
 
-  auto load_step = [&](int i) {  // step n of instance i: recompute its stages next
+  // step n of instance i: its start, and the stage sums acc_s = a_s1 k1
+  // (kb[s-1], s = 2..7) that the recompute rounds complete
+  auto load_step = [&](int i) {
     const size_t o = (size_t)n * a.B + i;
+    const float4* py = reinterpret_cast<const float4*>(a.tp_y + o * D + coff);
+    const float4* pk = reinterpret_cast<const float4*>(a.tp_k1 + o * D + coff);
+    float k1[16];
 #pragma unroll
-    for (int r = 0; r < C; ++r) {
-      yn[r] = a.tp_y[o * D + coff + r];
-      kslot[r] = a.tp_k1[o * D + coff + r];  // k1 (FSAL stage)
+    for (int v = 0; v < 4; ++v) {
+      const float4 u = py[v], w = pk[v];
+      yn[4 * v] = u.x, yn[4 * v + 1] = u.y, yn[4 * v + 2] = u.z, yn[4 * v + 3] = u.w;
+      k1[4 * v] = w.x, k1[4 * v + 1] = w.y, k1[4 * v + 2] = w.z, k1[4 * v + 3] = w.w;
     }
     tn = a.tp_t[o];
     h = a.tp_h[o];
     tnext = (n == N - 1) ? a.t1[i] : tn + (double)h;
-    ph = AP_A;  // stage 2
+#pragma unroll
+    for (int j = 1; j < 7; ++j)
+#pragma unroll
+      for (int r = 0; r < C; ++r) kb[j][r] = dp_a(j + 1, 1) * k1[r];
+    act = true;
   };
-  // advance through instances until this row has a step to work on (or none)
+  // finish the current instance (if `finishing`) and move to the next one
+  // that has a step to reverse
   auto next_work = [&](bool finishing) {
     while (true) {
       if (finishing) {
@@ -870,7 +931,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
         finishing = false;
       }
       if (inst >= a.B) {
-        ph = AP_IDLE;
+        act = false;
         return;
       }
       const int i = inst;
@@ -894,119 +955,138 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   };
   next_work(false);
 
+  auto barrier = [&]() {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  auto wait_mma = [&]() {
+    if (!tc::mbar_wait(&mbar_mma, parity)) atomicExch(&abort_s, 1);
+    parity ^= 1u;
+    tc::fence_after_sync();
+  };
+  // hidden epilogue: h = tanh(acc + b) into a split tile
+  auto hidden_epi = [&](const float* bl, unsigned char* th, unsigned char* tlo) {
+#pragma unroll
+    for (int c = 0; c < HC; c += 16) {
+      const int col = half * HC + c;
+      float v[16];
+      tc::tmem_ld16(tl + L::T_R + col, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = tanh_acc(v[j] + bl[col + j]);
+      store_row16<true>(th, tlo, row, col, H, v);
+    }
+  };
+  // backward epilogue: delta = acc (1 - h^2) with h = hi + lo of the tile;
+  // the split delta replaces h in place (row-local; its other readers are done)
+  auto delta_epi = [&](unsigned char* th, unsigned char* tlo) {
+#pragma unroll
+    for (int c = 0; c < HC; c += 16) {
+      const int col = half * HC + c;
+      float v[16];
+      tc::tmem_ld16(tl + L::T_R + col, v);
+#pragma unroll
+      for (int c8 = 0; c8 < 2; ++c8) {
+        const uint32_t off = tc::cm_offset(row, col + 8 * c8, H);
+        const uint4 hv = *reinterpret_cast<const uint4*>(th + off);
+        const uint4 lv = *reinterpret_cast<const uint4*>(tlo + off);
+        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
+          const __nv_bfloat162 l2 = *reinterpret_cast<const __nv_bfloat162*>(&lw[j]);
+          const float x0 = __low2float(h2) + __low2float(l2);
+          const float x1 = __high2float(h2) + __high2float(l2);
+          v[8 * c8 + 2 * j] *= madd(-x0, x0, 1.0f);
+          v[8 * c8 + 2 * j + 1] *= madd(-x1, x1, 1.0f);
+        }
+      }
+      store_row16<true>(th, tlo, row, col, H, v);
+    }
+  };
+  const float bw[7] = {float(Cc::b1), 0.0f, float(Cc::b3), float(Cc::b4), float(Cc::b5),
+                       float(Cc::b6), 0.0f};
   const uint32_t idH = tc::idesc_bf16_f32(128, H);
-  while (true) {
-    const bool any = __syncthreads_or(ph != AP_IDLE) != 0;
-    if (!any || abort_s) break;
 
-    // ---- stage input [Y_s; t_s] and stage cotangent of this row
-    const int s = (ph >= AP_C) ? 14 - ph : ph + 1;  // stage 1..7 (idle: 0)
+  for (int rnd = 0;; ++rnd) {
+    const int ph = rnd % ADJ_ROUNDS;
+    if (ph == 0 && __syncthreads_or(act) == 0) break;
+    const bool rev = ph >= 5;
+    const int s = rev ? 12 - ph : ph + 2;  // stage of this round (block-uniform)
+
+    // ---- stage input [Y_s; t_s] and, in reverse rounds, the cotangent kbar_s
     float Y[16], d3[16];
     float tin = 0.0f;
-    if (ph == AP_IDLE) {
+    if (!rev) {
+      float acc[16];
+      pick7(kb, s - 1, acc);
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = d3[r] = 0.0f;
-    } else {
-      // Y_s = y_n + h sum_{j<s} a_sj k_j (the forward's formulas; Y_7 = y_{n+1})
+      for (int r = 0; r < C; ++r) Y[r] = act ? madd(h, acc[r], yn[r]) : 0.0f;
+      tc::tmem_st16(tl + L::y_col(s, half), Y);  // kept for the reverse round
+      tc::tmem_wait_st();
+    } else if (s == 7) {
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = 0.0f;
-      if (s >= 2) {
-        float kj[16];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          if (j >= s - 1) break;
-          float c;
-          switch (s) {
-            case 2: c = float(Cc::a21); break;
-            case 3: c = j == 0 ? float(Cc::a31) : float(Cc::a32); break;
-            case 4: c = j == 0 ? float(Cc::a41) : j == 1 ? float(Cc::a42) : float(Cc::a43); break;
-            case 5: c = j == 0 ? float(Cc::a51) : j == 1 ? float(Cc::a52) : j == 2 ? float(Cc::a53)
-                                                                             : float(Cc::a54);
-                    break;
-            case 6: c = j == 0 ? float(Cc::a61) : j == 1 ? float(Cc::a62) : j == 2 ? float(Cc::a63)
-                      : j == 3 ? float(Cc::a64) : float(Cc::a65);
-                    break;
-            default: c = bw[j]; break;
-          }
-#pragma unroll
-          for (int r = 0; r < C; ++r) kj[r] = kslot[j * D + r];
-#pragma unroll
-          for (int r = 0; r < C; ++r) Y[r] = (j == 0) ? c * kj[r] : madd(c, kj[r], Y[r]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = (s == 7) ? yn[r] + h * Y[r] : madd(h, Y[r], yn[r]);
-      double cs = 0.0;
-      switch (s) {
-        case 2: cs = Cc::c2; break;
-        case 3: cs = Cc::c3; break;
-        case 4: cs = Cc::c4; break;
-        case 5: cs = Cc::c5; break;
-        case 6: case 7: cs = 1.0; break;
-        default: cs = 0.0; break;
-      }
-      tin = (float)(tn + cs * (double)h);
-#pragma unroll
-      for (int r = 0; r < C; ++r) {
-        float v = 0.0f;
+      for (int r = 0; r < C; ++r) Y[r] = act ? yn[r] + h * kb[6][r] : 0.0f;
+      if (act) {
+        // kbar_i = h b_i ybar_{n+1} + sum_{tau in step} h b_i(theta_tau) ybar_tau
+        const int i = inst;
 #pragma unroll
         for (int j = 0; j < 7; ++j)
-          if (ph >= AP_C && j == s - 1) v = kb[j][r];
-        d3[r] = v;
+#pragma unroll
+          for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
+        const long long kt = tkey(tn), kn = tkey(tnext);
+        while (q >= 0) {
+          const double tq = a.te[(size_t)i * a.K + q];
+          const long long kq = tkey(tq);
+          if (!(kq > kt)) break;
+          if (a.gye) {
+            float gq[16], w[7];
+#pragma unroll
+            for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + coff + r];
+            if (kq == kn) {
+#pragma unroll
+              for (int j = 0; j < 7; ++j) w[j] = bw[j];
+            } else {
+              dense_weights<float>(float(tq - tn) / h, w);
+            }
+#pragma unroll
+            for (int j = 0; j < 7; ++j)
+#pragma unroll
+              for (int r = 0; r < C; ++r) kb[j][r] = madd(h * w[j], gq[r], kb[j][r]);
+#pragma unroll
+            for (int r = 0; r < C; ++r) yb[r] += gq[r];
+          }
+          q--;
+        }
       }
+    } else if (s >= 2) {
+      tc::tmem_ld16(tl + L::y_col(s, half), Y);
+      tc::tmem_wait_ld();
+      if (!act)
+#pragma unroll
+        for (int r = 0; r < C; ++r) Y[r] = 0.0f;
+    } else {
+#pragma unroll
+      for (int r = 0; r < C; ++r) Y[r] = act ? yn[r] : 0.0f;
+    }
+    if (act) tin = (float)(tn + dp_c(s) * (double)h);
+    if (rev) {
+      pick7(kb, s - 1, d3);
+      if (!act)
+#pragma unroll
+        for (int r = 0; r < C; ++r) d3[r] = 0.0f;
+      store_row16<true>(sD3h, sD3l, row, coff, D, d3);
     }
     store_row16<true>(sXh, sXl, row, coff, K0, Y);
-    store_row16<true>(sD3h, sD3l, row, coff, D, d3);
     if (half == 1) {
       const __nv_bfloat16 th = __float2bfloat16_rn(tin);
-      const __nv_bfloat16 tl = __float2bfloat16_rn(tin - __bfloat162float(th));
+      const __nv_bfloat16 tlo = __float2bfloat16_rn(tin - __bfloat162float(th));
       *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(row, D, K0)) = th;
-      *reinterpret_cast<__nv_bfloat16*>(sXl + tc::cm_offset(row, D, K0)) = tl;
+      *reinterpret_cast<__nv_bfloat16*>(sXl + tc::cm_offset(row, D, K0)) = tlo;
     }
-    auto barrier = [&]() {
-      tc::fence_proxy_async();
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
-    };
-    auto wait_mma = [&]() {
-      if (!tc::mbar_wait(&mbar_mma, parity)) atomicExch(&abort_s, 1);
-      parity ^= 1u;
-      tc::fence_after_sync();
-    };
-    // hidden epilogue: h = tanh(acc + b) into a split tile
-    auto hidden_epi = [&](const float* bl, unsigned char* th, unsigned char* tl) {
-#pragma unroll
-      for (int c = 0; c < HC; c += 16) {
-        const int col = half * HC + c;
-        float v[16];
-        tc::tmem_ld16(tbase + lane_base + L::T_R + col, v);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = tanh_acc(v[j] + bl[col + j]);
-        store_row16<true>(th, tl, row, col, H, v);
-      }
-    };
-    // backward epilogue: delta = acc (1 - h^2), h = hi + lo of the tile; the
-    // split delta replaces h in place (row-local; the tile's other readers
-    // are done)
-    auto delta_epi = [&](unsigned char* th, unsigned char* tl) {
-#pragma unroll
-      for (int c = 0; c < HC; c += 16) {
-        const int col = half * HC + c;
-        float v[16];
-        tc::tmem_ld16(tbase + lane_base + L::T_R + col, v);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t off = tc::cm_offset(row, col + j, H);
-          const float hv = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(th + off)) +
-                           __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tl + off));
-          v[j] = v[j] * madd(-hv, hv, 1.0f);
-        }
-        store_row16<true>(th, tl, row, col, H, v);
-      }
-    };
     barrier();
 
     // F0: acc = X W1^T (hi + lo)
@@ -1039,202 +1119,150 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
     wait_mma();
     hidden_epi(sBias + H, sH2h, sH2l);
     barrier();
-    // L2: acc[0:D] = h2 W3^T  (f for rows recomputing stages)
-    if (tid == 0) {
-      const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(2));
-      const uint32_t idD = tc::idesc_bf16_f32(128, D);
-      for (int kk = 0; kk < H / 16; ++kk) {
-        const uint64_t db = tc::smem_desc(wa + kk * 256, 128, H * 16);
-        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2h) + kk * 256, 128, H * 16), db,
-                     idD, kk > 0);
-        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2l) + kk * 256, 128, H * 16), db,
-                     idD, true);
+
+    float fg[16];  // f = k_s (recompute) or g = J^T kbar_s (reverse)
+    if (!rev) {
+      // L2: acc[0:D] = h2 W3^T
+      if (tid == 0) {
+        const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(2));
+        const uint32_t idD = tc::idesc_bf16_f32(128, D);
+        for (int kk = 0; kk < H / 16; ++kk) {
+          const uint64_t db = tc::smem_desc(wa + kk * 256, 128, H * 16);
+          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2h) + kk * 256, 128, H * 16),
+                       db, idD, kk > 0);
+          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2l) + kk * 256, 128, H * 16),
+                       db, idD, true);
+        }
+        tc::mma_commit(&mbar_mma);
       }
-      tc::mma_commit(&mbar_mma);
-    }
-    wait_mma();
-    float f[16];
-    {
+      wait_mma();
       float v[16];
-      tc::tmem_ld16(tbase + lane_base + L::T_R + coff, v);
+      tc::tmem_ld16(tl + L::T_R + coff, v);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int r = 0; r < C; ++r) f[r] = v[r] + sBias[2 * H + coff + r];
-    }
-    barrier();
-    // B2: acc = kbar W3;  dW3^T += h2^T kbar  (split operands: hi*hi + lo*hi + hi*lo)
-    if (tid == 0) {
-      const uint32_t w3 = tc::smem_u32(sW + Cfg::W_off(2));
-      const uint32_t dh = tc::smem_u32(sD3h), dl = tc::smem_u32(sD3l);
-      const uint32_t idR = tc::idesc_bf16_f32(128, H, false, true);
-      for (int kk = 0; kk < D / 16; ++kk) {
-        const uint64_t db = tc::smem_desc_mn(w3 + kk * 2 * (H * 16), H * 16);
-        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, D * 16), db, idR, kk > 0);
-        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, D * 16), db, idR, true);
+      for (int r = 0; r < C; ++r) fg[r] = v[r] + sBias[2 * H + coff + r];
+    } else {
+      const bool acc0 = !dw_first;
+      // B2: acc = kbar W3;  dW3^T += h2^T kbar  (split: hi*hi + lo*hi + hi*lo)
+      if (tid == 0) {
+        const uint32_t w3 = tc::smem_u32(sW + Cfg::W_off(2));
+        const uint32_t dh = tc::smem_u32(sD3h), dl = tc::smem_u32(sD3l);
+        const uint32_t idR = tc::idesc_bf16_f32(128, H, false, true);
+        for (int kk = 0; kk < D / 16; ++kk) {
+          const uint64_t db = tc::smem_desc_mn(w3 + kk * 2 * (H * 16), H * 16);
+          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, D * 16), db, idR, kk > 0);
+          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, D * 16), db, idR, true);
+        }
+        const uint32_t idT = tc::idesc_bf16_f32(128, D, true, true);
+        const uint32_t hh = tc::smem_u32(sH2h), hl = tc::smem_u32(sH2l);
+        for (int kk = 0; kk < 128 / 16; ++kk) {
+          const uint64_t bh = tc::smem_desc_mn(dh + kk * 2 * (D * 16), D * 16);
+          const uint64_t bl = tc::smem_desc_mn(dl + kk * 2 * (D * 16), D * 16);
+          const uint64_t ah = tc::smem_desc_mn(hh + kk * 2 * (H * 16), H * 16);
+          const uint64_t al = tc::smem_desc_mn(hl + kk * 2 * (H * 16), H * 16);
+          tc::mma_bf16(tbase + L::T_D2, ah, bh, idT, acc0 || kk > 0);
+          tc::mma_bf16(tbase + L::T_D2, al, bh, idT, true);
+          tc::mma_bf16(tbase + L::T_D2, ah, bl, idT, true);
+        }
+        tc::mma_commit(&mbar_mma);
       }
-      const uint32_t idT = tc::idesc_bf16_f32(128, D, true, true);
-      const uint32_t hh = tc::smem_u32(sH2h), hl = tc::smem_u32(sH2l);
-      for (int kk = 0; kk < 128 / 16; ++kk) {
-        const uint64_t bh = tc::smem_desc_mn(dh + kk * 2 * (D * 16), D * 16);
-        const uint64_t bl = tc::smem_desc_mn(dl + kk * 2 * (D * 16), D * 16);
-        const uint64_t ah = tc::smem_desc_mn(hh + kk * 2 * (H * 16), H * 16);
-        const uint64_t al = tc::smem_desc_mn(hl + kk * 2 * (H * 16), H * 16);
-        tc::mma_bf16(tbase + L::T_D2, ah, bh, idT, !(first_round && kk == 0));
-        tc::mma_bf16(tbase + L::T_D2, al, bh, idT, true);
-        tc::mma_bf16(tbase + L::T_D2, ah, bl, idT, true);
+      wait_mma();
+      delta_epi(sH2h, sH2l);  // delta2 replaces h2
+      barrier();
+      // B1: acc = delta2 W2;  dW2 += delta2^T h1;  db2 += delta2^T 1
+      if (tid == 0) {
+        const uint32_t w2 = tc::smem_u32(sW + Cfg::W_off(1));
+        const uint32_t dh = tc::smem_u32(sH2h), dl = tc::smem_u32(sH2l);
+        const uint32_t idR = tc::idesc_bf16_f32(128, H, false, true);
+        for (int kk = 0; kk < H / 16; ++kk) {
+          const uint64_t db = tc::smem_desc_mn(w2 + kk * 2 * (H * 16), H * 16);
+          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, H * 16), db, idR, kk > 0);
+          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, H * 16), db, idR, true);
+        }
+        const uint32_t idT = tc::idesc_bf16_f32(128, H, true, true);
+        const uint32_t idB = tc::idesc_bf16_f32(128, 16, true, true);
+        const uint32_t hh = tc::smem_u32(sH1h), hl = tc::smem_u32(sH1l);
+        for (int kk = 0; kk < 128 / 16; ++kk) {
+          const uint64_t ah = tc::smem_desc_mn(dh + kk * 2 * (H * 16), H * 16);
+          const uint64_t al = tc::smem_desc_mn(dl + kk * 2 * (H * 16), H * 16);
+          const uint64_t bh = tc::smem_desc_mn(hh + kk * 2 * (H * 16), H * 16);
+          const uint64_t bl = tc::smem_desc_mn(hl + kk * 2 * (H * 16), H * 16);
+          const uint64_t b1 = tc::smem_desc_mn(tc::smem_u32(sOnes) + kk * 2 * (16 * 16), 16 * 16);
+          const bool acc = acc0 || kk > 0;
+          tc::mma_bf16(tbase + L::T_D1, ah, bh, idT, acc);
+          tc::mma_bf16(tbase + L::T_D1, al, bh, idT, true);
+          tc::mma_bf16(tbase + L::T_D1, ah, bl, idT, true);
+          tc::mma_bf16(tbase + L::T_DB, ah, b1, idB, acc);
+          tc::mma_bf16(tbase + L::T_DB, al, b1, idB, true);
+        }
+        tc::mma_commit(&mbar_mma);
       }
-      tc::mma_commit(&mbar_mma);
-    }
-    wait_mma();
-    delta_epi(sH2h, sH2l);  // delta2 replaces h2
-    barrier();
-    // B1: acc = delta2 W2;  dW2 += delta2^T h1;  db2 += delta2^T 1
-    if (tid == 0) {
-      const uint32_t w2 = tc::smem_u32(sW + Cfg::W_off(1));
-      const uint32_t dh = tc::smem_u32(sH2h), dl = tc::smem_u32(sH2l);
-      const uint32_t idR = tc::idesc_bf16_f32(128, H, false, true);
-      for (int kk = 0; kk < H / 16; ++kk) {
-        const uint64_t db = tc::smem_desc_mn(w2 + kk * 2 * (H * 16), H * 16);
-        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, H * 16), db, idR, kk > 0);
-        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, H * 16), db, idR, true);
+      wait_mma();
+      delta_epi(sH1h, sH1l);  // delta1 replaces h1
+      barrier();
+      // B0: acc = delta1 W1;  dW1 += delta1^T [X | 1]
+      if (tid == 0) {
+        const uint32_t w1 = tc::smem_u32(sW + Cfg::W_off(0));
+        const uint32_t dh = tc::smem_u32(sH1h), dl = tc::smem_u32(sH1l);
+        const uint32_t idR = tc::idesc_bf16_f32(128, K0, false, true);
+        for (int kk = 0; kk < H / 16; ++kk) {
+          const uint64_t db = tc::smem_desc_mn(w1 + kk * 2 * (K0 * 16), K0 * 16);
+          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, H * 16), db, idR, kk > 0);
+          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, H * 16), db, idR, true);
+        }
+        const uint32_t idT = tc::idesc_bf16_f32(128, K0, true, true);
+        const uint32_t xh = tc::smem_u32(sXh), xl = tc::smem_u32(sXl);
+        for (int kk = 0; kk < 128 / 16; ++kk) {
+          const uint64_t ah = tc::smem_desc_mn(dh + kk * 2 * (H * 16), H * 16);
+          const uint64_t al = tc::smem_desc_mn(dl + kk * 2 * (H * 16), H * 16);
+          const uint64_t bh = tc::smem_desc_mn(xh + kk * 2 * (K0 * 16), K0 * 16);
+          const uint64_t bl = tc::smem_desc_mn(xl + kk * 2 * (K0 * 16), K0 * 16);
+          const bool acc = acc0 || kk > 0;
+          tc::mma_bf16(tbase + L::T_D0, ah, bh, idT, acc);
+          tc::mma_bf16(tbase + L::T_D0, al, bh, idT, true);
+          tc::mma_bf16(tbase + L::T_D0, ah, bl, idT, true);
+        }
+        tc::mma_commit(&mbar_mma);
       }
-      const uint32_t idT = tc::idesc_bf16_f32(128, H, true, true);
-      const uint32_t idB = tc::idesc_bf16_f32(128, 16, true, true);
-      const uint32_t hh = tc::smem_u32(sH1h), hl = tc::smem_u32(sH1l);
-      for (int kk = 0; kk < 128 / 16; ++kk) {
-        const uint64_t ah = tc::smem_desc_mn(dh + kk * 2 * (H * 16), H * 16);
-        const uint64_t al = tc::smem_desc_mn(dl + kk * 2 * (H * 16), H * 16);
-        const uint64_t bh = tc::smem_desc_mn(hh + kk * 2 * (H * 16), H * 16);
-        const uint64_t bl = tc::smem_desc_mn(hl + kk * 2 * (H * 16), H * 16);
-        const uint64_t b1 = tc::smem_desc_mn(tc::smem_u32(sOnes) + kk * 2 * (16 * 16), 16 * 16);
-        const bool acc = !(first_round && kk == 0);
-        tc::mma_bf16(tbase + L::T_D1, ah, bh, idT, acc);
-        tc::mma_bf16(tbase + L::T_D1, al, bh, idT, true);
-        tc::mma_bf16(tbase + L::T_D1, ah, bl, idT, true);
-        tc::mma_bf16(tbase + L::T_DB, ah, b1, idB, acc);
-        tc::mma_bf16(tbase + L::T_DB, al, b1, idB, true);
-      }
-      tc::mma_commit(&mbar_mma);
-    }
-    wait_mma();
-    delta_epi(sH1h, sH1l);  // delta1 replaces h1
-    barrier();
-    // B0: acc = delta1 W1;  dW1 += delta1^T [X | 1]
-    if (tid == 0) {
-      const uint32_t w1 = tc::smem_u32(sW + Cfg::W_off(0));
-      const uint32_t dh = tc::smem_u32(sH1h), dl = tc::smem_u32(sH1l);
-      const uint32_t idR = tc::idesc_bf16_f32(128, K0, false, true);
-      for (int kk = 0; kk < H / 16; ++kk) {
-        const uint64_t db = tc::smem_desc_mn(w1 + kk * 2 * (K0 * 16), K0 * 16);
-        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, H * 16), db, idR, kk > 0);
-        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, H * 16), db, idR, true);
-      }
-      const uint32_t idT = tc::idesc_bf16_f32(128, K0, true, true);
-      const uint32_t xh = tc::smem_u32(sXh), xl = tc::smem_u32(sXl);
-      for (int kk = 0; kk < 128 / 16; ++kk) {
-        const uint64_t ah = tc::smem_desc_mn(dh + kk * 2 * (H * 16), H * 16);
-        const uint64_t al = tc::smem_desc_mn(dl + kk * 2 * (H * 16), H * 16);
-        const uint64_t bh = tc::smem_desc_mn(xh + kk * 2 * (K0 * 16), K0 * 16);
-        const uint64_t bl = tc::smem_desc_mn(xl + kk * 2 * (K0 * 16), K0 * 16);
-        const bool acc = !(first_round && kk == 0);
-        tc::mma_bf16(tbase + L::T_D0, ah, bh, idT, acc);
-        tc::mma_bf16(tbase + L::T_D0, al, bh, idT, true);
-        tc::mma_bf16(tbase + L::T_D0, ah, bl, idT, true);
-      }
-      tc::mma_commit(&mbar_mma);
-    }
-    wait_mma();
-    float g[16];
-    {
-      float v[16];
-      tc::tmem_ld16(tbase + lane_base + L::T_R + coff, v);
+      wait_mma();
+      tc::tmem_ld16(tl + L::T_R + coff, fg);
       tc::tmem_wait_ld();
-#pragma unroll
-      for (int r = 0; r < C; ++r) g[r] = v[r];
+      dw_first = false;
     }
-    first_round = false;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    if (abort_s) break;
 
-    // ---- consume
-    if (ph == AP_IDLE) continue;
-    const int i = inst;
-    if (ph < AP_C) {
-      // recomputed stage s: store k_s
+    // ---- consume (row-local)
+    if (!act) continue;
+    if (!rev) {
+      // k_s joins the stage sums of the later stages (the forward's order;
+      // stage 7 has no k_2 term)
 #pragma unroll
-      for (int r = 0; r < C; ++r) kslot[(s - 1) * D + r] = f[r];
-      if (s < 7) {
-        ph += 1;
-      } else {
-        // stage cotangents from ybar_{n+1} and the step's dense outputs
+      for (int j = 2; j < 7; ++j) {  // kb[j] = acc of stage j+1
+        if (j + 1 <= s || (j == 6 && s == 2)) continue;
+        const float c = dp_a(j + 1, s);
 #pragma unroll
-        for (int j = 0; j < 7; ++j)
-#pragma unroll
-          for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
-        dense7 = false;
-        const long long kt = tkey(tn), kn = tkey(tnext);
-        while (q >= 0) {
-          const double tq = a.te[(size_t)i * a.K + q];
-          const long long kq = tkey(tq);
-          if (!(kq > kt)) break;
-          if (a.gye) {
-            float gq[16], w[7];
-#pragma unroll
-            for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + coff + r];
-            if (kq == kn) {
-#pragma unroll
-              for (int j = 0; j < 7; ++j) w[j] = bw[j];
-            } else {
-              dense_weights<float>(float(tq - tn) / h, w);
-              dense7 = true;
-            }
-#pragma unroll
-            for (int j = 0; j < 7; ++j)
-#pragma unroll
-              for (int r = 0; r < C; ++r) kb[j][r] = madd(h * w[j], gq[r], kb[j][r]);
-#pragma unroll
-            for (int r = 0; r < C; ++r) yb[r] += gq[r];
-          }
-          q--;
-        }
-        ph = dense7 ? AP_C : AP_C + 1;  // reverse from stage 7 (or 6: kbar_7 = 0)
+        for (int r = 0; r < C; ++r) kb[j][r] = madd(c, fg[r], kb[j][r]);
       }
     } else {
-      // reversed stage s: g = J_f(Y_s)^T kbar_s
+      float kbs[16];
+      pick7(kb, s - 1, kbs);
 #pragma unroll
-      for (int r = 0; r < C; ++r) db3[r] += (s == 7) ? kb[6][r] : 0.0f;
+      for (int r = 0; r < C; ++r) db3[r] += kbs[r];
 #pragma unroll
-      for (int j = 0; j < 6; ++j)
+      for (int j = 0; j < 6; ++j) {  // kbar_j += h a_{s,j} g  (j < s)
+        if (j + 1 >= s) continue;
+        const float c = h * dp_a(s, j + 1);
 #pragma unroll
-        for (int r = 0; r < C; ++r)
-          if (j == s - 1) db3[r] += kb[j][r];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        if (j >= s - 1) break;
-        float c;
-        switch (s) {
-          case 2: c = float(Cc::a21); break;
-          case 3: c = j == 0 ? float(Cc::a31) : float(Cc::a32); break;
-          case 4: c = j == 0 ? float(Cc::a41) : j == 1 ? float(Cc::a42) : float(Cc::a43); break;
-          case 5: c = j == 0 ? float(Cc::a51) : j == 1 ? float(Cc::a52) : j == 2 ? float(Cc::a53)
-                                                                           : float(Cc::a54);
-                  break;
-          case 6: c = j == 0 ? float(Cc::a61) : j == 1 ? float(Cc::a62) : j == 2 ? float(Cc::a63)
-                    : j == 3 ? float(Cc::a64) : float(Cc::a65);
-                  break;
-          default: c = bw[j]; break;
-        }
-#pragma unroll
-        for (int r = 0; r < C; ++r) kb[j][r] = madd(h * c, g[r], kb[j][r]);
+        for (int r = 0; r < C; ++r) kb[j][r] = madd(c, fg[r], kb[j][r]);
       }
 #pragma unroll
-      for (int r = 0; r < C; ++r) yb[r] += g[r];
-      if (s > 1) {
-        ph += 1;
-      } else {
-        n -= 1;  // step n reversed
-        if (n >= 0) load_step(i);
+      for (int r = 0; r < C; ++r) yb[r] += fg[r];
+      if (s == 1) {  // step n reversed
+        n -= 1;
+        if (n >= 0) load_step(inst);
         else next_work(true);
       }
     }
@@ -1244,30 +1272,29 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   float* P = a.part + (size_t)blockIdx.x * L::P_FLOATS;
   tc::fence_after_sync();
   {
-    const uint32_t lb = tbase + lane_base;
     float v[16];
     // dW1 (and its t and bias columns): lane = output unit of layer 1
     for (int c = half * 32; c < (half ? K0 : 32); c += 16) {
-      tc::tmem_ld16(lb + L::T_D0 + c, v);
+      tc::tmem_ld16(tl + L::T_D0 + c, v);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < 16; ++j) P[L::P_W0 + row * K0 + c + j] = v[j];
+      for (int j = 0; j < 16; ++j) P[L::P_W0 + row * K0 + c + j] = dw_first ? 0.0f : v[j];
     }
 #pragma unroll
     for (int c = 0; c < HC; c += 16) {
       const int col = half * HC + c;
-      tc::tmem_ld16(lb + L::T_D1 + col, v);
+      tc::tmem_ld16(tl + L::T_D1 + col, v);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < 16; ++j) P[L::P_W1 + row * H + col + j] = v[j];
+      for (int j = 0; j < 16; ++j) P[L::P_W1 + row * H + col + j] = dw_first ? 0.0f : v[j];
     }
-    tc::tmem_ld16(lb + L::T_DB, v);
+    tc::tmem_ld16(tl + L::T_DB, v);
     tc::tmem_wait_ld();
-    if (half == 0) P[L::P_B1 + row] = v[0];
-    tc::tmem_ld16(lb + L::T_D2 + coff, v);
+    if (half == 0) P[L::P_B1 + row] = dw_first ? 0.0f : v[0];
+    tc::tmem_ld16(tl + L::T_D2 + coff, v);
     tc::tmem_wait_ld();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) P[L::P_W2T + row * D + coff + j] = v[j];
+    for (int j = 0; j < 16; ++j) P[L::P_W2T + row * D + coff + j] = dw_first ? 0.0f : v[j];
   }
   // db3: sum the rows' accumulators in a fixed order (reuses the h2 tile)
   float* sDb = reinterpret_cast<float*>(sH2h);
@@ -1425,7 +1452,6 @@ size_t mlp_adjoint_scratch_bytes(int B, int num_sms) {
   using L = MlpAdjLayout<Cfg32s>;
   const long long grid = std::min<long long>((B + 127) / 128, num_sms);
   return align256(256) + align256((size_t)Cfg32s::WIMG_BYTES) +
-         align256((size_t)grid * 128 * 7 * Cfg32s::D * 4) +
          align256((size_t)grid * L::P_FLOATS * 4);
 }
 
@@ -1460,8 +1486,6 @@ tode_err mlp_adjoint(const AdjReq& r) {
   unsigned char* img = (unsigned char*)p;
   a.wimg = img;
   p += align256((size_t)Cfg::WIMG_BYTES);
-  a.kscr = (float*)p;
-  p += align256((size_t)grid * 128 * 7 * Cfg::D * 4);
   a.part = (float*)p;
   a.overflow = r.overflow;
   for (int l = 0; l < 3; ++l) {

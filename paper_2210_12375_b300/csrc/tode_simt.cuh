@@ -132,7 +132,10 @@ __global__ void k_plain_step(SolveArgs<T> a) {
   plain_load<T, R, G>(a, i, s);
   const int acc_before = s.n_acc;
   const bool run = inst_attempt<Field, T, R, G>(F, s, a.o, i, a.D, inst_out(a, i), a.trace);
-  if (run && s.n_acc != acc_before) tape_store<T, R, G>(a.tape, i, s);
+  if (s.n_acc != acc_before) {
+    tape_store_hacc<T, R, G>(a.tape, i, s);
+    if (run) tape_store<T, R, G>(a.tape, i, s);
+  }
   plain_store<T, R, G>(a, i, s);
   if (!run) {
     inst_finalize<T, R, G>(s, a.o, i, a.D, a.yf, a.n_acc, a.n_rej, a.n_fe, a.status, a.trace);
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
     }
     const int acc_before = s.n_acc;
     const bool run = inst_attempt<Field, T, R, G>(F, s, a.o, i, a.D, inst_out(a, i), a.trace);
+    if (s.n_acc != acc_before) tape_store_hacc<T, R, G>(a.tape, i, s);
     if (run) {
       if (s.n_acc != acc_before) tape_store<T, R, G>(a.tape, i, s);
     } else {
@@ -197,6 +201,7 @@ template <typename T> TapeDev<T> make_tape(const tode_tape* tp, int B, int D) {
   d.h = (T*)tp->h;
   d.err_prev = (T*)tp->err_prev;
   d.flags = tp->flags;
+  d.h_acc = (T*)tp->h_acc;
   return d;
 }
 

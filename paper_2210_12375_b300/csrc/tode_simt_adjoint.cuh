@@ -8,10 +8,12 @@
 //                  kbar_j += h a_ij g_i  (j < i)
 //   ybar_n = ybar_{n+1} + sum_tau ybar_tau + sum_i g_i.
 // Step-start states come from the checkpoint tape: slot j holds the solver
-// state (including its FSAL stage) at the start of accepted step j*stride;
-// the segment up to the next slot is re-run with the forward routine (a
-// bit-identical mesh), its step-start states parked in scratch, then
-// reversed.
+// state (including its FSAL stage) at the start of accepted step j*stride.
+// With one slot per accepted step and the accepted step sizes recorded, each
+// step is reversed straight from its slot.  Otherwise the segment up to the
+// next slot is re-run with the forward routine (a bit-identical mesh), its
+// step-start states parked in scratch, then reversed.  Either way the first
+// stage derivative is the forward's own FSAL value k1.
 #pragma once
 #include "tode_simt.cuh"
 
@@ -107,6 +109,7 @@ template <typename T> struct AdjArgs {
   int32_t* overflow;
   int32_t* counter;
   T* sy;        // [stride][B][D]
+  T* sk1;       // [stride][B][D]
   double* st;   // [stride][B]
   T* sh;        // [stride][B]
 };
@@ -115,14 +118,16 @@ template <typename T> struct AdjArgs {
 // q: cursor over the instance's evaluation points, from the last backwards.
 template <class AF, typename T, int R, int G>
 __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, int D, double t,
-                                             T h, double t_next, const T (&y)[R], T (&yb)[R],
-                                             int& q) {
+                                             T h, double t_next, const T (&y)[R],
+                                             const T (&k1)[R], T (&yb)[R], int& q) {
   using C = DP5;
   T Y[7][R], k[7][R];
   const double hd = (double)h;
 #pragma unroll
-  for (int r = 0; r < R; ++r) Y[0][r] = y[r];
-  F.eval(t, Y[0], k[0]);
+  for (int r = 0; r < R; ++r) {
+    Y[0][r] = y[r];
+    k[0][r] = k1[r];
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) Y[1][r] = madd(h, T(C::a21) * k[0][r], y[r]);
   F.eval(t + C::c2 * hd, Y[1], k[1]);
@@ -260,7 +265,21 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs<T> a) {
     for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
     int q = a.K - 1;
     const double t1 = a.t1[i];
-    for (int j = nseg - 1; j >= 0 && !bad; --j) {
+    const bool direct = m == 1 && a.tape.h_acc != nullptr;
+    for (int n = N - 1; direct && n >= 0 && !bad; --n) {
+      const size_t o = (size_t)n * a.B + i;
+      T y[R], k1[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        y[r] = a.tape.y[o * D + g * R + r];
+        k1[r] = a.tape.k1[o * D + g * R + r];
+      }
+      const double t = a.tape.t[o];
+      const T h = a.tape.h_acc[o];
+      const double t_next = (n == N - 1) ? t1 : t + (double)h;
+      reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, yb, q);
+    }
+    for (int j = nseg - 1; !direct && j >= 0 && !bad; --j) {
       const int n0 = j * m;
       const int n1 = (n0 + m < N) ? n0 + m : N;
       // restore the slot and re-run the forward over the segment
@@ -291,15 +310,21 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs<T> a) {
       while (s.n_acc < n1 && s.status == ST_RUNNING) {
         const int before = s.n_acc;
         const double tb = s.t;
-        T ys[R];
+        T ys[R], ks[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) ys[r] = s.y[r];
+        for (int r = 0; r < R; ++r) {
+          ys[r] = s.y[r];
+          ks[r] = s.k1[r];
+        }
         inst_attempt<AF, T, R, G>(F, s, ro, i, D, no_out, no_trace);
         const T hb = s.h_last;
         if (s.n_acc != before) {
           const size_t p = (size_t)(before - n0) * a.B + i;
 #pragma unroll
-          for (int r = 0; r < R; ++r) a.sy[p * D + g * R + r] = ys[r];
+          for (int r = 0; r < R; ++r) {
+            a.sy[p * D + g * R + r] = ys[r];
+            a.sk1[p * D + g * R + r] = ks[r];
+          }
           if (g == 0) {
             a.st[p] = tb;
             a.sh[p] = hb;
@@ -313,13 +338,16 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs<T> a) {
       if constexpr (G > 1) __syncwarp(Grp<G>::mask());
       for (int n = n1 - 1; n >= n0; --n) {
         const size_t p = (size_t)(n - n0) * a.B + i;
-        T y[R];
+        T y[R], k1[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) y[r] = a.sy[p * D + g * R + r];
+        for (int r = 0; r < R; ++r) {
+          y[r] = a.sy[p * D + g * R + r];
+          k1[r] = a.sk1[p * D + g * R + r];
+        }
         const double t = a.st[p];
         const T h = a.sh[p];
         const double t_next = (n == N - 1) ? t1 : t + (double)h;
-        reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, yb, q);
+        reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, yb, q);
       }
       if constexpr (G > 1) __syncwarp(Grp<G>::mask());
     }
@@ -368,6 +396,8 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   p += align256(256);
   const int m = r.tape->stride;
   a.sy = (T*)p;
+  p += align256((size_t)m * r.B * r.D * sizeof(T));
+  a.sk1 = (T*)p;
   p += align256((size_t)m * r.B * r.D * sizeof(T));
   a.st = (double*)p;
   p += align256((size_t)m * r.B * 8);

@@ -120,3 +120,29 @@ def test_adjoint_recompute_matches_forward_mesh_for_every_group(group):
     ref = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"],
                          a["gye"], a["gyf"])
     assert _rel(a["gy0"], ref["gy0"]) <= 1e-4
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_adjoint_direct_from_tape_equals_rerun(cfg):
+    """With one slot per accepted step the adjoint reverses straight from the
+    tape (accepted step sizes recorded); without the recorded sizes it
+    re-runs each step's attempts from its slot.  Same bits."""
+    import dataclasses
+    w = make(cfg, B=300)
+    dtype = torch.float64 if cfg == 1 else torch.float32
+    B, D = w["y0"].shape
+    probe = gpu_solve(w, dtype, "fused")
+    tape = tode.TapeBuffers.allocate(B, D, dtype, int(probe["n_acc"].max()), 1, "cuda")
+    g = gpu_solve(w, dtype, "fused", tape=tape)
+    dev = g["_dev"]
+    rng = np.random.default_rng(3)
+    gye = torch.tensor(rng.standard_normal(g["y_eval"].shape), dtype=dtype, device="cuda")
+    gyf = torch.tensor(rng.standard_normal(g["y_final"].shape), dtype=dtype, device="cuda")
+    outs = []
+    for tp in (tape, dataclasses.replace(tape, h_acc=None)):
+        gy0, gp, ovf = tode.adjoint(dev["field"], dev["t0"], dev["t1"], dev["te"], g["_sol"], tp,
+                                    gye, gyf, rtol=w["rtol"], atol=w["atol"])
+        torch.cuda.synchronize()
+        assert int(ovf.item()) == 0
+        outs.append((gy0.cpu().numpy(), gp.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
