@@ -7,6 +7,7 @@ this package only marshals torch tensors into it.
 """
 from . import _abi  # noqa: F401
 from .api import MLP, Linear, Solution, TapeBuffers, VdP, adjoint, make_options, solve  # noqa: F401
+from .autograd import odeint_adjoint  # noqa: F401
 
 __all__ = ["VdP", "Linear", "MLP", "solve", "adjoint", "TapeBuffers", "Solution",
-           "make_options"]
+           "make_options", "odeint_adjoint"]

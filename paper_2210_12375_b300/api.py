@@ -33,6 +33,12 @@ class VdP:
     def params(self):
         return self.mu
 
+    def tensors(self):
+        return [self.mu]
+
+    def with_tensors(self, ts):
+        return VdP(ts[0])
+
 
 class Linear:
     """y' = A_i y; A: [B, D, D] row-major."""
@@ -50,10 +56,18 @@ class Linear:
     def params(self):
         return self.A
 
+    def tensors(self):
+        return [self.A]
+
+    def with_tensors(self, ts):
+        return Linear(ts[0])
+
 
 class MLP:
-    """f(t, y) = W_L tanh(... tanh(W_1 [y; t] + b_1) ...) + b_L with BF16
-    weights W_l [out, in] and float biases b_l [out]."""
+    """f(t, y) = W_L tanh(... tanh(W_1 [y; t] + b_1) ...) + b_L with weights
+    W_l [out, in] and float biases b_l [out].  The field computes with BF16
+    weights: float weights are rounded to BF16 for each call (their gradients
+    from the adjoint are then float, with respect to the rounded values)."""
     kind = _abi.TODE_MLP
 
     def __init__(self, weights, biases, split: bool = False):
@@ -70,7 +84,10 @@ class MLP:
         f.kind, f.B, f.D = self.kind, B, D
         wd = self.widths
         wa = (C.c_int * len(wd))(*wd)
-        Wp = (C.c_void_p * len(self.W))(*[w.data_ptr() for w in self.W])
+        Wb = [w if w.dtype == torch.bfloat16 else w.detach().to(torch.bfloat16).contiguous()
+              for w in self.W]
+        keep += Wb
+        Wp = (C.c_void_p * len(self.W))(*[w.data_ptr() for w in Wb])
         bp = (C.c_void_p * len(self.b))(*[b.data_ptr() for b in self.b])
         keep += [wa, Wp, bp]
         f.n_layers = len(self.W)
@@ -81,6 +98,13 @@ class MLP:
 
     def params(self):
         return None
+
+    def tensors(self):
+        return self.W + self.b
+
+    def with_tensors(self, ts):
+        n = len(self.W)
+        return MLP(list(ts[:n]), list(ts[n:]), split=self.split)
 
 
 # ------------------------------------------------------------------ options

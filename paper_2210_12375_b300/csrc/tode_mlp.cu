@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 
 namespace tode {
 
@@ -1359,6 +1360,19 @@ __global__ void k_mlp_grad_reduce(const float* part, int grid, float* gW0, float
 }
 
 // ---------------------------------------------------------------- host side
+// Opts a kernel into its dynamic shared memory once per device: the
+// attribute is host-side state, and doing it once keeps later calls (for
+// instance inside a CUDA-graph capture) free of it.
+static tode_err smem_optin(const void* fn, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  TODE_CUDA_TRY(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load() & bit) return TODE_OK;
+  TODE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit);
+  return TODE_OK;
+}
+
 using Cfg32 = MlpCfg<32, 128, 3, false>;
 using Cfg32s = MlpCfg<32, 128, 3, true>;
 
@@ -1433,8 +1447,11 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   }
   TODE_CUDA_TRY(cudaGetLastError());
   TODE_CUDA_TRY(cudaMemsetAsync(r.ws, 0, 256, st));  // queue counter and error flag
-  TODE_CUDA_TRY(cudaFuncSetAttribute(k_mlp_fused<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     Cfg::S_END));
+  {
+    static std::atomic<uint64_t> done{0};
+    const tode_err e = smem_optin((const void*)k_mlp_fused<Cfg>, Cfg::S_END, done);
+    if (e != TODE_OK) return e;
+  }
   long long grid = (r.B + 127) / 128;
   if (grid > r.num_sms) grid = r.num_sms;
   k_mlp_fused<Cfg><<<(int)grid, 256, Cfg::S_END, st>>>(a);
@@ -1495,8 +1512,11 @@ tode_err mlp_adjoint(const AdjReq& r) {
   }
   TODE_CUDA_TRY(cudaGetLastError());
   TODE_CUDA_TRY(cudaMemsetAsync(r.scratch, 0, 256, st));
-  TODE_CUDA_TRY(cudaFuncSetAttribute(k_mlp_adjoint<Cfg>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::S_END));
+  {
+    static std::atomic<uint64_t> done{0};
+    const tode_err e = smem_optin((const void*)k_mlp_adjoint<Cfg>, L::S_END, done);
+    if (e != TODE_OK) return e;
+  }
   k_mlp_adjoint<Cfg><<<(int)grid, 256, L::S_END, st>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   const int total = Cfg::H * (Cfg::D + 1) + Cfg::H + Cfg::H * Cfg::H + Cfg::H +

@@ -1,0 +1,97 @@
+"""odeint_adjoint: the torch.autograd.Function around the fused solve and
+the discrete adjoint (App. A).  Gradients of L = sum y(t_eval)^2 + <d, y(t1)>
+against the FP64 oracle adjoint on the GPU's mesh, the checkpoint budget
+(recomputed segments give the same bits), and the MLP's weight gradients."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2210_12375_b300 as tode
+from gpu_helpers import device_field, gpu_solve, make
+from oracle.oracle import mesh_from_trace
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _inputs(w, dtype):
+    dev = "cuda"
+    y0 = torch.tensor(w["y0"], dtype=dtype, device=dev, requires_grad=True)
+    t0 = torch.tensor(w["t0"], dtype=torch.float64, device=dev)
+    t1 = torch.tensor(w["t1"], dtype=torch.float64, device=dev)
+    te = torch.tensor(w["t_eval"], dtype=torch.float64, device=dev)
+    return y0, t0, t1, te
+
+
+def _loss_and_grads(w, dtype, field, **kw):
+    y0, t0, t1, te = _inputs(w, dtype)
+    ts = [t.requires_grad_(True) for t in field.tensors()]
+    ye, yf, n_acc, n_rej, status = tode.odeint_adjoint(field, y0, t0, t1, te, rtol=w["rtol"],
+                                                       atol=w["atol"], **kw)
+    d = torch.linspace(-1.0, 1.0, yf.shape[1], dtype=yf.dtype, device=yf.device)
+    loss = (ye ** 2).sum() + (yf * d).sum()
+    grads = torch.autograd.grad(loss, [y0] + ts)
+    return ye.detach(), yf.detach(), n_acc, [g.double().cpu().numpy() for g in grads]
+
+
+def test_autograd_vdp_f64_vs_oracle_adjoint():
+    w = make(1, B=96)
+    field = device_field(w, torch.float64)
+    ye, yf, n_acc, (gy0, gmu) = _loss_and_grads(w, torch.float64, field)
+    probe = gpu_solve(w, torch.float64, "fused", trace_cap=4000)
+    assert np.array_equal(probe["n_acc"], n_acc.cpu().numpy())
+    mt, mh, mn = mesh_from_trace(probe)
+    D = w["y0"].shape[1]
+    gye = 2.0 * ye.cpu().numpy()
+    gyf = np.tile(np.linspace(-1.0, 1.0, D), (w["B"], 1))
+    ref = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"], gye, gyf)
+    assert _rel(gy0, ref["gy0"]) <= 1e-10
+    assert _rel(gmu, ref["gmu"]) <= 1e-10
+
+
+def test_autograd_budget_recompute_is_bitwise():
+    """A tape budget below one slot per step (segments recomputed) gives the
+    same gradients as a full tape."""
+    w = make(2, B=512)
+    field = device_field(w, torch.float32)
+    full = _loss_and_grads(w, torch.float32, field)
+    per_slot = tode.TapeBuffers.bytes_per_slot(512, 16, 4)
+    small = _loss_and_grads(w, torch.float32, field, hbm_budget_bytes=per_slot * 5, slots_hint=2)
+    for a, b in zip(full[3], small[3]):
+        assert np.array_equal(a, b)
+
+
+def test_autograd_mlp_matches_direct_adjoint_call():
+    """Float master weights: the autograd path returns exactly the direct
+    adjoint's float gradients (taken at the BF16-rounded weights)."""
+    w = dict(make(4, B=300), split=True)
+    f = w["field"]
+    W32 = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in f["W"]]
+    b32 = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in f["b"]]
+    field = tode.MLP(W32, b32, split=True)
+    ye, yf, n_acc, grads = _loss_and_grads(w, torch.float32, field)
+    # the same through solve + adjoint
+    g = gpu_solve(w, torch.float32, "fused")
+    B, D = w["y0"].shape
+    tape = tode.TapeBuffers.allocate(B, D, torch.float32, int(g["n_acc"].max()), 1, "cuda")
+    y0, t0, t1, te = _inputs(w, torch.float32)
+    sol = tode.solve(field, y0.detach(), t0, t1, te, tape=tape, rtol=w["rtol"], atol=w["atol"])
+    assert torch.equal(sol.y_eval, ye)
+    d = torch.linspace(-1.0, 1.0, D, dtype=torch.float32, device="cuda")
+    gy0, (gW, gb), ovf = tode.adjoint(field, t0, t1, te, sol, tape, 2.0 * sol.y_eval,
+                                      d.expand(B, D).contiguous(), rtol=w["rtol"],
+                                      atol=w["atol"])
+    ref = [gy0] + gW + gb
+    for a, b in zip(grads, ref):
+        assert np.array_equal(a, b.double().cpu().numpy())
+
+
+def test_autograd_mlp_over_budget_raises():
+    w = dict(make(4, B=128), split=True)
+    field = device_field(w, torch.float32)
+    with pytest.raises(RuntimeError):
+        _loss_and_grads(w, torch.float32, field, hbm_budget_bytes=1, slots_hint=1)
