@@ -188,7 +188,7 @@ def run_tode(args):
     n_att = int((probe.n_acc.long() + probe.n_rej.long()).sum().item())
     n_acc_total = int(probe.n_acc.long().sum().item())
     n_acc_max = int(probe.n_acc.max().item())
-    # every field has the adjoint; the MLP field has no plain form yet
+    # every field has the adjoint and both forms
     with_adjoint = True
     tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev)
 
@@ -202,7 +202,7 @@ def run_tode(args):
 
     # matched error: both forms against the exact solution of the same batch
     sol_f = fwd("fused")
-    sol_p = fwd("plain") if not mlp else None
+    sol_p = fwd("plain")
     torch.cuda.synchronize()
     same = bool(torch.equal(sol_f.y_eval, sol_p.y_eval)) if sol_p is not None else None
     err = None
@@ -269,9 +269,8 @@ def run_tode(args):
         k_adj_ms = kernel_ms(nk, True) if with_adjoint else None
     clocks = clk.summary()
     ms_fused_fwd, _ = timed("fused", nk, False)
-    if not mlp:
-        ms_plain, _ = timed("plain", args.plain_steps, True)
-        ms_plain_fwd, _ = timed("plain", args.plain_steps, False)
+    ms_plain, _ = timed("plain", args.plain_steps, True)
+    ms_plain_fwd, _ = timed("plain", args.plain_steps, False)
 
     per_step = ms_fused / args.steps
     value = world * n_att / (per_step * 1e-3)
@@ -383,13 +382,12 @@ def run_tode(args):
             "adjoint_kernel_ms": k_adj_ms,
             "accepted_steps_per_pass": n_acc_total,
         })
-    if not mlp:
-        breakdown.update({
-            "plain_fwd_adj": world * n_att / (ms_plain / args.plain_steps * 1e-3),
-            "plain_fwd": world * n_att / (ms_plain_fwd / args.plain_steps * 1e-3),
-            "fused_over_plain_fwd_adj": (ms_plain / args.plain_steps) / per_step,
-            "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
-        })
+    breakdown.update({
+        "plain_fwd_adj": world * n_att / (ms_plain / args.plain_steps * 1e-3),
+        "plain_fwd": world * n_att / (ms_plain_fwd / args.plain_steps * 1e-3),
+        "fused_over_plain_fwd_adj": (ms_plain / args.plain_steps) / per_step,
+        "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
+    })
     # our kernels per timed step: fused forward (+3 weight-image builds for the
     # MLP) and the adjoint (+3 image builds and the ordered dW reduction)
     gpu_launches = 4 + 5 if mlp else 2

@@ -124,7 +124,7 @@ void tode_default_options(tode_options* o) {
 
 size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int K) {
   if (K < 0 || !opts_ok(o) || field_ok(f, o) != TODE_OK) return 0;
-  if (f->kind == TODE_MLP) return mlp_workspace_bytes(f);
+  if (f->kind == TODE_MLP) return mlp_workspace_bytes(f, o);
   return simt_workspace_bytes(f->B, f->D, state_size(o), o->form);
 }
 

@@ -59,7 +59,22 @@ struct MlpArgs {
   float* tp_k1;
   double* tp_t;
   float* tp_h;
+  // plain form: solver state between launches, and the "some instance is
+  // still running" flag the host polls
+  float* wy;
+  float* wylo;
+  float* wk1;
+  double* wt;
+  float* wh;
+  float* wep;
+  int32_t* wcur;
+  int32_t* wfl;
+  int32_t* active;
 };
+
+// Kernel modes of the MLP solver body: the fused persistent form, and the
+// plain form's initialising launch and per-attempt launch.
+enum : int { MLP_FUSED = 0, MLP_PLAIN_INIT = 1, MLP_PLAIN_STEP = 2 };
 
 template <int D_, int H_, int NL_, bool SPLIT_> struct MlpCfg {
   static constexpr int D = D_, H = H_, NL = NL_;
@@ -141,8 +156,14 @@ struct MlpRow {
   bool last;
 };
 
-template <class Cfg>
-__global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
+// The solver body shared by the fused form and the plain form.  Fused: a
+// persistent grid, each row takes instances from a global counter and
+// integrates them to their end.  Plain: tile c of 128 instances belongs to
+// CTA c mod grid; the initialising launch runs the starting-step rounds, every
+// later launch one attempt (six stage rounds) per running instance, with the
+// state parked in the workspace in between.
+template <class Cfg, int MODE>
+__device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   constexpr int D = Cfg::D, H = Cfg::H, NL = Cfg::NL, K0 = Cfg::K0, C = Cfg::C;
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar_mma, mbar_w;
@@ -213,89 +234,166 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
 #pragma unroll
     for (int j = 0; j < 7; ++j) k[j][r] = 0.0f;
   }
-  bool need_grab = true;
+  bool need_grab = MODE == MLP_FUSED;  // fused: this row takes the next instance
+  bool need_load = MODE != MLP_FUSED;  // plain: this row loads its instance of the tile
+  int tile = blockIdx.x;
 
-  while (true) {
-    // ---- hand out instances to rows that need one (one atomic per row)
-    if (need_grab && half == 0) sNxt[row] = atomicAdd(a.counter, 1);
-    __syncthreads();
-    if (need_grab) {
-      need_grab = false;
-      const int i = sNxt[row];
-      if (i >= a.B) {
-        s.phase = PH_IDLE;
-        s.inst = -1;
+  // load and validate instance i, write its points at t0 and pick the phase
+  auto start_instance = [&](const int i) {
+    // load and validate the instance (Sec. 3: per-instance bounds / points)
+    s.inst = i;
+    s.t0 = a.t0[i];
+    s.t1 = a.t1[i];
+    s.t = s.t0;
+    s.rtol = (float)(a.rtol_b ? a.rtol_b[i] : a.rtol);
+    s.atol = (float)(a.atol_b ? a.atol_b[i] : a.atol);
+    s.n_acc = s.n_rej = 0;
+    s.cursor = 0;
+    s.flags = 0;
+    s.err_prev = 1.0f;
+    s.h = s.h0h = 0.0f;
+    s.last = false;
+    s.status = ST_RUNNING;
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      y[r] = a.y0[(size_t)i * D + coff + r];
+      ylo[r] = 0.0f;
+    }
+    const double* te = a.te + (size_t)i * a.K;
+    bool ok = tfinite(s.t0) && tfinite(s.t1) && !(s.t1 < s.t0);
+    const long long k0 = tkey(s.t0), k1 = tkey(s.t1);
+    long long kprev = k0;
+    for (int q = 0; q < a.K && ok; ++q) {
+      const long long kv = tkey(te[q]);
+      ok = tfinite(te[q]) && kv >= kprev && kv <= k1;
+      kprev = kv;
+    }
+    float* ye = a.ye + (size_t)i * a.K * D + coff;
+    bool done = false;
+    if (!ok) {
+      s.status = ST_INVALID;
+      for (int q = 0; q < a.K; ++q)
+#pragma unroll
+        for (int r = 0; r < C; ++r) ye[(size_t)q * D + r] = nan_(0.0f);
+      done = true;
+    } else {
+      while (s.cursor < a.K && tkey(te[s.cursor]) == k0) {
+#pragma unroll
+        for (int r = 0; r < C; ++r) ye[(size_t)s.cursor * D + r] = y[r];
+        s.cursor++;
+      }
+      if (k1 == k0) {
+        s.status = ST_SUCCESS;
+        done = true;
       } else {
-        // load and validate the instance (Sec. 3: per-instance bounds / points)
-        s.inst = i;
-        s.t0 = a.t0[i];
-        s.t1 = a.t1[i];
-        s.t = s.t0;
-        s.rtol = (float)(a.rtol_b ? a.rtol_b[i] : a.rtol);
-        s.atol = (float)(a.atol_b ? a.atol_b[i] : a.atol);
-        s.n_acc = s.n_rej = 0;
-        s.cursor = 0;
-        s.flags = 0;
-        s.err_prev = 1.0f;
-        s.h = s.h0h = 0.0f;
-        s.last = false;
-        s.status = ST_RUNNING;
-#pragma unroll
-        for (int r = 0; r < C; ++r) {
-          y[r] = a.y0[(size_t)i * D + coff + r];
-          ylo[r] = 0.0f;
-        }
-        const double* te = a.te + (size_t)i * a.K;
-        bool ok = tfinite(s.t0) && tfinite(s.t1) && !(s.t1 < s.t0);
-        const long long k0 = tkey(s.t0), k1 = tkey(s.t1);
-        long long kprev = k0;
-        for (int q = 0; q < a.K && ok; ++q) {
-          const long long kv = tkey(te[q]);
-          ok = tfinite(te[q]) && kv >= kprev && kv <= k1;
-          kprev = kv;
-        }
-        float* ye = a.ye + (size_t)i * a.K * D + coff;
-        bool done = false;
-        if (!ok) {
-          s.status = ST_INVALID;
-          for (int q = 0; q < a.K; ++q)
-#pragma unroll
-            for (int r = 0; r < C; ++r) ye[(size_t)q * D + r] = nan_(0.0f);
-          done = true;
-        } else {
-          while (s.cursor < a.K && tkey(te[s.cursor]) == k0) {
-#pragma unroll
-            for (int r = 0; r < C; ++r) ye[(size_t)s.cursor * D + r] = y[r];
-            s.cursor++;
-          }
-          if (k1 == k0) {
-            s.status = ST_SUCCESS;
-            done = true;
-          } else {
-            s.rem = __double2float_rd(s.t1 - s.t0);
-            s.hmin = (float)(1e-14 * tmax(fabs(s.t0), fabs(s.t1)));
-            s.phase = PH_INIT0;
-          }
-        }
-        if (done) {
-          // finalize immediately, take another instance next round
-#pragma unroll
-          for (int r = 0; r < C; ++r)
-            a.yf[(size_t)i * D + coff + r] = s.status == ST_INVALID ? nan_(0.0f) : y[r];
-          if (half == 0) {
-            a.n_acc[i] = a.n_rej[i] = a.n_fe[i] = 0;
-            a.status[i] = s.status;
-            if (a.trace.cap > 0) a.trace.len[i] = 0;
-          }
-          s.phase = PH_IDLE;
-          need_grab = true;
-        }
+        s.rem = __double2float_rd(s.t1 - s.t0);
+        s.hmin = (float)(1e-14 * tmax(fabs(s.t0), fabs(s.t1)));
+        s.phase = PH_INIT0;
       }
     }
-    // all rows idle and the queue exhausted -> done
+    if (done) {
+      // finalize immediately, take another instance next round
+#pragma unroll
+      for (int r = 0; r < C; ++r)
+        a.yf[(size_t)i * D + coff + r] = s.status == ST_INVALID ? nan_(0.0f) : y[r];
+      if (half == 0) {
+        a.n_acc[i] = a.n_rej[i] = a.n_fe[i] = 0;
+        a.status[i] = s.status;
+        if (a.trace.cap > 0) a.trace.len[i] = 0;
+      }
+      s.phase = PH_IDLE;
+      if (MODE == MLP_FUSED) need_grab = true;
+    }
+  };
+  // plain form: park the row's solver state for the next launch
+  auto park = [&]() {
+    const int i = s.inst;
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      const size_t o = (size_t)i * D + coff + r;
+      a.wy[o] = y[r];
+      a.wylo[o] = ylo[r];
+      a.wk1[o] = k[0][r];
+    }
+    if (half == 0) {
+      a.wt[i] = s.t;
+      a.wh[i] = s.h;
+      a.wep[i] = s.err_prev;
+      a.wcur[i] = s.cursor;
+      a.wfl[i] = s.flags;
+      a.n_acc[i] = s.n_acc;
+      a.n_rej[i] = s.n_rej;
+      a.status[i] = ST_RUNNING;
+      *a.active = 1;
+    }
+    s.phase = PH_IDLE;
+  };
+  // plain form: resume a parked instance at the start of its next attempt
+  auto resume = [&](const int i) {
+    s.inst = i;
+    s.t0 = a.t0[i];
+    s.t1 = a.t1[i];
+    s.t = a.wt[i];
+    s.rtol = (float)(a.rtol_b ? a.rtol_b[i] : a.rtol);
+    s.atol = (float)(a.atol_b ? a.atol_b[i] : a.atol);
+    s.n_acc = a.n_acc[i];
+    s.n_rej = a.n_rej[i];
+    s.cursor = a.wcur[i];
+    s.flags = a.wfl[i];
+    s.err_prev = a.wep[i];
+    s.h = a.wh[i];
+    s.h0h = 0.0f;
+    s.last = false;
+    s.status = ST_RUNNING;
+    s.rem = __double2float_rd(s.t1 - s.t);  // functions of (t, t0, t1), as in the fused form
+    s.hmin = (float)(1e-14 * tmax(fabs(s.t0), fabs(s.t1)));
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      const size_t o = (size_t)i * D + coff + r;
+      y[r] = a.wy[o];
+      ylo[r] = a.wylo[o];
+      k[0][r] = a.wk1[o];
+    }
+    s.phase = PH_STAGE;
+  };
+
+  while (true) {
+    if (MODE == MLP_FUSED) {
+      // ---- hand out instances to rows that need one (one atomic per row)
+      if (need_grab && half == 0) sNxt[row] = atomicAdd(a.counter, 1);
+      __syncthreads();
+      if (need_grab) {
+        need_grab = false;
+        const int i = sNxt[row];
+        if (i >= a.B) {
+          s.phase = PH_IDLE;
+          s.inst = -1;
+        } else {
+          start_instance(i);
+        }
+      }
+    } else if (need_load) {
+      need_load = false;
+      const int i = tile * 128 + row;
+      s.phase = PH_IDLE;
+      s.inst = -1;
+      if (i < a.B) {
+        if (MODE == MLP_PLAIN_INIT) start_instance(i);
+        else if (a.status[i] == ST_RUNNING) resume(i);
+      }
+    }
+    // all rows idle and the queue exhausted (fused) or the tile done (plain)
     const bool any_work = __syncthreads_or(s.phase != PH_IDLE || need_grab) != 0;
-    if (!any_work || abort_s) break;
-    if (__syncthreads_or(need_grab && s.phase == PH_IDLE && s.inst >= 0) != 0) {
+    if (abort_s) break;
+    if (!any_work) {
+      if (MODE == MLP_FUSED) break;
+      tile += gridDim.x;
+      if ((long long)tile * 128 >= a.B) break;
+      need_load = true;
+      continue;
+    }
+    if (MODE == MLP_FUSED &&
+        __syncthreads_or(need_grab && s.phase == PH_IDLE && s.inst >= 0) != 0) {
       // some row finished without work this round: refill first
       continue;
     }
@@ -507,6 +605,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
       if (a.o.h0 > 0.0) {
         s.h = (float)a.o.h0;
         s.phase = PH_STAGE;
+        if (MODE == MLP_PLAIN_INIT) park();
       } else {
         // starting step, HNW Sec. II.4
         const float d0 = sqrtf(s0 / float(D)), d1 = sqrtf(s1 / float(D));
@@ -525,6 +624,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
       s.h = h;
       s.err_prev = 1.0f;
       s.phase = PH_STAGE;
+      if (MODE == MLP_PLAIN_INIT) park();
     } else if (s.phase >= PH_STAGE && stage < 7) {
       s.phase += 1;
     } else if (s.phase >= PH_STAGE) {
@@ -638,6 +738,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
       }
       if (s.status == ST_RUNNING) {
         s.phase = PH_STAGE;  // next attempt, FSAL k1 in hand
+        if (MODE == MLP_PLAIN_STEP) park();
       } else {
 #pragma unroll
         for (int r = 0; r < C; ++r) a.yf[(size_t)i * D + coff + r] = y[r];
@@ -650,7 +751,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
           if (a.trace.cap > 0) a.trace.len[i] = at < a.trace.cap ? at : a.trace.cap;
         }
         s.phase = PH_IDLE;
-        need_grab = true;
+        if (MODE == MLP_FUSED) need_grab = true;
       }
     }
   }
@@ -658,6 +759,19 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, Cfg::TMEM_COLS);
+}
+
+template <class Cfg>
+__global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
+  mlp_solver<Cfg, MLP_FUSED>(a);
+}
+template <class Cfg>
+__global__ void __launch_bounds__(256, 1) k_mlp_plain_init(MlpArgs a) {
+  mlp_solver<Cfg, MLP_PLAIN_INIT>(a);
+}
+template <class Cfg>
+__global__ void __launch_bounds__(256, 1) k_mlp_plain_step(MlpArgs a) {
+  mlp_solver<Cfg, MLP_PLAIN_STEP>(a);
 }
 
 // W_l [N][K_in] BF16 row-major -> core-matrix image with K padded to K_l.
@@ -1382,9 +1496,13 @@ bool mlp_supported(const tode_field_desc* f) {
          f->widths[3] == 32;
 }
 
-size_t mlp_workspace_bytes(const tode_field_desc* f) {
-  (void)f;
-  return align256(256) + align256((size_t)Cfg32::WIMG_BYTES);
+size_t mlp_workspace_bytes(const tode_field_desc* f, const tode_options* o) {
+  size_t b = align256(256) + align256((size_t)Cfg32::WIMG_BYTES);
+  if (o->form == TODE_PLAIN) {  // parked solver state (must match launch_mlp)
+    const size_t B = (size_t)f->B, D = (size_t)f->D;
+    b += 3 * align256(B * D * 4) + align256(B * 8) + 4 * align256(B * 4);
+  }
+  return b;
 }
 
 template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
@@ -1434,10 +1552,31 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   for (int l = 0; l < MLP_MAX_LAYERS; ++l) a.bias[l] = l < Cfg::NL ? r.f->b[l] : nullptr;
   char* p = r.ws;
   a.counter = (int32_t*)p;
+  a.active = (int32_t*)(p + 64);
   a.err = (int32_t*)(p + 128);
   p += align256(256);
   unsigned char* img = (unsigned char*)p;
   a.wimg = img;
+  p += align256((size_t)Cfg::WIMG_BYTES);
+  if (r.o->form == TODE_PLAIN) {
+    const size_t B = (size_t)r.B, D = (size_t)r.D;
+    a.wy = (float*)p;
+    p += align256(B * D * 4);
+    a.wylo = (float*)p;
+    p += align256(B * D * 4);
+    a.wk1 = (float*)p;
+    p += align256(B * D * 4);
+    a.wt = (double*)p;
+    p += align256(B * 8);
+    a.wh = (float*)p;
+    p += align256(B * 4);
+    a.wep = (float*)p;
+    p += align256(B * 4);
+    a.wcur = (int32_t*)p;
+    p += align256(B * 4);
+    a.wfl = (int32_t*)p;
+    p += align256(B * 4);
+  }
   const cudaStream_t st = r.stream;
   for (int l = 0; l < Cfg::NL; ++l) {
     const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
@@ -1454,13 +1593,43 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   }
   long long grid = (r.B + 127) / 128;
   if (grid > r.num_sms) grid = r.num_sms;
+  if (grid == 0) return TODE_OK;
+  if (r.o->form == TODE_PLAIN) {
+    {
+      static std::atomic<uint64_t> d0{0}, d1{0};
+      tode_err e = smem_optin((const void*)k_mlp_plain_init<Cfg>, Cfg::S_END, d0);
+      if (e == TODE_OK) e = smem_optin((const void*)k_mlp_plain_step<Cfg>, Cfg::S_END, d1);
+      if (e != TODE_OK) return e;
+    }
+    k_mlp_plain_init<Cfg><<<(int)grid, 256, Cfg::S_END, st>>>(a);
+    TODE_CUDA_TRY(cudaGetLastError());
+    const int poll = r.o->poll_every > 0 ? r.o->poll_every : 16;
+    long long launched = 0;
+    const long long limit = (long long)r.o->max_steps + 2LL * poll + 2;
+    while (true) {
+      for (int c = 0; c < poll - 1; ++c)
+        k_mlp_plain_step<Cfg><<<(int)grid, 256, Cfg::S_END, st>>>(a);
+      TODE_CUDA_TRY(cudaMemsetAsync(a.active, 0, sizeof(int32_t), st));
+      k_mlp_plain_step<Cfg><<<(int)grid, 256, Cfg::S_END, st>>>(a);
+      TODE_CUDA_TRY(cudaGetLastError());
+      launched += poll;
+      int32_t any = 0;
+      TODE_CUDA_TRY(cudaMemcpyAsync(&any, a.active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      TODE_CUDA_TRY(cudaStreamSynchronize(st));
+      if (!any) break;
+      // one attempt per launch for every running instance: max_steps bounds
+      // the loop; this guard is never expected to fire
+      if (launched > limit) return TODE_ETIMEOUT;
+    }
+    return TODE_OK;
+  }
   k_mlp_fused<Cfg><<<(int)grid, 256, Cfg::S_END, st>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
 }
 
 tode_err mlp_solve(const SolveReq& r, bool split) {
-  if (r.o->form != TODE_FUSED) return TODE_EUNSUPPORTED;
+  if (r.o->form != TODE_FUSED && r.o->form != TODE_PLAIN) return TODE_EUNSUPPORTED;
   if (r.tape && r.tape->stride != 1) return TODE_EUNSUPPORTED;
   return split ? launch_mlp<Cfg32s>(r) : launch_mlp<Cfg32>(r);
 }

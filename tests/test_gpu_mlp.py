@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import gpu_solve, make, oracle_solve, subset
+from gpu_helpers import gpu_solve, make, oracle_solve, subset  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +76,34 @@ def test_mlp_edge_cases():
 
 
 def test_mlp_unsupported_requests_fail_loudly():
+    """The MLP tape keeps every accepted step: a checkpoint stride is refused."""
     import paper_2210_12375_b300 as tode
     w = dict(make(4, B=64), split=True)
+    tape = tode.TapeBuffers.allocate(64, 32, torch.float32, 8, 2, "cuda")
     with pytest.raises(tode._abi.TodeError):
-        gpu_solve(w, torch.float32, "plain")
+        gpu_solve(w, torch.float32, "fused", tape=tape)
+
+
+@pytest.mark.parametrize("B", [300, 148 * 128 + 256])
+def test_mlp_plain_form_equals_fused_bitwise(B):
+    """Plain form (one launch per attempt over the masked batch, state parked
+    in the workspace; several tiles per CTA at the larger size) and fused
+    form give the same bits, including the checkpoint tape and the trace."""
+    import paper_2210_12375_b300 as tode
+    base = make(4)
+    w = dict(subset(base, np.arange(B) % base["B"]), split=True)
+    out = {}
+    for form in ("fused", "plain"):
+        tape = tode.TapeBuffers.allocate(B, 32, torch.float32, 16, 1, "cuda")
+        for t in (tape.y, tape.k1, tape.t, tape.h_acc):
+            t.zero_()  # slots past an instance's last step stay zero
+        g = gpu_solve(w, torch.float32, form, tape=tape, trace_cap=32)
+        out[form] = (g, tape)
+    (gf, tf), (gp, tp) = out["fused"], out["plain"]
+    assert (gf["status"] == 0).all()
+    for k in ("y_eval", "y_final", "n_acc", "n_rej", "n_feval", "status", "trace_t", "trace_h",
+              "trace_err", "trace_accepted", "trace_len"):
+        assert np.array_equal(gf[k], gp[k]), k
+    N = int(gf["n_acc"].max())
+    for name in ("y", "k1", "t", "h_acc"):
+        assert torch.equal(getattr(tf, name)[:N], getattr(tp, name)[:N]), name
