@@ -246,7 +246,22 @@ template <typename T, int R> struct Inst {
 struct SolveOpts {
   double safety, fac_min, fac_max, beta1, beta2, h0;
   int max_steps;
+  // the same controller constants rounded to FP32 once on the host (an FP32
+  // kernel then does no double-to-float conversion per attempt)
+  float safety_f, fac_min_f, fac_max_f, beta1_f, beta2_f;
 };
+inline void opts_round_f32(SolveOpts& s) {
+  s.safety_f = (float)s.safety;
+  s.fac_min_f = (float)s.fac_min;
+  s.fac_max_f = (float)s.fac_max;
+  s.beta1_f = (float)s.beta1;
+  s.beta2_f = (float)s.beta2;
+}
+// controller constant in the state type
+template <typename T> __device__ __forceinline__ T opt_v(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return T(d);
+}
 
 // Output pointers for one instance.
 template <typename T> struct InstOut {
@@ -585,12 +600,12 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     }
     T fac;
     if (err == T(0)) {
-      fac = T(o.fac_max);
+      fac = opt_v<T>(o.fac_max, o.fac_max_f);
     } else {
-      fac = T(o.safety) * ctl_pow(err, T(-o.beta1));
-      if (o.beta2 != 0.0) fac = fac * ctl_pow(s.err_prev, T(o.beta2));
+      fac = opt_v<T>(o.safety, o.safety_f) * ctl_pow(err, -opt_v<T>(o.beta1, o.beta1_f));
+      if (o.beta2 != 0.0) fac = fac * ctl_pow(s.err_prev, opt_v<T>(o.beta2, o.beta2_f));
     }
-    fac = tmin(tmax(fac, T(o.fac_min)), T(o.fac_max));
+    fac = tmin(tmax(fac, opt_v<T>(o.fac_min, o.fac_min_f)), opt_v<T>(o.fac_max, o.fac_max_f));
     if (s.flags & FL_PREV_REJ) fac = tmin(fac, T(1));
     h_next = h * fac;
     s.err_prev = tmax(err, T(1e-4));
@@ -608,8 +623,12 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     }
     if (last) s.status = ST_SUCCESS;
   } else {
-    const T fac = finite ? tmin(tmax(T(o.safety) * ctl_pow(err, T(-o.beta1)), T(o.fac_min)), T(1))
-                         : T(o.fac_min);
+    const T fmin = opt_v<T>(o.fac_min, o.fac_min_f);
+    const T fac =
+        finite ? tmin(tmax(opt_v<T>(o.safety, o.safety_f) * ctl_pow(err, -opt_v<T>(o.beta1, o.beta1_f)),
+                           fmin),
+                      T(1))
+               : fmin;
     h_next = h * fac;
     s.flags |= FL_PREV_REJ;
     s.n_rej++;

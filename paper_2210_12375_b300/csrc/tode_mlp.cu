@@ -699,12 +699,12 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         }
         float fac;
         if (err == 0.0f) {
-          fac = (float)a.o.fac_max;
+          fac = a.o.fac_max_f;
         } else {
-          fac = (float)a.o.safety * ctl_pow(err, (float)-a.o.beta1);
-          if (a.o.beta2 != 0.0) fac = fac * ctl_pow(s.err_prev, (float)a.o.beta2);
+          fac = a.o.safety_f * ctl_pow(err, -a.o.beta1_f);
+          if (a.o.beta2 != 0.0) fac = fac * ctl_pow(s.err_prev, a.o.beta2_f);
         }
-        fac = tmin(tmax(fac, (float)a.o.fac_min), (float)a.o.fac_max);
+        fac = tmin(tmax(fac, a.o.fac_min_f), a.o.fac_max_f);
         if (s.flags & FL_PREV_REJ) fac = tmin(fac, 1.0f);
         h_next = h * fac;
         s.err_prev = tmax(err, 1e-4f);
@@ -721,10 +721,10 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         else s.rem = __double2float_rd(s.t1 - s.t);
       } else {
         const float fac =
-            finite ? tmin(tmax((float)a.o.safety * ctl_pow(err, (float)-a.o.beta1),
-                               (float)a.o.fac_min),
+            finite ? tmin(tmax(a.o.safety_f * ctl_pow(err, -a.o.beta1_f),
+                               a.o.fac_min_f),
                           1.0f)
-                   : (float)a.o.fac_min;
+                   : a.o.fac_min_f;
         h_next = h * fac;
         s.flags |= FL_PREV_REJ;
         s.n_rej++;
@@ -1530,6 +1530,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   a.o.beta2 = r.o->beta2;
   a.o.h0 = r.o->h0;
   a.o.max_steps = r.o->max_steps;
+  opts_round_f32(a.o);
   if (r.tape) {
     a.slots = r.tape->slots;
     a.tp_y = (float*)r.tape->y;

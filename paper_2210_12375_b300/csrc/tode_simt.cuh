@@ -214,6 +214,7 @@ inline SolveOpts make_opts(const tode_options* o) {
   s.beta2 = o->beta2;
   s.h0 = o->h0;
   s.max_steps = o->max_steps;
+  opts_round_f32(s);
   return s;
 }
 

@@ -47,45 +47,53 @@ template <typename T> struct VdpAdj {
 template <typename T, int R_, int G_> struct LinearAdj {
   static constexpr int R = R_, G = G_, D = R_ * G_;
   LinearField<T, R, G> f;
-  T acol[R][D];  // columns g*R+r of A_i: acol[r][j] = A[j][g*R + r]
-  T gA[R][D];    // rows g*R+r of dL/dA_i
+  const T* acol;  // column g*R of A_i: A[j][g*R + r] = acol[j*D + r] (read through the cache)
+  T gA[R][D];     // columns g*R+r of dL/dA_i: gA[r][j] = dL/dA[j][g*R + r]
   __device__ __forceinline__ void load(const T* p, int i) {
     f.load(p, i);
-    const int g = Grp<G>::rank();
-    const T* A = p + (size_t)i * D * D;
+    acol = p + (size_t)i * D * D + Grp<G>::rank() * R;
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int j = 0; j < D; ++j) {
-        acol[r][j] = A[(size_t)j * D + g * R + r];
-        gA[r][j] = T(0);
-      }
+      for (int j = 0; j < D; ++j) gA[r][j] = T(0);
   }
   __device__ __forceinline__ void eval(double t, const T (&y)[R], T (&o)[R]) const {
     f.eval(t, y, o);
   }
-  // gy = A^T v,  dL/dA += v Y^T
+  // gy = A^T v,  dL/dA += v Y^T.  The lane owns columns of dL/dA, so both
+  // products need the gathered v and only the lane's own components of Y.
   __device__ __forceinline__ void vjp(const T (&y)[R], const T (&v)[R], T (&gy)[R]) {
-    T vall[D], yall[D];
+    T vall[D];
     f.gather(v, vall);
-    f.gather(y, yall);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      T s = T(0);
+      if constexpr (sizeof(T) == 8 || D < 8) {
+        T s = T(0);  // FP64: left-to-right (the oracle's order)
 #pragma unroll
-      for (int j = 0; j < D; ++j) s = madd(acol[r][j], vall[j], s);
-      gy[r] = s;
+        for (int j = 0; j < D; ++j) s = madd(__ldg(acol + j * D + r), vall[j], s);
+        gy[r] = s;
+      } else {
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
-      for (int c = 0; c < D; ++c) gA[r][c] = madd(v[r], yall[c], gA[r][c]);
+        for (int j = 0; j < D; j += 4) {
+          s0 = madd(__ldg(acol + j * D + r), vall[j], s0);
+          s1 = madd(__ldg(acol + (j + 1) * D + r), vall[j + 1], s1);
+          s2 = madd(__ldg(acol + (j + 2) * D + r), vall[j + 2], s2);
+          s3 = madd(__ldg(acol + (j + 3) * D + r), vall[j + 3], s3);
+        }
+        gy[r] = (s0 + s1) + (s2 + s3);
+      }
+#pragma unroll
+      for (int j = 0; j < D; ++j) gA[r][j] = madd(vall[j], y[r], gA[r][j]);
     }
   }
   __device__ __forceinline__ void store_param(T* gp, int i, bool bad) const {
     const int g = Grp<G>::rank();
-    T* dst = gp + (size_t)i * D * D + (size_t)g * R * D;
+    T* dst = gp + (size_t)i * D * D + (size_t)g * R;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int j = 0; j < D; ++j)
 #pragma unroll
-      for (int c = 0; c < D; ++c) dst[r * D + c] = bad ? nan_(T(0)) : gA[r][c];
+      for (int r = 0; r < R; ++r) dst[(size_t)j * D + r] = bad ? nan_(T(0)) : gA[r][j];
   }
 };
 
@@ -237,7 +245,7 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
 }
 
 template <class AF, typename T>
-__global__ void __launch_bounds__(256) k_adjoint(AdjArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs<T> a) {
   constexpr int R = AF::R, G = AF::G;
   const int D = a.D;
   const int groups_total = (int)((gridDim.x * (size_t)blockDim.x) / G);
