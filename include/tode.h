@@ -242,8 +242,11 @@ tode_err tode_adjoint_static(const tode_field_desc* f, const tode_options* o, co
  * tensor memory.  A is [M][K] row-major (K-major operand) or, with flags bit
  * 0, [K][M] row-major (MN-major operand); likewise B is [N][K] or, with bit
  * 1, [K][N].  Bit 2 swaps the two stride fields of MN-major descriptors.
- * M = 128; N, K multiples of 16 in [16, 256] (K <= 128 and N <= 144 when
- * any flag is set).  err (device int32) is set to
+ * M = 128 or 64; N, K multiples of 16 in [16, 256] (K <= 128 and N <= 144
+ * when any flag is set; no MN-major A with M = 64).  With M = 64, C must hold
+ * [128][N]: it receives all 128 tensor-memory lanes, each lane's N columns,
+ * with -12345 wherever the MMA wrote nothing (this shows the M = 64
+ * accumulator layout).  err (device int32) is set to
  * 1 if the tensor cores did not signal completion within about a second (C
  * is then left unwritten). */
 tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, int N, int K, int flags,

@@ -11,8 +11,8 @@ namespace tode {
 // for B ([K][N]); bit 2: swap the two core-matrix strides of MN-major
 // operands (which descriptor field is which is what this probe checks).
 __global__ void __launch_bounds__(128, 1)
-    k_tc_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, float* C, int N,
-              int K, int flags, int32_t* err) {
+    k_tc_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, float* C, int M,
+              int N, int K, int flags, int32_t* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(128, 1)
   // operands into the core-matrix layout: K-major tiles are [rows][K]; an
   // MN-major operand is stored as the [K][rows] tile it was given, i.e. its
   // M (or N) index runs along the core matrices' 16-byte rows
-  for (int e = tid; e < 128 * K; e += 128) {
+  for (int e = tid; e < M * K; e += 128) {
     if (a_mn) {
       const int k = e / 128, m = e % 128;
       *reinterpret_cast<uint16_t*>(sA + tc::cm_offset(k, m, 128)) = A[e];
@@ -58,16 +58,27 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = tmem_base;
+  if (M == 64) {
+    // M = 64: mark every lane first, so the dump shows where the 64 rows land
+    float mark[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) mark[j] = -12345.0f;
+    for (int c = 0; c < N; c += 16) tc::tmem_st16(tbase + ((uint32_t)(warp * 32) << 16) + c, mark);
+    tc::tmem_wait_st();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
 
   if (tid == 0) {
-    const uint32_t idesc = tc::idesc_bf16_f32(128, N, a_mn, b_mn);
+    const uint32_t idesc = tc::idesc_bf16_f32(M, N, a_mn, b_mn);
     const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
     for (int kk = 0; kk < K / 16; ++kk) {
       // K-major: next K slice is 2 core matrices (256 B) along K.  MN-major:
       // 2 groups of 8 K-rows, each MN*16 bytes.
       uint64_t da, db;
       if (a_mn) {
-        const uint32_t kst = 128 * 16, mst = 128;
+        const uint32_t kst = (uint32_t)M * 16, mst = 128;
         da = swap ? tc::smem_desc(a0 + kk * 2 * kst, kst, mst)
                   : tc::smem_desc(a0 + kk * 2 * kst, mst, kst);
       } else {
@@ -107,7 +118,9 @@ __global__ void __launch_bounds__(128, 1)
 extern "C" tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, int N, int K,
                                  int flags, int32_t* err, void* stream) {
   if (!A || !B || !C || !err) return TODE_EINVAL;
-  if (M != 128 || N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16) return TODE_EINVAL;
+  if ((M != 128 && M != 64) || N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16)
+    return TODE_EINVAL;
+  if (M == 64 && (flags & 1)) return TODE_EINVAL;
   if (flags & ~7) return TODE_EINVAL;
   if (flags && (K > 128 || N > 144)) return TODE_EINVAL;
   const size_t smem = flags ? (size_t)215040 : (size_t)(128 + N) * K * 2;
@@ -118,7 +131,7 @@ extern "C" tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, 
     return TODE_ECUDA;
   }
   tode::k_tc_gemm<<<1, 128, smem, (cudaStream_t)stream>>>((const uint16_t*)A, (const uint16_t*)B,
-                                                          C, N, K, flags, err);
+                                                          C, M, N, K, flags, err);
   if (cudaGetLastError() != cudaSuccess) return TODE_ECUDA;
   return TODE_OK;
 }

@@ -33,7 +33,7 @@ def test_tc_gemm_matches_fp32_product(N, K):
 def test_tc_gemm_rejects_bad_shapes():
     lib = _abi.load()
     p = C.c_void_p(0x1000)
-    for (M, N, K) in [(64, 16, 16), (128, 8, 16), (128, 16, 8), (128, 272, 16)]:
+    for (M, N, K) in [(32, 16, 16), (128, 8, 16), (128, 16, 8), (128, 272, 16)]:
         assert lib.tode_tc_gemm(p, p, p, M, N, K, 0, p, None) == _abi.TODE_EINVAL
     assert lib.tode_tc_gemm(p, p, p, 128, 16, 16, 8, p, None) == _abi.TODE_EINVAL
 
@@ -60,3 +60,38 @@ def test_tc_gemm_mn_major_operands(flags, N):
     assert rc == 0 and int(err.item()) == 0
     ref = (A.double() @ B.double().T).cuda()
     assert (Cm.double() - ref).abs().max().item() <= 1e-5 * max(1.0, ref.abs().max().item())
+
+
+@pytest.mark.parametrize("N", [64, 128, 256])
+def test_tc_gemm_m64_accumulator_lanes(N):
+    """M = 64 tiles: every one of the 64 result rows appears exactly in one
+    tensor-memory lane; the lane of row m is (m // 16) * 32 + m % 16 (16 rows
+    in each warp's lane quarter), the map the 64-row MLP tile relies on."""
+    import json
+    import os
+    lib = _abi.load()
+    K = 64
+    g = torch.Generator(device="cpu").manual_seed(64 + N)
+    A = torch.randn(64, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    Cm = torch.full((128, N), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.tode_tc_gemm(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
+                          C.c_void_p(Cm.data_ptr()), 64, N, K, 0, C.c_void_p(err.data_ptr()),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == 0 and int(err.item()) == 0
+    ref = (A.double() @ B.double().T).cpu()
+    dump = Cm.double().cpu()
+    tol = 1e-5 * max(1.0, ref.abs().max().item())
+    lanes = {}
+    for m in range(64):
+        hit = [ln for ln in range(128) if (dump[ln] - ref[m]).abs().max().item() <= tol]
+        lanes[m] = hit
+    out = os.path.join(os.environ.get("GRAFT_REPO_ROOT", "."), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, f"m64_lanes_N{N}.json"), "w") as fh:
+            json.dump({"lanes": lanes, "untouched": [ln for ln in range(128)
+                                                     if (dump[ln] == -12345.0).all().item()]}, fh)
+    assert all(len(v) == 1 for v in lanes.values()), lanes
+    assert [lanes[m][0] for m in range(64)] == [(m // 16) * 32 + m % 16 for m in range(64)]
