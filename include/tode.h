@@ -246,7 +246,10 @@ tode_err tode_adjoint_static(const tode_field_desc* f, const tode_options* o, co
  * when any flag is set; no MN-major A with M = 64).  With M = 64, C must hold
  * [128][N]: it receives all 128 tensor-memory lanes, each lane's N columns,
  * with -12345 wherever the MMA wrote nothing (this shows the M = 64
- * accumulator layout).  err (device int32) is set to
+ * accumulator layout); with flags bit 3 (M = 64, N >= 48) each thread of
+ * warp w instead writes the 16 values of one 16x32bx2 tensor-memory load
+ * (half-split offset 32 columns) to C[32w + lane][0:16].  err (device int32)
+ * is set to
  * 1 if the tensor cores did not signal completion within about a second (C
  * is then left unwritten). */
 tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, int N, int K, int flags,

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(128, 1)
   // MN-major probes keep A and B 100 KB apart so that either reading of the
   // descriptor's two stride fields stays inside this CTA's allocation
   unsigned char* sA = smem;  // 128 x K
-  unsigned char* sB = smem + (flags ? (size_t)102400 : (size_t)128 * K * 2);  // N x K
+  unsigned char* sB = smem + ((flags & 7) ? (size_t)102400 : (size_t)128 * K * 2);  // N x K
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   const bool a_mn = flags & 1, b_mn = flags & 2, swap = flags & 4;
@@ -98,7 +98,14 @@ __global__ void __launch_bounds__(128, 1)
   const bool ok = tc::mbar_wait(&mbar, 0);
   if (!ok && lane == 0) atomicExch(err, 1);
   tc::fence_after_sync();
-  if (ok) {
+  if (ok && M == 64 && (flags & 8)) {
+    // the 16x32bx2 access shape: thread t's 16 values go to C[warp*32 + t][0:16]
+    float v[16];
+    tc::tmem_ld16x2<32>(tbase + ((uint32_t)(warp * 32) << 16), v);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) C[(size_t)(warp * 32 + lane) * N + j] = v[j];
+  } else if (ok) {
     const int row = warp * 32 + lane;
     for (int c = 0; c < N; c += 16) {
       float v[16];
@@ -121,9 +128,11 @@ extern "C" tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, 
   if ((M != 128 && M != 64) || N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16)
     return TODE_EINVAL;
   if (M == 64 && (flags & 1)) return TODE_EINVAL;
-  if (flags & ~7) return TODE_EINVAL;
-  if (flags && (K > 128 || N > 144)) return TODE_EINVAL;
-  const size_t smem = flags ? (size_t)215040 : (size_t)(128 + N) * K * 2;
+  if (flags & ~15) return TODE_EINVAL;
+  if ((flags & 8) && (M != 64 || N < 48)) return TODE_EINVAL;
+  const int lay = flags & 7;  // operand-layout flags
+  if (lay && (K > 128 || N > 144)) return TODE_EINVAL;
+  const size_t smem = lay ? (size_t)215040 : (size_t)(128 + N) * K * 2;
   cudaError_t e = cudaFuncSetAttribute(tode::k_tc_gemm,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) {

@@ -95,3 +95,30 @@ def test_tc_gemm_m64_accumulator_lanes(N):
                                                      if (dump[ln] == -12345.0).all().item()]}, fh)
     assert all(len(v) == 1 for v in lanes.values()), lanes
     assert [lanes[m][0] for m in range(64)] == [(m // 16) * 32 + m % 16 for m in range(64)]
+
+
+def test_tc_gemm_m64_half_split_load():
+    """The 16x32bx2 load on an M = 64 accumulator: thread t < 16 of warp w gets
+    row 16w + t at columns [0, 16), thread t >= 16 row 16w + t - 16 at
+    columns [32, 48) -- every thread of the warp carries a useful row."""
+    lib = _abi.load()
+    N, K = 64, 64
+    g = torch.Generator(device="cpu").manual_seed(4242)
+    A = torch.randn(64, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    Cm = torch.full((128, N), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.tode_tc_gemm(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
+                          C.c_void_p(Cm.data_ptr()), 64, N, K, 8, C.c_void_p(err.data_ptr()),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == 0 and int(err.item()) == 0
+    ref = (A.double() @ B.double().T).cpu()
+    got = Cm.double().cpu()[:, :16]
+    exp = torch.empty(128, 16, dtype=torch.float64)
+    for w in range(4):
+        for t in range(32):
+            row = 16 * w + (t % 16)
+            c0 = 0 if t < 16 else 32
+            exp[32 * w + t] = ref[row, c0:c0 + 16]
+    assert (got - exp).abs().max().item() <= 1e-5 * max(1.0, ref.abs().max().item())
