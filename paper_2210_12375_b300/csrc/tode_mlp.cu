@@ -76,14 +76,33 @@ struct MlpArgs {
 // plain form's initialising launch and per-attempt launch.
 enum : int { MLP_FUSED = 0, MLP_PLAIN_INIT = 1, MLP_PLAIN_STEP = 2 };
 
+// Tile geometry and weight residency of the MLP solver, one struct per
+// network family.
+//
+// MlpCfg: 128-row tiles, two threads per row, all weights resident in shared
+// memory (the D = 32, H = 128 network: 49 KB of BF16 weights); M = 128 MMAs,
+// row r of the tile in tensor-memory lane r.
 template <int D_, int H_, int NL_, bool SPLIT_> struct MlpCfg {
   static constexpr int D = D_, H = H_, NL = NL_;
-  static constexpr bool SPLIT = SPLIT_;
+  static constexpr bool SPLIT = SPLIT_, STREAM = false;
+  static constexpr int ROWS = 128, TPR = 2, NT = 256;  // rows per tile, threads per row
   static constexpr int K0 = ((D + 1 + 15) / 16) * 16;  // [y; t] padded to 16
-  static constexpr int C = D / 2;                        // state components per thread
-  static constexpr int HC = H / 2;                       // hidden columns per thread
+  static constexpr int C = D / TPR;                      // state components per thread
+  static constexpr int HC = H / TPR;                     // hidden columns per thread
   static constexpr int TMEM_COLS = (H + D <= 256) ? 256 : 512;
   static constexpr int ACC_COL = 0, OUT_COL = H;
+  __device__ static int row_of(int tid) { return tid & 127; }
+  __device__ static int sub_of(int tid) { return tid >> 7; }
+  // 16 hidden-accumulator columns [sub*HC + c, +16) of this thread's row
+  __device__ static void hid_ld(uint32_t tbase, int tid, int c, float (&v)[16]) {
+    const uint32_t lanes = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
+    tc::tmem_ld16(tbase + lanes + ACC_COL + sub_of(tid) * HC + c, v);
+  }
+  // the output layer's columns of this thread's components
+  __device__ static void out_ld(uint32_t tbase, int tid, float (&v)[C]) {
+    const uint32_t lanes = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
+    tc::tmem_ld16(tbase + lanes + OUT_COL + sub_of(tid) * C, v);
+  }
   // layer l: N_l x K_l
   __host__ __device__ static constexpr int N_of(int l) { return l == NL - 1 ? D : H; }
   __host__ __device__ static constexpr int K_of(int l) { return l == 0 ? K0 : H; }
@@ -108,6 +127,74 @@ template <int D_, int H_, int NL_, bool SPLIT_> struct MlpCfg {
   static constexpr int S_END = S_NXT + 128 * 4;
   static_assert(D % 32 == 0 && H % 32 == 0 && NL >= 2 && NL <= MLP_MAX_LAYERS, "shape");
   static_assert(H <= 256 && D <= 256, "one MMA per layer and K slice");
+};
+
+// MlpBigCfg: the wide network (H = 512; 1.2 MB of BF16 weights).  Split
+// activations of 128 rows would need 256 KB, so a tile has 64 rows (M = 64
+// MMAs: row m of the tile lands in tensor-memory lane (m/16)*32 + m%16), four
+// threads per row.  The weights are streamed through shared memory in
+// 16-column K chunks (a 4-stage ring of bulk copies on mbarriers) every round.
+template <int D_, int H_, int NL_> struct MlpBigCfg {
+  static constexpr int D = D_, H = H_, NL = NL_;
+  static constexpr bool SPLIT = true, STREAM = true;
+  static constexpr int ROWS = 64, TPR = 4, NT = 256;
+  static constexpr int K0 = ((D + 1 + 15) / 16) * 16;
+  static constexpr int C = D / TPR;
+  static constexpr int HC = H / TPR;
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int ACC_COL = 0, OUT_COL = 0;  // the output reuses the hidden accumulator
+  static_assert(C == 16 && H == 512 && D <= 256 && HC % 16 == 0, "shape");
+  // warp w reads lane quarter w%4 (rows 16*(w%4) .. +15 in lanes 0-15); lanes
+  // 0-15 and 16-31 of the warp take different column ranges of the same rows
+  __device__ static int row_of(int tid) { return 16 * ((tid >> 5) & 3) + (tid & 15); }
+  __device__ static int sub_of(int tid) { return 2 * (tid >> 7) + ((tid >> 4) & 1); }
+  __device__ static void hid_ld(uint32_t tbase, int tid, int c, float (&v)[16]) {
+    const uint32_t lanes = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
+    tc::tmem_ld16x2<HC>(tbase + lanes + ACC_COL + (tid >> 7) * 2 * HC + c, v);
+  }
+  __device__ static void out_ld(uint32_t tbase, int tid, float (&v)[C]) {
+    const uint32_t lanes = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
+    tc::tmem_ld16x2<C>(tbase + lanes + OUT_COL + (tid >> 7) * 2 * C, v);
+  }
+  // layer l: N_l x K_l, image = K chunks of [N_l][16] core-matrix tiles
+  __host__ __device__ static constexpr int N_of(int l) { return l == NL - 1 ? D : H; }
+  __host__ __device__ static constexpr int K_of(int l) { return l == 0 ? K0 : H; }
+  __host__ __device__ static constexpr int W_bytes(int l) { return N_of(l) * K_of(l) * 2; }
+  __host__ __device__ static constexpr int W_off(int l) {
+    int o = 0;
+    for (int j = 0; j < l; ++j) o += W_bytes(j);
+    return o;
+  }
+  static constexpr int WIMG_BYTES = W_off(NL);
+  static constexpr int BIAS_FLOATS = (NL - 1) * H + D;
+  static constexpr int KC = 16, NS = 4;                       // chunk K, ring stages
+  static constexpr int STAGE_BYTES = H * KC * 2;             // the largest chunk
+  __host__ __device__ static constexpr int chunks(int l) { return K_of(l) / KC; }
+  __host__ __device__ static constexpr int chunks_per_round() {
+    int n = 0;
+    for (int l = 0; l < NL; ++l) n += chunks(l);
+    return n;
+  }
+  // global chunk index -> image offset and size
+  __device__ static void chunk_src(uint32_t g, int& off, int& bytes) {
+    int c = (int)(g % (uint32_t)chunks_per_round());
+    int l = 0;
+    while (c >= chunks(l)) c -= chunks(l++);
+    bytes = N_of(l) * KC * 2;
+    off = W_off(l) + c * bytes;
+  }
+  // shared-memory carve (bytes)
+  static constexpr int S_XH = 0;
+  static constexpr int S_XL = S_XH + ROWS * K0 * 2;
+  static constexpr int S_HH = S_XL + ROWS * K0 * 2;
+  static constexpr int S_HL = S_HH + ROWS * H * 2;
+  static constexpr int S_W = S_HL + ROWS * H * 2;  // the chunk ring
+  static constexpr int S_BIAS = S_W + NS * STAGE_BYTES;
+  static constexpr int S_RED = S_BIAS + BIAS_FLOATS * 4;
+  static constexpr int S_FIN = S_RED + TPR * ROWS * 2 * 4;
+  static constexpr int S_NXT = S_FIN + TPR * ROWS * 4;
+  static constexpr int S_END = S_NXT + ROWS * 4;
+  static_assert(S_END <= 232448 - 1024, "shared memory");
 };
 
 enum : int { PH_IDLE = 0, PH_INIT0 = 1, PH_INIT1 = 2, PH_STAGE = 3 };  // PH_STAGE + s - 2
@@ -158,7 +245,7 @@ struct MlpRow {
 
 // The solver body shared by the fused form and the plain form.  Fused: a
 // persistent grid, each row takes instances from a global counter and
-// integrates them to their end.  Plain: tile c of 128 instances belongs to
+// integrates them to their end.  Plain: tile c of ROWS instances belongs to
 // CTA c mod grid; the initialising launch runs the starting-step rounds, every
 // later launch one attempt (six stage rounds) per running instance, with the
 // state parked in the workspace in between.
@@ -175,40 +262,60 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   unsigned char* sHh = sm + Cfg::S_HH;
   unsigned char* sHl = sm + Cfg::S_HL;
   float* sBias = reinterpret_cast<float*>(sm + Cfg::S_BIAS);
-  float* sRed = reinterpret_cast<float*>(sm + Cfg::S_RED);  // [half][row][2]
-  int* sFin = reinterpret_cast<int*>(sm + Cfg::S_FIN);      // [half][row]
+  float* sRed = reinterpret_cast<float*>(sm + Cfg::S_RED);  // [sub][row][2]
+  int* sFin = reinterpret_cast<int*>(sm + Cfg::S_FIN);      // [sub][row]
   int* sNxt = reinterpret_cast<int*>(sm + Cfg::S_NXT);      // [row]
+  constexpr int ROWS = Cfg::ROWS, TPR = Cfg::TPR, NT = Cfg::NT;
+  static_assert(C == 16, "16 state components per thread");
+  // streamed weights: a ring of chunk buffers with full / empty barriers
+  __shared__ __align__(8) uint64_t mbar_full[4], mbar_empty[4];
+  uint32_t g_chunk = 0;  // chunks consumed so far (thread 0)
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int row = tid & 127, half = tid >> 7;
-  const int coff = half * C;  // first state component of this thread
-  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const int row = Cfg::row_of(tid), sub = Cfg::sub_of(tid);
+  const int coff = sub * C;  // first state component of this thread
 
   // ---- set-up: barriers, weights (bulk copy), biases, tensor memory
   if (tid == 0) {
     tc::mbar_init(&mbar_mma, 1);
     tc::mbar_init(&mbar_w, 1);
+    if constexpr (Cfg::STREAM)
+      for (int b = 0; b < Cfg::NS; ++b) {
+        tc::mbar_init(&mbar_full[b], 1);
+        tc::mbar_init(&mbar_empty[b], 1);
+      }
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   if (tid == 0) {
-    tc::mbar_expect_tx(&mbar_w, (uint32_t)Cfg::WIMG_BYTES);
+    if constexpr (Cfg::STREAM) {
+      static_assert(Cfg::NS <= 4, "ring barriers");
+      for (int b = 0; b < Cfg::NS; ++b) {  // the ring starts with chunks 0 .. NS-1
+        int off, bytes;
+        Cfg::chunk_src((uint32_t)b, off, bytes);
+        tc::mbar_expect_tx(&mbar_full[b], (uint32_t)bytes);
+        tc::bulk_g2s(sW + b * Cfg::STAGE_BYTES, a.wimg + off, (uint32_t)bytes, &mbar_full[b]);
+      }
+    } else {
+      tc::mbar_expect_tx(&mbar_w, (uint32_t)Cfg::WIMG_BYTES);
 #pragma unroll
-    for (int l = 0; l < NL; ++l)
-      tc::bulk_g2s(sW + Cfg::W_off(l), a.wimg + Cfg::W_off(l), (uint32_t)Cfg::W_bytes(l), &mbar_w);
+      for (int l = 0; l < NL; ++l)
+        tc::bulk_g2s(sW + Cfg::W_off(l), a.wimg + Cfg::W_off(l), (uint32_t)Cfg::W_bytes(l),
+                     &mbar_w);
+    }
   }
   {
     int o = 0;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       const int n = Cfg::N_of(l);
-      for (int j = tid; j < n; j += 256) sBias[o + j] = a.bias[l] ? a.bias[l][j] : 0.0f;
+      for (int j = tid; j < n; j += NT) sBias[o + j] = a.bias[l] ? a.bias[l][j] : 0.0f;
       o += n;
     }
   }
   // zero the input tiles once (padding columns stay zero)
-  for (int j = tid; j < 128 * K0 * 2 / 16; j += 256) {
+  for (int j = tid; j < ROWS * K0 * 2 / 16; j += NT) {
     reinterpret_cast<uint4*>(sXh)[j] = make_uint4(0, 0, 0, 0);
     reinterpret_cast<uint4*>(sXl)[j] = make_uint4(0, 0, 0, 0);
   }
@@ -216,8 +323,10 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     tc::tmem_alloc(&tmem_base_s, Cfg::TMEM_COLS);
     tc::tmem_relinquish();
   }
-  const bool w_ok = tc::mbar_wait(&mbar_w, 0);
-  if (!w_ok) atomicExch(&abort_s, 1);
+  if constexpr (!Cfg::STREAM) {
+    const bool w_ok = tc::mbar_wait(&mbar_w, 0);
+    if (!w_ok) atomicExch(&abort_s, 1);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -296,7 +405,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
 #pragma unroll
       for (int r = 0; r < C; ++r)
         a.yf[(size_t)i * D + coff + r] = s.status == ST_INVALID ? nan_(0.0f) : y[r];
-      if (half == 0) {
+      if (sub == 0) {
         a.n_acc[i] = a.n_rej[i] = a.n_fe[i] = 0;
         a.status[i] = s.status;
         if (a.trace.cap > 0) a.trace.len[i] = 0;
@@ -315,7 +424,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       a.wylo[o] = ylo[r];
       a.wk1[o] = k[0][r];
     }
-    if (half == 0) {
+    if (sub == 0) {
       a.wt[i] = s.t;
       a.wh[i] = s.h;
       a.wep[i] = s.err_prev;
@@ -360,7 +469,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   while (true) {
     if (MODE == MLP_FUSED) {
       // ---- hand out instances to rows that need one (one atomic per row)
-      if (need_grab && half == 0) sNxt[row] = atomicAdd(a.counter, 1);
+      if (need_grab && sub == 0) sNxt[row] = atomicAdd(a.counter, 1);
       __syncthreads();
       if (need_grab) {
         need_grab = false;
@@ -374,7 +483,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       }
     } else if (need_load) {
       need_load = false;
-      const int i = tile * 128 + row;
+      const int i = tile * ROWS + row;
       s.phase = PH_IDLE;
       s.inst = -1;
       if (i < a.B) {
@@ -388,7 +497,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     if (!any_work) {
       if (MODE == MLP_FUSED) break;
       tile += gridDim.x;
-      if ((long long)tile * 128 >= a.B) break;
+      if ((long long)tile * ROWS >= a.B) break;
       need_load = true;
       continue;
     }
@@ -472,7 +581,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       tin = (float)(s.t + cs * (double)h);
     }
     store_row16<true>(sXh, sXl, row, coff, K0, Y);
-    if (half == 1) {  // the time input, hi + lo, in column D
+    if (sub == TPR - 1) {  // the time input, hi + lo, in column D
       const __nv_bfloat16 th = __float2bfloat16_rn(tin);
       const __nv_bfloat16 tl = __float2bfloat16_rn(tin - __bfloat162float(th));
       *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(row, D, K0)) = th;
@@ -488,19 +597,55 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     for (int l = 0; l < NL; ++l) {
       const int Kl = Cfg::K_of(l), Nl = Cfg::N_of(l);
       const uint32_t dcol = (l == NL - 1) ? Cfg::OUT_COL : Cfg::ACC_COL;
-      if (tid == 0) {
-        const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
-        const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(l));
+      if (tid == 0 && !abort_s) {
         const uint32_t ah = tc::smem_u32(l == 0 ? sXh : sHh);
         const uint32_t al = tc::smem_u32(l == 0 ? sXl : sHl);
-        const bool lo = (l == 0) || Cfg::SPLIT;
-        for (int kk = 0; kk < Kl / 16; ++kk) {
-          const uint64_t db = tc::smem_desc(wa + kk * 256, 128, Kl * 16);
-          tc::mma_bf16(tbase + dcol, tc::smem_desc(ah + kk * 256, 128, Kl * 16), db, idesc,
-                       kk > 0);
-          if (lo)
-            tc::mma_bf16(tbase + dcol, tc::smem_desc(al + kk * 256, 128, Kl * 16), db, idesc,
-                         true);
+        if constexpr (Cfg::STREAM) {
+          // K chunk c of layer l sits in ring slot g % NS; after issuing chunk
+          // g, the slot of chunk g-1 is refilled with chunk g-1+NS once its
+          // MMAs are done
+          constexpr int NS = Cfg::NS;
+          const int nh = Nl > 256 ? Nl / 256 : 1, nw = Nl > 256 ? 256 : Nl;
+          const uint32_t idesc = tc::idesc_bf16_f32(ROWS, nw);
+          bool ok = true;
+          for (int c = 0; c < Kl / Cfg::KC && ok; ++c, ++g_chunk) {
+            const int b = (int)(g_chunk % NS);
+            ok = tc::mbar_wait(&mbar_full[b], (g_chunk / NS) & 1u);
+            if (!ok) break;
+            const uint32_t wb = tc::smem_u32(sW + b * Cfg::STAGE_BYTES);
+            const uint64_t dh = tc::smem_desc(ah + c * 256, 128, Kl * 16);
+            const uint64_t dl = tc::smem_desc(al + c * 256, 128, Kl * 16);
+            for (int j = 0; j < nh; ++j) {
+              const uint64_t db = tc::smem_desc(wb + j * (256 / 8) * 256, 128, 256);
+              tc::mma_bf16(tbase + dcol + 256 * j, dh, db, idesc, c > 0);
+              tc::mma_bf16(tbase + dcol + 256 * j, dl, db, idesc, true);
+            }
+            tc::mma_commit(&mbar_empty[b]);
+            if (g_chunk >= 1) {
+              const uint32_t gp = g_chunk - 1;
+              const int pb = (int)(gp % NS);
+              ok = tc::mbar_wait(&mbar_empty[pb], (gp / NS) & 1u);
+              if (!ok) break;
+              int off, bytes;
+              Cfg::chunk_src(gp + NS, off, bytes);
+              tc::mbar_expect_tx(&mbar_full[pb], (uint32_t)bytes);
+              tc::bulk_g2s(sW + pb * Cfg::STAGE_BYTES, a.wimg + off, (uint32_t)bytes,
+                           &mbar_full[pb]);
+            }
+          }
+          if (!ok) atomicExch(&abort_s, 1);
+        } else {
+          const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
+          const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(l));
+          const bool lo = (l == 0) || Cfg::SPLIT;
+          for (int kk = 0; kk < Kl / 16; ++kk) {
+            const uint64_t db = tc::smem_desc(wa + kk * 256, 128, Kl * 16);
+            tc::mma_bf16(tbase + dcol, tc::smem_desc(ah + kk * 256, 128, Kl * 16), db, idesc,
+                         kk > 0);
+            if (lo)
+              tc::mma_bf16(tbase + dcol, tc::smem_desc(al + kk * 256, 128, Kl * 16), db, idesc,
+                           true);
+          }
         }
         tc::mma_commit(&mbar_mma);
       }
@@ -513,9 +658,9 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         const float* bl = sBias + l * H;
 #pragma unroll
         for (int c = 0; c < Cfg::HC; c += 16) {
-          const int col = half * Cfg::HC + c;
+          const int col = sub * Cfg::HC + c;
           float v[16];
-          tc::tmem_ld16(tbase + lane_base + Cfg::ACC_COL + col, v);
+          Cfg::hid_ld(tbase, tid, c, v);
           tc::tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
@@ -534,7 +679,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     float f[16];
     {
       float v[16];
-      tc::tmem_ld16(tbase + lane_base + Cfg::OUT_COL + coff, v);
+      Cfg::out_ld(tbase, tid, v);
       tc::tmem_wait_ld();
       const float* bo = sBias + (NL - 1) * H;
 #pragma unroll
@@ -592,13 +737,18 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         }
       }
     }
-    sRed[(half * 128 + row) * 2 + 0] = p0;
-    sRed[(half * 128 + row) * 2 + 1] = p1;
-    sFin[half * 128 + row] = fin;
+    sRed[(sub * ROWS + row) * 2 + 0] = p0;
+    sRed[(sub * ROWS + row) * 2 + 1] = p1;
+    sFin[sub * ROWS + row] = fin;
     __syncthreads();
-    const float s0 = sRed[row * 2 + 0] + sRed[(128 + row) * 2 + 0];
-    const float s1 = sRed[row * 2 + 1] + sRed[(128 + row) * 2 + 1];
-    const bool fin_all = sFin[row] && sFin[128 + row];
+    float s0 = sRed[row * 2 + 0], s1 = sRed[row * 2 + 1];
+    bool fin_all = sFin[row] != 0;
+#pragma unroll
+    for (int u = 1; u < TPR; ++u) {  // the row's threads in a fixed order
+      s0 += sRed[(u * ROWS + row) * 2 + 0];
+      s1 += sRed[(u * ROWS + row) * 2 + 1];
+      fin_all = fin_all && sFin[u * ROWS + row] != 0;
+    }
 
     const int i = s.inst;
     if (s.phase == PH_INIT0) {
@@ -635,7 +785,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       const bool finite = isfinite(err) && fin_all;
       const bool accept = finite && err <= 1.0f;
       const int att = s.n_acc + s.n_rej;
-      if (a.trace.cap > 0 && att < a.trace.cap && half == 0) {
+      if (a.trace.cap > 0 && att < a.trace.cap && sub == 0) {
         const size_t q = (size_t)i * a.trace.cap + att;
         a.trace.t[q] = s.t;
         a.trace.h[q] = hd;
@@ -658,7 +808,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
             a.tp_y[o * D + coff + r] = y[r];
             a.tp_k1[o * D + coff + r] = k[0][r];
           }
-          if (half == 0) {
+          if (sub == 0) {
             a.tp_t[o] = s.t;
             a.tp_h[o] = h;
           }
@@ -742,7 +892,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       } else {
 #pragma unroll
         for (int r = 0; r < C; ++r) a.yf[(size_t)i * D + coff + r] = y[r];
-        if (half == 0) {
+        if (sub == 0) {
           const int at = s.n_acc + s.n_rej;
           a.n_acc[i] = s.n_acc;
           a.n_rej[i] = s.n_rej;
@@ -753,6 +903,14 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         s.phase = PH_IDLE;
         if (MODE == MLP_FUSED) need_grab = true;
       }
+    }
+  }
+  if constexpr (Cfg::STREAM) {
+    if (tid == 0) {
+      // the ring's copies still in flight land before the CTA exits
+      const uint32_t first = g_chunk, last = g_chunk == 0 ? Cfg::NS - 1 : g_chunk + Cfg::NS - 2;
+      for (uint32_t x = first; x <= last; ++x)
+        if (!tc::mbar_wait(&mbar_full[x % Cfg::NS], (x / Cfg::NS) & 1u)) atomicExch(&abort_s, 1);
     }
   }
   if (abort_s && tid == 0) atomicExch(a.err, 1);
@@ -774,14 +932,18 @@ __global__ void __launch_bounds__(256, 1) k_mlp_plain_step(MlpArgs a) {
   mlp_solver<Cfg, MLP_PLAIN_STEP>(a);
 }
 
-// W_l [N][K_in] BF16 row-major -> core-matrix image with K padded to K_l.
+// W_l [N][K_in] BF16 row-major -> core-matrix image with K padded to K_l:
+// one [N][K_l] tile, or (chunked) K_l/16 consecutive [N][16] tiles, the
+// pieces the streamed-weight solver copies one at a time.
 __global__ void k_mlp_weight_image(const uint16_t* __restrict__ W, int N, int Kin, int Kp,
-                                   unsigned char* img) {
+                                   unsigned char* img, int chunked) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * Kp) return;
   const int n = e / Kp, kk = e % Kp;
   const uint16_t v = kk < Kin ? W[(size_t)n * Kin + kk] : (uint16_t)0;
-  *reinterpret_cast<uint16_t*>(img + tc::cm_offset(n, kk, Kp)) = v;
+  const uint32_t off = chunked ? (uint32_t)(kk / 16) * (uint32_t)N * 32u + tc::cm_offset(n, kk % 16, 16)
+                               : tc::cm_offset(n, kk, Kp);
+  *reinterpret_cast<uint16_t*>(img + off) = v;
 }
 
 // ======================================================================
@@ -1489,15 +1651,26 @@ static tode_err smem_optin(const void* fn, int bytes, std::atomic<uint64_t>& don
 
 using Cfg32 = MlpCfg<32, 128, 3, false>;
 using Cfg32s = MlpCfg<32, 128, 3, true>;
+using Cfg64w = MlpBigCfg<64, 512, 4>;
+
+// the two networks the MLP field is built for
+static bool is_d32_h128(const tode_field_desc* f) {
+  return f->n_layers == 3 && f->D == 32 && f->widths[0] == 33 && f->widths[1] == 128 &&
+         f->widths[2] == 128 && f->widths[3] == 32;
+}
+static bool is_d64_h512(const tode_field_desc* f) {
+  return f->n_layers == 4 && f->D == 64 && f->widths[0] == 65 && f->widths[1] == 512 &&
+         f->widths[2] == 512 && f->widths[3] == 512 && f->widths[4] == 64;
+}
 
 bool mlp_supported(const tode_field_desc* f) {
-  if (!f || f->kind != TODE_MLP || !f->widths || f->n_layers != 3) return false;
-  return f->D == 32 && f->widths[0] == 33 && f->widths[1] == 128 && f->widths[2] == 128 &&
-         f->widths[3] == 32;
+  if (!f || f->kind != TODE_MLP || !f->widths) return false;
+  return is_d32_h128(f) || is_d64_h512(f);
 }
 
 size_t mlp_workspace_bytes(const tode_field_desc* f, const tode_options* o) {
-  size_t b = align256(256) + align256((size_t)Cfg32::WIMG_BYTES);
+  const size_t img = is_d64_h512(f) ? (size_t)Cfg64w::WIMG_BYTES : (size_t)Cfg32::WIMG_BYTES;
+  size_t b = align256(256) + align256(img);
   if (o->form == TODE_PLAIN) {  // parked solver state (must match launch_mlp)
     const size_t B = (size_t)f->B, D = (size_t)f->D;
     b += 3 * align256(B * D * 4) + align256(B * 8) + 4 * align256(B * 4);
@@ -1583,7 +1756,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
     const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
     const int n = N * Kp;
     k_mlp_weight_image<<<(n + 255) / 256, 256, 0, st>>>((const uint16_t*)r.f->W[l], N, Kin, Kp,
-                                                         img + Cfg::W_off(l));
+                                                         img + Cfg::W_off(l), (int)Cfg::STREAM);
   }
   TODE_CUDA_TRY(cudaGetLastError());
   TODE_CUDA_TRY(cudaMemsetAsync(r.ws, 0, 256, st));  // queue counter and error flag
@@ -1592,7 +1765,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
     const tode_err e = smem_optin((const void*)k_mlp_fused<Cfg>, Cfg::S_END, done);
     if (e != TODE_OK) return e;
   }
-  long long grid = (r.B + 127) / 128;
+  long long grid = (r.B + Cfg::ROWS - 1) / Cfg::ROWS;
   if (grid > r.num_sms) grid = r.num_sms;
   if (grid == 0) return TODE_OK;
   if (r.o->form == TODE_PLAIN) {
@@ -1602,16 +1775,16 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
       if (e == TODE_OK) e = smem_optin((const void*)k_mlp_plain_step<Cfg>, Cfg::S_END, d1);
       if (e != TODE_OK) return e;
     }
-    k_mlp_plain_init<Cfg><<<(int)grid, 256, Cfg::S_END, st>>>(a);
+    k_mlp_plain_init<Cfg><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
     TODE_CUDA_TRY(cudaGetLastError());
     const int poll = r.o->poll_every > 0 ? r.o->poll_every : 16;
     long long launched = 0;
     const long long limit = (long long)r.o->max_steps + 2LL * poll + 2;
     while (true) {
       for (int c = 0; c < poll - 1; ++c)
-        k_mlp_plain_step<Cfg><<<(int)grid, 256, Cfg::S_END, st>>>(a);
+        k_mlp_plain_step<Cfg><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
       TODE_CUDA_TRY(cudaMemsetAsync(a.active, 0, sizeof(int32_t), st));
-      k_mlp_plain_step<Cfg><<<(int)grid, 256, Cfg::S_END, st>>>(a);
+      k_mlp_plain_step<Cfg><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
       TODE_CUDA_TRY(cudaGetLastError());
       launched += poll;
       int32_t any = 0;
@@ -1624,7 +1797,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
     }
     return TODE_OK;
   }
-  k_mlp_fused<Cfg><<<(int)grid, 256, Cfg::S_END, st>>>(a);
+  k_mlp_fused<Cfg><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
 }
@@ -1632,12 +1805,14 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
 tode_err mlp_solve(const SolveReq& r, bool split) {
   if (r.o->form != TODE_FUSED && r.o->form != TODE_PLAIN) return TODE_EUNSUPPORTED;
   if (r.tape && r.tape->stride != 1) return TODE_EUNSUPPORTED;
+  if (is_d64_h512(r.f)) return split ? launch_mlp<Cfg64w>(r) : TODE_EUNSUPPORTED;
   return split ? launch_mlp<Cfg32s>(r) : launch_mlp<Cfg32>(r);
 }
 
-size_t mlp_adjoint_scratch_bytes(int B, int num_sms) {
+size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, int num_sms) {
   using L = MlpAdjLayout<Cfg32s>;
-  const long long grid = std::min<long long>((B + 127) / 128, num_sms);
+  if (!is_d32_h128(f)) return 0;  // the adjoint is built for the D = 32 network
+  const long long grid = std::min<long long>((f->B + 127) / 128, num_sms);
   return align256(256) + align256((size_t)Cfg32s::WIMG_BYTES) +
          align256((size_t)grid * L::P_FLOATS * 4);
 }
@@ -1645,6 +1820,7 @@ size_t mlp_adjoint_scratch_bytes(int B, int num_sms) {
 tode_err mlp_adjoint(const AdjReq& r) {
   using Cfg = Cfg32s;
   using L = MlpAdjLayout<Cfg>;
+  if (!is_d32_h128(r.f)) return TODE_EUNSUPPORTED;
   if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->k1 || !r.tape->y || !r.tape->t)
     return TODE_EINVAL;
   if (!r.gW || !r.gW[0] || !r.gW[1] || !r.gW[2]) return TODE_EINVAL;
@@ -1678,7 +1854,7 @@ tode_err mlp_adjoint(const AdjReq& r) {
   for (int l = 0; l < 3; ++l) {
     const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
     k_mlp_weight_image<<<(N * Kp + 255) / 256, 256, 0, st>>>((const uint16_t*)r.f->W[l], N, Kin,
-                                                             Kp, img + Cfg::W_off(l));
+                                                             Kp, img + Cfg::W_off(l), 0);
   }
   TODE_CUDA_TRY(cudaGetLastError());
   TODE_CUDA_TRY(cudaMemsetAsync(r.scratch, 0, 256, st));
