@@ -45,6 +45,8 @@ def _args():
     p.add_argument("--plain-steps", type=int, default=30)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--autotune", action="store_true",
+                   help="time the launch-shape candidates on this batch first (fused form)")
     return p.parse_args()
 
 
@@ -179,6 +181,10 @@ def run_tode(args):
     gye = torch.tensor(rng.standard_normal((B, K, D)), dtype=dtype, device=dev)
     gyf = torch.tensor(rng.standard_normal((B, D)), dtype=dtype, device=dev)
     opt = dict(rtol=w["rtol"], atol=w["atol"])
+    tuned = None
+    if args.autotune and not mlp:
+        tuned = tode.autotune(field, y0, t0, t1, te, with_adjoint=True, reps=3, **opt)
+        opt.update(tuned)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     # probe: step counts (identical every pass) and the tape size
@@ -402,7 +408,8 @@ def run_tode(args):
                    "pass": "fwd+adjoint" if with_adjoint else "fwd",
                    "state": "f32 (compensated), time f64", "controller": "I (beta1=0.2)",
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
-                   "parallelism": f"dp{world} (independent replicas of the batch)"},
+                   "parallelism": f"dp{world} (independent replicas of the batch)",
+                   "launch": tuned if tuned is not None else "defaults"},
         "gpu_launches": gpu_launches * args.steps,
         "clocks": clocks, "e2e": e2e, "roofline": roofline, "breakdown": breakdown,
         "wall_s_timed_region": wall_fused,
