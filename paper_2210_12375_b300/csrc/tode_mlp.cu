@@ -113,6 +113,7 @@ template <int D_, int H_, int NL_, bool SPLIT_> struct MlpCfg {
     return o;
   }
   static constexpr int WIMG_BYTES = W_off(NL);
+  static constexpr int WREP = 1, WIMG_STRIDE = ((WIMG_BYTES + 255) / 256) * 256;
   static constexpr int BIAS_FLOATS = (NL - 1) * H + D;
   // shared-memory carve (bytes)
   static constexpr int S_W = 0;
@@ -166,6 +167,9 @@ template <int D_, int H_, int NL_> struct MlpBigCfg {
     return o;
   }
   static constexpr int WIMG_BYTES = W_off(NL);
+  // every CTA streams the same chunks at about the same time; CTAs read one
+  // of WREP copies of the image so the requests spread over the L2 slices
+  static constexpr int WREP = 16, WIMG_STRIDE = ((WIMG_BYTES + 255) / 256) * 256;
   static constexpr int BIAS_FLOATS = (NL - 1) * H + D;
   static constexpr int KC = 16, NS = 4;                       // chunk K, ring stages
   static constexpr int STAGE_BYTES = H * KC * 2;             // the largest chunk
@@ -274,6 +278,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = Cfg::row_of(tid), sub = Cfg::sub_of(tid);
   const int coff = sub * C;  // first state component of this thread
+  const unsigned char* wimg = a.wimg + (size_t)(blockIdx.x % Cfg::WREP) * Cfg::WIMG_STRIDE;
 
   // ---- set-up: barriers, weights (bulk copy), biases, tensor memory
   if (tid == 0) {
@@ -295,13 +300,13 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         int off, bytes;
         Cfg::chunk_src((uint32_t)b, off, bytes);
         tc::mbar_expect_tx(&mbar_full[b], (uint32_t)bytes);
-        tc::bulk_g2s(sW + b * Cfg::STAGE_BYTES, a.wimg + off, (uint32_t)bytes, &mbar_full[b]);
+        tc::bulk_g2s(sW + b * Cfg::STAGE_BYTES, wimg + off, (uint32_t)bytes, &mbar_full[b]);
       }
     } else {
       tc::mbar_expect_tx(&mbar_w, (uint32_t)Cfg::WIMG_BYTES);
 #pragma unroll
       for (int l = 0; l < NL; ++l)
-        tc::bulk_g2s(sW + Cfg::W_off(l), a.wimg + Cfg::W_off(l), (uint32_t)Cfg::W_bytes(l),
+        tc::bulk_g2s(sW + Cfg::W_off(l), wimg + Cfg::W_off(l), (uint32_t)Cfg::W_bytes(l),
                      &mbar_w);
     }
   }
@@ -629,7 +634,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
               int off, bytes;
               Cfg::chunk_src(gp + NS, off, bytes);
               tc::mbar_expect_tx(&mbar_full[pb], (uint32_t)bytes);
-              tc::bulk_g2s(sW + pb * Cfg::STAGE_BYTES, a.wimg + off, (uint32_t)bytes,
+              tc::bulk_g2s(sW + pb * Cfg::STAGE_BYTES, wimg + off, (uint32_t)bytes,
                            &mbar_full[pb]);
             }
           }
@@ -1669,8 +1674,9 @@ bool mlp_supported(const tode_field_desc* f) {
 }
 
 size_t mlp_workspace_bytes(const tode_field_desc* f, const tode_options* o) {
-  const size_t img = is_d64_h512(f) ? (size_t)Cfg64w::WIMG_BYTES : (size_t)Cfg32::WIMG_BYTES;
-  size_t b = align256(256) + align256(img);
+  const size_t img = is_d64_h512(f) ? (size_t)Cfg64w::WREP * Cfg64w::WIMG_STRIDE
+                                    : (size_t)Cfg32::WREP * Cfg32::WIMG_STRIDE;
+  size_t b = align256(256) + img;
   if (o->form == TODE_PLAIN) {  // parked solver state (must match launch_mlp)
     const size_t B = (size_t)f->B, D = (size_t)f->D;
     b += 3 * align256(B * D * 4) + align256(B * 8) + 4 * align256(B * 4);
@@ -1731,7 +1737,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   p += align256(256);
   unsigned char* img = (unsigned char*)p;
   a.wimg = img;
-  p += align256((size_t)Cfg::WIMG_BYTES);
+  p += (size_t)Cfg::WREP * Cfg::WIMG_STRIDE;
   if (r.o->form == TODE_PLAIN) {
     const size_t B = (size_t)r.B, D = (size_t)r.D;
     a.wy = (float*)p;
@@ -1752,12 +1758,14 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
     p += align256(B * 4);
   }
   const cudaStream_t st = r.stream;
-  for (int l = 0; l < Cfg::NL; ++l) {
-    const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
-    const int n = N * Kp;
-    k_mlp_weight_image<<<(n + 255) / 256, 256, 0, st>>>((const uint16_t*)r.f->W[l], N, Kin, Kp,
-                                                         img + Cfg::W_off(l), (int)Cfg::STREAM);
-  }
+  for (int rep = 0; rep < Cfg::WREP; ++rep)
+    for (int l = 0; l < Cfg::NL; ++l) {
+      const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
+      const int n = N * Kp;
+      k_mlp_weight_image<<<(n + 255) / 256, 256, 0, st>>>(
+          (const uint16_t*)r.f->W[l], N, Kin, Kp,
+          img + (size_t)rep * Cfg::WIMG_STRIDE + Cfg::W_off(l), (int)Cfg::STREAM);
+    }
   TODE_CUDA_TRY(cudaGetLastError());
   TODE_CUDA_TRY(cudaMemsetAsync(r.ws, 0, 256, st));  // queue counter and error flag
   {
