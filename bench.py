@@ -43,6 +43,8 @@ def _args():
     p.add_argument("--impl", default="tode", choices=["tode", "reference"])
     p.add_argument("--workload", type=int, default=2)
     p.add_argument("--plain-steps", type=int, default=30)
+    p.add_argument("--batch", type=int, default=0, help="instances (default: the workload's)")
+    p.add_argument("--kernel-reps", type=int, default=20)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--autotune", action="store_true",
@@ -158,7 +160,7 @@ def run_tode(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    w = workloads.make(args.workload)
+    w = workloads.make(args.workload, args.batch or None)
     kind = w["field"]["kind"]
     dtype = torch.float64 if w["prec"] == "f64" else torch.float32
     B, D = w["y0"].shape
@@ -194,8 +196,8 @@ def run_tode(args):
     n_att = int((probe.n_acc.long() + probe.n_rej.long()).sum().item())
     n_acc_total = int(probe.n_acc.long().sum().item())
     n_acc_max = int(probe.n_acc.max().item())
-    # every field has the adjoint and both forms
-    with_adjoint = True
+    # every field has both forms; the wide MLP (D = 64, H = 512) has no adjoint yet
+    with_adjoint = not (mlp and D == 64)
     tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev)
 
     def fwd(form, sol=None, ws=None):
@@ -268,14 +270,14 @@ def run_tode(args):
         torch.cuda.synchronize()
         return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
-    nk = max(20, args.steps // 4)
+    nk = max(1, args.kernel_reps)
     with ClockSampler(local) as clk:
         ms_fused, wall_fused = timed("fused", args.steps, with_adjoint)
         k_fwd_ms = kernel_ms(nk, False)
         k_adj_ms = kernel_ms(nk, True) if with_adjoint else None
     clocks = clk.summary()
     ms_fused_fwd, _ = timed("fused", nk, False)
-    ms_plain, _ = timed("plain", args.plain_steps, True)
+    ms_plain, _ = timed("plain", args.plain_steps, with_adjoint)
     ms_plain_fwd, _ = timed("plain", args.plain_steps, False)
 
     per_step = ms_fused / args.steps
@@ -354,14 +356,14 @@ def run_tode(args):
         wd = [x.shape[1] for x in w["field"]["W"]] + [w["field"]["W"][-1].shape[0]]
         S = sum(wd[l] * wd[l + 1] for l in range(len(wd) - 1))  # MACs of one evaluation
         peak = peaks["bf16_tflops"]
+        net = f"D={D},H={wd[1]},{len(wd) - 2} hidden layers,split"
         kf = {"achieved": 6 * 2 * S * n_att / (k_fwd_ms * 1e-3) / 1e12,
-              "kernel": "k_mlp_fused<D=32,H=128,3 layers,split> (fused forward)",
-              "kernel_ms": k_fwd_ms}
+              "kernel": f"k_mlp_fused<{net}> (fused forward)", "kernel_ms": k_fwd_ms}
         # per accepted step: 7 evaluations (stages recomputed, activations at
         # every stage input) and 6 transposed products dX + dW (2 x 2S MACs)
         ka = {"achieved": (7 * 2 * S + 6 * 4 * S) * n_acc_total / (k_adj_ms * 1e-3) / 1e12,
-              "kernel": "k_mlp_adjoint<D=32,H=128,3 layers,split>", "kernel_ms": k_adj_ms}
-        for r in (kf, ka):
+              "kernel": f"k_mlp_adjoint<{net}>", "kernel_ms": k_adj_ms} if with_adjoint else None
+        for r in (kf, ka) if with_adjoint else (kf,):
             r.update(bound="tensor", peak=peak, unit="TFLOP/s", frac=r["achieved"] / peak,
                      traffic=None, peak_source=f"bf16 burst, {src} (MEASURED_PEAKS.json)")
     else:
@@ -374,7 +376,10 @@ def run_tode(args):
             r.update(bound="alu", peak=fp32_peak, unit="TFLOP/s",
                      frac=r["achieved"] / fp32_peak, traffic=None, peak_source=psrc)
     # the dominant kernel of the timed step (forward + adjoint) is the roofline line
-    roofline, other = (ka, kf) if k_adj_ms >= k_fwd_ms else (kf, ka)
+    if with_adjoint:
+        roofline, other = (ka, kf) if k_adj_ms >= k_fwd_ms else (kf, ka)
+    else:
+        roofline, other = kf, None
     breakdown = {
         "fused_fwd": world * n_att / (ms_fused_fwd / nk * 1e-3),
         "max_err_over_tol_vs_closed_form": err,
@@ -394,9 +399,15 @@ def run_tode(args):
         "fused_over_plain_fwd_adj": (ms_plain / args.plain_steps) / per_step,
         "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
     })
-    # our kernels per timed step: fused forward (+3 weight-image builds for the
-    # MLP) and the adjoint (+3 image builds and the ordered dW reduction)
-    gpu_launches = 4 + 5 if mlp else 2
+    # our kernels per timed step: fused forward (+ the weight-image builds for
+    # the MLP, one per layer and copy) and the adjoint (+ one image build per
+    # layer and the ordered dW reduction)
+    if mlp:
+        n_layers = len(w["field"]["W"])
+        reps = 16 if D == 64 else 1
+        gpu_launches = reps * n_layers + 1 + ((n_layers + 2) if with_adjoint else 0)
+    else:
+        gpu_launches = 2
     result = {
         "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
