@@ -45,6 +45,7 @@ def _args():
     p.add_argument("--plain-steps", type=int, default=30)
     p.add_argument("--batch", type=int, default=0, help="instances (default: the workload's)")
     p.add_argument("--kernel-reps", type=int, default=20)
+    p.add_argument("--fwd-only", action="store_true", help="time the forward solve alone")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--autotune", action="store_true",
@@ -196,8 +197,8 @@ def run_tode(args):
     n_att = int((probe.n_acc.long() + probe.n_rej.long()).sum().item())
     n_acc_total = int(probe.n_acc.long().sum().item())
     n_acc_max = int(probe.n_acc.max().item())
-    # every field has both forms; the wide MLP (D = 64, H = 512) has no adjoint yet
-    with_adjoint = not (mlp and D == 64)
+    # every field has both forms and the adjoint (--fwd-only drops the latter)
+    with_adjoint = not args.fwd_only
     tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev)
 
     def fwd(form, sol=None, ws=None):
@@ -405,7 +406,11 @@ def run_tode(args):
     if mlp:
         n_layers = len(w["field"]["W"])
         reps = 16 if D == 64 else 1
-        gpu_launches = reps * n_layers + 1 + ((n_layers + 2) if with_adjoint else 0)
+        if D == 64:  # wide: 2 images x copies, ones fill, per slice the kernel + 20 GEMMs, copy
+            adj = 2 * reps * n_layers + 1 + -(-B // (148 * 64)) * 1 + 1
+        else:
+            adj = n_layers + 2
+        gpu_launches = reps * n_layers + 1 + (adj if with_adjoint else 0)
     else:
         gpu_launches = 2
     result = {

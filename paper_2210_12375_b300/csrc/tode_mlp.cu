@@ -28,8 +28,11 @@
 
 #include <cuda_bf16.h>
 
+#include <cublas_v2.h>
+
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 
 namespace tode {
 
@@ -1596,6 +1599,596 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   if (warp == 0) tc::tmem_dealloc(tbase, L::T_COLS);
 }
 
+// ======================================================================
+// Discrete adjoint of the wide MLP field (D = 64, three tanh layers of
+// 512; App. A).  Same schedule as k_mlp_adjoint -- rows reverse their own
+// instances, 12 lockstep rounds per accepted step -- on 64-row tiles with the
+// weights streamed through a chunk ring.  The reverse rounds need the
+// transposed weights too (W_l^T, K chunks along the layer's outputs).
+//
+// The weight gradients do not fit in tensor memory (two 512 x 512 layers),
+// so every reverse round writes the rows of its layer inputs (X, h1, h2, h3)
+// and of its pre-activation cotangents (delta1, delta2, delta3, kbar), as
+// BF16 hi + lo, to a staging area; dW_l = delta_l^T act_l and the bias sums
+// are then plain GEMMs over the staged rows (mlp_wide_dw).
+// ======================================================================
+template <class Cfg> struct WideAdjLayout {
+  static constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, ROWS = Cfg::ROWS;
+  static_assert(Cfg::NL == 4 && D == 64 && H == 512 && K0 == 80 && ROWS == 64, "network");
+  static constexpr int NS = 3;                         // ring stages
+  static constexpr int STAGE_BYTES = 16 * H * 2;      // the largest chunk (16 x 512)
+  static constexpr int S_XH = 0;
+  static constexpr int S_XL = S_XH + ROWS * K0 * 2;
+  static constexpr int S_HH = S_XL + ROWS * K0 * 2;   // the hidden / delta tile
+  static constexpr int S_HL = S_HH + ROWS * H * 2;
+  static constexpr int S_KH = S_HL + ROWS * H * 2;    // kbar tile
+  static constexpr int S_KL = S_KH + ROWS * D * 2;
+  static constexpr int S_W = S_KL + ROWS * D * 2;     // chunk ring
+  static constexpr int S_BIAS = S_W + NS * STAGE_BYTES;
+  static constexpr int S_END = S_BIAS + Cfg::BIAS_FLOATS * 4;
+  static_assert(S_END <= 232448 - 1024, "shared memory");
+  // transposed image: layer l, chunk c = outputs [16c, 16c+16) as an MN-major
+  // [16][IN_l] core-matrix tile
+  __host__ __device__ static constexpr int IN_of(int l) { return Cfg::K_of(l); }
+  __host__ __device__ static constexpr int T_bytes(int l) { return Cfg::N_of(l) * IN_of(l) * 2; }
+  __host__ __device__ static constexpr int T_off(int l) {
+    int o = 0;
+    for (int j = 0; j < l; ++j) o += T_bytes(j);
+    return o;
+  }
+  static constexpr int TIMG_BYTES = T_off(Cfg::NL);
+  static constexpr int TIMG_STRIDE = ((TIMG_BYTES + 255) / 256) * 256;
+  // chunk schedule of one step: 5 recompute rounds (forward layers 0..3) then
+  // 7 reverse rounds (forward layers 0..2, transposed layers 3, 2, 1, 0)
+  static constexpr int REC_CHUNKS = 5 + 32 + 32 + 32, REV_CHUNKS = 5 + 32 + 32 + 4 + 32 + 32 + 32;
+  static constexpr int STEP_CHUNKS = 5 * REC_CHUNKS + 7 * REV_CHUNKS;
+  // global chunk index -> (transposed?, layer, chunk) -> image offset, bytes
+  __device__ static void chunk_src(uint32_t g, bool& tr, int& off, int& bytes) {
+    int p = (int)(g % (uint32_t)STEP_CHUNKS);
+    int seq[7], n = 0;
+    if (p < 5 * REC_CHUNKS) {
+      p %= REC_CHUNKS;
+      tr = false;
+      const int c[4] = {5, 32, 32, 32};
+      int l = 0;
+      while (p >= c[l]) p -= c[l++];
+      bytes = Cfg::N_of(l) * 32;
+      off = Cfg::W_off(l) + p * bytes;
+      (void)seq;
+      (void)n;
+      return;
+    }
+    p = (p - 5 * REC_CHUNKS) % REV_CHUNKS;
+    const int cnt[7] = {5, 32, 32, 4, 32, 32, 32};
+    const int lay[7] = {0, 1, 2, 3, 2, 1, 0};
+    int k = 0;
+    while (p >= cnt[k]) p -= cnt[k++];
+    const int l = lay[k];
+    if (k < 3) {
+      tr = false;
+      bytes = Cfg::N_of(l) * 32;
+      off = Cfg::W_off(l) + p * bytes;
+    } else {
+      tr = true;
+      bytes = 16 * IN_of(l) * 2;
+      off = T_off(l) + p * bytes;
+    }
+  }
+};
+
+struct WideAdjArgs {
+  int i0, B, K;  // the slice: instances i0 .. i0+B-1 of the batch
+  const double* t0;
+  const double* t1;
+  const double* te;
+  const int32_t* n_acc;
+  const int32_t* status;
+  int slots, Btot;
+  const float* tp_y;
+  const float* tp_k1;
+  const double* tp_t;
+  const float* tp_h;
+  const float* gye;
+  const float* gyf;
+  float* gy0;
+  const unsigned char* wimg;  // forward chunk image (copies WIMG_STRIDE apart)
+  const unsigned char* timg;  // transposed chunk image (copies TIMG_STRIDE apart)
+  const float* bias[MLP_MAX_LAYERS];
+  // staging: rows (c*cap + round)*64 + row; hi and lo planes
+  uint16_t* sa[4][2];  // X [80], h1, h2, h3 [512]
+  uint16_t* sg[4][2];  // delta1, delta2, delta3 [512], kbar [64]
+  int cap;             // reverse rounds per CTA
+  float* yscr;         // [grid][64][5][D]: stage inputs Y_2..Y_6 of the step being reversed
+  int32_t* overflow;
+  int32_t* err;
+};
+
+// Stores 16 values of a row as BF16 hi / lo into two row-major planes.
+__device__ __forceinline__ void stage_row16(uint16_t* hp, uint16_t* lp, size_t off,
+                                            const float (&v)[16]) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float a0 = v[c * 8 + 2 * j], b0 = v[c * 8 + 2 * j + 1];
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, b0);
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(a0 - __low2float(h2), b0 - __high2float(h2));
+      hw[j] = *reinterpret_cast<const uint32_t*>(&h2);
+      lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
+    }
+    *reinterpret_cast<uint4*>(hp + off + 8 * c) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(lp + off + 8 * c) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+// 16 values hi + lo of a staged row, as floats
+__device__ __forceinline__ void unstage_row16(const uint16_t* hp, const uint16_t* lp, size_t off,
+                                              float (&v)[16]) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const uint4 h = *reinterpret_cast<const uint4*>(hp + off + 8 * c);
+    const uint4 l = *reinterpret_cast<const uint4*>(lp + off + 8 * c);
+    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
+      const __nv_bfloat162 l2 = *reinterpret_cast<const __nv_bfloat162*>(&lw[j]);
+      v[c * 8 + 2 * j] = __low2float(h2) + __low2float(l2);
+      v[c * 8 + 2 * j + 1] = __high2float(h2) + __high2float(l2);
+    }
+  }
+}
+
+template <class Cfg>
+__global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
+  using L = WideAdjLayout<Cfg>;
+  using Cc = DP5;
+  constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, HC = Cfg::HC, ROWS = 64;
+  constexpr int NS = L::NS;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar_mma, mbar_full[NS], mbar_empty[NS];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  unsigned char* sXh = sm + L::S_XH;
+  unsigned char* sXl = sm + L::S_XL;
+  unsigned char* sHh = sm + L::S_HH;
+  unsigned char* sHl = sm + L::S_HL;
+  unsigned char* sKh = sm + L::S_KH;
+  unsigned char* sKl = sm + L::S_KL;
+  unsigned char* sW = sm + L::S_W;
+  float* sBias = reinterpret_cast<float*>(sm + L::S_BIAS);
+
+  const int tid = threadIdx.x;
+  const int row = Cfg::row_of(tid), sub = Cfg::sub_of(tid);
+  const int coff = sub * C;
+  const int grid = gridDim.x;
+  const unsigned char* wimg = a.wimg + (size_t)(blockIdx.x % Cfg::WREP) * Cfg::WIMG_STRIDE;
+  const unsigned char* timg = a.timg + (size_t)(blockIdx.x % Cfg::WREP) * L::TIMG_STRIDE;
+  uint32_t g_chunk = 0;
+
+  if (tid == 0) {
+    tc::mbar_init(&mbar_mma, 1);
+    for (int b = 0; b < NS; ++b) {
+      tc::mbar_init(&mbar_full[b], 1);
+      tc::mbar_init(&mbar_empty[b], 1);
+    }
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue_copy = [&](uint32_t g, int slot) {
+    bool tr;
+    int off, bytes;
+    L::chunk_src(g, tr, off, bytes);
+    tc::mbar_expect_tx(&mbar_full[slot], (uint32_t)bytes);
+    tc::bulk_g2s(sW + slot * L::STAGE_BYTES, (tr ? timg : wimg) + off, (uint32_t)bytes,
+                 &mbar_full[slot]);
+  };
+  if (tid == 0)
+    for (int b = 0; b < NS; ++b) issue_copy((uint32_t)b, b);
+  {
+    int o = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int n = Cfg::N_of(l);
+      for (int j = tid; j < n; j += 256) sBias[o + j] = a.bias[l] ? a.bias[l][j] : 0.0f;
+      o += n;
+    }
+  }
+  for (int j = tid; j < ROWS * K0 * 2 / 16; j += 256) {
+    reinterpret_cast<uint4*>(sXh)[j] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(sXl)[j] = make_uint4(0, 0, 0, 0);
+  }
+  __syncthreads();
+  if (tid < ROWS)  // the constant 1 column (D + 1) gives db1 through dW1
+    *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(tid, D + 1, K0)) =
+        __float2bfloat16_rn(1.0f);
+  if ((tid >> 5) == 0) {
+    tc::tmem_alloc(&tmem_base_s, 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tmem_base_s;
+  uint32_t parity = 0;
+
+  // ---- per-row reverse state (as in k_mlp_adjoint)
+  int inst = a.i0 + blockIdx.x * ROWS + row;
+  const int iend = a.i0 + a.B;
+  bool act = false;
+  int n = -1, N = 0, q = -1;
+  bool bad = false;
+  double tn = 0.0, tnext = 0.0;
+  float h = 0.0f;
+  float yn[16], yb[16], kb[7][16];
+#pragma unroll
+  for (int r = 0; r < C; ++r) {
+    yn[r] = yb[r] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) kb[j][r] = 0.0f;
+  }
+  auto load_step = [&](int i) {
+    const size_t o = (size_t)n * a.Btot + i;
+    float k1[16];
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      yn[r] = a.tp_y[o * D + coff + r];
+      k1[r] = a.tp_k1[o * D + coff + r];
+    }
+    tn = a.tp_t[o];
+    h = a.tp_h[o];
+    tnext = (n == N - 1) ? a.t1[i] : tn + (double)h;
+#pragma unroll
+    for (int j = 1; j < 7; ++j)
+#pragma unroll
+      for (int r = 0; r < C; ++r) kb[j][r] = dp_a(j + 1, 1) * k1[r];
+    act = true;
+  };
+  auto next_work = [&](bool finishing) {
+    while (true) {
+      if (finishing) {
+        const int i = inst;
+        if (!bad && a.gye) {
+          const long long k0 = tkey(a.t0[i]);
+          for (; q >= 0; --q)
+            if (tkey(a.te[(size_t)i * a.K + q]) == k0)
+#pragma unroll
+              for (int r = 0; r < C; ++r) yb[r] += a.gye[((size_t)i * a.K + q) * D + coff + r];
+        }
+#pragma unroll
+        for (int r = 0; r < C; ++r) a.gy0[(size_t)i * D + coff + r] = bad ? nan_(0.0f) : yb[r];
+        inst += grid * ROWS;
+        finishing = false;
+      }
+      if (inst >= iend) {
+        act = false;
+        return;
+      }
+      const int i = inst;
+      N = a.n_acc[i];
+      bad = a.status[i] != ST_SUCCESS;
+      if (!bad && N > a.slots) {
+        bad = true;
+        if (sub == 0) atomicExch(a.overflow, 1);
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + coff + r] : 0.0f;
+      q = a.K - 1;
+      n = N - 1;
+      if (bad || n < 0) {
+        finishing = true;
+        continue;
+      }
+      load_step(i);
+      return;
+    }
+  };
+  next_work(false);
+
+  auto barrier = [&]() {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  auto wait_mma = [&]() {
+    if (!tc::mbar_wait(&mbar_mma, parity)) atomicExch(&abort_s, 1);
+    parity ^= 1u;
+    tc::fence_after_sync();
+  };
+  // one GEMM of the round through the ring: A = the layer's input tile (K
+  // major, hi and lo), B = the next K chunks; N = 512 as two halves of 256
+  // or one MMA of width nw.  Transposed chunks are MN-major [16][IN] tiles.
+  auto gemm = [&](uint32_t ah, uint32_t al, int Ka, int nchunks, int Nl, bool tr) {
+    if (tid != 0 || abort_s) return;
+    const int nh = Nl > 256 ? Nl / 256 : 1, nw = Nl > 256 ? 256 : Nl;
+    const uint32_t idesc = tc::idesc_bf16_f32(ROWS, nw, false, tr);
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c, ++g_chunk) {
+      const int b = (int)(g_chunk % NS);
+      ok = tc::mbar_wait(&mbar_full[b], (g_chunk / NS) & 1u);
+      if (!ok) break;
+      const uint32_t wb = tc::smem_u32(sW + b * L::STAGE_BYTES);
+      const uint64_t dh = tc::smem_desc(ah + c * 256, 128, Ka * 16);
+      const uint64_t dl = tc::smem_desc(al + c * 256, 128, Ka * 16);
+      for (int j = 0; j < nh; ++j) {
+        const uint64_t db = tr ? tc::smem_desc_mn(wb + j * (256 / 8) * 128, Nl * 16)
+                               : tc::smem_desc(wb + j * (256 / 8) * 256, 128, 256);
+        tc::mma_bf16(tbase + 256 * j, dh, db, idesc, c > 0);
+        tc::mma_bf16(tbase + 256 * j, dl, db, idesc, true);
+      }
+      tc::mma_commit(&mbar_empty[b]);
+      if (g_chunk >= 1) {
+        const uint32_t gp = g_chunk - 1;
+        const int pb = (int)(gp % NS);
+        ok = tc::mbar_wait(&mbar_empty[pb], (gp / NS) & 1u);
+        if (!ok) break;
+        issue_copy(gp + NS, pb);
+      }
+    }
+    if (!ok) atomicExch(&abort_s, 1);
+    tc::mma_commit(&mbar_mma);
+  };
+  // hidden epilogue: h = tanh(acc + b) into the tile; reverse rounds also
+  // stage the row
+  auto hidden_epi = [&](const float* bl, bool stage, uint16_t* shp, uint16_t* slp, size_t srow) {
+#pragma unroll
+    for (int c = 0; c < HC; c += 16) {
+      const int col = sub * HC + c;
+      float v[16];
+      Cfg::hid_ld(tbase, tid, c, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = tanh_acc(v[j] + bl[col + j]);
+      store_row16<true>(sHh, sHl, row, col, H, v);
+      if (stage) stage_row16(shp, slp, srow * H + col, v);
+    }
+  };
+  // delta epilogue: delta = acc (1 - h^2); h from the tile (own layer) or
+  // from the staged row; the split delta replaces the tile, and is staged
+  auto delta_epi = [&](bool h_in_tile, const uint16_t* hhp, const uint16_t* hlp, uint16_t* shp,
+                       uint16_t* slp, size_t srow) {
+#pragma unroll
+    for (int c = 0; c < HC; c += 16) {
+      const int col = sub * HC + c;
+      float v[16], hv[16];
+      Cfg::hid_ld(tbase, tid, c, v);
+      if (h_in_tile) {
+#pragma unroll
+        for (int c8 = 0; c8 < 2; ++c8) {
+          const uint32_t off = tc::cm_offset(row, col + 8 * c8, H);
+          const uint4 hh = *reinterpret_cast<const uint4*>(sHh + off);
+          const uint4 ll = *reinterpret_cast<const uint4*>(sHl + off);
+          const uint32_t hw[4] = {hh.x, hh.y, hh.z, hh.w}, lw[4] = {ll.x, ll.y, ll.z, ll.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
+            const __nv_bfloat162 l2 = *reinterpret_cast<const __nv_bfloat162*>(&lw[j]);
+            hv[8 * c8 + 2 * j] = __low2float(h2) + __low2float(l2);
+            hv[8 * c8 + 2 * j + 1] = __high2float(h2) + __high2float(l2);
+          }
+        }
+      } else {
+        unstage_row16(hhp, hlp, srow * H + col, hv);
+      }
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] *= madd(-hv[j], hv[j], 1.0f);
+      store_row16<true>(sHh, sHl, row, col, H, v);
+      stage_row16(shp, slp, srow * H + col, v);
+    }
+  };
+  const float bw[7] = {float(Cc::b1), 0.0f, float(Cc::b3), float(Cc::b4), float(Cc::b5),
+                       float(Cc::b6), 0.0f};
+  int rev_round = 0;  // reverse rounds staged by this CTA
+
+  for (int rnd = 0;; ++rnd) {
+    const int ph = rnd % ADJ_ROUNDS;
+    if (ph == 0 && __syncthreads_or(act) == 0) break;
+    if (abort_s) break;
+    const bool rev = ph >= 5;
+    const int s = rev ? 12 - ph : ph + 2;
+    if (rev && rev_round >= a.cap) {  // cannot happen: the staging is sized for it
+      if (tid == 0) atomicExch(a.err, 2);
+      break;
+    }
+    const size_t srow = ((size_t)blockIdx.x * a.cap + rev_round) * ROWS + row;
+
+    // ---- stage input and cotangent; Y_2..Y_6 of the step wait in a small
+    // per-row scratch (L2-resident) between the recompute and reverse rounds
+    float Y[16], d3[16];
+    float tin = 0.0f;
+    if (!rev) {
+      float acc[16];
+      pick7(kb, s - 1, acc);
+#pragma unroll
+      for (int r = 0; r < C; ++r) Y[r] = act ? madd(h, acc[r], yn[r]) : 0.0f;
+      float4* ys = reinterpret_cast<float4*>(
+          a.yscr + (((size_t)blockIdx.x * ROWS + row) * 5 + (s - 2)) * D + coff);
+#pragma unroll
+      for (int v4 = 0; v4 < 4; ++v4)
+        ys[v4] = make_float4(Y[4 * v4], Y[4 * v4 + 1], Y[4 * v4 + 2], Y[4 * v4 + 3]);
+    } else if (s == 7) {
+#pragma unroll
+      for (int r = 0; r < C; ++r) Y[r] = act ? yn[r] + h * kb[6][r] : 0.0f;
+      if (act) {
+        const int i = inst;
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+#pragma unroll
+          for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
+        const long long kt = tkey(tn), kn = tkey(tnext);
+        while (q >= 0) {
+          const double tq = a.te[(size_t)i * a.K + q];
+          const long long kq = tkey(tq);
+          if (!(kq > kt)) break;
+          if (a.gye) {
+            float gq[16], w[7];
+#pragma unroll
+            for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + coff + r];
+            if (kq == kn) {
+#pragma unroll
+              for (int j = 0; j < 7; ++j) w[j] = bw[j];
+            } else {
+              dense_weights<float>(float(tq - tn) / h, w);
+            }
+#pragma unroll
+            for (int j = 0; j < 7; ++j)
+#pragma unroll
+              for (int r = 0; r < C; ++r) kb[j][r] = madd(h * w[j], gq[r], kb[j][r]);
+#pragma unroll
+            for (int r = 0; r < C; ++r) yb[r] += gq[r];
+          }
+          q--;
+        }
+      }
+    } else if (s >= 2) {
+      const float4* ys = reinterpret_cast<const float4*>(
+          a.yscr + (((size_t)blockIdx.x * ROWS + row) * 5 + (s - 2)) * D + coff);
+#pragma unroll
+      for (int v4 = 0; v4 < 4; ++v4) {
+        const float4 u = ys[v4];
+        Y[4 * v4] = act ? u.x : 0.0f;
+        Y[4 * v4 + 1] = act ? u.y : 0.0f;
+        Y[4 * v4 + 2] = act ? u.z : 0.0f;
+        Y[4 * v4 + 3] = act ? u.w : 0.0f;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < C; ++r) Y[r] = act ? yn[r] : 0.0f;
+    }
+    if (act) tin = (float)(tn + dp_c(s) * (double)h);
+    store_row16<true>(sXh, sXl, row, coff, K0, Y);
+    if (sub == Cfg::TPR - 1) {
+      const __nv_bfloat16 th = __float2bfloat16_rn(tin);
+      const __nv_bfloat16 tlo = __float2bfloat16_rn(tin - __bfloat162float(th));
+      *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(row, D, K0)) = th;
+      *reinterpret_cast<__nv_bfloat16*>(sXl + tc::cm_offset(row, D, K0)) = tlo;
+    }
+    if (rev) {
+      pick7(kb, s - 1, d3);
+      if (!act)
+#pragma unroll
+        for (int r = 0; r < C; ++r) d3[r] = 0.0f;
+      store_row16<true>(sKh, sKl, row, coff, D, d3);
+      // staged rows: X = [Y; t; 1; 0...] and kbar
+      stage_row16(a.sa[0][0], a.sa[0][1], srow * K0 + coff, Y);
+      stage_row16(a.sg[3][0], a.sg[3][1], srow * D + coff, d3);
+      if (sub == Cfg::TPR - 1) {
+        float tail[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tail[j] = 0.0f;
+        tail[0] = tin;
+        tail[1] = 1.0f;
+        stage_row16(a.sa[0][0], a.sa[0][1], srow * K0 + D, tail);
+      }
+    }
+    barrier();
+
+    // ---- forward layers at Y_s
+    gemm(tc::smem_u32(sXh), tc::smem_u32(sXl), K0, K0 / 16, H, false);
+    wait_mma();
+    hidden_epi(sBias, rev, a.sa[1][0], a.sa[1][1], srow);
+    barrier();
+    gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, false);
+    wait_mma();
+    hidden_epi(sBias + H, rev, a.sa[2][0], a.sa[2][1], srow);
+    barrier();
+    gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, false);
+    wait_mma();
+    hidden_epi(sBias + 2 * H, rev, a.sa[3][0], a.sa[3][1], srow);
+    barrier();
+
+    float fg[16];
+    if (!rev) {
+      // output layer: f = k_s
+      gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, D, false);
+      wait_mma();
+      float v[16];
+      Cfg::out_ld(tbase, tid, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int r = 0; r < C; ++r) fg[r] = v[r] + sBias[3 * H + coff + r];
+    } else {
+      // gh3 = kbar W3 -> delta3 (h3 in the tile)
+      gemm(tc::smem_u32(sKh), tc::smem_u32(sKl), D, D / 16, H, true);
+      wait_mma();
+      delta_epi(true, nullptr, nullptr, a.sg[2][0], a.sg[2][1], srow);
+      barrier();
+      // gh2 = delta3 W2 -> delta2 (h2 staged)
+      gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, true);
+      wait_mma();
+      delta_epi(false, a.sa[2][0], a.sa[2][1], a.sg[1][0], a.sg[1][1], srow);
+      barrier();
+      // gh1 = delta2 W1 -> delta1 (h1 staged)
+      gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, true);
+      wait_mma();
+      delta_epi(false, a.sa[1][0], a.sa[1][1], a.sg[0][0], a.sg[0][1], srow);
+      barrier();
+      // gx = delta1 W0: the state part of the cotangent
+      gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, K0, true);
+      wait_mma();
+      Cfg::out_ld(tbase, tid, fg);
+      tc::tmem_wait_ld();
+      rev_round++;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (abort_s) break;
+
+    // ---- consume (row-local; as in k_mlp_adjoint)
+    if (!act) continue;
+    if (!rev) {
+#pragma unroll
+      for (int j = 2; j < 7; ++j) {
+        if (j + 1 <= s || (j == 6 && s == 2)) continue;
+        const float c = dp_a(j + 1, s);
+#pragma unroll
+        for (int r = 0; r < C; ++r) kb[j][r] = madd(c, fg[r], kb[j][r]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j + 1 >= s) continue;
+        const float c = h * dp_a(s, j + 1);
+#pragma unroll
+        for (int r = 0; r < C; ++r) kb[j][r] = madd(c, fg[r], kb[j][r]);
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) yb[r] += fg[r];
+      if (s == 1) {
+        n -= 1;
+        if (n >= 0) load_step(inst);
+        else next_work(true);
+      }
+    }
+  }
+  if (tid == 0) {  // the ring's copies still in flight land before the CTA exits
+    const uint32_t first = g_chunk, last = g_chunk == 0 ? NS - 1 : g_chunk + NS - 2;
+    for (uint32_t x = first; x <= last; ++x)
+      if (!tc::mbar_wait(&mbar_full[x % NS], (x / NS) & 1u)) atomicExch(&abort_s, 1);
+  }
+  if (abort_s && tid == 0) atomicExch(a.err, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if ((tid >> 5) == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+// W_l [N][K_in] BF16 -> transposed chunk image: chunk c holds outputs
+// [16c, 16c+16) as an MN-major [16][IN] core-matrix tile (IN = K_l padded).
+__global__ void k_mlp_weight_image_t(const uint16_t* __restrict__ W, int N, int Kin, int IN,
+                                     unsigned char* img) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * IN) return;
+  const int o = e / IN, i = e % IN;
+  const uint16_t v = i < Kin ? W[(size_t)o * Kin + i] : (uint16_t)0;
+  const uint32_t off = (uint32_t)(o / 16) * 16u * (uint32_t)IN * 2u + tc::cm_offset(o % 16, i, IN);
+  *reinterpret_cast<uint16_t*>(img + off) = v;
+}
+
 // Sums the per-CTA partials in CTA order into the caller's gradients
 // (layouts of the weights: W_l [out][in], b_l [out]).
 template <class Cfg>
@@ -1817,17 +2410,192 @@ tode_err mlp_solve(const SolveReq& r, bool split) {
   return split ? launch_mlp<Cfg32s>(r) : launch_mlp<Cfg32>(r);
 }
 
-size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, int num_sms) {
+// ---- wide network: scratch plan of the staged adjoint
+struct WidePlan {
+  int grid, cap;       // CTAs, reverse rounds per CTA per slice
+  size_t rows;         // staged rows per slice
+  size_t off_timg, off_stage[8], off_dw0, off_ones, off_yscr, off_cublas, total;
+};
+static constexpr size_t WIDE_CUBLAS_WS = 32u << 20;
+static WidePlan wide_plan(int B, int slots, int num_sms) {
+  using Cfg = Cfg64w;
+  using L = WideAdjLayout<Cfg>;
+  WidePlan p{};
+  p.grid = (int)std::min<long long>((B + 63) / 64, num_sms);
+  p.cap = 7 * std::max(slots, 1);  // one instance per row per slice
+  p.rows = (size_t)p.grid * p.cap * 64;
+  size_t o = align256(256) + (size_t)Cfg::WREP * Cfg::WIMG_STRIDE;
+  p.off_timg = o;
+  o += (size_t)Cfg::WREP * L::TIMG_STRIDE;
+  const int width[8] = {Cfg::K0, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::D};
+  for (int q = 0; q < 8; ++q) {  // sa[0..3], sg[0..3]; hi then lo planes
+    p.off_stage[q] = o;
+    o += 2 * align256(p.rows * width[q] * 2);
+  }
+  p.off_dw0 = o;
+  o += align256((size_t)Cfg::H * Cfg::K0 * 4);
+  p.off_ones = o;
+  o += align256(p.rows * 2);
+  p.off_yscr = o;
+  o += align256((size_t)p.grid * 64 * 5 * Cfg::D * 4);
+  p.off_cublas = o;
+  o += WIDE_CUBLAS_WS;
+  p.total = o;
+  return p;
+}
+
+size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, int slots, int num_sms) {
   using L = MlpAdjLayout<Cfg32s>;
-  if (!is_d32_h128(f)) return 0;  // the adjoint is built for the D = 32 network
+  if (is_d64_h512(f)) return wide_plan(f->B, slots, num_sms).total;
+  if (!is_d32_h128(f)) return 0;
   const long long grid = std::min<long long>((f->B + 127) / 128, num_sms);
   return align256(256) + align256((size_t)Cfg32s::WIMG_BYTES) +
          align256((size_t)grid * L::P_FLOATS * 4);
 }
 
+__global__ void k_fill_bf16_one(uint16_t* p, size_t n) {
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e < n) p[e] = 0x3F80;  // BF16 1.0
+}
+// gW0 [H][65] from the padded [H][80] accumulator
+__global__ void k_copy_cols(const float* src, int rows, int ld, int cols, float* dst) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < rows * cols) dst[e] = src[(size_t)(e / cols) * ld + e % cols];
+}
+
+// one cuBLAS handle per device, created on first use
+static cublasHandle_t cublas_for_device(int dev) {
+  static std::mutex mu;
+  static cublasHandle_t handles[64] = {};
+  std::lock_guard<std::mutex> g(mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!handles[dev] && cublasCreate(&handles[dev]) != CUBLAS_STATUS_SUCCESS) handles[dev] = nullptr;
+  return handles[dev];
+}
+
+static tode_err mlp_wide_adjoint(const AdjReq& r) {
+  using Cfg = Cfg64w;
+  using L = WideAdjLayout<Cfg>;
+  const cudaStream_t st = r.stream;
+  const WidePlan p = wide_plan(r.B, r.tape->slots, r.num_sms);
+  if (r.scratch_bytes < p.total) return TODE_EWORKSPACE;
+  int dev = 0;
+  TODE_CUDA_TRY(cudaGetDevice(&dev));
+  cublasHandle_t hb = cublas_for_device(dev);
+  if (!hb) return TODE_ECUDA;
+  char* base = r.scratch;
+  WideAdjArgs a{};
+  a.K = r.K;
+  a.t0 = r.t0;
+  a.t1 = r.t1;
+  a.te = r.te;
+  a.n_acc = r.n_acc;
+  a.status = r.status;
+  a.slots = r.tape->slots;
+  a.Btot = r.B;
+  a.tp_y = (const float*)r.tape->y;
+  a.tp_k1 = (const float*)r.tape->k1;
+  a.tp_t = r.tape->t;
+  a.tp_h = (const float*)r.tape->h_acc;
+  a.gye = (const float*)r.gye;
+  a.gyf = (const float*)r.gyf;
+  a.gy0 = (float*)r.gy0;
+  for (int l = 0; l < MLP_MAX_LAYERS; ++l) a.bias[l] = r.f->b[l];
+  a.err = (int32_t*)(base + 128);
+  a.overflow = r.overflow;
+  a.cap = p.cap;
+  a.yscr = (float*)(base + p.off_yscr);
+  unsigned char* img = (unsigned char*)base + align256(256);
+  unsigned char* timg = (unsigned char*)base + p.off_timg;
+  a.wimg = img;
+  a.timg = timg;
+  const int width[8] = {Cfg::K0, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::D};
+  uint16_t* planes[8][2];
+  for (int q = 0; q < 8; ++q) {
+    planes[q][0] = (uint16_t*)(base + p.off_stage[q]);
+    planes[q][1] = (uint16_t*)(base + p.off_stage[q] + align256(p.rows * width[q] * 2));
+  }
+  for (int j = 0; j < 4; ++j)
+    for (int k = 0; k < 2; ++k) {
+      a.sa[j][k] = planes[j][k];
+      a.sg[j][k] = planes[4 + j][k];
+    }
+  float* dw0 = (float*)(base + p.off_dw0);
+  uint16_t* ones = (uint16_t*)(base + p.off_ones);
+  // weight images (forward chunks and transposed chunks, WREP copies each)
+  for (int rep = 0; rep < Cfg::WREP; ++rep)
+    for (int l = 0; l < Cfg::NL; ++l) {
+      const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
+      k_mlp_weight_image<<<(N * Kp + 255) / 256, 256, 0, st>>>(
+          (const uint16_t*)r.f->W[l], N, Kin, Kp, img + (size_t)rep * Cfg::WIMG_STRIDE + Cfg::W_off(l),
+          1);
+      k_mlp_weight_image_t<<<(N * Kp + 255) / 256, 256, 0, st>>>(
+          (const uint16_t*)r.f->W[l], N, Kin, Kp, timg + (size_t)rep * L::TIMG_STRIDE + L::T_off(l));
+    }
+  k_fill_bf16_one<<<(unsigned)((p.rows + 255) / 256), 256, 0, st>>>(ones, p.rows);
+  TODE_CUDA_TRY(cudaGetLastError());
+  TODE_CUDA_TRY(cudaMemsetAsync(base, 0, 256, st));
+  TODE_CUDA_TRY(cudaMemsetAsync(dw0, 0, (size_t)Cfg::H * Cfg::K0 * 4, st));
+  for (int l = 1; l < 4; ++l)
+    TODE_CUDA_TRY(cudaMemsetAsync(r.gW[l], 0, (size_t)Cfg::N_of(l) * Cfg::K_of(l) * 4, st));
+  if (r.gb)
+    for (int l = 0; l < 4; ++l)
+      if (r.gb[l]) TODE_CUDA_TRY(cudaMemsetAsync(r.gb[l], 0, (size_t)Cfg::N_of(l) * 4, st));
+  {
+    static std::atomic<uint64_t> done{0};
+    const tode_err e = smem_optin((const void*)k_mlp_adjoint_wide<Cfg>, L::S_END, done);
+    if (e != TODE_OK) return e;
+  }
+  if (cublasSetStream(hb, st) != CUBLAS_STATUS_SUCCESS ||
+      cublasSetWorkspace(hb, base + p.off_cublas, WIDE_CUBLAS_WS) != CUBLAS_STATUS_SUCCESS)
+    return TODE_ECUDA;
+  const float one = 1.0f;
+  // dW_l (row-major [out][in]) += delta_l^T act_l: in cuBLAS's column-major
+  // terms C[in x out] += act[in x R] * delta[out x R]^T
+  auto gemm = [&](const uint16_t* act_p, int in, const uint16_t* del_p, int out, float* C) {
+    return cublasGemmEx(hb, CUBLAS_OP_N, CUBLAS_OP_T, in, out, (int)p.rows, &one, act_p,
+                        CUDA_R_16BF, in, del_p, CUDA_R_16BF, out, &one, C, CUDA_R_32F, in,
+                        CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) == CUBLAS_STATUS_SUCCESS;
+  };
+  auto colsum = [&](const uint16_t* del_p, int out, float* C) {  // db += delta^T 1
+    return cublasGemmEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, out, 1, (int)p.rows, &one, del_p,
+                        CUDA_R_16BF, out, ones, CUDA_R_16BF, (int)p.rows, &one, C, CUDA_R_32F,
+                        out, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) == CUBLAS_STATUS_SUCCESS;
+  };
+  const int slice = p.grid * 64;
+  for (int i0 = 0; i0 < r.B; i0 += slice) {
+    for (int q = 0; q < 8; ++q)
+      TODE_CUDA_TRY(cudaMemsetAsync(planes[q][0], 0, 2 * align256(p.rows * width[q] * 2), st));
+    a.i0 = i0;
+    a.B = std::min(slice, r.B - i0);
+    k_mlp_adjoint_wide<Cfg><<<p.grid, 256, L::S_END, st>>>(a);
+    TODE_CUDA_TRY(cudaGetLastError());
+    for (int l = 0; l < 4; ++l) {
+      const int in = Cfg::K_of(l), out = Cfg::N_of(l);
+      float* C = l == 0 ? dw0 : r.gW[l];
+      bool ok = gemm(planes[l][0], in, planes[4 + l][0], out, C) &&  // hi * hi
+                gemm(planes[l][1], in, planes[4 + l][0], out, C) &&  // lo * hi
+                gemm(planes[l][0], in, planes[4 + l][1], out, C);    // hi * lo
+      if (ok && r.gb && r.gb[l])
+        ok = colsum(planes[4 + l][0], out, r.gb[l]) && colsum(planes[4 + l][1], out, r.gb[l]);
+      if (!ok) return TODE_ECUDA;
+    }
+  }
+  k_copy_cols<<<(Cfg::H * (Cfg::D + 1) + 255) / 256, 256, 0, st>>>(dw0, Cfg::H, Cfg::K0, Cfg::D + 1,
+                                                                   r.gW[0]);
+  TODE_CUDA_TRY(cudaGetLastError());
+  return TODE_OK;
+}
+
 tode_err mlp_adjoint(const AdjReq& r) {
   using Cfg = Cfg32s;
   using L = MlpAdjLayout<Cfg>;
+  if (is_d64_h512(r.f)) {
+    if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->k1 || !r.tape->y || !r.tape->t)
+      return TODE_EINVAL;
+    if (!r.gW || !r.gW[0] || !r.gW[1] || !r.gW[2] || !r.gW[3]) return TODE_EINVAL;
+    return mlp_wide_adjoint(r);
+  }
   if (!is_d32_h128(r.f)) return TODE_EUNSUPPORTED;
   if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->k1 || !r.tape->y || !r.tape->t)
     return TODE_EINVAL;

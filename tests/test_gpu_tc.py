@@ -122,3 +122,26 @@ def test_tc_gemm_m64_half_split_load():
             c0 = 0 if t < 16 else 32
             exp[32 * w + t] = ref[row, c0:c0 + 16]
     assert (got - exp).abs().max().item() <= 1e-5 * max(1.0, ref.abs().max().item())
+
+
+@pytest.mark.parametrize("N", [80, 128, 144])
+def test_tc_gemm_m64_mn_major_b(N):
+    """M = 64 tiles with an MN-major B operand ([K][N] tile), the shape of the
+    wide adjoint's transposed-weight products."""
+    lib = _abi.load()
+    K = 64
+    g = torch.Generator(device="cpu").manual_seed(6400 + N)
+    A = torch.randn(64, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    Cm = torch.full((128, N), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Ad, Bd = A.cuda(), B.T.contiguous().cuda()
+    rc = lib.tode_tc_gemm(C.c_void_p(Ad.data_ptr()), C.c_void_p(Bd.data_ptr()),
+                          C.c_void_p(Cm.data_ptr()), 64, N, K, 6, C.c_void_p(err.data_ptr()),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == 0 and int(err.item()) == 0
+    ref = (A.double() @ B.double().T)
+    rows = [(m // 16) * 32 + m % 16 for m in range(64)]
+    got = Cm.double().cpu()[rows]
+    assert (got - ref).abs().max().item() <= 1e-5 * max(1.0, ref.abs().max().item())
