@@ -284,7 +284,10 @@ def run_tode(args):
     per_step = ms_fused / args.steps
     value = world * n_att / (per_step * 1e-3)
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers: every step
+    # copies its inputs host -> device, solves + reverses, and copies its
+    # results back; two buffer sets let step k+1's input copy and step k-1's
+    # output copy overlap step k's kernels (three streams)
     e2e = None
     if not args.no_e2e:
         src = dict(y0=y0, t0=t0, t1=t1, te=te)
@@ -294,59 +297,83 @@ def run_tode(args):
         else:
             src.update(P=field.params())
         host = {k: v.cpu().pin_memory() for k, v in src.items()}
-        dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-        if kind == "linear":
-            field_e2e = tode.Linear(dev_in["P"])
-        elif mlp:
-            field_e2e = tode.MLP([dev_in[f"W{l}"] for l in range(len(field.W))], field.b,
-                                 split=True)
-        else:
-            field_e2e = tode.VdP(dev_in["P"])
-        sol = fwd("fused")
-        out_h = {}
         h2d = sum(v.numel() * v.element_size() for v in host.values())
+        s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        NBUF = 2
+        bufs = []
+        for _ in range(NBUF):
+            d_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+            if kind == "linear":
+                f_b = tode.Linear(d_in["P"])
+            elif mlp:
+                f_b = tode.MLP([d_in[f"W{l}"] for l in range(len(field.W))], field.b, split=True)
+            else:
+                f_b = tode.VdP(d_in["P"])
+            bufs.append(dict(d_in=d_in, field=f_b, sol=None, out_h={},
+                             ev_in=torch.cuda.Event(), ev_done=torch.cuda.Event(),
+                             ev_out=torch.cuda.Event()))
+        ws_e2e = [None]
 
-        def e2e_step():
-            for k, v in host.items():
-                dev_in[k].copy_(v, non_blocking=True)
-            s = tode.solve(field_e2e, dev_in["y0"], dev_in["t0"], dev_in["t1"], dev_in["te"],
-                           form="fused", tape=tape, out=sol, workspace=sol.extra["workspace"],
-                           **opt)
-            res = dict(y_eval=s.y_eval, y_final=s.y_final, n_acc=s.n_acc, n_rej=s.n_rej,
-                       n_feval=s.n_feval, status=s.status)
-            if with_adjoint:
-                g0, gp, _ = tode.adjoint(field_e2e, dev_in["t0"], dev_in["t1"], dev_in["te"],
-                                         s, tape, dev_in["gye"], dev_in["gyf"], **opt)
-                res["gy0"] = g0
-                if mlp:  # (gW, gb) lists of the MLP field
-                    res.update({f"gW{l}": x for l, x in enumerate(gp[0])})
-                    res.update({f"gb{l}": x for l, x in enumerate(gp[1])})
-                else:
-                    res["gp"] = gp
-            for k, v in res.items():
-                if k not in out_h:
-                    out_h[k] = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
-                out_h[k].copy_(v, non_blocking=True)
+        def issue(k):
+            bb = bufs[k % NBUF]
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(bb["ev_done"])  # step k-NBUF no longer reads the inputs
+                for name, v in host.items():
+                    bb["d_in"][name].copy_(v, non_blocking=True)
+                bb["ev_in"].record(s_in)
+            with torch.cuda.stream(s_cmp):
+                s_cmp.wait_event(bb["ev_in"])
+                s_cmp.wait_event(bb["ev_out"])  # step k-NBUF's results are copied out
+                d = bb["d_in"]
+                sl = tode.solve(bb["field"], d["y0"], d["t0"], d["t1"], d["te"], form="fused",
+                                tape=tape, out=bb["sol"], workspace=ws_e2e[0], stream=s_cmp,
+                                **opt)
+                bb["sol"] = sl
+                ws_e2e[0] = sl.extra["workspace"]
+                res = dict(y_eval=sl.y_eval, y_final=sl.y_final, n_acc=sl.n_acc,
+                           n_rej=sl.n_rej, n_feval=sl.n_feval, status=sl.status)
+                if with_adjoint:
+                    g0, gp, _ = tode.adjoint(bb["field"], d["t0"], d["t1"], d["te"], sl, tape,
+                                             d["gye"], d["gyf"], stream=s_cmp, **opt)
+                    res["gy0"] = g0
+                    if mlp:  # (gW, gb) lists of the MLP field
+                        res.update({f"gW{l}": x for l, x in enumerate(gp[0])})
+                        res.update({f"gb{l}": x for l, x in enumerate(gp[1])})
+                    else:
+                        res["gp"] = gp
+                bb["ev_done"].record(s_cmp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(bb["ev_done"])
+                for name, v in res.items():
+                    if name not in bb["out_h"]:
+                        bb["out_h"][name] = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+                    bb["out_h"][name].copy_(v, non_blocking=True)
+                    v.record_stream(s_out)
+                bb["ev_out"].record(s_out)
 
-        for _ in range(args.warmup):
-            e2e_step()
+        for bb in bufs:  # events start out complete
+            for e in ("ev_done", "ev_out"):
+                bb[e].record(torch.cuda.current_stream())
+        for k in range(max(args.warmup, NBUF)):
+            issue(k)
         torch.cuda.synchronize()
-        d2h = sum(v.numel() * v.element_size() for v in out_h.values())
-        ev = _events(torch, nk)
+        d2h = sum(v.numel() * v.element_size() for v in bufs[0]["out_h"].values())
+        e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_start.record(s_in)
         for k in range(nk):
-            flush.zero_()
-            ev[k][0].record(stream)
-            e2e_step()
-            ev[k][1].record(stream)
+            issue(k)
+        s_in.wait_stream(s_out)
+        e_end.record(s_in)
         torch.cuda.synchronize()
-        ms_e2e = float(sum(a.elapsed_time(b) for a, b in ev)) / nk
+        ms_e2e = e_start.elapsed_time(e_end) / nk
         if world > 1:
             t = torch.tensor([ms_e2e], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_e2e = float(t.item())
         e2e = {"value": world * n_att / (ms_e2e * 1e-3), "unit": "instance-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": ms_e2e}
+               "ms_per_step": ms_e2e,
+               "pipelining": f"{NBUF} buffer sets, copies on their own streams"}
 
     peaks, src = _peaks()
     clk_mhz = peaks.get("sm_max_mhz", 2032.0)
@@ -372,7 +399,7 @@ def run_tode(args):
         kf = {"achieved": flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12,
               "kernel": "k_fused<LinearField<float,2,8>> (fused forward)", "kernel_ms": k_fwd_ms}
         ka = {"achieved": adjoint_flops_per_step(kind, D) * n_acc_total / (k_adj_ms * 1e-3)
-              / 1e12, "kernel": "k_adjoint<LinearAdj<float,2,8>>", "kernel_ms": k_adj_ms}
+              / 1e12, "kernel": "k_adjoint<LinearAdj<float,1,16>> (stride-1 tape, 16 lanes)", "kernel_ms": k_adj_ms}
         for r in (kf, ka):
             r.update(bound="alu", peak=fp32_peak, unit="TFLOP/s",
                      frac=r["achieved"] / fp32_peak, traffic=None, peak_source=psrc)
@@ -467,8 +494,13 @@ def cpu_baseline(w, budget_s=12.0, nthreads=0, with_adjoint=True):
     while dt < budget_s / 4 and n < w["B"]:
         n = min(w["B"], int(n * max(2.0, budget_s / max(dt, 1e-3) * 0.8)))
         att, dt, thr = run(n)
+    passes = 1
+    while dt < budget_s / 2:  # the whole workload is quick: repeat it
+        a2, d2, thr = run(n)
+        att, dt, passes = att + a2, dt + d2, passes + 1
     return {"value": att / dt, "unit": "instance-steps/s", "cores": thr, "kind": "oracle",
-            "sample": f"first {n} of {w['B']} instances of {w['name']}, "
+            "sample": f"first {n} of {w['B']} instances of {w['name']}"
+                      f"{f' x {passes} passes' if passes > 1 else ''}, "
                       f"{'fwd+adjoint' if with_adjoint else 'fwd'}, {dt:.1f} s"}
 
 

@@ -46,16 +46,28 @@ template <typename T> struct VdpAdj {
 
 template <typename T, int R_, int G_> struct LinearAdj {
   static constexpr int R = R_, G = G_, D = R_ * G_;
+  // One column per lane (R = 1) stays in registers; wider lanes read their
+  // columns through the L1 cache to keep the register count at two CTAs/SM.
+  static constexpr bool REG_COLS = (R == 1);
   LinearField<T, R, G> f;
-  const T* acol;  // column g*R of A_i: A[j][g*R + r] = acol[j*D + r] (read through the cache)
-  T gA[R][D];     // columns g*R+r of dL/dA_i: gA[r][j] = dL/dA[j][g*R + r]
+  const T* acol;       // column g*R of A_i: A[j][g*R + r] = acol[j*D + r]
+  T acr[REG_COLS ? D : 1];  // R = 1: the column itself
+  T gA[R][D];          // columns g*R+r of dL/dA_i: gA[r][j] = dL/dA[j][g*R + r]
   __device__ __forceinline__ void load(const T* p, int i) {
     f.load(p, i);
     acol = p + (size_t)i * D * D + Grp<G>::rank() * R;
+    if constexpr (REG_COLS) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) acr[j] = acol[j * D];
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
       for (int j = 0; j < D; ++j) gA[r][j] = T(0);
+  }
+  __device__ __forceinline__ T a_col(int j, int r) const {
+    if constexpr (REG_COLS) return acr[j];
+    else return __ldg(acol + j * D + r);
   }
   __device__ __forceinline__ void eval(double t, const T (&y)[R], T (&o)[R]) const {
     f.eval(t, y, o);
@@ -70,16 +82,16 @@ template <typename T, int R_, int G_> struct LinearAdj {
       if constexpr (sizeof(T) == 8 || D < 8) {
         T s = T(0);  // FP64: left-to-right (the oracle's order)
 #pragma unroll
-        for (int j = 0; j < D; ++j) s = madd(__ldg(acol + j * D + r), vall[j], s);
+        for (int j = 0; j < D; ++j) s = madd(a_col(j, r), vall[j], s);
         gy[r] = s;
       } else {
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
         for (int j = 0; j < D; j += 4) {
-          s0 = madd(__ldg(acol + j * D + r), vall[j], s0);
-          s1 = madd(__ldg(acol + (j + 1) * D + r), vall[j + 1], s1);
-          s2 = madd(__ldg(acol + (j + 2) * D + r), vall[j + 2], s2);
-          s3 = madd(__ldg(acol + (j + 3) * D + r), vall[j + 3], s3);
+          s0 = madd(a_col(j, r), vall[j], s0);
+          s1 = madd(a_col(j + 1, r), vall[j + 1], s1);
+          s2 = madd(a_col(j + 2, r), vall[j + 2], s2);
+          s3 = madd(a_col(j + 3, r), vall[j + 3], s3);
         }
         gy[r] = (s0 + s1) + (s2 + s3);
       }
@@ -424,11 +436,17 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   return TODE_OK;
 }
 
-// The adjoint re-runs the forward's attempts, so it must use the forward's
-// lane grouping (linear_group): the FP32 error norm's butterfly order, and
-// with it the recomputed mesh, depends on the group size.
+// A strided tape makes the adjoint re-run the forward's attempts, so it must
+// use the forward's lane grouping (linear_group): the FP32 error norm's
+// butterfly order, and with it the recomputed mesh, depends on the group
+// size.  A stride-1 tape with the accepted step sizes is reversed directly,
+// and reversing a step gives the same bits for every grouping (each lane
+// holds whole rows and columns), so D = 16 then takes 16 lanes with A's
+// column in registers (measured fastest for the adjoint).
 template <typename T> tode_err simt_adjoint(const AdjReq& r) {
   if (r.f->kind == TODE_VDP) return launch_adjoint<VdpAdj<T>, T>(r);
+  const bool direct = r.tape->stride == 1 && r.tape->h_acc != nullptr;
+  if (direct && r.D == 16) return launch_adjoint<LinearAdj<T, 1, 16>, T>(r);
   switch (linear_group(r.D, r.o->group)) {
     case 1: return launch_adjoint<LinearAdj<T, 1, 1>, T>(r);
     case 2: return launch_adjoint<LinearAdj<T, 1, 2>, T>(r);
