@@ -128,7 +128,11 @@ template <int D_, int H_, int NL_, bool SPLIT_> struct MlpCfg {
   static constexpr int S_RED = S_BIAS + BIAS_FLOATS * 4;
   static constexpr int S_FIN = S_RED + 2 * 128 * 2 * 4;
   static constexpr int S_NXT = S_FIN + 2 * 128 * 4;
-  static constexpr int S_END = S_NXT + 128 * 4;
+  // stage derivatives k2..k6 of every thread: [stage][float4][thread]
+  static constexpr bool KSMEM = true;
+  static constexpr int S_K = S_NXT + 128 * 4;
+  static constexpr int S_END = S_K + 5 * 4 * NT * 16;
+  static_assert(S_END <= 232448 - 1024, "shared memory");
   static_assert(D % 32 == 0 && H % 32 == 0 && NL >= 2 && NL <= MLP_MAX_LAYERS, "shape");
   static_assert(H <= 256 && D <= 256, "one MMA per layer and K slice");
 };
@@ -200,6 +204,8 @@ template <int D_, int H_, int NL_> struct MlpBigCfg {
   static constexpr int S_RED = S_BIAS + BIAS_FLOATS * 4;
   static constexpr int S_FIN = S_RED + TPR * ROWS * 2 * 4;
   static constexpr int S_NXT = S_FIN + TPR * ROWS * 4;
+  static constexpr bool KSMEM = false;  // no room: the stage derivatives stay in the thread
+  static constexpr int S_K = 0;
   static constexpr int S_END = S_NXT + ROWS * 4;
   static_assert(S_END <= 232448 - 1024, "shared memory");
 };
@@ -242,6 +248,33 @@ __device__ __forceinline__ void store_row16(unsigned char* th, unsigned char* tl
   }
 }
 
+// a_{s,j} of the tableau (stage 7 row = b), as float; s = 2..7, j = 1..6
+__device__ __forceinline__ float dp_a(int s, int j) {
+  using C = DP5;
+  switch (s * 8 + j) {
+    case 17: return float(C::a21);
+    case 25: return float(C::a31);
+    case 26: return float(C::a32);
+    case 33: return float(C::a41);
+    case 34: return float(C::a42);
+    case 35: return float(C::a43);
+    case 41: return float(C::a51);
+    case 42: return float(C::a52);
+    case 43: return float(C::a53);
+    case 44: return float(C::a54);
+    case 49: return float(C::a61);
+    case 50: return float(C::a62);
+    case 51: return float(C::a63);
+    case 52: return float(C::a64);
+    case 53: return float(C::a65);
+    case 57: return float(C::b1);
+    case 59: return float(C::b3);
+    case 60: return float(C::b4);
+    case 61: return float(C::b5);
+    case 62: return float(C::b6);
+    default: return 0.0f;
+  }
+}
 // Per-row solver state (identical scalars in both threads of the row).
 struct MlpRow {
   int inst, phase, cursor, status, flags, n_acc, n_rej;
@@ -344,13 +377,35 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   MlpRow s;
   s.inst = -1;
   s.phase = PH_IDLE;
-  float y[C], ylo[C], k[7][C];
+  // k1 (FSAL) in registers; k2..k6 of the attempt in shared memory when the
+  // config has room (else in the thread's local array); k7 is the last f
+  float y[C], ylo[C], k1[C];
 #pragma unroll
-  for (int r = 0; r < C; ++r) {
-    y[r] = ylo[r] = 0.0f;
+  for (int r = 0; r < C; ++r) y[r] = ylo[r] = k1[r] = 0.0f;
+  float kloc[Cfg::KSMEM ? 1 : 5][C];
+  float4* sK = reinterpret_cast<float4*>(sm + Cfg::S_K);
+  auto kput = [&](int j, const float (&v)[16]) {  // stage j = 2..6
+    if constexpr (Cfg::KSMEM) {
 #pragma unroll
-    for (int j = 0; j < 7; ++j) k[j][r] = 0.0f;
-  }
+      for (int q = 0; q < 4; ++q)
+        sK[((j - 2) * 4 + q) * NT + tid] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < C; ++r) kloc[j - 2][r] = v[r];
+    }
+  };
+  auto kget = [&](int j, float (&v)[16]) {
+    if constexpr (Cfg::KSMEM) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 u = sK[((j - 2) * 4 + q) * NT + tid];
+        v[4 * q] = u.x, v[4 * q + 1] = u.y, v[4 * q + 2] = u.z, v[4 * q + 3] = u.w;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < C; ++r) v[r] = kloc[j - 2][r];
+    }
+  };
   bool need_grab = MODE == MLP_FUSED;  // fused: this row takes the next instance
   bool need_load = MODE != MLP_FUSED;  // plain: this row loads its instance of the tile
   int tile = blockIdx.x;
@@ -430,7 +485,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       const size_t o = (size_t)i * D + coff + r;
       a.wy[o] = y[r];
       a.wylo[o] = ylo[r];
-      a.wk1[o] = k[0][r];
+      a.wk1[o] = k1[r];
     }
     if (sub == 0) {
       a.wt[i] = s.t;
@@ -469,7 +524,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       const size_t o = (size_t)i * D + coff + r;
       y[r] = a.wy[o];
       ylo[r] = a.wylo[o];
-      k[0][r] = a.wk1[o];
+      k1[r] = a.wk1[o];
     }
     s.phase = PH_STAGE;
   };
@@ -526,7 +581,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       tin = (float)s.t;
     } else if (s.phase == PH_INIT1) {
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = madd(s.h0h, k[0][r], y[r]);
+      for (int r = 0; r < C; ++r) Y[r] = madd(s.h0h, k1[r], y[r]);
       tin = (float)(s.t + (double)s.h0h);
     } else {
       if (stage == 2) {  // a new attempt starts: clip at t1
@@ -540,45 +595,22 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       }
       const float h = s.h;
       double cs = 0.0;
+      // Y_s = y + h sum_j a_sj k_j, the terms in the order j = 1, 2, ...
+      // (the stage-7 row is b, which has no k2 term)
+      float acc[16];
+      const float a1 = dp_a(stage, 1);
 #pragma unroll
-      for (int r = 0; r < C; ++r) {
-        float acc;
-        switch (stage) {
-          case 2:
-            acc = float(Cc::a21) * k[0][r];
-            break;
-          case 3:
-            acc = float(Cc::a31) * k[0][r];
-            acc = madd(float(Cc::a32), k[1][r], acc);
-            break;
-          case 4:
-            acc = float(Cc::a41) * k[0][r];
-            acc = madd(float(Cc::a42), k[1][r], acc);
-            acc = madd(float(Cc::a43), k[2][r], acc);
-            break;
-          case 5:
-            acc = float(Cc::a51) * k[0][r];
-            acc = madd(float(Cc::a52), k[1][r], acc);
-            acc = madd(float(Cc::a53), k[2][r], acc);
-            acc = madd(float(Cc::a54), k[3][r], acc);
-            break;
-          case 6:
-            acc = float(Cc::a61) * k[0][r];
-            acc = madd(float(Cc::a62), k[1][r], acc);
-            acc = madd(float(Cc::a63), k[2][r], acc);
-            acc = madd(float(Cc::a64), k[3][r], acc);
-            acc = madd(float(Cc::a65), k[4][r], acc);
-            break;
-          default:  // 7: the new solution (SSAL)
-            acc = float(Cc::b1) * k[0][r];
-            acc = madd(float(Cc::b3), k[2][r], acc);
-            acc = madd(float(Cc::b4), k[3][r], acc);
-            acc = madd(float(Cc::b5), k[4][r], acc);
-            acc = madd(float(Cc::b6), k[5][r], acc);
-            break;
-        }
-        Y[r] = (stage == 7) ? y[r] + h * acc : madd(h, acc, y[r]);
+      for (int r = 0; r < C; ++r) acc[r] = a1 * k1[r];
+      for (int j = 2; j < stage && j <= 6; ++j) {
+        if (stage == 7 && j == 2) continue;
+        float kj[16];
+        kget(j, kj);
+        const float c = dp_a(stage, j);
+#pragma unroll
+        for (int r = 0; r < C; ++r) acc[r] = madd(c, kj[r], acc[r]);
       }
+#pragma unroll
+      for (int r = 0; r < C; ++r) Y[r] = (stage == 7) ? y[r] + h * acc[r] : madd(h, acc[r], y[r]);
       switch (stage) {
         case 2: cs = Cc::c2; break;
         case 3: cs = Cc::c3; break;
@@ -698,10 +730,11 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     float p0 = 0.0f, p1 = 0.0f;
     int fin = 1;
     float inc[16];
+    float k3[16], k4[16], k5[16], k6[16];  // stage 7: the attempt's k3..k6
     if (s.phase == PH_INIT0) {
 #pragma unroll
       for (int r = 0; r < C; ++r) {
-        k[0][r] = f[r];
+        k1[r] = f[r];
         const float sc = madd(s.rtol, fabsf(y[r]), s.atol);
         const float q0 = y[r] / sc, q1 = f[r] / sc;
         p0 = madd(q0, q0, p0);
@@ -711,32 +744,31 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
 #pragma unroll
       for (int r = 0; r < C; ++r) {
         const float sc = madd(s.rtol, fabsf(y[r]), s.atol);
-        const float q = (f[r] - k[0][r]) / sc;
+        const float q = (f[r] - k1[r]) / sc;
         p0 = madd(q, q, p0);
       }
     } else if (s.phase >= PH_STAGE) {
-#pragma unroll
-      for (int j = 1; j < 7; ++j)
-        if (j == stage - 1) {
-#pragma unroll
-          for (int r = 0; r < C; ++r) k[j][r] = f[r];
-        }
+      if (stage < 7) kput(stage, f);
       if (stage == 7) {
+        kget(3, k3);
+        kget(4, k4);
+        kget(5, k5);
+        kget(6, k6);
 #pragma unroll
         for (int r = 0; r < C; ++r) {
-          float acc = float(Cc::b1) * k[0][r];
-          acc = madd(float(Cc::b3), k[2][r], acc);
-          acc = madd(float(Cc::b4), k[3][r], acc);
-          acc = madd(float(Cc::b5), k[4][r], acc);
-          acc = madd(float(Cc::b6), k[5][r], acc);
+          float acc = float(Cc::b1) * k1[r];
+          acc = madd(float(Cc::b3), k3[r], acc);
+          acc = madd(float(Cc::b4), k4[r], acc);
+          acc = madd(float(Cc::b5), k5[r], acc);
+          acc = madd(float(Cc::b6), k6[r], acc);
           inc[r] = s.h * acc;
           const float y1 = y[r] + inc[r];
-          float e = float(Cc::e1) * k[0][r];
-          e = madd(float(Cc::e3), k[2][r], e);
-          e = madd(float(Cc::e4), k[3][r], e);
-          e = madd(float(Cc::e5), k[4][r], e);
-          e = madd(float(Cc::e6), k[5][r], e);
-          e = madd(float(Cc::e7), k[6][r], e);
+          float e = float(Cc::e1) * k1[r];
+          e = madd(float(Cc::e3), k3[r], e);
+          e = madd(float(Cc::e4), k4[r], e);
+          e = madd(float(Cc::e5), k5[r], e);
+          e = madd(float(Cc::e6), k6[r], e);
+          e = madd(float(Cc::e7), f[r], e);
           e = s.h * e;
           const float sc = madd(s.rtol, tmax(fabsf(y[r]), fabsf(y1)), s.atol);
           const float q = e / sc;
@@ -814,7 +846,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
 #pragma unroll
           for (int r = 0; r < C; ++r) {
             a.tp_y[o * D + coff + r] = y[r];
-            a.tp_k1[o * D + coff + r] = k[0][r];
+            a.tp_k1[o * D + coff + r] = k1[r];
           }
           if (sub == 0) {
             a.tp_t[o] = s.t;
@@ -844,12 +876,12 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
             dense_weights<float>(th, w);
 #pragma unroll
             for (int r = 0; r < C; ++r) {
-              float acc = w[0] * k[0][r];
-              acc = madd(w[2], k[2][r], acc);
-              acc = madd(w[3], k[3][r], acc);
-              acc = madd(w[4], k[4][r], acc);
-              acc = madd(w[5], k[5][r], acc);
-              acc = madd(w[6], k[6][r], acc);
+              float acc = w[0] * k1[r];
+              acc = madd(w[2], k3[r], acc);
+              acc = madd(w[3], k4[r], acc);
+              acc = madd(w[4], k5[r], acc);
+              acc = madd(w[5], k6[r], acc);
+              acc = madd(w[6], f[r], acc);
               dst[r] = y[r] + madd(h, acc, ylo[r]);
             }
           }
@@ -873,7 +905,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         for (int r = 0; r < C; ++r) {
           y[r] = yn[r];
           ylo[r] = ylon[r];
-          k[0][r] = k[6][r];  // FSAL
+          k1[r] = f[r];  // FSAL: k1 <- k7
         }
         if (last) s.status = ST_SUCCESS;
         else s.rem = __double2float_rd(s.t1 - s.t);
@@ -1038,33 +1070,6 @@ struct MlpAdjArgs {
 
 constexpr int ADJ_ROUNDS = 12;
 
-// a_{s,j} of the tableau (stage 7 row = b), as float; s = 2..7, j = 1..6
-__device__ __forceinline__ float dp_a(int s, int j) {
-  using C = DP5;
-  switch (s * 8 + j) {
-    case 17: return float(C::a21);
-    case 25: return float(C::a31);
-    case 26: return float(C::a32);
-    case 33: return float(C::a41);
-    case 34: return float(C::a42);
-    case 35: return float(C::a43);
-    case 41: return float(C::a51);
-    case 42: return float(C::a52);
-    case 43: return float(C::a53);
-    case 44: return float(C::a54);
-    case 49: return float(C::a61);
-    case 50: return float(C::a62);
-    case 51: return float(C::a63);
-    case 52: return float(C::a64);
-    case 53: return float(C::a65);
-    case 57: return float(C::b1);
-    case 59: return float(C::b3);
-    case 60: return float(C::b4);
-    case 61: return float(C::b5);
-    case 62: return float(C::b6);
-    default: return 0.0f;
-  }
-}
 __device__ __forceinline__ double dp_c(int s) {
   using C = DP5;
   return s == 2 ? C::c2 : s == 3 ? C::c3 : s == 4 ? C::c4 : s == 5 ? C::c5 : s >= 6 ? 1.0 : 0.0;
