@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2210_12375_b300 import workloads  # noqa: E402
+from paper_2210_12375_b300.dist import max_over_ranks  # noqa: E402
 
 METRIC = "instance-steps/s, dopri5 fwd and fwd+adjoint, fused vs plain form at matched error"
 L2_FLUSH_BYTES = 256 << 20
@@ -248,10 +249,8 @@ def run_tode(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t_wall
         ms = float(sum(a.elapsed_time(b) for a, b in ev))
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        if world > 1:  # the slowest rank's time (instances are independent: no other exchange)
+            ms = max_over_ranks(ms, dev)
             dist.barrier()
         return ms, wall
 
@@ -367,9 +366,7 @@ def run_tode(args):
         torch.cuda.synchronize()
         ms_e2e = e_start.elapsed_time(e_end) / nk
         if world > 1:
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+            ms_e2e = max_over_ranks(ms_e2e, dev)
         e2e = {"value": world * n_att / (ms_e2e * 1e-3), "unit": "instance-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": ms_e2e,
