@@ -393,10 +393,15 @@ def run_tode(args):
                      traffic=None, peak_source=f"bf16 burst, {src} (MEASURED_PEAKS.json)")
     else:
         psrc = f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {clk_mhz:.0f} MHz"
+        tn = "double" if dtype == torch.float64 else "float"
+        if kind == "linear":  # lanes per instance: 8 forward, 16 for the direct adjoint
+            fld, adj = f"LinearField<{tn},2,8>", f"LinearAdj<{tn},1,16>"
+        else:
+            fld, adj = f"VdpField<{tn}>", f"VdpAdj<{tn}>"
         kf = {"achieved": flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12,
-              "kernel": "k_fused<LinearField<float,2,8>> (fused forward)", "kernel_ms": k_fwd_ms}
+              "kernel": f"k_fused<{fld}> (fused forward)", "kernel_ms": k_fwd_ms}
         ka = {"achieved": adjoint_flops_per_step(kind, D) * n_acc_total / (k_adj_ms * 1e-3)
-              / 1e12, "kernel": "k_adjoint<LinearAdj<float,1,16>> (stride-1 tape, 16 lanes)", "kernel_ms": k_adj_ms}
+              / 1e12, "kernel": f"k_adjoint<{adj}> (stride-1 tape)", "kernel_ms": k_adj_ms}
         for r in (kf, ka):
             r.update(bound="alu", peak=fp32_peak, unit="TFLOP/s",
                      frac=r["achieved"] / fp32_peak, traffic=None, peak_source=psrc)
