@@ -200,7 +200,7 @@ def run_tode(args):
     n_acc_max = int(probe.n_acc.max().item())
     # every field has both forms and the adjoint (--fwd-only drops the latter)
     with_adjoint = not args.fwd_only
-    tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev)
+    tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev, stages=mlp)
 
     def fwd(form, sol=None, ws=None):
         return tode.solve(field, y0, t0, t1, te, form=form, tape=tape, out=sol, workspace=ws,

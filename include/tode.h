@@ -124,7 +124,8 @@ typedef struct {
  * With stride 1 and h_acc given (the same tape struct for both calls), every
  * accepted step is on the tape with its size and tode_adjoint reverses it
  * directly, without re-running the forward's attempts.
- * MLP field: stride must be 1 and only y, k1, t and h_acc are used. */
+ * MLP field: stride must be 1; y, k1, t, h_acc and y_stage are used (the
+ * adjoint reverses every step from its recorded stage inputs). */
 typedef struct {
   int slots;
   int stride;
@@ -139,6 +140,9 @@ typedef struct {
   void* h_acc;      /* [slots][B] state dtype: size of the accepted step that
                        starts at the slot (written when that step is accepted;
                        required for the MLP field, optional otherwise) */
+  void* y_stage;    /* [slots][B][6][D] state dtype: the stage inputs Y_2..Y_7
+                       of the accepted step (MLP field: required; other fields
+                       ignore it, may be NULL) */
 } tode_tape;
 
 /* Per-attempt trace (testing and diagnostics): for instance i, attempt n <

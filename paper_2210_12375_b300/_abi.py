@@ -74,6 +74,7 @@ class Tape(C.Structure):
         ("err_prev", _vp),
         ("flags", _vp),
         ("h_acc", _vp),
+        ("y_stage", _vp),
     ]
 
 

@@ -150,7 +150,9 @@ def _ptr(t: Optional[torch.Tensor]):
 @dataclass
 class TapeBuffers:
     """Checkpoint tape for the adjoint: slot j = solver state at the start of
-    accepted step j*stride (state, FSAL stage, time, step, controller)."""
+    accepted step j*stride (state, FSAL stage, time, step, controller); with
+    ``stages`` (required for the MLP field) also the stage inputs Y_2..Y_7 of
+    every accepted step."""
     slots: int
     stride: int
     y: torch.Tensor
@@ -161,9 +163,10 @@ class TapeBuffers:
     err_prev: torch.Tensor
     flags: torch.Tensor
     h_acc: Optional[torch.Tensor]  # None: the adjoint re-runs each segment's attempts
+    y_stage: Optional[torch.Tensor] = None  # [slots, B, 6, D]: Y_2..Y_7 (MLP field)
 
     @staticmethod
-    def allocate(B, D, dtype, slots, stride, device):
+    def allocate(B, D, dtype, slots, stride, device, stages: bool = False):
         comp = (slots, B, D) if dtype != torch.float64 else (1,)
         return TapeBuffers(slots, stride,
                            torch.empty((slots, B, D), dtype=dtype, device=device),
@@ -173,12 +176,15 @@ class TapeBuffers:
                            torch.empty((slots, B), dtype=dtype, device=device),
                            torch.empty((slots, B), dtype=dtype, device=device),
                            torch.empty((slots, B), dtype=torch.int32, device=device),
-                           torch.empty((slots, B), dtype=dtype, device=device))
+                           torch.empty((slots, B), dtype=dtype, device=device),
+                           torch.empty((slots, B, 6, D), dtype=dtype, device=device)
+                           if stages else None)
 
     @staticmethod
-    def bytes_per_slot(B, D, itemsize):
+    def bytes_per_slot(B, D, itemsize, stages: bool = False):
         comp = D * itemsize if itemsize == 4 else 0
-        return B * (2 * D * itemsize + comp + 8 + 3 * itemsize + 4)
+        return B * (2 * D * itemsize + comp + 8 + 3 * itemsize + 4 +
+                    (6 * D * itemsize if stages else 0))
 
     def c(self) -> _abi.Tape:
         tp = _abi.Tape()
@@ -187,6 +193,7 @@ class TapeBuffers:
         tp.t, tp.h = self.t.data_ptr(), self.h.data_ptr()
         tp.err_prev, tp.flags = self.err_prev.data_ptr(), self.flags.data_ptr()
         tp.h_acc = self.h_acc.data_ptr() if self.h_acc is not None else None
+        tp.y_stage = self.y_stage.data_ptr() if self.y_stage is not None else None
         return tp
 
 

@@ -56,7 +56,8 @@ static tode_err field_ok(const tode_field_desc* f, const tode_options* o) {
 
 static bool tape_ok(const tode_tape* tp, const tode_options* o, const tode_field_desc* f) {
   if (f->kind == TODE_MLP)
-    return tp->slots >= 1 && tp->stride == 1 && tp->y && tp->k1 && tp->t && tp->h_acc;
+    return tp->slots >= 1 && tp->stride == 1 && tp->y && tp->k1 && tp->t && tp->h_acc &&
+           tp->y_stage;
   return tp->slots >= 1 && tp->stride >= 1 && tp->y && tp->k1 && tp->t && tp->h &&
          tp->err_prev && tp->flags && (o->prec == TODE_F64 || tp->y_lo);
 }

@@ -62,6 +62,7 @@ struct MlpArgs {
   float* tp_k1;
   double* tp_t;
   float* tp_h;
+  float* tp_ys;  // [slots][B][6][D]: stage inputs Y_2..Y_7 of the accepted step
   // plain form: solver state between launches, and the "some instance is
   // still running" flag the host polls
   float* wy;
@@ -621,6 +622,15 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       tin = (float)(s.t + cs * (double)h);
     }
     store_row16<true>(sXh, sXl, row, coff, K0, Y);
+    if (s.phase >= PH_STAGE && s.n_acc < a.slots) {
+      // tape: the stage inputs of this attempt (a retry after a rejection
+      // overwrites them; the accepted attempt's stay)
+      float4* dst = reinterpret_cast<float4*>(
+          a.tp_ys + (((size_t)s.n_acc * a.B + s.inst) * 6 + (stage - 2)) * D + coff);
+#pragma unroll
+      for (int q = 0; q < C / 4; ++q)
+        dst[q] = make_float4(Y[4 * q], Y[4 * q + 1], Y[4 * q + 2], Y[4 * q + 3]);
+    }
     if (sub == TPR - 1) {  // the time input, hi + lo, in column D
       const __nv_bfloat16 th = __float2bfloat16_rn(tin);
       const __nv_bfloat16 tl = __float2bfloat16_rn(tin - __bfloat162float(th));
@@ -994,11 +1004,10 @@ __global__ void k_mlp_weight_image(const uint16_t* __restrict__ W, int N, int Ki
 // Rows of a 128-row tile reverse their own instances (assigned statically,
 // row r of CTA c takes instances c*128 + r, c*128 + r + 128*grid, ..., so the
 // weight gradients are summed in a fixed order).  Reversing one accepted step
-// takes 12 rounds for every row, so all rows of a tile stay in step:
-//   rounds 0..4   recompute stages 2..6: forward layers at Y_s, f = k_s
-//   rounds 5..11  reverse stages 7..1: hidden layers at Y_s, then the
-//                 backward chain for the stage cotangent kbar_s
-// A reverse round, for the whole tile:
+// takes 7 rounds for every row (stages 7..1), so all rows of a tile stay in
+// step; the forward recorded each accepted step's stage inputs Y_2..Y_7, so a
+// round runs the hidden layers at Y_s and then the backward chain for the
+// stage cotangent kbar_s.  A round, for the whole tile:
 //   gh2 = kbar W3        dW3^T += h2^T kbar          (h2: split BF16 tile)
 //   delta2 = gh2 (1 - h2^2)
 //   gh1 = delta2 W2      dW2 += delta2^T h1, db2 += delta2^T 1
@@ -1007,9 +1016,7 @@ __global__ void k_mlp_weight_image(const uint16_t* __restrict__ W, int N, int Ki
 // Transposed operands are the same shared-memory tiles read MN-major; dW
 // accumulates in tensor memory over the whole kernel and is written once
 // per CTA as a partial, which k_mlp_grad_reduce sums over CTAs in order.
-// The stage inputs Y_2..Y_6 of the step being reversed wait in tensor memory
-// between the recompute and the reverse rounds; Y_7 comes from the stage
-// sums still in registers, Y_1 is the step's start.
+// Y_1 is the step's start, Y_2..Y_7 come from the tape.
 // ======================================================================
 template <class Cfg> struct MlpAdjLayout {
   static constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0;
@@ -1030,13 +1037,8 @@ template <class Cfg> struct MlpAdjLayout {
   static_assert(S_END <= 232448 - 1024, "shared memory");
   // tensor memory columns: accumulators on 32-column boundaries
   //   R [0,128)  D1 [128,256)  D0 [256,304)  DB [320,336)  D2 [352,384)
-  // and ten 16-column halves of the stage inputs Y_2..Y_6 in the gaps
   static constexpr uint32_t T_R = 0, T_D1 = 128, T_D0 = 256, T_DB = 320, T_D2 = 352,
                             T_COLS = 512;
-  __device__ static uint32_t y_col(int s, int half) {
-    const int u = (s - 2) * 2 + half;  // 0..9
-    return u == 0 ? 304u : (u == 1 ? 336u : 384u + 16u * (uint32_t)(u - 2));
-  }
   // per-CTA partial gradient block (floats)
   static constexpr int P_W0 = 0;                 // [H][K0]  (col D: t weight, col D+1: db1)
   static constexpr int P_W1 = P_W0 + H * K0;     // [H][H]
@@ -1058,6 +1060,7 @@ struct MlpAdjArgs {
   const float* tp_k1;
   const double* tp_t;
   const float* tp_h;
+  const float* tp_ys;  // [slots][B][6][D]: Y_2..Y_7
   const float* gye;
   const float* gyf;
   float* gy0;
@@ -1068,7 +1071,7 @@ struct MlpAdjArgs {
   int32_t* err;
 };
 
-constexpr int ADJ_ROUNDS = 12;
+constexpr int ADJ_ROUNDS = 7;  // one reverse round per stage, 7..1
 
 __device__ __forceinline__ double dp_c(int s) {
   using C = DP5;
@@ -1172,35 +1175,34 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   bool bad = false;
   double tn = 0.0, tnext = 0.0;
   float h = 0.0f;
-  float yn[16], yb[16], db3[16], kb[7][16];
+  float yb[16], db3[16], kb[7][16];
 #pragma unroll
   for (int r = 0; r < C; ++r) {
-    yn[r] = yb[r] = db3[r] = 0.0f;
+    yb[r] = db3[r] = 0.0f;
 #pragma unroll
     for (int j = 0; j < 7; ++j) kb[j][r] = 0.0f;
   }
 
-  // step n of instance i: its start, and the stage sums acc_s = a_s1 k1
-  // (kb[s-1], s = 2..7) that the recompute rounds complete
+  // step n of instance i: its time and size (the stage inputs come from the
+  // tape round by round)
   auto load_step = [&](int i) {
     const size_t o = (size_t)n * a.B + i;
-    const float4* py = reinterpret_cast<const float4*>(a.tp_y + o * D + coff);
-    const float4* pk = reinterpret_cast<const float4*>(a.tp_k1 + o * D + coff);
-    float k1[16];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const float4 u = py[v], w = pk[v];
-      yn[4 * v] = u.x, yn[4 * v + 1] = u.y, yn[4 * v + 2] = u.z, yn[4 * v + 3] = u.w;
-      k1[4 * v] = w.x, k1[4 * v + 1] = w.y, k1[4 * v + 2] = w.z, k1[4 * v + 3] = w.w;
-    }
     tn = a.tp_t[o];
     h = a.tp_h[o];
     tnext = (n == N - 1) ? a.t1[i] : tn + (double)h;
-#pragma unroll
-    for (int j = 1; j < 7; ++j)
-#pragma unroll
-      for (int r = 0; r < C; ++r) kb[j][r] = dp_a(j + 1, 1) * k1[r];
     act = true;
+  };
+  // Y_s of the step being reversed: Y_1 = y_n, Y_2..Y_7 as the forward recorded
+  auto load_stage = [&](int s_, float (&Yo)[16]) {
+    const size_t o = (size_t)n * a.B + inst;
+    const float4* p = s_ == 1
+        ? reinterpret_cast<const float4*>(a.tp_y + o * D + coff)
+        : reinterpret_cast<const float4*>(a.tp_ys + (o * 6 + (s_ - 2)) * D + coff);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float4 u = p[v];
+      Yo[4 * v] = u.x, Yo[4 * v + 1] = u.y, Yo[4 * v + 2] = u.z, Yo[4 * v + 3] = u.w;
+    }
   };
   // finish the current instance (if `finishing`) and move to the next one
   // that has a step to reverse
@@ -1304,73 +1306,53 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   for (int rnd = 0;; ++rnd) {
     const int ph = rnd % ADJ_ROUNDS;
     if (ph == 0 && __syncthreads_or(act) == 0) break;
-    const bool rev = ph >= 5;
-    const int s = rev ? 12 - ph : ph + 2;  // stage of this round (block-uniform)
+    const int s = 7 - ph;  // stage reversed this round (block-uniform)
 
-    // ---- stage input [Y_s; t_s] and, in reverse rounds, the cotangent kbar_s
+    // ---- stage input [Y_s; t_s] and the cotangent kbar_s of this row
     float Y[16], d3[16];
     float tin = 0.0f;
-    if (!rev) {
-      float acc[16];
-      pick7(kb, s - 1, acc);
+    if (act && s == 7) {
+      // kbar_i = h b_i ybar_{n+1} + sum_{tau in step} h b_i(theta_tau) ybar_tau
+      const int i = inst;
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = act ? madd(h, acc[r], yn[r]) : 0.0f;
-      tc::tmem_st16(tl + L::y_col(s, half), Y);  // kept for the reverse round
-      tc::tmem_wait_st();
-    } else if (s == 7) {
+      for (int j = 0; j < 7; ++j)
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = act ? yn[r] + h * kb[6][r] : 0.0f;
-      if (act) {
-        // kbar_i = h b_i ybar_{n+1} + sum_{tau in step} h b_i(theta_tau) ybar_tau
-        const int i = inst;
+        for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
+      const long long kt = tkey(tn), kn = tkey(tnext);
+      while (q >= 0) {
+        const double tq = a.te[(size_t)i * a.K + q];
+        const long long kq = tkey(tq);
+        if (!(kq > kt)) break;
+        if (a.gye) {
+          float gq[16], w[7];
 #pragma unroll
-        for (int j = 0; j < 7; ++j)
+          for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + coff + r];
+          if (kq == kn) {
 #pragma unroll
-          for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
-        const long long kt = tkey(tn), kn = tkey(tnext);
-        while (q >= 0) {
-          const double tq = a.te[(size_t)i * a.K + q];
-          const long long kq = tkey(tq);
-          if (!(kq > kt)) break;
-          if (a.gye) {
-            float gq[16], w[7];
-#pragma unroll
-            for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + coff + r];
-            if (kq == kn) {
-#pragma unroll
-              for (int j = 0; j < 7; ++j) w[j] = bw[j];
-            } else {
-              dense_weights<float>(float(tq - tn) / h, w);
-            }
-#pragma unroll
-            for (int j = 0; j < 7; ++j)
-#pragma unroll
-              for (int r = 0; r < C; ++r) kb[j][r] = madd(h * w[j], gq[r], kb[j][r]);
-#pragma unroll
-            for (int r = 0; r < C; ++r) yb[r] += gq[r];
+            for (int j = 0; j < 7; ++j) w[j] = bw[j];
+          } else {
+            dense_weights<float>(float(tq - tn) / h, w);
           }
-          q--;
-        }
-      }
-    } else if (s >= 2) {
-      tc::tmem_ld16(tl + L::y_col(s, half), Y);
-      tc::tmem_wait_ld();
-      if (!act)
 #pragma unroll
-        for (int r = 0; r < C; ++r) Y[r] = 0.0f;
+          for (int j = 0; j < 7; ++j)
+#pragma unroll
+            for (int r = 0; r < C; ++r) kb[j][r] = madd(h * w[j], gq[r], kb[j][r]);
+#pragma unroll
+          for (int r = 0; r < C; ++r) yb[r] += gq[r];
+        }
+        q--;
+      }
+    }
+    if (act) {
+      load_stage(s, Y);
+      tin = (float)(tn + dp_c(s) * (double)h);
+      pick7(kb, s - 1, d3);
     } else {
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = act ? yn[r] : 0.0f;
-    }
-    if (act) tin = (float)(tn + dp_c(s) * (double)h);
-    if (rev) {
-      pick7(kb, s - 1, d3);
-      if (!act)
-#pragma unroll
-        for (int r = 0; r < C; ++r) d3[r] = 0.0f;
-      store_row16<true>(sD3h, sD3l, row, coff, D, d3);
+      for (int r = 0; r < C; ++r) Y[r] = d3[r] = 0.0f;
     }
     store_row16<true>(sXh, sXl, row, coff, K0, Y);
+    store_row16<true>(sD3h, sD3l, row, coff, D, d3);
     if (half == 1) {
       const __nv_bfloat16 th = __float2bfloat16_rn(tin);
       const __nv_bfloat16 tlo = __float2bfloat16_rn(tin - __bfloat162float(th));
@@ -1410,28 +1392,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
     hidden_epi(sBias + H, sH2h, sH2l);
     barrier();
 
-    float fg[16];  // f = k_s (recompute) or g = J^T kbar_s (reverse)
-    if (!rev) {
-      // L2: acc[0:D] = h2 W3^T
-      if (tid == 0) {
-        const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(2));
-        const uint32_t idD = tc::idesc_bf16_f32(128, D);
-        for (int kk = 0; kk < H / 16; ++kk) {
-          const uint64_t db = tc::smem_desc(wa + kk * 256, 128, H * 16);
-          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2h) + kk * 256, 128, H * 16),
-                       db, idD, kk > 0);
-          tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2l) + kk * 256, 128, H * 16),
-                       db, idD, true);
-        }
-        tc::mma_commit(&mbar_mma);
-      }
-      wait_mma();
-      float v[16];
-      tc::tmem_ld16(tl + L::T_R + coff, v);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int r = 0; r < C; ++r) fg[r] = v[r] + sBias[2 * H + coff + r];
-    } else {
+    float fg[16];  // g = J_f(Y_s)^T kbar_s
+    {
       const bool acc0 = !dw_first;
       // B2: acc = kbar W3;  dW3^T += h2^T kbar  (split: hi*hi + lo*hi + hi*lo)
       if (tid == 0) {
@@ -1526,17 +1488,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 
     // ---- consume (row-local)
     if (!act) continue;
-    if (!rev) {
-      // k_s joins the stage sums of the later stages (the forward's order;
-      // stage 7 has no k_2 term)
-#pragma unroll
-      for (int j = 2; j < 7; ++j) {  // kb[j] = acc of stage j+1
-        if (j + 1 <= s || (j == 6 && s == 2)) continue;
-        const float c = dp_a(j + 1, s);
-#pragma unroll
-        for (int r = 0; r < C; ++r) kb[j][r] = madd(c, fg[r], kb[j][r]);
-      }
-    } else {
+    {
       float kbs[16];
       pick7(kb, s - 1, kbs);
 #pragma unroll
@@ -1607,8 +1559,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 // ======================================================================
 // Discrete adjoint of the wide MLP field (D = 64, three tanh layers of
 // 512; App. A).  Same schedule as k_mlp_adjoint -- rows reverse their own
-// instances, 12 lockstep rounds per accepted step -- on 64-row tiles with the
-// weights streamed through a chunk ring.  The reverse rounds need the
+// instances, 7 lockstep rounds per accepted step, stage inputs from the tape
+// -- on 64-row tiles with the weights streamed through a chunk ring.  The reverse rounds need the
 // transposed weights too (W_l^T, K chunks along the layer's outputs).
 //
 // The weight gradients do not fit in tensor memory (two 512 x 512 layers),
@@ -1643,27 +1595,12 @@ template <class Cfg> struct WideAdjLayout {
   }
   static constexpr int TIMG_BYTES = T_off(Cfg::NL);
   static constexpr int TIMG_STRIDE = ((TIMG_BYTES + 255) / 256) * 256;
-  // chunk schedule of one step: 5 recompute rounds (forward layers 0..3) then
-  // 7 reverse rounds (forward layers 0..2, transposed layers 3, 2, 1, 0)
-  static constexpr int REC_CHUNKS = 5 + 32 + 32 + 32, REV_CHUNKS = 5 + 32 + 32 + 4 + 32 + 32 + 32;
-  static constexpr int STEP_CHUNKS = 5 * REC_CHUNKS + 7 * REV_CHUNKS;
+  // chunk schedule of a reverse round: forward layers 0..2, then the
+  // transposed layers 3, 2, 1, 0
+  static constexpr int REV_CHUNKS = 5 + 32 + 32 + 4 + 32 + 32 + 32;
   // global chunk index -> (transposed?, layer, chunk) -> image offset, bytes
   __device__ static void chunk_src(uint32_t g, bool& tr, int& off, int& bytes) {
-    int p = (int)(g % (uint32_t)STEP_CHUNKS);
-    int seq[7], n = 0;
-    if (p < 5 * REC_CHUNKS) {
-      p %= REC_CHUNKS;
-      tr = false;
-      const int c[4] = {5, 32, 32, 32};
-      int l = 0;
-      while (p >= c[l]) p -= c[l++];
-      bytes = Cfg::N_of(l) * 32;
-      off = Cfg::W_off(l) + p * bytes;
-      (void)seq;
-      (void)n;
-      return;
-    }
-    p = (p - 5 * REC_CHUNKS) % REV_CHUNKS;
+    int p = (int)(g % (uint32_t)REV_CHUNKS);
     const int cnt[7] = {5, 32, 32, 4, 32, 32, 32};
     const int lay[7] = {0, 1, 2, 3, 2, 1, 0};
     int k = 0;
@@ -1703,7 +1640,7 @@ struct WideAdjArgs {
   uint16_t* sa[4][2];  // X [80], h1, h2, h3 [512]
   uint16_t* sg[4][2];  // delta1, delta2, delta3 [512], kbar [64]
   int cap;             // reverse rounds per CTA
-  float* yscr;         // [grid][64][5][D]: stage inputs Y_2..Y_6 of the step being reversed
+  const float* tp_ys;  // [slots][Btot][6][D]: Y_2..Y_7
   int32_t* overflow;
   int32_t* err;
 };
@@ -1827,29 +1764,31 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
   bool bad = false;
   double tn = 0.0, tnext = 0.0;
   float h = 0.0f;
-  float yn[16], yb[16], kb[7][16];
+  float yb[16], kb[7][16];
 #pragma unroll
   for (int r = 0; r < C; ++r) {
-    yn[r] = yb[r] = 0.0f;
+    yb[r] = 0.0f;
 #pragma unroll
     for (int j = 0; j < 7; ++j) kb[j][r] = 0.0f;
   }
   auto load_step = [&](int i) {
     const size_t o = (size_t)n * a.Btot + i;
-    float k1[16];
-#pragma unroll
-    for (int r = 0; r < C; ++r) {
-      yn[r] = a.tp_y[o * D + coff + r];
-      k1[r] = a.tp_k1[o * D + coff + r];
-    }
     tn = a.tp_t[o];
     h = a.tp_h[o];
     tnext = (n == N - 1) ? a.t1[i] : tn + (double)h;
-#pragma unroll
-    for (int j = 1; j < 7; ++j)
-#pragma unroll
-      for (int r = 0; r < C; ++r) kb[j][r] = dp_a(j + 1, 1) * k1[r];
     act = true;
+  };
+  // Y_s of the step being reversed: Y_1 = y_n, Y_2..Y_7 as the forward recorded
+  auto load_stage = [&](int s_, float (&Yo)[16]) {
+    const size_t o = (size_t)n * a.Btot + inst;
+    const float4* p = s_ == 1
+        ? reinterpret_cast<const float4*>(a.tp_y + o * D + coff)
+        : reinterpret_cast<const float4*>(a.tp_ys + (o * 6 + (s_ - 2)) * D + coff);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float4 u = p[v];
+      Yo[4 * v] = u.x, Yo[4 * v + 1] = u.y, Yo[4 * v + 2] = u.z, Yo[4 * v + 3] = u.w;
+    }
   };
   auto next_work = [&](bool finishing) {
     while (true) {
@@ -1993,78 +1932,55 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     const int ph = rnd % ADJ_ROUNDS;
     if (ph == 0 && __syncthreads_or(act) == 0) break;
     if (abort_s) break;
-    const bool rev = ph >= 5;
-    const int s = rev ? 12 - ph : ph + 2;
-    if (rev && rev_round >= a.cap) {  // cannot happen: the staging is sized for it
+    const int s = 7 - ph;  // stage reversed this round (block-uniform)
+    if (rev_round >= a.cap) {  // cannot happen: the staging is sized for it
       if (tid == 0) atomicExch(a.err, 2);
       break;
     }
     const size_t srow = ((size_t)blockIdx.x * a.cap + rev_round) * ROWS + row;
 
-    // ---- stage input and cotangent; Y_2..Y_6 of the step wait in a small
-    // per-row scratch (L2-resident) between the recompute and reverse rounds
+    // ---- stage input [Y_s; t_s] and the cotangent kbar_s of this row
     float Y[16], d3[16];
     float tin = 0.0f;
-    if (!rev) {
-      float acc[16];
-      pick7(kb, s - 1, acc);
+    if (act && s == 7) {
+      const int i = inst;
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = act ? madd(h, acc[r], yn[r]) : 0.0f;
-      float4* ys = reinterpret_cast<float4*>(
-          a.yscr + (((size_t)blockIdx.x * ROWS + row) * 5 + (s - 2)) * D + coff);
+      for (int j = 0; j < 7; ++j)
 #pragma unroll
-      for (int v4 = 0; v4 < 4; ++v4)
-        ys[v4] = make_float4(Y[4 * v4], Y[4 * v4 + 1], Y[4 * v4 + 2], Y[4 * v4 + 3]);
-    } else if (s == 7) {
+        for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
+      const long long kt = tkey(tn), kn = tkey(tnext);
+      while (q >= 0) {
+        const double tq = a.te[(size_t)i * a.K + q];
+        const long long kq = tkey(tq);
+        if (!(kq > kt)) break;
+        if (a.gye) {
+          float gq[16], w[7];
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = act ? yn[r] + h * kb[6][r] : 0.0f;
-      if (act) {
-        const int i = inst;
+          for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + coff + r];
+          if (kq == kn) {
 #pragma unroll
-        for (int j = 0; j < 7; ++j)
-#pragma unroll
-          for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
-        const long long kt = tkey(tn), kn = tkey(tnext);
-        while (q >= 0) {
-          const double tq = a.te[(size_t)i * a.K + q];
-          const long long kq = tkey(tq);
-          if (!(kq > kt)) break;
-          if (a.gye) {
-            float gq[16], w[7];
-#pragma unroll
-            for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + coff + r];
-            if (kq == kn) {
-#pragma unroll
-              for (int j = 0; j < 7; ++j) w[j] = bw[j];
-            } else {
-              dense_weights<float>(float(tq - tn) / h, w);
-            }
-#pragma unroll
-            for (int j = 0; j < 7; ++j)
-#pragma unroll
-              for (int r = 0; r < C; ++r) kb[j][r] = madd(h * w[j], gq[r], kb[j][r]);
-#pragma unroll
-            for (int r = 0; r < C; ++r) yb[r] += gq[r];
+            for (int j = 0; j < 7; ++j) w[j] = bw[j];
+          } else {
+            dense_weights<float>(float(tq - tn) / h, w);
           }
-          q--;
-        }
-      }
-    } else if (s >= 2) {
-      const float4* ys = reinterpret_cast<const float4*>(
-          a.yscr + (((size_t)blockIdx.x * ROWS + row) * 5 + (s - 2)) * D + coff);
 #pragma unroll
-      for (int v4 = 0; v4 < 4; ++v4) {
-        const float4 u = ys[v4];
-        Y[4 * v4] = act ? u.x : 0.0f;
-        Y[4 * v4 + 1] = act ? u.y : 0.0f;
-        Y[4 * v4 + 2] = act ? u.z : 0.0f;
-        Y[4 * v4 + 3] = act ? u.w : 0.0f;
+          for (int j = 0; j < 7; ++j)
+#pragma unroll
+            for (int r = 0; r < C; ++r) kb[j][r] = madd(h * w[j], gq[r], kb[j][r]);
+#pragma unroll
+          for (int r = 0; r < C; ++r) yb[r] += gq[r];
+        }
+        q--;
       }
+    }
+    if (act) {
+      load_stage(s, Y);
+      tin = (float)(tn + dp_c(s) * (double)h);
+      pick7(kb, s - 1, d3);
     } else {
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = act ? yn[r] : 0.0f;
+      for (int r = 0; r < C; ++r) Y[r] = d3[r] = 0.0f;
     }
-    if (act) tin = (float)(tn + dp_c(s) * (double)h);
     store_row16<true>(sXh, sXl, row, coff, K0, Y);
     if (sub == Cfg::TPR - 1) {
       const __nv_bfloat16 th = __float2bfloat16_rn(tin);
@@ -2072,51 +1988,36 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
       *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(row, D, K0)) = th;
       *reinterpret_cast<__nv_bfloat16*>(sXl + tc::cm_offset(row, D, K0)) = tlo;
     }
-    if (rev) {
-      pick7(kb, s - 1, d3);
-      if (!act)
+    store_row16<true>(sKh, sKl, row, coff, D, d3);
+    // staged rows: X = [Y; t; 1; 0...] and kbar
+    stage_row16(a.sa[0][0], a.sa[0][1], srow * K0 + coff, Y);
+    stage_row16(a.sg[3][0], a.sg[3][1], srow * D + coff, d3);
+    if (sub == Cfg::TPR - 1) {
+      float tail[16];
 #pragma unroll
-        for (int r = 0; r < C; ++r) d3[r] = 0.0f;
-      store_row16<true>(sKh, sKl, row, coff, D, d3);
-      // staged rows: X = [Y; t; 1; 0...] and kbar
-      stage_row16(a.sa[0][0], a.sa[0][1], srow * K0 + coff, Y);
-      stage_row16(a.sg[3][0], a.sg[3][1], srow * D + coff, d3);
-      if (sub == Cfg::TPR - 1) {
-        float tail[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) tail[j] = 0.0f;
-        tail[0] = tin;
-        tail[1] = 1.0f;
-        stage_row16(a.sa[0][0], a.sa[0][1], srow * K0 + D, tail);
-      }
+      for (int j = 0; j < 16; ++j) tail[j] = 0.0f;
+      tail[0] = tin;
+      tail[1] = 1.0f;
+      stage_row16(a.sa[0][0], a.sa[0][1], srow * K0 + D, tail);
     }
     barrier();
 
     // ---- forward layers at Y_s
     gemm(tc::smem_u32(sXh), tc::smem_u32(sXl), K0, K0 / 16, H, false);
     wait_mma();
-    hidden_epi(sBias, rev, a.sa[1][0], a.sa[1][1], srow);
+    hidden_epi(sBias, true, a.sa[1][0], a.sa[1][1], srow);
     barrier();
     gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, false);
     wait_mma();
-    hidden_epi(sBias + H, rev, a.sa[2][0], a.sa[2][1], srow);
+    hidden_epi(sBias + H, true, a.sa[2][0], a.sa[2][1], srow);
     barrier();
     gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, false);
     wait_mma();
-    hidden_epi(sBias + 2 * H, rev, a.sa[3][0], a.sa[3][1], srow);
+    hidden_epi(sBias + 2 * H, true, a.sa[3][0], a.sa[3][1], srow);
     barrier();
 
     float fg[16];
-    if (!rev) {
-      // output layer: f = k_s
-      gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, D, false);
-      wait_mma();
-      float v[16];
-      Cfg::out_ld(tbase, tid, v);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int r = 0; r < C; ++r) fg[r] = v[r] + sBias[3 * H + coff + r];
-    } else {
+    {
       // gh3 = kbar W3 -> delta3 (h3 in the tile)
       gemm(tc::smem_u32(sKh), tc::smem_u32(sKl), D, D / 16, H, true);
       wait_mma();
@@ -2146,15 +2047,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
 
     // ---- consume (row-local; as in k_mlp_adjoint)
     if (!act) continue;
-    if (!rev) {
-#pragma unroll
-      for (int j = 2; j < 7; ++j) {
-        if (j + 1 <= s || (j == 6 && s == 2)) continue;
-        const float c = dp_a(j + 1, s);
-#pragma unroll
-        for (int r = 0; r < C; ++r) kb[j][r] = madd(c, fg[r], kb[j][r]);
-      }
-    } else {
+    {
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
         if (j + 1 >= s) continue;
@@ -2314,6 +2207,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
     a.tp_k1 = (float*)r.tape->k1;
     a.tp_t = r.tape->t;
     a.tp_h = (float*)r.tape->h_acc;
+    a.tp_ys = (float*)r.tape->y_stage;
   } else {
     a.slots = 0;
   }
@@ -2419,7 +2313,7 @@ tode_err mlp_solve(const SolveReq& r, bool split) {
 struct WidePlan {
   int grid, cap;       // CTAs, reverse rounds per CTA per slice
   size_t rows;         // staged rows per slice
-  size_t off_timg, off_stage[8], off_dw0, off_ones, off_yscr, off_cublas, total;
+  size_t off_timg, off_stage[8], off_dw0, off_ones, off_cublas, total;
 };
 static constexpr size_t WIDE_CUBLAS_WS = 32u << 20;
 static WidePlan wide_plan(int B, int slots, int num_sms) {
@@ -2441,8 +2335,6 @@ static WidePlan wide_plan(int B, int slots, int num_sms) {
   o += align256((size_t)Cfg::H * Cfg::K0 * 4);
   p.off_ones = o;
   o += align256(p.rows * 2);
-  p.off_yscr = o;
-  o += align256((size_t)p.grid * 64 * 5 * Cfg::D * 4);
   p.off_cublas = o;
   o += WIDE_CUBLAS_WS;
   p.total = o;
@@ -2509,7 +2401,7 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   a.err = (int32_t*)(base + 128);
   a.overflow = r.overflow;
   a.cap = p.cap;
-  a.yscr = (float*)(base + p.off_yscr);
+  a.tp_ys = (const float*)r.tape->y_stage;
   unsigned char* img = (unsigned char*)base + align256(256);
   unsigned char* timg = (unsigned char*)base + p.off_timg;
   a.wimg = img;
@@ -2596,13 +2488,13 @@ tode_err mlp_adjoint(const AdjReq& r) {
   using Cfg = Cfg32s;
   using L = MlpAdjLayout<Cfg>;
   if (is_d64_h512(r.f)) {
-    if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->k1 || !r.tape->y || !r.tape->t)
+    if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->y || !r.tape->t || !r.tape->y_stage)
       return TODE_EINVAL;
     if (!r.gW || !r.gW[0] || !r.gW[1] || !r.gW[2] || !r.gW[3]) return TODE_EINVAL;
     return mlp_wide_adjoint(r);
   }
   if (!is_d32_h128(r.f)) return TODE_EUNSUPPORTED;
-  if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->k1 || !r.tape->y || !r.tape->t)
+  if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->y || !r.tape->t || !r.tape->y_stage)
     return TODE_EINVAL;
   if (!r.gW || !r.gW[0] || !r.gW[1] || !r.gW[2]) return TODE_EINVAL;
   const cudaStream_t st = r.stream;
@@ -2620,6 +2512,7 @@ tode_err mlp_adjoint(const AdjReq& r) {
   a.tp_k1 = (const float*)r.tape->k1;
   a.tp_t = r.tape->t;
   a.tp_h = (const float*)r.tape->h_acc;
+  a.tp_ys = (const float*)r.tape->y_stage;
   a.gye = (const float*)r.gye;
   a.gyf = (const float*)r.gyf;
   a.gy0 = (float*)r.gy0;

@@ -141,7 +141,8 @@ def autotune(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
                 probe = api.solve(field, y0, t0, t1, t_eval, form="fused", **opt_kw)
                 torch.cuda.synchronize()
                 slots = max(1, int(probe.n_acc.max().item()))
-                tape = api.TapeBuffers.allocate(B, D, y0.dtype, slots, 1, y0.device)
+                tape = api.TapeBuffers.allocate(B, D, y0.dtype, slots, 1, y0.device,
+                                                stages=kind == "mlp")
 
             def timer(o):
                 def run():

@@ -77,7 +77,8 @@ def test_autograd_mlp_matches_direct_adjoint_call():
     # the same through solve + adjoint
     g = gpu_solve(w, torch.float32, "fused")
     B, D = w["y0"].shape
-    tape = tode.TapeBuffers.allocate(B, D, torch.float32, int(g["n_acc"].max()), 1, "cuda")
+    tape = tode.TapeBuffers.allocate(B, D, torch.float32, int(g["n_acc"].max()), 1, "cuda",
+                                     stages=True)
     y0, t0, t1, te = _inputs(w, torch.float32)
     sol = tode.solve(field, y0.detach(), t0, t1, te, tape=tape, rtol=w["rtol"], atol=w["atol"])
     assert torch.equal(sol.y_eval, ye)

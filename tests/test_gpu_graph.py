@@ -49,7 +49,7 @@ def test_fused_step_replays_under_cuda_graph(cfg):
     probe = tode.solve(field, x["y0"], x["t0"], x["t1"], x["te"], form="fused", **opt)
     torch.cuda.synchronize()
     slots = int(probe.n_acc.max().item()) + 8
-    tape = tode.TapeBuffers.allocate(B, D, dtype, slots, 1, "cuda")
+    tape = tode.TapeBuffers.allocate(B, D, dtype, slots, 1, "cuda", stages=cfg == 4)
     # eager reference for the original inputs and for a second input set
     ref1 = _flat(*_step(field, x, tape, opt)[:3])
     w2 = subset(w, np.random.default_rng(5).permutation(B))

@@ -79,7 +79,7 @@ def test_mlp_unsupported_requests_fail_loudly():
     """The MLP tape keeps every accepted step: a checkpoint stride is refused."""
     import paper_2210_12375_b300 as tode
     w = dict(make(4, B=64), split=True)
-    tape = tode.TapeBuffers.allocate(64, 32, torch.float32, 8, 2, "cuda")
+    tape = tode.TapeBuffers.allocate(64, 32, torch.float32, 8, 2, "cuda", stages=True)
     with pytest.raises(tode._abi.TodeError):
         gpu_solve(w, torch.float32, "fused", tape=tape)
 
@@ -94,8 +94,8 @@ def test_mlp_plain_form_equals_fused_bitwise(B):
     w = dict(subset(base, np.arange(B) % base["B"]), split=True)
     out = {}
     for form in ("fused", "plain"):
-        tape = tode.TapeBuffers.allocate(B, 32, torch.float32, 16, 1, "cuda")
-        for t in (tape.y, tape.k1, tape.t, tape.h_acc):
+        tape = tode.TapeBuffers.allocate(B, 32, torch.float32, 16, 1, "cuda", stages=True)
+        for t in (tape.y, tape.k1, tape.t, tape.h_acc, tape.y_stage):
             t.zero_()  # slots past an instance's last step stay zero
         g = gpu_solve(w, torch.float32, form, tape=tape, trace_cap=32)
         out[form] = (g, tape)
@@ -105,5 +105,5 @@ def test_mlp_plain_form_equals_fused_bitwise(B):
               "trace_err", "trace_accepted", "trace_len"):
         assert np.array_equal(gf[k], gp[k]), k
     N = int(gf["n_acc"].max())
-    for name in ("y", "k1", "t", "h_acc"):
+    for name in ("y", "k1", "t", "h_acc", "y_stage"):
         assert torch.equal(getattr(tf, name)[:N], getattr(tp, name)[:N]), name

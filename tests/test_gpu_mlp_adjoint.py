@@ -30,7 +30,8 @@ def _run(w, slots=None, mask=None, seed=1, repeat=1):
     probe = gpu_solve(w, torch.float32, "fused", trace_cap=256)
     assert (probe["n_acc"] + probe["n_rej"] <= 256).all()
     N = int(probe["n_acc"].max())
-    tape = tode.TapeBuffers.allocate(B, D, torch.float32, slots or max(N, 1), 1, "cuda")
+    tape = tode.TapeBuffers.allocate(B, D, torch.float32, slots or max(N, 1), 1, "cuda",
+                                     stages=True)
     g = gpu_solve(w, torch.float32, "fused", tape=tape)
     for k in ("y_eval", "n_acc", "status"):
         assert np.array_equal(g[k], probe[k], equal_nan=True), k  # the tape changes nothing
@@ -161,7 +162,7 @@ def test_mlp_adjoint_zero_length_interval():
 def test_mlp_adjoint_needs_split_precision():
     w = dict(make(4, B=64), split=False)
     B, D = w["y0"].shape
-    tape = tode.TapeBuffers.allocate(B, D, torch.float32, 64, 1, "cuda")
+    tape = tode.TapeBuffers.allocate(B, D, torch.float32, 64, 1, "cuda", stages=True)
     g = gpu_solve(w, torch.float32, "fused", tape=tape)
     dev = g["_dev"]
     with pytest.raises(tode._abi.TodeError):

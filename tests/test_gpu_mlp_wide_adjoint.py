@@ -25,7 +25,8 @@ def _run(w, mask=None, seed=1, repeat=1):
     B, D = w["y0"].shape
     probe = gpu_solve(w, torch.float32, "fused", trace_cap=128)
     assert (probe["n_acc"] + probe["n_rej"] <= 128).all()
-    tape = tode.TapeBuffers.allocate(B, D, torch.float32, int(probe["n_acc"].max()), 1, "cuda")
+    tape = tode.TapeBuffers.allocate(B, D, torch.float32, int(probe["n_acc"].max()), 1, "cuda",
+                                     stages=True)
     g = gpu_solve(w, torch.float32, "fused", tape=tape)
     assert np.array_equal(g["y_eval"], probe["y_eval"], equal_nan=True)
     rng = np.random.default_rng(seed)
