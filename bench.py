@@ -130,15 +130,16 @@ def flops_per_attempt(kind: str, D: int) -> float:
     return 6 * f_eval + comb
 
 
-def adjoint_flops_per_step(kind: str, D: int) -> float:
-    """Algorithmic FLOPs of reversing one accepted step: 7 stage
-    re-evaluations, 6 transposed-Jacobian products with their parameter outer
-    products, and the stage-cotangent combinations."""
+def adjoint_flops_per_step(kind: str, D: int, recorded: bool) -> float:
+    """Algorithmic FLOPs of reversing one accepted step: the stage
+    re-evaluations (none when the tape recorded the stage inputs), 6
+    transposed-Jacobian products with their parameter outer products, and the
+    stage-cotangent combinations."""
     if kind == "linear":
         f_eval, vjp = 2 * D * D, 4 * D * D
     else:
         f_eval, vjp = 6, 12
-    return 7 * f_eval + 6 * vjp + 2 * (26 + 21) * D
+    return (0 if recorded else 7 * f_eval) + 6 * vjp + 2 * (26 + 21) * D
 
 
 def _events(torch, n):
@@ -200,7 +201,8 @@ def run_tode(args):
     n_acc_max = int(probe.n_acc.max().item())
     # every field has both forms and the adjoint (--fwd-only drops the latter)
     with_adjoint = not args.fwd_only
-    tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev, stages=mlp)
+    tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev,
+                                     stages=mlp or kind == "linear")
 
     def fwd(form, sol=None, ws=None):
         return tode.solve(field, y0, t0, t1, te, form=form, tape=tape, out=sol, workspace=ws,
@@ -384,9 +386,11 @@ def run_tode(args):
         net = f"D={D},H={wd[1]},{len(wd) - 2} hidden layers,split"
         kf = {"achieved": 6 * 2 * S * n_att / (k_fwd_ms * 1e-3) / 1e12,
               "kernel": f"k_mlp_fused<{net}> (fused forward)", "kernel_ms": k_fwd_ms}
-        # per accepted step: 7 evaluations (stages recomputed, activations at
-        # every stage input) and 6 transposed products dX + dW (2 x 2S MACs)
-        ka = {"achieved": (7 * 2 * S + 6 * 4 * S) * n_acc_total / (k_adj_ms * 1e-3) / 1e12,
+        # per accepted step, at each of the 7 recorded stage inputs: the
+        # hidden activations (2 S_hid) and the transposed products dX + dW
+        # (2 x 2S); the output layer is not re-evaluated
+        S_hid = sum(wd[l] * wd[l + 1] for l in range(len(wd) - 2))
+        ka = {"achieved": 7 * (2 * S_hid + 4 * S) * n_acc_total / (k_adj_ms * 1e-3) / 1e12,
               "kernel": f"k_mlp_adjoint<{net}>", "kernel_ms": k_adj_ms} if with_adjoint else None
         for r in (kf, ka) if with_adjoint else (kf,):
             r.update(bound="tensor", peak=peak, unit="TFLOP/s", frac=r["achieved"] / peak,
@@ -400,7 +404,8 @@ def run_tode(args):
             fld, adj = f"VdpField<{tn}>", f"VdpAdj<{tn}>"
         kf = {"achieved": flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12,
               "kernel": f"k_fused<{fld}> (fused forward)", "kernel_ms": k_fwd_ms}
-        ka = {"achieved": adjoint_flops_per_step(kind, D) * n_acc_total / (k_adj_ms * 1e-3)
+        ka = {"achieved": adjoint_flops_per_step(kind, D, kind == "linear") * n_acc_total
+              / (k_adj_ms * 1e-3)
               / 1e12, "kernel": f"k_adjoint<{adj}> (stride-1 tape)", "kernel_ms": k_adj_ms}
         for r in (kf, ka):
             r.update(bound="alu", peak=fp32_peak, unit="TFLOP/s",

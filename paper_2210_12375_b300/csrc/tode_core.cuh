@@ -323,7 +323,8 @@ template <typename T> struct TapeDev {
   T* h;
   T* err_prev;
   int32_t* flags;
-  T* h_acc;  // optional: size of the accepted step that starts at the slot
+  T* h_acc;   // optional: size of the accepted step that starts at the slot
+  T* ystage;  // optional: its stage inputs Y_2..Y_7, [slots][B][6][D]
 };
 struct TraceDev {
   int cap;
@@ -358,15 +359,24 @@ __device__ __forceinline__ void tape_store(const TapeDev<T>& tp, int i, const In
   }
 }
 
-// After an accepted attempt: the size of that step (n = n_acc - 1) into its
-// slot, so that a stride-1 adjoint can reverse straight from the tape.
+// After an accepted attempt: the size of that step (n = n_acc - 1) and, when
+// the tape keeps them, its stage inputs into its slot, so that a stride-1
+// adjoint can reverse straight from the tape.
 template <typename T, int R, int G>
-__device__ __forceinline__ void tape_store_hacc(const TapeDev<T>& tp, int i, const Inst<T, R>& s) {
+__device__ __forceinline__ void tape_store_hacc(const TapeDev<T>& tp, int i, const Inst<T, R>& s,
+                                                const T (&ys)[6][R]) {
   const int n = s.n_acc - 1;
   if (tp.slots == 0 || !tp.h_acc || (n % tp.stride) != 0) return;
   const int j = n / tp.stride;
   if (j >= tp.slots) return;
   if (Grp<G>::rank() == 0) tp.h_acc[(size_t)j * tp.B + i] = s.h_last;
+  if (tp.ystage && tp.stride == 1) {
+    T* dst = tp.ystage + ((size_t)j * tp.B + i) * 6 * tp.D + Grp<G>::rank() * R;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[q * tp.D + r] = ys[q][r];
+  }
 }
 
 // ---------------------------------------------------------------- init (a1, a2)
@@ -460,7 +470,7 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
 // Returns true while the instance is still running.
 template <class Field, typename T, int R, int G>
 __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, int i, int D,
-                             const InstOut<T>& out, const TraceDev& tr) {
+                             const InstOut<T>& out, const TraceDev& tr, T (&ys)[6][R]) {
   using C = DP5;
   T h = s.h;
   bool last = false;
@@ -480,6 +490,8 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
   T k2[R], k3[R], k4[R], k5[R], k6[R], k7[R], Y[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) Y[r] = madd(h, T(C::a21) * s.k1[r], s.y[r]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[0][r] = Y[r];
   F.eval(s.t + C::c2 * hd, Y, k2);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -487,6 +499,8 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     a = madd(T(C::a32), k2[r], a);
     Y[r] = madd(h, a, s.y[r]);
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[1][r] = Y[r];
   F.eval(s.t + C::c3 * hd, Y, k3);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -495,6 +509,8 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     a = madd(T(C::a43), k3[r], a);
     Y[r] = madd(h, a, s.y[r]);
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[2][r] = Y[r];
   F.eval(s.t + C::c4 * hd, Y, k4);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -504,6 +520,8 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     a = madd(T(C::a54), k4[r], a);
     Y[r] = madd(h, a, s.y[r]);
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[3][r] = Y[r];
   F.eval(s.t + C::c5 * hd, Y, k5);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -514,6 +532,8 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     a = madd(T(C::a65), k5[r], a);
     Y[r] = madd(h, a, s.y[r]);
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[4][r] = Y[r];
   F.eval(s.t + hd, Y, k6);
   T y1[R], inc[R];
 #pragma unroll
@@ -526,6 +546,8 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     inc[r] = h * a;
     y1[r] = s.y[r] + inc[r];  // SSAL: the 7th stage input is the new solution
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[5][r] = y1[r];
   F.eval(s.t + hd, y1, k7);
   // embedded error estimate and its norm
   T ev[R], sc[R];

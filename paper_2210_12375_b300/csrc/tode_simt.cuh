@@ -131,9 +131,11 @@ __global__ void k_plain_step(SolveArgs<T> a) {
   Inst<T, R> s;
   plain_load<T, R, G>(a, i, s);
   const int acc_before = s.n_acc;
-  const bool run = inst_attempt<Field, T, R, G>(F, s, a.o, i, a.D, inst_out(a, i), a.trace);
+  T ys[6][R];
+  const bool run =
+      inst_attempt<Field, T, R, G>(F, s, a.o, i, a.D, inst_out(a, i), a.trace, ys);
   if (s.n_acc != acc_before) {
-    tape_store_hacc<T, R, G>(a.tape, i, s);
+    tape_store_hacc<T, R, G>(a.tape, i, s, ys);
     if (run) tape_store<T, R, G>(a.tape, i, s);
   }
   plain_store<T, R, G>(a, i, s);
@@ -170,8 +172,10 @@ __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
       tape_store<T, R, G>(a.tape, i, s);
     }
     const int acc_before = s.n_acc;
-    const bool run = inst_attempt<Field, T, R, G>(F, s, a.o, i, a.D, inst_out(a, i), a.trace);
-    if (s.n_acc != acc_before) tape_store_hacc<T, R, G>(a.tape, i, s);
+    T ys[6][R];
+    const bool run =
+        inst_attempt<Field, T, R, G>(F, s, a.o, i, a.D, inst_out(a, i), a.trace, ys);
+    if (s.n_acc != acc_before) tape_store_hacc<T, R, G>(a.tape, i, s, ys);
     if (run) {
       if (s.n_acc != acc_before) tape_store<T, R, G>(a.tape, i, s);
     } else {
@@ -202,6 +206,7 @@ template <typename T> TapeDev<T> make_tape(const tode_tape* tp, int B, int D) {
   d.err_prev = (T*)tp->err_prev;
   d.flags = tp->flags;
   d.h_acc = (T*)tp->h_acc;
+  d.ystage = (T*)tp->y_stage;
   return d;
 }
 

@@ -139,62 +139,72 @@ template <typename T> struct AdjArgs {
 template <class AF, typename T, int R, int G>
 __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, int D, double t,
                                              T h, double t_next, const T (&y)[R],
-                                             const T (&k1)[R], T (&yb)[R], int& q) {
+                                             const T (&k1)[R], const T* ys, T (&yb)[R], int& q) {
   using C = DP5;
-  T Y[7][R], k[7][R];
-  const double hd = (double)h;
+  T Y[7][R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    Y[0][r] = y[r];
-    k[0][r] = k1[r];
+  for (int r = 0; r < R; ++r) Y[0][r] = y[r];
+  if (ys) {
+    // the forward recorded this step's stage inputs Y_2..Y_7 ([6][D], this
+    // lane's components at g*R)
+    const int g = Grp<G>::rank();
+#pragma unroll
+    for (int q6 = 0; q6 < 6; ++q6)
+#pragma unroll
+      for (int r = 0; r < R; ++r) Y[q6 + 1][r] = ys[q6 * D + g * R + r];
+  } else {
+    // recompute them with the forward's operations (bit for bit)
+    T k[6][R];
+    const double hd = (double)h;
+#pragma unroll
+    for (int r = 0; r < R; ++r) k[0][r] = k1[r];
+#pragma unroll
+    for (int r = 0; r < R; ++r) Y[1][r] = madd(h, T(C::a21) * k[0][r], y[r]);
+    F.eval(t + C::c2 * hd, Y[1], k[1]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T s = T(C::a31) * k[0][r];
+      s = madd(T(C::a32), k[1][r], s);
+      Y[2][r] = madd(h, s, y[r]);
+    }
+    F.eval(t + C::c3 * hd, Y[2], k[2]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T s = T(C::a41) * k[0][r];
+      s = madd(T(C::a42), k[1][r], s);
+      s = madd(T(C::a43), k[2][r], s);
+      Y[3][r] = madd(h, s, y[r]);
+    }
+    F.eval(t + C::c4 * hd, Y[3], k[3]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T s = T(C::a51) * k[0][r];
+      s = madd(T(C::a52), k[1][r], s);
+      s = madd(T(C::a53), k[2][r], s);
+      s = madd(T(C::a54), k[3][r], s);
+      Y[4][r] = madd(h, s, y[r]);
+    }
+    F.eval(t + C::c5 * hd, Y[4], k[4]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T s = T(C::a61) * k[0][r];
+      s = madd(T(C::a62), k[1][r], s);
+      s = madd(T(C::a63), k[2][r], s);
+      s = madd(T(C::a64), k[3][r], s);
+      s = madd(T(C::a65), k[4][r], s);
+      Y[5][r] = madd(h, s, y[r]);
+    }
+    F.eval(t + hd, Y[5], k[5]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T s = T(C::b1) * k[0][r];
+      s = madd(T(C::b3), k[2][r], s);
+      s = madd(T(C::b4), k[3][r], s);
+      s = madd(T(C::b5), k[4][r], s);
+      s = madd(T(C::b6), k[5][r], s);
+      Y[6][r] = y[r] + h * s;  // the forward's new solution y + (h s)
+    }
   }
-#pragma unroll
-  for (int r = 0; r < R; ++r) Y[1][r] = madd(h, T(C::a21) * k[0][r], y[r]);
-  F.eval(t + C::c2 * hd, Y[1], k[1]);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T s = T(C::a31) * k[0][r];
-    s = madd(T(C::a32), k[1][r], s);
-    Y[2][r] = madd(h, s, y[r]);
-  }
-  F.eval(t + C::c3 * hd, Y[2], k[2]);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T s = T(C::a41) * k[0][r];
-    s = madd(T(C::a42), k[1][r], s);
-    s = madd(T(C::a43), k[2][r], s);
-    Y[3][r] = madd(h, s, y[r]);
-  }
-  F.eval(t + C::c4 * hd, Y[3], k[3]);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T s = T(C::a51) * k[0][r];
-    s = madd(T(C::a52), k[1][r], s);
-    s = madd(T(C::a53), k[2][r], s);
-    s = madd(T(C::a54), k[3][r], s);
-    Y[4][r] = madd(h, s, y[r]);
-  }
-  F.eval(t + C::c5 * hd, Y[4], k[4]);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T s = T(C::a61) * k[0][r];
-    s = madd(T(C::a62), k[1][r], s);
-    s = madd(T(C::a63), k[2][r], s);
-    s = madd(T(C::a64), k[3][r], s);
-    s = madd(T(C::a65), k[4][r], s);
-    Y[5][r] = madd(h, s, y[r]);
-  }
-  F.eval(t + hd, Y[5], k[5]);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T s = T(C::b1) * k[0][r];
-    s = madd(T(C::b3), k[2][r], s);
-    s = madd(T(C::b4), k[3][r], s);
-    s = madd(T(C::b5), k[4][r], s);
-    s = madd(T(C::b6), k[5][r], s);
-    Y[6][r] = madd(h, s, y[r]);
-  }
-  F.eval(t + hd, Y[6], k[6]);
 
   // cotangents of the stage derivatives
   const T bw[7] = {T(C::b1), T(0), T(C::b3), T(C::b4), T(C::b5), T(C::b6), T(0)};
@@ -221,7 +231,7 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
       } else {
         T th;
         if constexpr (Comp<T>::on) th = T(tq - t) / h;
-        else th = T((tq - t) / hd);
+        else th = T((tq - t) / (double)h);
         dense_weights<T>(th, w);
         dense7 = true;
       }
@@ -297,7 +307,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
       const double t = a.tape.t[o];
       const T h = a.tape.h_acc[o];
       const double t_next = (n == N - 1) ? t1 : t + (double)h;
-      reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, yb, q);
+      const T* ys = a.tape.ystage ? a.tape.ystage + o * 6 * D : nullptr;
+      reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, ys, yb, q);
     }
     for (int j = nseg - 1; !direct && j >= 0 && !bad; --j) {
       const int n0 = j * m;
@@ -336,7 +347,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
           ys[r] = s.y[r];
           ks[r] = s.k1[r];
         }
-        inst_attempt<AF, T, R, G>(F, s, ro, i, D, no_out, no_trace);
+        T ysd[6][R];
+        inst_attempt<AF, T, R, G>(F, s, ro, i, D, no_out, no_trace, ysd);
         const T hb = s.h_last;
         if (s.n_acc != before) {
           const size_t p = (size_t)(before - n0) * a.B + i;
@@ -367,7 +379,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
         const double t = a.st[p];
         const T h = a.sh[p];
         const double t_next = (n == N - 1) ? t1 : t + (double)h;
-        reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, yb, q);
+        reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, nullptr, yb, q);
       }
       if constexpr (G > 1) __syncwarp(Grp<G>::mask());
     }

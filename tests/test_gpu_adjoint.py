@@ -146,3 +146,30 @@ def test_adjoint_direct_from_tape_equals_rerun(cfg):
         assert int(ovf.item()) == 0
         outs.append((gy0.cpu().numpy(), gp.cpu().numpy()))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_adjoint_recorded_stage_inputs_equal_recomputed(cfg):
+    """A tape that also records each accepted step's stage inputs Y_2..Y_7
+    lets the adjoint skip the stage re-evaluations; the reverse sweep gives
+    the same bits as recomputing them."""
+    w = make(cfg, B=300)
+    dtype = torch.float64 if cfg == 1 else torch.float32
+    B, D = w["y0"].shape
+    probe = gpu_solve(w, dtype, "fused")
+    N = int(probe["n_acc"].max())
+    outs = []
+    for stages in (False, True):
+        tape = tode.TapeBuffers.allocate(B, D, dtype, N, 1, "cuda", stages=stages)
+        g = gpu_solve(w, dtype, "fused", tape=tape)
+        dev = g["_dev"]
+        rng = np.random.default_rng(4)
+        gye = torch.tensor(rng.standard_normal(g["y_eval"].shape), dtype=dtype, device="cuda")
+        gyf = torch.tensor(rng.standard_normal(g["y_final"].shape), dtype=dtype, device="cuda")
+        gy0, gp, ovf = tode.adjoint(dev["field"], dev["t0"], dev["t1"], dev["te"], g["_sol"], tape,
+                                    gye, gyf, rtol=w["rtol"], atol=w["atol"])
+        torch.cuda.synchronize()
+        assert int(ovf.item()) == 0
+        outs.append((gy0.cpu().numpy(), gp.cpu().numpy(), g["y_eval"]))
+    assert np.array_equal(outs[0][2], outs[1][2])  # recording changes nothing in the solve
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
