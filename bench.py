@@ -434,17 +434,13 @@ def run_tode(args):
         "fused_over_plain_fwd_adj": (ms_plain / args.plain_steps) / per_step,
         "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
     })
-    # our kernels per timed step: fused forward (+ the weight-image builds for
-    # the MLP, one per layer and copy) and the adjoint (+ one image build per
-    # layer and the ordered dW reduction)
+    # our kernels per timed step: the fused forward (+ one weight-image build
+    # for the MLP) and the adjoint (MLP D=32: image, adjoint, ordered dW
+    # reduction; wide MLP: two images, a fill, one adjoint per batch slice and
+    # a copy -- the weight-gradient GEMMs are cuBLAS's)
     if mlp:
-        n_layers = len(w["field"]["W"])
-        reps = 16 if D == 64 else 1
-        if D == 64:  # wide: 2 images x copies, ones fill, per slice the kernel + 20 GEMMs, copy
-            adj = 2 * reps * n_layers + 1 + -(-B // (148 * 64)) * 1 + 1
-        else:
-            adj = n_layers + 2
-        gpu_launches = reps * n_layers + 1 + (adj if with_adjoint else 0)
+        adj = (3 + -(-B // (148 * 64)) + 1) if D == 64 else 3
+        gpu_launches = 2 + (adj if with_adjoint else 0)
     else:
         gpu_launches = 2
     result = {

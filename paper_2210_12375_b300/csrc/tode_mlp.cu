@@ -17,7 +17,7 @@
 // Threads: 256 per CTA, two per row (threads r and r + 128 share TMEM lane r
 // and each owns D/2 state components and H/2 hidden columns).  Shared memory
 // holds the weights (loaded once by bulk copy from a core-matrix image that
-// k_mlp_weight_image builds), the BF16 input tile and the BF16 hidden tile.
+// k_mlp_images builds), the BF16 input tile and the BF16 hidden tile.
 // The input [Y; t] is always split into two BF16 terms (hi + lo, two MMAs
 // into the same accumulator), so the state enters the field with ~16
 // significant bits; hidden activations are split too when SPLIT is set, with
@@ -982,18 +982,62 @@ __global__ void __launch_bounds__(256, 1) k_mlp_plain_step(MlpArgs a) {
   mlp_solver<Cfg, MLP_PLAIN_STEP>(a);
 }
 
-// W_l [N][K_in] BF16 row-major -> core-matrix image with K padded to K_l:
-// one [N][K_l] tile, or (chunked) K_l/16 consecutive [N][16] tiles, the
-// pieces the streamed-weight solver copies one at a time.
-__global__ void k_mlp_weight_image(const uint16_t* __restrict__ W, int N, int Kin, int Kp,
-                                   unsigned char* img, int chunked) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * Kp) return;
-  const int n = e / Kp, kk = e % Kp;
-  const uint16_t v = kk < Kin ? W[(size_t)n * Kin + kk] : (uint16_t)0;
-  const uint32_t off = chunked ? (uint32_t)(kk / 16) * (uint32_t)N * 32u + tc::cm_offset(n, kk % 16, 16)
-                               : tc::cm_offset(n, kk, Kp);
-  *reinterpret_cast<uint16_t*>(img + off) = v;
+// The BF16 weights W_l [N_l][K_in,l] (row-major) as core-matrix images with
+// K padded to K_l, for all layers and all copies in one launch.  Layouts:
+//   IMG_TILE    one [N_l][K_l] tile per layer (weights resident in shared memory)
+//   IMG_CHUNKS  K_l/16 consecutive [N_l][16] tiles (the streamed K chunks)
+//   IMG_TCHUNKS N_l/16 consecutive MN-major [16][K_l] tiles: W_l^T in K chunks
+//               along the layer's outputs (the transposed products)
+enum : int { IMG_TILE = 0, IMG_CHUNKS = 1, IMG_TCHUNKS = 2 };
+struct ImageJob {
+  const uint16_t* W[MLP_MAX_LAYERS];
+  int N[MLP_MAX_LAYERS], Kin[MLP_MAX_LAYERS], Kp[MLP_MAX_LAYERS];
+  size_t off[MLP_MAX_LAYERS];      // layer offset inside one copy
+  long long start[MLP_MAX_LAYERS + 1];  // element ranges of the layers
+  int nl, reps, mode;
+  size_t stride;  // bytes between copies
+};
+__global__ void k_mlp_images(ImageJob j, unsigned char* img) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= j.start[j.nl]) return;
+  int l = 0;
+  while (e >= j.start[l + 1]) ++l;
+  const long long x = e - j.start[l];
+  const int Kp = j.Kp[l], N = j.N[l];
+  const int n = (int)(x / Kp), k = (int)(x % Kp);
+  const uint16_t v = k < j.Kin[l] ? j.W[l][(size_t)n * j.Kin[l] + k] : (uint16_t)0;
+  uint32_t off;
+  if (j.mode == IMG_TILE) off = tc::cm_offset(n, k, Kp);
+  else if (j.mode == IMG_CHUNKS) off = (uint32_t)(k / 16) * (uint32_t)N * 32u + tc::cm_offset(n, k % 16, 16);
+  else off = (uint32_t)(n / 16) * 16u * (uint32_t)Kp * 2u + tc::cm_offset(n % 16, k, Kp);
+  for (int r = 0; r < j.reps; ++r)
+    *reinterpret_cast<uint16_t*>(img + (size_t)r * j.stride + j.off[l] + off) = v;
+}
+
+// Host side: the image job of a network config (W_off / T_off give the
+// layer offsets of the chosen layout).
+template <class Cfg>
+static tode_err build_images(const tode_field_desc* f, unsigned char* img, int mode, int reps,
+                             size_t stride, const size_t (&layer_off)[MLP_MAX_LAYERS],
+                             cudaStream_t st) {
+  ImageJob j{};
+  j.nl = Cfg::NL;
+  j.reps = reps;
+  j.mode = mode;
+  j.stride = stride;
+  j.start[0] = 0;
+  for (int l = 0; l < Cfg::NL; ++l) {
+    j.W[l] = (const uint16_t*)f->W[l];
+    j.N[l] = Cfg::N_of(l);
+    j.Kin[l] = f->widths[l];
+    j.Kp[l] = Cfg::K_of(l);
+    j.off[l] = layer_off[l];
+    j.start[l + 1] = j.start[l] + (long long)j.N[l] * j.Kp[l];
+  }
+  const long long n = j.start[Cfg::NL];
+  k_mlp_images<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(j, img);
+  TODE_CUDA_TRY(cudaGetLastError());
+  return TODE_OK;
 }
 
 // ======================================================================
@@ -2075,17 +2119,6 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
   if ((tid >> 5) == 0) tc::tmem_dealloc(tbase, 512);
 }
 
-// W_l [N][K_in] BF16 -> transposed chunk image: chunk c holds outputs
-// [16c, 16c+16) as an MN-major [16][IN] core-matrix tile (IN = K_l padded).
-__global__ void k_mlp_weight_image_t(const uint16_t* __restrict__ W, int N, int Kin, int IN,
-                                     unsigned char* img) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * IN) return;
-  const int o = e / IN, i = e % IN;
-  const uint16_t v = i < Kin ? W[(size_t)o * Kin + i] : (uint16_t)0;
-  const uint32_t off = (uint32_t)(o / 16) * 16u * (uint32_t)IN * 2u + tc::cm_offset(o % 16, i, IN);
-  *reinterpret_cast<uint16_t*>(img + off) = v;
-}
 
 // Sums the per-CTA partials in CTA order into the caller's gradients
 // (layouts of the weights: W_l [out][in], b_l [out]).
@@ -2095,10 +2128,16 @@ __global__ void k_mlp_grad_reduce(const float* part, int grid, float* gW0, float
   using L = MlpAdjLayout<Cfg>;
   constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, IN = D + 1;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  // eight interleaved partial sums over the CTAs, combined as a fixed tree
+  // (the same order on every call: deterministic)
   auto sum = [&](int off) {
-    float acc = 0.0f;
-    for (int c = 0; c < grid; ++c) acc += part[(size_t)c * L::P_FLOATS + off];
-    return acc;
+    float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    int c = 0;
+    for (; c + 8 <= grid; c += 8)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] += part[(size_t)(c + u) * L::P_FLOATS + off];
+    for (int u = 0; c < grid; ++c, ++u) acc[u] += part[(size_t)c * L::P_FLOATS + off];
+    return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   };
   int k = e;
   if (k < H * IN) {
@@ -2250,15 +2289,13 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
     p += align256(B * 4);
   }
   const cudaStream_t st = r.stream;
-  for (int rep = 0; rep < Cfg::WREP; ++rep)
-    for (int l = 0; l < Cfg::NL; ++l) {
-      const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
-      const int n = N * Kp;
-      k_mlp_weight_image<<<(n + 255) / 256, 256, 0, st>>>(
-          (const uint16_t*)r.f->W[l], N, Kin, Kp,
-          img + (size_t)rep * Cfg::WIMG_STRIDE + Cfg::W_off(l), (int)Cfg::STREAM);
-    }
-  TODE_CUDA_TRY(cudaGetLastError());
+  {
+    size_t loff[MLP_MAX_LAYERS] = {};
+    for (int l = 0; l < Cfg::NL; ++l) loff[l] = Cfg::W_off(l);
+    const tode_err e = build_images<Cfg>(r.f, img, Cfg::STREAM ? IMG_CHUNKS : IMG_TILE, Cfg::WREP,
+                                         Cfg::WIMG_STRIDE, loff, st);
+    if (e != TODE_OK) return e;
+  }
   TODE_CUDA_TRY(cudaMemsetAsync(r.ws, 0, 256, st));  // queue counter and error flag
   {
     static std::atomic<uint64_t> done{0};
@@ -2420,15 +2457,17 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   float* dw0 = (float*)(base + p.off_dw0);
   uint16_t* ones = (uint16_t*)(base + p.off_ones);
   // weight images (forward chunks and transposed chunks, WREP copies each)
-  for (int rep = 0; rep < Cfg::WREP; ++rep)
+  {
+    size_t woff[MLP_MAX_LAYERS] = {}, toff[MLP_MAX_LAYERS] = {};
     for (int l = 0; l < Cfg::NL; ++l) {
-      const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
-      k_mlp_weight_image<<<(N * Kp + 255) / 256, 256, 0, st>>>(
-          (const uint16_t*)r.f->W[l], N, Kin, Kp, img + (size_t)rep * Cfg::WIMG_STRIDE + Cfg::W_off(l),
-          1);
-      k_mlp_weight_image_t<<<(N * Kp + 255) / 256, 256, 0, st>>>(
-          (const uint16_t*)r.f->W[l], N, Kin, Kp, timg + (size_t)rep * L::TIMG_STRIDE + L::T_off(l));
+      woff[l] = Cfg::W_off(l);
+      toff[l] = L::T_off(l);
     }
+    tode_err e = build_images<Cfg>(r.f, img, IMG_CHUNKS, Cfg::WREP, Cfg::WIMG_STRIDE, woff, st);
+    if (e == TODE_OK)
+      e = build_images<Cfg>(r.f, timg, IMG_TCHUNKS, Cfg::WREP, L::TIMG_STRIDE, toff, st);
+    if (e != TODE_OK) return e;
+  }
   k_fill_bf16_one<<<(unsigned)((p.rows + 255) / 256), 256, 0, st>>>(ones, p.rows);
   TODE_CUDA_TRY(cudaGetLastError());
   TODE_CUDA_TRY(cudaMemsetAsync(base, 0, 256, st));
@@ -2525,12 +2564,12 @@ tode_err mlp_adjoint(const AdjReq& r) {
   p += align256((size_t)Cfg::WIMG_BYTES);
   a.part = (float*)p;
   a.overflow = r.overflow;
-  for (int l = 0; l < 3; ++l) {
-    const int N = Cfg::N_of(l), Kp = Cfg::K_of(l), Kin = r.f->widths[l];
-    k_mlp_weight_image<<<(N * Kp + 255) / 256, 256, 0, st>>>((const uint16_t*)r.f->W[l], N, Kin,
-                                                             Kp, img + Cfg::W_off(l), 0);
+  {
+    size_t loff[MLP_MAX_LAYERS] = {};
+    for (int l = 0; l < Cfg::NL; ++l) loff[l] = Cfg::W_off(l);
+    const tode_err e = build_images<Cfg>(r.f, img, IMG_TILE, 1, Cfg::WIMG_STRIDE, loff, st);
+    if (e != TODE_OK) return e;
   }
-  TODE_CUDA_TRY(cudaGetLastError());
   TODE_CUDA_TRY(cudaMemsetAsync(r.scratch, 0, 256, st));
   {
     static std::atomic<uint64_t> done{0};
