@@ -13,7 +13,11 @@
  * Conventions for every entry point:
  *  - Pointers are DEVICE pointers unless marked "host".  The caller owns and
  *    allocates every buffer (inputs, outputs, workspace, tape, scratch); the
- *    library never allocates or frees device memory.
+ *    library never allocates or frees device memory, with one exception: the
+ *    wide MLP field's adjoint (D = 64, three layers of 512) computes its
+ *    weight gradients with cuBLAS GEMMs, and cuBLAS creates one handle per
+ *    device on first use (its workspace is carved from the caller's
+ *    scratch).  Make that first call before any stream capture.
  *  - Calls enqueue work on `stream` (a cudaStream_t, NULL = legacy default)
  *    and return.  Outputs are valid once the stream has synchronised.  The
  *    plain form (TODE_PLAIN) additionally synchronises `stream` every
@@ -182,15 +186,19 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
                     int32_t* n_feval, int32_t* status, const tode_tape* tape,
                     const tode_trace* trace, void* workspace, size_t ws_bytes, void* stream);
 
-/* Bytes of device scratch tode_adjoint needs (256-byte aligned base). */
+/* Bytes of device scratch tode_adjoint needs (256-byte aligned base).  For
+ * the MLP field it depends on the current device's SM count and, for the
+ * wide network, on tape->slots (the reverse rounds are staged per batch
+ * slice of SMs x 64 instances). */
 size_t tode_adjoint_scratch_size(const tode_field_desc* f, const tode_options* o,
                                  const tode_tape* tape);
 
 /* Discrete adjoint of the fixed-mesh map of a previous tode_solve with the
  * same f, o, inputs and a filled tape (App. A: gradients by backpropagation
  * through the solver).  The mesh (accepted t_n, h_n) is a constant.  For
- * every instance it reverses the accepted steps, recomputing the stages
- * from the checkpoints, and writes
+ * every instance it reverses the accepted steps -- from the recorded stage
+ * inputs when the tape has them (y_stage; required for the MLP field),
+ * otherwise recomputing the stages from the checkpoints -- and writes
  *   gy0 [B][D]       = dL/dy0
  *   gparam           = VDP: dL/dmu [B]; LINEAR: dL/dA [B][D][D] (state
  *                      dtype, per instance); MLP: unused (NULL)
