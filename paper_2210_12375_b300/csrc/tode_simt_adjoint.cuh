@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
     int q = a.K - 1;
     const double t1 = a.t1[i];
     const bool direct = m == 1 && a.tape.h_acc != nullptr;
+    double t_after = t1;  // the end of step n: t1, or the start of step n+1 (its slot's t)
     for (int n = N - 1; direct && n >= 0 && !bad; --n) {
       const size_t o = (size_t)n * a.B + i;
       T y[R], k1[R];
@@ -306,7 +307,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
       }
       const double t = a.tape.t[o];
       const T h = a.tape.h_acc[o];
-      const double t_next = (n == N - 1) ? t1 : t + (double)h;
+      const double t_next = t_after;  // the forward's t + h, bit for bit
+      t_after = t;
       const T* ys = a.tape.ystage ? a.tape.ystage + o * 6 * D : nullptr;
       reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, ys, yb, q);
     }
