@@ -266,6 +266,90 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
   }
 }
 
+// Cotangents of evaluation points sitting at t0 (they are y0 itself), then
+// the instance's results: dL/dy0 and the field's parameter gradient.
+template <class AF, typename T>
+__device__ __forceinline__ void adjoint_finish(AF& F, const AdjArgs<T>& a, int i, int q, bool bad,
+                                               T (&yb)[AF::R]) {
+  constexpr int R = AF::R, G = AF::G;
+  const int D = a.D;
+  const int g = Grp<G>::rank();
+  if (!bad && a.gye) {
+    const long long k0 = tkey(a.t0[i]);
+    for (; q >= 0; --q) {
+      if (tkey(a.te[(size_t)i * a.K + q]) == k0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          yb[r] = yb[r] + a.gye[((size_t)i * a.K + q) * D + g * R + r];
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) a.gy0[(size_t)i * D + g * R + r] = bad ? nan_(T(0)) : yb[r];
+  if (a.gparam) F.store_param(a.gparam, i, bad);
+}
+
+// Direct form (stride-1 tape with the accepted step sizes): one loop
+// iteration reverses one step straight from its slot, and a group whose
+// instance is done finishes it and steals the next at once, so the groups of
+// a warp stay on the common step body whatever their step counts.
+template <class AF, typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(AdjArgs<T> a) {
+  constexpr int R = AF::R, G = AF::G;
+  const int D = a.D;
+  const int groups_total = (int)((gridDim.x * (size_t)blockDim.x) / G);
+  int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
+  const int g = Grp<G>::rank();
+  AF F;
+  T yb[R];
+  int n = -1;          // next step to reverse; < 0: the instance is done
+  int q = 0;           // evaluation-point cursor, from the last backwards
+  bool bad = false;
+  bool have = false;
+  double t_after = 0.0;  // end of step n: t1, or the start of step n+1 (its slot's t)
+  while (true) {
+    if (n < 0) {
+      if (have) {
+        adjoint_finish<AF, T>(F, a, i, q, bad, yb);
+        have = false;
+        i = grab_instance<G>(a.counter, groups_total);
+      }
+      if (i >= a.B) break;
+      F.load(a.fparam, i);
+      const int N = a.n_acc[i];
+      bad = a.status[i] != ST_SUCCESS;
+      if (!bad && N > a.tape.slots) {
+        bad = true;
+        if (g == 0) *a.overflow = 1;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
+      q = a.K - 1;
+      t_after = a.t1[i];
+      n = bad ? -1 : N - 1;
+      have = true;
+      if (n < 0) continue;
+    }
+    const size_t o = (size_t)n * a.B + i;
+    T y[R], k1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      y[r] = a.tape.y[o * D + g * R + r];
+      k1[r] = a.tape.k1[o * D + g * R + r];
+    }
+    const double t = a.tape.t[o];
+    const T h = a.tape.h_acc[o];
+    const double t_next = t_after;  // the forward's t + h, bit for bit
+    t_after = t;
+    const T* ys = a.tape.ystage ? a.tape.ystage + o * 6 * D : nullptr;
+    reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, ys, yb, q);
+    --n;
+  }
+}
+
+// Re-running form (strided tape, or no recorded step sizes): each segment
+// between slots is re-run with the forward routine from its slot, its
+// step-start states parked in scratch, then reversed.
 template <class AF, typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs<T> a) {
   constexpr int R = AF::R, G = AF::G;
@@ -295,24 +379,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
     for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
     int q = a.K - 1;
     const double t1 = a.t1[i];
-    const bool direct = m == 1 && a.tape.h_acc != nullptr;
-    double t_after = t1;  // the end of step n: t1, or the start of step n+1 (its slot's t)
-    for (int n = N - 1; direct && n >= 0 && !bad; --n) {
-      const size_t o = (size_t)n * a.B + i;
-      T y[R], k1[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        y[r] = a.tape.y[o * D + g * R + r];
-        k1[r] = a.tape.k1[o * D + g * R + r];
-      }
-      const double t = a.tape.t[o];
-      const T h = a.tape.h_acc[o];
-      const double t_next = t_after;  // the forward's t + h, bit for bit
-      t_after = t;
-      const T* ys = a.tape.ystage ? a.tape.ystage + o * 6 * D : nullptr;
-      reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, ys, yb, q);
-    }
-    for (int j = nseg - 1; !direct && j >= 0 && !bad; --j) {
+    for (int j = nseg - 1; j >= 0 && !bad; --j) {
       const int n0 = j * m;
       const int n1 = (n0 + m < N) ? n0 + m : N;
       // restore the slot and re-run the forward over the segment
@@ -385,25 +452,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
       }
       if constexpr (G > 1) __syncwarp(Grp<G>::mask());
     }
-    // evaluation points at t0 are y0 itself
-    if (!bad && a.gye) {
-      const long long k0 = tkey(a.t0[i]);
-      for (; q >= 0; --q) {
-        if (tkey(a.te[(size_t)i * a.K + q]) == k0) {
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-            yb[r] = yb[r] + a.gye[((size_t)i * a.K + q) * D + g * R + r];
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) a.gy0[(size_t)i * D + g * R + r] = bad ? nan_(T(0)) : yb[r];
-    if (a.gparam) F.store_param(a.gparam, i, bad);
+    adjoint_finish<AF, T>(F, a, i, q, bad, yb);
     i = grab_instance<G>(a.counter, groups_total);
   }
 }
 
 template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
+  const bool direct = r.tape->stride == 1 && r.tape->h_acc != nullptr;
   AdjArgs<T> a{};
   a.B = r.B;
   a.D = r.D;
@@ -437,15 +492,16 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   p += align256((size_t)m * r.B * 8);
   a.sh = (T*)p;
   const int block = 256;
+  auto kern = direct ? k_adjoint_steps<AF, T> : k_adjoint<AF, T>;
   int per_sm = 0;
-  TODE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<AF, T>, block, 0));
+  TODE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
   if (per_sm < 1) per_sm = 1;
   long long grid = (long long)r.num_sms * per_sm;
   const long long need = ((long long)r.B * AF::G + block - 1) / block;
   if (grid > need) grid = need;
   if (grid == 0) return TODE_OK;
   TODE_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int32_t), r.stream));
-  k_adjoint<AF, T><<<(int)grid, block, 0, r.stream>>>(a);
+  kern<<<(int)grid, block, 0, r.stream>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
 }
