@@ -435,14 +435,15 @@ def run_tode(args):
         "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
     })
     # our kernels per timed step: the fused forward (+ one weight-image build
-    # for the MLP) and the adjoint (MLP D=32: image, adjoint, ordered dW
-    # reduction; wide MLP: two images, a fill, one adjoint per batch slice and
-    # a copy -- the weight-gradient GEMMs are cuBLAS's)
+    # for the MLP) and the adjoint (SIMT fields: the longest-first work order
+    # and the reverse sweep; MLP D=32: image, adjoint, ordered dW reduction;
+    # wide MLP: two images, a fill, one adjoint per batch slice and a copy --
+    # the weight-gradient GEMMs are cuBLAS's)
     if mlp:
         adj = (3 + -(-B // (148 * 64)) + 1) if D == 64 else 3
         gpu_launches = 2 + (adj if with_adjoint else 0)
     else:
-        gpu_launches = 2
+        gpu_launches = 1 + (2 if with_adjoint else 0)
     result = {
         "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,

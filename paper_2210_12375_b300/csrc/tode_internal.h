@@ -75,10 +75,11 @@ inline size_t simt_workspace_bytes(int B, int D, size_t ts, int form) {
   return s;
 }
 
-// Scratch bytes of the SIMT adjoint: one segment of `stride` step-start
-// states per instance (y, t, h) plus the work counter.
+// Scratch bytes of the SIMT adjoint: the work counter, the work order (one
+// int32 per instance) and one segment of `stride` step-start states per
+// instance (y, k1, t, h).
 inline size_t simt_adjoint_scratch_bytes(int B, int D, size_t ts, int stride) {
-  return align256(256) + 2 * align256((size_t)stride * B * D * ts) +
+  return align256(256) + align256((size_t)B * 4) + 2 * align256((size_t)stride * B * D * ts) +
          align256((size_t)stride * B * 8) + align256((size_t)stride * B * ts);
 }
 

@@ -128,6 +128,7 @@ template <typename T> struct AdjArgs {
   const T* fparam;
   int32_t* overflow;
   int32_t* counter;
+  const int32_t* order;  // instances by decreasing step count (work queue order)
   T* sy;        // [stride][B][D]
   T* sk1;       // [stride][B][D]
   double* st;   // [stride][B]
@@ -266,6 +267,63 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
   }
 }
 
+// ---------------------------------------------------------------- work order
+// The reverse sweeps are handed out longest first (by the forward's accepted
+// step counts), so that the long instances do not start last and stretch
+// the tail of the persistent grid.  One CTA counting-sorts the instances by
+// decreasing step count (capped at ORDER_BINS - 1); the order inside a bin is
+// arbitrary, which changes no result: every instance is reversed
+// independently of the others.
+constexpr int ORDER_BINS = 1024;
+
+template <int BINS>
+__global__ void __launch_bounds__(BINS) k_order_by_steps(const int32_t* n_acc,
+                                                         const int32_t* status, int B,
+                                                         int32_t* order) {
+  static_assert(BINS == 1024, "one thread per bin, 32 warps of 32");
+  __shared__ int cnt[BINS];
+  __shared__ int warp_tot[BINS / 32];
+  const int t = threadIdx.x;
+  cnt[t] = 0;
+  __syncthreads();
+  auto bin_of = [&](int i) {
+    // descending: bin 0 holds the longest; failed instances do no work
+    const int n = status[i] == ST_SUCCESS ? n_acc[i] : 0;
+    return BINS - 1 - (n < 0 ? 0 : (n > BINS - 1 ? BINS - 1 : n));
+  };
+  for (int i = t; i < B; i += BINS) atomicAdd(&cnt[bin_of(i)], 1);
+  __syncthreads();
+  // exclusive prefix sum over the bins (bin t is owned by thread t)
+  const int lane = t & 31, w = t >> 5;
+  const int c = cnt[t];
+  int incl = c;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int x = warp_tot[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += v;
+    }
+    warp_tot[lane] = x;  // inclusive over warps
+  }
+  __syncthreads();
+  cnt[t] = (w > 0 ? warp_tot[w - 1] : 0) + incl - c;
+  __syncthreads();
+  for (int i = t; i < B; i += BINS) order[atomicAdd(&cnt[bin_of(i)], 1)] = i;
+}
+
+// Instance at queue position j (B past the end of the queue).
+template <typename T> __device__ __forceinline__ int queued(const AdjArgs<T>& a, int j) {
+  return j < a.B ? a.order[j] : a.B;
+}
+
 // Cotangents of evaluation points sitting at t0 (they are y0 itself), then
 // the instance's results: dL/dy0 and the field's parameter gradient.
 template <class AF, typename T>
@@ -298,7 +356,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
   constexpr int R = AF::R, G = AF::G;
   const int D = a.D;
   const int groups_total = (int)((gridDim.x * (size_t)blockDim.x) / G);
-  int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
+  int i = queued(a, (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G));
   const int g = Grp<G>::rank();
   AF F;
   T yb[R];
@@ -312,7 +370,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
       if (have) {
         adjoint_finish<AF, T>(F, a, i, q, bad, yb);
         have = false;
-        i = grab_instance<G>(a.counter, groups_total);
+        i = queued(a, grab_instance<G>(a.counter, groups_total));
       }
       if (i >= a.B) break;
       F.load(a.fparam, i);
@@ -355,7 +413,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
   constexpr int R = AF::R, G = AF::G;
   const int D = a.D;
   const int groups_total = (int)((gridDim.x * (size_t)blockDim.x) / G);
-  int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
+  int i = queued(a, (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G));
   const int g = Grp<G>::rank();
   SolveOpts ro = a.o;
   ro.max_steps = 0x7fffffff;  // the re-run never stops on a step count
@@ -453,7 +511,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
       if constexpr (G > 1) __syncwarp(Grp<G>::mask());
     }
     adjoint_finish<AF, T>(F, a, i, q, bad, yb);
-    i = grab_instance<G>(a.counter, groups_total);
+    i = queued(a, grab_instance<G>(a.counter, groups_total));
   }
 }
 
@@ -483,6 +541,9 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   char* p = r.scratch;
   a.counter = (int32_t*)p;
   p += align256(256);
+  int32_t* order = (int32_t*)p;
+  a.order = order;
+  p += align256((size_t)r.B * 4);
   const int m = r.tape->stride;
   a.sy = (T*)p;
   p += align256((size_t)m * r.B * r.D * sizeof(T));
@@ -501,6 +562,8 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   if (grid > need) grid = need;
   if (grid == 0) return TODE_OK;
   TODE_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int32_t), r.stream));
+  k_order_by_steps<ORDER_BINS><<<1, ORDER_BINS, 0, r.stream>>>(r.n_acc, r.status, r.B, order);
+  TODE_CUDA_TRY(cudaGetLastError());
   kern<<<(int)grid, block, 0, r.stream>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
