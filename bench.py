@@ -49,8 +49,12 @@ def _args():
     p.add_argument("--fwd-only", action="store_true", help="time the forward solve alone")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--autotune", action="store_true",
-                   help="time the launch-shape candidates on this batch first (fused form)")
+    p.add_argument("--order", type=int, default=0, choices=[0, 1],
+                   help="work order of the SIMT solvers: 0 index, 1 longest interval first")
+    p.add_argument("--no-graph", action="store_true",
+                   help="issue the fused step eagerly instead of replaying a CUDA graph")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="library default launch shapes instead of the autotuner's choice")
     return p.parse_args()
 
 
@@ -186,10 +190,19 @@ def run_tode(args):
     gye = torch.tensor(rng.standard_normal((B, K, D)), dtype=dtype, device=dev)
     gyf = torch.tensor(rng.standard_normal((B, D)), dtype=dtype, device=dev)
     opt = dict(rtol=w["rtol"], atol=w["atol"])
-    tuned = None
-    if args.autotune and not mlp:
+    if not mlp:
+        opt["order"] = args.order
+    tuned = tuned_plain = None
+    opt_plain = dict(opt)
+    if not args.no_autotune and not mlp:
+        # the launch shape (lanes per instance, CTA size, resident CTAs, work
+        # order; for the plain form its poll interval) the autotuner picks for
+        # this batch, timed on it (fwd + adjoint), for each form
         tuned = tode.autotune(field, y0, t0, t1, te, with_adjoint=True, reps=3, **opt)
+        tuned_plain = tode.autotune(field, y0, t0, t1, te, form="plain", with_adjoint=True,
+                                    reps=2, **opt)
         opt.update(tuned)
+        opt_plain.update(tuned_plain)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     # probe: step counts (identical every pass) and the tape size
@@ -206,11 +219,12 @@ def run_tode(args):
 
     def fwd(form, sol=None, ws=None):
         return tode.solve(field, y0, t0, t1, te, form=form, tape=tape, out=sol, workspace=ws,
-                          **opt)
+                          **(opt if form == "fused" else opt_plain))
 
     def step(form, sol=None, ws=None, scratch=None):
         s = fwd(form, sol, ws)
-        return s, tode.adjoint(field, t0, t1, te, s, tape, gye, gyf, scratch=scratch, **opt)
+        return s, tode.adjoint(field, t0, t1, te, s, tape, gye, gyf, scratch=scratch,
+                               **(opt if form == "fused" else opt_plain))
 
     # matched error: both forms against the exact solution of the same batch
     sol_f = fwd("fused")
@@ -226,14 +240,44 @@ def run_tode(args):
         ye = sol_f.y_eval.double().cpu().numpy()
         err = float(np.max(np.abs(ye - exact) / (w["atol"] + w["rtol"] * np.abs(exact))))
 
+    def capture(fn):
+        """A CUDA graph of the work fn enqueues (fn runs once outside the
+        capture first); None when this build's calls cannot be captured."""
+        if args.no_graph:
+            return None
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            fn()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        try:
+            with torch.cuda.graph(g):
+                fn()
+        except RuntimeError as e:  # report it in the JSON line and time eagerly
+            graph_notes.append(str(e).splitlines()[0][:160])
+            torch.cuda.synchronize()
+            return None
+        return g
+
+    graph_notes = []
+
+    def runner(form, with_adj, sol, ws):
+        """One pass as the timed loop issues it: the fused form as a CUDA
+        graph replay (host launch cost off the device timeline), the plain
+        form eagerly (its host loop polls the device for completion)."""
+        def eager():
+            return step(form, sol, ws) if with_adj else fwd(form, sol, ws)
+        g = capture(eager) if form == "fused" else None
+        return (g.replay, True) if g is not None else (eager, False)
+
     def timed(form, nsteps, with_adj=True):
         sol = fwd(form)
         ws = sol.extra["workspace"]
+        run, graphed = runner(form, with_adj, sol, ws)
         for _ in range(args.warmup):
-            if with_adj:
-                step(form, sol, ws)
-            else:
-                fwd(form, sol, ws)
+            run()
         torch.cuda.synchronize()
         ev = _events(torch, nsteps)
         if world > 1:
@@ -243,10 +287,7 @@ def run_tode(args):
         for k in range(nsteps):
             flush.zero_()  # L2 flush, outside the timed events
             ev[k][0].record(stream)
-            if with_adj:
-                step(form, sol, ws)
-            else:
-                fwd(form, sol, ws)
+            run()
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t_wall
@@ -254,33 +295,42 @@ def run_tode(args):
         if world > 1:  # the slowest rank's time (instances are independent: no other exchange)
             ms = max_over_ranks(ms, dev)
             dist.barrier()
-        return ms, wall
+        return ms, wall, graphed
 
     def kernel_ms(nrep, adjoint_only):
+        """Device time of the fused forward alone, or of the adjoint alone
+        (its work-order kernel included), replayed from a CUDA graph."""
         sol = fwd("fused")
         ws = sol.extra["workspace"]
+        torch.cuda.synchronize()
+        if adjoint_only:
+            def eager():
+                return tode.adjoint(field, t0, t1, te, sol, tape, gye, gyf, **opt)
+        else:
+            def eager():
+                return fwd("fused", sol, ws)
+        g = capture(eager)
+        run = g.replay if g is not None else eager
+        run()
         torch.cuda.synchronize()
         ev = _events(torch, nrep)
         for k in range(nrep):
             flush.zero_()
             ev[k][0].record(stream)
-            if adjoint_only:
-                tode.adjoint(field, t0, t1, te, sol, tape, gye, gyf, **opt)
-            else:
-                fwd("fused", sol, ws)
+            run()
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
     nk = max(1, args.kernel_reps)
     with ClockSampler(local) as clk:
-        ms_fused, wall_fused = timed("fused", args.steps, with_adjoint)
+        ms_fused, wall_fused, graphed = timed("fused", args.steps, with_adjoint)
         k_fwd_ms = kernel_ms(nk, False)
         k_adj_ms = kernel_ms(nk, True) if with_adjoint else None
     clocks = clk.summary()
-    ms_fused_fwd, _ = timed("fused", nk, False)
-    ms_plain, _ = timed("plain", args.plain_steps, with_adjoint)
-    ms_plain_fwd, _ = timed("plain", args.plain_steps, False)
+    ms_fused_fwd, _, _ = timed("fused", nk, False)
+    ms_plain, _, _ = timed("plain", args.plain_steps, with_adjoint)
+    ms_plain_fwd, _, _ = timed("plain", args.plain_steps, False)
 
     per_step = ms_fused / args.steps
     value = world * n_att / (per_step * 1e-3)
@@ -398,8 +448,12 @@ def run_tode(args):
     else:
         psrc = f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {clk_mhz:.0f} MHz"
         tn = "double" if dtype == torch.float64 else "float"
-        if kind == "linear":  # lanes per instance: 8 forward, 16 for the direct adjoint
-            fld, adj = f"LinearField<{tn},2,8>", f"LinearAdj<{tn},1,16>"
+        if kind == "linear":  # lanes per instance: the launch's group (default 8 for D = 16,
+            # D for D <= 8, 16 for D = 32); the stride-1 adjoint of D = 16 takes 16
+            g = int(opt.get("group") or 0) or {16: 8, 32: 16}.get(D, D)
+            ga = 16 if D == 16 else g
+            fld = f"LinearField<{tn},{D // g},{g}>"
+            adj = f"LinearAdj<{tn},{D // ga},{ga}>"
         else:
             fld, adj = f"VdpField<{tn}>", f"VdpAdj<{tn}>"
         kf = {"achieved": flops_per_attempt(kind, D) * n_att / (k_fwd_ms * 1e-3) / 1e12,
@@ -456,7 +510,12 @@ def run_tode(args):
                    "state": "f32 (compensated), time f64", "controller": "I (beta1=0.2)",
                    "l2": "flushed between timed steps (256 MiB write outside the events)",
                    "parallelism": f"dp{world} (independent replicas of the batch)",
-                   "launch": tuned if tuned is not None else "defaults"},
+                   "launch": tuned if tuned is not None else "defaults",
+                   "launch_plain": tuned_plain if tuned_plain is not None else "defaults",
+                   "issue": ("fused step replayed as one CUDA graph (forward + adjoint), "
+                             "plain form from its host loop" if graphed else
+                             "eager calls (graph capture off or unavailable)")
+                   + ("; capture: " + "; ".join(graph_notes) if graph_notes else "")},
         "gpu_launches": gpu_launches * args.steps,
         "clocks": clocks, "e2e": e2e, "roofline": roofline, "breakdown": breakdown,
         "wall_s_timed_region": wall_fused,

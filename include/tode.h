@@ -113,9 +113,17 @@ typedef struct {
   tode_form form;
   /* launch tuning (0 = default / autotuned) */
   int group;                  /* lanes per instance (linear field, D = 16: 4, 8 or 16) */
-  int block;                  /* threads per block (multiple of 32, <= 256) */
+  int block;                  /* threads per block (multiple of 32, <= 256; 0 = 128, or
+                                 fewer when the batch has under 128 threads per SM);
+                                 Van der Pol and linear: tode_solve and tode_adjoint */
   int ctas_per_sm;            /* fused form: resident CTAs per SM */
   int poll_every;             /* plain form: steps between host polls */
+  /* work order of the Van der Pol and linear solvers (both forms):
+   * 0 = index order, 1 = longest integration interval t1 - t0 first (lane
+   * groups that share a warp then tend to take similar step counts and long
+   * instances start early, but a warp's per-instance stores scatter).
+   * Results do not depend on it; the autotuner tries both. */
+  int order;
 } tode_options;
 
 /* Checkpoint tape written by tode_solve for tode_adjoint.  Slot j of
@@ -163,12 +171,14 @@ typedef struct {
 
 /* Fills *o with the defaults: rtol = atol = 1e-6, safety 0.9, fac_min 0.2,
  * fac_max 10, beta1 0.2, beta2 0 (integral controller), h0 = 0 (heuristic),
- * max_steps 100000, TODE_F32, TODE_FUSED, tuning fields 0. */
+ * max_steps 100000, TODE_F32, TODE_FUSED, tuning fields 0, order 0. */
 void tode_default_options(tode_options* o);
 
 /* Bytes of device workspace tode_solve needs for this problem (the base
- * pointer must be 256-byte aligned).  Returns 0 for an unsupported or
- * invalid combination. */
+ * pointer must be 256-byte aligned): for the Van der Pol and linear fields
+ * a work counter and the work order (one int32 per instance), plus the
+ * per-instance solver state between launches for the plain form.  Returns 0
+ * for an unsupported or invalid combination. */
 size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int K);
 
 /* Solve all B instances (Sec. 3: independent parallel solving).

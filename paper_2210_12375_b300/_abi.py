@@ -59,6 +59,7 @@ class Options(C.Structure):
         ("block", C.c_int),
         ("ctas_per_sm", C.c_int),
         ("poll_every", C.c_int),
+        ("order", C.c_int),
     ]
 
 

@@ -121,7 +121,7 @@ def _prec_of(field, y0: torch.Tensor) -> int:
 def make_options(*, rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, fac_min=0.2,
                  fac_max=10.0, beta1=0.2, beta2=0.0, h0=0.0, max_steps=100000,
                  prec=_abi.TODE_F32, form="fused", group=0, block=0, ctas_per_sm=0,
-                 poll_every=0) -> _abi.Options:
+                 poll_every=0, order=0) -> _abi.Options:
     o = _abi.Options()
     o.rtol, o.atol = float(rtol), float(atol)
     o.rtol_b = rtol_b.data_ptr() if rtol_b is not None else None
@@ -134,6 +134,7 @@ def make_options(*, rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, 
         if isinstance(form, str) else int(form)
     o.group, o.block, o.ctas_per_sm, o.poll_every = int(group), int(block), int(ctas_per_sm), \
         int(poll_every)
+    o.order = int(order)
     return o
 
 

@@ -27,6 +27,7 @@ static bool opts_ok(const tode_options* o) {
   if (o->max_steps < 1) return false;
   if (o->form != TODE_PLAIN && o->form != TODE_FUSED) return false;
   if (o->block < 0 || o->group < 0 || o->ctas_per_sm < 0 || o->poll_every < 0) return false;
+  if (o->order != 0 && o->order != 1) return false;
   return true;
 }
 

@@ -695,6 +695,76 @@ __device__ void inst_finalize(const Inst<T, R>& s, const SolveOpts& o, int i, in
   }
 }
 
+// ---------------------------------------------------------------- work order
+// One CTA counting-sorts the instances into a work queue by a bin number
+// (bin 0 first).  Every instance is solved or reversed independently of the
+// others, so the order changes no result; it only decides which instances
+// share a warp and which start first.  The order inside a bin is arbitrary.
+constexpr int ORDER_BINS = 1024;
+
+template <class BinOf>
+__global__ void __launch_bounds__(ORDER_BINS) k_counting_order(int B, BinOf bin_of,
+                                                               int32_t* order) {
+  __shared__ int cnt[ORDER_BINS];
+  __shared__ int warp_tot[ORDER_BINS / 32];
+  const int t = threadIdx.x;
+  cnt[t] = 0;
+  __syncthreads();
+  for (int i = t; i < B; i += ORDER_BINS) atomicAdd(&cnt[bin_of(i)], 1);
+  __syncthreads();
+  // exclusive prefix sum over the bins (thread t owns bin t)
+  const int lane = t & 31, w = t >> 5;
+  const int c = cnt[t];
+  int incl = c;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int x = warp_tot[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += v;
+    }
+    warp_tot[lane] = x;  // inclusive over warps
+  }
+  __syncthreads();
+  cnt[t] = (w > 0 ? warp_tot[w - 1] : 0) + incl - c;
+  __syncthreads();
+  for (int i = t; i < B; i += ORDER_BINS) order[atomicAdd(&cnt[bin_of(i)], 1)] = i;
+}
+
+// Longest integration interval first: t1 - t0 binned by its binary exponent
+// and two leading mantissa bits (a quarter octave per bin, 2^-128 .. 2^128).
+// Empty and invalid intervals, which finish at initialisation, go last.
+struct IntervalBin {
+  const double* t0;
+  const double* t1;
+  __device__ __forceinline__ int operator()(int i) const {
+    const double len = t1[i] - t0[i];
+    if (!(len > 0.0) || !tfinite(len)) return ORDER_BINS - 1;
+    const long long b = __double_as_longlong(len);
+    const int key = (int)(((b >> 52) & 0x7ff) - 1023 + 128) * 4 + (int)((b >> 50) & 3);
+    const int k = key < 0 ? 0 : (key > ORDER_BINS - 2 ? ORDER_BINS - 2 : key);
+    return ORDER_BINS - 2 - k;
+  }
+};
+
+// Most accepted steps first (the adjoint's sweep lengths, capped at
+// ORDER_BINS - 1); instances that failed do no work.
+struct StepsBin {
+  const int32_t* n_acc;
+  const int32_t* status;
+  __device__ __forceinline__ int operator()(int i) const {
+    const int n = status[i] == ST_SUCCESS ? n_acc[i] : 0;
+    return ORDER_BINS - 1 - (n < 0 ? 0 : (n > ORDER_BINS - 1 ? ORDER_BINS - 1 : n));
+  }
+};
+
 // ---------------------------------------------------------------- work stealing
 // Hands the next instance index to every group of the calling lanes with one
 // atomic per warp (lanes of a group always arrive together).

@@ -65,7 +65,8 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Workspace bytes of the SIMT solver for state dtype size `ts`.
 inline size_t simt_workspace_bytes(int B, int D, size_t ts, int form) {
   size_t s = 0;
-  s += align256(256);  // any-active flag + work counter
+  s += align256(256);             // any-active flag + work counter
+  s += align256((size_t)B * 4);    // work order
   if (form == TODE_PLAIN) {
     s += 3 * align256((size_t)B * D * ts);  // y, y_lo, k1
     s += align256((size_t)B * 8);           // t

@@ -35,8 +35,14 @@ template <typename T> struct SolveArgs {
   int32_t* wcur;
   int32_t* wfl;
   int32_t* active;
-  int32_t* counter;  // fused form: next instance to hand out
+  int32_t* counter;  // fused form: next queue position to hand out
+  const int32_t* order;  // work queue: instance at each position (NULL: index order)
 };
+
+// Instance at queue position j (B past the end of the queue).
+template <typename T> __device__ __forceinline__ int queued(const SolveArgs<T>& a, int j) {
+  return j >= a.B ? a.B : (a.order ? a.order[j] : j);
+}
 
 template <typename T>
 __device__ __forceinline__ InstOut<T> inst_out(const SolveArgs<T>& a, int i) {
@@ -54,22 +60,25 @@ template <typename T> __device__ __forceinline__ double atol_of(const SolveArgs<
   return a.atol_b ? a.atol_b[i] : a.atol;
 }
 
+// Plain-form state between launches, kept at the queue position j (so a
+// warp's accesses stay contiguous); the outputs are at the instance i.
 template <typename T, int R, int G>
-__device__ __forceinline__ void plain_store(const SolveArgs<T>& a, int i, const Inst<T, R>& s) {
+__device__ __forceinline__ void plain_store(const SolveArgs<T>& a, int j, int i,
+                                            const Inst<T, R>& s) {
   const int g = Grp<G>::rank();
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const size_t q = ((size_t)r * a.B + i) * G + g;
+    const size_t q = ((size_t)r * a.B + j) * G + g;
     a.wy[q] = s.y[r];
     if constexpr (Comp<T>::on) a.wylo[q] = s.ylo[r];
     a.wk[q] = s.k1[r];
   }
   if (g == 0) {
-    a.wt[i] = s.t;
-    a.wh[i] = s.h;
-    a.wep[i] = s.err_prev;
-    a.wcur[i] = s.cursor;
-    a.wfl[i] = s.flags;
+    a.wt[j] = s.t;
+    a.wh[j] = s.h;
+    a.wep[j] = s.err_prev;
+    a.wcur[j] = s.cursor;
+    a.wfl[j] = s.flags;
     a.n_acc[i] = s.n_acc;
     a.n_rej[i] = s.n_rej;
     a.status[i] = s.status;
@@ -77,22 +86,23 @@ __device__ __forceinline__ void plain_store(const SolveArgs<T>& a, int i, const 
 }
 
 template <typename T, int R, int G>
-__device__ __forceinline__ void plain_load(const SolveArgs<T>& a, int i, Inst<T, R>& s) {
+__device__ __forceinline__ void plain_load(const SolveArgs<T>& a, int j, int i,
+                                           Inst<T, R>& s) {
   const int g = Grp<G>::rank();
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const size_t q = ((size_t)r * a.B + i) * G + g;
+    const size_t q = ((size_t)r * a.B + j) * G + g;
     s.y[r] = a.wy[q];
     s.ylo[r] = Comp<T>::on ? a.wylo[q] : T(0);
     s.k1[r] = a.wk[q];
   }
-  s.t = a.wt[i];
+  s.t = a.wt[j];
   s.t0 = a.t0[i];
   s.t1 = a.t1[i];
-  s.h = a.wh[i];
-  s.err_prev = a.wep[i];
-  s.cursor = a.wcur[i];
-  s.flags = a.wfl[i];
+  s.h = a.wh[j];
+  s.err_prev = a.wep[j];
+  s.cursor = a.wcur[j];
+  s.flags = a.wfl[j];
   s.n_acc = a.n_acc[i];
   s.n_rej = a.n_rej[i];
   s.status = a.status[i];
@@ -107,8 +117,9 @@ __device__ __forceinline__ void plain_load(const SolveArgs<T>& a, int i, Inst<T,
 // ---------------------------------------------------------------- plain form
 template <class Field, typename T, int R, int G>
 __global__ void k_plain_init(SolveArgs<T> a) {
-  const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
-  if (i >= a.B) return;
+  const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
+  if (j >= a.B) return;
+  const int i = queued(a, j);
   Field F;
   F.load(a.fparam, i);
   Inst<T, R> s;
@@ -116,20 +127,21 @@ __global__ void k_plain_init(SolveArgs<T> a) {
       inst_init<Field, T, R, G>(F, s, a.o, i, a.D, a.y0, a.t0, a.t1, rtol_of(a, i),
                                 atol_of(a, i), inst_out(a, i));
   if (run) tape_store<T, R, G>(a.tape, i, s);
-  plain_store<T, R, G>(a, i, s);
+  plain_store<T, R, G>(a, j, i, s);
   if (!run) inst_finalize<T, R, G>(s, a.o, i, a.D, a.yf, a.n_acc, a.n_rej, a.n_fe, a.status,
                                    a.trace);
 }
 
 template <class Field, typename T, int R, int G>
 __global__ void k_plain_step(SolveArgs<T> a) {
-  const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
-  if (i >= a.B) return;
+  const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
+  if (j >= a.B) return;
+  const int i = queued(a, j);
   if (a.status[i] != ST_RUNNING) return;  // masked: finished instances do no work
   Field F;
   F.load(a.fparam, i);
   Inst<T, R> s;
-  plain_load<T, R, G>(a, i, s);
+  plain_load<T, R, G>(a, j, i, s);
   const int acc_before = s.n_acc;
   T ys[6][R];
   const bool run =
@@ -138,7 +150,7 @@ __global__ void k_plain_step(SolveArgs<T> a) {
     tape_store_hacc<T, R, G>(a.tape, i, s, ys);
     if (run) tape_store<T, R, G>(a.tape, i, s);
   }
-  plain_store<T, R, G>(a, i, s);
+  plain_store<T, R, G>(a, j, i, s);
   if (!run) {
     inst_finalize<T, R, G>(s, a.o, i, a.D, a.yf, a.n_acc, a.n_rej, a.n_fe, a.status, a.trace);
   } else if (Grp<G>::rank() == 0) {
@@ -153,7 +165,7 @@ __global__ void k_plain_step(SolveArgs<T> a) {
 template <class Field, typename T, int R, int G>
 __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
   const int groups_total = (int)((gridDim.x * (size_t)blockDim.x) / G);
-  int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
+  int i = queued(a, (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G));
   Field F;
   Inst<T, R> s;
   bool have = false;
@@ -166,7 +178,7 @@ __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
       if (!have) {
         inst_finalize<T, R, G>(s, a.o, i, a.D, a.yf, a.n_acc, a.n_rej, a.n_fe, a.status,
                                a.trace);
-        i = grab_instance<G>(a.counter, groups_total);
+        i = queued(a, grab_instance<G>(a.counter, groups_total));
         continue;
       }
       tape_store<T, R, G>(a.tape, i, s);
@@ -181,7 +193,7 @@ __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
     } else {
       inst_finalize<T, R, G>(s, a.o, i, a.D, a.yf, a.n_acc, a.n_rej, a.n_fe, a.status, a.trace);
       have = false;
-      i = grab_instance<G>(a.counter, groups_total);
+      i = queued(a, grab_instance<G>(a.counter, groups_total));
     }
   }
 }
@@ -260,6 +272,8 @@ template <typename T> SolveArgs<T> make_solve_args(const SolveReq& r) {
   a.active = (int32_t*)p;
   a.counter = (int32_t*)(p + 128);
   p += align256(256);
+  a.order = r.o->order == 1 ? (const int32_t*)p : nullptr;
+  p += align256((size_t)r.B * 4);
   if (r.o->form == TODE_PLAIN) {
     const size_t ts = sizeof(T);
     a.wy = (T*)p;
@@ -282,13 +296,28 @@ template <typename T> SolveArgs<T> make_solve_args(const SolveReq& r) {
   return a;
 }
 
+// Default threads per CTA: 128, or fewer (down to one warp) when the batch
+// has fewer than 128 threads per SM, so that a small batch still spreads
+// over every SM instead of filling a few.
+inline int default_block(long long threads, int num_sms) {
+  const long long per_sm = (threads + num_sms - 1) / (num_sms > 0 ? num_sms : 1);
+  int b = 32;
+  while (b < 128 && b < per_sm) b *= 2;
+  return b;
+}
+
 template <class Field, typename T, int R, int G>
 tode_err launch_solve(const SolveReq& r) {
   SolveArgs<T> a = make_solve_args<T>(r);
   const cudaStream_t st = r.stream;
-  const int block = r.o->block > 0 ? r.o->block : 256;
-  if (block % 32 != 0 || block > 256) return TODE_EINVAL;
   const long long threads = (long long)r.B * G;
+  const int block = r.o->block > 0 ? r.o->block : default_block(threads, r.num_sms);
+  if (block % 32 != 0 || block > 256) return TODE_EINVAL;
+  if (a.order) {
+    k_counting_order<<<1, ORDER_BINS, 0, st>>>(r.B, IntervalBin{r.t0, r.t1},
+                                               const_cast<int32_t*>(a.order));
+    TODE_CUDA_TRY(cudaGetLastError());
+  }
   if (r.o->form == TODE_PLAIN) {
     const int grid = (int)((threads + block - 1) / block);
     if (grid == 0) return TODE_OK;

@@ -269,55 +269,8 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
 
 // ---------------------------------------------------------------- work order
 // The reverse sweeps are handed out longest first (by the forward's accepted
-// step counts), so that the long instances do not start last and stretch
-// the tail of the persistent grid.  One CTA counting-sorts the instances by
-// decreasing step count (capped at ORDER_BINS - 1); the order inside a bin is
-// arbitrary, which changes no result: every instance is reversed
-// independently of the others.
-constexpr int ORDER_BINS = 1024;
-
-template <int BINS>
-__global__ void __launch_bounds__(BINS) k_order_by_steps(const int32_t* n_acc,
-                                                         const int32_t* status, int B,
-                                                         int32_t* order) {
-  static_assert(BINS == 1024, "one thread per bin, 32 warps of 32");
-  __shared__ int cnt[BINS];
-  __shared__ int warp_tot[BINS / 32];
-  const int t = threadIdx.x;
-  cnt[t] = 0;
-  __syncthreads();
-  auto bin_of = [&](int i) {
-    // descending: bin 0 holds the longest; failed instances do no work
-    const int n = status[i] == ST_SUCCESS ? n_acc[i] : 0;
-    return BINS - 1 - (n < 0 ? 0 : (n > BINS - 1 ? BINS - 1 : n));
-  };
-  for (int i = t; i < B; i += BINS) atomicAdd(&cnt[bin_of(i)], 1);
-  __syncthreads();
-  // exclusive prefix sum over the bins (bin t is owned by thread t)
-  const int lane = t & 31, w = t >> 5;
-  const int c = cnt[t];
-  int incl = c;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += v;
-  }
-  if (lane == 31) warp_tot[w] = incl;
-  __syncthreads();
-  if (w == 0) {
-    int x = warp_tot[lane];
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane >= d) x += v;
-    }
-    warp_tot[lane] = x;  // inclusive over warps
-  }
-  __syncthreads();
-  cnt[t] = (w > 0 ? warp_tot[w - 1] : 0) + incl - c;
-  __syncthreads();
-  for (int i = t; i < B; i += BINS) order[atomicAdd(&cnt[bin_of(i)], 1)] = i;
-}
+// step counts, StepsBin), so that the long instances do not start last and
+// stretch the tail of the persistent grid.
 
 // Instance at queue position j (B past the end of the queue).
 template <typename T> __device__ __forceinline__ int queued(const AdjArgs<T>& a, int j) {
@@ -552,17 +505,19 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   a.st = (double*)p;
   p += align256((size_t)m * r.B * 8);
   a.sh = (T*)p;
-  const int block = 256;
+  const long long threads = (long long)r.B * AF::G;
+  const int block = r.o->block > 0 ? r.o->block : default_block(threads, r.num_sms);
+  if (block % 32 != 0 || block > 256) return TODE_EINVAL;
   auto kern = direct ? k_adjoint_steps<AF, T> : k_adjoint<AF, T>;
   int per_sm = 0;
   TODE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
   if (per_sm < 1) per_sm = 1;
   long long grid = (long long)r.num_sms * per_sm;
-  const long long need = ((long long)r.B * AF::G + block - 1) / block;
+  const long long need = (threads + block - 1) / block;
   if (grid > need) grid = need;
   if (grid == 0) return TODE_OK;
   TODE_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int32_t), r.stream));
-  k_order_by_steps<ORDER_BINS><<<1, ORDER_BINS, 0, r.stream>>>(r.n_acc, r.status, r.B, order);
+  k_counting_order<<<1, ORDER_BINS, 0, r.stream>>>(r.B, StepsBin{r.n_acc, r.status}, order);
   TODE_CUDA_TRY(cudaGetLastError());
   kern<<<(int)grid, block, 0, r.stream>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());

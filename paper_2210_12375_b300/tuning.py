@@ -3,9 +3,12 @@
 The fused persistent kernel and its adjoint take three launch knobs
 (``tode_options``): ``group`` (lanes per instance of the linear field),
 ``block`` (threads per CTA) and ``ctas_per_sm`` (resident CTAs per SM of the
-persistent grid); the plain form also takes ``poll_every``.  ``autotune``
-times the candidates on the caller's own batch (solve, or solve + adjoint)
-with CUDA events and returns the fastest, and caches the choice in a JSON
+persistent grid); the plain form also takes ``poll_every``, and both forms
+take ``order`` (index order, or longest integration interval first).
+``autotune`` times the candidates on the caller's own batch (solve, or
+solve + adjoint) with CUDA events -- the fused form replayed from a CUDA
+graph, so that host launch costs stay off the device timeline -- and
+returns the fastest, and caches the choice in a JSON
 file keyed by field kind, state size, precision, form, batch size (rounded
 to a power of two) and GPU name.  The cache file is ``$TODE_AUTOTUNE_CACHE``
 or the path given to ``set_cache_path``; without either, choices live in
@@ -81,16 +84,17 @@ def candidates(kind: str, D: int, form: str) -> List[dict]:
     groups = [0]
     if kind == "linear":
         groups = {16: [4, 8, 16], 32: [16]}.get(D, [D])
-    blocks = [128, 256]
+    blocks = [32, 64, 128, 256]
     out = []
     for g in groups:
         for b in blocks:
-            if form == "plain":
-                for p in (8, 16, 32):
-                    out.append({"group": g, "block": b, "poll_every": p})
-            else:
-                for c in (0, 1, 2, 4):
-                    out.append({"group": g, "block": b, "ctas_per_sm": c})
+            for order in (0, 1):
+                if form == "plain":
+                    for p in (8, 16, 32):
+                        out.append({"group": g, "block": b, "poll_every": p, "order": order})
+                else:
+                    for c in (0, 1, 2, 4):
+                        out.append({"group": g, "block": b, "ctas_per_sm": c, "order": order})
     return out
 
 
@@ -98,9 +102,16 @@ def _kind(field) -> str:
     return {api.VdP: "vdp", api.Linear: "linear", api.MLP: "mlp"}[type(field)]
 
 
-def _time_candidate(run: Callable[[], None], reps: int) -> float:
-    run()  # warm-up
+def _time_candidate(run: Callable[[], None], reps: int, graph: bool = False) -> float:
+    run()  # warm-up (and first-call set-up outside any capture)
     torch.cuda.synchronize()
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            run()
+        run = g.replay
+        run()
+        torch.cuda.synchronize()
     times = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -142,15 +153,16 @@ def autotune(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
                 torch.cuda.synchronize()
                 slots = max(1, int(probe.n_acc.max().item()))
                 tape = api.TapeBuffers.allocate(B, D, y0.dtype, slots, 1, y0.device,
-                                                stages=kind == "mlp")
+                                                stages=kind in ("mlp", "linear"))
 
             def timer(o):
                 def run():
-                    s = api.solve(field, y0, t0, t1, t_eval, form=form, tape=tape, **opt_kw, **o)
+                    kw = dict(opt_kw, **o)  # the candidate's knobs override the caller's
+                    s = api.solve(field, y0, t0, t1, t_eval, form=form, tape=tape, **kw)
                     if with_adjoint:
                         gy = torch.ones_like(s.y_final)
-                        api.adjoint(field, t0, t1, t_eval, s, tape, None, gy, **opt_kw, **o)
-                return _time_candidate(run, reps)
+                        api.adjoint(field, t0, t1, t_eval, s, tape, None, gy, **kw)
+                return _time_candidate(run, reps, graph=form == "fused")
         results = []
         for o in cands:
             try:

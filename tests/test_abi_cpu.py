@@ -71,7 +71,11 @@ def test_workspace_size_rules():
     n = lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 1000, 2)), C.byref(o), 16)
     assert n > 1000 * 2 * 8 * 3 and n % 256 == 0
     o2 = _opts(prec=_abi.TODE_F64, form=_abi.TODE_FUSED)
-    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 1000, 2)), C.byref(o2), 16) == 256
+    # fused: the work counter and the work order (1000 int32, 256-byte padded)
+    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 1000, 2)), C.byref(o2), 16) \
+        == 256 + 4096
+    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 1000, 2)),
+                                   C.byref(_opts(prec=_abi.TODE_F64, order=2)), 16) == 0
     # unsupported or invalid combinations report 0
     assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 10, 3)), C.byref(o), 1) == 0
     assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_LINEAR, 10, 5)), C.byref(o), 1) == 0

@@ -20,8 +20,9 @@ def _field_and_inputs(B=1000, D=16):
 def test_candidates_cover_the_knobs():
     c = at.candidates("linear", 16, "fused")
     assert {o["group"] for o in c} == {4, 8, 16}
-    assert {o["block"] for o in c} == {128, 256}
+    assert {o["block"] for o in c} == {32, 64, 128, 256}
     assert {o["ctas_per_sm"] for o in c} == {0, 1, 2, 4}
+    assert {o["order"] for o in c} == {0, 1}
     assert all("poll_every" in o for o in at.candidates("vdp", 2, "plain"))
     assert at.candidates("mlp", 32, "fused") == [{}]
 
@@ -31,13 +32,14 @@ def test_autotune_picks_fastest_and_caches(tmp_path):
     at._mem.clear()
     try:
         f, y0, t0, t1 = _field_and_inputs()
-        cost = lambda o: 1.0 + abs(o["group"] - 8) + 0.1 * o["ctas_per_sm"] + o["block"] / 1e4
+        cost = lambda o: (1.0 + abs(o["group"] - 8) + 0.1 * o["ctas_per_sm"]
+                          + abs(o["block"] - 128) / 1e4 - 0.01 * o["order"])
         best = at.autotune(f, y0, t0, t1, timer=cost)
-        assert best == {"group": 8, "block": 128, "ctas_per_sm": 0}
+        assert best == {"group": 8, "block": 128, "ctas_per_sm": 0, "order": 1}
         data = json.loads((tmp_path / "tune.json").read_text())
         (key, entry), = data.items()
         assert "linear|D16|B1024|float32|fused|fwd" in key
-        assert entry["options"] == best and len(entry["tried"]) == 24
+        assert entry["options"] == best and len(entry["tried"]) == 96
 
         def boom(o):
             raise AssertionError("the cache should answer")
