@@ -241,6 +241,9 @@ template <typename T, int R> struct Inst {
   T err_prev;
   T rtol, atol;
   int n_acc, n_rej, cursor, status, flags;
+  // the evaluation times at the cursor and after it (+inf past the last),
+  // held in registers so that the end-of-step test loads nothing
+  double tq, tq2;
 };
 
 struct SolveOpts {
@@ -269,6 +272,19 @@ template <typename T> struct InstOut {
   T* ye;             // [K][D]
   int K;
 };
+
+// Evaluation time q of the instance, +inf past the last one.
+template <typename T> __device__ __forceinline__ double te_at(const InstOut<T>& out, int q) {
+  return q < out.K ? out.te[q] : __longlong_as_double(0x7ff0000000000000LL);
+}
+// Moves the cursor past the point just written: the register pair shifts and
+// the time after the next one is loaded (its latency overlaps the attempt).
+template <typename T, int R>
+__device__ __forceinline__ void advance_cursor(Inst<T, R>& s, const InstOut<T>& out) {
+  s.cursor++;
+  s.tq = s.tq2;
+  s.tq2 = te_at(out, s.cursor + 1);
+}
 
 // Dense-output weights b_i(theta), each by Horner's rule (w[1] = 0).
 template <typename T> __device__ __forceinline__ void dense_weights(T th, T (&w)[7]) {
@@ -409,15 +425,21 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
     s.ylo[r] = T(0);
     s.k1[r] = T(0);
   }
-  // validity of the time arguments (Sec. 3: per-instance bounds and points)
+  // validity of the time arguments (Sec. 3: per-instance bounds and points):
+  // t0 <= te[0] <= ... <= te[K-1] <= t1, all finite; the group's lanes check
+  // the points in parallel (point q against its predecessor)
   bool ok = tfinite(s.t0) && tfinite(s.t1) && !(s.t1 < s.t0);
   const long long k0 = tkey(s.t0), k1 = tkey(s.t1);
-  long long kprev = k0;
-  for (int q = 0; q < out.K && ok; ++q) {
-    const double v = out.te[q];
-    const long long kv = tkey(v);
-    ok = tfinite(v) && kv >= kprev && kv <= k1;
-    kprev = kv;
+  {
+    bool okl = true;
+    for (int q = g; q < out.K; q += G) {
+      const double v = out.te[q];
+      const long long kv = tkey(v);
+      const long long kp = q > 0 ? tkey(out.te[q - 1]) : k0;
+      okl = okl && tfinite(v) && kv >= kp && kv <= k1;
+    }
+    if constexpr (G > 1) okl = __all_sync(Grp<G>::mask(), okl) != 0;
+    ok = ok && okl;
   }
   if (!ok) {
     s.status = ST_INVALID;
@@ -427,9 +449,11 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
     for (int q = 0; q < out.K; ++q) store_point<T, R, G>(out.ye + (size_t)q * D, nanv);
     return false;
   }
-  while (s.cursor < out.K && tkey(out.te[s.cursor]) == k0) {
+  s.tq = te_at(out, 0);
+  s.tq2 = te_at(out, 1);
+  while (tkey(s.tq) == k0) {  // points at t0 are y0 itself
     store_point<T, R, G>(out.ye + (size_t)s.cursor * D, s.y);
-    s.cursor++;
+    advance_cursor(s, out);
   }
   if (k1 == k0) {
     s.status = ST_SUCCESS;
@@ -602,8 +626,8 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
         ylon[r] = T(0);
       }
     }
-    while (s.cursor < out.K) {
-      const double tq = out.te[s.cursor];
+    while (true) {  // the points in (t, t_next]; +inf past the last point
+      const double tq = s.tq;
       const long long kq = tkey(tq);
       if (kq > kn) break;
       T* dst = out.ye + (size_t)s.cursor * D;
@@ -618,7 +642,7 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
         dense_point<T, R>(theta, h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
         store_point<T, R, G>(dst, v);
       }
-      s.cursor++;
+      advance_cursor(s, out);
     }
     T fac;
     if (err == T(0)) {

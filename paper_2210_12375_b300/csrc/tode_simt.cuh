@@ -103,6 +103,9 @@ __device__ __forceinline__ void plain_load(const SolveArgs<T>& a, int j, int i,
   s.err_prev = a.wep[j];
   s.cursor = a.wcur[j];
   s.flags = a.wfl[j];
+  const InstOut<T> out = inst_out(a, i);
+  s.tq = te_at(out, s.cursor);
+  s.tq2 = te_at(out, s.cursor + 1);
   s.n_acc = a.n_acc[i];
   s.n_rej = a.n_rej[i];
   s.status = a.status[i];

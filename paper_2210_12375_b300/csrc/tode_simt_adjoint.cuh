@@ -135,12 +135,55 @@ template <typename T> struct AdjArgs {
   T* sh;        // [stride][B]
 };
 
+// Cursor over an instance's evaluation points, from the last backwards: the
+// time of point q and of point q - 1 (-inf before the first) and the
+// cotangent of point q, held in registers so that a step with no point of
+// its own loads nothing, and a consumed point's successor is fetched while
+// the step is reversed.
+template <typename T, int R> struct AdjCursor {
+  int q;
+  double tq, tq2;
+  T gq[R];
+};
+
+template <typename T>
+__device__ __forceinline__ double adj_te(const AdjArgs<T>& a, int i, int q) {
+  return q >= 0 ? a.te[(size_t)i * a.K + q] : __longlong_as_double((long long)0xfff0000000000000ULL);
+}
+
+template <typename T, int R, int G>
+__device__ __forceinline__ void adj_gq(const AdjArgs<T>& a, int i, int D, int q, T (&gq)[R]) {
+  const int g = Grp<G>::rank();
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    gq[r] = (a.gye && q >= 0) ? a.gye[((size_t)i * a.K + q) * D + g * R + r] : T(0);
+}
+
+template <typename T, int R, int G>
+__device__ __forceinline__ void adj_cursor_start(AdjCursor<T, R>& c, const AdjArgs<T>& a, int i,
+                                                 int D) {
+  c.q = a.K - 1;
+  c.tq = adj_te(a, i, c.q);
+  c.tq2 = adj_te(a, i, c.q - 1);
+  adj_gq<T, R, G>(a, i, D, c.q, c.gq);
+}
+
+template <typename T, int R, int G>
+__device__ __forceinline__ void adj_cursor_next(AdjCursor<T, R>& c, const AdjArgs<T>& a, int i,
+                                                int D) {
+  c.q--;
+  c.tq = c.tq2;
+  c.tq2 = adj_te(a, i, c.q - 1);
+  adj_gq<T, R, G>(a, i, D, c.q, c.gq);
+}
+
 // Reverse one accepted step.  y: step-start state, yb: running cotangent,
-// q: cursor over the instance's evaluation points, from the last backwards.
+// c: cursor over the instance's evaluation points, from the last backwards.
 template <class AF, typename T, int R, int G>
 __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, int D, double t,
                                              T h, double t_next, const T (&y)[R],
-                                             const T (&k1)[R], const T* ys, T (&yb)[R], int& q) {
+                                             const T (&k1)[R], const T* ys, T (&yb)[R],
+                                             AdjCursor<T, R>& c) {
   using C = DP5;
   T Y[7][R];
 #pragma unroll
@@ -215,16 +258,13 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
 #pragma unroll
     for (int r = 0; r < R; ++r) kb[s][r] = h * bw[s] * yb[r];
   bool dense7 = false;
-  const int g = Grp<G>::rank();
   const long long kt = tkey(t), kn = tkey(t_next);
-  while (q >= 0) {
-    const double tq = a.te[(size_t)i * a.K + q];
+  while (true) {  // the points in (t, t_next]
+    const double tq = c.tq;
     const long long kq = tkey(tq);
     if (!(kq > kt)) break;
     if (a.gye) {
-      T gq[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + g * R + r];
+      const T (&gq)[R] = c.gq;
       T w[7];
       if (kq == kn) {
 #pragma unroll
@@ -243,7 +283,7 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
 #pragma unroll
       for (int r = 0; r < R; ++r) yb[r] = yb[r] + gq[r];
     }
-    q--;
+    adj_cursor_next<T, R, G>(c, a, i, D);
   }
   // reverse stage sweep
   const T A[7][6] = {{T(0), T(0), T(0), T(0), T(0), T(0)},
@@ -314,14 +354,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
   AF F;
   T yb[R];
   int n = -1;          // next step to reverse; < 0: the instance is done
-  int q = 0;           // evaluation-point cursor, from the last backwards
+  AdjCursor<T, R> c;   // evaluation-point cursor, from the last backwards
+  c.q = -1;
   bool bad = false;
   bool have = false;
   double t_after = 0.0;  // end of step n: t1, or the start of step n+1 (its slot's t)
   while (true) {
     if (n < 0) {
       if (have) {
-        adjoint_finish<AF, T>(F, a, i, q, bad, yb);
+        adjoint_finish<AF, T>(F, a, i, c.q, bad, yb);
         have = false;
         i = queued(a, grab_instance<G>(a.counter, groups_total));
       }
@@ -335,7 +376,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
-      q = a.K - 1;
+      adj_cursor_start<T, R, G>(c, a, i, D);
       t_after = a.t1[i];
       n = bad ? -1 : N - 1;
       have = true;
@@ -353,7 +394,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
     const double t_next = t_after;  // the forward's t + h, bit for bit
     t_after = t;
     const T* ys = a.tape.ystage ? a.tape.ystage + o * 6 * D : nullptr;
-    reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, ys, yb, q);
+    reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, ys, yb, c);
     --n;
   }
 }
@@ -388,7 +429,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
     T yb[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
-    int q = a.K - 1;
+    AdjCursor<T, R> c;
+    adj_cursor_start<T, R, G>(c, a, i, D);
     const double t1 = a.t1[i];
     for (int j = nseg - 1; j >= 0 && !bad; --j) {
       const int n0 = j * m;
@@ -413,6 +455,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
       s.n_acc = n0;
       s.n_rej = 0;
       s.cursor = 0;
+      s.tq = s.tq2 = te_at(no_out, 0);  // no evaluation points in a re-run
       s.status = ST_RUNNING;
       if constexpr (Comp<T>::on) {  // functions of (t, t0, t1), as in the forward
         s.rem = __double2float_rd(s.t1 - s.t);
@@ -459,11 +502,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
         const double t = a.st[p];
         const T h = a.sh[p];
         const double t_next = (n == N - 1) ? t1 : t + (double)h;
-        reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, nullptr, yb, q);
+        reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, nullptr, yb, c);
       }
       if constexpr (G > 1) __syncwarp(Grp<G>::mask());
     }
-    adjoint_finish<AF, T>(F, a, i, q, bad, yb);
+    adjoint_finish<AF, T>(F, a, i, c.q, bad, yb);
     i = queued(a, grab_instance<G>(a.counter, groups_total));
   }
 }
