@@ -116,6 +116,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
+# DRAM bytes (read + write) of one launch of a kernel on a workload, from
+# one ncu capture of that kernel as it stands (summaries under profiles/);
+# kernels without a capture of their current code report null.
+TRAFFIC = {
+    ("linear_d16_b8192", "k_fused<LinearField<float,1,16>>"): 47.84e6,
+    ("linear_d16_b8192", "k_adjoint_steps<LinearAdj<float,1,16>>"): 98.98e6,
+    ("mlp_d32_h128", "k_mlp_fused"): 19.21e6,
+    ("mlp_d32_h128", "k_mlp_adjoint"): 67.30e6,
+}
+
+
+def _traffic(workload: str, kernel: str):
+    for (wl, prefix), v in TRAFFIC.items():
+        if wl == workload and kernel.startswith(prefix):
+            return v
+    return None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -444,7 +462,8 @@ def run_tode(args):
               "kernel": f"k_mlp_adjoint<{net}>", "kernel_ms": k_adj_ms} if with_adjoint else None
         for r in (kf, ka) if with_adjoint else (kf,):
             r.update(bound="tensor", peak=peak, unit="TFLOP/s", frac=r["achieved"] / peak,
-                     traffic=None, peak_source=f"bf16 burst, {src} (MEASURED_PEAKS.json)")
+                     traffic=_traffic(w["name"], r["kernel"]),
+                     peak_source=f"bf16 burst, {src} (MEASURED_PEAKS.json)")
     else:
         psrc = f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {clk_mhz:.0f} MHz"
         tn = "double" if dtype == torch.float64 else "float"
@@ -460,10 +479,11 @@ def run_tode(args):
               "kernel": f"k_fused<{fld}> (fused forward)", "kernel_ms": k_fwd_ms}
         ka = {"achieved": adjoint_flops_per_step(kind, D, kind == "linear") * n_acc_total
               / (k_adj_ms * 1e-3)
-              / 1e12, "kernel": f"k_adjoint<{adj}> (stride-1 tape)", "kernel_ms": k_adj_ms}
+              / 1e12, "kernel": f"k_adjoint_steps<{adj}> (stride-1 tape)", "kernel_ms": k_adj_ms}
         for r in (kf, ka):
             r.update(bound="alu", peak=fp32_peak, unit="TFLOP/s",
-                     frac=r["achieved"] / fp32_peak, traffic=None, peak_source=psrc)
+                     frac=r["achieved"] / fp32_peak, traffic=_traffic(w["name"], r["kernel"]),
+                     peak_source=psrc)
     # the dominant kernel of the timed step (forward + adjoint) is the roofline line
     if with_adjoint:
         roofline, other = (ka, kf) if k_adj_ms >= k_fwd_ms else (kf, ka)

@@ -734,6 +734,8 @@ __global__ void __launch_bounds__(ORDER_BINS) k_counting_order(int B, BinOf bin_
   const int t = threadIdx.x;
   cnt[t] = 0;
   __syncthreads();
+  // independent iterations: unrolled so that their loads overlap
+#pragma unroll 8
   for (int i = t; i < B; i += ORDER_BINS) atomicAdd(&cnt[bin_of(i)], 1);
   __syncthreads();
   // exclusive prefix sum over the bins (thread t owns bin t)
@@ -759,6 +761,7 @@ __global__ void __launch_bounds__(ORDER_BINS) k_counting_order(int B, BinOf bin_
   __syncthreads();
   cnt[t] = (w > 0 ? warp_tot[w - 1] : 0) + incl - c;
   __syncthreads();
+#pragma unroll 8
   for (int i = t; i < B; i += ORDER_BINS) order[atomicAdd(&cnt[bin_of(i)], 1)] = i;
 }
 
