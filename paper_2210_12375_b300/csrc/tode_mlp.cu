@@ -224,6 +224,16 @@ __device__ __forceinline__ float tanh_acc(float x) {
   return copysignf(__fdividef(1.0f - e, 1.0f + e), x);
 }
 
+// tanh_acc of two values, the additions packed in pairs (FP32x2 operations
+// round each lane as the scalar ones: the same results, half the additions).
+__device__ __forceinline__ float2 tanh_acc2(float2 z) {
+  const float2 e = make_float2(__expf(-2.0f * fabsf(z.x)), __expf(-2.0f * fabsf(z.y)));
+  const float2 num = __ffma2_rn(e, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));  // 1 - e
+  const float2 den = __fadd2_rn(e, make_float2(1.0f, 1.0f));                           // 1 + e
+  return make_float2(copysignf(__fdividef(num.x, den.x), z.x),
+                     copysignf(__fdividef(num.y, den.y), z.y));
+}
+
 // Stores 16 consecutive values of a row as BF16 (hi, and lo = x - hi) into
 // core-matrix tiles with K columns, starting at column k0 (a multiple of 8).
 template <bool LO>
@@ -238,8 +248,10 @@ __device__ __forceinline__ void store_row16(unsigned char* th, unsigned char* tl
       const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
       hw[j] = *reinterpret_cast<const uint32_t*>(&h2);
       if (LO) {
-        const __nv_bfloat162 l2 =
-            __floats2bfloat162_rn(a - __low2float(h2), b - __high2float(h2));
+        // (a, b) - hi: the product hi * -1 is exact, so one rounding as a - hi
+        const float2 d = __ffma2_rn(make_float2(__low2float(h2), __high2float(h2)),
+                                    make_float2(-1.0f, -1.0f), make_float2(a, b));
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(d.x, d.y);
         lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
       }
     }
@@ -706,18 +718,38 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       if (l < NL - 1) {
         // hidden epilogue: bias, tanh, BF16 (split) into the hidden tile
         const float* bl = sBias + l * H;
+        // the accumulator loads of up to four 16-column chunks in flight
+        // together, one wait, then bias + tanh + split per chunk (the wide
+        // network, short of registers, takes one chunk at a time)
+        constexpr int NLD = Cfg::STREAM ? 1 : (Cfg::HC / 16 < 4 ? Cfg::HC / 16 : 4);
 #pragma unroll
-        for (int c = 0; c < Cfg::HC; c += 16) {
-          const int col = sub * Cfg::HC + c;
-          float v[16];
-          Cfg::hid_ld(tbase, tid, c, v);
+        for (int c0 = 0; c0 < Cfg::HC; c0 += 16 * NLD) {
+          float v[NLD][16];
+#pragma unroll
+          for (int u = 0; u < NLD; ++u) Cfg::hid_ld(tbase, tid, c0 + 16 * u, v[u]);
           tc::tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float z = v[j] + bl[col + j];
-            v[j] = Cfg::SPLIT ? tanh_acc(z) : tanh_fast(z);
+          for (int u = 0; u < NLD; ++u) {
+            const int col = sub * Cfg::HC + c0 + 16 * u;
+            const float4* b4 = reinterpret_cast<const float4*>(bl + col);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 bq = b4[q];
+              const float2 z0 = __fadd2_rn(make_float2(v[u][4 * q], v[u][4 * q + 1]),
+                                           make_float2(bq.x, bq.y));
+              const float2 z1 = __fadd2_rn(make_float2(v[u][4 * q + 2], v[u][4 * q + 3]),
+                                           make_float2(bq.z, bq.w));
+              if constexpr (Cfg::SPLIT) {
+                const float2 t0 = tanh_acc2(z0), t1 = tanh_acc2(z1);
+                v[u][4 * q] = t0.x, v[u][4 * q + 1] = t0.y;
+                v[u][4 * q + 2] = t1.x, v[u][4 * q + 3] = t1.y;
+              } else {
+                v[u][4 * q] = tanh_fast(z0.x), v[u][4 * q + 1] = tanh_fast(z0.y);
+                v[u][4 * q + 2] = tanh_fast(z1.x), v[u][4 * q + 3] = tanh_fast(z1.y);
+              }
+            }
+            store_row16<Cfg::SPLIT>(sHh, sHl, row, col, H, v[u]);
           }
-          store_row16<Cfg::SPLIT>(sHh, sHl, row, col, H, v);
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
