@@ -121,7 +121,6 @@ class ClockSampler:
 # kernels without a capture of their current code report null.
 TRAFFIC = {
     ("linear_d16_b8192", "k_fused<LinearField<float,1,16>>"): 47.84e6,
-    ("linear_d16_b8192", "k_adjoint_steps<LinearAdj<float,1,16>>"): 98.98e6,
     ("mlp_d32_h128", "k_mlp_fused"): 19.21e6,
     ("mlp_d32_h128", "k_mlp_adjoint"): 67.30e6,
 }

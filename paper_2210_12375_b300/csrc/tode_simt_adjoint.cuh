@@ -177,25 +177,60 @@ __device__ __forceinline__ void adj_cursor_next(AdjCursor<T, R>& c, const AdjArg
   adj_gq<T, R, G>(a, i, D, c.q, c.gq);
 }
 
-// Reverse one accepted step.  y: step-start state, yb: running cotangent,
-// c: cursor over the instance's evaluation points, from the last backwards.
-template <class AF, typename T, int R, int G>
-__device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, int D, double t,
-                                             T h, double t_next, const T (&y)[R],
-                                             const T (&k1)[R], const T* ys, T (&yb)[R],
+// One accepted step as the reverse sweep needs it: its start state y, the
+// FSAL stage k1 (when the stage inputs are recomputed) or the recorded stage
+// inputs Y_2..Y_7 (this lane's components), its start time and its size.
+template <typename T, int R> struct AdjSlot {
+  T y[R];
+  T k1[R];
+  T ys[6][R];
+  double t;
+  T h;
+};
+
+// Loads slot n of instance i from a stride-1 tape (YS: with stage inputs).
+template <bool YS, typename T, int R, int G>
+__device__ __forceinline__ void adj_load_slot(const AdjArgs<T>& a, int i, int D, int n,
+                                              AdjSlot<T, R>& sl) {
+  const int g = Grp<G>::rank();
+  const size_t o = (size_t)n * a.B + i;
+#pragma unroll
+  for (int r = 0; r < R; ++r) sl.y[r] = a.tape.y[o * D + g * R + r];
+  if constexpr (YS) {
+    const T* ys = a.tape.ystage + o * 6 * D + g * R;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+#pragma unroll
+      for (int r = 0; r < R; ++r) sl.ys[q][r] = ys[q * D + r];
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) sl.k1[r] = a.tape.k1[o * D + g * R + r];
+  }
+  sl.t = a.tape.t[o];
+  sl.h = a.tape.h_acc[o];
+}
+
+// Reverse one accepted step.  sl: the step (YS: with its recorded stage
+// inputs), yb: running cotangent, c: cursor over the instance's evaluation
+// points, from the last backwards.
+template <bool YS, class AF, typename T, int R, int G>
+__device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, int D,
+                                             const AdjSlot<T, R>& sl, double t_next, T (&yb)[R],
                                              AdjCursor<T, R>& c) {
   using C = DP5;
+  const double t = sl.t;
+  const T h = sl.h;
+  const T (&y)[R] = sl.y;
+  const T (&k1)[R] = sl.k1;
   T Y[7][R];
 #pragma unroll
   for (int r = 0; r < R; ++r) Y[0][r] = y[r];
-  if (ys) {
-    // the forward recorded this step's stage inputs Y_2..Y_7 ([6][D], this
-    // lane's components at g*R)
-    const int g = Grp<G>::rank();
+  if constexpr (YS) {
+    // the forward recorded this step's stage inputs Y_2..Y_7
 #pragma unroll
     for (int q6 = 0; q6 < 6; ++q6)
 #pragma unroll
-      for (int r = 0; r < R; ++r) Y[q6 + 1][r] = ys[q6 * D + g * R + r];
+      for (int r = 0; r < R; ++r) Y[q6 + 1][r] = sl.ys[q6][r];
   } else {
     // recompute them with the forward's operations (bit for bit)
     T k[6][R];
@@ -344,7 +379,7 @@ __device__ __forceinline__ void adjoint_finish(AF& F, const AdjArgs<T>& a, int i
 // iteration reverses one step straight from its slot, and a group whose
 // instance is done finishes it and steals the next at once, so the groups of
 // a warp stay on the common step body whatever their step counts.
-template <class AF, typename T>
+template <class AF, typename T, bool YS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(AdjArgs<T> a) {
   constexpr int R = AF::R, G = AF::G;
   const int D = a.D;
@@ -359,6 +394,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
   bool bad = false;
   bool have = false;
   double t_after = 0.0;  // end of step n: t1, or the start of step n+1 (its slot's t)
+  AdjSlot<T, R> cur, nxt;  // step n, and step n - 1 in flight
   while (true) {
     if (n < 0) {
       if (have) {
@@ -381,20 +417,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
       n = bad ? -1 : N - 1;
       have = true;
       if (n < 0) continue;
+      adj_load_slot<YS, T, R, G>(a, i, D, n, cur);
     }
-    const size_t o = (size_t)n * a.B + i;
-    T y[R], k1[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      y[r] = a.tape.y[o * D + g * R + r];
-      k1[r] = a.tape.k1[o * D + g * R + r];
-    }
-    const double t = a.tape.t[o];
-    const T h = a.tape.h_acc[o];
+    // the next step's slot is fetched while this one is reversed
+    if (n > 0) adj_load_slot<YS, T, R, G>(a, i, D, n - 1, nxt);
     const double t_next = t_after;  // the forward's t + h, bit for bit
-    t_after = t;
-    const T* ys = a.tape.ystage ? a.tape.ystage + o * 6 * D : nullptr;
-    reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, ys, yb, c);
+    t_after = cur.t;
+    reverse_step<YS, AF, T, R, G>(F, a, i, D, cur, t_next, yb, c);
+    cur = nxt;
     --n;
   }
 }
@@ -493,16 +523,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
       if constexpr (G > 1) __syncwarp(Grp<G>::mask());
       for (int n = n1 - 1; n >= n0; --n) {
         const size_t p = (size_t)(n - n0) * a.B + i;
-        T y[R], k1[R];
+        AdjSlot<T, R> sl;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          y[r] = a.sy[p * D + g * R + r];
-          k1[r] = a.sk1[p * D + g * R + r];
+          sl.y[r] = a.sy[p * D + g * R + r];
+          sl.k1[r] = a.sk1[p * D + g * R + r];
         }
-        const double t = a.st[p];
-        const T h = a.sh[p];
-        const double t_next = (n == N - 1) ? t1 : t + (double)h;
-        reverse_step<AF, T, R, G>(F, a, i, D, t, h, t_next, y, k1, nullptr, yb, c);
+        sl.t = a.st[p];
+        sl.h = a.sh[p];
+        const double t_next = (n == N - 1) ? t1 : sl.t + (double)sl.h;
+        reverse_step<false, AF, T, R, G>(F, a, i, D, sl, t_next, yb, c);
       }
       if constexpr (G > 1) __syncwarp(Grp<G>::mask());
     }
@@ -551,7 +581,8 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   const long long threads = (long long)r.B * AF::G;
   const int block = r.o->block > 0 ? r.o->block : default_block(threads, r.num_sms);
   if (block % 32 != 0 || block > 256) return TODE_EINVAL;
-  auto kern = direct ? k_adjoint_steps<AF, T> : k_adjoint<AF, T>;
+  auto kern = !direct ? k_adjoint<AF, T>
+              : r.tape->y_stage ? k_adjoint_steps<AF, T, true> : k_adjoint_steps<AF, T, false>;
   int per_sm = 0;
   TODE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
   if (per_sm < 1) per_sm = 1;
