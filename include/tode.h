@@ -137,22 +137,25 @@ typedef struct {
  * accepted step is on the tape with its size and tode_adjoint reverses it
  * directly, without re-running the forward's attempts.
  * MLP field: stride must be 1; y, k1, t, h_acc and y_stage are used (the
- * adjoint reverses every step from its recorded stage inputs). */
+ * adjoint reverses every step from its recorded stage inputs).
+ * Every array is instance-major ([B][slots]...): the slots of one instance
+ * are contiguous, so a lane group's successive checkpoint stores (and the
+ * adjoint's loads) stay within the same cache lines. */
 typedef struct {
   int slots;
   int stride;
-  void* y;          /* [slots][B][D] state dtype */
-  void* y_lo;       /* [slots][B][D] float: compensation term of an FP32 state
+  void* y;          /* [B][slots][D] state dtype */
+  void* y_lo;       /* [B][slots][D] float: compensation term of an FP32 state
                        (TODE_F32 / TODE_BF16W); ignored for TODE_F64 (may be NULL) */
-  void* k1;         /* [slots][B][D] state dtype: f(t, y) carried by FSAL */
-  double* t;        /* [slots][B] */
-  void* h;          /* [slots][B] state dtype: step proposed for the next attempt */
-  void* err_prev;   /* [slots][B] state dtype */
-  int32_t* flags;   /* [slots][B] */
-  void* h_acc;      /* [slots][B] state dtype: size of the accepted step that
+  void* k1;         /* [B][slots][D] state dtype: f(t, y) carried by FSAL */
+  double* t;        /* [B][slots] */
+  void* h;          /* [B][slots] state dtype: step proposed for the next attempt */
+  void* err_prev;   /* [B][slots] state dtype */
+  int32_t* flags;   /* [B][slots] */
+  void* h_acc;      /* [B][slots] state dtype: size of the accepted step that
                        starts at the slot (written when that step is accepted;
                        required for the MLP field, optional otherwise) */
-  void* y_stage;    /* [slots][B][6][D] state dtype: the stage inputs Y_2..Y_7
+  void* y_stage;    /* [B][slots][6][D] state dtype: the stage inputs Y_2..Y_7
                        of the accepted step (MLP field: required; other fields
                        ignore it, may be NULL) */
 } tode_tape;

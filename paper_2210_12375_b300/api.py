@@ -153,7 +153,8 @@ class TapeBuffers:
     """Checkpoint tape for the adjoint: slot j = solver state at the start of
     accepted step j*stride (state, FSAL stage, time, step, controller); with
     ``stages`` (required for the MLP field) also the stage inputs Y_2..Y_7 of
-    every accepted step."""
+    every accepted step.  Instance-major: every array is [B, slots, ...], so
+    an instance's slots are contiguous."""
     slots: int
     stride: int
     y: torch.Tensor
@@ -164,21 +165,21 @@ class TapeBuffers:
     err_prev: torch.Tensor
     flags: torch.Tensor
     h_acc: Optional[torch.Tensor]  # None: the adjoint re-runs each segment's attempts
-    y_stage: Optional[torch.Tensor] = None  # [slots, B, 6, D]: Y_2..Y_7 (MLP field)
+    y_stage: Optional[torch.Tensor] = None  # [B, slots, 6, D]: Y_2..Y_7
 
     @staticmethod
     def allocate(B, D, dtype, slots, stride, device, stages: bool = False):
-        comp = (slots, B, D) if dtype != torch.float64 else (1,)
+        comp = (B, slots, D) if dtype != torch.float64 else (1,)
         return TapeBuffers(slots, stride,
-                           torch.empty((slots, B, D), dtype=dtype, device=device),
+                           torch.empty((B, slots, D), dtype=dtype, device=device),
                            torch.empty(comp, dtype=dtype, device=device),
-                           torch.empty((slots, B, D), dtype=dtype, device=device),
-                           torch.empty((slots, B), dtype=torch.float64, device=device),
-                           torch.empty((slots, B), dtype=dtype, device=device),
-                           torch.empty((slots, B), dtype=dtype, device=device),
-                           torch.empty((slots, B), dtype=torch.int32, device=device),
-                           torch.empty((slots, B), dtype=dtype, device=device),
-                           torch.empty((slots, B, 6, D), dtype=dtype, device=device)
+                           torch.empty((B, slots, D), dtype=dtype, device=device),
+                           torch.empty((B, slots), dtype=torch.float64, device=device),
+                           torch.empty((B, slots), dtype=dtype, device=device),
+                           torch.empty((B, slots), dtype=dtype, device=device),
+                           torch.empty((B, slots), dtype=torch.int32, device=device),
+                           torch.empty((B, slots), dtype=dtype, device=device),
+                           torch.empty((B, slots, 6, D), dtype=dtype, device=device)
                            if stages else None)
 
     @staticmethod

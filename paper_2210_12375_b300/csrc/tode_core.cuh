@@ -340,7 +340,7 @@ template <typename T> struct TapeDev {
   T* err_prev;
   int32_t* flags;
   T* h_acc;   // optional: size of the accepted step that starts at the slot
-  T* ystage;  // optional: its stage inputs Y_2..Y_7, [slots][B][6][D]
+  T* ystage;  // optional: its stage inputs Y_2..Y_7, [B][slots][6][D]
 };
 struct TraceDev {
   int cap;
@@ -356,7 +356,7 @@ __device__ __forceinline__ void tape_store(const TapeDev<T>& tp, int i, const In
   if (tp.slots == 0 || (s.n_acc % tp.stride) != 0) return;
   const int j = s.n_acc / tp.stride;
   if (j >= tp.slots) return;
-  const size_t o = (size_t)j * tp.B + i;
+  const size_t o = (size_t)i * tp.slots + j;  // instance-major: [B][slots]
   const int g = Grp<G>::rank();
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -385,9 +385,9 @@ __device__ __forceinline__ void tape_store_hacc(const TapeDev<T>& tp, int i, con
   if (tp.slots == 0 || !tp.h_acc || (n % tp.stride) != 0) return;
   const int j = n / tp.stride;
   if (j >= tp.slots) return;
-  if (Grp<G>::rank() == 0) tp.h_acc[(size_t)j * tp.B + i] = s.h_last;
+  if (Grp<G>::rank() == 0) tp.h_acc[(size_t)i * tp.slots + j] = s.h_last;
   if (tp.ystage && tp.stride == 1) {
-    T* dst = tp.ystage + ((size_t)j * tp.B + i) * 6 * tp.D + Grp<G>::rank() * R;
+    T* dst = tp.ystage + ((size_t)i * tp.slots + j) * 6 * tp.D + Grp<G>::rank() * R;
 #pragma unroll
     for (int q = 0; q < 6; ++q)
 #pragma unroll

@@ -62,7 +62,7 @@ struct MlpArgs {
   float* tp_k1;
   double* tp_t;
   float* tp_h;
-  float* tp_ys;  // [slots][B][6][D]: stage inputs Y_2..Y_7 of the accepted step
+  float* tp_ys;  // [B][slots][6][D]: stage inputs Y_2..Y_7 of the accepted step
   // plain form: solver state between launches, and the "some instance is
   // still running" flag the host polls
   float* wy;
@@ -638,7 +638,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       // tape: the stage inputs of this attempt (a retry after a rejection
       // overwrites them; the accepted attempt's stay)
       float4* dst = reinterpret_cast<float4*>(
-          a.tp_ys + (((size_t)s.n_acc * a.B + s.inst) * 6 + (stage - 2)) * D + coff);
+          a.tp_ys + (((size_t)s.inst * a.slots + s.n_acc) * 6 + (stage - 2)) * D + coff);
 #pragma unroll
       for (int q = 0; q < C / 4; ++q)
         dst[q] = make_float4(Y[4 * q], Y[4 * q + 1], Y[4 * q + 2], Y[4 * q + 3]);
@@ -884,7 +884,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         }
         const long long kn = tkey(t_next);
         if (s.n_acc < a.slots) {  // tape: the state this accepted step started from
-          const size_t o = (size_t)s.n_acc * a.B + i;
+          const size_t o = (size_t)i * a.slots + s.n_acc;
 #pragma unroll
           for (int r = 0; r < C; ++r) {
             a.tp_y[o * D + coff + r] = y[r];
@@ -1136,7 +1136,7 @@ struct MlpAdjArgs {
   const float* tp_k1;
   const double* tp_t;
   const float* tp_h;
-  const float* tp_ys;  // [slots][B][6][D]: Y_2..Y_7
+  const float* tp_ys;  // [B][slots][6][D]: Y_2..Y_7
   const float* gye;
   const float* gyf;
   float* gy0;
@@ -1262,7 +1262,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   // step n of instance i: its time and size (the stage inputs come from the
   // tape round by round)
   auto load_step = [&](int i) {
-    const size_t o = (size_t)n * a.B + i;
+    const size_t o = (size_t)i * a.slots + n;
     tn = a.tp_t[o];
     h = a.tp_h[o];
     tnext = (n == N - 1) ? a.t1[i] : tn + (double)h;
@@ -1270,7 +1270,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   };
   // Y_s of the step being reversed: Y_1 = y_n, Y_2..Y_7 as the forward recorded
   auto load_stage = [&](int s_, float (&Yo)[16]) {
-    const size_t o = (size_t)n * a.B + inst;
+    const size_t o = (size_t)inst * a.slots + n;
     const float4* p = s_ == 1
         ? reinterpret_cast<const float4*>(a.tp_y + o * D + coff)
         : reinterpret_cast<const float4*>(a.tp_ys + (o * 6 + (s_ - 2)) * D + coff);
@@ -1716,7 +1716,7 @@ struct WideAdjArgs {
   uint16_t* sa[4][2];  // X [80], h1, h2, h3 [512]
   uint16_t* sg[4][2];  // delta1, delta2, delta3 [512], kbar [64]
   int cap;             // reverse rounds per CTA
-  const float* tp_ys;  // [slots][Btot][6][D]: Y_2..Y_7
+  const float* tp_ys;  // [Btot][slots][6][D]: Y_2..Y_7
   int32_t* overflow;
   int32_t* err;
 };
@@ -1848,7 +1848,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     for (int j = 0; j < 7; ++j) kb[j][r] = 0.0f;
   }
   auto load_step = [&](int i) {
-    const size_t o = (size_t)n * a.Btot + i;
+    const size_t o = (size_t)i * a.slots + n;
     tn = a.tp_t[o];
     h = a.tp_h[o];
     tnext = (n == N - 1) ? a.t1[i] : tn + (double)h;
@@ -1856,7 +1856,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
   };
   // Y_s of the step being reversed: Y_1 = y_n, Y_2..Y_7 as the forward recorded
   auto load_stage = [&](int s_, float (&Yo)[16]) {
-    const size_t o = (size_t)n * a.Btot + inst;
+    const size_t o = (size_t)inst * a.slots + n;
     const float4* p = s_ == 1
         ? reinterpret_cast<const float4*>(a.tp_y + o * D + coff)
         : reinterpret_cast<const float4*>(a.tp_ys + (o * 6 + (s_ - 2)) * D + coff);

@@ -193,7 +193,7 @@ template <bool YS, typename T, int R, int G>
 __device__ __forceinline__ void adj_load_slot(const AdjArgs<T>& a, int i, int D, int n,
                                               AdjSlot<T, R>& sl) {
   const int g = Grp<G>::rank();
-  const size_t o = (size_t)n * a.B + i;
+  const size_t o = (size_t)i * a.tape.slots + n;
 #pragma unroll
   for (int r = 0; r < R; ++r) sl.y[r] = a.tape.y[o * D + g * R + r];
   if constexpr (YS) {
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
       const int n1 = (n0 + m < N) ? n0 + m : N;
       // restore the slot and re-run the forward over the segment
       Inst<T, R> s;
-      const size_t o = (size_t)j * a.B + i;
+      const size_t o = (size_t)i * a.tape.slots + j;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         s.y[r] = a.tape.y[o * D + g * R + r];
