@@ -232,7 +232,7 @@ def run_tode(args):
     # every field has both forms and the adjoint (--fwd-only drops the latter)
     with_adjoint = not args.fwd_only
     tape = tode.TapeBuffers.allocate(B, D, dtype, max(1, n_acc_max), 1, dev,
-                                     stages=mlp or kind == "linear")
+                                     stages=mlp or kind == "linear", minimal=True)
 
     def fwd(form, sol=None, ws=None):
         return tode.solve(field, y0, t0, t1, te, form=form, tape=tape, out=sol, workspace=ws,

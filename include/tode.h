@@ -140,7 +140,12 @@ typedef struct {
  * adjoint reverses every step from its recorded stage inputs).
  * Every array is instance-major ([B][slots]...): the slots of one instance
  * are contiguous, so a lane group's successive checkpoint stores (and the
- * adjoint's loads) stay within the same cache lines. */
+ * adjoint's loads) stay within the same cache lines.  Every array must be
+ * 16-byte aligned (TODE_EINVAL otherwise).
+ * A stride-1 tape with h_acc needs only y, t, h_acc and either k1 or
+ * y_stage: y_lo, h, err_prev and flags (and k1 when y_stage is given) may
+ * be NULL and are then not written -- they serve the re-run of strided
+ * segments only.  The MLP field never needs k1. */
 typedef struct {
   int slots;
   int stride;

@@ -158,44 +158,56 @@ class TapeBuffers:
     slots: int
     stride: int
     y: torch.Tensor
-    y_lo: torch.Tensor
-    k1: torch.Tensor
+    y_lo: Optional[torch.Tensor]  # None: a minimal tape (below)
+    k1: Optional[torch.Tensor]
     t: torch.Tensor
-    h: torch.Tensor
-    err_prev: torch.Tensor
-    flags: torch.Tensor
+    h: Optional[torch.Tensor]
+    err_prev: Optional[torch.Tensor]
+    flags: Optional[torch.Tensor]
     h_acc: Optional[torch.Tensor]  # None: the adjoint re-runs each segment's attempts
     y_stage: Optional[torch.Tensor] = None  # [B, slots, 6, D]: Y_2..Y_7
 
     @staticmethod
-    def allocate(B, D, dtype, slots, stride, device, stages: bool = False):
+    def allocate(B, D, dtype, slots, stride, device, stages: bool = False,
+                 minimal: bool = False):
+        """``minimal`` (stride 1 only): just what the direct adjoint reads --
+        y, t, the accepted step sizes and k1 (or, with ``stages``, the stage
+        inputs instead); the forward then writes nothing else."""
+        if minimal and stride != 1:
+            raise ValueError("a minimal tape needs stride 1")
+
+        def e(shape, dt=dtype, keep=True):
+            return torch.empty(shape, dtype=dt, device=device) if keep else None
+        full = not minimal
         comp = (B, slots, D) if dtype != torch.float64 else (1,)
         return TapeBuffers(slots, stride,
-                           torch.empty((B, slots, D), dtype=dtype, device=device),
-                           torch.empty(comp, dtype=dtype, device=device),
-                           torch.empty((B, slots, D), dtype=dtype, device=device),
-                           torch.empty((B, slots), dtype=torch.float64, device=device),
-                           torch.empty((B, slots), dtype=dtype, device=device),
-                           torch.empty((B, slots), dtype=dtype, device=device),
-                           torch.empty((B, slots), dtype=torch.int32, device=device),
-                           torch.empty((B, slots), dtype=dtype, device=device),
-                           torch.empty((B, slots, 6, D), dtype=dtype, device=device)
-                           if stages else None)
+                           e((B, slots, D)),
+                           e(comp, keep=full),
+                           e((B, slots, D), keep=full or not stages),
+                           e((B, slots), torch.float64),
+                           e((B, slots), keep=full),
+                           e((B, slots), keep=full),
+                           e((B, slots), torch.int32, keep=full),
+                           e((B, slots)),
+                           e((B, slots, 6, D), keep=stages))
 
     @staticmethod
-    def bytes_per_slot(B, D, itemsize, stages: bool = False):
+    def bytes_per_slot(B, D, itemsize, stages: bool = False, minimal: bool = False):
+        if minimal:  # y, k1 or the stage inputs, t, h_acc
+            return B * (D * itemsize + (6 * D if stages else D) * itemsize + 8 + itemsize)
         comp = D * itemsize if itemsize == 4 else 0
         return B * (2 * D * itemsize + comp + 8 + 3 * itemsize + 4 +
                     (6 * D * itemsize if stages else 0))
 
     def c(self) -> _abi.Tape:
+        def ptr(x):
+            return x.data_ptr() if x is not None else None
         tp = _abi.Tape()
         tp.slots, tp.stride = self.slots, self.stride
-        tp.y, tp.y_lo, tp.k1 = self.y.data_ptr(), self.y_lo.data_ptr(), self.k1.data_ptr()
-        tp.t, tp.h = self.t.data_ptr(), self.h.data_ptr()
-        tp.err_prev, tp.flags = self.err_prev.data_ptr(), self.flags.data_ptr()
-        tp.h_acc = self.h_acc.data_ptr() if self.h_acc is not None else None
-        tp.y_stage = self.y_stage.data_ptr() if self.y_stage is not None else None
+        tp.y, tp.y_lo, tp.k1 = ptr(self.y), ptr(self.y_lo), ptr(self.k1)
+        tp.t, tp.h = ptr(self.t), ptr(self.h)
+        tp.err_prev, tp.flags = ptr(self.err_prev), ptr(self.flags)
+        tp.h_acc, tp.y_stage = ptr(self.h_acc), ptr(self.y_stage)
         return tp
 
 

@@ -31,22 +31,25 @@ def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint):
     B, D = y0.shape
     dev, dtype = y0.device, y0.dtype
     mlp = isinstance(field, api.MLP)
-    per_slot = api.TapeBuffers.bytes_per_slot(B, D, y0.element_size(), stages=mlp)
+    per_slot = api.TapeBuffers.bytes_per_slot(B, D, y0.element_size(), stages=mlp,
+                                              minimal=True)
     max_slots = max(1, budget // max(per_slot, 1))
     slots = max(1, min(max_slots, hint))
-    tape = api.TapeBuffers.allocate(B, D, dtype, slots, 1, dev, stages=mlp)
+    tape = api.TapeBuffers.allocate(B, D, dtype, slots, 1, dev, stages=mlp, minimal=True)
     sol = api.solve(field, y0, t0, t1, t_eval, tape=tape, form="fused", **opt)
     N = int(sol.n_acc.max().item()) if B > 0 else 0
     if N > slots:
+        full_slot = api.TapeBuffers.bytes_per_slot(B, D, y0.element_size(), stages=mlp)
         if N <= max_slots:
             stride = 1
         elif mlp:
             raise RuntimeError(f"the MLP adjoint keeps every accepted step: {N} slots of "
                                f"{per_slot} bytes exceed the tape budget of {budget} bytes")
-        else:
-            stride = math.ceil(N / max_slots)
+        else:  # strided segments are re-run: the tape keeps the whole state
+            stride = math.ceil(N / max(1, budget // max(full_slot, 1)))
         slots = math.ceil(N / stride)
-        tape = api.TapeBuffers.allocate(B, D, dtype, slots, stride, dev, stages=mlp)
+        tape = api.TapeBuffers.allocate(B, D, dtype, slots, stride, dev, stages=mlp,
+                                        minimal=stride == 1)
         # the solve is deterministic: the re-run fills the tape on the same mesh
         sol = api.solve(field, y0, t0, t1, t_eval, tape=tape, form="fused", **opt)
     return sol, tape, N

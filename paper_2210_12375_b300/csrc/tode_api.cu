@@ -55,12 +55,20 @@ static tode_err field_ok(const tode_field_desc* f, const tode_options* o) {
   return TODE_EINVAL;
 }
 
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 static bool tape_ok(const tode_tape* tp, const tode_options* o, const tode_field_desc* f) {
-  if (f->kind == TODE_MLP)
-    return tp->slots >= 1 && tp->stride == 1 && tp->y && tp->k1 && tp->t && tp->h_acc &&
-           tp->y_stage;
-  return tp->slots >= 1 && tp->stride >= 1 && tp->y && tp->k1 && tp->t && tp->h &&
-         tp->err_prev && tp->flags && (o->prec == TODE_F64 || tp->y_lo);
+  const void* arrays[] = {tp->y, tp->y_lo, tp->k1, tp->t, tp->h, tp->err_prev, tp->flags,
+                          tp->h_acc, tp->y_stage};
+  for (const void* p : arrays)
+    if (!aligned16(p)) return false;  // NULL passes
+  if (tp->slots < 1 || tp->stride < 1 || !tp->y || !tp->t) return false;
+  if (f->kind == TODE_MLP) return tp->stride == 1 && tp->h_acc && tp->y_stage;
+  // stride 1 with the accepted step sizes: reversed straight from the slots,
+  // which need the FSAL stage only when the stage inputs are not recorded
+  if (tp->stride == 1 && tp->h_acc) return tp->k1 || tp->y_stage;
+  // otherwise segments are re-run from their slots: the whole solver state
+  return tp->k1 && tp->h && tp->err_prev && tp->flags && (o->prec == TODE_F64 || tp->y_lo);
 }
 
 static int sm_count_or_zero() {

@@ -330,6 +330,36 @@ __device__ __forceinline__ void store_point(T* dst, const T (&v)[R]) {
 }
 
 // ---------------------------------------------------------------- tape / trace
+// R consecutive components of one lane at p (p aligned to R * sizeof(T)
+// when that is 8 or 16 bytes): one vector access instead of R.
+template <typename T, int R> __device__ __forceinline__ void st_row(T* p, const T (&v)[R]) {
+  if constexpr (R == 2 && sizeof(T) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (R == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 2 && sizeof(T) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[r] = v[r];
+  }
+}
+template <typename T, int R> __device__ __forceinline__ void ld_row(const T* p, T (&v)[R]) {
+  if constexpr (R == 2 && sizeof(T) == 4) {
+    const float2 u = *reinterpret_cast<const float2*>(p);
+    v[0] = u.x, v[1] = u.y;
+  } else if constexpr (R == 4 && sizeof(T) == 4) {
+    const float4 u = *reinterpret_cast<const float4*>(p);
+    v[0] = u.x, v[1] = u.y, v[2] = u.z, v[3] = u.w;
+  } else if constexpr (R == 2 && sizeof(T) == 8) {
+    const double2 u = *reinterpret_cast<const double2*>(p);
+    v[0] = u.x, v[1] = u.y;
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = p[r];
+  }
+}
+
 template <typename T> struct TapeDev {
   int slots, stride, B, D;
   T* y;
@@ -358,20 +388,18 @@ __device__ __forceinline__ void tape_store(const TapeDev<T>& tp, int i, const In
   if (j >= tp.slots) return;
   const size_t o = (size_t)i * tp.slots + j;  // instance-major: [B][slots]
   const int g = Grp<G>::rank();
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    tp.y[o * tp.D + g * R + r] = s.y[r];
-    tp.k1[o * tp.D + g * R + r] = s.k1[r];
-  }
+  st_row<T, R>(tp.y + o * tp.D + g * R, s.y);
+  // a stride-1 tape with the accepted step sizes may leave out what only a
+  // re-run needs (k1 too when it records the stage inputs)
+  if (tp.k1) st_row<T, R>(tp.k1 + o * tp.D + g * R, s.k1);
   if constexpr (Comp<T>::on) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) tp.ylo[o * tp.D + g * R + r] = s.ylo[r];
+    if (tp.ylo) st_row<T, R>(tp.ylo + o * tp.D + g * R, s.ylo);
   }
   if (g == 0) {
     tp.t[o] = s.t;
-    tp.h[o] = s.h;
-    tp.err_prev[o] = s.err_prev;
-    tp.flags[o] = s.flags;
+    if (tp.h) tp.h[o] = s.h;
+    if (tp.err_prev) tp.err_prev[o] = s.err_prev;
+    if (tp.flags) tp.flags[o] = s.flags;
   }
 }
 
@@ -389,9 +417,7 @@ __device__ __forceinline__ void tape_store_hacc(const TapeDev<T>& tp, int i, con
   if (tp.ystage && tp.stride == 1) {
     T* dst = tp.ystage + ((size_t)i * tp.slots + j) * 6 * tp.D + Grp<G>::rank() * R;
 #pragma unroll
-    for (int q = 0; q < 6; ++q)
-#pragma unroll
-      for (int r = 0; r < R; ++r) dst[q * tp.D + r] = ys[q][r];
+    for (int q = 0; q < 6; ++q) st_row<T, R>(dst + q * tp.D, ys[q]);
   }
 }
 

@@ -888,7 +888,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
 #pragma unroll
           for (int r = 0; r < C; ++r) {
             a.tp_y[o * D + coff + r] = y[r];
-            a.tp_k1[o * D + coff + r] = k1[r];
+            if (a.tp_k1) a.tp_k1[o * D + coff + r] = k1[r];
           }
           if (sub == 0) {
             a.tp_t[o] = s.t;

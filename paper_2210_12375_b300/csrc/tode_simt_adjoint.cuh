@@ -194,17 +194,13 @@ __device__ __forceinline__ void adj_load_slot(const AdjArgs<T>& a, int i, int D,
                                               AdjSlot<T, R>& sl) {
   const int g = Grp<G>::rank();
   const size_t o = (size_t)i * a.tape.slots + n;
-#pragma unroll
-  for (int r = 0; r < R; ++r) sl.y[r] = a.tape.y[o * D + g * R + r];
+  ld_row<T, R>(a.tape.y + o * D + g * R, sl.y);
   if constexpr (YS) {
     const T* ys = a.tape.ystage + o * 6 * D + g * R;
 #pragma unroll
-    for (int q = 0; q < 6; ++q)
-#pragma unroll
-      for (int r = 0; r < R; ++r) sl.ys[q][r] = ys[q * D + r];
+    for (int q = 0; q < 6; ++q) ld_row<T, R>(ys + q * D, sl.ys[q]);
   } else {
-#pragma unroll
-    for (int r = 0; r < R; ++r) sl.k1[r] = a.tape.k1[o * D + g * R + r];
+    ld_row<T, R>(a.tape.k1 + o * D + g * R, sl.k1);
   }
   sl.t = a.tape.t[o];
   sl.h = a.tape.h_acc[o];

@@ -153,7 +153,7 @@ def autotune(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
                 torch.cuda.synchronize()
                 slots = max(1, int(probe.n_acc.max().item()))
                 tape = api.TapeBuffers.allocate(B, D, y0.dtype, slots, 1, y0.device,
-                                                stages=kind in ("mlp", "linear"))
+                                                stages=kind in ("mlp", "linear"), minimal=True)
 
             def timer(o):
                 def run():

@@ -149,3 +149,40 @@ def test_adjoint_rejects_bad_arguments():
     assert lib.tode_adjoint(C.byref(f), C.byref(o), p, p, p, 2, p, p, C.byref(tp), p, p, p,
                             p, None, None, p, p, C.c_size_t(need - 1), None) == \
         _abi.TODE_EWORKSPACE
+
+
+def _tape(**kw):
+    tp = _abi.Tape()
+    tp.slots, tp.stride = 4, 1
+    for k in ("y", "y_lo", "k1", "t", "h", "err_prev", "flags", "h_acc"):
+        setattr(tp, k, 0x1000)
+    tp.y_stage = None
+    for k, v in kw.items():
+        setattr(tp, k, v)
+    return tp
+
+
+@pytest.mark.parametrize("tape_kw,ok", [
+    (dict(), True),
+    (dict(y=0x1008), False),                                  # not 16-byte aligned
+    (dict(y_lo=None, h=None, err_prev=None, flags=None), True),  # minimal direct tape
+    (dict(y_lo=None, h=None, err_prev=None, flags=None, k1=None), False),  # no k1, no stages
+    (dict(y_lo=None, h=None, err_prev=None, flags=None, k1=None, y_stage=0x2000), True),
+    (dict(y_lo=None, h=None, err_prev=None, flags=None, stride=2), False),  # re-run needs all
+    (dict(h_acc=None, h=None), False),                         # no step sizes: re-run
+    (dict(t=None), False),
+])
+def test_tape_fields_checked_before_launch(tape_kw, ok):
+    """Which tape arrays a solve needs: everything for strided (re-run)
+    tapes; y, t, h_acc and k1 or y_stage for a stride-1 tape with step
+    sizes; every array 16-byte aligned.  A rejected tape returns EINVAL
+    before any device work; an accepted one passes on to the workspace
+    check (here: too small)."""
+    lib = _abi.load()
+    o = _opts()
+    f = _desc(_abi.TODE_VDP, 4, 2)
+    p = C.c_void_p(0x1000)
+    tp = _tape(**tape_kw)
+    rc = lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, C.byref(tp), None,
+                        p, C.c_size_t(0), None)
+    assert rc == (_abi.TODE_EWORKSPACE if ok else _abi.TODE_EINVAL)

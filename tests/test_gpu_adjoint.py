@@ -173,3 +173,42 @@ def test_adjoint_recorded_stage_inputs_equal_recomputed(cfg):
         outs.append((gy0.cpu().numpy(), gp.cpu().numpy(), g["y_eval"]))
     assert np.array_equal(outs[0][2], outs[1][2])  # recording changes nothing in the solve
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("cfg,stages", [(2, True), (2, False), (3, False), (1, False)])
+def test_minimal_tape_reverses_like_the_full_tape(cfg, stages):
+    """A stride-1 tape that keeps only y, t, the accepted step sizes and k1
+    (or the stage inputs) gives the adjoint the same bits as the full tape,
+    and the forward's outputs are unchanged."""
+    w = make(cfg, B=700 if cfg != 1 else 128)
+    dtype = torch.float64 if cfg == 1 else torch.float32
+    B, D = w["y0"].shape
+    probe = gpu_solve(w, dtype, "fused")
+    slots = max(1, int(probe["n_acc"].max()))
+    res = []
+    for minimal in (False, True):
+        tape = tode.TapeBuffers.allocate(B, D, dtype, slots, 1, "cuda", stages=stages,
+                                         minimal=minimal)
+        if minimal:
+            assert tape.y_lo is None and tape.h is None and tape.flags is None
+            assert (tape.k1 is None) == stages
+        g = gpu_solve(w, dtype, "fused", tape=tape)
+        dev = g["_dev"]
+        rng = np.random.default_rng(4)
+        gye = torch.tensor(rng.standard_normal(g["y_eval"].shape), dtype=dtype, device="cuda")
+        gyf = torch.tensor(rng.standard_normal((B, D)), dtype=dtype, device="cuda")
+        gy0, gp, ovf = tode.adjoint(dev["field"], dev["t0"], dev["t1"], dev["te"], g["_sol"],
+                                    tape, gye, gyf, rtol=w["rtol"], atol=w["atol"])
+        torch.cuda.synchronize()
+        res.append((g, gy0.cpu().numpy(), gp.cpu().numpy(), int(ovf.item())))
+    (g0, a0, p0, o0), (g1, a1, p1, o1) = res
+    assert o0 == o1 == 0
+    for k in ("y_eval", "y_final", "n_acc", "n_rej", "status"):
+        assert np.array_equal(g0[k], g1[k], equal_nan=True), k
+    assert np.array_equal(a0, a1, equal_nan=True)
+    assert np.array_equal(p0, p1, equal_nan=True)
+
+
+def test_minimal_tape_needs_stride_one():
+    with pytest.raises(ValueError):
+        tode.TapeBuffers.allocate(8, 16, torch.float32, 4, 2, "cuda", minimal=True)
