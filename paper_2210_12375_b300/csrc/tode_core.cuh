@@ -750,24 +750,34 @@ __device__ void inst_finalize(const Inst<T, R>& s, const SolveOpts& o, int i, in
 // (bin 0 first).  Every instance is solved or reversed independently of the
 // others, so the order changes no result; it only decides which instances
 // share a warp and which start first.  The order inside a bin is arbitrary.
-constexpr int ORDER_BINS = 1024;
+constexpr int ORDER_BINS = 256;
+constexpr int ORDER_THREADS = 1024;  // 32 warps, each with its own row of counters
 
+// The counters are per (bin, warp), bin-major, so that lanes of different
+// warps never contend for one counter (the bins of a batch are few and
+// crowded) and the queue stays ordered by bin.
 template <class BinOf>
-__global__ void __launch_bounds__(ORDER_BINS) k_counting_order(int B, BinOf bin_of,
-                                                               int32_t* order) {
-  __shared__ int cnt[ORDER_BINS];
-  __shared__ int warp_tot[ORDER_BINS / 32];
-  const int t = threadIdx.x;
-  cnt[t] = 0;
+__global__ void __launch_bounds__(ORDER_THREADS) k_counting_order(int B, BinOf bin_of,
+                                                                  int32_t* order) {
+  constexpr int W = ORDER_THREADS / 32, PER = ORDER_BINS * W / ORDER_THREADS;
+  __shared__ int cnt[ORDER_BINS * W];  // [bin][warp]
+  __shared__ int warp_tot[W];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) cnt[t * PER + k] = 0;
   __syncthreads();
   // independent iterations: unrolled so that their loads overlap
 #pragma unroll 8
-  for (int i = t; i < B; i += ORDER_BINS) atomicAdd(&cnt[bin_of(i)], 1);
+  for (int i = t; i < B; i += ORDER_THREADS) atomicAdd(&cnt[bin_of(i) * W + w], 1);
   __syncthreads();
-  // exclusive prefix sum over the bins (thread t owns bin t)
-  const int lane = t & 31, w = t >> 5;
-  const int c = cnt[t];
-  int incl = c;
+  // exclusive prefix sum over the (bin, warp) counters, PER per thread
+  int loc[PER], sum = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    loc[k] = sum;
+    sum += cnt[t * PER + k];
+  }
+  int incl = sum;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int v = __shfl_up_sync(0xffffffffu, incl, d);
@@ -785,15 +795,18 @@ __global__ void __launch_bounds__(ORDER_BINS) k_counting_order(int B, BinOf bin_
     warp_tot[lane] = x;  // inclusive over warps
   }
   __syncthreads();
-  cnt[t] = (w > 0 ? warp_tot[w - 1] : 0) + incl - c;
+  const int before = (w > 0 ? warp_tot[w - 1] : 0) + incl - sum;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) cnt[t * PER + k] = before + loc[k];
   __syncthreads();
 #pragma unroll 8
-  for (int i = t; i < B; i += ORDER_BINS) order[atomicAdd(&cnt[bin_of(i)], 1)] = i;
+  for (int i = t; i < B; i += ORDER_THREADS) order[atomicAdd(&cnt[bin_of(i) * W + w], 1)] = i;
 }
 
 // Longest integration interval first: t1 - t0 binned by its binary exponent
-// and two leading mantissa bits (a quarter octave per bin, 2^-128 .. 2^128).
-// Empty and invalid intervals, which finish at initialisation, go last.
+// and two leading mantissa bits (a quarter octave per bin, 2^-32 .. 2^32,
+// clamped outside).  Empty and invalid intervals, which finish at
+// initialisation, go last.
 struct IntervalBin {
   const double* t0;
   const double* t1;
@@ -801,7 +814,7 @@ struct IntervalBin {
     const double len = t1[i] - t0[i];
     if (!(len > 0.0) || !tfinite(len)) return ORDER_BINS - 1;
     const long long b = __double_as_longlong(len);
-    const int key = (int)(((b >> 52) & 0x7ff) - 1023 + 128) * 4 + (int)((b >> 50) & 3);
+    const int key = (int)(((b >> 52) & 0x7ff) - 1023 + 32) * 4 + (int)((b >> 50) & 3);
     const int k = key < 0 ? 0 : (key > ORDER_BINS - 2 ? ORDER_BINS - 2 : key);
     return ORDER_BINS - 2 - k;
   }

@@ -317,7 +317,7 @@ tode_err launch_solve(const SolveReq& r) {
   const int block = r.o->block > 0 ? r.o->block : default_block(threads, r.num_sms);
   if (block % 32 != 0 || block > 256) return TODE_EINVAL;
   if (a.order) {
-    k_counting_order<<<1, ORDER_BINS, 0, st>>>(r.B, IntervalBin{r.t0, r.t1},
+    k_counting_order<<<1, ORDER_THREADS, 0, st>>>(r.B, IntervalBin{r.t0, r.t1},
                                                const_cast<int32_t*>(a.order));
     TODE_CUDA_TRY(cudaGetLastError());
   }

@@ -587,7 +587,7 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   if (grid > need) grid = need;
   if (grid == 0) return TODE_OK;
   TODE_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int32_t), r.stream));
-  k_counting_order<<<1, ORDER_BINS, 0, r.stream>>>(r.B, StepsBin{r.n_acc, r.status}, order);
+  k_counting_order<<<1, ORDER_THREADS, 0, r.stream>>>(r.B, StepsBin{r.n_acc, r.status}, order);
   TODE_CUDA_TRY(cudaGetLastError());
   kern<<<(int)grid, block, 0, r.stream>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
