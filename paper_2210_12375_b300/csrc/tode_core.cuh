@@ -18,6 +18,7 @@
 // left to right, so their accept/reject sequences are reproducible bit for bit
 // by any IEEE-754 implementation that follows the same order.
 #pragma once
+#include "tode_internal.h"
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -750,25 +751,31 @@ __device__ void inst_finalize(const Inst<T, R>& s, const SolveOpts& o, int i, in
 // (bin 0 first).  Every instance is solved or reversed independently of the
 // others, so the order changes no result; it only decides which instances
 // share a warp and which start first.  The order inside a bin is arbitrary.
-constexpr int ORDER_BINS = 256;
-constexpr int ORDER_THREADS = 1024;  // 32 warps, each with its own row of counters
 
 // The counters are per (bin, warp), bin-major, so that lanes of different
 // warps never contend for one counter (the bins of a batch are few and
 // crowded) and the queue stays ordered by bin.
+constexpr int ORDER_CACHE = 12288;  // bins kept in shared memory for batches up to this size
+
 template <class BinOf>
 __global__ void __launch_bounds__(ORDER_THREADS) k_counting_order(int B, BinOf bin_of,
                                                                   int32_t* order) {
   constexpr int W = ORDER_THREADS / 32, PER = ORDER_BINS * W / ORDER_THREADS;
   __shared__ int cnt[ORDER_BINS * W];  // [bin][warp]
   __shared__ int warp_tot[W];
+  __shared__ unsigned char bins[ORDER_CACHE];  // a small batch's bins, for the second pass
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const bool cached = B <= ORDER_CACHE;
 #pragma unroll
   for (int k = 0; k < PER; ++k) cnt[t * PER + k] = 0;
   __syncthreads();
   // independent iterations: unrolled so that their loads overlap
 #pragma unroll 8
-  for (int i = t; i < B; i += ORDER_THREADS) atomicAdd(&cnt[bin_of(i) * W + w], 1);
+  for (int i = t; i < B; i += ORDER_THREADS) {
+    const int b = bin_of(i);
+    if (cached) bins[i] = (unsigned char)b;
+    atomicAdd(&cnt[b * W + w], 1);
+  }
   __syncthreads();
   // exclusive prefix sum over the (bin, warp) counters, PER per thread
   int loc[PER], sum = 0;
@@ -800,21 +807,109 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_counting_order(int B, BinOf b
   for (int k = 0; k < PER; ++k) cnt[t * PER + k] = before + loc[k];
   __syncthreads();
 #pragma unroll 8
-  for (int i = t; i < B; i += ORDER_THREADS) order[atomicAdd(&cnt[bin_of(i) * W + w], 1)] = i;
+  for (int i = t; i < B; i += ORDER_THREADS) {
+    const int b = cached ? (int)bins[i] : bin_of(i);
+    order[atomicAdd(&cnt[b * W + w], 1)] = i;
+  }
+}
+
+// Multi-CTA form for large batches: every CTA counts its instances per bin
+// (k_order_count), one CTA turns the counts into queue offsets, bin-major
+// and CTA-minor (k_order_offsets), and every CTA places its instances from
+// its own offsets (k_order_place; the same grid-stride walk as the count).
+template <class BinOf>
+__global__ void __launch_bounds__(ORDER_THREADS) k_order_count(int B, BinOf bin_of, int* part) {
+  __shared__ int cnt[ORDER_BINS];
+  const int t = threadIdx.x;
+  if (t < ORDER_BINS) cnt[t] = 0;
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * ORDER_THREADS;
+#pragma unroll 4
+  for (long long i = (long long)blockIdx.x * ORDER_THREADS + t; i < B; i += stride)
+    atomicAdd(&cnt[bin_of((int)i)], 1);
+  __syncthreads();
+  if (t < ORDER_BINS) part[(size_t)blockIdx.x * ORDER_BINS + t] = cnt[t];
+}
+
+template <int NB>
+__global__ void __launch_bounds__(NB) k_order_offsets(int ctas, int* part) {
+  static_assert(NB == ORDER_BINS, "one thread per bin");
+  __shared__ int warp_tot[NB / 32];
+  const int b = threadIdx.x, lane = b & 31, w = b >> 5;
+  int total = 0;
+  for (int c = 0; c < ctas; ++c) total += part[(size_t)c * ORDER_BINS + b];
+  int incl = total;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  int before = 0;
+  for (int k = 0; k < w; ++k) before += warp_tot[k];
+  int run = before + incl - total;  // queue start of bin b
+  for (int c = 0; c < ctas; ++c) {
+    const size_t q = (size_t)c * ORDER_BINS + b;
+    const int v = part[q];
+    part[q] = run;
+    run += v;
+  }
+}
+
+template <class BinOf>
+__global__ void __launch_bounds__(ORDER_THREADS) k_order_place(int B, BinOf bin_of,
+                                                               const int* part, int32_t* order) {
+  __shared__ int cur[ORDER_BINS];
+  const int t = threadIdx.x;
+  if (t < ORDER_BINS) cur[t] = part[(size_t)blockIdx.x * ORDER_BINS + t];
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * ORDER_THREADS;
+#pragma unroll 4
+  for (long long i = (long long)blockIdx.x * ORDER_THREADS + t; i < B; i += stride)
+    order[atomicAdd(&cur[bin_of((int)i)], 1)] = (int32_t)i;
+}
+
+// Fills order[0..B) (part: order_part_bytes(B) of scratch, unused for a
+// small batch).
+template <class BinOf>
+inline cudaError_t launch_order(int B, BinOf bin_of, int32_t* order, int* part,
+                                cudaStream_t st) {
+  if (B <= ORDER_SMALL_B) {
+    k_counting_order<<<1, ORDER_THREADS, 0, st>>>(B, bin_of, order);
+    return cudaGetLastError();
+  }
+  const int g = order_ctas(B);
+  k_order_count<<<g, ORDER_THREADS, 0, st>>>(B, bin_of, part);
+  k_order_offsets<ORDER_BINS><<<1, ORDER_BINS, 0, st>>>(g, part);
+  k_order_place<<<g, ORDER_THREADS, 0, st>>>(B, bin_of, part, order);
+  return cudaGetLastError();
 }
 
 // Longest integration interval first: t1 - t0 binned by its binary exponent
-// and two leading mantissa bits (a quarter octave per bin, 2^-32 .. 2^32,
-// clamped outside).  Empty and invalid intervals, which finish at
-// initialisation, go last.
+// and two leading fraction bits (a quarter octave per bin, 2^-32 .. 2^32,
+// clamped outside).  An ordering key only, so the length is taken in FP32
+// from times truncated to FP32 on the integer pipe (no FP64 operation on the
+// single SM that sorts).  Empty, reversed or non-finite intervals, which
+// finish at initialisation, go last.
+__device__ __forceinline__ float trunc_to_float(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned sign = hi & 0x80000000u;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | ((hi & 0xfffffu) ? 1u : 0u));
+  const int ef = e - 1023 + 127;
+  if (ef < 1) return __uint_as_float(sign);                 // below float's normal range: 0
+  if (ef > 254) return __uint_as_float(sign | 0x7f7fffffu);  // above: the largest float
+  return __uint_as_float(sign | ((unsigned)ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
 struct IntervalBin {
   const double* t0;
   const double* t1;
   __device__ __forceinline__ int operator()(int i) const {
-    const double len = t1[i] - t0[i];
-    if (!(len > 0.0) || !tfinite(len)) return ORDER_BINS - 1;
-    const long long b = __double_as_longlong(len);
-    const int key = (int)(((b >> 52) & 0x7ff) - 1023 + 32) * 4 + (int)((b >> 50) & 3);
+    const float len = trunc_to_float(t1[i]) - trunc_to_float(t0[i]);
+    if (!(len > 0.0f) || !(len <= 3.4e38f)) return ORDER_BINS - 1;
+    const unsigned b = __float_as_uint(len);
+    const int key = ((int)((b >> 23) & 0xffu) - 127 + 32) * 4 + (int)((b >> 21) & 3u);
     const int k = key < 0 ? 0 : (key > ORDER_BINS - 2 ? ORDER_BINS - 2 : key);
     return ORDER_BINS - 2 - k;
   }

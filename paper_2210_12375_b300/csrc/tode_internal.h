@@ -62,11 +62,27 @@ struct AdjReq {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Work order (k_counting_order and its multi-CTA form): 256 bins; a batch
+// above ORDER_SMALL_B instances is counted by up to 1024 CTAs, whose per-CTA
+// bin counts (then their queue offsets) live in scratch.
+constexpr int ORDER_BINS = 256;
+constexpr int ORDER_THREADS = 1024;
+constexpr int ORDER_SMALL_B = 16384;
+inline int order_ctas(int B) {
+  const int g = (B + ORDER_THREADS - 1) / ORDER_THREADS;
+  return g > 1024 ? 1024 : g;
+}
+inline size_t order_part_bytes(int B) {
+  return B <= ORDER_SMALL_B ? 0 : align256((size_t)order_ctas(B) * ORDER_BINS * 4);
+}
+
+
 // Workspace bytes of the SIMT solver for state dtype size `ts`.
 inline size_t simt_workspace_bytes(int B, int D, size_t ts, int form) {
   size_t s = 0;
   s += align256(256);             // any-active flag + work counter
   s += align256((size_t)B * 4);    // work order
+  s += order_part_bytes(B);        // and the sort's per-CTA counts
   if (form == TODE_PLAIN) {
     s += 3 * align256((size_t)B * D * ts);  // y, y_lo, k1
     s += align256((size_t)B * 8);           // t
@@ -80,7 +96,8 @@ inline size_t simt_workspace_bytes(int B, int D, size_t ts, int form) {
 // int32 per instance) and one segment of `stride` step-start states per
 // instance (y, k1, t, h).
 inline size_t simt_adjoint_scratch_bytes(int B, int D, size_t ts, int stride) {
-  return align256(256) + align256((size_t)B * 4) + 2 * align256((size_t)stride * B * D * ts) +
+  return align256(256) + align256((size_t)B * 4) + order_part_bytes(B) +
+         2 * align256((size_t)stride * B * D * ts) +
          align256((size_t)stride * B * 8) + align256((size_t)stride * B * ts);
 }
 

@@ -37,6 +37,7 @@ template <typename T> struct SolveArgs {
   int32_t* active;
   int32_t* counter;  // fused form: next queue position to hand out
   const int32_t* order;  // work queue: instance at each position (NULL: index order)
+  int* order_part;       // the large-batch sort's per-CTA counts
 };
 
 // Instance at queue position j (B past the end of the queue).
@@ -277,6 +278,8 @@ template <typename T> SolveArgs<T> make_solve_args(const SolveReq& r) {
   p += align256(256);
   a.order = r.o->order == 1 ? (const int32_t*)p : nullptr;
   p += align256((size_t)r.B * 4);
+  a.order_part = (int*)p;
+  p += order_part_bytes(r.B);
   if (r.o->form == TODE_PLAIN) {
     const size_t ts = sizeof(T);
     a.wy = (T*)p;
@@ -317,9 +320,8 @@ tode_err launch_solve(const SolveReq& r) {
   const int block = r.o->block > 0 ? r.o->block : default_block(threads, r.num_sms);
   if (block % 32 != 0 || block > 256) return TODE_EINVAL;
   if (a.order) {
-    k_counting_order<<<1, ORDER_THREADS, 0, st>>>(r.B, IntervalBin{r.t0, r.t1},
-                                               const_cast<int32_t*>(a.order));
-    TODE_CUDA_TRY(cudaGetLastError());
+    TODE_CUDA_TRY(launch_order(r.B, IntervalBin{r.t0, r.t1}, const_cast<int32_t*>(a.order),
+                               a.order_part, st));
   }
   if (r.o->form == TODE_PLAIN) {
     const int grid = (int)((threads + block - 1) / block);

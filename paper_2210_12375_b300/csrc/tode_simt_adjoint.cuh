@@ -566,6 +566,8 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   int32_t* order = (int32_t*)p;
   a.order = order;
   p += align256((size_t)r.B * 4);
+  int* order_part = (int*)p;
+  p += order_part_bytes(r.B);
   const int m = r.tape->stride;
   a.sy = (T*)p;
   p += align256((size_t)m * r.B * r.D * sizeof(T));
@@ -587,8 +589,7 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   if (grid > need) grid = need;
   if (grid == 0) return TODE_OK;
   TODE_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int32_t), r.stream));
-  k_counting_order<<<1, ORDER_THREADS, 0, r.stream>>>(r.B, StepsBin{r.n_acc, r.status}, order);
-  TODE_CUDA_TRY(cudaGetLastError());
+  TODE_CUDA_TRY(launch_order(r.B, StepsBin{r.n_acc, r.status}, order, order_part, r.stream));
   kern<<<(int)grid, block, 0, r.stream>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;

@@ -1,7 +1,8 @@
 """The work order of the Van der Pol and linear solvers (longest interval
 first, or index order) decides only which instances share a warp and which
 start first: every output of both forms and of the adjoint is the same bits
-either way, including instances that are invalid or finish at t0."""
+either way, including instances that are invalid or finish at t0.  Batches
+above 16384 instances take the multi-CTA sort."""
 import numpy as np
 import pytest
 import torch
@@ -24,7 +25,7 @@ def _workload(cfg, B):
     return dict(w, t1=t1, t_eval=te)
 
 
-@pytest.mark.parametrize("cfg,B", [(2, 1500), (3, 3000), (1, 256)])
+@pytest.mark.parametrize("cfg,B", [(2, 1500), (3, 3000), (1, 256), (3, 40000)])
 @pytest.mark.parametrize("form", ["fused", "plain"])
 def test_order_changes_no_bit(cfg, B, form):
     w = _workload(cfg, B)
@@ -36,7 +37,7 @@ def test_order_changes_no_bit(cfg, B, form):
     assert res[0]["status"][1] == tode._abi.STATUS["SUCCESS"] and res[0]["n_acc"][1] == 0
 
 
-@pytest.mark.parametrize("cfg,B", [(2, 1500), (3, 3000)])
+@pytest.mark.parametrize("cfg,B", [(2, 1500), (3, 3000), (3, 40000)])
 def test_adjoint_order_changes_no_bit(cfg, B):
     """The forward's order (either) feeds a tape; the adjoint reverses it
     longest first: gradients equal those of the index-order forward."""
