@@ -219,7 +219,7 @@ def run_tode(args):
         # the launch shape (lanes per instance, CTA size, resident CTAs, work
         # order; for the plain form its poll interval) the autotuner picks for
         # this batch, timed on it (fwd + adjoint), for each form
-        tuned = tode.autotune(field, y0, t0, t1, te, with_adjoint=True, reps=3, **opt)
+        tuned = tode.autotune(field, y0, t0, t1, te, with_adjoint=True, reps=7, **opt)
         tuned_plain = tode.autotune(field, y0, t0, t1, te, form="plain", with_adjoint=True,
                                     reps=2, **opt)
         opt.update(tuned)

@@ -67,7 +67,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // bin counts (then their queue offsets) live in scratch.
 constexpr int ORDER_BINS = 256;
 constexpr int ORDER_THREADS = 1024;
-constexpr int ORDER_SMALL_B = 16384;
+constexpr int ORDER_SMALL_B = 2048;
 inline int order_ctas(int B) {
   const int g = (B + ORDER_THREADS - 1) / ORDER_THREADS;
   return g > 1024 ? 1024 : g;

@@ -2,7 +2,8 @@
 first, or index order) decides only which instances share a warp and which
 start first: every output of both forms and of the adjoint is the same bits
 either way, including instances that are invalid or finish at t0.  Batches
-above 16384 instances take the multi-CTA sort."""
+above 2048 instances take the multi-CTA sort, the 256-instance one the
+one-CTA sort."""
 import numpy as np
 import pytest
 import torch
