@@ -26,7 +26,7 @@ def _workload(cfg, B):
     return dict(w, t1=t1, t_eval=te)
 
 
-@pytest.mark.parametrize("cfg,B", [(2, 1500), (3, 3000), (1, 256), (3, 40000)])
+@pytest.mark.parametrize("cfg,B", [(2, 1500), (2, 2049), (3, 3000), (1, 256), (3, 40000)])
 @pytest.mark.parametrize("form", ["fused", "plain"])
 def test_order_changes_no_bit(cfg, B, form):
     w = _workload(cfg, B)
