@@ -1241,6 +1241,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   tc::fence_after_sync();
   const uint32_t tbase = tmem_base_s;
   const uint32_t tl = tbase + lane_base;  // this warp's lane quarter
+  // accumulator chunks in flight per wait in the hidden epilogue (2 and 4
+  // measured no faster here: the round's registers are mostly the cotangents)
+  constexpr int ADJ_NLD = 1;
   uint32_t parity = 0;
   bool dw_first = true;  // the next backward round starts the dW accumulators
 
@@ -1335,16 +1338,30 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
     tc::fence_after_sync();
   };
   // hidden epilogue: h = tanh(acc + b) into a split tile
+  // (ADJ_NLD accumulator chunks in flight per wait, additions in FP32x2 pairs)
   auto hidden_epi = [&](const float* bl, unsigned char* th, unsigned char* tlo) {
 #pragma unroll
-    for (int c = 0; c < HC; c += 16) {
-      const int col = half * HC + c;
-      float v[16];
-      tc::tmem_ld16(tl + L::T_R + col, v);
+    for (int c0 = 0; c0 < HC; c0 += 16 * ADJ_NLD) {
+      float v[ADJ_NLD][16];
+#pragma unroll
+      for (int u = 0; u < ADJ_NLD; ++u) tc::tmem_ld16(tl + L::T_R + half * HC + c0 + 16 * u, v[u]);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = tanh_acc(v[j] + bl[col + j]);
-      store_row16<true>(th, tlo, row, col, H, v);
+      for (int u = 0; u < ADJ_NLD; ++u) {
+        const int col = half * HC + c0 + 16 * u;
+        const float4* b4 = reinterpret_cast<const float4*>(bl + col);
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float4 bq = b4[q4];
+          const float2 t0 = tanh_acc2(__fadd2_rn(make_float2(v[u][4 * q4], v[u][4 * q4 + 1]),
+                                                 make_float2(bq.x, bq.y)));
+          const float2 t1 = tanh_acc2(__fadd2_rn(make_float2(v[u][4 * q4 + 2], v[u][4 * q4 + 3]),
+                                                 make_float2(bq.z, bq.w)));
+          v[u][4 * q4] = t0.x, v[u][4 * q4 + 1] = t0.y;
+          v[u][4 * q4 + 2] = t1.x, v[u][4 * q4 + 3] = t1.y;
+        }
+        store_row16<true>(th, tlo, row, col, H, v[u]);
+      }
     }
   };
   // backward epilogue: delta = acc (1 - h^2) with h = hi + lo of the tile;
