@@ -127,7 +127,6 @@ TRAFFIC = {
     ("vdp_mix_b262144", "k_fused<VdpField<float>>"): 8 * 91.90e6,
     ("vdp_mix_b262144", "k_adjoint_steps<VdpAdj<float>>"): 8 * 124.08e6,
     ("mlp_d32_h128", "k_mlp_fused"): 12.51e6,
-    ("mlp_d32_h128", "k_mlp_adjoint"): 67.14e6,
 }
 
 
