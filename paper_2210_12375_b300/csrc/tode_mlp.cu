@@ -1383,10 +1383,13 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
         for (int j = 0; j < 4; ++j) {
           const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
           const __nv_bfloat162 l2 = *reinterpret_cast<const __nv_bfloat162*>(&lw[j]);
-          const float x0 = __low2float(h2) + __low2float(l2);
-          const float x1 = __high2float(h2) + __high2float(l2);
-          v[8 * c8 + 2 * j] *= madd(-x0, x0, 1.0f);
-          v[8 * c8 + 2 * j + 1] *= madd(-x1, x1, 1.0f);
+          // x = hi + lo, then v * (1 - x^2), the pair's operations packed
+          const float2 x = __fadd2_rn(make_float2(__low2float(h2), __high2float(h2)),
+                                      make_float2(__low2float(l2), __high2float(l2)));
+          const float2 g = __ffma2_rn(make_float2(-x.x, -x.y), x, make_float2(1.0f, 1.0f));
+          const float2 d = __fmul2_rn(make_float2(v[8 * c8 + 2 * j], v[8 * c8 + 2 * j + 1]), g);
+          v[8 * c8 + 2 * j] = d.x;
+          v[8 * c8 + 2 * j + 1] = d.y;
         }
       }
       store_row16<true>(th, tlo, row, col, H, v);
