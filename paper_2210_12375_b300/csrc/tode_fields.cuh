@@ -61,15 +61,19 @@ template <typename T, int R, int G> struct LinearField {
         for (int c = 0; c < D; ++c) s = madd(a[r][c], yall[c], s);
         f[r] = s;
       } else {
-        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        // four partial sums over the columns c = 0, 1, 2, 3 (mod 4), added as
+        // (s0 + s1) + (s2 + s3); (s0, s1) and (s2, s3) run as FP32x2 pairs
+        // over adjacent columns (each lane rounds as a scalar fused
+        // multiply-add: the same bits, half the instructions)
+        float2 p01 = make_float2(0.0f, 0.0f), p23 = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int c = 0; c < D; c += 4) {
-          s0 = madd(a[r][c], yall[c], s0);
-          s1 = madd(a[r][c + 1], yall[c + 1], s1);
-          s2 = madd(a[r][c + 2], yall[c + 2], s2);
-          s3 = madd(a[r][c + 3], yall[c + 3], s3);
+          p01 = __ffma2_rn(make_float2(a[r][c], a[r][c + 1]), make_float2(yall[c], yall[c + 1]),
+                           p01);
+          p23 = __ffma2_rn(make_float2(a[r][c + 2], a[r][c + 3]),
+                           make_float2(yall[c + 2], yall[c + 3]), p23);
         }
-        f[r] = (s0 + s1) + (s2 + s3);
+        f[r] = (p01.x + p01.y) + (p23.x + p23.y);
       }
     }
   }

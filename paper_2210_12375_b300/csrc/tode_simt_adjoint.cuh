@@ -85,18 +85,31 @@ template <typename T, int R_, int G_> struct LinearAdj {
         for (int j = 0; j < D; ++j) s = madd(a_col(j, r), vall[j], s);
         gy[r] = s;
       } else {
-        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        // partial sums over j = 0, 1, 2, 3 (mod 4) as two FP32x2 pairs of
+        // adjacent rows (same bits as scalar fused multiply-adds)
+        float2 p01 = make_float2(0.0f, 0.0f), p23 = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int j = 0; j < D; j += 4) {
-          s0 = madd(a_col(j, r), vall[j], s0);
-          s1 = madd(a_col(j + 1, r), vall[j + 1], s1);
-          s2 = madd(a_col(j + 2, r), vall[j + 2], s2);
-          s3 = madd(a_col(j + 3, r), vall[j + 3], s3);
+          p01 = __ffma2_rn(make_float2(a_col(j, r), a_col(j + 1, r)),
+                           make_float2(vall[j], vall[j + 1]), p01);
+          p23 = __ffma2_rn(make_float2(a_col(j + 2, r), a_col(j + 3, r)),
+                           make_float2(vall[j + 2], vall[j + 3]), p23);
         }
-        gy[r] = (s0 + s1) + (s2 + s3);
+        gy[r] = (p01.x + p01.y) + (p23.x + p23.y);
       }
+      if constexpr (sizeof(T) == 4 && D % 2 == 0) {
+        const float2 yy = make_float2(y[r], y[r]);
 #pragma unroll
-      for (int j = 0; j < D; ++j) gA[r][j] = madd(vall[j], y[r], gA[r][j]);
+        for (int j = 0; j < D; j += 2) {
+          const float2 g2 = __ffma2_rn(make_float2(vall[j], vall[j + 1]), yy,
+                                       make_float2(gA[r][j], gA[r][j + 1]));
+          gA[r][j] = g2.x;
+          gA[r][j + 1] = g2.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < D; ++j) gA[r][j] = madd(vall[j], y[r], gA[r][j]);
+      }
     }
   }
   __device__ __forceinline__ void store_param(T* gp, int i, bool bad) const {
