@@ -755,7 +755,7 @@ __device__ void inst_finalize(const Inst<T, R>& s, const SolveOpts& o, int i, in
 // The counters are per (bin, warp), bin-major, so that lanes of different
 // warps never contend for one counter (the bins of a batch are few and
 // crowded) and the queue stays ordered by bin.
-constexpr int ORDER_CACHE = 12288;  // bins kept in shared memory for batches up to this size
+constexpr int ORDER_CACHE = ORDER_SMALL_B;  // bins kept in shared memory for the second pass
 
 template <class BinOf>
 __global__ void __launch_bounds__(ORDER_THREADS) k_counting_order(int B, BinOf bin_of,
