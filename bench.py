@@ -264,7 +264,7 @@ def run_tode(args):
 
     def capture(fn):
         """A CUDA graph of the work fn enqueues (fn runs once outside the
-        capture first); None when this build's calls cannot be captured."""
+        capture first); None when the calls cannot be captured."""
         if args.no_graph:
             return None
         side = torch.cuda.Stream()
