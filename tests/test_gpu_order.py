@@ -58,3 +58,19 @@ def test_adjoint_order_changes_no_bit(cfg, B):
     assert outs[0][2] == outs[1][2] == 0
     assert np.array_equal(outs[0][0], outs[1][0], equal_nan=True)
     assert np.array_equal(outs[0][1], outs[1][1], equal_nan=True)
+
+
+def test_order_sort_grid_stride_batch():
+    """More instances than the multi-CTA sort has threads (1024 CTAs x 1024):
+    its CTAs walk the batch in more than one stride, and the forward (no
+    tape, Van der Pol, durations cut short) gives the same bits either way."""
+    base = make(3)
+    B = 1024 * 1024 + 4099
+    w = subset(base, np.arange(B) % base["B"])
+    w = dict(w, t1=np.minimum(w["t1"], w["t0"] + 0.5))
+    w = dict(w, t_eval=np.linspace(0.0, 1.0, 3)[None, :] * (w["t1"] - w["t0"])[:, None]
+             + w["t0"][:, None])
+    res = [gpu_solve(w, torch.float32, "fused", order=o) for o in (0, 1)]
+    for k in KEYS:
+        assert np.array_equal(res[0][k], res[1][k], equal_nan=True), k
+    assert (res[0]["status"] == 0).all()
