@@ -161,7 +161,7 @@ def test_adjoint_recorded_stage_inputs_equal_recomputed(cfg):
     outs = []
     for stages in (False, True):
         tape = tode.TapeBuffers.allocate(B, D, dtype, N, 1, "cuda", stages=stages)
-        g = gpu_solve(w, dtype, "fused", tape=tape)
+        g = gpu_solve(w, dtype, form, tape=tape)
         dev = g["_dev"]
         rng = np.random.default_rng(4)
         gye = torch.tensor(rng.standard_normal(g["y_eval"].shape), dtype=dtype, device="cuda")
@@ -175,8 +175,9 @@ def test_adjoint_recorded_stage_inputs_equal_recomputed(cfg):
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
+@pytest.mark.parametrize("form", ["fused", "plain"])
 @pytest.mark.parametrize("cfg,stages", [(2, True), (2, False), (3, False), (1, False)])
-def test_minimal_tape_reverses_like_the_full_tape(cfg, stages):
+def test_minimal_tape_reverses_like_the_full_tape(cfg, stages, form):
     """A stride-1 tape that keeps only y, t, the accepted step sizes and k1
     (or the stage inputs) gives the adjoint the same bits as the full tape,
     and the forward's outputs are unchanged."""
@@ -192,7 +193,7 @@ def test_minimal_tape_reverses_like_the_full_tape(cfg, stages):
         if minimal:
             assert tape.y_lo is None and tape.h is None and tape.flags is None
             assert (tape.k1 is None) == stages
-        g = gpu_solve(w, dtype, "fused", tape=tape)
+        g = gpu_solve(w, dtype, form, tape=tape)
         dev = g["_dev"]
         rng = np.random.default_rng(4)
         gye = torch.tensor(rng.standard_normal(g["y_eval"].shape), dtype=dtype, device="cuda")
