@@ -161,7 +161,7 @@ def test_adjoint_recorded_stage_inputs_equal_recomputed(cfg):
     outs = []
     for stages in (False, True):
         tape = tode.TapeBuffers.allocate(B, D, dtype, N, 1, "cuda", stages=stages)
-        g = gpu_solve(w, dtype, form, tape=tape)
+        g = gpu_solve(w, dtype, "fused", tape=tape)
         dev = g["_dev"]
         rng = np.random.default_rng(4)
         gye = torch.tensor(rng.standard_normal(g["y_eval"].shape), dtype=dtype, device="cuda")
