@@ -513,15 +513,19 @@ def run_tode(args):
         "fused_over_plain_fwd": (ms_plain_fwd / args.plain_steps) / (ms_fused_fwd / nk),
     })
     # our kernels per timed step: the fused forward (+ one weight-image build
-    # for the MLP) and the adjoint (SIMT fields: the longest-first work order
-    # and the reverse sweep; MLP D=32: image, adjoint, ordered dW reduction;
-    # wide MLP: two images, a fill, one adjoint per batch slice and a copy --
-    # the weight-gradient GEMMs are cuBLAS's)
+    # for the MLP; for the SIMT fields the work-order sort when the launch
+    # orders longest first) and the adjoint (SIMT fields: the longest-first
+    # sort and the reverse sweep; MLP D=32: image, adjoint, ordered dW
+    # reduction; wide MLP: two images, a fill, one adjoint per batch slice and
+    # a copy -- the weight-gradient GEMMs are cuBLAS's).  The sort is one
+    # launch up to 2048 instances, three above.
     if mlp:
         adj = (3 + -(-B // (148 * 64)) + 1) if D == 64 else 3
         gpu_launches = 2 + (adj if with_adjoint else 0)
     else:
-        gpu_launches = 1 + (2 if with_adjoint else 0)
+        sort = 1 if B <= 2048 else 3
+        fwd_sort = sort if int(opt.get("order") or 0) == 1 else 0
+        gpu_launches = 1 + fwd_sort + ((1 + sort) if with_adjoint else 0)
     result = {
         "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
