@@ -136,7 +136,7 @@ typedef struct {
  * With stride 1 and h_acc given (the same tape struct for both calls), every
  * accepted step is on the tape with its size and tode_adjoint reverses it
  * directly, without re-running the forward's attempts.
- * MLP field: stride must be 1; y, k1, t, h_acc and y_stage are used (the
+ * MLP field: stride must be 1; y, t, h_acc and y_stage are used (the
  * adjoint reverses every step from its recorded stage inputs).
  * Every array is instance-major ([B][slots]...): the slots of one instance
  * are contiguous, so a lane group's successive checkpoint stores (and the
@@ -161,8 +161,9 @@ typedef struct {
                        starts at the slot (written when that step is accepted;
                        required for the MLP field, optional otherwise) */
   void* y_stage;    /* [B][slots][6][D] state dtype: the stage inputs Y_2..Y_7
-                       of the accepted step (MLP field: required; other fields
-                       ignore it, may be NULL) */
+                       of the accepted step (MLP field: required; other fields:
+                       optional -- with stride 1 and h_acc the adjoint then
+                       reads them instead of re-evaluating the stages) */
 } tode_tape;
 
 /* Per-attempt trace (testing and diagnostics): for instance i, attempt n <
@@ -184,9 +185,10 @@ void tode_default_options(tode_options* o);
 
 /* Bytes of device workspace tode_solve needs for this problem (the base
  * pointer must be 256-byte aligned): for the Van der Pol and linear fields
- * a work counter and the work order (one int32 per instance), plus the
- * per-instance solver state between launches for the plain form.  Returns 0
- * for an unsupported or invalid combination. */
+ * a work counter, the work order (one int32 per instance) and, above 2048
+ * instances, the work-order sort's per-CTA counts, plus the per-instance
+ * solver state between launches for the plain form.  Returns 0 for an
+ * unsupported or invalid combination. */
 size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int K);
 
 /* Solve all B instances (Sec. 3: independent parallel solving).
