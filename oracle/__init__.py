@@ -9,6 +9,7 @@ from .oracle import (  # noqa: F401
     field_eval,
     dense_weights,
     solve,
+    solve_joint,
     replay,
     adjoint,
     tableau_doubles,

@@ -42,6 +42,8 @@ class _Field(C.Structure):
         ("widths", C.POINTER(C.c_int)),
         ("W", C.POINTER(_dp)),
         ("bias", C.POINTER(_dp)),
+        ("inner", C.c_void_p),
+        ("n_inner", C.c_int),
     ]
 
 
@@ -252,6 +254,61 @@ def solve(field: dict, y0, t0, t1, t_eval=None, opts: dict | None = None,
                          C.byref(tr) if tr is not None else None, C.c_int(nthreads))
     out.update(y_eval=y_eval, y_final=y_final, n_acc=n_acc, n_rej=n_rej, n_feval=n_fe,
                status=st, threads=used)
+    return out
+
+
+def solve_joint(field: dict, y0, t0: float, t1: float, t_eval=None, opts: dict | None = None,
+                trace_cap: int = 0) -> dict:
+    """Joint ("stacked") solving, Sec. 4.1: the B instances concatenated into
+    one problem of size B*D -- one step size, one error norm over all B*D
+    components, one accept/reject decision for the whole batch.
+
+    The concatenation is a field of its own (block b of the state evolves by
+    instance b's f) handed to the single-instance solver unchanged, so the
+    norm, the starting step and the controller are those of one problem.
+    y0 [B,D]; t0, t1 scalars; t_eval [K] shared.  Returns y_eval [B,K,D],
+    y_final [B,D] and the one problem's n_acc, n_rej, n_feval, status (ints)
+    and, when trace_cap > 0, its trace (1-D arrays).
+    """
+    lib = _load()
+    opts = default_opts(**(opts or {}))
+    assert opts.get("rtol_b") is None and opts.get("atol_b") is None, \
+        "joint solving takes scalar tolerances"
+    y0 = np.asarray(y0, dtype=np.float64)
+    B = y0.shape[0]
+    inner = _FieldHolder(field, B)
+    D = inner.D
+    f = _Field()
+    f.kind = 4  # stacked
+    f.D = B * D
+    f.inner = C.cast(C.pointer(inner.f), C.c_void_p)
+    f.n_inner = B
+    y0 = _f64(y0, (1, B * D))
+    te = np.zeros((1, 0)) if t_eval is None else _f64(t_eval, (1, -1))
+    K = te.shape[1]
+    keep = []
+    o = _opts_struct(opts, 1, keep)
+    y_eval = np.zeros((1, K, B * D))
+    y_final = np.zeros((1, B * D))
+    n_acc, n_rej, n_fe, st = (np.zeros(1, np.int32) for _ in range(4))
+    tr = None
+    out = {}
+    if trace_cap > 0:
+        tt, th, terr = (np.zeros((1, trace_cap)) for _ in range(3))
+        ta = np.zeros((1, trace_cap), np.int32)
+        tl = np.zeros(1, np.int32)
+        tr = _Trace(trace_cap, _ptr(tt), _ptr(th), _ptr(terr), _iptr(ta), _iptr(tl))
+    lib.orc_solve(C.byref(f), C.byref(o), C.c_int(1), _ptr(y0), _ptr(_f64([t0], (1,))),
+                  _ptr(_f64([t1], (1,))), _ptr(te), C.c_int(K), _ptr(y_eval), _ptr(y_final),
+                  _iptr(n_acc), _iptr(n_rej), _iptr(n_fe), _iptr(st),
+                  C.byref(tr) if tr is not None else None, C.c_int(1))
+    if tr is not None:
+        n = int(tl[0])
+        out.update(trace_t=tt[0, :n], trace_h=th[0, :n], trace_err=terr[0, :n],
+                   trace_accepted=ta[0, :n], trace_len=n)
+    out.update(y_eval=y_eval.reshape(K, B, D).transpose(1, 0, 2).copy(),
+               y_final=y_final.reshape(B, D), n_acc=int(n_acc[0]), n_rej=int(n_rej[0]),
+               n_feval=int(n_fe[0]), status=int(st[0]))
     return out
 
 

@@ -20,6 +20,11 @@
  *     last error estimates (Soderlind 2002/2003); the PI subset is used here.
  *   - App. A, FEN benchmark: gradients by backpropagation through the solver
  *     (discretize-then-optimize) -> the discrete adjoint of the fixed-mesh map.
+ *   - Sec. 4.1 "Batching ODEs": joint ("stacked") solving, the comparison
+ *     semantics of the batching experiment -- n problems of size p handed to
+ *     this same single-problem solver as one problem of size np (a stacked
+ *     field, ORC_STACKED), so that they share step size, error norm and
+ *     accept/reject decisions.
  *
  * Readings of passages the paper leaves open (it prints no tableau, norm,
  * controller constants, starting-step rule or interpolant):
@@ -102,13 +107,13 @@ void orc_tableau(double *c, double *a, double *b, double *bhat, double *q) {
 /* ------------------------------------------------------------------------ */
 /* Problem description.                                                      */
 /* ------------------------------------------------------------------------ */
-enum { ORC_VDP = 1, ORC_LINEAR = 2, ORC_MLP = 3 };
+enum { ORC_VDP = 1, ORC_LINEAR = 2, ORC_MLP = 3, ORC_STACKED = 4 };
 enum { ST_SUCCESS = 0, ST_MAX_STEPS = 1, ST_DT_UNDERFLOW = 2, ST_NONFINITE = 3,
        ST_INVALID_INPUT = 4, ST_RUNNING = -1 };
 
 #define MLP_MAX_LAYERS 8
 
-typedef struct {
+typedef struct orc_field_s {
   int kind;
   int D;
   const double *mu;          /* Van der Pol: [B] damping */
@@ -117,6 +122,12 @@ typedef struct {
   const int *widths;         /* MLP: [n_layers+1]; widths[0]=D+1, widths[n_layers]=D */
   const double *const *W;    /* MLP: W[l] is [widths[l+1]][widths[l]] row-major */
   const double *const *bias; /* MLP: bias[l] is [widths[l+1]] */
+  /* Stacked: n_inner instances of `inner` concatenated into one problem of
+   * size D = n_inner * inner->D (Sec. 4.1: a mini-batch of n problems of
+   * size p solved as a single problem of size np); block b of the state is
+   * instance b of the inner field. */
+  const struct orc_field_s *inner;
+  int n_inner;
 } orc_field;
 
 typedef struct {
@@ -197,6 +208,13 @@ static void feval(fctx *c, double t, const double *y, double *out) {
     f_vdp(F->mu[c->i], y, out);
   } else if (F->kind == ORC_LINEAR) {
     f_linear(F->A + (size_t)c->i * F->D * F->D, F->D, y, out);
+  } else if (F->kind == ORC_STACKED) {
+    /* the concatenated field: every block evolves by its own instance's f */
+    const int d = F->inner->D;
+    for (int b = 0; b < F->n_inner; ++b) {
+      fctx sub = {F->inner, b, c->act, 0};
+      feval(&sub, t, y + (size_t)b * d, out + (size_t)b * d);
+    }
   } else {
     f_mlp(F, t, y, out, c->act);
   }
@@ -206,9 +224,10 @@ static void feval(fctx *c, double t, const double *y, double *out) {
 void orc_field_eval(const orc_field *F, int i, double t, const double *y, double *out) {
   fctx c = {F, i, NULL, 0};
   double *act = NULL;
-  if (F->kind == ORC_MLP) {
+  const orc_field *M = F->kind == ORC_STACKED ? F->inner : F;
+  if (M->kind == ORC_MLP) {
     int tot = 0;
-    for (int l = 0; l <= F->n_layers; ++l) tot += F->widths[l];
+    for (int l = 0; l <= M->n_layers; ++l) tot += M->widths[l];
     act = (double *)malloc(sizeof(double) * tot);
     c.act = act;
   }
@@ -775,9 +794,10 @@ static void *worker(void *p) {
   const job *J = a->J;
   const int D = J->F->D;
   int acts = 0, maxw = 8;
-  if (J->F->kind == ORC_MLP) {
-    for (int l = 0; l <= J->F->n_layers; ++l) acts += J->F->widths[l];
-    maxw = mlp_max_width(J->F);
+  const orc_field *M = J->F->kind == ORC_STACKED ? J->F->inner : J->F;
+  if (M->kind == ORC_MLP) {
+    for (int l = 0; l <= M->n_layers; ++l) acts += M->widths[l];
+    maxw = mlp_max_width(M);
   }
   double *work = (double *)malloc(sizeof(double) * (size_t)(40 * D + 64));
   double *act = (double *)malloc(sizeof(double) * (size_t)(acts + 8));
@@ -881,6 +901,9 @@ int orc_adjoint(const orc_field *F, int B, const double *y0, const double *t0, c
                 const double *t_eval, int K, const double *gy_eval, const double *gy_final,
                 double *gy0, double *gparam, double *const *gW, double *const *gb,
                 int nthreads) {
+  /* the adjoint of a stacked problem is the per-instance adjoint on the
+   * shared mesh (every block's Jacobian is its own); call it that way */
+  if (F->kind == ORC_STACKED) return -1;
   job J;
   memset(&J, 0, sizeof(J));
   J.F = F;
