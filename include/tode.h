@@ -124,6 +124,18 @@ typedef struct {
    * instances start early, but a warp's per-instance stores scatter).
    * Results do not depend on it; the autotuner tries both. */
   int order;
+  /* 0 = every instance solved independently (Sec. 3).  1 = joint
+   * ("stacked") solving, the semantics Sec. 4.1 compares against: the batch
+   * is one problem of size B*D with one step size, one RMS error norm over
+   * all B*D components and one accept/reject decision per attempt.  Van der
+   * Pol and linear fields, scalar rtol/atol; every instance must have the
+   * same t0, t1 and t_eval as instance 0, else every instance is reported
+   * TODE_S_INVALID_INPUT.  n_acc/n_rej/status are the problem's, repeated
+   * for every instance.  One launch per attempt (form, order and
+   * ctas_per_sm do not apply; block and poll_every do); a tape must be
+   * stride 1 with h_acc, and tode_adjoint then reverses the shared mesh
+   * per instance as usual. */
+  int joint;
 } tode_options;
 
 /* Checkpoint tape written by tode_solve for tode_adjoint.  Slot j of
@@ -180,15 +192,17 @@ typedef struct {
 
 /* Fills *o with the defaults: rtol = atol = 1e-6, safety 0.9, fac_min 0.2,
  * fac_max 10, beta1 0.2, beta2 0 (integral controller), h0 = 0 (heuristic),
- * max_steps 100000, TODE_F32, TODE_FUSED, tuning fields 0, order 0. */
+ * max_steps 100000, TODE_F32, TODE_FUSED, tuning fields 0, order 0, joint 0. */
 void tode_default_options(tode_options* o);
 
 /* Bytes of device workspace tode_solve needs for this problem (the base
  * pointer must be 256-byte aligned): for the Van der Pol and linear fields
  * a work counter, the work order (one int32 per instance) and, above 2048
  * instances, the work-order sort's per-CTA counts, plus the per-instance
- * solver state between launches for the plain form.  Returns 0 for an
- * unsupported or invalid combination. */
+ * solver state between launches for the plain form, or for joint solving a
+ * control block, per-CTA partial sums and 16 * B * D state values (the
+ * state, the pending attempt's new state, stages and stage inputs).
+ * Returns 0 for an unsupported or invalid combination. */
 size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int K);
 
 /* Solve all B instances (Sec. 3: independent parallel solving).

@@ -60,6 +60,7 @@ class Options(C.Structure):
         ("ctas_per_sm", C.c_int),
         ("poll_every", C.c_int),
         ("order", C.c_int),
+        ("joint", C.c_int),
     ]
 
 

@@ -121,7 +121,7 @@ def _prec_of(field, y0: torch.Tensor) -> int:
 def make_options(*, rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, fac_min=0.2,
                  fac_max=10.0, beta1=0.2, beta2=0.0, h0=0.0, max_steps=100000,
                  prec=_abi.TODE_F32, form="fused", group=0, block=0, ctas_per_sm=0,
-                 poll_every=0, order=0) -> _abi.Options:
+                 poll_every=0, order=0, joint=False) -> _abi.Options:
     o = _abi.Options()
     o.rtol, o.atol = float(rtol), float(atol)
     o.rtol_b = rtol_b.data_ptr() if rtol_b is not None else None
@@ -135,6 +135,7 @@ def make_options(*, rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, 
     o.group, o.block, o.ctas_per_sm, o.poll_every = int(group), int(block), int(ctas_per_sm), \
         int(poll_every)
     o.order = int(order)
+    o.joint = int(bool(joint))
     return o
 
 
@@ -228,7 +229,9 @@ def solve(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
           trace_cap: int = 0, stream: Optional[torch.cuda.Stream] = None,
           out: Optional[Solution] = None, workspace: Optional[torch.Tensor] = None,
           **opt_kw) -> Solution:
-    """Solve every instance of the batch independently (Sec. 3).
+    """Solve every instance of the batch independently (Sec. 3), or, with
+    ``joint=True``, the batch as one stacked problem (Sec. 4.1: one step size,
+    error norm and accept decision; equal t0, t1 and t_eval rows required).
 
     y0 [B, D] (float64 or float32; MLP: float32), t0/t1 [B] float64,
     t_eval [B, K] float64.  Keyword options as in ``make_options``.

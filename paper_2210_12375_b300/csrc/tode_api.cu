@@ -28,6 +28,7 @@ static bool opts_ok(const tode_options* o) {
   if (o->form != TODE_PLAIN && o->form != TODE_FUSED) return false;
   if (o->block < 0 || o->group < 0 || o->ctas_per_sm < 0 || o->poll_every < 0) return false;
   if (o->order != 0 && o->order != 1) return false;
+  if (o->joint != 0 && o->joint != 1) return false;
   return true;
 }
 
@@ -132,10 +133,19 @@ void tode_default_options(tode_options* o) {
   o->form = TODE_FUSED;
 }
 
+// Joint solving (Sec. 4.1) covers the Van der Pol and linear fields with
+// scalar tolerances (one problem has one norm).
+static tode_err joint_ok(const tode_field_desc* f, const tode_options* o) {
+  if (!o->joint) return TODE_OK;
+  if (f->kind == TODE_MLP) return TODE_EUNSUPPORTED;
+  if (o->rtol_b || o->atol_b) return TODE_EINVAL;
+  return TODE_OK;
+}
+
 size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int K) {
-  if (K < 0 || !opts_ok(o) || field_ok(f, o) != TODE_OK) return 0;
+  if (K < 0 || !opts_ok(o) || field_ok(f, o) != TODE_OK || joint_ok(f, o) != TODE_OK) return 0;
   if (f->kind == TODE_MLP) return mlp_workspace_bytes(f, o);
-  return simt_workspace_bytes(f->B, f->D, state_size(o), o->form);
+  return simt_workspace_bytes(f->B, f->D, state_size(o), o->form, o->joint);
 }
 
 tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void* y0,
@@ -146,11 +156,15 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
   if (!opts_ok(o) || K < 0) return TODE_EINVAL;
   tode_err e = field_ok(f, o);
   if (e != TODE_OK) return e;
+  e = joint_ok(f, o);
+  if (e != TODE_OK) return e;
   if (f->B == 0) return TODE_OK;
   if (!y0 || !t0 || !t1 || !y_final || !n_acc || !n_rej || !n_feval || !status)
     return TODE_EINVAL;
   if (K > 0 && (!t_eval || !y_eval)) return TODE_EINVAL;
   if (tape && !tape_ok(tape, o, f)) return TODE_EINVAL;
+  // a joint mesh is reversed from the tape, never re-run per instance
+  if (tape && o->joint && !(tape->stride == 1 && tape->h_acc)) return TODE_EINVAL;
   if (trace) {
     if (trace->cap < 0) return TODE_EINVAL;
     if (trace->cap > 0 &&

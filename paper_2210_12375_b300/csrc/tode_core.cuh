@@ -517,6 +517,105 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
   return true;
 }
 
+// ---------------------------------------------------------------- stages (a3, a4)
+// The six new stages of one attempt from (t, y, k1) with step h: the stage
+// inputs Y_2..Y_7 into ys (Y_7 is the new solution y1, SSAL), k3..k7 (k2 is
+// used only inside), the increment inc = h sum_i b_i k_i and y1 = y + inc.
+template <class Field, typename T, int R>
+__device__ __forceinline__ void attempt_stages(const Field& F, double t, T h, const T (&y)[R],
+                                               const T (&k1)[R], T (&ys)[6][R], T (&k3)[R],
+                                               T (&k4)[R], T (&k5)[R], T (&k6)[R], T (&k7)[R],
+                                               T (&y1)[R], T (&inc)[R]) {
+  using C = DP5;
+  const double hd = (double)h;
+  T k2[R], Y[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) Y[r] = madd(h, T(C::a21) * k1[r], y[r]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[0][r] = Y[r];
+  F.eval(t + C::c2 * hd, Y, k2);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::a31) * k1[r];
+    a = madd(T(C::a32), k2[r], a);
+    Y[r] = madd(h, a, y[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[1][r] = Y[r];
+  F.eval(t + C::c3 * hd, Y, k3);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::a41) * k1[r];
+    a = madd(T(C::a42), k2[r], a);
+    a = madd(T(C::a43), k3[r], a);
+    Y[r] = madd(h, a, y[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[2][r] = Y[r];
+  F.eval(t + C::c4 * hd, Y, k4);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::a51) * k1[r];
+    a = madd(T(C::a52), k2[r], a);
+    a = madd(T(C::a53), k3[r], a);
+    a = madd(T(C::a54), k4[r], a);
+    Y[r] = madd(h, a, y[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[3][r] = Y[r];
+  F.eval(t + C::c5 * hd, Y, k5);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::a61) * k1[r];
+    a = madd(T(C::a62), k2[r], a);
+    a = madd(T(C::a63), k3[r], a);
+    a = madd(T(C::a64), k4[r], a);
+    a = madd(T(C::a65), k5[r], a);
+    Y[r] = madd(h, a, y[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[4][r] = Y[r];
+  F.eval(t + hd, Y, k6);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::b1) * k1[r];
+    a = madd(T(C::b3), k3[r], a);
+    a = madd(T(C::b4), k4[r], a);
+    a = madd(T(C::b5), k5[r], a);
+    a = madd(T(C::b6), k6[r], a);
+    inc[r] = h * a;
+    y1[r] = y[r] + inc[r];  // SSAL: the 7th stage input is the new solution
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) ys[5][r] = y1[r];
+  F.eval(t + hd, y1, k7);
+}
+
+// Embedded error estimate e = h sum_i (b_i - bhat_i) k_i and the norm's
+// weights atol + rtol max(|y|, |y1|) (a4, a5); returns whether this lane's
+// components of y1 are finite.
+template <typename T, int R>
+__device__ __forceinline__ bool error_terms(T h, const T (&y)[R], const T (&y1)[R],
+                                            const T (&k1)[R], const T (&k3)[R], const T (&k4)[R],
+                                            const T (&k5)[R], const T (&k6)[R], const T (&k7)[R],
+                                            T rtol, T atol, T (&ev)[R], T (&sc)[R]) {
+  using C = DP5;
+  bool fin = true;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T a = T(C::e1) * k1[r];
+    a = madd(T(C::e3), k3[r], a);
+    a = madd(T(C::e4), k4[r], a);
+    a = madd(T(C::e5), k5[r], a);
+    a = madd(T(C::e6), k6[r], a);
+    a = madd(T(C::e7), k7[r], a);
+    ev[r] = h * a;
+    sc[r] = madd(rtol, T(tmax(fabs(y[r]), fabs(y1[r]))), atol);
+    fin = fin && finite_(y1[r]);
+  }
+  return fin;
+}
+
 // ---------------------------------------------------------------- one attempt (a3..a9)
 // Returns true while the instance is still running.
 template <class Field, typename T, int R, int G>
@@ -538,83 +637,10 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
   }
   s.h_last = h;
   const double hd = (double)h;
-  T k2[R], k3[R], k4[R], k5[R], k6[R], k7[R], Y[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) Y[r] = madd(h, T(C::a21) * s.k1[r], s.y[r]);
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[0][r] = Y[r];
-  F.eval(s.t + C::c2 * hd, Y, k2);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::a31) * s.k1[r];
-    a = madd(T(C::a32), k2[r], a);
-    Y[r] = madd(h, a, s.y[r]);
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[1][r] = Y[r];
-  F.eval(s.t + C::c3 * hd, Y, k3);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::a41) * s.k1[r];
-    a = madd(T(C::a42), k2[r], a);
-    a = madd(T(C::a43), k3[r], a);
-    Y[r] = madd(h, a, s.y[r]);
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[2][r] = Y[r];
-  F.eval(s.t + C::c4 * hd, Y, k4);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::a51) * s.k1[r];
-    a = madd(T(C::a52), k2[r], a);
-    a = madd(T(C::a53), k3[r], a);
-    a = madd(T(C::a54), k4[r], a);
-    Y[r] = madd(h, a, s.y[r]);
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[3][r] = Y[r];
-  F.eval(s.t + C::c5 * hd, Y, k5);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::a61) * s.k1[r];
-    a = madd(T(C::a62), k2[r], a);
-    a = madd(T(C::a63), k3[r], a);
-    a = madd(T(C::a64), k4[r], a);
-    a = madd(T(C::a65), k5[r], a);
-    Y[r] = madd(h, a, s.y[r]);
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[4][r] = Y[r];
-  F.eval(s.t + hd, Y, k6);
-  T y1[R], inc[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::b1) * s.k1[r];
-    a = madd(T(C::b3), k3[r], a);
-    a = madd(T(C::b4), k4[r], a);
-    a = madd(T(C::b5), k5[r], a);
-    a = madd(T(C::b6), k6[r], a);
-    inc[r] = h * a;
-    y1[r] = s.y[r] + inc[r];  // SSAL: the 7th stage input is the new solution
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[5][r] = y1[r];
-  F.eval(s.t + hd, y1, k7);
-  // embedded error estimate and its norm
-  T ev[R], sc[R];
-  bool fin_local = true;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::e1) * s.k1[r];
-    a = madd(T(C::e3), k3[r], a);
-    a = madd(T(C::e4), k4[r], a);
-    a = madd(T(C::e5), k5[r], a);
-    a = madd(T(C::e6), k6[r], a);
-    a = madd(T(C::e7), k7[r], a);
-    ev[r] = h * a;
-    sc[r] = madd(s.rtol, T(tmax(fabs(s.y[r]), fabs(y1[r]))), s.atol);
-    fin_local = fin_local && finite_(y1[r]);
-  }
+  T k3[R], k4[R], k5[R], k6[R], k7[R], y1[R], inc[R], ev[R], sc[R];
+  attempt_stages<Field, T, R>(F, s.t, h, s.y, s.k1, ys, k3, k4, k5, k6, k7, y1, inc);
+  const bool fin_local = error_terms<T, R>(h, s.y, y1, s.k1, k3, k4, k5, k6, k7, s.rtol, s.atol,
+                                           ev, sc);
   const T err = rms_norm<T, R, G>(ev, sc);
   bool finite = finite_(err);
   if constexpr (G > 1) finite = finite && (__all_sync(Grp<G>::mask(), fin_local) != 0);
@@ -729,10 +755,16 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
 // ---------------------------------------------------------------- finalize
 template <typename T, int R, int G>
 __device__ void inst_finalize(const Inst<T, R>& s, const SolveOpts& o, int i, int D,
-                              T* y_final, int32_t* n_acc, int32_t* n_rej, int32_t* n_fe,
-                              int32_t* status, const TraceDev& tr) {
+                              const InstOut<T>& out, T* y_final, int32_t* n_acc, int32_t* n_rej,
+                              int32_t* n_fe, int32_t* status, const TraceDev& tr) {
   const int g = Grp<G>::rank();
   const bool invalid = s.status == ST_INVALID;
+  if (s.status != ST_SUCCESS && !invalid) {  // points a failed instance never reached
+    T nanv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) nanv[r] = nan_(T(0));
+    for (int q = s.cursor; q < out.K; ++q) store_point<T, R, G>(out.ye + (size_t)q * D, nanv);
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) y_final[(size_t)i * D + g * R + r] = invalid ? nan_(T(0)) : s.y[r];
   if (g == 0) {

@@ -77,12 +77,25 @@ inline size_t order_part_bytes(int B) {
 }
 
 
+// Joint solve: a control block, three partial sums per CTA (at most one CTA
+// per instance), and per instance y, y_lo, k1, the pending new state and its
+// compensation term, the pending k3..k7 and stage inputs Y_2..Y_7.
+constexpr size_t JOINT_CTL_BYTES = 512;
+inline size_t joint_ws_offset(int B) {
+  return align256(256) + align256((size_t)B * 4) + order_part_bytes(B);
+}
+inline size_t joint_part_bytes(int B) { return align256((size_t)(B + 1) * 3 * 8); }
+inline size_t joint_state_bytes(int B, int D, size_t ts) {
+  return 5 * align256((size_t)B * D * ts) + align256(11 * (size_t)B * D * ts);
+}
+
 // Workspace bytes of the SIMT solver for state dtype size `ts`.
-inline size_t simt_workspace_bytes(int B, int D, size_t ts, int form) {
+inline size_t simt_workspace_bytes(int B, int D, size_t ts, int form, int joint) {
   size_t s = 0;
   s += align256(256);             // any-active flag + work counter
   s += align256((size_t)B * 4);    // work order
   s += order_part_bytes(B);        // and the sort's per-CTA counts
+  if (joint) return s + JOINT_CTL_BYTES + joint_part_bytes(B) + joint_state_bytes(B, D, ts);
   if (form == TODE_PLAIN) {
     s += 3 * align256((size_t)B * D * ts);  // y, y_lo, k1
     s += align256((size_t)B * 8);           // t
@@ -101,7 +114,7 @@ inline size_t simt_adjoint_scratch_bytes(int B, int D, size_t ts, int stride) {
          align256((size_t)stride * B * 8) + align256((size_t)stride * B * ts);
 }
 
-tode_err simt_solve_f64(const SolveReq& r);
+tode_err simt_solve_f64(const SolveReq& r);  // both: independent or joint (o->joint)
 tode_err simt_solve_f32(const SolveReq& r);
 tode_err simt_adjoint_f64(const AdjReq& r);
 tode_err simt_adjoint_f32(const AdjReq& r);

@@ -972,6 +972,12 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         s.phase = PH_STAGE;  // next attempt, FSAL k1 in hand
         if (MODE == MLP_PLAIN_STEP) park();
       } else {
+        if (s.status != ST_SUCCESS) {  // points the failed instance never reached
+          float* ye = a.ye + (size_t)i * a.K * D + coff;
+          for (int q = s.cursor; q < a.K; ++q)
+#pragma unroll
+            for (int r = 0; r < C; ++r) ye[(size_t)q * D + r] = nan_(0.0f);
+        }
 #pragma unroll
         for (int r = 0; r < C; ++r) a.yf[(size_t)i * D + coff + r] = y[r];
         if (sub == 0) {

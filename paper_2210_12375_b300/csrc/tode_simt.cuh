@@ -132,8 +132,9 @@ __global__ void k_plain_init(SolveArgs<T> a) {
                                 atol_of(a, i), inst_out(a, i));
   if (run) tape_store<T, R, G>(a.tape, i, s);
   plain_store<T, R, G>(a, j, i, s);
-  if (!run) inst_finalize<T, R, G>(s, a.o, i, a.D, a.yf, a.n_acc, a.n_rej, a.n_fe, a.status,
-                                   a.trace);
+  if (!run)
+    inst_finalize<T, R, G>(s, a.o, i, a.D, inst_out(a, i), a.yf, a.n_acc, a.n_rej, a.n_fe,
+                           a.status, a.trace);
 }
 
 template <class Field, typename T, int R, int G>
@@ -156,7 +157,8 @@ __global__ void k_plain_step(SolveArgs<T> a) {
   }
   plain_store<T, R, G>(a, j, i, s);
   if (!run) {
-    inst_finalize<T, R, G>(s, a.o, i, a.D, a.yf, a.n_acc, a.n_rej, a.n_fe, a.status, a.trace);
+    inst_finalize<T, R, G>(s, a.o, i, a.D, inst_out(a, i), a.yf, a.n_acc, a.n_rej, a.n_fe,
+                           a.status, a.trace);
   } else if (Grp<G>::rank() == 0) {
     *a.active = 1;
   }
@@ -180,8 +182,8 @@ __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
       have = inst_init<Field, T, R, G>(F, s, a.o, i, a.D, a.y0, a.t0, a.t1, rtol_of(a, i),
                                        atol_of(a, i), inst_out(a, i));
       if (!have) {
-        inst_finalize<T, R, G>(s, a.o, i, a.D, a.yf, a.n_acc, a.n_rej, a.n_fe, a.status,
-                               a.trace);
+        inst_finalize<T, R, G>(s, a.o, i, a.D, inst_out(a, i), a.yf, a.n_acc, a.n_rej,
+                               a.n_fe, a.status, a.trace);
         i = queued(a, grab_instance<G>(a.counter, groups_total));
         continue;
       }
@@ -195,7 +197,8 @@ __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
     if (run) {
       if (s.n_acc != acc_before) tape_store<T, R, G>(a.tape, i, s);
     } else {
-      inst_finalize<T, R, G>(s, a.o, i, a.D, a.yf, a.n_acc, a.n_rej, a.n_fe, a.status, a.trace);
+      inst_finalize<T, R, G>(s, a.o, i, a.D, inst_out(a, i), a.yf, a.n_acc, a.n_rej, a.n_fe,
+                           a.status, a.trace);
       have = false;
       i = queued(a, grab_instance<G>(a.counter, groups_total));
     }

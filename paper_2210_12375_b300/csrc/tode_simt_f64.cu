@@ -2,8 +2,11 @@
 // multiply-add is contracted and every sum is taken left to right: the FP64
 // path's accept/reject decisions are reproducible on any IEEE-754 machine.
 #include "tode_simt_adjoint.cuh"
+#include "tode_simt_joint.cuh"
 
 namespace tode {
-tode_err simt_solve_f64(const SolveReq& r) { return simt_solve<double>(r); }
+tode_err simt_solve_f64(const SolveReq& r) {
+  return r.o->joint ? simt_joint<double>(r) : simt_solve<double>(r);
+}
 tode_err simt_adjoint_f64(const AdjReq& r) { return simt_adjoint<double>(r); }
 }  // namespace tode

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2210_12375_b300 import _abi
@@ -81,6 +82,18 @@ def test_workspace_size_rules():
     assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_LINEAR, 10, 5)), C.byref(o), 1) == 0
     bad = _opts(fac_min=2.0)
     assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 10, 2)), C.byref(bad), 1) == 0
+    # joint solving: the fused form's part, a 512-byte control block, three
+    # partial sums per possible CTA and 16 state arrays of B*D
+    oj = _opts(prec=_abi.TODE_F64, joint=1)
+    B, D = 1000, 2
+    bd = -(-B * D * 8 // 256) * 256
+    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, B, D)), C.byref(oj), 16) == \
+        256 + 4096 + 512 + 24064 + 5 * bd + (-(-11 * B * D * 8 // 256) * 256)
+    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, B, D)),
+                                   C.byref(_opts(prec=_abi.TODE_F64, joint=2)), 16) == 0
+    rb = np.ones(B)
+    oj_b = _opts(prec=_abi.TODE_F64, joint=1, rtol_b=rb.ctypes.data)
+    assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, B, D)), C.byref(oj_b), 16) == 0
 
 
 @pytest.mark.parametrize("mutate,code", [

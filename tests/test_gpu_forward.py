@@ -230,6 +230,11 @@ def test_max_steps_and_given_h0(form):
     assert (g["status"] == 1).all() and ((g["n_acc"] + g["n_rej"]) == 7).all()
     o = oracle_solve(w, max_steps=7)
     assert _rel_close(g["y_final"], o["y_final"], 1e-12).all()
+    # evaluation points past the last accepted step are NaN, as in the oracle
+    nan_g, nan_o = np.isnan(g["y_eval"]), np.isnan(o["y_eval"])
+    assert np.array_equal(nan_g, nan_o) and nan_g.any() and not nan_g.all()
+    assert _rel_close(np.where(nan_g, 0, g["y_eval"]), np.where(nan_o, 0, o["y_eval"]),
+                      1e-12).all()
     g = gpu_solve(w, torch.float64, form, h0=1e-3)
     o = oracle_solve(w, h0=1e-3)
     assert np.array_equal(g["n_acc"], o["n_acc"])

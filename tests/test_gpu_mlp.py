@@ -69,10 +69,23 @@ def test_mlp_edge_cases():
     assert g["status"][3] == 0 and g["n_acc"][3] == 0
     assert np.array_equal(g["y_eval"][3], np.repeat(y0[3:4].astype(np.float32), 8, 0))
     assert g["status"][4] == 3 and o["status"][4] == 3
+    assert np.array_equal(np.isnan(g["y_eval"][4]), np.isnan(o["y_eval"][4]))
     assert (g["status"][5:] == 0).all()
     # the healthy rows of the same tiles are unaffected
     ref = gpu_solve(subset(w, np.arange(5, 200)), torch.float32, "fused")
     assert np.array_equal(ref["y_eval"], g["y_eval"][5:])
+
+
+@pytest.mark.parametrize("form", ["plain", "fused"])
+def test_mlp_max_steps_leaves_unreached_points_nan(form):
+    w = dict(make(4, B=300), split=True)
+    g = gpu_solve(w, torch.float32, form, max_steps=2)
+    assert (g["status"] == 1).all() and ((g["n_acc"] + g["n_rej"]) == 2).all()
+    nan = np.isnan(g["y_eval"])
+    rows = nan.any(axis=2)
+    assert np.array_equal(nan.all(axis=2), rows)           # whole points
+    assert (np.diff(rows.astype(int), axis=1) >= 0).all()  # from some point to the end
+    assert rows[:, -1].all() and not rows[:, 0].any()
 
 
 def test_mlp_unsupported_requests_fail_loudly():
