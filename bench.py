@@ -55,6 +55,9 @@ def _args():
                    help="issue the fused step eagerly instead of replaying a CUDA graph")
     p.add_argument("--no-autotune", action="store_true",
                    help="library default launch shapes instead of the autotuner's choice")
+    p.add_argument("--joint", action="store_true",
+                   help="the batching experiment of Sec. 4.1: one batch of strongly damped "
+                        "oscillators solved jointly (one stacked problem) and independently")
     return p.parse_args()
 
 
@@ -171,6 +174,104 @@ def adjoint_flops_per_step(kind: str, D: int, recorded: bool) -> float:
 def _events(torch, n):
     return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             for _ in range(n)]
+
+
+# ------------------------------------------------------------------ joint solving
+# Bytes one k_joint_step launch moves per instance and component while the
+# problem runs: it reads the state y, y_lo, k1 from one half of the double
+# buffer and writes the candidate to the other (6 values); the dense output
+# (K points over the whole solve) is left out.
+JOINT_VALUES_PER_COMPONENT = 6
+
+
+def run_joint(args):
+    """Sec. 4.1 / Fig. 1 on the B300: B Van der Pol oscillators with strong
+    damping (mu = 10) and varying initial states, on one shared time axis,
+    solved jointly (one stacked problem: one step size, norm and decision)
+    and independently (the fused solver).  The line's value is the joint
+    solve's instance-attempts per second; "batching" holds both step counts
+    and both times."""
+    import torch
+
+    import paper_2210_12375_b300 as tode
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    B = args.batch or (1 << 21)
+    mu, T, K, tol = 10.0, 40.0, 16, 1e-6
+    rng = np.random.default_rng(20221023)
+    y0 = torch.tensor(rng.uniform(-2.0, 2.0, (B, 2)), dtype=torch.float32, device=dev)
+    field = tode.VdP(torch.full((B,), mu, dtype=torch.float32, device=dev))
+    t0 = torch.zeros(B, dtype=torch.float64, device=dev)
+    t1 = torch.full((B,), T, dtype=torch.float64, device=dev)
+    te = torch.linspace(0.0, T, K, dtype=torch.float64, device=dev).expand(B, K).contiguous()
+    opt = dict(rtol=tol, atol=tol)
+    poll = 64
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    ind = tode.solve(field, y0, t0, t1, te, form="fused", **opt)
+    jnt = tode.solve(field, y0, t0, t1, te, joint=True, poll_every=poll, **opt)
+    torch.cuda.synchronize()
+    assert int((ind.status != 0).sum()) == 0 and int((jnt.status != 0).sum()) == 0
+    j_acc, j_rej = int(jnt.n_acc[0]), int(jnt.n_rej[0])
+    i_acc = ind.n_acc.double()
+    i_att = int((ind.n_acc.long() + ind.n_rej.long()).sum())
+
+    def timed(fn, n):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        ev = _events(torch, n)
+        for k in range(n):
+            flush.zero_()
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    sol_i, sol_j = ind, jnt
+    ws_i, ws_j = ind.extra["workspace"], jnt.extra["workspace"]
+    n = max(3, min(args.steps, 10))
+    with ClockSampler(0) as clk:
+        ms_j = timed(lambda: tode.solve(field, y0, t0, t1, te, joint=True, poll_every=poll,
+                                        out=sol_j, workspace=ws_j, **opt), n)
+        ms_i = timed(lambda: tode.solve(field, y0, t0, t1, te, form="fused", out=sol_i,
+                                        workspace=ws_i, **opt), n)
+    clocks = clk.summary()
+    # launches: init, first step, then attempts + the final commit, issued in
+    # groups of `poll` (the group that finishes the solve ends in no-ops)
+    step_launches = -(-(j_acc + j_rej + 1) // poll) * poll
+    launches = 2 + step_launches
+    per_launch_ms = ms_j / launches  # an upper bound: host polls and no-op launches included
+    by = B * 2 * (JOINT_VALUES_PER_COMPONENT * 4) + B * 4  # + mu
+    peaks, src = _peaks()
+    achieved = by / (per_launch_ms * 1e-3) / 1e9
+    value = B * (j_acc + j_rej) / (ms_j * 1e-3)
+    print(json.dumps({
+        "metric": "instance-steps/s, joint (stacked) dopri5 solve, Sec. 4.1 batching experiment",
+        "value": value, "unit": "instance-steps/s", "n_gpus": 1, "steps": n,
+        "warmup": max(args.warmup, 1), "ms_per_step": ms_j, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Van der Pol oscillators, mu = 10, y0 ~ U[-2,2]^2)",
+        "config": {"workload": f"vdp_joint_mu10_b{B}", "B": B, "t": [0.0, T], "t_eval": K,
+                   "rtol": tol, "atol": tol, "pass": "fwd", "l2": "flushed between passes",
+                   "poll_every": poll},
+        "batching": {"joint_n_acc": j_acc, "joint_n_rej": j_rej,
+                     "independent_n_acc_mean": float(i_acc.mean()),
+                     "independent_n_acc_max": int(i_acc.max()),
+                     "steps_ratio_vs_mean": j_acc / float(i_acc.mean()),
+                     "joint_ms": ms_j, "independent_ms": ms_i, "time_ratio": ms_j / ms_i,
+                     "independent_instance_steps_per_s": i_att / (ms_i * 1e-3)},
+        "roofline": {"bound": "hbm", "kernel": "k_joint_step<VdpField<float>>",
+                     "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "peak_source": src,
+                     "traffic": None, "kernel_ms": per_launch_ms,
+                     "bytes_per_launch": by},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }), flush=True)
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -644,5 +745,7 @@ if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.joint:
+        run_joint(a)
     else:
         run_tode(a)

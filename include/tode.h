@@ -131,8 +131,8 @@ typedef struct {
    * Pol and linear fields, scalar rtol/atol; every instance must have the
    * same t0, t1 and t_eval as instance 0, else every instance is reported
    * TODE_S_INVALID_INPUT.  n_acc/n_rej/status are the problem's, repeated
-   * for every instance.  One launch per attempt (form, order and
-   * ctas_per_sm do not apply; block and poll_every do); a tape must be
+   * for every instance.  One launch per attempt (form and order do not
+   * apply; block, ctas_per_sm and poll_every do); a tape must be
    * stride 1 with h_acc, and tode_adjoint then reverses the shared mesh
    * per instance as usual. */
   int joint;
@@ -200,8 +200,8 @@ void tode_default_options(tode_options* o);
  * a work counter, the work order (one int32 per instance) and, above 2048
  * instances, the work-order sort's per-CTA counts, plus the per-instance
  * solver state between launches for the plain form, or for joint solving a
- * control block, per-CTA partial sums and 16 * B * D state values (the
- * state, the pending attempt's new state, stages and stage inputs).
+ * control block, per-CTA partial sums and a double buffer of the state
+ * (6 * B * D values: y, its FP32 compensation term, k1).
  * Returns 0 for an unsupported or invalid combination. */
 size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int K);
 

@@ -78,15 +78,14 @@ inline size_t order_part_bytes(int B) {
 
 
 // Joint solve: a control block, three partial sums per CTA (at most one CTA
-// per instance), and per instance y, y_lo, k1, the pending new state and its
-// compensation term, the pending k3..k7 and stage inputs Y_2..Y_7.
+// per instance) and a double buffer of the per-instance state y, y_lo, k1.
 constexpr size_t JOINT_CTL_BYTES = 512;
 inline size_t joint_ws_offset(int B) {
   return align256(256) + align256((size_t)B * 4) + order_part_bytes(B);
 }
 inline size_t joint_part_bytes(int B) { return align256((size_t)(B + 1) * 3 * 8); }
 inline size_t joint_state_bytes(int B, int D, size_t ts) {
-  return 5 * align256((size_t)B * D * ts) + align256(11 * (size_t)B * D * ts);
+  return 6 * align256((size_t)B * D * ts);
 }
 
 // Workspace bytes of the SIMT solver for state dtype size `ts`.

@@ -5,16 +5,23 @@
 // experiment (Fig. 1) compares independent solving against; every instance
 // still evaluates its own field.
 //
-// One launch per attempt.  Launch n first commits the decision taken on
-// attempt n-1 (its trace entry and, if it was accepted, the dense output
-// over the step, the new state and the tape slots), then, while the problem
-// runs, computes attempt n for every instance together with each CTA's
+// One launch per attempt.  Launch n commits the decision taken on attempt
+// n-1 (its trace entry and the decision-dependent tape fields), then, while
+// the problem runs, computes attempt n for every instance with each CTA's
 // partial sum of squared scaled errors.  The CTA that finishes last (a
 // ticket counter: no CTA ever waits for another) sums the partials in CTA
 // order, takes the decision, runs the controller and writes the control
-// block that launch n+1 reads.  Two launches before the first attempt
-// validate the batch and pick the first step (the HNW Sec. II.4 heuristic
-// with its norms over the whole batch).
+// block that launch n+1 reads.
+//
+// Every instance shares the decision, so an attempt writes its results as if
+// it were accepted: the candidate state goes to the other half of a double
+// buffer (an acceptance only flips the buffer index), the dense output of
+// the points in (t, t + h] and the tape slots straight to their places.  A
+// rejected attempt's points are written again by the accepted step that
+// later covers them, and a failed solve turns every point past its last
+// accepted step into NaN, so nothing but the state is ever staged.  Two
+// launches before the first attempt validate the batch and pick the first
+// step (the HNW Sec. II.4 heuristic with its norms over the whole batch).
 #pragma once
 #include "tode_simt.cuh"
 
@@ -27,26 +34,26 @@ enum : int { JD_NONE = 0, JD_ACC = 1, JD_REJ = 2 };  // decision the next launch
 // that finishes last in a launch, after every other CTA has read it).
 template <typename T> struct JointCtl {
   double t, t0, t1;
-  double dec_t, dec_t_next;  // the decided attempt: its start, its end if accepted
+  double dec_t;              // start of the decided attempt
   T h;                       // step proposed for the next attempt
   T h_use;                   // the next attempt's step, clipped at t1
   T err_prev, rem, hmin;
   T d1, h0;                  // starting-step heuristic between its two launches
   T dec_h, dec_err;
   int use_last, flags, n_acc, n_rej, status, phase, cursor;
-  int dec, dec_att, dec_cur0;
+  int cur;                   // half of the state double buffer that holds the state
+  int dec, dec_att;
   unsigned int ticket;       // CTAs finished in the current launch
 };
 static_assert(sizeof(JointCtl<double>) <= JOINT_CTL_BYTES, "control block");
 
 template <typename T> struct JointArgs {
-  SolveArgs<T> a;  // problem, outputs, options; a.wy/wylo/wk hold y, y_lo, k1
+  SolveArgs<T> a;  // problem, outputs, options
   JointCtl<T>* ctl;
   double* part;    // [grid][3] per-CTA partial sums
-  T* wyn;          // pending new state and its compensation term
-  T* wylon;
-  T* wks;          // pending k3..k7, 5 arrays of B*D
-  T* wys;          // pending stage inputs Y_2..Y_7, 6 arrays of B*D (tape with y_stage only)
+  T* y[2];         // state double buffer: y, its compensation term, k1 (FSAL)
+  T* ylo[2];
+  T* k1[2];
 };
 
 // Per-instance arrays are lane-interleaved like the plain form's state:
@@ -64,14 +71,17 @@ __device__ __forceinline__ void jst(T* p, int B, int i, const T (&v)[R]) {
   for (int r = 0; r < R; ++r) p[((size_t)r * B + i) * G + g] = v[r];
 }
 
-// Sum of one double per thread over the CTA in a fixed order (a butterfly
-// in each warp, then the warps in order); the result is valid in thread 0.
-__device__ __forceinline__ double cta_sum(double v, double* red) {
+// Sum of one value per thread over the CTA in a fixed order (a butterfly in
+// each warp, then the warps in order), in the state type: an FP32 batch
+// reduces on the FP32 pipe (B300's FP64 pipe is narrow), an FP64 batch in
+// FP64.  The result is valid in thread 0.
+template <typename T> __device__ __forceinline__ T cta_sum(T v, double* red_d) {
+  T* red = reinterpret_cast<T*>(red_d);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = T(0);
   if (threadIdx.x == 0)
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
   __syncthreads();
@@ -92,11 +102,21 @@ __device__ __forceinline__ bool joint_last_cta(unsigned int* ticket, int* flag) 
 }
 
 // The last CTA's sum of partial k over all CTAs, in CTA order per thread
-// and then a fixed tree; valid in thread 0.
+// and then a fixed tree, in FP64; valid in thread 0.
 __device__ __forceinline__ double joint_total(const double* part, int k, double* red) {
   double s = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(part + 3 * b + k);
-  return cta_sum(s, red);
+  const int n = (int)gridDim.x, stride = (int)blockDim.x;
+  for (int b0 = threadIdx.x; b0 < n; b0 += 4 * stride) {
+    double v[4];  // four loads in flight, added in order
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int b = b0 + u * stride;
+      v[u] = b < n ? __ldcg(part + 3 * b + k) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s += v[u];
+  }
+  return cta_sum<double>(s, red);
 }
 
 // The next attempt's step: the proposal, clipped so that the step ends at t1.
@@ -126,10 +146,14 @@ __global__ void __launch_bounds__(256) k_joint_init(JointArgs<T> ja) {
   const SolveArgs<T>& a = ja.a;
   __shared__ double red[32];
   __shared__ int last_s;
-  const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
   const int g = Grp<G>::rank();
-  double s0 = 0.0, s1 = 0.0, bad = 0.0;
-  if (i < a.B) {
+  T s0 = T(0), s1 = T(0);
+  bool bad = false;
+  // grid-stride over the instances (lane groups stay within one warp);
+  // each thread accumulates its instances in index order
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j / G < a.B;
+       j += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(j / G);
     Field F;
     F.load(a.fparam, i);
     Inst<T, R> s;
@@ -141,9 +165,9 @@ __global__ void __launch_bounds__(256) k_joint_init(JointArgs<T> ja) {
     bool same = tkey(a.t0[i]) == tkey(a.t0[0]) && tkey(a.t1[i]) == tkey(a.t1[0]);
     for (int q = g; q < a.K; q += G) same = same && tkey(out.te[q]) == tkey(a.te[q]);
     if constexpr (G > 1) same = __all_sync(Grp<G>::mask(), same) != 0;
-    jst<T, R, G>(a.wy, a.B, i, s.y);
-    jst<T, R, G>(a.wylo, a.B, i, s.ylo);
-    jst<T, R, G>(a.wk, a.B, i, s.k1);
+    jst<T, R, G>(ja.y[0], a.B, i, s.y);
+    if constexpr (Comp<T>::on) jst<T, R, G>(ja.ylo[0], a.B, i, s.ylo);
+    jst<T, R, G>(ja.k1[0], a.B, i, s.k1);
     T q0[R], q1[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -154,20 +178,20 @@ __global__ void __launch_bounds__(256) k_joint_init(JointArgs<T> ja) {
     }
     const T S0 = group_sum<T, R, G>(q0), S1 = group_sum<T, R, G>(q1);
     if (g == 0) {
-      bad = (s.status == ST_INVALID || !same) ? 1.0 : 0.0;
+      bad = bad || s.status == ST_INVALID || !same;
       if (run) {
-        s0 = (double)S0;
-        s1 = (double)S1;
+        s0 += S0;
+        s1 += S1;
       }
     }
   }
-  s0 = cta_sum(s0, red);
-  s1 = cta_sum(s1, red);
-  bad = cta_sum(bad, red);
+  const int nbad = __syncthreads_count(bad);
+  s0 = cta_sum<T>(s0, red);
+  s1 = cta_sum<T>(s1, red);
   if (threadIdx.x == 0) {
-    ja.part[3 * blockIdx.x + 0] = s0;
-    ja.part[3 * blockIdx.x + 1] = s1;
-    ja.part[3 * blockIdx.x + 2] = bad;
+    ja.part[3 * blockIdx.x + 0] = (double)s0;
+    ja.part[3 * blockIdx.x + 1] = (double)s1;
+    ja.part[3 * blockIdx.x + 2] = (double)nbad;
   }
   if (!joint_last_cta(&ja.ctl->ticket, &last_s)) return;
   const double S0 = joint_total(ja.part, 0, red);
@@ -217,15 +241,18 @@ __global__ void __launch_bounds__(256) k_joint_h0(JointArgs<T> ja) {
   if (c.phase != JP_H0) return;
   __shared__ double red[32];
   __shared__ int last_s;
-  const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
-  double s2 = 0.0;
-  if (i < a.B) {
+  T s2 = T(0);
+  // grid-stride over the instances (lane groups stay within one warp);
+  // each thread accumulates its instances in index order
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j / G < a.B;
+       j += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(j / G);
     Field F;
     F.load(a.fparam, i);
     const T rtol = T(a.rtol), atol = T(a.atol);
     T y[R], k1[R], w[R], f1[R], q[R];
-    jld<T, R, G>(a.wy, a.B, i, y);
-    jld<T, R, G>(a.wk, a.B, i, k1);
+    jld<T, R, G>(ja.y[0], a.B, i, y);
+    jld<T, R, G>(ja.k1[0], a.B, i, k1);
 #pragma unroll
     for (int r = 0; r < R; ++r) w[r] = madd(c.h0, k1[r], y[r]);
     F.eval(c.t0 + (double)c.h0, w, f1);
@@ -236,10 +263,10 @@ __global__ void __launch_bounds__(256) k_joint_h0(JointArgs<T> ja) {
       q[r] = u * u;
     }
     const T S2 = group_sum<T, R, G>(q);
-    if (Grp<G>::rank() == 0) s2 = (double)S2;
+    if (Grp<G>::rank() == 0) s2 += S2;
   }
-  s2 = cta_sum(s2, red);
-  if (threadIdx.x == 0) ja.part[3 * blockIdx.x] = s2;
+  s2 = cta_sum<T>(s2, red);
+  if (threadIdx.x == 0) ja.part[3 * blockIdx.x] = (double)s2;
   if (!joint_last_cta(&ja.ctl->ticket, &last_s)) return;
   const double S2 = joint_total(ja.part, 0, red);
   if (threadIdx.x != 0) return;
@@ -259,6 +286,24 @@ __global__ void __launch_bounds__(256) k_joint_h0(JointArgs<T> ja) {
 }
 
 // ---------------------------------------------------------------- launch 3..: attempts
+// The state slot that an accepted attempt opens, written before the
+// decision: y, y_lo, k1 and t (h, err_prev and flags follow the decision).
+// Joint tapes have stride 1.
+template <typename T, int R, int G>
+__device__ __forceinline__ void joint_tape_state(const TapeDev<T>& tp, int i, int j, double t,
+                                                 const T (&y)[R], const T (&ylo)[R],
+                                                 const T (&k1)[R]) {
+  if (tp.slots == 0 || j >= tp.slots) return;
+  const size_t o = (size_t)i * tp.slots + j;
+  const int g = Grp<G>::rank();
+  st_row<T, R>(tp.y + o * tp.D + g * R, y);
+  if (tp.k1) st_row<T, R>(tp.k1 + o * tp.D + g * R, k1);
+  if constexpr (Comp<T>::on) {
+    if (tp.ylo) st_row<T, R>(tp.ylo + o * tp.D + g * R, ylo);
+  }
+  if (g == 0) tp.t[o] = t;
+}
+
 template <class Field, typename T, int R, int G>
 __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
   const SolveArgs<T>& a = ja.a;
@@ -266,31 +311,17 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
   if (c.phase != JP_RUN) return;
   __shared__ double red[32];
   __shared__ int last_s;
-  const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
   const int g = Grp<G>::rank();
-  const size_t BD = (size_t)a.B * a.D;
-  double sq = 0.0, nonfin = 0.0;
-  if (i < a.B) {
-    Field F;
-    F.load(a.fparam, i);
+  T sq = T(0);
+  bool nonfin = false;
+  // grid-stride over the instances (lane groups stay within one warp);
+  // each thread accumulates its instances in index order
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j / G < a.B;
+       j += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(j / G);
     const InstOut<T> out = inst_out(a, i);
-    Inst<T, R> s;
-    jld<T, R, G>(a.wy, a.B, i, s.y);
-    jld<T, R, G>(a.wylo, a.B, i, s.ylo);
-    jld<T, R, G>(a.wk, a.B, i, s.k1);
-    s.t0 = c.t0;
-    s.t1 = c.t1;
-    s.rtol = T(a.rtol);
-    s.atol = T(a.atol);
-    s.n_acc = c.n_acc;
-    s.n_rej = c.n_rej;
-    s.status = c.status;
-    s.cursor = c.cursor;
-    s.t = c.t;
-    s.h = c.h;
-    s.err_prev = c.err_prev;
-    s.flags = c.flags;
-    // ---- commit the decided attempt
+    // ---- commit the decided attempt: its trace entry, and the controller
+    // state of the tape slot it opened
     if (c.dec != JD_NONE && a.trace.cap > 0 && c.dec_att < a.trace.cap && g == 0) {
       const size_t q = (size_t)i * a.trace.cap + c.dec_att;
       a.trace.t[q] = c.dec_t;
@@ -298,56 +329,34 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
       a.trace.err[q] = (double)c.dec_err;
       a.trace.acc[q] = c.dec == JD_ACC ? 1 : 0;
     }
-    if (c.dec == JD_ACC) {
-      T k3[R], k4[R], k5[R], k6[R], k7[R], yn[R], ylon[R];
-      jld<T, R, G>(ja.wks + 0 * BD, a.B, i, k3);
-      jld<T, R, G>(ja.wks + 1 * BD, a.B, i, k4);
-      jld<T, R, G>(ja.wks + 2 * BD, a.B, i, k5);
-      jld<T, R, G>(ja.wks + 3 * BD, a.B, i, k6);
-      jld<T, R, G>(ja.wks + 4 * BD, a.B, i, k7);
-      jld<T, R, G>(ja.wyn, a.B, i, yn);
-      jld<T, R, G>(ja.wylon, a.B, i, ylon);
-      const T h = c.dec_h;
-      const double hd = (double)h;
-      const long long kn = tkey(c.dec_t_next);
-      for (int q = c.dec_cur0; q < a.K; ++q) {  // the points in (t, t_next]
-        const double tq = out.te[q];
-        const long long kq = tkey(tq);
-        if (kq > kn) break;
-        T* dst = out.ye + (size_t)q * a.D;
-        if (kq == kn) {
-          store_point<T, R, G>(dst, yn);
-        } else {
-          T theta;
-          if constexpr (Comp<T>::on) theta = T(tq - c.dec_t) / h;
-          else theta = T((tq - c.dec_t) / hd);
-          T v[R];
-          dense_point<T, R>(theta, h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
-          store_point<T, R, G>(dst, v);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        s.y[r] = yn[r];
-        s.ylo[r] = ylon[r];
-        s.k1[r] = k7[r];  // FSAL
-      }
-      jst<T, R, G>(a.wy, a.B, i, s.y);
-      jst<T, R, G>(a.wylo, a.B, i, s.ylo);
-      jst<T, R, G>(a.wk, a.B, i, s.k1);
-      if (a.tape.slots > 0) {
-        T ys[6][R];
-        if (a.tape.ystage) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) jld<T, R, G>(ja.wys + k * BD, a.B, i, ys[k]);
-        }
-        s.h_last = h;
-        tape_store_hacc<T, R, G>(a.tape, i, s, ys);
-        if (c.status == ST_RUNNING) tape_store<T, R, G>(a.tape, i, s);
-      }
-    } else if (c.dec == JD_NONE && c.status == ST_RUNNING) {
-      tape_store<T, R, G>(a.tape, i, s);  // slot 0: the first launch of attempts
+    if (c.dec == JD_ACC && c.status == ST_RUNNING && g == 0 && c.n_acc < a.tape.slots) {
+      const size_t o = (size_t)i * a.tape.slots + c.n_acc;
+      if (a.tape.h) a.tape.h[o] = c.h;
+      if (a.tape.err_prev) a.tape.err_prev[o] = c.err_prev;
+      if (a.tape.flags) a.tape.flags[o] = c.flags;
     }
+    Inst<T, R> s;
+    jld<T, R, G>(ja.y[c.cur], a.B, i, s.y);
+    if constexpr (Comp<T>::on) {
+      jld<T, R, G>(ja.ylo[c.cur], a.B, i, s.ylo);
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) s.ylo[r] = T(0);
+    }
+    jld<T, R, G>(ja.k1[c.cur], a.B, i, s.k1);
+    s.t0 = c.t0;
+    s.t1 = c.t1;
+    s.t = c.t;
+    s.h = c.h;
+    s.err_prev = c.err_prev;
+    s.flags = c.flags;
+    s.rtol = T(a.rtol);
+    s.atol = T(a.atol);
+    s.n_acc = c.n_acc;
+    s.n_rej = c.n_rej;
+    s.status = c.status;
+    s.cursor = c.cursor;
+    if (c.dec == JD_NONE && c.status == ST_RUNNING) tape_store<T, R, G>(a.tape, i, s);  // slot 0
     if (c.status != ST_RUNNING) {
       if (c.status == ST_INVALID) {  // the batch is not one problem: no output is defined
         T nanv[R];
@@ -359,7 +368,10 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
                              a.trace);
     } else {
       // ---- attempt n with the batch's step
+      Field F;
+      F.load(a.fparam, i);
       const T h = c.h_use;
+      const double hd = (double)h;
       T ys[6][R], k3[R], k4[R], k5[R], k6[R], k7[R], y1[R], inc[R], ev[R], sc[R], q2[R];
       attempt_stages<Field, T, R>(F, c.t, h, s.y, s.k1, ys, k3, k4, k5, k6, k7, y1, inc);
       bool fin = error_terms<T, R>(h, s.y, y1, s.k1, k3, k4, k5, k6, k7, s.rtol, s.atol, ev, sc);
@@ -371,8 +383,8 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
       const T S = group_sum<T, R, G>(q2);
       if constexpr (G > 1) fin = __all_sync(Grp<G>::mask(), fin) != 0;
       if (g == 0) {
-        sq = (double)S;
-        nonfin = fin ? 0.0 : 1.0;
+        sq += S;
+        nonfin = nonfin || !fin;
       }
       T yn[R], ylon[R];
 #pragma unroll
@@ -386,24 +398,45 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
           ylon[r] = T(0);
         }
       }
-      jst<T, R, G>(ja.wyn, a.B, i, yn);
-      jst<T, R, G>(ja.wylon, a.B, i, ylon);
-      jst<T, R, G>(ja.wks + 0 * BD, a.B, i, k3);
-      jst<T, R, G>(ja.wks + 1 * BD, a.B, i, k4);
-      jst<T, R, G>(ja.wks + 2 * BD, a.B, i, k5);
-      jst<T, R, G>(ja.wks + 3 * BD, a.B, i, k6);
-      jst<T, R, G>(ja.wks + 4 * BD, a.B, i, k7);
-      if (a.tape.ystage) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) jst<T, R, G>(ja.wys + k * BD, a.B, i, ys[k]);
+      const int nb = c.cur ^ 1;
+      jst<T, R, G>(ja.y[nb], a.B, i, yn);
+      if constexpr (Comp<T>::on) jst<T, R, G>(ja.ylo[nb], a.B, i, ylon);
+      jst<T, R, G>(ja.k1[nb], a.B, i, k7);  // FSAL
+      // ---- the results of an acceptance, written before the decision
+      double t_next = c.use_last ? c.t1 : c.t + hd;
+      if constexpr (Comp<T>::on) {
+        if (!c.use_last && tkey(t_next) >= tkey(c.t1)) t_next = c.t1;  // landed on t1
+      }
+      const long long kn = tkey(t_next);
+      for (int q = c.cursor; q < a.K; ++q) {  // the points in (t, t_next]
+        const double tq = a.te[q];  // the batch's evaluation times (equal in every row)
+        const long long kq = tkey(tq);
+        if (kq > kn) break;
+        T* dst = out.ye + (size_t)q * a.D;
+        if (kq == kn) {
+          store_point<T, R, G>(dst, yn);
+        } else {
+          T theta;
+          if constexpr (Comp<T>::on) theta = T(tq - c.t) / h;
+          else theta = T((tq - c.t) / hd);
+          T v[R];
+          dense_point<T, R>(theta, h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
+          store_point<T, R, G>(dst, v);
+        }
+      }
+      if (a.tape.slots > 0) {
+        s.n_acc = c.n_acc + 1;
+        s.h_last = h;
+        tape_store_hacc<T, R, G>(a.tape, i, s, ys);
+        joint_tape_state<T, R, G>(a.tape, i, c.n_acc + 1, t_next, yn, ylon, k7);
       }
     }
   }
-  sq = cta_sum(sq, red);
-  nonfin = cta_sum(nonfin, red);
+  const int nnf = __syncthreads_count(nonfin);
+  sq = cta_sum<T>(sq, red);
   if (threadIdx.x == 0) {
-    ja.part[3 * blockIdx.x + 0] = sq;
-    ja.part[3 * blockIdx.x + 1] = nonfin;
+    ja.part[3 * blockIdx.x + 0] = (double)sq;
+    ja.part[3 * blockIdx.x + 1] = (double)nnf;
   }
   if (!joint_last_cta(&ja.ctl->ticket, &last_s)) return;
   const double S = joint_total(ja.part, 0, red);
@@ -418,7 +451,7 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
     *ja.ctl = n;
     return;
   }
-  const T err = T(sqrt(S / (double)BD));
+  const T err = T(sqrt(S / ((double)a.B * a.D)));
   const bool finite = NF == 0.0 && finite_(err);
   const bool accept = finite && err <= T(1);
   const T h = c.h_use;
@@ -428,7 +461,6 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
   n.dec_h = h;
   n.dec_err = err;
   n.dec_att = c.n_acc + c.n_rej;
-  n.dec_cur0 = c.cursor;
   T h_next;
   if (accept) {
     double t_next = last ? c.t1 : c.t + hd;
@@ -455,12 +487,12 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
     n.flags = c.flags & ~FL_PREV_REJ;
     n.n_acc = c.n_acc + 1;
     n.t = t_next;
+    n.cur = c.cur ^ 1;
     if constexpr (Comp<T>::on) {
       if (!last) n.rem = __double2float_rd(c.t1 - t_next);
     }
     if (last) n.status = ST_SUCCESS;
     n.dec = JD_ACC;
-    n.dec_t_next = t_next;
   } else {
     const T fmin = opt_v<T>(a.o.fac_min, a.o.fac_min_f);
     const T fac =
@@ -497,26 +529,19 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
 // Workspace of the joint solve (must match simt_workspace_bytes).
 template <typename T> JointArgs<T> make_joint_args(const SolveReq& r) {
   JointArgs<T> j{};
-  j.a = make_solve_args<T>(r);  // carves the work order part, unused here
+  j.a = make_solve_args<T>(r);
+  j.a.order = nullptr;  // one problem: every instance takes every attempt
   char* p = r.ws + joint_ws_offset(r.B);
   const size_t bd = align256((size_t)r.B * r.D * sizeof(T));
   j.ctl = (JointCtl<T>*)p;
   p += JOINT_CTL_BYTES;
   j.part = (double*)p;
   p += joint_part_bytes(r.B);
-  j.a.wy = (T*)p;
-  p += bd;
-  j.a.wylo = (T*)p;
-  p += bd;
-  j.a.wk = (T*)p;
-  p += bd;
-  j.wyn = (T*)p;
-  p += bd;
-  j.wylon = (T*)p;
-  p += bd;
-  j.wks = (T*)p;
-  p += 5 * (size_t)r.B * r.D * sizeof(T);
-  j.wys = (T*)p;
+  T** arrays[6] = {&j.y[0], &j.y[1], &j.ylo[0], &j.ylo[1], &j.k1[0], &j.k1[1]};
+  for (T** q : arrays) {
+    *q = (T*)p;
+    p += bd;
+  }
   return j;
 }
 
@@ -524,18 +549,27 @@ template <class Field, typename T, int R, int G>
 tode_err launch_joint(const SolveReq& r) {
   if (r.B == 0) return TODE_OK;
   JointArgs<T> ja = make_joint_args<T>(r);
-  ja.a.order = nullptr;  // one problem: every instance takes every attempt
   const cudaStream_t st = r.stream;
   const long long threads = (long long)r.B * G;
   const int block = r.o->block > 0 ? r.o->block : default_block(threads, r.num_sms);
   if (block % 32 != 0 || block > 256) return TODE_EINVAL;
-  const int grid = (int)((threads + block - 1) / block);
+  // as many CTAs as are resident at once (one partial sum each, so the CTA
+  // that finishes last has few to add), at most one per lane group
+  int per_sm = r.o->ctas_per_sm;
+  if (per_sm <= 0) {
+    TODE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_joint_step<Field, T, R, G>, block, 0));
+    if (per_sm < 1) per_sm = 1;
+  }
+  long long grid_ll = (threads + block - 1) / block;
+  if (grid_ll > (long long)r.num_sms * per_sm) grid_ll = (long long)r.num_sms * per_sm;
+  const int grid = (int)grid_ll;
   TODE_CUDA_TRY(cudaMemsetAsync(ja.ctl, 0, sizeof(JointCtl<T>), st));
   k_joint_init<Field, T, R, G><<<grid, block, 0, st>>>(ja);
   k_joint_h0<Field, T, R, G><<<grid, block, 0, st>>>(ja);
   TODE_CUDA_TRY(cudaGetLastError());
   const int poll = r.o->poll_every > 0 ? r.o->poll_every : 16;
-  // one launch per attempt plus the one that commits the last decision
+  // one launch per attempt plus the one that finalizes
   const long long limit = (long long)r.o->max_steps + 2LL * poll + 2;
   long long launched = 0;
   while (true) {

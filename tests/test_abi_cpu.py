@@ -83,12 +83,12 @@ def test_workspace_size_rules():
     bad = _opts(fac_min=2.0)
     assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, 10, 2)), C.byref(bad), 1) == 0
     # joint solving: the fused form's part, a 512-byte control block, three
-    # partial sums per possible CTA and 16 state arrays of B*D
+    # partial sums per possible CTA and a double buffer of y, y_lo, k1
     oj = _opts(prec=_abi.TODE_F64, joint=1)
     B, D = 1000, 2
     bd = -(-B * D * 8 // 256) * 256
     assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, B, D)), C.byref(oj), 16) == \
-        256 + 4096 + 512 + 24064 + 5 * bd + (-(-11 * B * D * 8 // 256) * 256)
+        256 + 4096 + 512 + 24064 + 6 * bd
     assert lib.tode_workspace_size(C.byref(_desc(_abi.TODE_VDP, B, D)),
                                    C.byref(_opts(prec=_abi.TODE_F64, joint=2)), 16) == 0
     rb = np.ones(B)

@@ -71,9 +71,12 @@ def test_joint_f32_linear_matches_oracle(block):
 
 
 @pytest.mark.parametrize("B", [1, 33, 1000, 20000])
-def test_joint_ragged_and_multi_cta_batches(B):
+@pytest.mark.parametrize("launch", [dict(block=64), dict(block=32, ctas_per_sm=1)])
+def test_joint_ragged_and_multi_cta_batches(B, launch):
+    # the second launch shape runs 148 CTAs of one warp: each thread takes
+    # several instances in turn on the larger batches
     w = _joint(1, B, 6.0, 5)
-    g = gpu_solve(w, torch.float64, "plain", joint=True, block=64)
+    g = gpu_solve(w, torch.float64, "plain", joint=True, **launch)
     o = _oracle_joint(w)
     assert (g["status"] == o["status"]).all()
     assert (g["n_acc"] == o["n_acc"]).all() and (g["n_rej"] == o["n_rej"]).all()
