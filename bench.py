@@ -131,6 +131,7 @@ TRAFFIC = {
     ("vdp_mix_b262144", "k_fused<VdpField<float>>"): 8 * 91.90e6,
     ("vdp_mix_b262144", "k_adjoint_steps<VdpAdj<float>>"): 8 * 124.08e6,
     ("mlp_d32_h128", "k_mlp_fused"): 12.51e6,
+    ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 70.45e6,
 }
 
 
@@ -267,7 +268,8 @@ def run_joint(args):
         "roofline": {"bound": "hbm", "kernel": "k_joint_step<VdpField<float>>",
                      "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "peak_source": src,
-                     "traffic": None, "kernel_ms": per_launch_ms,
+                     "traffic": _traffic(f"vdp_joint_mu10_b{B}", "k_joint_step<VdpField<float>>"),
+                     "kernel_ms": per_launch_ms,
                      "bytes_per_launch": by},
         "clocks": clocks,
         "gpu_launches": launches,
