@@ -60,6 +60,7 @@ class _Opts(C.Structure):
         ("beta2", C.c_double),
         ("h0", C.c_double),
         ("max_steps", C.c_int),
+        ("beta3", C.c_double),
     ]
 
 
@@ -111,7 +112,7 @@ def _iptr(a):
 def default_opts(**kw) -> dict:
     """Integral controller defaults (App. A uses an I controller everywhere)."""
     o = dict(rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, fac_min=0.2,
-             fac_max=10.0, beta1=0.2, beta2=0.0, h0=0.0, max_steps=100000)
+             fac_max=10.0, beta1=0.2, beta2=0.0, beta3=0.0, h0=0.0, max_steps=100000)
     o.update(kw)
     return o
 
@@ -161,7 +162,7 @@ class _FieldHolder:
 
 def _opts_struct(opts: dict, B: int, keep: list):
     o = _Opts()
-    for k in ("rtol", "atol", "safety", "fac_min", "fac_max", "beta1", "beta2", "h0"):
+    for k in ("rtol", "atol", "safety", "fac_min", "fac_max", "beta1", "beta2", "beta3", "h0"):
         setattr(o, k, float(opts[k]))
     o.max_steps = int(opts["max_steps"])
     for k in ("rtol_b", "atol_b"):

@@ -34,7 +34,9 @@
  *     Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.6, expanded into one
  *     quartic polynomial b_i(theta) per stage and evaluated by Horner's rule;
  *   - error norm: the weighted RMS norm of HNW Sec. II.4, per instance;
- *   - controller: factor = safety * err^-beta1 * err_prev^beta2, clamped;
+ *   - controller: factor = safety * err^-beta1 * err_prev^beta2 *
+ *     err_prev2^-beta3, clamped (App. C: a PID controller looks at the last
+ *     three error estimates; beta3 = beta2 = 0 is the I controller);
  *   - powers err^-beta: a fixed exp/log procedure (orc_pow) so that every
  *     IEEE machine running it reproduces the controller's step sizes;
  *   - starting step: the heuristic of HNW Sec. II.4 ("starting step size").
@@ -136,6 +138,7 @@ typedef struct {
   double safety, fac_min, fac_max, beta1, beta2;
   double h0;                     /* > 0: first step given; 0: starting-step heuristic */
   int max_steps;                 /* attempted steps per instance */
+  double beta3;                  /* derivative term: exponent of err_prev2 (App. C) */
 } orc_opts;
 
 typedef struct {
@@ -495,7 +498,7 @@ static void solve_one(const job *J, int i, double *work, double *act) {
   feval(&c, t, y, k); /* k1 = f(t0, y0) */
   double h = (O->h0 > 0.0) ? O->h0
                            : starting_step(&c, t0, t1, y, k, D, rtol, atol, w1, w2, sc);
-  double err_prev = 1.0;
+  double err_prev = 1.0, err_prev2 = 1.0; /* the last two accepted steps' errors */
   int prev_rejected = 0;
 
   while (st == ST_RUNNING) {
@@ -533,17 +536,19 @@ static void solve_one(const job *J, int i, double *work, double *act) {
         }
         cur++;
       }
-      /* controller: factor = safety * err^-beta1 * err_prev^beta2 */
+      /* controller: factor = safety * err^-beta1 * err_prev^beta2 * err_prev2^-beta3 */
       double fac;
       if (err == 0.0) {
         fac = O->fac_max;
       } else {
         fac = O->safety * orc_pow(err, -O->beta1);
         if (O->beta2 != 0.0) fac = fac * orc_pow(err_prev, O->beta2);
+        if (O->beta3 != 0.0) fac = fac * orc_pow(err_prev2, -O->beta3);
       }
       fac = dmin(dmax(fac, O->fac_min), O->fac_max);
       if (prev_rejected) fac = dmin(fac, 1.0);
       h_next = h * fac;
+      err_prev2 = err_prev;
       err_prev = dmax(err, 1e-4);
       prev_rejected = 0;
       n_acc++;

@@ -220,21 +220,55 @@ def test_controller_power_function_accuracy():
     assert math.isnan(lib.orc_pow(float("nan"), 0.2))
 
 
-@pytest.mark.parametrize("beta1,beta2", [(0.2, 0.0), (0.14, 0.08)])
-def test_controller_steady_state(beta1, beta2):
+@pytest.mark.parametrize("beta1,beta2,beta3", [(0.2, 0.0, 0.0), (0.14, 0.08, 0.0),
+                                               (0.16, 0.1, 0.02)])
+def test_controller_steady_state(beta1, beta2, beta3):
     """For a smooth problem in the asymptotic regime (err ~ C h^p) the
-    controller factor safety*err^-b1*err_prev^b2 drives accepted errors to
-    the fixed point err* = safety^(1/(b1-b2)), whatever p is (App. C: the
-    PI(D) family; App. A: I controller, b2 = 0)."""
+    controller factor safety*err^-b1*err_prev^b2*err_prev2^-b3 drives
+    accepted errors to the fixed point err* = safety^(1/(b1-b2+b3)),
+    whatever p is (App. C: the PID family over the last three error
+    estimates; App. A: I controller, b2 = b3 = 0)."""
     field = {"kind": "linear", "A": np.array([[[1.0]]])}
     r = oracle.solve(field, np.ones((1, 1)), np.zeros(1), np.array([12.0]), None,
-                     dict(rtol=1e-10, atol=0.0, beta1=beta1, beta2=beta2), trace_cap=10000)
+                     dict(rtol=1e-10, atol=0.0, beta1=beta1, beta2=beta2, beta3=beta3),
+                     trace_cap=10000)
     L = r["trace_len"][0]
     acc = r["trace_accepted"][0, :L].astype(bool)
     errs = r["trace_err"][0, :L][acc][:-1]  # drop the clipped last step
-    target = 0.9 ** (1.0 / (beta1 - beta2))
+    target = 0.9 ** (1.0 / (beta1 - beta2 + beta3))
     tail = errs[len(errs) // 2:]
     assert np.abs(tail / target - 1).max() < 0.03, (tail.min(), tail.max(), target)
+
+
+def test_pid_step_sequence_from_its_own_errors():
+    """Every step after an accepted one is h * clamp(0.9 err_n^-b1
+    err_{n-1}^b2 err_{n-2}^-b3) with the errors of the last three accepted
+    steps (floored at 1e-4, 1 before the first), recomputed here with the
+    platform pow from the trace: catches a wrong index or sign in the
+    controller's history."""
+    w = workloads.make(1, B=4)
+    b1, b2, b3 = 0.16, 0.1, 0.02
+    r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], None,
+                     dict(rtol=1e-7, atol=1e-7, beta1=b1, beta2=b2, beta3=b3), trace_cap=5000)
+    checked = 0
+    for i in range(4):
+        L = r["trace_len"][i]
+        h, e, a = r["trace_h"][i, :L], r["trace_err"][i, :L], r["trace_accepted"][i, :L]
+        hist = [1.0, 1.0]  # err_{n-2}, err_{n-1}
+        prev_rej = False
+        for n in range(L - 2):  # the last attempt's successor is clipped or absent
+            if a[n]:
+                fac = 0.9 * math.pow(e[n], -b1) * math.pow(hist[1], b2) * math.pow(hist[0], -b3)
+                fac = min(max(fac, 0.2), 10.0)
+                if prev_rej:
+                    fac = min(fac, 1.0)
+                hist = [hist[1], max(e[n], 1e-4)]
+                clipped = r["trace_t"][i, n + 1] + h[n + 1] == w["t1"][i]
+                if not clipped:
+                    assert abs(h[n + 1] / (h[n] * fac) - 1) < 1e-13, (i, n)
+                    checked += 1
+            prev_rej = not a[n]
+    assert checked > 400
 
 
 def test_controller_clamps_and_no_growth_after_reject():
