@@ -104,8 +104,9 @@ typedef struct {
   double rtol, atol;          /* scalar tolerances */
   const double* rtol_b;       /* optional per-instance tolerances [B] (device), NULL = scalar */
   const double* atol_b;
-  /* controller: factor = safety * err^-beta1 * err_prev^beta2, clamped to
-   * [fac_min, fac_max]; beta2 = 0 is the integral controller of App. A. */
+  /* controller: factor = safety * err^-beta1 * err_prev^beta2 *
+   * err_prev2^-beta3 (beta3 below), clamped to [fac_min, fac_max]; beta2 =
+   * beta3 = 0 is the integral controller of App. A. */
   double safety, fac_min, fac_max, beta1, beta2;
   double h0;                  /* > 0: first step size; 0: starting-step heuristic */
   int max_steps;              /* attempted steps per instance (>= 1) */
@@ -136,6 +137,12 @@ typedef struct {
    * stride 1 with h_acc, and tode_adjoint then reverses the shared mesh
    * per instance as usual. */
   int joint;
+  /* derivative term of the PID controller (App. C: the decision looks at
+   * the last three error estimates): the exponent of err_prev2, the error
+   * of the accepted step before the previous one (1 before there is one).
+   * 0 = the PI / I controller.  A strided tape needs err_prev2 when it is
+   * not 0. */
+  double beta3;
 } tode_options;
 
 /* Checkpoint tape written by tode_solve for tode_adjoint.  Slot j of
@@ -176,6 +183,9 @@ typedef struct {
                        of the accepted step (MLP field: required; other fields:
                        optional -- with stride 1 and h_acc the adjoint then
                        reads them instead of re-evaluating the stages) */
+  void* err_prev2;  /* [B][slots] state dtype: the PID controller's second error
+                       history entry; needed by a re-run tape when beta3 != 0,
+                       may be NULL otherwise */
 } tode_tape;
 
 /* Per-attempt trace (testing and diagnostics): for instance i, attempt n <
@@ -191,7 +201,7 @@ typedef struct {
 } tode_trace;
 
 /* Fills *o with the defaults: rtol = atol = 1e-6, safety 0.9, fac_min 0.2,
- * fac_max 10, beta1 0.2, beta2 0 (integral controller), h0 = 0 (heuristic),
+ * fac_max 10, beta1 0.2, beta2 = beta3 = 0 (integral controller), h0 = 0 (heuristic),
  * max_steps 100000, TODE_F32, TODE_FUSED, tuning fields 0, order 0, joint 0. */
 void tode_default_options(tode_options* o);
 

@@ -61,6 +61,7 @@ class Options(C.Structure):
         ("poll_every", C.c_int),
         ("order", C.c_int),
         ("joint", C.c_int),
+        ("beta3", C.c_double),
     ]
 
 
@@ -77,6 +78,7 @@ class Tape(C.Structure):
         ("flags", _vp),
         ("h_acc", _vp),
         ("y_stage", _vp),
+        ("err_prev2", _vp),
     ]
 
 

@@ -119,7 +119,7 @@ def _prec_of(field, y0: torch.Tensor) -> int:
 
 
 def make_options(*, rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, fac_min=0.2,
-                 fac_max=10.0, beta1=0.2, beta2=0.0, h0=0.0, max_steps=100000,
+                 fac_max=10.0, beta1=0.2, beta2=0.0, beta3=0.0, h0=0.0, max_steps=100000,
                  prec=_abi.TODE_F32, form="fused", group=0, block=0, ctas_per_sm=0,
                  poll_every=0, order=0, joint=False) -> _abi.Options:
     o = _abi.Options()
@@ -136,6 +136,7 @@ def make_options(*, rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, 
         int(poll_every)
     o.order = int(order)
     o.joint = int(bool(joint))
+    o.beta3 = float(beta3)
     return o
 
 
@@ -167,6 +168,7 @@ class TapeBuffers:
     flags: Optional[torch.Tensor]
     h_acc: Optional[torch.Tensor]  # None: the adjoint re-runs each segment's attempts
     y_stage: Optional[torch.Tensor] = None  # [B, slots, 6, D]: Y_2..Y_7
+    err_prev2: Optional[torch.Tensor] = None  # [B, slots]: the PID's second error entry
 
     @staticmethod
     def allocate(B, D, dtype, slots, stride, device, stages: bool = False,
@@ -190,14 +192,15 @@ class TapeBuffers:
                            e((B, slots), keep=full),
                            e((B, slots), torch.int32, keep=full),
                            e((B, slots)),
-                           e((B, slots, 6, D), keep=stages))
+                           e((B, slots, 6, D), keep=stages),
+                           e((B, slots), keep=full))
 
     @staticmethod
     def bytes_per_slot(B, D, itemsize, stages: bool = False, minimal: bool = False):
         if minimal:  # y, k1 or the stage inputs, t, h_acc
             return B * (D * itemsize + (6 * D if stages else D) * itemsize + 8 + itemsize)
         comp = D * itemsize if itemsize == 4 else 0
-        return B * (2 * D * itemsize + comp + 8 + 3 * itemsize + 4 +
+        return B * (2 * D * itemsize + comp + 8 + 4 * itemsize + 4 +
                     (6 * D * itemsize if stages else 0))
 
     def c(self) -> _abi.Tape:
@@ -209,6 +212,7 @@ class TapeBuffers:
         tp.t, tp.h = ptr(self.t), ptr(self.h)
         tp.err_prev, tp.flags = ptr(self.err_prev), ptr(self.flags)
         tp.h_acc, tp.y_stage = ptr(self.h_acc), ptr(self.y_stage)
+        tp.err_prev2 = ptr(self.err_prev2)
         return tp
 
 

@@ -22,7 +22,9 @@ static bool opts_ok(const tode_options* o) {
   if (!o->rtol_b && !o->atol_b && !(o->rtol + o->atol > 0.0)) return false;
   if (!(o->safety > 0.0) || !(o->fac_min > 0.0) || !(o->fac_min <= 1.0) || !(o->fac_max >= 1.0))
     return false;
-  if (!(o->beta1 > 0.0) || !std::isfinite(o->beta1) || !std::isfinite(o->beta2)) return false;
+  if (!(o->beta1 > 0.0) || !std::isfinite(o->beta1) || !std::isfinite(o->beta2) ||
+      !std::isfinite(o->beta3))
+    return false;
   if (!(o->h0 >= 0.0) || !std::isfinite(o->h0)) return false;
   if (o->max_steps < 1) return false;
   if (o->form != TODE_PLAIN && o->form != TODE_FUSED) return false;
@@ -59,8 +61,8 @@ static tode_err field_ok(const tode_field_desc* f, const tode_options* o) {
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 static bool tape_ok(const tode_tape* tp, const tode_options* o, const tode_field_desc* f) {
-  const void* arrays[] = {tp->y, tp->y_lo, tp->k1, tp->t, tp->h, tp->err_prev, tp->flags,
-                          tp->h_acc, tp->y_stage};
+  const void* arrays[] = {tp->y,     tp->y_lo,  tp->k1,      tp->t,        tp->h,
+                          tp->err_prev, tp->flags, tp->h_acc, tp->y_stage, tp->err_prev2};
   for (const void* p : arrays)
     if (!aligned16(p)) return false;  // NULL passes
   if (tp->slots < 1 || tp->stride < 1 || !tp->y || !tp->t) return false;
@@ -69,7 +71,8 @@ static bool tape_ok(const tode_tape* tp, const tode_options* o, const tode_field
   // which need the FSAL stage only when the stage inputs are not recorded
   if (tp->stride == 1 && tp->h_acc) return tp->k1 || tp->y_stage;
   // otherwise segments are re-run from their slots: the whole solver state
-  return tp->k1 && tp->h && tp->err_prev && tp->flags && (o->prec == TODE_F64 || tp->y_lo);
+  return tp->k1 && tp->h && tp->err_prev && tp->flags && (o->prec == TODE_F64 || tp->y_lo) &&
+         (o->beta3 == 0.0 || tp->err_prev2);
 }
 
 static int sm_count_or_zero() {

@@ -239,7 +239,7 @@ template <typename T, int R> struct Inst {
   T h_last;      // step size the last attempt used (clipped at t1)
   T rem;         // FP32 state: t1 - t rounded down to float (last-step test)
   T hmin;        // FP32 state: step-size underflow threshold 1e-14 max(|t0|,|t1|)
-  T err_prev;
+  T err_prev, err_prev2;  // error estimates of the last two accepted steps
   T rtol, atol;
   int n_acc, n_rej, cursor, status, flags;
   // the evaluation times at the cursor and after it (+inf past the last),
@@ -248,11 +248,11 @@ template <typename T, int R> struct Inst {
 };
 
 struct SolveOpts {
-  double safety, fac_min, fac_max, beta1, beta2, h0;
+  double safety, fac_min, fac_max, beta1, beta2, beta3, h0;
   int max_steps;
   // the same controller constants rounded to FP32 once on the host (an FP32
   // kernel then does no double-to-float conversion per attempt)
-  float safety_f, fac_min_f, fac_max_f, beta1_f, beta2_f;
+  float safety_f, fac_min_f, fac_max_f, beta1_f, beta2_f, beta3_f;
 };
 inline void opts_round_f32(SolveOpts& s) {
   s.safety_f = (float)s.safety;
@@ -260,6 +260,7 @@ inline void opts_round_f32(SolveOpts& s) {
   s.fac_max_f = (float)s.fac_max;
   s.beta1_f = (float)s.beta1;
   s.beta2_f = (float)s.beta2;
+  s.beta3_f = (float)s.beta3;
 }
 // controller constant in the state type
 template <typename T> __device__ __forceinline__ T opt_v(double d, float f) {
@@ -369,6 +370,7 @@ template <typename T> struct TapeDev {
   double* t;
   T* h;
   T* err_prev;
+  T* err_prev2;
   int32_t* flags;
   T* h_acc;   // optional: size of the accepted step that starts at the slot
   T* ystage;  // optional: its stage inputs Y_2..Y_7, [B][slots][6][D]
@@ -400,6 +402,7 @@ __device__ __forceinline__ void tape_store(const TapeDev<T>& tp, int i, const In
     tp.t[o] = s.t;
     if (tp.h) tp.h[o] = s.h;
     if (tp.err_prev) tp.err_prev[o] = s.err_prev;
+    if (tp.err_prev2) tp.err_prev2[o] = s.err_prev2;
     if (tp.flags) tp.flags[o] = s.flags;
   }
 }
@@ -441,6 +444,7 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
   s.cursor = 0;
   s.flags = 0;
   s.err_prev = T(1);
+  s.err_prev2 = T(1);
   s.h = T(0);
   s.h_last = T(0);
   s.rem = T(0);
@@ -703,10 +707,12 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     } else {
       fac = opt_v<T>(o.safety, o.safety_f) * ctl_pow(err, -opt_v<T>(o.beta1, o.beta1_f));
       if (o.beta2 != 0.0) fac = fac * ctl_pow(s.err_prev, opt_v<T>(o.beta2, o.beta2_f));
+      if (o.beta3 != 0.0) fac = fac * ctl_pow(s.err_prev2, -opt_v<T>(o.beta3, o.beta3_f));
     }
     fac = tmin(tmax(fac, opt_v<T>(o.fac_min, o.fac_min_f)), opt_v<T>(o.fac_max, o.fac_max_f));
     if (s.flags & FL_PREV_REJ) fac = tmin(fac, T(1));
     h_next = h * fac;
+    s.err_prev2 = s.err_prev;
     s.err_prev = tmax(err, T(1e-4));
     s.flags &= ~FL_PREV_REJ;
     s.n_acc++;

@@ -98,7 +98,7 @@ inline size_t simt_workspace_bytes(int B, int D, size_t ts, int form, int joint)
   if (form == TODE_PLAIN) {
     s += 3 * align256((size_t)B * D * ts);  // y, y_lo, k1
     s += align256((size_t)B * 8);           // t
-    s += 2 * align256((size_t)B * ts);      // h, err_prev
+    s += 3 * align256((size_t)B * ts);      // h, err_prev, err_prev2
     s += 2 * align256((size_t)B * 4);       // cursor, flags
   }
   return s;

@@ -71,6 +71,7 @@ struct MlpArgs {
   double* wt;
   float* wh;
   float* wep;
+  float* wep2;
   int32_t* wcur;
   int32_t* wfl;
   int32_t* active;
@@ -292,7 +293,7 @@ __device__ __forceinline__ float dp_a(int s, int j) {
 struct MlpRow {
   int inst, phase, cursor, status, flags, n_acc, n_rej;
   double t, t0, t1;
-  float h, h0h, err_prev, rtol, atol, rem, hmin;
+  float h, h0h, err_prev, err_prev2, rtol, atol, rem, hmin;
   bool last;
 };
 
@@ -436,6 +437,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     s.cursor = 0;
     s.flags = 0;
     s.err_prev = 1.0f;
+    s.err_prev2 = 1.0f;
     s.h = s.h0h = 0.0f;
     s.last = false;
     s.status = ST_RUNNING;
@@ -504,6 +506,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       a.wt[i] = s.t;
       a.wh[i] = s.h;
       a.wep[i] = s.err_prev;
+      a.wep2[i] = s.err_prev2;
       a.wcur[i] = s.cursor;
       a.wfl[i] = s.flags;
       a.n_acc[i] = s.n_acc;
@@ -526,6 +529,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     s.cursor = a.wcur[i];
     s.flags = a.wfl[i];
     s.err_prev = a.wep[i];
+    s.err_prev2 = a.wep2[i];
     s.h = a.wh[i];
     s.h0h = 0.0f;
     s.last = false;
@@ -855,6 +859,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       if (!(h > 0.0f && isfinite(h))) h = (float)(s.t1 - s.t0);
       s.h = h;
       s.err_prev = 1.0f;
+      s.err_prev2 = 1.0f;
       s.phase = PH_STAGE;
       if (MODE == MLP_PLAIN_INIT) park();
     } else if (s.phase >= PH_STAGE && stage < 7) {
@@ -935,10 +940,12 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         } else {
           fac = a.o.safety_f * ctl_pow(err, -a.o.beta1_f);
           if (a.o.beta2 != 0.0) fac = fac * ctl_pow(s.err_prev, a.o.beta2_f);
+          if (a.o.beta3 != 0.0) fac = fac * ctl_pow(s.err_prev2, -a.o.beta3_f);
         }
         fac = tmin(tmax(fac, a.o.fac_min_f), a.o.fac_max_f);
         if (s.flags & FL_PREV_REJ) fac = tmin(fac, 1.0f);
         h_next = h * fac;
+        s.err_prev2 = s.err_prev;
         s.err_prev = tmax(err, 1e-4f);
         s.flags &= ~FL_PREV_REJ;
         s.n_acc++;
@@ -2267,7 +2274,7 @@ size_t mlp_workspace_bytes(const tode_field_desc* f, const tode_options* o) {
   size_t b = align256(256) + img;
   if (o->form == TODE_PLAIN) {  // parked solver state (must match launch_mlp)
     const size_t B = (size_t)f->B, D = (size_t)f->D;
-    b += 3 * align256(B * D * 4) + align256(B * 8) + 4 * align256(B * 4);
+    b += 3 * align256(B * D * 4) + align256(B * 8) + 5 * align256(B * 4);
   }
   return b;
 }
@@ -2295,6 +2302,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   a.o.fac_max = r.o->fac_max;
   a.o.beta1 = r.o->beta1;
   a.o.beta2 = r.o->beta2;
+  a.o.beta3 = r.o->beta3;
   a.o.h0 = r.o->h0;
   a.o.max_steps = r.o->max_steps;
   opts_round_f32(a.o);
@@ -2340,6 +2348,8 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
     a.wh = (float*)p;
     p += align256(B * 4);
     a.wep = (float*)p;
+    p += align256(B * 4);
+    a.wep2 = (float*)p;
     p += align256(B * 4);
     a.wcur = (int32_t*)p;
     p += align256(B * 4);

@@ -32,6 +32,7 @@ template <typename T> struct SolveArgs {
   double* wt;
   T* wh;
   T* wep;
+  T* wep2;
   int32_t* wcur;
   int32_t* wfl;
   int32_t* active;
@@ -78,6 +79,7 @@ __device__ __forceinline__ void plain_store(const SolveArgs<T>& a, int j, int i,
     a.wt[j] = s.t;
     a.wh[j] = s.h;
     a.wep[j] = s.err_prev;
+    a.wep2[j] = s.err_prev2;
     a.wcur[j] = s.cursor;
     a.wfl[j] = s.flags;
     a.n_acc[i] = s.n_acc;
@@ -102,6 +104,7 @@ __device__ __forceinline__ void plain_load(const SolveArgs<T>& a, int j, int i,
   s.t1 = a.t1[i];
   s.h = a.wh[j];
   s.err_prev = a.wep[j];
+  s.err_prev2 = a.wep2[j];
   s.cursor = a.wcur[j];
   s.flags = a.wfl[j];
   const InstOut<T> out = inst_out(a, i);
@@ -223,6 +226,7 @@ template <typename T> TapeDev<T> make_tape(const tode_tape* tp, int B, int D) {
   d.t = tp->t;
   d.h = (T*)tp->h;
   d.err_prev = (T*)tp->err_prev;
+  d.err_prev2 = (T*)tp->err_prev2;
   d.flags = tp->flags;
   d.h_acc = (T*)tp->h_acc;
   d.ystage = (T*)tp->y_stage;
@@ -236,6 +240,7 @@ inline SolveOpts make_opts(const tode_options* o) {
   s.fac_max = o->fac_max;
   s.beta1 = o->beta1;
   s.beta2 = o->beta2;
+  s.beta3 = o->beta3;
   s.h0 = o->h0;
   s.max_steps = o->max_steps;
   opts_round_f32(s);
@@ -296,6 +301,8 @@ template <typename T> SolveArgs<T> make_solve_args(const SolveReq& r) {
     a.wh = (T*)p;
     p += align256((size_t)r.B * ts);
     a.wep = (T*)p;
+    p += align256((size_t)r.B * ts);
+    a.wep2 = (T*)p;
     p += align256((size_t)r.B * ts);
     a.wcur = (int32_t*)p;
     p += align256((size_t)r.B * 4);

@@ -486,6 +486,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
       s.t = a.tape.t[o];
       s.h = a.tape.h[o];
       s.err_prev = a.tape.err_prev[o];
+      s.err_prev2 = a.tape.err_prev2 ? a.tape.err_prev2[o] : T(1);  // present when beta3 != 0
       s.flags = a.tape.flags[o];
       s.t0 = a.t0[i];
       s.t1 = t1;

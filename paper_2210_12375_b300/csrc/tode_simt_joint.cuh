@@ -37,7 +37,7 @@ template <typename T> struct JointCtl {
   double dec_t;              // start of the decided attempt
   T h;                       // step proposed for the next attempt
   T h_use;                   // the next attempt's step, clipped at t1
-  T err_prev, rem, hmin;
+  T err_prev, err_prev2, rem, hmin;
   T d1, h0;                  // starting-step heuristic between its two launches
   T dec_h, dec_err;
   int use_last, flags, n_acc, n_rej, status, phase, cursor;
@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(256) k_joint_init(JointArgs<T> ja) {
   c.t1 = a.t1[0];
   c.t = c.t0;
   c.err_prev = T(1);
+  c.err_prev2 = T(1);
   c.phase = JP_RUN;
   c.dec = JD_NONE;
   while (c.cursor < a.K && tkey(a.te[c.cursor]) == tkey(c.t0)) c.cursor++;
@@ -333,6 +334,7 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
       const size_t o = (size_t)i * a.tape.slots + c.n_acc;
       if (a.tape.h) a.tape.h[o] = c.h;
       if (a.tape.err_prev) a.tape.err_prev[o] = c.err_prev;
+      if (a.tape.err_prev2) a.tape.err_prev2[o] = c.err_prev2;
       if (a.tape.flags) a.tape.flags[o] = c.flags;
     }
     Inst<T, R> s;
@@ -349,6 +351,7 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
     s.t = c.t;
     s.h = c.h;
     s.err_prev = c.err_prev;
+    s.err_prev2 = c.err_prev2;
     s.flags = c.flags;
     s.rtol = T(a.rtol);
     s.atol = T(a.atol);
@@ -478,11 +481,14 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
     } else {
       fac = opt_v<T>(a.o.safety, a.o.safety_f) * ctl_pow(err, -opt_v<T>(a.o.beta1, a.o.beta1_f));
       if (a.o.beta2 != 0.0) fac = fac * ctl_pow(c.err_prev, opt_v<T>(a.o.beta2, a.o.beta2_f));
+      if (a.o.beta3 != 0.0)
+        fac = fac * ctl_pow(c.err_prev2, -opt_v<T>(a.o.beta3, a.o.beta3_f));
     }
     fac = tmin(tmax(fac, opt_v<T>(a.o.fac_min, a.o.fac_min_f)),
                opt_v<T>(a.o.fac_max, a.o.fac_max_f));
     if (c.flags & FL_PREV_REJ) fac = tmin(fac, T(1));
     h_next = h * fac;
+    n.err_prev2 = c.err_prev;
     n.err_prev = tmax(err, T(1e-4));
     n.flags = c.flags & ~FL_PREV_REJ;
     n.n_acc = c.n_acc + 1;

@@ -271,6 +271,39 @@ def test_pid_step_sequence_from_its_own_errors():
     assert checked > 400
 
 
+def _vdp_cycle(mu):
+    """A rough limit-cycle period of Van der Pol's oscillator (relaxation
+    form for large mu, 2 pi for small)."""
+    if mu <= 1.0:
+        return 2 * math.pi
+    return (3 - 2 * math.log(2)) * mu + 2 * math.pi / (1 + mu) + 4.676 * mu ** (-1 / 3)
+
+
+PID_BETAS = ((0.3 + 0.3 + 0.1) / 5, (0.3 + 2 * 0.1) / 5, 0.1 / 5)  # gains (p, i, d) / order 5
+
+
+@pytest.mark.parametrize("mu,pid_better", [(5.0, False), (10.0, False), (25.0, True),
+                                           (50.0, True)])
+def test_pid_trade_off_over_one_vdp_cycle(mu, pid_better):
+    """App. C: over one cycle of Van der Pol, PID control costs steps while
+    the step size varies little (mu < 15) and saves steps once it varies by
+    orders of magnitude (mu > 25).  Gains (p, i, d) = (0.3, 0.3, 0.1) are a
+    choice of this test (the paper's come from external documentation)."""
+    f = dict(kind="vdp", mu=np.array([mu]))
+    T = _vdp_cycle(mu)
+
+    def attempts(b1, b2, b3):
+        r = oracle.solve(f, np.array([[2.0, 0.0]]), [0.0], [T], None,
+                         dict(rtol=1e-6, atol=1e-6, beta1=b1, beta2=b2, beta3=b3))
+        assert r["status"][0] == 0
+        return int(r["n_acc"][0] + r["n_rej"][0])
+    i_ctl, pid = attempts(0.2, 0.0, 0.0), attempts(*PID_BETAS)
+    if pid_better:
+        assert pid < 0.97 * i_ctl, (pid, i_ctl)
+    else:
+        assert pid > i_ctl, (pid, i_ctl)
+
+
 def test_controller_clamps_and_no_growth_after_reject():
     w = workloads.make(1, B=8)
     # tiny first step: err ~ 0 -> factor clamped to fac_max exactly
