@@ -131,7 +131,7 @@ TRAFFIC = {
     ("vdp_mix_b262144", "k_fused<VdpField<float>>"): 8 * 91.90e6,
     ("vdp_mix_b262144", "k_adjoint_steps<VdpAdj<float>>"): 8 * 124.08e6,
     ("mlp_d32_h128", "k_mlp_fused"): 12.51e6,
-    ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 70.45e6,
+    ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 69.93e6,
 }
 
 

@@ -316,10 +316,31 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
   T sq = T(0);
   bool nonfin = false;
   // grid-stride over the instances (lane groups stay within one warp);
-  // each thread accumulates its instances in index order
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j / G < a.B;
-       j += (long long)gridDim.x * blockDim.x) {
+  // each thread accumulates its instances in index order.  The next
+  // instance's state and field are loaded one iteration ahead, so that
+  // their latency overlaps the current instance's attempt.
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  T ny[R], nylo[R], nk1[R];
+  Field nF;
+  auto fetch = [&](int i) {
+    jld<T, R, G>(ja.y[c.cur], a.B, i, ny);
+    if constexpr (Comp<T>::on) jld<T, R, G>(ja.ylo[c.cur], a.B, i, nylo);
+    jld<T, R, G>(ja.k1[c.cur], a.B, i, nk1);
+    nF.load(a.fparam, i);
+  };
+  if (j / G < a.B) fetch((int)(j / G));
+  for (; j / G < a.B; j += stride) {
     const int i = (int)(j / G);
+    Inst<T, R> s;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      s.y[r] = ny[r];
+      s.ylo[r] = Comp<T>::on ? nylo[r] : T(0);
+      s.k1[r] = nk1[r];
+    }
+    const Field F = nF;
+    if ((j + stride) / G < a.B) fetch((int)((j + stride) / G));
     const InstOut<T> out = inst_out(a, i);
     // ---- commit the decided attempt: its trace entry, and the controller
     // state of the tape slot it opened
@@ -337,15 +358,6 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
       if (a.tape.err_prev2) a.tape.err_prev2[o] = c.err_prev2;
       if (a.tape.flags) a.tape.flags[o] = c.flags;
     }
-    Inst<T, R> s;
-    jld<T, R, G>(ja.y[c.cur], a.B, i, s.y);
-    if constexpr (Comp<T>::on) {
-      jld<T, R, G>(ja.ylo[c.cur], a.B, i, s.ylo);
-    } else {
-#pragma unroll
-      for (int r = 0; r < R; ++r) s.ylo[r] = T(0);
-    }
-    jld<T, R, G>(ja.k1[c.cur], a.B, i, s.k1);
     s.t0 = c.t0;
     s.t1 = c.t1;
     s.t = c.t;
@@ -371,8 +383,6 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
                              a.trace);
     } else {
       // ---- attempt n with the batch's step
-      Field F;
-      F.load(a.fparam, i);
       const T h = c.h_use;
       const double hd = (double)h;
       T ys[6][R], k3[R], k4[R], k5[R], k6[R], k7[R], y1[R], inc[R], ev[R], sc[R], q2[R];
