@@ -6,7 +6,8 @@ backpropagation through the solver, on the forward's frozen mesh).
 The tape is sized from the forward's accepted-step counts under an HBM
 budget: one slot per accepted step when it fits, otherwise one slot every m
 steps with the segments recomputed in the backward pass (gradients bitwise
-equal to m = 1).  The MLP field keeps every step (m = 1).
+equal to m = 1).  The MLP field and joint solves (Sec. 4.1, ``joint=True``:
+one shared mesh, reversed per instance) keep every step (m = 1).
 """
 from __future__ import annotations
 
@@ -42,8 +43,9 @@ def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint):
         full_slot = api.TapeBuffers.bytes_per_slot(B, D, y0.element_size(), stages=mlp)
         if N <= max_slots:
             stride = 1
-        elif mlp:
-            raise RuntimeError(f"the MLP adjoint keeps every accepted step: {N} slots of "
+        elif mlp or opt.get("joint"):
+            what = "the MLP adjoint" if mlp else "the adjoint of a joint solve"
+            raise RuntimeError(f"{what} keeps every accepted step: {N} slots of "
                                f"{per_slot} bytes exceed the tape budget of {budget} bytes")
         else:  # strided segments are re-run: the tape keeps the whole state
             stride = math.ceil(N / max(1, budget // max(full_slot, 1)))

@@ -96,3 +96,28 @@ def test_autograd_mlp_over_budget_raises():
     field = device_field(w, torch.float32)
     with pytest.raises(RuntimeError):
         _loss_and_grads(w, torch.float32, field, hbm_budget_bytes=1, slots_hint=1)
+
+
+def test_autograd_joint_solve_vs_oracle_adjoint_on_the_shared_mesh():
+    """Sec. 4.1's joint solve under autograd: the gradient is each
+    instance's discrete adjoint on the one shared mesh; a budget too small
+    for one slot per step is refused (a joint mesh is never re-run)."""
+    w = make(1, B=40)
+    T = 6.0
+    te_row = np.linspace(0.0, T, 7)
+    w = dict(w, t0=np.zeros(40), t1=np.full(40, T), t_eval=np.tile(te_row, (40, 1)))
+    field = device_field(w, torch.float64)
+    ye, yf, n_acc, (gy0, gmu) = _loss_and_grads(w, torch.float64, field, joint=True)
+    probe = gpu_solve(w, torch.float64, "plain", joint=True, trace_cap=4000)
+    assert np.array_equal(probe["n_acc"], n_acc.cpu().numpy())
+    assert (probe["n_acc"] == probe["n_acc"][0]).all()
+    mt, mh, mn = mesh_from_trace(probe)
+    D = w["y0"].shape[1]
+    gye = 2.0 * ye.cpu().numpy()
+    gyf = np.tile(np.linspace(-1.0, 1.0, D), (w["B"], 1))
+    ref = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"], gye, gyf)
+    assert _rel(gy0, ref["gy0"]) <= 1e-10
+    assert _rel(gmu, ref["gmu"]) <= 1e-10
+    with pytest.raises(RuntimeError):
+        _loss_and_grads(w, torch.float64, field, joint=True, hbm_budget_bytes=40 * 40,
+                        slots_hint=1)
