@@ -58,10 +58,13 @@ def test_joint_f64_vdp_matches_oracle():
     assert _rel_close(g["y_final"], o["y_final"], 1e-10).all()
 
 
-@pytest.mark.parametrize("block", [32, 256])
-def test_joint_f32_linear_matches_oracle(block):
+@pytest.mark.parametrize("launch", [dict(block=32), dict(block=256),
+                                    dict(block=32, ctas_per_sm=1, group=16)])
+def test_joint_f32_linear_matches_oracle(launch):
+    # the last launch shape: 16-lane groups, 148 one-warp CTAs, so some
+    # threads take a second instance in the grid-stride loop
     w = _joint(2, 300, 1.5, 32)
-    g = gpu_solve(w, torch.float32, "plain", joint=True, block=block)
+    g = gpu_solve(w, torch.float32, "plain", joint=True, **launch)
     o = _oracle_joint(w)
     assert (g["status"] == 0).all() and o["status"] == 0
     assert (g["n_acc"] == g["n_acc"][0]).all()
