@@ -20,6 +20,9 @@
  *     last error estimates (Soderlind 2002/2003); the PI subset is used here.
  *   - App. A, FEN benchmark: gradients by backpropagation through the solver
  *     (discretize-then-optimize) -> the discrete adjoint of the fixed-mesh map.
+ *   - integration backward in time (t1 < t0): the same method with negative
+ *     steps; the controller acts on |h|, evaluation points run from t0 down
+ *     to t1 (a reading: the paper only uses forward integration).
  *   - Sec. 4.1 "Batching ODEs": joint ("stacked") solving, the comparison
  *     semantics of the batching experiment -- n problems of size p handed to
  *     this same single-problem solver as one problem of size np (a stacked
@@ -344,21 +347,24 @@ double orc_pow(double x, double y) {
 
 /* Starting step size, HNW Sec. II.4 (PARITY UNPINNED, see header).  f0 =
  * f(t0, y0) is supplied and reused as the first step's k1 (FSAL). */
-static double starting_step(fctx *c, double t0, double t1, const double *y0, const double *f0,
-                            int D, double rtol, double atol, double *w1, double *w2, double *sc) {
+/* Magnitude of the first step; the trial step goes in the direction dir of
+ * integration (+1 forward, -1 from t0 down to t1). */
+static double starting_step(fctx *c, double t0, double t1, double dir, const double *y0,
+                            const double *f0, int D, double rtol, double atol, double *w1,
+                            double *w2, double *sc) {
   for (int j = 0; j < D; ++j) sc[j] = atol + rtol * fabs(y0[j]);
   double d0 = rms(y0, sc, D);
   double d1 = rms(f0, sc, D);
   double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * (d0 / d1);
-  for (int j = 0; j < D; ++j) w1[j] = y0[j] + h0 * f0[j];
-  feval(c, t0 + h0, w1, w2);
+  for (int j = 0; j < D; ++j) w1[j] = y0[j] + (dir * h0) * f0[j];
+  feval(c, t0 + dir * h0, w1, w2);
   for (int j = 0; j < D; ++j) w2[j] = w2[j] - f0[j];
   double d2 = rms(w2, sc, D) / h0;
   double m = (d1 > d2) ? d1 : d2;
   double h1 = (m <= 1e-15) ? dmax(1e-6, h0 * 1e-3) : orc_pow(0.01 / m, 1.0 / 5.0);
   double h = dmin(100.0 * h0, h1);
-  h = dmin(h, t1 - t0);
-  if (!(h > 0.0 && isfinite(h))) h = t1 - t0;
+  h = dmin(h, dir * (t1 - t0));
+  if (!(h > 0.0 && isfinite(h))) h = dir * (t1 - t0);
   return h;
 }
 
@@ -420,11 +426,14 @@ void orc_dense_weights(double theta, double *bt) {
 /* ------------------------------------------------------------------------ */
 /* Input checks (Sec. 3: per-instance bounds and evaluation points).         */
 /* ------------------------------------------------------------------------ */
+/* Finite times; evaluation points between t0 and t1 and ordered in the
+ * direction of integration (t1 < t0 integrates backward in time). */
 static int instance_inputs_valid(double t0, double t1, const double *te, int K) {
-  if (!isfinite(t0) || !isfinite(t1) || t1 < t0) return 0;
+  if (!isfinite(t0) || !isfinite(t1)) return 0;
+  const double dir = (t1 < t0) ? -1.0 : 1.0;
   for (int q = 0; q < K; ++q) {
-    if (!isfinite(te[q]) || te[q] < t0 || te[q] > t1) return 0;
-    if (q > 0 && te[q] < te[q - 1]) return 0;
+    if (!isfinite(te[q]) || dir * te[q] < dir * t0 || dir * te[q] > dir * t1) return 0;
+    if (q > 0 && dir * te[q] < dir * te[q - 1]) return 0;
   }
   return 1;
 }
@@ -494,22 +503,26 @@ static void solve_one(const job *J, int i, double *work, double *act) {
     return;
   }
 
+  /* backward in time when t1 < t0: the same method with negative steps
+   * hs = dir * h; h, the controller's quantity, stays positive */
+  const double dir = (t1 < t0) ? -1.0 : 1.0;
   double t = t0;
   feval(&c, t, y, k); /* k1 = f(t0, y0) */
   double h = (O->h0 > 0.0) ? O->h0
-                           : starting_step(&c, t0, t1, y, k, D, rtol, atol, w1, w2, sc);
+                           : starting_step(&c, t0, t1, dir, y, k, D, rtol, atol, w1, w2, sc);
   double err_prev = 1.0, err_prev2 = 1.0; /* the last two accepted steps' errors */
   int prev_rejected = 0;
 
   while (st == ST_RUNNING) {
     int last = 0;
-    if (t + h >= t1) {
-      h = t1 - t;
+    if (dir * (t + dir * h) >= dir * t1) {
+      h = dir * (t1 - t);
       last = 1;
     }
-    dp_stages(&c, t, h, y, D, k, Y);
+    const double hs = dir * h;
+    dp_stages(&c, t, hs, y, D, k, Y);
     for (int j = 0; j < D; ++j) y1[j] = Y[6 * D + j]; /* SSAL: y1 is the last stage input */
-    double err = dp_error(h, y, y1, k, D, rtol, atol, e, sc);
+    double err = dp_error(hs, y, y1, k, D, rtol, atol, e, sc);
     int finite = isfinite(err);
     for (int j = 0; j < D; ++j) finite = finite && isfinite(y1[j]);
     int accept = finite && err <= 1.0;
@@ -517,7 +530,7 @@ static void solve_one(const job *J, int i, double *work, double *act) {
     if (J->trace && tr < J->trace->cap) {
       size_t o = (size_t)i * J->trace->cap + tr;
       J->trace->t[o] = t;
-      J->trace->h[o] = h;
+      J->trace->h[o] = hs;
       J->trace->err[o] = err;
       J->trace->accepted[o] = accept;
       tr++;
@@ -525,14 +538,14 @@ static void solve_one(const job *J, int i, double *work, double *act) {
 
     double h_next;
     if (accept) {
-      double t_next = last ? t1 : t + h;
+      double t_next = last ? t1 : t + hs;
       /* dense output for every evaluation point in (t, t_next] */
-      while (cur < K && te[cur] <= t_next) {
+      while (cur < K && dir * te[cur] <= dir * t_next) {
         double *o = ye + (size_t)cur * D;
         if (te[cur] == t_next) {
           for (int j = 0; j < D; ++j) o[j] = y1[j];
         } else {
-          dp_dense((te[cur] - t) / h, h, y, k, D, o);
+          dp_dense((te[cur] - t) / hs, hs, y, k, D, o);
         }
         cur++;
       }
@@ -568,7 +581,7 @@ static void solve_one(const job *J, int i, double *work, double *act) {
     h = h_next;
     if (st == ST_RUNNING) {
       double scale = dmax(fabs(t), fabs(t1));
-      if (t + h == t || h < 1e-14 * scale || !(h > 0.0))
+      if (t + dir * h == t || h < 1e-14 * scale || !(h > 0.0))
         st = finite ? ST_DT_UNDERFLOW : ST_NONFINITE;
       else if (n_acc + n_rej >= O->max_steps)
         st = ST_MAX_STEPS;
@@ -596,6 +609,7 @@ static void replay_one(const job *J, int i, double *work, double *act, double *y
   const orc_field *F = J->F;
   const int D = F->D, K = J->K, N = J->mesh_n[i];
   const double t0 = J->t0[i];
+  const double dir = (J->t1[i] < t0) ? -1.0 : 1.0; /* mesh steps carry this sign */
   const double *te = J->t_eval + (size_t)i * K;
   double *ye = J->y_eval + (size_t)i * K * D;
   double *y = work, *k = y + D, *Y = k + NS * D;
@@ -616,7 +630,7 @@ static void replay_one(const job *J, int i, double *work, double *act, double *y
     feval(&c, t, y, k);
     dp_stages(&c, t, h, y, D, k, Y);
     const double *y1 = Y + 6 * D;
-    while (cur < K && te[cur] <= t_next) {
+    while (cur < K && dir * te[cur] <= dir * t_next) {
       double *o = ye + (size_t)cur * D;
       if (te[cur] == t_next) {
         for (int j = 0; j < D; ++j) o[j] = y1[j];
@@ -710,6 +724,7 @@ static void adjoint_one(const job *J, int i, double *work, double *act, double *
   const orc_field *F = J->F;
   const int D = F->D, K = J->K, N = J->mesh_n[i];
   const double t0 = J->t0[i];
+  const double dir = (J->t1[i] < t0) ? -1.0 : 1.0; /* mesh steps carry this sign */
   const double *te = J->t_eval + (size_t)i * K;
   const double *gye = J->gy_eval ? J->gy_eval + (size_t)i * K * D : NULL;
   double *ys = (double *)malloc(sizeof(double) * (size_t)(N + 1) * D);
@@ -739,7 +754,7 @@ static void adjoint_one(const job *J, int i, double *work, double *act, double *
     /* cotangents of the stage values */
     for (int s = 0; s < NS; ++s)
       for (int j = 0; j < D; ++j) kb[s * D + j] = h * DP_B[s] * yb[j];
-    while (cur >= 0 && te[cur] > t) {
+    while (cur >= 0 && dir * te[cur] > dir * t) {
       if (gye) {
         const double *gq = gye + (size_t)cur * D;
         if (te[cur] == t_next) {

@@ -513,3 +513,50 @@ def test_adjoint_linear_closed_form_jacobian():
                                  gyf)
             # row `col` of M: d y_col(T) / d y0
             assert np.abs(adj["gy0"][i] - M[col]).max() < 1e-8
+
+
+def test_backward_in_time_is_forward_with_the_negated_field():
+    """Integration from t0 down to t1 < t0 (the method with negative steps)
+    equals, bit for bit, forward integration of the negated field in s = -t:
+    y'(t) = A y backward is z'(s) = -A z forward (IEEE rounding is symmetric
+    under negation, so every step, point and decision coincides)."""
+    rng = np.random.default_rng(7)
+    B, D = 6, 4
+    A = rng.standard_normal((B, D, D)) * 0.8
+    y0 = rng.standard_normal((B, D))
+    t0, t1 = np.full(B, 2.0), rng.uniform(-3.0, 0.5, B)
+    te = np.stack([np.linspace(2.0, t, 9) for t in t1])
+    back = oracle.solve({"kind": "linear", "A": A}, y0, t0, t1, te, dict(rtol=1e-7, atol=1e-7),
+                        trace_cap=2000)
+    fwd = oracle.solve({"kind": "linear", "A": -A}, y0, -t0, -t1, -te,
+                       dict(rtol=1e-7, atol=1e-7), trace_cap=2000)
+    assert (back["status"] == 0).all()
+    for k in ("y_eval", "y_final", "n_acc", "n_rej", "n_feval", "trace_len", "trace_accepted",
+              "trace_err"):
+        assert np.array_equal(back[k], fwd[k]), k
+    assert np.array_equal(back["trace_t"], -fwd["trace_t"])
+    assert np.array_equal(back["trace_h"], -fwd["trace_h"])
+    L = back["trace_len"][0]
+    assert (back["trace_h"][0, :L] < 0).all()
+
+
+def test_backward_in_time_closed_form_and_round_trip():
+    """Linear: y(t) = Q exp(-Lambda t) Q^T y0 for t < t0 = 0 within the
+    tolerance's band; Van der Pol: forward to t1 and back to t0 returns y0
+    to the accuracy of the two solves."""
+    w = workloads.make(2, B=16)
+    Q, lam = w["field"]["Q"], w["field"]["lam"]
+    t1 = -np.full(16, 0.4)
+    te = np.stack([np.linspace(0.0, -0.4, 5)] * 16)
+    r = oracle.solve(w["field"], w["y0"], np.zeros(16), t1, te, dict(rtol=1e-10, atol=1e-10))
+    c = np.einsum("bji,bj->bi", Q, w["y0"])
+    exact = np.einsum("bij,bkj->bki", Q, np.exp(-lam[:, None, :] * te[:, :, None]) * c[:, None, :])
+    assert (r["status"] == 0).all()
+    assert np.abs(r["y_eval"] - exact).max() <= 1e-7 * max(1.0, np.abs(exact).max())
+    # (Van der Pol's limit cycle repels backward in time: a short horizon)
+    v = workloads.make(1, B=8)
+    v1 = np.full(8, 1.5)
+    f = oracle.solve(v["field"], v["y0"], v["t0"], v1, None, dict(rtol=1e-11, atol=1e-11))
+    b = oracle.solve(v["field"], f["y_final"], v1, v["t0"], None, dict(rtol=1e-11, atol=1e-11))
+    assert (b["status"] == 0).all() and (b["n_acc"] > 10).all()
+    assert np.abs(b["y_final"] - v["y0"]).max() < 1e-6
