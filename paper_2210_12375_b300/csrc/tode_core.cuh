@@ -64,7 +64,25 @@ struct DP5 {
 
 enum : int { ST_SUCCESS = 0, ST_MAX_STEPS = 1, ST_DT_UNDERFLOW = 2, ST_NONFINITE = 3,
              ST_INVALID = 4, ST_RUNNING = -1 };
-enum : int { FL_PREV_REJ = 1 };
+enum : int { FL_PREV_REJ = 1, FL_REVERSE = 2 };
+
+// Integration backward in time (t1 < t0) runs in tau = -t: every time the
+// solver holds (t, t0, t1, the evaluation points, the tape's t) is -t and
+// every step size stays positive, while the fields return -f (and their
+// transposed products take -v).  IEEE rounding is symmetric under negation,
+// so this is bit for bit the method with negative steps.  The sign is one
+// bit (FL_REVERSE in the instance's flags) applied by xor, off the FP64 pipe.
+constexpr unsigned long long SIGN_BIT = 0x8000000000000000ULL;
+__device__ __forceinline__ unsigned long long rev_mask(int flags) {
+  return (flags & FL_REVERSE) ? SIGN_BIT : 0ULL;
+}
+__device__ __forceinline__ double flip(double x, unsigned long long m) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)m);
+}
+// The direction of instance i from its raw t0, t1 (NaN: forward, and invalid).
+__device__ __forceinline__ bool reversed_at(const double* t0, const double* t1, int i) {
+  return t1[i] < t0[i];
+}
 
 // ---------------------------------------------------------------- scalar helpers
 // a*b + c.  Both translation units are built with -fmad=false, so nothing is
@@ -275,9 +293,11 @@ template <typename T> struct InstOut {
   int K;
 };
 
-// Evaluation time q of the instance, +inf past the last one.
-template <typename T> __device__ __forceinline__ double te_at(const InstOut<T>& out, int q) {
-  return q < out.K ? out.te[q] : __longlong_as_double(0x7ff0000000000000LL);
+// Evaluation time q of the instance in the direction of integration (m:
+// its rev_mask), +inf past the last one.
+template <typename T>
+__device__ __forceinline__ double te_at(const InstOut<T>& out, int q, unsigned long long m) {
+  return q < out.K ? flip(out.te[q], m) : __longlong_as_double(0x7ff0000000000000LL);
 }
 // Moves the cursor past the point just written: the register pair shifts and
 // the time after the next one is loaded (its latency overlaps the attempt).
@@ -285,7 +305,7 @@ template <typename T, int R>
 __device__ __forceinline__ void advance_cursor(Inst<T, R>& s, const InstOut<T>& out) {
   s.cursor++;
   s.tq = s.tq2;
-  s.tq2 = te_at(out, s.cursor + 1);
+  s.tq2 = te_at(out, s.cursor + 1, rev_mask(s.flags));
 }
 
 // Dense-output weights b_i(theta), each by Horner's rule (w[1] = 0).
@@ -435,14 +455,16 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
                           const T* y0, const double* t0p, const double* t1p, double rtol,
                           double atol, const InstOut<T>& out) {
   const int g = Grp<G>::rank();
-  s.t0 = t0p[i];
-  s.t1 = t1p[i];
+  const bool rev = reversed_at(t0p, t1p, i);
+  const unsigned long long msk = rev ? SIGN_BIT : 0ULL;
+  s.t0 = flip(t0p[i], msk);
+  s.t1 = flip(t1p[i], msk);
   s.t = s.t0;
   s.rtol = T(rtol);
   s.atol = T(atol);
   s.n_acc = s.n_rej = 0;
   s.cursor = 0;
-  s.flags = 0;
+  s.flags = rev ? FL_REVERSE : 0;
   s.err_prev = T(1);
   s.err_prev2 = T(1);
   s.h = T(0);
@@ -464,9 +486,9 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
   {
     bool okl = true;
     for (int q = g; q < out.K; q += G) {
-      const double v = out.te[q];
+      const double v = flip(out.te[q], msk);
       const long long kv = tkey(v);
-      const long long kp = q > 0 ? tkey(out.te[q - 1]) : k0;
+      const long long kp = q > 0 ? tkey(flip(out.te[q - 1], msk)) : k0;
       okl = okl && tfinite(v) && kv >= kp && kv <= k1;
     }
     if constexpr (G > 1) okl = __all_sync(Grp<G>::mask(), okl) != 0;
@@ -480,8 +502,8 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
     for (int q = 0; q < out.K; ++q) store_point<T, R, G>(out.ye + (size_t)q * D, nanv);
     return false;
   }
-  s.tq = te_at(out, 0);
-  s.tq2 = te_at(out, 1);
+  s.tq = te_at(out, 0, msk);
+  s.tq2 = te_at(out, 1, msk);
   while (tkey(s.tq) == k0) {  // points at t0 are y0 itself
     store_point<T, R, G>(out.ye + (size_t)s.cursor * D, s.y);
     advance_cursor(s, out);
@@ -654,8 +676,8 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
   const int att = s.n_acc + s.n_rej;
   if (tr.cap > 0 && att < tr.cap && Grp<G>::rank() == 0) {
     const size_t q = (size_t)i * tr.cap + att;
-    tr.t[q] = s.t;
-    tr.h[q] = hd;
+    tr.t[q] = flip(s.t, rev_mask(s.flags));  // the caller's time and signed step
+    tr.h[q] = flip(hd, rev_mask(s.flags));
     tr.err[q] = (double)err;
     tr.acc[q] = accept ? 1 : 0;
   }
@@ -944,7 +966,7 @@ struct IntervalBin {
   const double* t0;
   const double* t1;
   __device__ __forceinline__ int operator()(int i) const {
-    const float len = trunc_to_float(t1[i]) - trunc_to_float(t0[i]);
+    const float len = fabsf(trunc_to_float(t1[i]) - trunc_to_float(t0[i]));  // either direction
     if (!(len > 0.0f) || !(len <= 3.4e38f)) return ORDER_BINS - 1;
     const unsigned b = __float_as_uint(len);
     const int key = ((int)((b >> 23) & 0xffu) - 127 + 32) * 4 + (int)((b >> 21) & 3u);

@@ -55,6 +55,11 @@ __device__ __forceinline__ InstOut<T> inst_out(const SolveArgs<T>& a, int i) {
   return o;
 }
 
+// The field's direction factor for instance i (-1: backward in time).
+template <typename T> __device__ __forceinline__ T dir_of(const SolveArgs<T>& a, int i) {
+  return reversed_at(a.t0, a.t1, i) ? T(-1) : T(1);
+}
+
 template <typename T> __device__ __forceinline__ double rtol_of(const SolveArgs<T>& a, int i) {
   return a.rtol_b ? a.rtol_b[i] : a.rtol;
 }
@@ -100,16 +105,17 @@ __device__ __forceinline__ void plain_load(const SolveArgs<T>& a, int j, int i,
     s.k1[r] = a.wk[q];
   }
   s.t = a.wt[j];
-  s.t0 = a.t0[i];
-  s.t1 = a.t1[i];
+  s.flags = a.wfl[j];
+  const unsigned long long m = rev_mask(s.flags);
+  s.t0 = flip(a.t0[i], m);
+  s.t1 = flip(a.t1[i], m);
   s.h = a.wh[j];
   s.err_prev = a.wep[j];
   s.err_prev2 = a.wep2[j];
   s.cursor = a.wcur[j];
-  s.flags = a.wfl[j];
   const InstOut<T> out = inst_out(a, i);
-  s.tq = te_at(out, s.cursor);
-  s.tq2 = te_at(out, s.cursor + 1);
+  s.tq = te_at(out, s.cursor, m);
+  s.tq2 = te_at(out, s.cursor + 1, m);
   s.n_acc = a.n_acc[i];
   s.n_rej = a.n_rej[i];
   s.status = a.status[i];
@@ -128,7 +134,7 @@ __global__ void k_plain_init(SolveArgs<T> a) {
   if (j >= a.B) return;
   const int i = queued(a, j);
   Field F;
-  F.load(a.fparam, i);
+  F.load(a.fparam, i, dir_of(a, i));
   Inst<T, R> s;
   const bool run =
       inst_init<Field, T, R, G>(F, s, a.o, i, a.D, a.y0, a.t0, a.t1, rtol_of(a, i),
@@ -147,7 +153,7 @@ __global__ void k_plain_step(SolveArgs<T> a) {
   const int i = queued(a, j);
   if (a.status[i] != ST_RUNNING) return;  // masked: finished instances do no work
   Field F;
-  F.load(a.fparam, i);
+  F.load(a.fparam, i, dir_of(a, i));
   Inst<T, R> s;
   plain_load<T, R, G>(a, j, i, s);
   const int acc_before = s.n_acc;
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
   while (true) {
     if (!have) {
       if (i >= a.B) break;
-      F.load(a.fparam, i);
+      F.load(a.fparam, i, dir_of(a, i));
       have = inst_init<Field, T, R, G>(F, s, a.o, i, a.D, a.y0, a.t0, a.t1, rtol_of(a, i),
                                        atol_of(a, i), inst_out(a, i));
       if (!have) {

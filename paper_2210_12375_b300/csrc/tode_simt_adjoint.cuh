@@ -24,15 +24,17 @@ template <typename T> struct VdpAdj {
   static constexpr int R = 2, G = 1;
   VdpField<T> f;
   T gmu;
-  __device__ __forceinline__ void load(const T* p, int i) {
-    f.load(p, i);
+  __device__ __forceinline__ void load(const T* p, int i, T dir) {
+    f.load(p, i, dir);
     gmu = T(0);
   }
   __device__ __forceinline__ void eval(double t, const T (&y)[2], T (&o)[2]) const {
     f.eval(t, y, o);
   }
-  // gy = J^T v with J = [[0, 1], [-2 mu y1 y2 - 1, mu (1 - y1^2)]]
-  __device__ __forceinline__ void vjp(const T (&y)[2], const T (&v)[2], T (&gy)[2]) {
+  // gy = J^T v with J = [[0, 1], [-2 mu y1 y2 - 1, mu (1 - y1^2)]] the
+  // Jacobian of f; the field evaluated is dir f, so v enters as dir v
+  __device__ __forceinline__ void vjp(const T (&y)[2], const T (&vin)[2], T (&gy)[2]) {
+    const T v[2] = {f.dir * vin[0], f.dir * vin[1]};
     const T mu = f.mu;
     const T one_m = madd(-y[0], y[0], T(1));  // 1 - y1^2
     gy[0] = v[1] * madd(T(-2) * mu * y[0], y[1], T(-1));
@@ -49,12 +51,14 @@ template <typename T, int R_, int G_> struct LinearAdj {
   // One column per lane (R = 1) stays in registers; wider lanes read their
   // columns through the L1 cache to keep the register count at two CTAs/SM.
   static constexpr bool REG_COLS = (R == 1);
-  LinearField<T, R, G> f;
+  LinearField<T, R, G> f;   // holds dir A_i (the field evaluated)
   const T* acol;       // column g*R of A_i: A[j][g*R + r] = acol[j*D + r]
   T acr[REG_COLS ? D : 1];  // R = 1: the column itself
   T gA[R][D];          // columns g*R+r of dL/dA_i: gA[r][j] = dL/dA[j][g*R + r]
-  __device__ __forceinline__ void load(const T* p, int i) {
-    f.load(p, i);
+  T dir;
+  __device__ __forceinline__ void load(const T* p, int i, T d) {
+    f.load(p, i, d);
+    dir = d;
     acol = p + (size_t)i * D * D + Grp<G>::rank() * R;
     if constexpr (REG_COLS) {
 #pragma unroll
@@ -72,10 +76,13 @@ template <typename T, int R_, int G_> struct LinearAdj {
   __device__ __forceinline__ void eval(double t, const T (&y)[R], T (&o)[R]) const {
     f.eval(t, y, o);
   }
-  // gy = A^T v,  dL/dA += v Y^T.  The lane owns columns of dL/dA, so both
-  // products need the gathered v and only the lane's own components of Y.
-  __device__ __forceinline__ void vjp(const T (&y)[R], const T (&v)[R], T (&gy)[R]) {
-    T vall[D];
+  // gy = A^T v,  dL/dA += v Y^T (v taken as dir v: the field is dir A y).
+  // The lane owns columns of dL/dA, so both products need the gathered v
+  // and only the lane's own components of Y.
+  __device__ __forceinline__ void vjp(const T (&y)[R], const T (&vin)[R], T (&gy)[R]) {
+    T v[R], vall[D];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = dir * vin[r];
     f.gather(v, vall);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -155,13 +162,16 @@ template <typename T> struct AdjArgs {
 // the step is reversed.
 template <typename T, int R> struct AdjCursor {
   int q;
-  double tq, tq2;
+  double tq, tq2;   // in the direction of integration (-t backward in time)
+  unsigned long long m;  // the instance's rev_mask
   T gq[R];
 };
 
 template <typename T>
-__device__ __forceinline__ double adj_te(const AdjArgs<T>& a, int i, int q) {
-  return q >= 0 ? a.te[(size_t)i * a.K + q] : __longlong_as_double((long long)0xfff0000000000000ULL);
+__device__ __forceinline__ double adj_te(const AdjArgs<T>& a, int i, int q,
+                                         unsigned long long m) {
+  return q >= 0 ? flip(a.te[(size_t)i * a.K + q], m)
+                : __longlong_as_double((long long)0xfff0000000000000ULL);
 }
 
 template <typename T, int R, int G>
@@ -176,8 +186,9 @@ template <typename T, int R, int G>
 __device__ __forceinline__ void adj_cursor_start(AdjCursor<T, R>& c, const AdjArgs<T>& a, int i,
                                                  int D) {
   c.q = a.K - 1;
-  c.tq = adj_te(a, i, c.q);
-  c.tq2 = adj_te(a, i, c.q - 1);
+  c.m = reversed_at(a.t0, a.t1, i) ? SIGN_BIT : 0ULL;
+  c.tq = adj_te(a, i, c.q, c.m);
+  c.tq2 = adj_te(a, i, c.q - 1, c.m);
   adj_gq<T, R, G>(a, i, D, c.q, c.gq);
 }
 
@@ -186,7 +197,7 @@ __device__ __forceinline__ void adj_cursor_next(AdjCursor<T, R>& c, const AdjArg
                                                 int D) {
   c.q--;
   c.tq = c.tq2;
-  c.tq2 = adj_te(a, i, c.q - 1);
+  c.tq2 = adj_te(a, i, c.q - 1, c.m);
   adj_gq<T, R, G>(a, i, D, c.q, c.gq);
 }
 
@@ -412,7 +423,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
         i = queued(a, grab_instance<G>(a.counter, groups_total));
       }
       if (i >= a.B) break;
-      F.load(a.fparam, i);
+      F.load(a.fparam, i, reversed_at(a.t0, a.t1, i) ? T(-1) : T(1));
       const int N = a.n_acc[i];
       bad = a.status[i] != ST_SUCCESS;
       if (!bad && N > a.tape.slots) {
@@ -422,7 +433,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
 #pragma unroll
       for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
       adj_cursor_start<T, R, G>(c, a, i, D);
-      t_after = a.t1[i];
+      t_after = flip(a.t1[i], c.m);
       n = bad ? -1 : N - 1;
       have = true;
       if (n < 0) continue;
@@ -456,7 +467,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
   no_out.K = 0;
   while (i < a.B) {
     AF F;
-    F.load(a.fparam, i);
+    F.load(a.fparam, i, reversed_at(a.t0, a.t1, i) ? T(-1) : T(1));
     const int N = a.n_acc[i];
     const int m = a.tape.stride;
     const int nseg = (N + m - 1) / m;
@@ -470,7 +481,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
     for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
     AdjCursor<T, R> c;
     adj_cursor_start<T, R, G>(c, a, i, D);
-    const double t1 = a.t1[i];
+    const double t1 = flip(a.t1[i], c.m);  // in the direction of integration
     for (int j = nseg - 1; j >= 0 && !bad; --j) {
       const int n0 = j * m;
       const int n1 = (n0 + m < N) ? n0 + m : N;
@@ -488,14 +499,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
       s.err_prev = a.tape.err_prev[o];
       s.err_prev2 = a.tape.err_prev2 ? a.tape.err_prev2[o] : T(1);  // present when beta3 != 0
       s.flags = a.tape.flags[o];
-      s.t0 = a.t0[i];
+      s.t0 = flip(a.t0[i], c.m);
       s.t1 = t1;
       s.rtol = T(a.rtol_b ? a.rtol_b[i] : a.rtol);
       s.atol = T(a.atol_b ? a.atol_b[i] : a.atol);
       s.n_acc = n0;
       s.n_rej = 0;
       s.cursor = 0;
-      s.tq = s.tq2 = te_at(no_out, 0);  // no evaluation points in a re-run
+      s.tq = s.tq2 = te_at(no_out, 0, 0ULL);  // no evaluation points in a re-run
       s.status = ST_RUNNING;
       if constexpr (Comp<T>::on) {  // functions of (t, t0, t1), as in the forward
         s.rem = __double2float_rd(s.t1 - s.t);

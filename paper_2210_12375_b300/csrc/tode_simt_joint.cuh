@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) k_joint_init(JointArgs<T> ja) {
        j += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(j / G);
     Field F;
-    F.load(a.fparam, i);
+    F.load(a.fparam, i, dir_of(a, i));
     Inst<T, R> s;
     SolveOpts o1 = a.o;
     o1.h0 = 1.0;  // the first step is the batch's: no per-instance heuristic here
@@ -199,14 +199,17 @@ __global__ void __launch_bounds__(256) k_joint_init(JointArgs<T> ja) {
   const double NB = joint_total(ja.part, 2, red);
   if (threadIdx.x != 0) return;
   JointCtl<T> c{};
-  c.t0 = a.t0[0];
-  c.t1 = a.t1[0];
+  const bool rev = reversed_at(a.t0, a.t1, 0);  // every instance's direction
+  const unsigned long long m = rev ? SIGN_BIT : 0ULL;
+  c.flags = rev ? FL_REVERSE : 0;
+  c.t0 = flip(a.t0[0], m);
+  c.t1 = flip(a.t1[0], m);
   c.t = c.t0;
   c.err_prev = T(1);
   c.err_prev2 = T(1);
   c.phase = JP_RUN;
   c.dec = JD_NONE;
-  while (c.cursor < a.K && tkey(a.te[c.cursor]) == tkey(c.t0)) c.cursor++;
+  while (c.cursor < a.K && tkey(flip(a.te[c.cursor], m)) == tkey(c.t0)) c.cursor++;
   if (NB > 0.0) {
     c.status = ST_INVALID;
   } else if (tkey(c.t1) == tkey(c.t0)) {
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(256) k_joint_h0(JointArgs<T> ja) {
        j += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(j / G);
     Field F;
-    F.load(a.fparam, i);
+    F.load(a.fparam, i, dir_of(a, i));
     const T rtol = T(a.rtol), atol = T(a.atol);
     T y[R], k1[R], w[R], f1[R], q[R];
     jld<T, R, G>(ja.y[0], a.B, i, y);
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
     jld<T, R, G>(ja.y[c.cur], a.B, i, ny);
     if constexpr (Comp<T>::on) jld<T, R, G>(ja.ylo[c.cur], a.B, i, nylo);
     jld<T, R, G>(ja.k1[c.cur], a.B, i, nk1);
-    nF.load(a.fparam, i);
+    nF.load(a.fparam, i, dir_of(a, i));
   };
   if (j / G < a.B) fetch((int)(j / G));
   for (; j / G < a.B; j += stride) {
@@ -346,8 +349,8 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
     // state of the tape slot it opened
     if (c.dec != JD_NONE && a.trace.cap > 0 && c.dec_att < a.trace.cap && g == 0) {
       const size_t q = (size_t)i * a.trace.cap + c.dec_att;
-      a.trace.t[q] = c.dec_t;
-      a.trace.h[q] = (double)c.dec_h;
+      a.trace.t[q] = flip(c.dec_t, rev_mask(c.flags));  // the caller's time and signed step
+      a.trace.h[q] = flip((double)c.dec_h, rev_mask(c.flags));
       a.trace.err[q] = (double)c.dec_err;
       a.trace.acc[q] = c.dec == JD_ACC ? 1 : 0;
     }
@@ -422,7 +425,8 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
       }
       const long long kn = tkey(t_next);
       for (int q = c.cursor; q < a.K; ++q) {  // the points in (t, t_next]
-        const double tq = a.te[q];  // the batch's evaluation times (equal in every row)
+        // the batch's evaluation times (equal in every row)
+        const double tq = flip(a.te[q], rev_mask(c.flags));
         const long long kq = tkey(tq);
         if (kq > kn) break;
         T* dst = out.ye + (size_t)q * a.D;
@@ -484,7 +488,7 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
       }
     }
     const long long kn = tkey(t_next);
-    while (n.cursor < a.K && tkey(a.te[n.cursor]) <= kn) n.cursor++;
+    while (n.cursor < a.K && tkey(flip(a.te[n.cursor], rev_mask(c.flags))) <= kn) n.cursor++;
     T fac;
     if (err == T(0)) {
       fac = opt_v<T>(a.o.fac_max, a.o.fac_max_f);
