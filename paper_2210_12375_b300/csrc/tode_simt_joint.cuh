@@ -326,11 +326,12 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
   long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   T ny[R], nylo[R], nk1[R];
   Field nF;
+  const T dir = (c.flags & FL_REVERSE) ? T(-1) : T(1);  // the batch's direction
   auto fetch = [&](int i) {
     jld<T, R, G>(ja.y[c.cur], a.B, i, ny);
     if constexpr (Comp<T>::on) jld<T, R, G>(ja.ylo[c.cur], a.B, i, nylo);
     jld<T, R, G>(ja.k1[c.cur], a.B, i, nk1);
-    nF.load(a.fparam, i, dir_of(a, i));
+    nF.load(a.fparam, i, dir);
   };
   if (j / G < a.B) fetch((int)(j / G));
   for (; j / G < a.B; j += stride) {
