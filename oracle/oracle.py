@@ -95,6 +95,7 @@ def _load():
     if _lib is None:
         lib = C.CDLL(build())
         lib.orc_solve.restype = C.c_int
+        lib.orc_solve_yp.restype = C.c_int
         lib.orc_replay.restype = C.c_int
         lib.orc_adjoint.restype = C.c_int
         _lib = lib
@@ -211,12 +212,14 @@ def _f64(a, shape):
 
 
 def solve(field: dict, y0, t0, t1, t_eval=None, opts: dict | None = None,
-          trace_cap: int = 0, nthreads: int = 0) -> dict:
+          trace_cap: int = 0, nthreads: int = 0, want_yp: bool = False) -> dict:
     """Adaptive dopri5 over B independent instances (Sec. 3).
 
     Returns y_eval [B,K,D], y_final [B,D], n_acc, n_rej, n_feval, status [B]
     and, when trace_cap > 0, per-attempt traces t/h/err/accepted [B,cap] with
-    their lengths.  ``threads`` is the number of host threads used.
+    their lengths.  ``threads`` is the number of host threads used.  With
+    ``want_yp``, also yp_eval [B,K,D]: dy/dt of the dense output at every
+    evaluation point (f(t0, y0) at points equal to t0).
     """
     lib = _load()
     opts = default_opts(**(opts or {}))
@@ -249,12 +252,16 @@ def solve(field: dict, y0, t0, t1, t_eval=None, opts: dict | None = None,
         tl = np.zeros(B, np.int32)
         tr = _Trace(trace_cap, _ptr(tt), _ptr(th), _ptr(te), _iptr(ta), _iptr(tl))
         out.update(trace_t=tt, trace_h=th, trace_err=te, trace_accepted=ta, trace_len=tl)
-    used = lib.orc_solve(C.byref(fh.f), C.byref(o), C.c_int(B), _ptr(y0), _ptr(t0), _ptr(t1),
-                         _ptr(t_eval), C.c_int(K), _ptr(y_eval), _ptr(y_final), _iptr(n_acc),
-                         _iptr(n_rej), _iptr(n_fe), _iptr(st),
-                         C.byref(tr) if tr is not None else None, C.c_int(nthreads))
+    yp = np.zeros((B, K, D)) if want_yp else None
+    used = lib.orc_solve_yp(C.byref(fh.f), C.byref(o), C.c_int(B), _ptr(y0), _ptr(t0),
+                            _ptr(t1), _ptr(t_eval), C.c_int(K), _ptr(y_eval),
+                            _ptr(yp) if yp is not None else None, _ptr(y_final),
+                            _iptr(n_acc), _iptr(n_rej), _iptr(n_fe), _iptr(st),
+                            C.byref(tr) if tr is not None else None, C.c_int(nthreads))
     out.update(y_eval=y_eval, y_final=y_final, n_acc=n_acc, n_rej=n_rej, n_feval=n_fe,
                status=st, threads=used)
+    if yp is not None:
+        out["yp_eval"] = yp
     return out
 
 

@@ -416,6 +416,22 @@ static void dp_dense(double theta, double h, const double *y, const double *k, i
 }
 
 /* Exported: dense-output weights b_i(theta), for the tests. */
+/* d/dt of the dense output y + hs sum_i b_i(theta) k_i with theta = (t -
+ * t_n) / hs: sum_i b_i'(theta) k_i, b_i'(theta) = q0 + 2 q1 theta + 3 q2
+ * theta^2 + 4 q3 theta^3 from the same quartics (the step's sign cancels). */
+static void dp_dense_deriv(double theta, const double *k, int D, double *out) {
+  double bd[NS];
+  for (int i = 0; i < NS; ++i) {
+    const double *q = DP_Q[i];
+    bd[i] = q[0] + theta * (2.0 * q[1] + theta * (3.0 * q[2] + theta * (4.0 * q[3])));
+  }
+  for (int j = 0; j < D; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < NS; ++i) s = s + bd[i] * k[i * D + j];
+    out[j] = s;
+  }
+}
+
 void orc_dense_weights(double theta, double *bt) {
   for (int i = 0; i < NS; ++i) {
     const double *q = DP_Q[i];
@@ -447,6 +463,7 @@ typedef struct {
   int B, K;
   const double *y0, *t0, *t1, *t_eval;
   double *y_eval, *y_final;
+  double *yp_eval; /* optional: dy/dt of the dense output at every evaluation point */
   int32_t *n_acc, *n_rej, *n_feval, *status;
   const orc_trace *trace;
   /* replay / adjoint */
@@ -473,6 +490,7 @@ static void solve_one(const job *J, int i, double *work, double *act) {
   const double t0 = J->t0[i], t1 = J->t1[i];
   const double *te = J->t_eval + (size_t)i * K;
   double *ye = J->y_eval + (size_t)i * K * D;
+  double *yp = J->yp_eval ? J->yp_eval + (size_t)i * K * D : NULL;
   double *yf = J->y_final + (size_t)i * D;
   double *y = work, *y1 = y + D, *k = y1 + D, *Y = k + NS * D, *e = Y + NS * D, *sc = e + D,
          *w1 = sc + D, *w2 = w1 + D;
@@ -480,6 +498,7 @@ static void solve_one(const job *J, int i, double *work, double *act) {
   int n_acc = 0, n_rej = 0, st = ST_RUNNING, tr = 0;
 
   fill_nan(ye, (size_t)K * D);
+  if (yp) fill_nan(yp, (size_t)K * D);
   if (!instance_inputs_valid(t0, t1, te, K)) {
     fill_nan(yf, D);
     J->n_acc[i] = J->n_rej[i] = J->n_feval[i] = 0;
@@ -494,6 +513,12 @@ static void solve_one(const job *J, int i, double *work, double *act) {
   while (cur < K && te[cur] == t0) {
     for (int j = 0; j < D; ++j) ye[(size_t)cur * D + j] = y[j];
     cur++;
+  }
+  if (yp && cur > 0) { /* the derivative at t0 is f(t0, y0) (not counted) */
+    fctx c0 = {F, i, act, 0};
+    feval(&c0, t0, y, w1);
+    for (int q = 0; q < cur; ++q)
+      for (int j = 0; j < D; ++j) yp[(size_t)q * D + j] = w1[j];
   }
   if (t1 == t0) {
     for (int j = 0; j < D; ++j) yf[j] = y[j];
@@ -547,6 +572,9 @@ static void solve_one(const job *J, int i, double *work, double *act) {
         } else {
           dp_dense((te[cur] - t) / hs, hs, y, k, D, o);
         }
+        if (yp) /* the interpolant's derivative; theta = 1 at the step's end */
+          dp_dense_deriv(te[cur] == t_next ? 1.0 : (te[cur] - t) / hs, k, D,
+                         yp + (size_t)cur * D);
         cur++;
       }
       /* controller: factor = safety * err^-beta1 * err_prev^beta2 * err_prev2^-beta3 */
@@ -869,10 +897,25 @@ static int run(job *J, int mode, int nthreads) {
 /* Exported entry points.  All arrays are host arrays, instance-major.       */
 /* Return value: the number of threads used.                                 */
 /* ------------------------------------------------------------------------ */
+int orc_solve_yp(const orc_field *F, const orc_opts *O, int B, const double *y0,
+                 const double *t0, const double *t1, const double *t_eval, int K,
+                 double *y_eval, double *yp_eval, double *y_final, int32_t *n_acc,
+                 int32_t *n_rej, int32_t *n_feval, int32_t *status, const orc_trace *trace,
+                 int nthreads);
 int orc_solve(const orc_field *F, const orc_opts *O, int B, const double *y0, const double *t0,
               const double *t1, const double *t_eval, int K, double *y_eval, double *y_final,
               int32_t *n_acc, int32_t *n_rej, int32_t *n_feval, int32_t *status,
               const orc_trace *trace, int nthreads) {
+  return orc_solve_yp(F, O, B, y0, t0, t1, t_eval, K, y_eval, NULL, y_final, n_acc, n_rej,
+                      n_feval, status, trace, nthreads);
+}
+/* orc_solve, plus dy/dt of the dense output at every evaluation point when
+ * yp_eval is not NULL ([B][K][D]; NaN where y_eval is). */
+int orc_solve_yp(const orc_field *F, const orc_opts *O, int B, const double *y0,
+                 const double *t0, const double *t1, const double *t_eval, int K,
+                 double *y_eval, double *yp_eval, double *y_final, int32_t *n_acc,
+                 int32_t *n_rej, int32_t *n_feval, int32_t *status, const orc_trace *trace,
+                 int nthreads) {
   job J;
   memset(&J, 0, sizeof(J));
   J.F = F;
@@ -884,6 +927,7 @@ int orc_solve(const orc_field *F, const orc_opts *O, int B, const double *y0, co
   J.t1 = t1;
   J.t_eval = t_eval;
   J.y_eval = y_eval;
+  J.yp_eval = yp_eval;
   J.y_final = y_final;
   J.n_acc = n_acc;
   J.n_rej = n_rej;

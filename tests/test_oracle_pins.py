@@ -560,3 +560,43 @@ def test_backward_in_time_closed_form_and_round_trip():
     b = oracle.solve(v["field"], f["y_final"], v1, v["t0"], None, dict(rtol=1e-11, atol=1e-11))
     assert (b["status"] == 0).all() and (b["n_acc"] > 10).all()
     assert np.abs(b["y_final"] - v["y0"]).max() < 1e-6
+
+
+def test_dense_output_derivative_pins():
+    """dy/dt at the evaluation points (the derivative of the dense-output
+    interpolant): central differences of the interpolant itself on the same
+    mesh (a replay with shifted t_eval), f(t1, y(t1)) at the end point (the
+    interpolant is C1 with the FSAL stage), f(t0, y0) at t0, and the linear
+    closed form's A y(t)."""
+    w = workloads.make(1, B=6)
+    B = 6
+    K = w["t_eval"].shape[1]
+    r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], w["t_eval"],
+                     dict(rtol=1e-7, atol=1e-7), trace_cap=4000, want_yp=True)
+    yp = r["yp_eval"]
+    mt, mh, mn = mesh_from_trace(r)
+    d = 1e-5
+    inner = w["t_eval"].copy()
+    inner[:, 0], inner[:, -1] = inner[:, 1], inner[:, -2]  # keep t0 and t1 out
+    lo = oracle.replay(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, inner - d)
+    hi = oracle.replay(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, inner + d)
+    fd = (hi["y_eval"] - lo["y_eval"]) / (2 * d)
+    for i in range(B):
+        # a step end within +-d of a point makes the difference one-sided: skip it
+        ends = np.concatenate([mt[i, :mn[i]], [w["t1"][i]]])
+        for q in range(1, K - 1):
+            if np.min(np.abs(ends - inner[i, q])) > 2 * d:
+                assert np.allclose(yp[i, q], fd[i, q], rtol=1e-6, atol=1e-6), (i, q)
+        f1 = oracle.field_eval(w["field"], i, w["t1"][i], r["y_final"][i], B)
+        assert np.allclose(yp[i, -1], f1, rtol=1e-12, atol=1e-12)
+        f0 = oracle.field_eval(w["field"], i, w["t0"][i], w["y0"][i], B)
+        assert np.array_equal(yp[i, 0], f0)
+    L = workloads.make(2, B=8)
+    Q, lam = L["field"]["Q"], L["field"]["lam"]
+    rl = oracle.solve(L["field"], L["y0"], L["t0"], L["t1"], L["t_eval"],
+                      dict(rtol=1e-11, atol=1e-11), want_yp=True)
+    c = np.einsum("bji,bj->bi", Q, L["y0"])
+    ex = np.einsum("bij,bkj->bki", Q, np.exp(-lam[:, None, :] * L["t_eval"][:, :, None])
+                   * c[:, None, :])
+    dex = np.einsum("bij,bkj->bki", L["field"]["A"], ex)
+    assert np.abs(rl["yp_eval"] - dex).max() <= 1e-6 * max(1.0, np.abs(dex).max())
