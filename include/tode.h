@@ -227,11 +227,17 @@ size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int 
  *  Evaluation points not reached (failed instance) are NaN; instances with
  *  TODE_S_INVALID_INPUT get NaN outputs and zero counters.
  *  tape: NULL or a checkpoint tape to fill for tode_adjoint.
+ *  yp_eval: NULL or [B][K][D] state dtype: dy/dt at every evaluation point,
+ *  the derivative of the dense-output interpolant there (f(t0, y0) at points
+ *  equal to t0; NaN where y_eval is NaN).  Van der Pol and linear fields,
+ *  independent solving; otherwise TODE_EUNSUPPORTED.  With it, the gradient
+ *  of a loss with respect to t_eval is <dL/dy_eval, yp_eval> per point
+ *  (tode_t_eval_grad).
  *  trace: NULL or a per-attempt trace to fill.
  *  workspace: >= tode_workspace_size bytes, 256-byte aligned. */
 tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void* y0,
                     const double* t0, const double* t1, const double* t_eval, int K,
-                    void* y_eval, void* y_final, int32_t* n_acc, int32_t* n_rej,
+                    void* y_eval, void* yp_eval, void* y_final, int32_t* n_acc, int32_t* n_rej,
                     int32_t* n_feval, int32_t* status, const tode_tape* tape,
                     const tode_trace* trace, void* workspace, size_t ws_bytes, void* stream);
 
@@ -295,6 +301,14 @@ tode_err tode_adjoint_static(const tode_field_desc* f, const tode_options* o, co
                              const int32_t* status, const tode_tape* tape, const void* gy_eval,
                              const void* gy_final, void* gy0, void* gparam, float* const* gW,
                              float* const* gb, int32_t* overflow, void* stream);
+
+/* Gradient with respect to the evaluation times of a solve that wrote
+ * yp_eval: g_t_eval[i][q] = sum_j gy_eval[i][q][j] yp_eval[i][q][j] (the
+ * output y(t_eval[i][q]) moves with its time at the rate yp_eval).  gy_eval
+ * and yp_eval [B][K][D] in the state dtype (prec TODE_F64 or TODE_F32),
+ * g_t_eval [B][K] double, all device pointers; enqueued on stream. */
+tode_err tode_t_eval_grad(int B, int K, int D, tode_prec prec, const void* gy_eval,
+                          const void* yp_eval, double* g_t_eval, void* stream);
 
 /* The MLP field's tensor-core building block on its own, for checking the
  * operand layouts and tensor-memory conventions against a plain product:

@@ -6,7 +6,8 @@ solver is the C-ABI library ``libtode.so`` (hand-written CUDA for sm_103a);
 this package only marshals torch tensors into it.
 """
 from . import _abi  # noqa: F401
-from .api import MLP, Linear, Solution, TapeBuffers, VdP, adjoint, make_options, solve  # noqa: F401
+from .api import (MLP, Linear, Solution, TapeBuffers, VdP, adjoint, make_options,  # noqa: F401
+                  solve, t_eval_grad)
 from .autograd import odeint_adjoint  # noqa: F401
 from .tuning import autotune, set_cache_path  # noqa: F401
 

@@ -20,7 +20,7 @@ STATUS = {"SUCCESS": 0, "MAX_STEPS": 1, "DT_UNDERFLOW": 2, "NONFINITE": 3, "INVA
 # entry points include/tode.h declares
 EXPORTS = ("tode_version", "tode_strerror", "tode_default_options", "tode_workspace_size",
            "tode_solve", "tode_adjoint_scratch_size", "tode_adjoint", "tode_adjoint_static",
-           "tode_tc_gemm")
+           "tode_tc_gemm", "tode_t_eval_grad")
 TODE_STATIC_ADJOINT_SCRATCH_BYTES = 32 << 20
 
 _vp = C.c_void_p
@@ -121,8 +121,10 @@ def load(path: str = LIB_PATH):
     lib.tode_workspace_size.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), C.c_int]
     lib.tode_solve.restype = C.c_int
     lib.tode_solve.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), _vp, _vp, _vp, _vp,
-                               C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(Tape),
+                               C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(Tape),
                                C.POINTER(Trace), _vp, C.c_size_t, _vp]
+    lib.tode_t_eval_grad.restype = C.c_int
+    lib.tode_t_eval_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp]
     lib.tode_adjoint_scratch_size.restype = C.c_size_t
     lib.tode_adjoint_scratch_size.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options),
                                               C.POINTER(Tape)]

@@ -226,19 +226,22 @@ class Solution:
     status: torch.Tensor
     trace: Optional[dict] = None
     extra: dict = dc_field(default_factory=dict)
+    yp_eval: Optional[torch.Tensor] = None  # dy/dt at t_eval, when requested
 
 
 def solve(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
           t_eval: Optional[torch.Tensor] = None, *, tape: Optional[TapeBuffers] = None,
           trace_cap: int = 0, stream: Optional[torch.cuda.Stream] = None,
           out: Optional[Solution] = None, workspace: Optional[torch.Tensor] = None,
-          **opt_kw) -> Solution:
+          want_yp: bool = False, **opt_kw) -> Solution:
     """Solve every instance of the batch independently (Sec. 3), or, with
     ``joint=True``, the batch as one stacked problem (Sec. 4.1: one step size,
     error norm and accept decision; equal t0, t1 and t_eval rows required).
 
     y0 [B, D] (float64 or float32; MLP: float32), t0/t1 [B] float64,
-    t_eval [B, K] float64.  Keyword options as in ``make_options``.
+    t_eval [B, K] float64.  Keyword options as in ``make_options``.  With
+    ``want_yp`` the solution also carries yp_eval [B, K, D], dy/dt of the
+    dense output at every evaluation point (Van der Pol and linear fields).
     """
     lib = _abi.load()
     B, D = y0.shape
@@ -256,6 +259,8 @@ def solve(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
             n_rej=torch.empty(B, dtype=torch.int32, device=dev),
             n_feval=torch.empty(B, dtype=torch.int32, device=dev),
             status=torch.empty(B, dtype=torch.int32, device=dev))
+    if want_yp and K > 0 and (out.yp_eval is None or out.yp_eval.shape != (B, K, D)):
+        out.yp_eval = torch.empty((B, K, D), dtype=y0.dtype, device=dev)
     trace_c = None
     if trace_cap > 0:
         tr = dict(t=torch.zeros((B, trace_cap), dtype=torch.float64, device=dev),
@@ -276,13 +281,27 @@ def solve(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
     code = lib.tode_solve(
         C.byref(fd), C.byref(opts), _ptr(y0), _ptr(t0), _ptr(t1),
         _ptr(t_eval) if K > 0 else None, int(K), _ptr(out.y_eval) if K > 0 else None,
-        _ptr(out.y_final), _ptr(out.n_acc), _ptr(out.n_rej), _ptr(out.n_feval), _ptr(out.status),
+        _ptr(out.yp_eval) if want_yp and K > 0 else None, _ptr(out.y_final), _ptr(out.n_acc), _ptr(out.n_rej), _ptr(out.n_feval), _ptr(out.status),
         C.byref(tape_c) if tape_c is not None else None,
         C.byref(trace_c) if trace_c is not None else None,
         _ptr(workspace), C.c_size_t(workspace.numel()), _stream_handle(stream))
     _abi.check(code, "tode_solve")
     out.extra["workspace"] = workspace
     return out
+
+
+def t_eval_grad(gy_eval: torch.Tensor, yp_eval: torch.Tensor,
+                stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """dL/dt_eval [B, K] (float64) = <dL/dy_eval, dy/dt> per evaluation point,
+    from the yp_eval of a solve (``want_yp=True``)."""
+    lib = _abi.load()
+    B, K, D = yp_eval.shape
+    prec = _abi.TODE_F64 if yp_eval.dtype == torch.float64 else _abi.TODE_F32
+    gy = gy_eval.to(yp_eval.dtype).contiguous()
+    g = torch.empty((B, K), dtype=torch.float64, device=yp_eval.device)
+    _abi.check(lib.tode_t_eval_grad(B, K, D, prec, _ptr(gy), _ptr(yp_eval), _ptr(g),
+                                    _stream_handle(stream)), "tode_t_eval_grad")
+    return g
 
 
 def adjoint(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=None,

@@ -28,7 +28,7 @@ def _tape_budget(dev, budget: Optional[int]) -> int:
     return int(min(DEFAULT_BUDGET_BYTES, free // 2))
 
 
-def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint):
+def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint, want_yp=False):
     B, D = y0.shape
     dev, dtype = y0.device, y0.dtype
     mlp = isinstance(field, api.MLP)
@@ -37,7 +37,7 @@ def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint):
     max_slots = max(1, budget // max(per_slot, 1))
     slots = max(1, min(max_slots, hint))
     tape = api.TapeBuffers.allocate(B, D, dtype, slots, 1, dev, stages=mlp, minimal=True)
-    sol = api.solve(field, y0, t0, t1, t_eval, tape=tape, form="fused", **opt)
+    sol = api.solve(field, y0, t0, t1, t_eval, tape=tape, form="fused", want_yp=want_yp, **opt)
     N = int(sol.n_acc.max().item()) if B > 0 else 0
     if N > slots:
         full_slot = api.TapeBuffers.bytes_per_slot(B, D, y0.element_size(), stages=mlp)
@@ -53,7 +53,8 @@ def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint):
         tape = api.TapeBuffers.allocate(B, D, dtype, slots, stride, dev, stages=mlp,
                                         minimal=stride == 1)
         # the solve is deterministic: the re-run fills the tape on the same mesh
-        sol = api.solve(field, y0, t0, t1, t_eval, tape=tape, form="fused", **opt)
+        sol = api.solve(field, y0, t0, t1, t_eval, tape=tape, form="fused", want_yp=want_yp,
+                        **opt)
     return sol, tape, N
 
 
@@ -61,8 +62,10 @@ class _Odeint(torch.autograd.Function):
     @staticmethod
     def forward(ctx, spec, y0, t0, t1, t_eval, *tensors):
         field = spec["field"].with_tensors(list(tensors))
+        # dL/dt_eval = <dL/dy_eval, dy/dt>: the forward also writes dy/dt there
+        want_yp = t_eval is not None and ctx.needs_input_grad[4]
         sol, tape, N = _solve_with_tape(field, y0, t0, t1, t_eval, spec["opt"],
-                                        spec["budget"], spec["hint"])
+                                        spec["budget"], spec["hint"], want_yp)
         spec["last_n_acc_max"] = N
         ctx.field, ctx.sol, ctx.tape, ctx.opt = field, sol, tape, spec["opt"]
         ctx.save_for_backward(t0, t1, t_eval)
@@ -84,7 +87,10 @@ class _Odeint(torch.autograd.Function):
             grads = [g.to(w.dtype) for g, w in zip(gW + gb, field.W + field.b)]
         else:
             grads = [gp]
-        return (None, gy0, None, None, None, *grads)
+        g_te = None
+        if sol.yp_eval is not None and gye is not None:
+            g_te = api.t_eval_grad(gye, sol.yp_eval).to(t_eval.dtype)
+        return (None, gy0, None, None, g_te, *grads)
 
 
 def odeint_adjoint(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
@@ -96,7 +102,8 @@ def odeint_adjoint(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
     discrete adjoint of the fixed-mesh map (App. A).
 
     Returns (y_eval [B,K,D], y_final [B,D], n_acc, n_rej, status); the counters
-    and the status carry no gradient.  Keyword options as in
+    and the status carry no gradient.  A t_eval that requires grad receives
+    dL/dt_eval through dy/dt of the dense output (Van der Pol and linear).  Keyword options as in
     ``make_options`` (the fused form is used).
     """
     opt = {k: v for k, v in opt_kw.items() if k != "form"}

@@ -153,7 +153,7 @@ size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int 
 
 tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void* y0,
                     const double* t0, const double* t1, const double* t_eval, int K,
-                    void* y_eval, void* y_final, int32_t* n_acc, int32_t* n_rej,
+                    void* y_eval, void* yp_eval, void* y_final, int32_t* n_acc, int32_t* n_rej,
                     int32_t* n_feval, int32_t* status, const tode_tape* tape,
                     const tode_trace* trace, void* workspace, size_t ws_bytes, void* stream) {
   if (!opts_ok(o) || K < 0) return TODE_EINVAL;
@@ -165,6 +165,8 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
   if (!y0 || !t0 || !t1 || !y_final || !n_acc || !n_rej || !n_feval || !status)
     return TODE_EINVAL;
   if (K > 0 && (!t_eval || !y_eval)) return TODE_EINVAL;
+  // the derivative at the points: the SIMT fields, solved independently
+  if (K > 0 && yp_eval && (f->kind == TODE_MLP || o->joint)) return TODE_EUNSUPPORTED;
   if (tape && !tape_ok(tape, o, f)) return TODE_EINVAL;
   // a joint mesh is reversed from the tape, never re-run per instance
   if (tape && o->joint && !(tape->stride == 1 && tape->h_acc)) return TODE_EINVAL;
@@ -187,6 +189,7 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
   r.t1 = t1;
   r.te = t_eval;
   r.ye = y_eval;
+  r.yp = K > 0 ? yp_eval : nullptr;
   r.yf = y_final;
   r.n_acc = n_acc;
   r.n_rej = n_rej;
@@ -260,4 +263,43 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
   return o->prec == TODE_F64 ? simt_adjoint_f64(r) : simt_adjoint_f32(r);
 }
 
+}  // extern "C"
+
+namespace tode {
+// g[i][q] = sum_j gy[i][q][j] yp[i][q][j], one warp per row, FP64 sums in a
+// fixed order (lane-strided partial sums, then a butterfly).
+template <typename T>
+__global__ void k_t_eval_grad(long long rows, int D, const T* gy, const T* yp, double* g) {
+  const long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;  // whole warps leave together
+  double s = 0.0;
+  for (int j = lane; j < D; j += 32) s += (double)gy[row * D + j] * (double)yp[row * D + j];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) g[row] = s;
+}
+}  // namespace tode
+
+extern "C" {
+tode_err tode_t_eval_grad(int B, int K, int D, tode_prec prec, const void* gy_eval,
+                          const void* yp_eval, double* g_t_eval, void* stream) {
+  if (B < 0 || K < 0 || D < 1) return TODE_EINVAL;
+  if (prec != TODE_F64 && prec != TODE_F32) return TODE_EUNSUPPORTED;
+  const long long rows = (long long)B * K;
+  if (rows == 0) return TODE_OK;
+  if (!gy_eval || !yp_eval || !g_t_eval) return TODE_EINVAL;
+  const int block = 256;
+  const long long grid = (rows * 32 + block - 1) / block;
+  if (grid > 0x7fffffffLL) return TODE_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (prec == TODE_F64)
+    tode::k_t_eval_grad<double><<<(unsigned)grid, block, 0, st>>>(
+        rows, D, (const double*)gy_eval, (const double*)yp_eval, g_t_eval);
+  else
+    tode::k_t_eval_grad<float><<<(unsigned)grid, block, 0, st>>>(
+        rows, D, (const float*)gy_eval, (const float*)yp_eval, g_t_eval);
+  TODE_CUDA_TRY(cudaGetLastError());
+  return TODE_OK;
+}
 }  // extern "C"

@@ -290,6 +290,7 @@ template <typename T> __device__ __forceinline__ T opt_v(double d, float f) {
 template <typename T> struct InstOut {
   const double* te;  // [K]
   T* ye;             // [K][D]
+  T* yp;             // [K][D] or NULL: dy/dt of the dense output at the points
   int K;
 };
 
@@ -340,6 +341,34 @@ __device__ __forceinline__ void dense_point(T theta, T h, const T (&y)[R], const
     s = madd(w[6], k7[r], s);
     if constexpr (Comp<T>::on) out[r] = y[r] + madd(h, s, ylo[r]);
     else out[r] = madd(h, s, y[r]);
+  }
+}
+
+// d/dt of the dense output at theta: sum_i b_i'(theta) k_i with b_i' the
+// derivatives of the same quartics (the step size cancels), times dir to
+// turn the solver's tau = dir t back into t.
+template <typename T, int R>
+__device__ __forceinline__ void dense_deriv(T th, T dir, const T (&k1)[R], const T (&k3)[R],
+                                            const T (&k4)[R], const T (&k5)[R],
+                                            const T (&k6)[R], const T (&k7)[R], T (&out)[R]) {
+  using C = DP5;
+  T w[7];
+  w[0] = madd(th, madd(th, madd(th, T(4) * T(C::q13), T(3) * T(C::q12)), T(2) * T(C::q11)),
+              T(C::q10));
+  w[2] = th * madd(th, madd(th, T(4) * T(C::q33), T(3) * T(C::q32)), T(2) * T(C::q31));
+  w[3] = th * madd(th, madd(th, T(4) * T(C::q43), T(3) * T(C::q42)), T(2) * T(C::q41));
+  w[4] = th * madd(th, madd(th, T(4) * T(C::q53), T(3) * T(C::q52)), T(2) * T(C::q51));
+  w[5] = th * madd(th, madd(th, T(4) * T(C::q63), T(3) * T(C::q62)), T(2) * T(C::q61));
+  w[6] = th * madd(th, madd(th, T(4) * T(C::q73), T(3) * T(C::q72)), T(2) * T(C::q71));
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T v = w[0] * k1[r];
+    v = madd(w[2], k3[r], v);
+    v = madd(w[3], k4[r], v);
+    v = madd(w[4], k5[r], v);
+    v = madd(w[5], k6[r], v);
+    v = madd(w[6], k7[r], v);
+    out[r] = dir * v;
   }
 }
 
@@ -500,6 +529,8 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
 #pragma unroll
     for (int r = 0; r < R; ++r) nanv[r] = nan_(T(0));
     for (int q = 0; q < out.K; ++q) store_point<T, R, G>(out.ye + (size_t)q * D, nanv);
+    if (out.yp)
+      for (int q = 0; q < out.K; ++q) store_point<T, R, G>(out.yp + (size_t)q * D, nanv);
     return false;
   }
   s.tq = te_at(out, 0, msk);
@@ -507,6 +538,14 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
   while (tkey(s.tq) == k0) {  // points at t0 are y0 itself
     store_point<T, R, G>(out.ye + (size_t)s.cursor * D, s.y);
     advance_cursor(s, out);
+  }
+  if (out.yp && s.cursor > 0) {  // and their derivative f(t0, y0)
+    T f0[R];
+    F.eval(s.t, s.y, f0);
+    const T dir = rev ? T(-1) : T(1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) f0[r] = dir * f0[r];
+    for (int q = 0; q < s.cursor; ++q) store_point<T, R, G>(out.yp + (size_t)q * D, f0);
   }
   if (k1 == k0) {
     s.status = ST_SUCCESS;
@@ -710,16 +749,22 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
       const long long kq = tkey(tq);
       if (kq > kn) break;
       T* dst = out.ye + (size_t)s.cursor * D;
+      T theta = T(1);
       if (kq == kn) {
         store_point<T, R, G>(dst, yn);
       } else {
         // abscissa: the difference tq - t in FP64, the ratio in the state type
-        T theta;
         if constexpr (Comp<T>::on) theta = T(tq - s.t) / h;
         else theta = T((tq - s.t) / hd);
         T v[R];
         dense_point<T, R>(theta, h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
         store_point<T, R, G>(dst, v);
+      }
+      if (out.yp) {
+        T v[R];
+        dense_deriv<T, R>(theta, (s.flags & FL_REVERSE) ? T(-1) : T(1), s.k1, k3, k4, k5, k6,
+                          k7, v);
+        store_point<T, R, G>(out.yp + (size_t)s.cursor * D, v);
       }
       advance_cursor(s, out);
     }
@@ -791,7 +836,10 @@ __device__ void inst_finalize(const Inst<T, R>& s, const SolveOpts& o, int i, in
     T nanv[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) nanv[r] = nan_(T(0));
-    for (int q = s.cursor; q < out.K; ++q) store_point<T, R, G>(out.ye + (size_t)q * D, nanv);
+    for (int q = s.cursor; q < out.K; ++q) {
+      store_point<T, R, G>(out.ye + (size_t)q * D, nanv);
+      if (out.yp) store_point<T, R, G>(out.yp + (size_t)q * D, nanv);
+    }
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) y_final[(size_t)i * D + g * R + r] = invalid ? nan_(T(0)) : s.y[r];

@@ -19,6 +19,7 @@ struct SolveReq {
   const double* t1;
   const double* te;
   void* ye;
+  void* yp;   // may be NULL: dy/dt at the evaluation points
   void* yf;
   int32_t *n_acc, *n_rej, *n_fe, *status;
   const tode_tape* tape;    // may be NULL

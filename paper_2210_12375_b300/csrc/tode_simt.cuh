@@ -19,6 +19,7 @@ template <typename T> struct SolveArgs {
   const double* atol_b;
   double rtol, atol;
   T* ye;
+  T* yp;  // NULL unless requested
   T* yf;
   int32_t *n_acc, *n_rej, *n_fe, *status;
   SolveOpts o;
@@ -52,6 +53,7 @@ __device__ __forceinline__ InstOut<T> inst_out(const SolveArgs<T>& a, int i) {
   o.K = a.K;
   o.te = a.te + (size_t)i * a.K;
   o.ye = a.ye + (size_t)i * a.K * a.D;
+  o.yp = a.yp ? a.yp + (size_t)i * a.K * a.D : nullptr;
   return o;
 }
 
@@ -267,6 +269,7 @@ template <typename T> SolveArgs<T> make_solve_args(const SolveReq& r) {
   a.rtol = r.o->rtol;
   a.atol = r.o->atol;
   a.ye = (T*)r.ye;
+  a.yp = (T*)r.yp;
   a.yf = (T*)r.yf;
   a.n_acc = r.n_acc;
   a.n_rej = r.n_rej;

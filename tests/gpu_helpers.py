@@ -44,6 +44,8 @@ def gpu_solve(w, dtype, form, rtol=None, atol=None, trace_cap=0, tape=None, **kw
     if sol.trace is not None:
         for k, v in sol.trace.items():
             out["trace_" + k] = v.cpu().numpy()
+    if sol.yp_eval is not None:
+        out["yp_eval"] = sol.yp_eval.cpu().numpy().astype(np.float64)
     out["_sol"] = sol
     out["_dev"] = dict(field=field, y0=y0, t0=t0, t1=t1, te=te)
     return out

@@ -108,7 +108,8 @@ def test_solve_rejects_bad_options_before_launch(mutate, code):
     o = _opts(**mutate)
     f = _desc(_abi.TODE_VDP, 4, 2)
     p = C.c_void_p(0x1000)
-    rc = lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, None, None, p,
+    rc = lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, None,
+                        p, p, p, p, p, None, None, p,
                         C.c_size_t(1 << 20), None)
     assert rc == code
 
@@ -119,29 +120,34 @@ def test_solve_rejects_null_pointers_and_small_workspace():
     f = _desc(_abi.TODE_VDP, 4, 2)
     p = C.c_void_p(0x1000)
     # null y0
-    assert lib.tode_solve(C.byref(f), C.byref(o), None, p, p, p, 2, p, p, p, p, p, p, None, None,
+    assert lib.tode_solve(C.byref(f), C.byref(o), None, p, p, p, 2, p, None,
+                          p, p, p, p, p, None, None,
                           p, C.c_size_t(1 << 20), None) == _abi.TODE_EINVAL
     # K > 0 without t_eval
-    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, None, 2, p, p, p, p, p, p, None, None,
+    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, None, 2, p, None,
+                          p, p, p, p, p, None, None,
                           p, C.c_size_t(1 << 20), None) == _abi.TODE_EINVAL
     # workspace too small / misaligned
-    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, None, None,
+    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, None, p, p, p, p, p, None, None,
                           p, C.c_size_t(8), None) == _abi.TODE_EWORKSPACE
-    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, None, None,
+    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, None, p, p, p, p, p, None, None,
                           C.c_void_p(0x1008), C.c_size_t(1 << 20), None) == _abi.TODE_EWORKSPACE
     # empty batch is a no-op
     f0 = _desc(_abi.TODE_VDP, 0, 2)
     assert lib.tode_solve(C.byref(f0), C.byref(o), None, None, None, None, 0, None, None, None,
-                          None, None, None, None, None, None, C.c_size_t(0), None) == _abi.TODE_OK
+                          None, None, None, None, None, None, None, C.c_size_t(0),
+                          None) == _abi.TODE_OK
     # bad tape: no slots, or an FP32 tape without its compensation buffer
     tp = _abi.Tape()
     tp.slots, tp.stride = 0, 1
-    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, C.byref(tp),
+    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, None,
+                          p, p, p, p, p, C.byref(tp),
                           None, p, C.c_size_t(1 << 20), None) == _abi.TODE_EINVAL
     tp.slots = 2
     tp.y = tp.t = tp.h = tp.err_prev = tp.flags = tp.k1 = 0x1000
     o32 = _opts(prec=_abi.TODE_F32)
-    assert lib.tode_solve(C.byref(f), C.byref(o32), p, p, p, p, 2, p, p, p, p, p, p, C.byref(tp),
+    assert lib.tode_solve(C.byref(f), C.byref(o32), p, p, p, p, 2, p, None,
+                          p, p, p, p, p, C.byref(tp),
                           None, p, C.c_size_t(1 << 20), None) == _abi.TODE_EINVAL
 
 
@@ -196,6 +202,7 @@ def test_tape_fields_checked_before_launch(tape_kw, ok):
     f = _desc(_abi.TODE_VDP, 4, 2)
     p = C.c_void_p(0x1000)
     tp = _tape(**tape_kw)
-    rc = lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, C.byref(tp), None,
+    rc = lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, None,
+                        p, p, p, p, p, C.byref(tp), None,
                         p, C.c_size_t(0), None)
     assert rc == (_abi.TODE_EWORKSPACE if ok else _abi.TODE_EINVAL)
