@@ -123,12 +123,12 @@ class ClockSampler:
 # one ncu capture of that kernel as it stands (summaries under profiles/);
 # kernels without a capture of their current code report null.
 TRAFFIC = {
-    ("linear_d16_b8192", "k_fused<LinearField<float,2,8>>"): 28.11e6,
-    ("linear_d16_b8192", "k_fused<LinearField<float,1,16>>"): 28.54e6,
-    ("linear_d16_b8192", "k_adjoint_steps<LinearAdj<float,1,16>>"): 86.69e6,
+    ("linear_d16_b8192", "k_fused<LinearField<float,2,8>>"): 28.52e6,
+    ("linear_d16_b8192", "k_fused<LinearField<float,1,16>>"): 27.59e6,
+    ("linear_d16_b8192", "k_adjoint_steps<LinearAdj<float,1,16>>"): 86.14e6,
     ("mlp_d32_h128", "k_mlp_adjoint"): 67.41e6,
     # captured on the first 32,768 instances, x8 (the tape grows with the steps)
-    ("vdp_mix_b262144", "k_fused<VdpField<float>>"): 8 * 91.80e6,
+    ("vdp_mix_b262144", "k_fused<VdpField<float>>"): 8 * 91.71e6,
     ("vdp_mix_b262144", "k_adjoint_steps<VdpAdj<float>>"): 8 * 124.07e6,
     ("mlp_d32_h128", "k_mlp_fused"): 12.68e6,
     ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 70.22e6,

@@ -683,7 +683,9 @@ __device__ __forceinline__ bool error_terms(T h, const T (&y)[R], const T (&y1)[
 
 // ---------------------------------------------------------------- one attempt (a3..a9)
 // Returns true while the instance is still running.
-template <class Field, typename T, int R, int G>
+// YP: the solve also writes dy/dt at the points (out.yp); a separate
+// instantiation, so that solves without it keep the leaner kernel.
+template <class Field, typename T, int R, int G, bool YP = false>
 __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, int i, int D,
                              const InstOut<T>& out, const TraceDev& tr, T (&ys)[6][R]) {
   using C = DP5;
@@ -760,7 +762,7 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
         dense_point<T, R>(theta, h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
         store_point<T, R, G>(dst, v);
       }
-      if (out.yp) {
+      if constexpr (YP) {
         T v[R];
         dense_deriv<T, R>(theta, (s.flags & FL_REVERSE) ? T(-1) : T(1), s.k1, k3, k4, k5, k6,
                           k7, v);
