@@ -131,7 +131,7 @@ TRAFFIC = {
     ("vdp_mix_b262144", "k_fused<VdpField<float>>"): 8 * 91.71e6,
     ("vdp_mix_b262144", "k_adjoint_steps<VdpAdj<float>>"): 8 * 124.07e6,
     ("mlp_d32_h128", "k_mlp_fused"): 12.68e6,
-    ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 70.22e6,
+    ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 69.53e6,
 }
 
 
