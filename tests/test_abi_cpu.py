@@ -206,3 +206,20 @@ def test_tape_fields_checked_before_launch(tape_kw, ok):
                         p, p, p, p, p, C.byref(tp), None,
                         p, C.c_size_t(0), None)
     assert rc == (_abi.TODE_EWORKSPACE if ok else _abi.TODE_EINVAL)
+
+
+def test_derivative_output_and_t_eval_grad_checked_before_launch():
+    """dy/dt at the points is for independent solving of the SIMT fields;
+    tode_t_eval_grad validates its sizes, precision and pointers."""
+    lib = _abi.load()
+    f = _desc(_abi.TODE_VDP, 4, 2)
+    p = C.c_void_p(0x1000)
+    o = _opts(prec=_abi.TODE_F64, joint=1)
+    # joint solving with yp_eval: refused before any pointer is touched
+    assert lib.tode_solve(C.byref(f), C.byref(o), p, p, p, p, 2, p, p, p, p, p, p, p, None,
+                          None, p, C.c_size_t(1 << 20), None) == _abi.TODE_EUNSUPPORTED
+    g = lib.tode_t_eval_grad
+    assert g(0, 5, 2, _abi.TODE_F64, None, None, None, None) == _abi.TODE_OK  # empty
+    assert g(4, 5, 2, _abi.TODE_F64, None, p, p, None) == _abi.TODE_EINVAL
+    assert g(4, 5, 0, _abi.TODE_F64, p, p, p, None) == _abi.TODE_EINVAL
+    assert g(4, 5, 2, _abi.TODE_BF16W, p, p, p, None) == _abi.TODE_EUNSUPPORTED
