@@ -7,7 +7,8 @@ instance-major, on the host.
 Parts follow the torchode paper (Sec. 3: independent per-instance solver
 state, FSAL/SSAL, Horner dense output; App. A: dopri5 with an integral
 controller; App. C: PI(D) controllers after Soderlind).  The starting-step
-heuristic (HNW Sec. II.4) is PARITY UNPINNED: the paper gives no rule.
+heuristic is HNW Sec. II.4's (the paper gives no rule), pinned by its closed
+form on diagonal linear systems and an exact evaluation on Van der Pol.
 """
 from __future__ import annotations
 

@@ -42,9 +42,11 @@
  *     three error estimates; beta3 = beta2 = 0 is the I controller);
  *   - powers err^-beta: a fixed exp/log procedure (orc_pow) so that every
  *     IEEE machine running it reproduces the controller's step sizes;
- *   - starting step: the heuristic of HNW Sec. II.4 ("starting step size").
- *     PARITY UNPINNED: the paper gives no starting-step rule and no worked
- *     example of it; only the other parts below are pinned by tests.
+ *   - starting step: the heuristic of HNW Sec. II.4 ("starting step size"),
+ *     with the probe evaluation taken in the direction of integration (the
+ *     paper gives no starting-step rule; the tests pin this one against its
+ *     closed form on diagonal linear systems and an exact rational
+ *     evaluation on Van der Pol, every branch of it deciding once).
  *
  * Arithmetic: double everywhere, built with -O2 -ffp-contract=off and no
  * fast-math, sums taken left to right in the order written.
@@ -345,7 +347,7 @@ double orc_pow(double x, double y) {
   return ctl_exp(y * ctl_ln(x));
 }
 
-/* Starting step size, HNW Sec. II.4 (PARITY UNPINNED, see header).  f0 =
+/* Starting step size, HNW Sec. II.4 (pinned by the tests, see header).  f0 =
  * f(t0, y0) is supplied and reused as the first step's k1 (FSAL). */
 /* Magnitude of the first step; the trial step goes in the direction dir of
  * integration (+1 forward, -1 from t0 down to t1). */

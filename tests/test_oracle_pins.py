@@ -600,3 +600,120 @@ def test_dense_output_derivative_pins():
                    * c[:, None, :])
     dex = np.einsum("bij,bkj->bki", L["field"]["A"], ex)
     assert np.abs(rl["yp_eval"] - dex).max() <= 1e-6 * max(1.0, np.abs(dex).max())
+
+
+# ---------------------------------------------------------------- starting step
+def _hnw_starting_step(lams, y0, rtol, atol, span):
+    """The starting-step heuristic of Hairer-Norsett-Wanner Sec. II.4 for
+    y' = diag(lams) y, every quantity written out from its definition:
+    d0 = ||y0||, d1 = ||f0||, h0 = 0.01 d0 / d1 (1e-6 when either norm is
+    below 1e-5), d2 = ||f(t0 + h0, y0 + h0 f0) - f0|| / h0 which for this
+    field is ||diag(lams)^2 y0|| exactly, h1 = (0.01 / max(d1, d2))^(1/5)
+    (max(1e-6, 1e-3 h0) when max(d1, d2) <= 1e-15), and the first step
+    min(100 h0, h1, |t1 - t0|).  The norm is the RMS weighted by
+    atol + rtol |y0|.  Returns the step and which of the three terms set it."""
+    lams = np.asarray(lams, dtype=np.float64)
+    y0 = np.asarray(y0, dtype=np.float64)
+    sc = atol + rtol * np.abs(y0)
+
+    def norm(v):
+        return math.sqrt(float(np.mean((v / sc) ** 2)))
+
+    d0 = norm(y0)
+    d1 = norm(lams * y0)
+    h0 = 1e-6 if (d0 < 1e-5 or d1 < 1e-5) else 0.01 * d0 / d1
+    d2 = norm(lams * lams * y0)
+    m = max(d1, d2)
+    h1 = max(1e-6, h0 * 1e-3) if m <= 1e-15 else (0.01 / m) ** 0.2
+    terms = {"100*h0": 100.0 * h0, "h1": h1, "span": span}
+    which = min(terms, key=terms.get)
+    return terms[which], which, h0
+
+
+@pytest.mark.parametrize("direction", [1.0, -1.0])
+def test_starting_step_matches_hnw_closed_form(direction):
+    """The oracle's first attempted step on diagonal linear systems equals
+    the HNW Sec. II.4 heuristic worked out in closed form, in both
+    directions of integration (a backward instance attempts -h first).  The
+    cases are chosen so that each term of min(100 h0, h1, t1 - t0) and each
+    fallback (h0 = 1e-6 for a tiny norm, h1 = max(1e-6, 1e-3 h0) for a
+    vanishing derivative) decides at least once: a wrong exponent, a missing
+    cap, a dropped fallback or a wrong sign fails one of them."""
+    cases = [  # lams, y0, rtol, atol, |t1 - t0|
+        ((-2.0,), (1.0,), 1e-6, 1e-6, 10.0),             # h1 decides (d2 > d1)
+        ((-0.3,), (1.5,), 1e-7, 1e-9, 10.0),             # h1 decides (d1 > d2)
+        ((-1000.0,), (1.0,), 1e-2, 1e-2, 10.0),          # 100 h0 decides
+        ((-0.5,), (2.0,), 1e-3, 1e-3, 1e-3),             # the interval decides
+        ((-1.0,), (1e-12,), 1e-6, 1e-6, 10.0),           # d0 < 1e-5: h0 = 1e-6
+        ((0.0,), (0.0,), 1e-6, 1e-6, 10.0),              # f = 0: both fallbacks
+        ((-3.0, 0.7), (1.3, -0.4), 1e-6, 1e-9, 10.0),    # two components, mixed signs
+        ((-40.0, -0.05), (0.2, 5.0), 1e-5, 1e-5, 10.0),  # two components, stiff and slow
+    ]
+    seen = set()
+    for lams, y0, rtol, atol, span in cases:
+        D = len(lams)
+        A = np.diag(lams).reshape(1, D, D)
+        t0 = 2.0
+        t1 = t0 + direction * span
+        expect, which, h0 = _hnw_starting_step(lams, y0, rtol, atol, span)
+        seen.add(which)
+        if which != "span":  # the decision is not a tie
+            others = sorted(v for v in (100.0 * h0, span) if v != expect)
+            assert not others or others[0] > expect * (1 + 1e-6)
+        r = oracle.solve({"kind": "linear", "A": A}, np.array([y0]), np.array([t0]),
+                         np.array([t1]), None, dict(rtol=rtol, atol=atol), trace_cap=2)
+        got = r["trace_h"][0, 0]
+        assert math.copysign(1.0, got) == direction, (lams, y0, got)
+        assert abs(abs(got) / expect - 1.0) < 1e-12, (lams, y0, which, got, expect)
+        assert r["trace_t"][0, 0] == t0
+    assert seen == {"100*h0", "h1", "span"}
+    # the fallbacks: h0 = 1e-6 from the tiny norm, then 100 h0 = 1e-4 decides
+    assert _hnw_starting_step((-1.0,), (1e-12,), 1e-6, 1e-6, 10.0)[0] == pytest.approx(1e-4)
+    # f = 0: h0 = 1e-6 and h1 = max(1e-6, 1e-9) = 1e-6
+    assert _hnw_starting_step((0.0,), (0.0,), 1e-6, 1e-6, 10.0)[0] == 1e-6
+
+
+@pytest.mark.parametrize("direction", [1.0, -1.0])
+def test_starting_step_van_der_pol_exact(direction):
+    """The same heuristic on the nonlinear Van der Pol field (Eq. 1), with
+    the probe evaluation f(t0 + h0, y0 + h0 f0) taken in the direction of
+    integration: d2 is computed in exact rational arithmetic from the
+    definition (for a linear field the direction of the probe cannot show,
+    here it moves d2 by ~1e-3).  The square roots and the 1/5 power are
+    taken at the end in FP64."""
+    from fractions import Fraction as Fr
+
+    mu, y0 = Fr(8), (Fr(7, 4), Fr(-1, 2))
+    rtol, atol = 1e-6, 1e-7
+    sc = [Fr(atol) + Fr(rtol) * abs(v) for v in y0]
+
+    def f(y):
+        return (y[1], mu * (1 - y[0] * y[0]) * y[1] - y[0])
+
+    def norm2(v):  # mean of squares, exact
+        return sum((x / s) ** 2 for x, s in zip(v, sc)) / len(v)
+
+    f0 = f(y0)
+    d0 = math.sqrt(norm2(y0))
+    d1 = math.sqrt(norm2(f0))
+    h0 = 0.01 * (d0 / d1)
+    assert d0 >= 1e-5 and d1 >= 1e-5
+    hs = Fr(direction * h0)  # the FP64 probe step, exactly
+    yp = tuple(a + hs * b for a, b in zip(y0, f0))
+    diff = tuple(a - b for a, b in zip(f(yp), f0))
+    d2 = math.sqrt(norm2(diff)) / h0
+    h1 = (0.01 / max(d1, d2)) ** 0.2
+    expect = min(100.0 * h0, h1, 20.0)
+    assert expect == h1 and d2 > d1
+    # the probe in the other direction would give a visibly different step
+    yq = tuple(a - hs * b for a, b in zip(y0, f0))
+    d2q = math.sqrt(norm2(tuple(a - b for a, b in zip(f(yq), f0)))) / h0
+    assert abs((0.01 / max(d1, d2q)) ** 0.2 / h1 - 1.0) > 1e-5
+    t0 = 1.0
+    r = oracle.solve({"kind": "vdp", "mu": np.array([float(mu)])},
+                     np.array([[float(y0[0]), float(y0[1])]]), np.array([t0]),
+                     np.array([t0 + direction * 20.0]), None, dict(rtol=rtol, atol=atol),
+                     trace_cap=2)
+    got = r["trace_h"][0, 0]
+    assert math.copysign(1.0, got) == direction
+    assert abs(abs(got) / expect - 1.0) < 1e-11, (got, expect)
