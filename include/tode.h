@@ -87,8 +87,9 @@ enum {
  *               widths[0] = D + 1 and widths[n_layers] = D; W (host array of
  *               device pointers) W[l] is [widths[l+1]][widths[l]] BF16
  *               (uint16 bit patterns); b (host array of device pointers)
- *               b[l] is [widths[l+1]] float (NULL = zero).  Built shape:
- *               widths {33, 128, 128, 32}; fused form only. */
+ *               b[l] is [widths[l+1]] float (NULL = zero).  Built shapes:
+ *               widths {33, 128, 128, 32} and {65, 512, 512, 512, 64};
+ *               both forms. */
 typedef struct {
   tode_field_kind kind;
   int B;
@@ -283,11 +284,13 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
  * its own, or code that must not call cudaMalloc in a latency-critical loop
  * because it can synchronise the device.  The paper has no counterpart; this
  * is a deployment convenience.
- *  - Arguments, outputs and errors are those of tode_adjoint minus scratch.
- *    The scratch is a library-owned device array of
- *    TODE_STATIC_ADJOINT_SCRATCH_BYTES; a problem whose
- *    tode_adjoint_scratch_size exceeds it is rejected with TODE_EWORKSPACE
- *    before any device work (lower tape->stride or split the batch).
+ *  - Arguments, outputs and errors are those of tode_adjoint minus scratch,
+ *    checked in the same order (an invalid argument or tape is
+ *    TODE_EINVAL / TODE_EUNSUPPORTED whatever its size).  The scratch is a
+ *    library-owned device array of TODE_STATIC_ADJOINT_SCRATCH_BYTES; a
+ *    valid problem whose tode_adjoint_scratch_size exceeds it is rejected
+ *    with TODE_EWORKSPACE before any device work (a strided tape: lower
+ *    tape->stride; otherwise split the batch).
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  *  - The first call on each device looks up the array's device address with
  *    that device current (cudaGetSymbolAddress) and caches it; make that

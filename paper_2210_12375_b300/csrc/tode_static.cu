@@ -55,11 +55,14 @@ extern "C" tode_err tode_adjoint_static(const tode_field_desc* f, const tode_opt
                                         const void* gy_eval, const void* gy_final, void* gy0,
                                         void* gparam, float* const* gW, float* const* gb,
                                         int32_t* overflow, void* stream) {
-  // the problem must fit the static scratch; checked before any device work
+  // Arguments and tape first: tode_adjoint without scratch validates
+  // everything and launches nothing, returning TODE_EWORKSPACE only when all
+  // else is valid (TODE_OK when the batch is empty, an argument error
+  // otherwise).  Then the size against the array, before any device work.
+  const tode_err v = tode_adjoint(f, o, t0, t1, t_eval, K, n_acc, status, tape, gy_eval,
+                                  gy_final, gy0, gparam, gW, gb, overflow, nullptr, 0, stream);
+  if (v != TODE_EWORKSPACE) return v;
   const size_t need = tode_adjoint_scratch_size(f, o, tape);
-  if (need == 0)  // invalid arguments: let tode_adjoint name the error (it launches nothing)
-    return tode_adjoint(f, o, t0, t1, t_eval, K, n_acc, status, tape, gy_eval, gy_final, gy0,
-                        gparam, gW, gb, overflow, nullptr, 0, stream);
   if (need > (size_t)TODE_STATIC_ADJOINT_SCRATCH_BYTES) return TODE_EWORKSPACE;
   void* scratch = nullptr;
   const tode_err e = static_scratch_address(&scratch);

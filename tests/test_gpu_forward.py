@@ -154,12 +154,13 @@ def test_vdp_mix_f32_full_size_sampled(form):
     err = np.abs(gs["y_eval"] - R)
     assert (err <= lim).all(), (err > lim).sum()
     # the FP32 arithmetic on the GPU's own mesh (GPU vs FP64 replay of that
-    # mesh) stays inside the band on the non-stiff instances; once relaxation
-    # phases appear even a finite frozen-mesh replay amplifies perturbations,
-    # so there the matched-error comparison below is the check
+    # mesh): inside the band on the non-stiff instances, inside twice the band
+    # up to mu = 10 (beyond that even a finite frozen-mesh replay amplifies
+    # perturbations, and the matched-error comparison below is the check)
     mu = ws["field"]["mu"]
     arith = np.abs(gs["y_eval"] - rep["y_eval"]) / band
-    assert (arith[rep_ok & (mu < 3.0)] <= 1.0).all()
+    assert (arith[rep_ok & (mu < 3.0)] <= 1.0).all(), arith[rep_ok & (mu < 3.0)].max()
+    assert (arith[rep_ok & (mu < 10.0)] <= 2.0).all(), arith[rep_ok & (mu < 10.0)].max()
     # matched error: FP32 meets the plain band as often as the FP64 path
     # does at the same tolerance (the misses are the method's global error)
     g64 = gpu_solve(ws, torch.float64, form)

@@ -22,11 +22,14 @@ from gpu_helpers import gpu_solve, make
 pytestmark = pytest.mark.gpu
 
 
-def _prepare(cfg, B, dtype, seed):
+def _prepare(cfg, B, dtype, seed, stride=1):
     w = make(cfg, B=B)
     probe = gpu_solve(w, dtype, "fused")
-    slots = max(1, int(probe["n_acc"].max()))
-    tape = tode.TapeBuffers.allocate(B, w["y0"].shape[1], dtype, slots, 1, "cuda")
+    n_max = max(1, int(probe["n_acc"].max()))
+    slots = -(-n_max // stride)
+    mlp = w["field"]["kind"] == "mlp"
+    tape = tode.TapeBuffers.allocate(B, w["y0"].shape[1], dtype, slots, stride, "cuda",
+                                     stages=mlp)
     g = gpu_solve(w, dtype, "fused", tape=tape)
     rng = np.random.default_rng(seed)
     gye = torch.tensor(rng.standard_normal(g["y_eval"].shape), dtype=dtype, device="cuda")
@@ -47,15 +50,27 @@ def _static_adjoint(w, g, tape, gye, gyf):
     K = dev["te"].shape[1]
     opts = api.make_options(prec=api._prec_of(field, sol.y_final), rtol=w["rtol"],
                             atol=w["atol"])
-    fd = field.desc(B, D, [])
+    keep = []
+    fd = field.desc(B, D, keep)
     tp = tape.c()
     gy0 = torch.full((B, D), float("nan"), dtype=sol.y_final.dtype, device="cuda")
-    gp = torch.full_like(field.params(), float("nan"))
     ovf = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gW_arg = gb_arg = None
+    if isinstance(field, tode.MLP):  # dW_l and db_l, summed over the batch
+        gp = ([torch.full(x.shape, float("nan"), dtype=torch.float32, device="cuda")
+               for x in field.W],
+              [torch.full((x.shape[0],), float("nan"), dtype=torch.float32, device="cuda")
+               for x in field.W])
+        gW_arg = (C.c_void_p * len(gp[0]))(*[x.data_ptr() for x in gp[0]])
+        gb_arg = (C.c_void_p * len(gp[1]))(*[x.data_ptr() for x in gp[1]])
+        gparam = None
+    else:
+        gp = torch.full_like(field.params(), float("nan"))
+        gparam = _ptr(gp)
     code = lib.tode_adjoint_static(
         C.byref(fd), C.byref(opts), _ptr(dev["t0"]), _ptr(dev["t1"]), _ptr(dev["te"]), K,
         _ptr(sol.n_acc), _ptr(sol.status), C.byref(tp), _ptr(gye), _ptr(gyf), _ptr(gy0),
-        _ptr(gp), None, None, _ptr(ovf), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        gparam, gW_arg, gb_arg, _ptr(ovf), C.c_void_p(torch.cuda.current_stream().cuda_stream))
     torch.cuda.synchronize()
     return code, gy0, gp, ovf
 
@@ -69,9 +84,17 @@ def _reference_adjoint(w, g, tape, gye, gyf):
 
 
 def _rel(a, b):
+    if isinstance(a, (tuple, list)):  # MLP: every dW_l and db_l
+        return max(_rel(x, y) for x, y in zip(a, b))
     a = a.double().cpu().numpy()
     b = b.double().cpu().numpy()
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _finite(g):
+    if isinstance(g, (tuple, list)):
+        return all(_finite(x) for x in g)
+    return bool(torch.isfinite(g).all())
 
 
 def test_static_scratch_adjoint_matches_caller_scratch_twice():
@@ -90,21 +113,70 @@ def test_static_scratch_adjoint_matches_caller_scratch_twice():
         assert _rel(gp, ref_gp) <= tol
 
 
-def test_static_scratch_rejects_problems_beyond_its_size():
-    w, g, tape, gye, gyf = _prepare(1, 256, torch.float64, seed=3)
+def test_static_scratch_strided_tape_and_mlp_twice():
+    """Strided tapes park the re-run segments' step-start states in the
+    array (its segment region, beyond the work counter and order): Van der
+    Pol FP64 with stride 4, then linear FP32 with stride 3, each checked
+    against the caller-scratch adjoint bit for bit (the same kernel on the
+    same data); then the MLP field (D = 32, H = 128), whose per-CTA weight
+    gradient partials also live in the array, at the MLP adjoint's
+    tolerance."""
+    for cfg, B, dtype, stride in [(1, 200, torch.float64, 4), (2, 300, torch.float32, 3)]:
+        w, g, tape, gye, gyf = _prepare(cfg, B, dtype, seed=10 + cfg, stride=stride)
+        ref_gy0, ref_gp, ref_ovf = _reference_adjoint(w, g, tape, gye, gyf)
+        code, gy0, gp, ovf = _static_adjoint(w, g, tape, gye, gyf)
+        assert code == _abi.TODE_OK, _abi.load().tode_strerror(code)
+        assert int(ovf.item()) == 0 and int(ref_ovf.item()) == 0
+        assert torch.isfinite(gy0).all()
+        assert torch.equal(gy0, ref_gy0) and torch.equal(gp, ref_gp)
+    for rep in range(2):
+        w, g, tape, gye, gyf = _prepare(4, 160, torch.float32, seed=20 + rep)
+        ref_gy0, ref_gp, ref_ovf = _reference_adjoint(w, g, tape, gye, gyf)
+        code, gy0, gp, ovf = _static_adjoint(w, g, tape, gye, gyf)
+        assert code == _abi.TODE_OK, _abi.load().tode_strerror(code)
+        assert int(ovf.item()) == 0 and int(ref_ovf.item()) == 0
+        assert torch.isfinite(gy0).all() and _finite(gp)
+        assert _rel(gy0, ref_gy0) <= 2e-3
+        assert _rel(gp, ref_gp) <= 2e-3
+
+
+def _static_code(w, g, tp, gye, gyf):
     lib = _abi.load()
     dev = g["_dev"]
     field, sol = dev["field"], g["_sol"]
+    B, D = sol.y_final.shape
     opts = api.make_options(prec=_abi.TODE_F64, rtol=w["rtol"], atol=w["atol"])
-    fd = field.desc(256, 2, [])
-    big = tape.c()
-    big.stride = 20000  # segments of 20000 steps per instance exceed the array
-    need = lib.tode_adjoint_scratch_size(C.byref(fd), C.byref(opts), C.byref(big))
-    assert need > _abi.TODE_STATIC_ADJOINT_SCRATCH_BYTES
-    gy0 = torch.zeros((256, 2), dtype=torch.float64, device="cuda")
+    fd = field.desc(B, D, [])
+    gy0 = torch.zeros((B, D), dtype=torch.float64, device="cuda")
+    gp = torch.zeros_like(field.params())
     ovf = torch.zeros(1, dtype=torch.int32, device="cuda")
+    need = lib.tode_adjoint_scratch_size(C.byref(fd), C.byref(opts), C.byref(tp))
     code = lib.tode_adjoint_static(
         C.byref(fd), C.byref(opts), _ptr(dev["t0"]), _ptr(dev["t1"]), _ptr(dev["te"]),
-        dev["te"].shape[1], _ptr(sol.n_acc), _ptr(sol.status), C.byref(big), _ptr(gye),
-        _ptr(gyf), _ptr(gy0), None, None, None, _ptr(ovf), None)
+        dev["te"].shape[1], _ptr(sol.n_acc), _ptr(sol.status), C.byref(tp), _ptr(gye),
+        _ptr(gyf), _ptr(gy0), _ptr(gp), None, None, _ptr(ovf), None)
+    torch.cuda.synchronize()
+    return code, need
+
+
+def test_static_scratch_rejects_problems_beyond_its_size():
+    # a valid strided tape (every field a re-run needs) whose segments of
+    # 20000 steps per instance need more scratch than the array holds
+    B = 256
+    w = make(1, B=B)
+    tape = tode.TapeBuffers.allocate(B, 2, torch.float64, 1, 20000, "cuda")
+    g = gpu_solve(w, torch.float64, "fused", tape=tape)
+    rng = np.random.default_rng(3)
+    gye = torch.tensor(rng.standard_normal(g["y_eval"].shape), device="cuda")
+    gyf = torch.tensor(rng.standard_normal(g["y_final"].shape), device="cuda")
+    code, need = _static_code(w, g, tape.c(), gye, gyf)
+    assert need > _abi.TODE_STATIC_ADJOINT_SCRATCH_BYTES
     assert code == _abi.TODE_EWORKSPACE
+    # an invalid tape is an argument error whatever its size: a minimal
+    # stride-1 tape (no controller state) cannot be re-run with stride 20000
+    w2, g2, tape2, gye2, gyf2 = _prepare(1, B, torch.float64, seed=4)
+    small = tode.TapeBuffers.allocate(B, 2, torch.float64, tape2.slots, 1, "cuda", minimal=True)
+    bad = small.c()
+    bad.stride = 20000
+    code, _ = _static_code(w2, g2, bad, gye2, gyf2)
+    assert code == _abi.TODE_EINVAL
