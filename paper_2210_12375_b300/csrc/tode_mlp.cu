@@ -89,7 +89,7 @@ enum : int { MLP_FUSED = 0, MLP_PLAIN_INIT = 1, MLP_PLAIN_STEP = 2 };
 // row r of the tile in tensor-memory lane r.
 template <int D_, int H_, int NL_, bool SPLIT_> struct MlpCfg {
   static constexpr int D = D_, H = H_, NL = NL_;
-  static constexpr bool SPLIT = SPLIT_, STREAM = false;
+  static constexpr bool SPLIT = SPLIT_, STREAM = false, STACKED = false;
   static constexpr int ROWS = 128, TPR = 2, NT = 256;  // rows per tile, threads per row
   static constexpr int K0 = ((D + 1 + 15) / 16) * 16;  // [y; t] padded to 16
   static constexpr int C = D / TPR;                      // state components per thread
@@ -146,7 +146,7 @@ template <int D_, int H_, int NL_, bool SPLIT_> struct MlpCfg {
 // 16-column K chunks (a 4-stage ring of bulk copies on mbarriers) every round.
 template <int D_, int H_, int NL_> struct MlpBigCfg {
   static constexpr int D = D_, H = H_, NL = NL_;
-  static constexpr bool SPLIT = true, STREAM = true;
+  static constexpr bool SPLIT = true, STREAM = true, STACKED = false;
   static constexpr int ROWS = 64, TPR = 4, NT = 256;
   static constexpr int K0 = ((D + 1 + 15) / 16) * 16;
   static constexpr int C = D / TPR;
@@ -211,6 +211,159 @@ template <int D_, int H_, int NL_> struct MlpBigCfg {
   static constexpr int S_END = S_NXT + ROWS * 4;
   static_assert(S_END <= 232448 - 1024, "shared memory");
 };
+
+// MlpWideCfg: the wide network (D = 64, H = 512, 1.2 MB of BF16 weights) on
+// full-rate M = 128 MMAs.  A tile holds 64 instances, and its activation
+// tiles stack each instance's two BF16 terms as adjacent rows: row 2r = hi,
+// row 2r + 1 = lo of instance r.  One M = 128 MMA then forms both partial
+// products (an M = 64 MMA runs at half the tensor rate: measured 128 cycles
+// for either shape), the accumulator's lanes 2r and 2r + 1 hold them, and the
+// epilogue adds the two with one lane shuffle.  The weights stream through
+// shared memory in stages of 32 KB (consecutive K chunks of one layer, one
+// bulk copy and one barrier each: per-copy completion, not bytes, paced the
+// 16 KB ring) through a 2-slot ring.
+//
+// Thread map (256 threads): warp w reads tensor-memory lane quarter w % 4
+// (stacked rows 32(w%4) .. +31 = instances 16(w%4) .. +15) and column half
+// w / 4; lane L holds instance 16(w%4) + L/2, the hi (even L) or lo (odd L)
+// product.  An instance's 16-component slices: sub = 2 (w / 4) + (L & 1).
+template <int D_, int H_, int NL_> struct MlpWideCfg {
+  static constexpr int D = D_, H = H_, NL = NL_;
+  static constexpr bool SPLIT = true, STREAM = true, STACKED = true;
+  static constexpr int ROWS = 64, TPR = 4, NT = 256;
+  static constexpr int K0 = ((D + 1 + 15) / 16) * 16;
+  static constexpr int C = D / TPR;
+  static constexpr int HC = H / TPR;
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int ACC_COL = 0, OUT_COL = 0;
+  static_assert(C == 16 && H == 512 && D == 64, "shape");
+  __device__ static int row_of(int tid) { return 16 * ((tid >> 5) & 3) + ((tid & 31) >> 1); }
+  __device__ static int sub_of(int tid) { return 2 * (tid >> 7) + (tid & 1); }
+  __host__ __device__ static constexpr int N_of(int l) { return l == NL - 1 ? D : H; }
+  __host__ __device__ static constexpr int K_of(int l) { return l == 0 ? K0 : H; }
+  __host__ __device__ static constexpr int W_bytes(int l) { return N_of(l) * K_of(l) * 2; }
+  __host__ __device__ static constexpr int W_off(int l) {
+    int o = 0;
+    for (int j = 0; j < l; ++j) o += W_bytes(j);
+    return o;
+  }
+  static constexpr int WIMG_BYTES = W_off(NL);
+  static constexpr int WREP = 16, WIMG_STRIDE = ((WIMG_BYTES + 255) / 256) * 256;
+  static constexpr int BIAS_FLOATS = (NL - 1) * H + D;
+  // weight stages: consecutive 16-column K chunks of one layer, up to 32 KB
+  static constexpr int KC = 16, NSL = 2, SLOT_BYTES = 32768;
+  __host__ __device__ static constexpr int chunk_bytes(int l) { return N_of(l) * KC * 2; }
+  __host__ __device__ static constexpr int chunks(int l) { return K_of(l) / KC; }
+  __host__ __device__ static constexpr int per_stage(int l) { return SLOT_BYTES / chunk_bytes(l); }
+  __host__ __device__ static constexpr int stages(int l) {
+    return (chunks(l) + per_stage(l) - 1) / per_stage(l);
+  }
+  __host__ __device__ static constexpr int first_stage(int l) {
+    int s = 0;
+    for (int j = 0; j < l; ++j) s += stages(j);
+    return s;
+  }
+  static constexpr int STAGES = first_stage(NL);  // per round
+  // stage g of the repeating round schedule: layer, first chunk, chunks, source
+  __device__ static void stage_of(uint32_t g, int& l, int& c0, int& nc, int& off, int& bytes) {
+    int st = (int)(g % (uint32_t)STAGES);
+    l = 0;
+    while (st >= stages(l)) st -= stages(l++);
+    c0 = st * per_stage(l);
+    nc = chunks(l) - c0 < per_stage(l) ? chunks(l) - c0 : per_stage(l);
+    bytes = nc * chunk_bytes(l);
+    off = W_off(l) + c0 * chunk_bytes(l);
+  }
+  // shared-memory carve (bytes): stacked [128][K] activation tiles
+  static constexpr int S_XH = 0, S_XL = 0;  // one stacked tile
+  static constexpr int S_HH = S_XH + 2 * ROWS * K0 * 2, S_HL = S_HH;
+  static constexpr int S_W = S_HH + 2 * ROWS * H * 2;  // the ring
+  static constexpr int S_BIAS = S_W + NSL * SLOT_BYTES;
+  static constexpr int S_RED = S_BIAS + BIAS_FLOATS * 4;
+  static constexpr int S_FIN = S_RED + TPR * ROWS * 2 * 4;
+  static constexpr int S_NXT = S_FIN + TPR * ROWS * 4;
+  static constexpr bool KSMEM = false;
+  static constexpr int S_K = 0;
+  static constexpr int S_END = S_NXT + ROWS * 4;
+  static_assert(S_END <= 232448 - 1024, "shared memory");
+  static_assert(SLOT_BYTES % chunk_bytes(0) == 0 && SLOT_BYTES % chunk_bytes(NL - 1) == 0, "stages");
+};
+
+// Stores 16 consecutive values of instance r as BF16 hi (stacked row 2r) and
+// lo (row 2r + 1) into a stacked core-matrix tile with K columns, from
+// column k0 (a multiple of 8).
+__device__ __forceinline__ void store_row16_stk(unsigned char* t, int r, int k0, int K,
+                                                const float (&v)[16]) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float a = v[c * 8 + 2 * j], b = v[c * 8 + 2 * j + 1];
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+      hw[j] = *reinterpret_cast<const uint32_t*>(&h2);
+      const float2 d = __ffma2_rn(make_float2(__low2float(h2), __high2float(h2)),
+                                  make_float2(-1.0f, -1.0f), make_float2(a, b));
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(d.x, d.y);
+      lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
+    }
+    *reinterpret_cast<uint4*>(t + tc::cm_offset(2 * r, k0 + 8 * c, K)) =
+        make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(t + tc::cm_offset(2 * r + 1, k0 + 8 * c, K)) =
+        make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
+// Lanes L and L ^ 1 of a warp hold the hi and lo products of one instance
+// for the same 16 accumulator columns; returns their sum over the 8 columns
+// this lane keeps (even lane: columns 0-7, odd lane: 8-15), hi + lo.
+__device__ __forceinline__ void combine_pair8(const float (&v)[16], int odd, float (&z)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float send = odd ? v[j] : v[8 + j];
+    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+    z[j] = odd ? recv + v[8 + j] : v[j] + recv;  // hi + lo
+  }
+}
+
+// The same pair sum over 32 columns [0,16) and [16,32) of the lane's row:
+// the even lane keeps columns 0-15, the odd lane 16-31.
+__device__ __forceinline__ void combine_pair16(const float (&v0)[16], const float (&v1)[16],
+                                               int odd, float (&z)[16]) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float send = odd ? v0[j] : v1[j];
+    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+    z[j] = odd ? recv + v1[j] : v0[j] + recv;  // hi + lo
+  }
+}
+
+// Eight values as BF16 hi and lo 16-byte rows.
+__device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo) {
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float a = v[2 * j], b = v[2 * j + 1];
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+    hw[j] = *reinterpret_cast<const uint32_t*>(&h2);
+    const float2 d = __ffma2_rn(make_float2(__low2float(h2), __high2float(h2)),
+                                make_float2(-1.0f, -1.0f), make_float2(a, b));
+    const __nv_bfloat162 l2 = __floats2bfloat162_rn(d.x, d.y);
+    lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
+  }
+  hi = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  lo = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+// Writes a lane's 8 hi and 8 lo values into a stacked tile (rows 2r, 2r+1),
+// the even lane's hi with the odd lane's lo in one store so that the warp's
+// rows cover all eight 16-byte bank groups.
+__device__ __forceinline__ void store_pair8(unsigned char* t, int r, int col, int K, int odd,
+                                            const uint4& hi, const uint4& lo) {
+  const uint4 first = odd ? lo : hi, second = odd ? hi : lo;
+  *reinterpret_cast<uint4*>(t + tc::cm_offset(2 * r + odd, col, K)) = first;
+  *reinterpret_cast<uint4*>(t + tc::cm_offset(2 * r + 1 - odd, col, K)) = second;
+}
 
 enum : int { PH_IDLE = 0, PH_INIT0 = 1, PH_INIT1 = 2, PH_STAGE = 3 };  // PH_STAGE + s - 2
 
@@ -323,7 +476,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   static_assert(C == 16, "16 state components per thread");
   // streamed weights: a ring of chunk buffers with full / empty barriers
   __shared__ __align__(8) uint64_t mbar_full[4], mbar_empty[4];
-  uint32_t g_chunk = 0;  // chunks consumed so far (thread 0)
+  uint32_t g_chunk = 0;  // chunks (stacked configs: stages) consumed so far
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = Cfg::row_of(tid), sub = Cfg::sub_of(tid);
@@ -335,7 +488,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     tc::mbar_init(&mbar_mma, 1);
     tc::mbar_init(&mbar_w, 1);
     if constexpr (Cfg::STREAM)
-      for (int b = 0; b < Cfg::NS; ++b) {
+      for (int b = 0; b < 4; ++b) {
         tc::mbar_init(&mbar_full[b], 1);
         tc::mbar_init(&mbar_empty[b], 1);
       }
@@ -344,7 +497,15 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   }
   __syncthreads();
   if (tid == 0) {
-    if constexpr (Cfg::STREAM) {
+    if constexpr (Cfg::STACKED) {
+      static_assert(Cfg::NSL <= 4, "ring barriers");
+      for (int b = 0; b < Cfg::NSL; ++b) {  // the ring starts with stages 0 .. NSL-1
+        int l_, c0_, nc_, off, bytes;
+        Cfg::stage_of((uint32_t)b, l_, c0_, nc_, off, bytes);
+        tc::mbar_expect_tx(&mbar_full[b], (uint32_t)bytes);
+        tc::bulk_g2s(sW + b * Cfg::SLOT_BYTES, wimg + off, (uint32_t)bytes, &mbar_full[b]);
+      }
+    } else if constexpr (Cfg::STREAM) {
       static_assert(Cfg::NS <= 4, "ring barriers");
       for (int b = 0; b < Cfg::NS; ++b) {  // the ring starts with chunks 0 .. NS-1
         int off, bytes;
@@ -370,9 +531,14 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     }
   }
   // zero the input tiles once (padding columns stay zero)
-  for (int j = tid; j < ROWS * K0 * 2 / 16; j += NT) {
-    reinterpret_cast<uint4*>(sXh)[j] = make_uint4(0, 0, 0, 0);
-    reinterpret_cast<uint4*>(sXl)[j] = make_uint4(0, 0, 0, 0);
+  if constexpr (Cfg::STACKED) {
+    for (int j = tid; j < 2 * ROWS * K0 * 2 / 16; j += NT)
+      reinterpret_cast<uint4*>(sXh)[j] = make_uint4(0, 0, 0, 0);
+  } else {
+    for (int j = tid; j < ROWS * K0 * 2 / 16; j += NT) {
+      reinterpret_cast<uint4*>(sXh)[j] = make_uint4(0, 0, 0, 0);
+      reinterpret_cast<uint4*>(sXl)[j] = make_uint4(0, 0, 0, 0);
+    }
   }
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base_s, Cfg::TMEM_COLS);
@@ -637,7 +803,8 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       }
       tin = (float)(s.t + cs * (double)h);
     }
-    store_row16<true>(sXh, sXl, row, coff, K0, Y);
+    if constexpr (Cfg::STACKED) store_row16_stk(sXh, row, coff, K0, Y);
+    else store_row16<true>(sXh, sXl, row, coff, K0, Y);
     if (s.phase >= PH_STAGE && s.n_acc < a.slots) {
       // tape: the stage inputs of this attempt (a retry after a rejection
       // overwrites them; the accepted attempt's stay)
@@ -650,8 +817,9 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     if (sub == TPR - 1) {  // the time input, hi + lo, in column D
       const __nv_bfloat16 th = __float2bfloat16_rn(tin);
       const __nv_bfloat16 tl = __float2bfloat16_rn(tin - __bfloat162float(th));
-      *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(row, D, K0)) = th;
-      *reinterpret_cast<__nv_bfloat16*>(sXl + tc::cm_offset(row, D, K0)) = tl;
+      const int rh = Cfg::STACKED ? 2 * row : row, rl = Cfg::STACKED ? 2 * row + 1 : row;
+      *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(rh, D, K0)) = th;
+      *reinterpret_cast<__nv_bfloat16*>(sXl + tc::cm_offset(rl, D, K0)) = tl;
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -666,7 +834,35 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       if (tid == 0 && !abort_s) {
         const uint32_t ah = tc::smem_u32(l == 0 ? sXh : sHh);
         const uint32_t al = tc::smem_u32(l == 0 ? sXl : sHl);
-        if constexpr (Cfg::STREAM) {
+        if constexpr (Cfg::STACKED) {
+          // the layer's stages: per K chunk one M = 128 MMA per N half over
+          // the stacked tile (hi and lo rows together), then a commit that
+          // frees the stage's slot; thread 32 refills it (below)
+          constexpr int NSL = Cfg::NSL;
+          const int nh = Nl > 256 ? Nl / 256 : 1, nw = Nl > 256 ? 256 : Nl;
+          const uint32_t idesc = tc::idesc_bf16_f32(128, nw);
+          const int cb = Cfg::chunk_bytes(l);
+          bool ok = true;
+          for (int st = 0; st < Cfg::stages(l) && ok; ++st) {
+            const uint32_t g = g_chunk + (uint32_t)st;
+            const int b = (int)(g % NSL);
+            ok = tc::mbar_wait(&mbar_full[b], (g / NSL) & 1u);
+            if (!ok) break;
+            int l_, c0, nc, off_, bytes_;
+            Cfg::stage_of(g, l_, c0, nc, off_, bytes_);
+            const uint32_t wb = tc::smem_u32(sW + b * Cfg::SLOT_BYTES);
+            for (int c = 0; c < nc; ++c) {
+              const int kc = c0 + c;
+              const uint64_t da = tc::smem_desc(ah + kc * 256, 128, Kl * 16);
+              for (int j = 0; j < nh; ++j) {
+                const uint64_t db = tc::smem_desc(wb + c * cb + j * (256 / 8) * 256, 128, 256);
+                tc::mma_bf16(tbase + 256 * j, da, db, idesc, kc > 0);
+              }
+            }
+            tc::mma_commit(&mbar_empty[b]);
+          }
+          if (!ok) atomicExch(&abort_s, 1);
+        } else if constexpr (Cfg::STREAM) {
           // K chunk c of layer l sits in ring slot g % NS; after issuing chunk
           // g, the slot of chunk g-1 is refilled with chunk g-1+NS once its
           // MMAs are done
@@ -715,11 +911,69 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         }
         tc::mma_commit(&mbar_mma);
       }
-      const bool ok = tc::mbar_wait(&mbar_mma, mma_parity);
+      if constexpr (Cfg::STACKED) {
+        if (tid == 32 && !abort_s) {
+          // producer: the slot of stage g takes stage g + NSL once the MMAs
+          // that read it are done (a thread of its own, so the issuer never
+          // waits on a copy it could have started earlier)
+          constexpr int NSL = Cfg::NSL;
+          bool ok = true;
+          for (int st = 0; st < Cfg::stages(l) && ok; ++st) {
+            const uint32_t g = g_chunk + (uint32_t)st;
+            const int b = (int)(g % NSL);
+            ok = tc::mbar_wait(&mbar_empty[b], (g / NSL) & 1u);
+            if (!ok) break;
+            int l2, c2, n2, off, bytes;
+            Cfg::stage_of(g + NSL, l2, c2, n2, off, bytes);
+            tc::mbar_expect_tx(&mbar_full[b], (uint32_t)bytes);
+            tc::bulk_g2s(sW + b * Cfg::SLOT_BYTES, wimg + off, (uint32_t)bytes, &mbar_full[b]);
+          }
+          if (!ok) atomicExch(&abort_s, 1);
+        }
+        g_chunk += (uint32_t)Cfg::stages(l);
+        __syncwarp();  // the other lanes of warps 0 and 1 wait for the issuer / producer here
+      }
+      const bool ok = Cfg::STACKED ? tc::mbar_wait_sleep(&mbar_mma, mma_parity)
+                                   : tc::mbar_wait(&mbar_mma, mma_parity);
       mma_parity ^= 1u;
       if (!ok) atomicExch(&abort_s, 1);
       tc::fence_after_sync();
-      if (l < NL - 1) {
+      if constexpr (Cfg::STACKED) {
+        if (l < NL - 1) {
+          // hidden epilogue on the stacked accumulator: the pair sum of the
+          // hi and lo rows, bias, tanh, BF16 hi + lo into the stacked tile
+          const float* bl = sBias + l * H;
+          const int lane = tid & 31, odd = lane & 1, hf = warp >> 2;
+          const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+#pragma unroll 1
+          for (int c = 0; c < 256; c += 32) {
+            float v0[16], v1[16];
+            tc::tmem_ld16(tbase + lanes + 256 * hf + c, v0);
+            tc::tmem_ld16(tbase + lanes + 256 * hf + c + 16, v1);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              float z[8];
+              combine_pair8(u == 0 ? v0 : v1, odd, z);
+              const int col = 256 * hf + c + 16 * u + 8 * odd;
+              const float4 b0 = *reinterpret_cast<const float4*>(bl + col);
+              const float4 b1 = *reinterpret_cast<const float4*>(bl + col + 4);
+              const float2 t0 = tanh_acc2(__fadd2_rn(make_float2(z[0], z[1]), make_float2(b0.x, b0.y)));
+              const float2 t1 = tanh_acc2(__fadd2_rn(make_float2(z[2], z[3]), make_float2(b0.z, b0.w)));
+              const float2 t2 = tanh_acc2(__fadd2_rn(make_float2(z[4], z[5]), make_float2(b1.x, b1.y)));
+              const float2 t3 = tanh_acc2(__fadd2_rn(make_float2(z[6], z[7]), make_float2(b1.z, b1.w)));
+              const float hv[8] = {t0.x, t0.y, t1.x, t1.y, t2.x, t2.y, t3.x, t3.y};
+              uint4 hi, lo;
+              split8(hv, hi, lo);
+              store_pair8(sHh, row, col, H, odd, hi, lo);
+            }
+          }
+          tc::fence_proxy_async();
+          tc::fence_before_sync();
+          __syncthreads();
+          tc::fence_after_sync();
+        }
+      } else if (l < NL - 1) {
         // hidden epilogue: bias, tanh, BF16 (split) into the hidden tile
         const float* bl = sBias + l * H;
         // the accumulator loads of up to four 16-column chunks in flight
@@ -763,7 +1017,18 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     }
     // ---- output: f for this thread's components
     float f[16];
-    {
+    if constexpr (Cfg::STACKED) {
+      // output columns [32 hf, 32 hf + 32) of the lane's stacked row, pair-summed
+      float v0[16], v1[16], z[16];
+      const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+      tc::tmem_ld16(tbase + lanes + 32 * (warp >> 2), v0);
+      tc::tmem_ld16(tbase + lanes + 32 * (warp >> 2) + 16, v1);
+      tc::tmem_wait_ld();
+      combine_pair16(v0, v1, tid & 1, z);
+      const float* bo = sBias + (NL - 1) * H;
+#pragma unroll
+      for (int r = 0; r < C; ++r) f[r] = z[r] + bo[coff + r];
+    } else {
       float v[16];
       Cfg::out_ld(tbase, tid, v);
       tc::tmem_wait_ld();
@@ -1000,7 +1265,16 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       }
     }
   }
-  if constexpr (Cfg::STREAM) {
+  if constexpr (Cfg::STACKED) {
+    if (tid == 0) {
+      // the ring's copies still in flight land before the CTA exits
+      // (stages g_chunk .. g_chunk + NSL - 1 were issued and not consumed)
+      constexpr uint32_t NSL = Cfg::NSL;
+      const uint32_t first = g_chunk, last = g_chunk + NSL - 1;
+      for (uint32_t x = first; x <= last; ++x)
+        if (!tc::mbar_wait(&mbar_full[x % NSL], (x / NSL) & 1u)) atomicExch(&abort_s, 1);
+    }
+  } else if constexpr (Cfg::STREAM) {
     if (tid == 0) {
       // the ring's copies still in flight land before the CTA exits
       const uint32_t first = g_chunk, last = g_chunk == 0 ? Cfg::NS - 1 : g_chunk + Cfg::NS - 2;
@@ -2252,6 +2526,7 @@ static tode_err smem_optin(const void* fn, int bytes, std::atomic<uint64_t>& don
 using Cfg32 = MlpCfg<32, 128, 3, false>;
 using Cfg32s = MlpCfg<32, 128, 3, true>;
 using Cfg64w = MlpBigCfg<64, 512, 4>;
+using Cfg64s = MlpWideCfg<64, 512, 4>;  // the wide network's solver (stacked M = 128 tiles)
 
 // the two networks the MLP field is built for
 static bool is_d32_h128(const tode_field_desc* f) {
@@ -2410,7 +2685,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
 tode_err mlp_solve(const SolveReq& r, bool split) {
   if (r.o->form != TODE_FUSED && r.o->form != TODE_PLAIN) return TODE_EUNSUPPORTED;
   if (r.tape && r.tape->stride != 1) return TODE_EUNSUPPORTED;
-  if (is_d64_h512(r.f)) return split ? launch_mlp<Cfg64w>(r) : TODE_EUNSUPPORTED;
+  if (is_d64_h512(r.f)) return split ? launch_mlp<Cfg64s>(r) : TODE_EUNSUPPORTED;
   return split ? launch_mlp<Cfg32s>(r) : launch_mlp<Cfg32>(r);
 }
 

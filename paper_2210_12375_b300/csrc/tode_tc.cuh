@@ -179,6 +179,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity,
   }
   return true;
 }
+// try_wait with a suspend-time hint (ns): a thread whose phase has not
+// completed sleeps up to the hint instead of spinning, so threads that wait
+// out a whole GEMM chain leave the issue slots to the ones that work.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* mbar, uint32_t parity,
+                                                   uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
+      "selp.b32 %0, 1, 0, P;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(mbar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return done != 0;
+}
+// As mbar_wait, sleeping between polls (for waits that span many MMAs).
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* mbar, uint32_t parity,
+                                                long long budget = 2000000000LL) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait_hint(mbar, parity, 200)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
                "r"(bytes)
