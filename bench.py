@@ -619,11 +619,11 @@ def run_tode(args):
     # for the MLP; for the SIMT fields the work-order sort when the launch
     # orders longest first) and the adjoint (SIMT fields: the longest-first
     # sort and the reverse sweep; MLP D=32: image, adjoint, ordered dW
-    # reduction; wide MLP: two images, a fill, one adjoint per batch slice and
-    # a copy -- the weight-gradient GEMMs are cuBLAS's).  The sort is one
-    # launch up to 2048 instances, three above.
+    # reduction; wide MLP: two images, the stable work order, per batch slice
+    # the reverse sweep and the weight-gradient products, and their ordered
+    # reduction).  The sort is one launch up to 2048 instances, three above.
     if mlp:
-        adj = (3 + -(-B // (148 * 64)) + 1) if D == 64 else 3
+        adj = (4 + 2 * -(-B // (148 * 64))) if D == 64 else 3
         gpu_launches = 2 + (adj if with_adjoint else 0)
     else:
         sort = 1 if B <= 2048 else 3

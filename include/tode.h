@@ -13,11 +13,8 @@
  * Conventions for every entry point:
  *  - Pointers are DEVICE pointers unless marked "host".  The caller owns and
  *    allocates every buffer (inputs, outputs, workspace, tape, scratch); the
- *    library never allocates or frees device memory, with one exception: the
- *    wide MLP field's adjoint (D = 64, three layers of 512) computes its
- *    weight gradients with cuBLAS GEMMs, and cuBLAS creates one handle per
- *    device on first use (its workspace is carved from the caller's
- *    scratch).  Make that first call before any stream capture.
+ *    library never allocates or frees device memory and calls no library
+ *    that does.
  *  - Calls enqueue work on `stream` (a cudaStream_t, NULL = legacy default)
  *    and return.  Outputs are valid once the stream has synchronised.  The
  *    plain form (TODE_PLAIN) additionally synchronises `stream` every
@@ -244,8 +241,11 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
 
 /* Bytes of device scratch tode_adjoint needs (256-byte aligned base).  For
  * the MLP field it depends on the current device's SM count and, for the
- * wide network, on tape->slots (the reverse rounds are staged per batch
- * slice of SMs x 64 instances). */
+ * wide network, on tape->slots: its reverse rounds stage the layer inputs
+ * and cotangents of every (instance, step, stage) for the weight-gradient
+ * products, one batch slice of SMs x 64 instances at a time, 7 * slots
+ * rounds of 64 rows per SM (about 0.8 MB per round; gigabytes for a few
+ * thousand-step slices). */
 size_t tode_adjoint_scratch_size(const tode_field_desc* f, const tode_options* o,
                                  const tode_tape* tape);
 

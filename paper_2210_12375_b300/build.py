@@ -2,8 +2,7 @@
 
 Every translation unit is compiled separately (the FP64 one with
 ``-fmad=false``) and linked into one shared library with the CUDA runtime
-linked statically (cuBLAS, dynamically linked, serves the plain weight-gradient
-GEMMs of the wide MLP adjoint).  Rebuilds only what changed.
+linked statically; no other library is linked.  Rebuilds only what changed.
 """
 from __future__ import annotations
 
@@ -60,7 +59,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
         changed = True
     if changed or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lcublas"]
+        cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs,]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)

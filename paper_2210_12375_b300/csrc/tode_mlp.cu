@@ -28,11 +28,8 @@
 
 #include <cuda_bf16.h>
 
-#include <cublas_v2.h>
-
 #include <algorithm>
 #include <atomic>
-#include <mutex>
 
 namespace tode {
 
@@ -137,79 +134,6 @@ template <int D_, int H_, int NL_, bool SPLIT_> struct MlpCfg {
   static_assert(S_END <= 232448 - 1024, "shared memory");
   static_assert(D % 32 == 0 && H % 32 == 0 && NL >= 2 && NL <= MLP_MAX_LAYERS, "shape");
   static_assert(H <= 256 && D <= 256, "one MMA per layer and K slice");
-};
-
-// MlpBigCfg: the wide network (H = 512; 1.2 MB of BF16 weights).  Split
-// activations of 128 rows would need 256 KB, so a tile has 64 rows (M = 64
-// MMAs: row m of the tile lands in tensor-memory lane (m/16)*32 + m%16), four
-// threads per row.  The weights are streamed through shared memory in
-// 16-column K chunks (a 4-stage ring of bulk copies on mbarriers) every round.
-template <int D_, int H_, int NL_> struct MlpBigCfg {
-  static constexpr int D = D_, H = H_, NL = NL_;
-  static constexpr bool SPLIT = true, STREAM = true, STACKED = false;
-  static constexpr int ROWS = 64, TPR = 4, NT = 256;
-  static constexpr int K0 = ((D + 1 + 15) / 16) * 16;
-  static constexpr int C = D / TPR;
-  static constexpr int HC = H / TPR;
-  static constexpr int TMEM_COLS = 512;
-  static constexpr int ACC_COL = 0, OUT_COL = 0;  // the output reuses the hidden accumulator
-  static_assert(C == 16 && H == 512 && D <= 256 && HC % 16 == 0, "shape");
-  // warp w reads lane quarter w%4 (rows 16*(w%4) .. +15 in lanes 0-15); lanes
-  // 0-15 and 16-31 of the warp take different column ranges of the same rows
-  __device__ static int row_of(int tid) { return 16 * ((tid >> 5) & 3) + (tid & 15); }
-  __device__ static int sub_of(int tid) { return 2 * (tid >> 7) + ((tid >> 4) & 1); }
-  __device__ static void hid_ld(uint32_t tbase, int tid, int c, float (&v)[16]) {
-    const uint32_t lanes = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
-    tc::tmem_ld16x2<HC>(tbase + lanes + ACC_COL + (tid >> 7) * 2 * HC + c, v);
-  }
-  __device__ static void out_ld(uint32_t tbase, int tid, float (&v)[C]) {
-    const uint32_t lanes = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
-    tc::tmem_ld16x2<C>(tbase + lanes + OUT_COL + (tid >> 7) * 2 * C, v);
-  }
-  // layer l: N_l x K_l, image = K chunks of [N_l][16] core-matrix tiles
-  __host__ __device__ static constexpr int N_of(int l) { return l == NL - 1 ? D : H; }
-  __host__ __device__ static constexpr int K_of(int l) { return l == 0 ? K0 : H; }
-  __host__ __device__ static constexpr int W_bytes(int l) { return N_of(l) * K_of(l) * 2; }
-  __host__ __device__ static constexpr int W_off(int l) {
-    int o = 0;
-    for (int j = 0; j < l; ++j) o += W_bytes(j);
-    return o;
-  }
-  static constexpr int WIMG_BYTES = W_off(NL);
-  // every CTA streams the same chunks at about the same time; CTAs read one
-  // of WREP copies of the image so the requests spread over the L2 slices
-  static constexpr int WREP = 16, WIMG_STRIDE = ((WIMG_BYTES + 255) / 256) * 256;
-  static constexpr int BIAS_FLOATS = (NL - 1) * H + D;
-  static constexpr int KC = 16, NS = 4;                       // chunk K, ring stages
-  static constexpr int STAGE_BYTES = H * KC * 2;             // the largest chunk
-  __host__ __device__ static constexpr int chunks(int l) { return K_of(l) / KC; }
-  __host__ __device__ static constexpr int chunks_per_round() {
-    int n = 0;
-    for (int l = 0; l < NL; ++l) n += chunks(l);
-    return n;
-  }
-  // global chunk index -> image offset and size
-  __device__ static void chunk_src(uint32_t g, int& off, int& bytes) {
-    int c = (int)(g % (uint32_t)chunks_per_round());
-    int l = 0;
-    while (c >= chunks(l)) c -= chunks(l++);
-    bytes = N_of(l) * KC * 2;
-    off = W_off(l) + c * bytes;
-  }
-  // shared-memory carve (bytes)
-  static constexpr int S_XH = 0;
-  static constexpr int S_XL = S_XH + ROWS * K0 * 2;
-  static constexpr int S_HH = S_XL + ROWS * K0 * 2;
-  static constexpr int S_HL = S_HH + ROWS * H * 2;
-  static constexpr int S_W = S_HL + ROWS * H * 2;  // the chunk ring
-  static constexpr int S_BIAS = S_W + NS * STAGE_BYTES;
-  static constexpr int S_RED = S_BIAS + BIAS_FLOATS * 4;
-  static constexpr int S_FIN = S_RED + TPR * ROWS * 2 * 4;
-  static constexpr int S_NXT = S_FIN + TPR * ROWS * 4;
-  static constexpr bool KSMEM = false;  // no room: the stage derivatives stay in the thread
-  static constexpr int S_K = 0;
-  static constexpr int S_END = S_NXT + ROWS * 4;
-  static_assert(S_END <= 232448 - 1024, "shared memory");
 };
 
 // MlpWideCfg: the wide network (D = 64, H = 512, 1.2 MB of BF16 weights) on
@@ -504,14 +428,6 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         Cfg::stage_of((uint32_t)b, l_, c0_, nc_, off, bytes);
         tc::mbar_expect_tx(&mbar_full[b], (uint32_t)bytes);
         tc::bulk_g2s(sW + b * Cfg::SLOT_BYTES, wimg + off, (uint32_t)bytes, &mbar_full[b]);
-      }
-    } else if constexpr (Cfg::STREAM) {
-      static_assert(Cfg::NS <= 4, "ring barriers");
-      for (int b = 0; b < Cfg::NS; ++b) {  // the ring starts with chunks 0 .. NS-1
-        int off, bytes;
-        Cfg::chunk_src((uint32_t)b, off, bytes);
-        tc::mbar_expect_tx(&mbar_full[b], (uint32_t)bytes);
-        tc::bulk_g2s(sW + b * Cfg::STAGE_BYTES, wimg + off, (uint32_t)bytes, &mbar_full[b]);
       }
     } else {
       tc::mbar_expect_tx(&mbar_w, (uint32_t)Cfg::WIMG_BYTES);
@@ -860,40 +776,6 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
               }
             }
             tc::mma_commit(&mbar_empty[b]);
-          }
-          if (!ok) atomicExch(&abort_s, 1);
-        } else if constexpr (Cfg::STREAM) {
-          // K chunk c of layer l sits in ring slot g % NS; after issuing chunk
-          // g, the slot of chunk g-1 is refilled with chunk g-1+NS once its
-          // MMAs are done
-          constexpr int NS = Cfg::NS;
-          const int nh = Nl > 256 ? Nl / 256 : 1, nw = Nl > 256 ? 256 : Nl;
-          const uint32_t idesc = tc::idesc_bf16_f32(ROWS, nw);
-          bool ok = true;
-          for (int c = 0; c < Kl / Cfg::KC && ok; ++c, ++g_chunk) {
-            const int b = (int)(g_chunk % NS);
-            ok = tc::mbar_wait(&mbar_full[b], (g_chunk / NS) & 1u);
-            if (!ok) break;
-            const uint32_t wb = tc::smem_u32(sW + b * Cfg::STAGE_BYTES);
-            const uint64_t dh = tc::smem_desc(ah + c * 256, 128, Kl * 16);
-            const uint64_t dl = tc::smem_desc(al + c * 256, 128, Kl * 16);
-            for (int j = 0; j < nh; ++j) {
-              const uint64_t db = tc::smem_desc(wb + j * (256 / 8) * 256, 128, 256);
-              tc::mma_bf16(tbase + dcol + 256 * j, dh, db, idesc, c > 0);
-              tc::mma_bf16(tbase + dcol + 256 * j, dl, db, idesc, true);
-            }
-            tc::mma_commit(&mbar_empty[b]);
-            if (g_chunk >= 1) {
-              const uint32_t gp = g_chunk - 1;
-              const int pb = (int)(gp % NS);
-              ok = tc::mbar_wait(&mbar_empty[pb], (gp / NS) & 1u);
-              if (!ok) break;
-              int off, bytes;
-              Cfg::chunk_src(gp + NS, off, bytes);
-              tc::mbar_expect_tx(&mbar_full[pb], (uint32_t)bytes);
-              tc::bulk_g2s(sW + pb * Cfg::STAGE_BYTES, wimg + off, (uint32_t)bytes,
-                           &mbar_full[pb]);
-            }
           }
           if (!ok) atomicExch(&abort_s, 1);
         } else {
@@ -1273,13 +1155,6 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       const uint32_t first = g_chunk, last = g_chunk + NSL - 1;
       for (uint32_t x = first; x <= last; ++x)
         if (!tc::mbar_wait(&mbar_full[x % NSL], (x / NSL) & 1u)) atomicExch(&abort_s, 1);
-    }
-  } else if constexpr (Cfg::STREAM) {
-    if (tid == 0) {
-      // the ring's copies still in flight land before the CTA exits
-      const uint32_t first = g_chunk, last = g_chunk == 0 ? Cfg::NS - 1 : g_chunk + Cfg::NS - 2;
-      for (uint32_t x = first; x <= last; ++x)
-        if (!tc::mbar_wait(&mbar_full[x % Cfg::NS], (x / Cfg::NS) & 1u)) atomicExch(&abort_s, 1);
     }
   }
   if (abort_s && tid == 0) atomicExch(a.err, 1);
@@ -1941,159 +1816,161 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 
 // ======================================================================
 // Discrete adjoint of the wide MLP field (D = 64, three tanh layers of
-// 512; App. A).  Same schedule as k_mlp_adjoint -- rows reverse their own
-// instances, 7 lockstep rounds per accepted step, stage inputs from the tape
-// -- on 64-row tiles with the weights streamed through a chunk ring.  The reverse rounds need the
-// transposed weights too (W_l^T, K chunks along the layer's outputs).
+// 512; App. A), on the stacked M = 128 tiles of MlpWideCfg.
 //
-// The weight gradients do not fit in tensor memory (two 512 x 512 layers),
-// so every reverse round writes the rows of its layer inputs (X, h1, h2, h3)
-// and of its pre-activation cotangents (delta1, delta2, delta3, kbar), as
-// BF16 hi + lo, to a staging area; dW_l = delta_l^T act_l and the bias sums
-// are then plain GEMMs over the staged rows (mlp_wide_dw).
+// Rows of a 64-instance tile reverse their own instances, 7 lockstep
+// rounds per accepted step (stages 7..1) from the recorded stage inputs.
+// A round runs the hidden layers at Y_s (forward weight chunks) and then
+// the backward chain for the stage cotangent kbar_s (transposed chunks):
+//   gh3 = kbar W4     delta3 = gh3 (1 - h3^2)
+//   gh2 = delta3 W3   delta2 = gh2 (1 - h2^2)
+//   gh1 = delta2 W2   delta1 = gh1 (1 - h1^2)
+//   gx  = delta1 W1   (the state part of the stage's cotangent)
+// The weight gradients dW_l = delta_l^T act_l sum over every reversed
+// (instance, step, stage).  Two 512 x 512 products do not fit in tensor
+// memory, so every round stages its 64 rows of act_l (X = [Y; t; 1], h1,
+// h2, h3) and delta_l (delta1..3, kbar) as BF16 hi + lo in the layout the
+// tensor cores read -- MN-major core-matrix blocks of 64 rows x (up to) 128
+// features -- and k_mlp_dw forms the products from them afterwards.  A row
+// whose instance is done runs on zeros: its kbar and hence every delta is
+// 0, so its staged rows add nothing.
 // ======================================================================
-template <class Cfg> struct WideAdjLayout {
+template <class Cfg> struct WideAdj {
   static constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, ROWS = Cfg::ROWS;
   static_assert(Cfg::NL == 4 && D == 64 && H == 512 && K0 == 80 && ROWS == 64, "network");
-  static constexpr int NS = 3;                         // ring stages
-  static constexpr int STAGE_BYTES = 16 * H * 2;      // the largest chunk (16 x 512)
-  static constexpr int S_XH = 0;
-  static constexpr int S_XL = S_XH + ROWS * K0 * 2;
-  static constexpr int S_HH = S_XL + ROWS * K0 * 2;   // the hidden / delta tile
-  static constexpr int S_HL = S_HH + ROWS * H * 2;
-  static constexpr int S_KH = S_HL + ROWS * H * 2;    // kbar tile
-  static constexpr int S_KL = S_KH + ROWS * D * 2;
-  static constexpr int S_W = S_KL + ROWS * D * 2;     // chunk ring
-  static constexpr int S_BIAS = S_W + NS * STAGE_BYTES;
+  static constexpr int NSL = 2, SLOT_BYTES = 32768;
+  // shared memory: the stacked input tile [128][K0] (after the first layer
+  // the stacked kbar tile [128][D] in the same place), the stacked hidden /
+  // delta tile [128][H], the weight ring, the biases
+  static constexpr int S_X = 0;
+  static constexpr int S_H = S_X + 2 * ROWS * K0 * 2;
+  static constexpr int S_W = S_H + 2 * ROWS * H * 2;
+  static constexpr int S_BIAS = S_W + NSL * SLOT_BYTES;
   static constexpr int S_END = S_BIAS + Cfg::BIAS_FLOATS * 4;
   static_assert(S_END <= 232448 - 1024, "shared memory");
-  // transposed image: layer l, chunk c = outputs [16c, 16c+16) as an MN-major
-  // [16][IN_l] core-matrix tile
-  __host__ __device__ static constexpr int IN_of(int l) { return Cfg::K_of(l); }
-  __host__ __device__ static constexpr int T_bytes(int l) { return Cfg::N_of(l) * IN_of(l) * 2; }
-  __host__ __device__ static constexpr int T_off(int l) {
-    int o = 0;
-    for (int j = 0; j < l; ++j) o += T_bytes(j);
-    return o;
+  // the round's weight stream: segments 0-2 the forward chunks of layers
+  // 0-2 ([N][16] K-major), segments 3-6 the transposed chunks of layers 3,
+  // 2, 1, 0 ([16 outputs][K] MN-major); both images hold layer l at W_off(l)
+  static constexpr int NSEG = 7;
+  __host__ __device__ static constexpr int seg_layer(int q) { return q < 3 ? q : 6 - q; }
+  __host__ __device__ static constexpr bool seg_tr(int q) { return q >= 3; }
+  __host__ __device__ static constexpr int seg_chunk_bytes(int q) {
+    return q < 3 ? Cfg::N_of(q) * 16 * 2 : 16 * Cfg::K_of(seg_layer(q)) * 2;
   }
-  static constexpr int TIMG_BYTES = T_off(Cfg::NL);
-  static constexpr int TIMG_STRIDE = ((TIMG_BYTES + 255) / 256) * 256;
-  // chunk schedule of a reverse round: forward layers 0..2, then the
-  // transposed layers 3, 2, 1, 0
-  static constexpr int REV_CHUNKS = 5 + 32 + 32 + 4 + 32 + 32 + 32;
-  // global chunk index -> (transposed?, layer, chunk) -> image offset, bytes
-  __device__ static void chunk_src(uint32_t g, bool& tr, int& off, int& bytes) {
-    int p = (int)(g % (uint32_t)REV_CHUNKS);
-    const int cnt[7] = {5, 32, 32, 4, 32, 32, 32};
-    const int lay[7] = {0, 1, 2, 3, 2, 1, 0};
-    int k = 0;
-    while (p >= cnt[k]) p -= cnt[k++];
-    const int l = lay[k];
-    if (k < 3) {
-      tr = false;
-      bytes = Cfg::N_of(l) * 32;
-      off = Cfg::W_off(l) + p * bytes;
-    } else {
-      tr = true;
-      bytes = 16 * IN_of(l) * 2;
-      off = T_off(l) + p * bytes;
-    }
+  __host__ __device__ static constexpr int seg_chunks(int q) {
+    return q < 3 ? Cfg::K_of(q) / 16 : Cfg::N_of(seg_layer(q)) / 16;
+  }
+  __host__ __device__ static constexpr int seg_per_stage(int q) {
+    return SLOT_BYTES / seg_chunk_bytes(q);
+  }
+  __host__ __device__ static constexpr int seg_stages(int q) {
+    return (seg_chunks(q) + seg_per_stage(q) - 1) / seg_per_stage(q);
+  }
+  __host__ __device__ static constexpr int stages() {
+    int s = 0;
+    for (int q = 0; q < NSEG; ++q) s += seg_stages(q);
+    return s;
+  }
+  __device__ static void stage_of(uint32_t g, int& q, int& c0, int& nc, int& off, int& bytes) {
+    int st = (int)(g % (uint32_t)stages());
+    q = 0;
+    while (st >= seg_stages(q)) st -= seg_stages(q++);
+    c0 = st * seg_per_stage(q);
+    nc = seg_chunks(q) - c0 < seg_per_stage(q) ? seg_chunks(q) - c0 : seg_per_stage(q);
+    bytes = nc * seg_chunk_bytes(q);
+    off = Cfg::W_off(seg_layer(q)) + c0 * seg_chunk_bytes(q);
+  }
+  // staged tensors; each splits into planes of (up to) 128 features, and a
+  // plane holds one block pair (hi, lo) per (chain CTA, reverse round)
+  enum { T_X = 0, T_H1 = 1, T_H2 = 2, T_H3 = 3, T_D1 = 4, T_D2 = 5, T_D3 = 6, T_K = 7, NTEN = 8 };
+  __host__ __device__ static constexpr int fb_width(int t) {
+    return t == T_X ? K0 : t == T_K ? D : 128;
+  }
+  __host__ __device__ static constexpr int t_fb(int t) { return t == T_X || t == T_K ? 1 : H / 128; }
+  __host__ __device__ static constexpr int blk_bytes(int t) { return ROWS * fb_width(t) * 2; }
+  __host__ __device__ static constexpr int plane_first(int t) {
+    int p = 0;
+    for (int j = 0; j < t; ++j) p += t_fb(j);
+    return p;
+  }
+  static constexpr int NPLANES = plane_first(NTEN);
+  // byte offset of 8 features [m, m+8) of row r inside a block of width F
+  __host__ __device__ static constexpr uint32_t blk_off(int r, int m, int F) {
+    return (uint32_t)((r >> 3) * F * 16 + (m >> 3) * 128 + (r & 7) * 16);
   }
 };
 
 struct WideAdjArgs {
-  int i0, B, K;  // the slice: instances i0 .. i0+B-1 of the batch
+  int i0, B, K;                  // the slice: queue positions i0 .. i0+B-1
+  const int32_t* order;          // queue position -> instance (most accepted steps first)
   const double* t0;
   const double* t1;
   const double* te;
   const int32_t* n_acc;
   const int32_t* status;
-  int slots, Btot;
+  int slots;
   const float* tp_y;
-  const float* tp_k1;
   const double* tp_t;
   const float* tp_h;
+  const float* tp_ys;            // [B][slots][6][D]: Y_2..Y_7
   const float* gye;
   const float* gyf;
   float* gy0;
-  const unsigned char* wimg;  // forward chunk image (copies WIMG_STRIDE apart)
-  const unsigned char* timg;  // transposed chunk image (copies TIMG_STRIDE apart)
+  const unsigned char* wimg;     // forward chunk image (copies WIMG_STRIDE apart)
+  const unsigned char* timg;     // transposed chunk image (same strides)
   const float* bias[MLP_MAX_LAYERS];
-  // staging: rows (c*cap + round)*64 + row; hi and lo planes
-  uint16_t* sa[4][2];  // X [80], h1, h2, h3 [512]
-  uint16_t* sg[4][2];  // delta1, delta2, delta3 [512], kbar [64]
-  int cap;             // reverse rounds per CTA
-  const float* tp_ys;  // [Btot][slots][6][D]: Y_2..Y_7
+  unsigned char* plane[32];      // staging planes (WideAdj::NPLANES used)
+  int cap;                       // reverse rounds per CTA the planes hold
+  int32_t* rounds;               // [grid]: reverse rounds staged by each CTA
   int32_t* overflow;
   int32_t* err;
 };
 
-// Stores 16 values of a row as BF16 hi / lo into two row-major planes.
-__device__ __forceinline__ void stage_row16(uint16_t* hp, uint16_t* lp, size_t off,
-                                            const float (&v)[16]) {
+// 8 floats from a BF16 hi + lo pair of 16-byte rows
+__device__ __forceinline__ void unsplit8(const uint4& hi, const uint4& lo, float (&v)[8]) {
+  const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    uint32_t hw[4], lw[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float a0 = v[c * 8 + 2 * j], b0 = v[c * 8 + 2 * j + 1];
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, b0);
-      const __nv_bfloat162 l2 = __floats2bfloat162_rn(a0 - __low2float(h2), b0 - __high2float(h2));
-      hw[j] = *reinterpret_cast<const uint32_t*>(&h2);
-      lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
-    }
-    *reinterpret_cast<uint4*>(hp + off + 8 * c) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    *reinterpret_cast<uint4*>(lp + off + 8 * c) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-  }
-}
-// 16 values hi + lo of a staged row, as floats
-__device__ __forceinline__ void unstage_row16(const uint16_t* hp, const uint16_t* lp, size_t off,
-                                              float (&v)[16]) {
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const uint4 h = *reinterpret_cast<const uint4*>(hp + off + 8 * c);
-    const uint4 l = *reinterpret_cast<const uint4*>(lp + off + 8 * c);
-    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
-      const __nv_bfloat162 l2 = *reinterpret_cast<const __nv_bfloat162*>(&lw[j]);
-      v[c * 8 + 2 * j] = __low2float(h2) + __low2float(l2);
-      v[c * 8 + 2 * j + 1] = __high2float(h2) + __high2float(l2);
-    }
+  for (int j = 0; j < 4; ++j) {
+    const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
+    const __nv_bfloat162 l2 = *reinterpret_cast<const __nv_bfloat162*>(&lw[j]);
+    v[2 * j] = __low2float(h2) + __low2float(l2);
+    v[2 * j + 1] = __high2float(h2) + __high2float(l2);
   }
 }
 
 template <class Cfg>
 __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
-  using L = WideAdjLayout<Cfg>;
+  using L = WideAdj<Cfg>;
   using Cc = DP5;
-  constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, HC = Cfg::HC, ROWS = 64;
-  constexpr int NS = L::NS;
+  constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, ROWS = Cfg::ROWS;
+  constexpr int NSL = L::NSL;
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mbar_mma, mbar_full[NS], mbar_empty[NS];
+  __shared__ __align__(8) uint64_t mbar_mma, mbar_full[NSL], mbar_empty[NSL];
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
-  unsigned char* sXh = sm + L::S_XH;
-  unsigned char* sXl = sm + L::S_XL;
-  unsigned char* sHh = sm + L::S_HH;
-  unsigned char* sHl = sm + L::S_HL;
-  unsigned char* sKh = sm + L::S_KH;
-  unsigned char* sKl = sm + L::S_KL;
+  unsigned char* sX = sm + L::S_X;  // input tile, then the kbar tile
+  unsigned char* sH = sm + L::S_H;
   unsigned char* sW = sm + L::S_W;
   float* sBias = reinterpret_cast<float*>(sm + L::S_BIAS);
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, odd = lane & 1, hf = warp >> 2;
   const int row = Cfg::row_of(tid), sub = Cfg::sub_of(tid);
   const int coff = sub * C;
-  const int grid = gridDim.x;
+  const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
   const unsigned char* wimg = a.wimg + (size_t)(blockIdx.x % Cfg::WREP) * Cfg::WIMG_STRIDE;
-  const unsigned char* timg = a.timg + (size_t)(blockIdx.x % Cfg::WREP) * L::TIMG_STRIDE;
-  uint32_t g_chunk = 0;
+  const unsigned char* timg = a.timg + (size_t)(blockIdx.x % Cfg::WREP) * Cfg::WIMG_STRIDE;
+  uint32_t g_stage = 0;  // weight stages consumed so far
 
+  auto issue_stage = [&](uint32_t g, int slot) {
+    int q, c0, nc, off, bytes;
+    L::stage_of(g, q, c0, nc, off, bytes);
+    tc::mbar_expect_tx(&mbar_full[slot], (uint32_t)bytes);
+    tc::bulk_g2s(sW + slot * L::SLOT_BYTES, (L::seg_tr(q) ? timg : wimg) + off, (uint32_t)bytes,
+                 &mbar_full[slot]);
+  };
   if (tid == 0) {
     tc::mbar_init(&mbar_mma, 1);
-    for (int b = 0; b < NS; ++b) {
+    for (int b = 0; b < NSL; ++b) {
       tc::mbar_init(&mbar_full[b], 1);
       tc::mbar_init(&mbar_empty[b], 1);
     }
@@ -2101,34 +1978,20 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  auto issue_copy = [&](uint32_t g, int slot) {
-    bool tr;
-    int off, bytes;
-    L::chunk_src(g, tr, off, bytes);
-    tc::mbar_expect_tx(&mbar_full[slot], (uint32_t)bytes);
-    tc::bulk_g2s(sW + slot * L::STAGE_BYTES, (tr ? timg : wimg) + off, (uint32_t)bytes,
-                 &mbar_full[slot]);
-  };
   if (tid == 0)
-    for (int b = 0; b < NS; ++b) issue_copy((uint32_t)b, b);
+    for (int b = 0; b < NSL; ++b) issue_stage((uint32_t)b, b);
   {
     int o = 0;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-      const int n = Cfg::N_of(l);
-      for (int j = tid; j < n; j += 256) sBias[o + j] = a.bias[l] ? a.bias[l][j] : 0.0f;
-      o += n;
+      const int nn = Cfg::N_of(l);
+      for (int j = tid; j < nn; j += 256) sBias[o + j] = a.bias[l] ? a.bias[l][j] : 0.0f;
+      o += nn;
     }
   }
-  for (int j = tid; j < ROWS * K0 * 2 / 16; j += 256) {
-    reinterpret_cast<uint4*>(sXh)[j] = make_uint4(0, 0, 0, 0);
-    reinterpret_cast<uint4*>(sXl)[j] = make_uint4(0, 0, 0, 0);
-  }
-  __syncthreads();
-  if (tid < ROWS)  // the constant 1 column (D + 1) gives db1 through dW1
-    *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(tid, D + 1, K0)) =
-        __float2bfloat16_rn(1.0f);
-  if ((tid >> 5) == 0) {
+  for (int j = tid; j < 2 * ROWS * K0 * 2 / 16; j += 256)
+    reinterpret_cast<uint4*>(sX)[j] = make_uint4(0, 0, 0, 0);
+  if (warp == 0) {
     tc::tmem_alloc(&tmem_base_s, 512);
     tc::tmem_relinquish();
   }
@@ -2139,12 +2002,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
   const uint32_t tbase = tmem_base_s;
   uint32_t parity = 0;
 
-  // ---- per-row reverse state (as in k_mlp_adjoint)
-  int inst = a.i0 + blockIdx.x * ROWS + row;
-  const int iend = a.i0 + a.B;
-  bool act = false;
+  // ---- this row's instance (one per row and slice) and its reverse state
+  const int pos = a.i0 + (int)blockIdx.x * ROWS + row;
+  const int inst = pos < a.i0 + a.B ? a.order[pos] : -1;
+  bool act = false, bad = false;
   int n = -1, N = 0, q = -1;
-  bool bad = false;
   double tn = 0.0, tnext = 0.0;
   float h = 0.0f;
   float yb[16], kb[7][16];
@@ -2154,12 +2016,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
 #pragma unroll
     for (int j = 0; j < 7; ++j) kb[j][r] = 0.0f;
   }
-  auto load_step = [&](int i) {
-    const size_t o = (size_t)i * a.slots + n;
+  auto load_step = [&]() {
+    const size_t o = (size_t)inst * a.slots + n;
     tn = a.tp_t[o];
     h = a.tp_h[o];
-    tnext = (n == N - 1) ? a.t1[i] : tn + (double)h;
-    act = true;
+    tnext = (n == N - 1) ? a.t1[inst] : tn + (double)h;
   };
   // Y_s of the step being reversed: Y_1 = y_n, Y_2..Y_7 as the forward recorded
   auto load_stage = [&](int s_, float (&Yo)[16]) {
@@ -2173,46 +2034,34 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
       Yo[4 * v] = u.x, Yo[4 * v + 1] = u.y, Yo[4 * v + 2] = u.z, Yo[4 * v + 3] = u.w;
     }
   };
-  auto next_work = [&](bool finishing) {
-    while (true) {
-      if (finishing) {
-        const int i = inst;
-        if (!bad && a.gye) {
-          const long long k0 = tkey(a.t0[i]);
-          for (; q >= 0; --q)
-            if (tkey(a.te[(size_t)i * a.K + q]) == k0)
+  // the instance is done: cotangents of points at t0, then dL/dy0
+  auto finish = [&]() {
+    if (!bad && a.gye) {
+      const long long k0 = tkey(a.t0[inst]);
+      for (; q >= 0; --q)
+        if (tkey(a.te[(size_t)inst * a.K + q]) == k0)
 #pragma unroll
-              for (int r = 0; r < C; ++r) yb[r] += a.gye[((size_t)i * a.K + q) * D + coff + r];
-        }
-#pragma unroll
-        for (int r = 0; r < C; ++r) a.gy0[(size_t)i * D + coff + r] = bad ? nan_(0.0f) : yb[r];
-        inst += grid * ROWS;
-        finishing = false;
-      }
-      if (inst >= iend) {
-        act = false;
-        return;
-      }
-      const int i = inst;
-      N = a.n_acc[i];
-      bad = a.status[i] != ST_SUCCESS;
-      if (!bad && N > a.slots) {
-        bad = true;
-        if (sub == 0) atomicExch(a.overflow, 1);
-      }
-#pragma unroll
-      for (int r = 0; r < C; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + coff + r] : 0.0f;
-      q = a.K - 1;
-      n = N - 1;
-      if (bad || n < 0) {
-        finishing = true;
-        continue;
-      }
-      load_step(i);
-      return;
+          for (int r = 0; r < C; ++r) yb[r] += a.gye[((size_t)inst * a.K + q) * D + coff + r];
     }
+#pragma unroll
+    for (int r = 0; r < C; ++r) a.gy0[(size_t)inst * D + coff + r] = bad ? nan_(0.0f) : yb[r];
+    act = false;
   };
-  next_work(false);
+  if (inst >= 0) {
+    N = a.n_acc[inst];
+    bad = a.status[inst] != ST_SUCCESS;
+    if (!bad && N > a.slots) {
+      bad = true;
+      if (sub == 0) atomicExch(a.overflow, 1);
+    }
+#pragma unroll
+    for (int r = 0; r < C; ++r) yb[r] = a.gyf ? a.gyf[(size_t)inst * D + coff + r] : 0.0f;
+    q = a.K - 1;
+    n = N - 1;
+    act = true;
+    if (bad || n < 0) finish();
+    else load_step();
+  }
 
   auto barrier = [&]() {
     tc::fence_proxy_async();
@@ -2221,126 +2070,178 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     tc::fence_after_sync();
   };
   auto wait_mma = [&]() {
-    if (!tc::mbar_wait(&mbar_mma, parity)) atomicExch(&abort_s, 1);
+    if (!tc::mbar_wait_sleep(&mbar_mma, parity)) atomicExch(&abort_s, 1);
     parity ^= 1u;
     tc::fence_after_sync();
   };
-  // one GEMM of the round through the ring: A = the layer's input tile (K
-  // major, hi and lo), B = the next K chunks; N = 512 as two halves of 256
-  // or one MMA of width nw.  Transposed chunks are MN-major [16][IN] tiles.
-  auto gemm = [&](uint32_t ah, uint32_t al, int Ka, int nchunks, int Nl, bool tr) {
-    if (tid != 0 || abort_s) return;
-    const int nh = Nl > 256 ? Nl / 256 : 1, nw = Nl > 256 ? 256 : Nl;
-    const uint32_t idesc = tc::idesc_bf16_f32(ROWS, nw, false, tr);
-    bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c, ++g_chunk) {
-      const int b = (int)(g_chunk % NS);
-      ok = tc::mbar_wait(&mbar_full[b], (g_chunk / NS) & 1u);
-      if (!ok) break;
-      const uint32_t wb = tc::smem_u32(sW + b * L::STAGE_BYTES);
-      const uint64_t dh = tc::smem_desc(ah + c * 256, 128, Ka * 16);
-      const uint64_t dl = tc::smem_desc(al + c * 256, 128, Ka * 16);
-      for (int j = 0; j < nh; ++j) {
-        const uint64_t db = tr ? tc::smem_desc_mn(wb + j * (256 / 8) * 128, Nl * 16)
-                               : tc::smem_desc(wb + j * (256 / 8) * 256, 128, 256);
-        tc::mma_bf16(tbase + 256 * j, dh, db, idesc, c > 0);
-        tc::mma_bf16(tbase + 256 * j, dl, db, idesc, true);
-      }
-      tc::mma_commit(&mbar_empty[b]);
-      if (g_chunk >= 1) {
-        const uint32_t gp = g_chunk - 1;
-        const int pb = (int)(gp % NS);
-        ok = tc::mbar_wait(&mbar_empty[pb], (gp / NS) & 1u);
+  // one GEMM of the round (segment qs): thread 0 issues M = 128 MMAs over
+  // the stacked A tile (K-major, Ka columns) as the stages arrive, thread 32
+  // refills each stage's slot with the stage NSL ahead once its MMAs are
+  // done.  N = 512 as two halves of 256, else one MMA of width Nl; the
+  // transposed chunks are MN-major [16][Nl] tiles.
+  auto gemm = [&](int qs, uint32_t a_addr, int Ka, int Nl) {
+    const bool tr = L::seg_tr(qs);
+    if (tid == 0 && !abort_s) {
+      const int nh = Nl > 256 ? Nl / 256 : 1, nw = Nl > 256 ? 256 : Nl;
+      const uint32_t idesc = tc::idesc_bf16_f32(128, nw, false, tr);
+      const int cb = L::seg_chunk_bytes(qs);
+      bool ok = true;
+      for (int st = 0; st < L::seg_stages(qs) && ok; ++st) {
+        const uint32_t g = g_stage + (uint32_t)st;
+        const int b = (int)(g % NSL);
+        ok = tc::mbar_wait(&mbar_full[b], (g / NSL) & 1u);
         if (!ok) break;
-        issue_copy(gp + NS, pb);
-      }
-    }
-    if (!ok) atomicExch(&abort_s, 1);
-    tc::mma_commit(&mbar_mma);
-  };
-  // hidden epilogue: h = tanh(acc + b) into the tile; reverse rounds also
-  // stage the row
-  auto hidden_epi = [&](const float* bl, bool stage, uint16_t* shp, uint16_t* slp, size_t srow) {
-#pragma unroll
-    for (int c = 0; c < HC; c += 16) {
-      const int col = sub * HC + c;
-      float v[16];
-      Cfg::hid_ld(tbase, tid, c, v);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = tanh_acc(v[j] + bl[col + j]);
-      store_row16<true>(sHh, sHl, row, col, H, v);
-      if (stage) stage_row16(shp, slp, srow * H + col, v);
-    }
-  };
-  // delta epilogue: delta = acc (1 - h^2); h from the tile (own layer) or
-  // from the staged row; the split delta replaces the tile, and is staged
-  auto delta_epi = [&](bool h_in_tile, const uint16_t* hhp, const uint16_t* hlp, uint16_t* shp,
-                       uint16_t* slp, size_t srow) {
-#pragma unroll
-    for (int c = 0; c < HC; c += 16) {
-      const int col = sub * HC + c;
-      float v[16], hv[16];
-      Cfg::hid_ld(tbase, tid, c, v);
-      if (h_in_tile) {
-#pragma unroll
-        for (int c8 = 0; c8 < 2; ++c8) {
-          const uint32_t off = tc::cm_offset(row, col + 8 * c8, H);
-          const uint4 hh = *reinterpret_cast<const uint4*>(sHh + off);
-          const uint4 ll = *reinterpret_cast<const uint4*>(sHl + off);
-          const uint32_t hw[4] = {hh.x, hh.y, hh.z, hh.w}, lw[4] = {ll.x, ll.y, ll.z, ll.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
-            const __nv_bfloat162 l2 = *reinterpret_cast<const __nv_bfloat162*>(&lw[j]);
-            hv[8 * c8 + 2 * j] = __low2float(h2) + __low2float(l2);
-            hv[8 * c8 + 2 * j + 1] = __high2float(h2) + __high2float(l2);
+        int q_, c0, nc, off_, bytes_;
+        L::stage_of(g, q_, c0, nc, off_, bytes_);
+        const uint32_t wb = tc::smem_u32(sW + b * L::SLOT_BYTES);
+        for (int c = 0; c < nc; ++c) {
+          const int kc = c0 + c;
+          const uint64_t da = tc::smem_desc(a_addr + kc * 256, 128, Ka * 16);
+          for (int j = 0; j < nh; ++j) {
+            const uint64_t db = tr ? tc::smem_desc_mn(wb + c * cb + j * 4096, Nl * 16)
+                                   : tc::smem_desc(wb + c * cb + j * 8192, 128, 256);
+            tc::mma_bf16(tbase + 256 * j, da, db, idesc, kc > 0);
           }
         }
-      } else {
-        unstage_row16(hhp, hlp, srow * H + col, hv);
+        tc::mma_commit(&mbar_empty[b]);
+      }
+      if (!ok) atomicExch(&abort_s, 1);
+      tc::mma_commit(&mbar_mma);
+    } else if (tid == 32 && !abort_s) {
+      bool ok = true;
+      for (int st = 0; st < L::seg_stages(qs) && ok; ++st) {
+        const uint32_t g = g_stage + (uint32_t)st;
+        const int b = (int)(g % NSL);
+        ok = tc::mbar_wait(&mbar_empty[b], (g / NSL) & 1u);
+        if (ok) issue_stage(g + NSL, b);
+      }
+      if (!ok) atomicExch(&abort_s, 1);
+    }
+    g_stage += (uint32_t)L::seg_stages(qs);
+    __syncwarp();
+  };
+  size_t blk = 0;  // this round's staging block
+  // stages 8 features (hi, lo) of tensor t for this row at column col
+  auto stage8 = [&](int t, int col, const uint4& hi, const uint4& lo) {
+    const int fw = L::fb_width(t);
+    const int fb = col / fw, m = col - fb * fw;
+    unsigned char* dst = a.plane[L::plane_first(t) + fb] + blk * 2 * (size_t)L::blk_bytes(t) +
+                         L::blk_off(row, m, fw);
+    *reinterpret_cast<uint4*>(dst) = hi;
+    *reinterpret_cast<uint4*>(dst + L::blk_bytes(t)) = lo;
+  };
+  auto stage16 = [&](int t, int col, const float (&v)[16]) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      float w8[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w8[j] = v[8 * u + j];
+      uint4 hi, lo;
+      split8(w8, hi, lo);
+      stage8(t, col + 8 * u, hi, lo);
+    }
+  };
+  // hidden epilogue: h = tanh(acc + b) into the stacked tile, staged as act
+  auto epi_hidden = [&](const float* bl, int t_act) {
+#pragma unroll 1
+    for (int c = 0; c < 256; c += 32) {
+      float v0[16], v1[16];
+      tc::tmem_ld16(tbase + lanes + 256 * hf + c, v0);
+      tc::tmem_ld16(tbase + lanes + 256 * hf + c + 16, v1);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        float z[8];
+        combine_pair8(u == 0 ? v0 : v1, odd, z);
+        const int col = 256 * hf + c + 16 * u + 8 * odd;
+        const float4 b0 = *reinterpret_cast<const float4*>(bl + col);
+        const float4 b1 = *reinterpret_cast<const float4*>(bl + col + 4);
+        const float2 t0 = tanh_acc2(__fadd2_rn(make_float2(z[0], z[1]), make_float2(b0.x, b0.y)));
+        const float2 t1 = tanh_acc2(__fadd2_rn(make_float2(z[2], z[3]), make_float2(b0.z, b0.w)));
+        const float2 t2 = tanh_acc2(__fadd2_rn(make_float2(z[4], z[5]), make_float2(b1.x, b1.y)));
+        const float2 t3 = tanh_acc2(__fadd2_rn(make_float2(z[6], z[7]), make_float2(b1.z, b1.w)));
+        const float hv[8] = {t0.x, t0.y, t1.x, t1.y, t2.x, t2.y, t3.x, t3.y};
+        uint4 hi, lo;
+        split8(hv, hi, lo);
+        store_pair8(sH, row, col, H, odd, hi, lo);
+        stage8(t_act, col, hi, lo);
+      }
+    }
+  };
+  // delta epilogue: delta = acc (1 - h^2), h from the tile (its own layer,
+  // read before it is overwritten) or from its staged rows; the split delta
+  // replaces the tile and is staged
+  auto epi_delta = [&](int t_h, bool h_in_tile, int t_del) {
+    const int fw = L::fb_width(t_h);
+#pragma unroll 1
+    for (int c = 0; c < 256; c += 32) {
+      float v0[16], v1[16];
+      tc::tmem_ld16(tbase + lanes + 256 * hf + c, v0);
+      tc::tmem_ld16(tbase + lanes + 256 * hf + c + 16, v1);
+      uint4 hh[2], hl[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int col = 256 * hf + c + 16 * u + 8 * odd;
+        if (h_in_tile) {
+          hh[u] = *reinterpret_cast<const uint4*>(sH + tc::cm_offset(2 * row, col, H));
+          hl[u] = *reinterpret_cast<const uint4*>(sH + tc::cm_offset(2 * row + 1, col, H));
+        } else {
+          const int fb = col / fw, m = col - fb * fw;
+          const unsigned char* src = a.plane[L::plane_first(t_h) + fb] +
+                                     blk * 2 * (size_t)L::blk_bytes(t_h) + L::blk_off(row, m, fw);
+          hh[u] = *reinterpret_cast<const uint4*>(src);
+          hl[u] = *reinterpret_cast<const uint4*>(src + L::blk_bytes(t_h));
+        }
       }
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] *= madd(-hv[j], hv[j], 1.0f);
-      store_row16<true>(sHh, sHl, row, col, H, v);
-      stage_row16(shp, slp, srow * H + col, v);
+      for (int u = 0; u < 2; ++u) {
+        float z[8], hv[8], dv[8];
+        combine_pair8(u == 0 ? v0 : v1, odd, z);
+        unsplit8(hh[u], hl[u], hv);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) dv[j] = z[j] * madd(-hv[j], hv[j], 1.0f);
+        const int col = 256 * hf + c + 16 * u + 8 * odd;
+        uint4 hi, lo;
+        split8(dv, hi, lo);
+        store_pair8(sH, row, col, H, odd, hi, lo);
+        stage8(t_del, col, hi, lo);
+      }
     }
   };
+
   const float bw[7] = {float(Cc::b1), 0.0f, float(Cc::b3), float(Cc::b4), float(Cc::b5),
                        float(Cc::b6), 0.0f};
-  int rev_round = 0;  // reverse rounds staged by this CTA
-
+  int k_round = 0;  // reverse rounds staged by this CTA
   for (int rnd = 0;; ++rnd) {
     const int ph = rnd % ADJ_ROUNDS;
     if (ph == 0 && __syncthreads_or(act) == 0) break;
     if (abort_s) break;
-    const int s = 7 - ph;  // stage reversed this round (block-uniform)
-    if (rev_round >= a.cap) {  // cannot happen: the staging is sized for it
+    const int s = 7 - ph;  // the stage reversed this round (block-uniform)
+    if (k_round >= a.cap) {  // cannot happen: the planes hold 7 rounds per tape slot
       if (tid == 0) atomicExch(a.err, 2);
       break;
     }
-    const size_t srow = ((size_t)blockIdx.x * a.cap + rev_round) * ROWS + row;
+    blk = (size_t)blockIdx.x * a.cap + k_round;
 
     // ---- stage input [Y_s; t_s] and the cotangent kbar_s of this row
-    float Y[16], d3[16];
+    float Y[16], kq[16];
     float tin = 0.0f;
     if (act && s == 7) {
-      const int i = inst;
 #pragma unroll
       for (int j = 0; j < 7; ++j)
 #pragma unroll
         for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
       const long long kt = tkey(tn), kn = tkey(tnext);
       while (q >= 0) {
-        const double tq = a.te[(size_t)i * a.K + q];
-        const long long kq = tkey(tq);
-        if (!(kq > kt)) break;
+        const double tq = a.te[(size_t)inst * a.K + q];
+        const long long kk = tkey(tq);
+        if (!(kk > kt)) break;
         if (a.gye) {
           float gq[16], w[7];
 #pragma unroll
-          for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)i * a.K + q) * D + coff + r];
-          if (kq == kn) {
+          for (int r = 0; r < C; ++r) gq[r] = a.gye[((size_t)inst * a.K + q) * D + coff + r];
+          if (kk == kn) {
 #pragma unroll
             for (int j = 0; j < 7; ++j) w[j] = bw[j];
           } else {
@@ -2359,103 +2260,394 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     if (act) {
       load_stage(s, Y);
       tin = (float)(tn + dp_c(s) * (double)h);
-      pick7(kb, s - 1, d3);
+      pick7(kb, s - 1, kq);
     } else {
 #pragma unroll
-      for (int r = 0; r < C; ++r) Y[r] = d3[r] = 0.0f;
+      for (int r = 0; r < C; ++r) Y[r] = kq[r] = 0.0f;
     }
-    store_row16<true>(sXh, sXl, row, coff, K0, Y);
+    store_row16_stk(sX, row, coff, K0, Y);
+    stage16(L::T_X, coff, Y);
+    stage16(L::T_K, coff, kq);
     if (sub == Cfg::TPR - 1) {
-      const __nv_bfloat16 th = __float2bfloat16_rn(tin);
-      const __nv_bfloat16 tlo = __float2bfloat16_rn(tin - __bfloat162float(th));
-      *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(row, D, K0)) = th;
-      *reinterpret_cast<__nv_bfloat16*>(sXl + tc::cm_offset(row, D, K0)) = tlo;
-    }
-    store_row16<true>(sKh, sKl, row, coff, D, d3);
-    // staged rows: X = [Y; t; 1; 0...] and kbar
-    stage_row16(a.sa[0][0], a.sa[0][1], srow * K0 + coff, Y);
-    stage_row16(a.sg[3][0], a.sg[3][1], srow * D + coff, d3);
-    if (sub == Cfg::TPR - 1) {
+      // columns D.. of the input: the time (hi + lo) and zero padding, all
+      // rewritten because the kbar tile of the last round shares the bytes;
+      // staged as [t; 1; 0...], the constant input whose weight gradient is db1
       float tail[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) tail[j] = 0.0f;
       tail[0] = tin;
+      store_row16_stk(sX, row, D, K0, tail);
       tail[1] = 1.0f;
-      stage_row16(a.sa[0][0], a.sa[0][1], srow * K0 + D, tail);
+      stage16(L::T_X, D, tail);
     }
     barrier();
 
     // ---- forward layers at Y_s
-    gemm(tc::smem_u32(sXh), tc::smem_u32(sXl), K0, K0 / 16, H, false);
+    gemm(0, tc::smem_u32(sX), K0, H);
     wait_mma();
-    hidden_epi(sBias, true, a.sa[1][0], a.sa[1][1], srow);
+    epi_hidden(sBias, L::T_H1);
+    store_row16_stk(sX, row, coff, D, kq);  // the kbar tile, now that X is read
     barrier();
-    gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, false);
+    gemm(1, tc::smem_u32(sH), H, H);
     wait_mma();
-    hidden_epi(sBias + H, true, a.sa[2][0], a.sa[2][1], srow);
+    epi_hidden(sBias + H, L::T_H2);
     barrier();
-    gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, false);
+    gemm(2, tc::smem_u32(sH), H, H);
     wait_mma();
-    hidden_epi(sBias + 2 * H, true, a.sa[3][0], a.sa[3][1], srow);
+    epi_hidden(sBias + 2 * H, L::T_H3);
     barrier();
-
+    // ---- backward chain
+    gemm(3, tc::smem_u32(sX), D, H);  // gh3 = kbar W4
+    wait_mma();
+    epi_delta(L::T_H3, true, L::T_D3);
+    barrier();
+    gemm(4, tc::smem_u32(sH), H, H);  // gh2 = delta3 W3
+    wait_mma();
+    epi_delta(L::T_H2, false, L::T_D2);
+    barrier();
+    gemm(5, tc::smem_u32(sH), H, H);  // gh1 = delta2 W2
+    wait_mma();
+    epi_delta(L::T_H1, false, L::T_D1);
+    barrier();
+    gemm(6, tc::smem_u32(sH), H, K0);  // gx = delta1 W1
+    wait_mma();
     float fg[16];
     {
-      // gh3 = kbar W3 -> delta3 (h3 in the tile)
-      gemm(tc::smem_u32(sKh), tc::smem_u32(sKl), D, D / 16, H, true);
-      wait_mma();
-      delta_epi(true, nullptr, nullptr, a.sg[2][0], a.sg[2][1], srow);
-      barrier();
-      // gh2 = delta3 W2 -> delta2 (h2 staged)
-      gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, true);
-      wait_mma();
-      delta_epi(false, a.sa[2][0], a.sa[2][1], a.sg[1][0], a.sg[1][1], srow);
-      barrier();
-      // gh1 = delta2 W1 -> delta1 (h1 staged)
-      gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, H, true);
-      wait_mma();
-      delta_epi(false, a.sa[1][0], a.sa[1][1], a.sg[0][0], a.sg[0][1], srow);
-      barrier();
-      // gx = delta1 W0: the state part of the cotangent
-      gemm(tc::smem_u32(sHh), tc::smem_u32(sHl), H, H / 16, K0, true);
-      wait_mma();
-      Cfg::out_ld(tbase, tid, fg);
+      float v0[16], v1[16];
+      tc::tmem_ld16(tbase + lanes + 32 * hf, v0);
+      tc::tmem_ld16(tbase + lanes + 32 * hf + 16, v1);
       tc::tmem_wait_ld();
-      rev_round++;
+      combine_pair16(v0, v1, odd, fg);
     }
+    k_round++;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (abort_s) break;
 
-    // ---- consume (row-local; as in k_mlp_adjoint)
+    // ---- consume (row-local)
     if (!act) continue;
-    {
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        if (j + 1 >= s) continue;
-        const float c = h * dp_a(s, j + 1);
+    for (int j = 0; j < 6; ++j) {
+      if (j + 1 >= s) continue;
+      const float cc = h * dp_a(s, j + 1);
 #pragma unroll
-        for (int r = 0; r < C; ++r) kb[j][r] = madd(c, fg[r], kb[j][r]);
-      }
+      for (int r = 0; r < C; ++r) kb[j][r] = madd(cc, fg[r], kb[j][r]);
+    }
 #pragma unroll
-      for (int r = 0; r < C; ++r) yb[r] += fg[r];
-      if (s == 1) {
-        n -= 1;
-        if (n >= 0) load_step(inst);
-        else next_work(true);
-      }
+    for (int r = 0; r < C; ++r) yb[r] += fg[r];
+    if (s == 1) {
+      n -= 1;
+      if (n >= 0) load_step();
+      else finish();
     }
   }
-  if (tid == 0) {  // the ring's copies still in flight land before the CTA exits
-    const uint32_t first = g_chunk, last = g_chunk == 0 ? NS - 1 : g_chunk + NS - 2;
-    for (uint32_t x = first; x <= last; ++x)
-      if (!tc::mbar_wait(&mbar_full[x % NS], (x / NS) & 1u)) atomicExch(&abort_s, 1);
+  if (tid == 0) {
+    a.rounds[blockIdx.x] = k_round;
+    // the ring's copies still in flight (stages g .. g + NSL - 1) land before the CTA exits
+    for (uint32_t x = g_stage; x < g_stage + NSL; ++x)
+      if (!tc::mbar_wait(&mbar_full[x % NSL], (x / NSL) & 1u)) atomicExch(&abort_s, 1);
   }
   if (abort_s && tid == 0) atomicExch(a.err, 1);
   tc::fence_before_sync();
   __syncthreads();
-  if ((tid >> 5) == 0) tc::tmem_dealloc(tbase, 512);
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+// ---------------------------------------------------------------- dW, db
+// The weight and bias gradients of the wide adjoint from the staged blocks:
+//   dW_l[o][i] = sum over staged rows of delta_l[row][o] act_l[row][i]
+// in three BF16 products per pair of split operands (hi*hi + lo*hi + hi*lo;
+// the lo*lo term is below FP32 rounding of the sum), FP32 accumulation in
+// tensor memory.  A job is one 128-feature block of the output's rows
+// (M = 128); its work items split the chain CTAs (the K dimension) into
+// parts, each accumulating its own partial in a fixed order, which
+// k_mlp_dw_reduce sums part by part: deterministic.
+//   kind 0: D[o][i] += A^T B over nb operand blocks of width bw (dW)
+//   kind 1: D[o][0] += A^T 1 (a bias: the delta's column sums)
+//   kind 2: D[*][i] += 1^T B (the output bias from the kbar rows)
+struct DwJob {
+  int kind, ta, fa, tb, nb, bw;  // tensors / feature blocks of A and B
+};
+constexpr int DW_MAX_JOBS = 32;
+constexpr int DW_PART_FLOATS = 128 * 512;
+struct DwArgs {
+  int njobs;
+  DwJob job[DW_MAX_JOBS];
+  int item0[DW_MAX_JOBS + 1];  // first work item of each job
+  int chain_grid, cap;         // the chain kernel's CTAs and plane capacity
+  const int32_t* rounds;       // [chain_grid]
+  const unsigned char* plane[32];
+  float* part;                 // [items][128][512]
+  int32_t* err;
+};
+
+template <class Cfg>
+__global__ void __launch_bounds__(128, 1) k_mlp_dw(DwArgs a) {
+  using L = WideAdj<Cfg>;
+  constexpr int NA = 2, NB = 3, SLOT = 32768;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t fullA[NA], emptyA[NA], fullB[NB], emptyB[NB], done;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + NA * SLOT;
+  unsigned char* sOnes = sm + (NA + NB) * SLOT;  // [128][16] K-major BF16 ones
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int item = blockIdx.x;
+  int j = 0;
+  while (j + 1 < a.njobs && item >= a.item0[j + 1]) ++j;
+  const DwJob jb = a.job[j];
+  const int P = a.item0[j + 1] - a.item0[j], p = item - a.item0[j];
+  const int c_lo = (int)((long long)a.chain_grid * p / P);
+  const int c_hi = (int)((long long)a.chain_grid * (p + 1) / P);
+  const bool hasA = jb.kind != 2, hasB = jb.kind != 1;
+  const int nbp = jb.kind == 0 ? jb.nb : 1;  // B parts per block (one MMA group each)
+  const int abytes = hasA ? 2 * L::blk_bytes(jb.ta) : 0;
+  const int bbytes = hasB ? 2 * L::blk_bytes(jb.tb) : 0;
+  const unsigned char* pa = hasA ? a.plane[L::plane_first(jb.ta) + jb.fa] : nullptr;
+
+  if (tid == 0) {
+    for (int b = 0; b < NA; ++b) {
+      tc::mbar_init(&fullA[b], 1);
+      tc::mbar_init(&emptyA[b], 1);
+    }
+    for (int b = 0; b < NB; ++b) {
+      tc::mbar_init(&fullB[b], 1);
+      tc::mbar_init(&emptyB[b], 1);
+    }
+    tc::mbar_init(&done, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int e = tid; e < 128 * 16 / 8; e += 128)
+    reinterpret_cast<uint4*>(sOnes)[e] =
+        make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base_s, 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tmem_base_s;
+  // the blocks of this item: CTAs [c_lo, c_hi), rounds [0, rounds[c])
+  int nblk = 0;
+  for (int c = c_lo; c < c_hi; ++c) nblk += a.rounds[c];
+
+  if (tid == 32) {
+    // producer: the same sequence the MMA thread consumes (A of a block,
+    // then its B parts); each ring slot is refilled once its MMAs are done
+    int ia = 0, ib = 0;
+    bool ok = true;
+    for (int c = c_lo; c < c_hi && ok; ++c)
+      for (int k = 0; k < a.rounds[c] && ok; ++k) {
+        const size_t bk = (size_t)c * a.cap + k;
+        if (hasA) {
+          const int s = ia % NA;
+          if (ia >= NA) ok = tc::mbar_wait(&emptyA[s], ((ia - NA) / NA) & 1u);
+          if (!ok) break;
+          tc::mbar_expect_tx(&fullA[s], (uint32_t)abytes);
+          tc::bulk_g2s(sA + s * SLOT, pa + bk * abytes, (uint32_t)abytes, &fullA[s]);
+          ++ia;
+        }
+        if (hasB)
+          for (int u = 0; u < nbp && ok; ++u) {
+            const int s = ib % NB;
+            if (ib >= NB) ok = tc::mbar_wait(&emptyB[s], ((ib - NB) / NB) & 1u);
+            if (!ok) break;
+            const unsigned char* pb = a.plane[L::plane_first(jb.tb) + u];
+            tc::mbar_expect_tx(&fullB[s], (uint32_t)bbytes);
+            tc::bulk_g2s(sB + s * SLOT, pb + bk * bbytes, (uint32_t)bbytes, &fullB[s]);
+            ++ib;
+          }
+      }
+    if (!ok) atomicExch(&abort_s, 1);
+  } else if (tid == 0) {
+    const int FA = hasA ? L::fb_width(jb.ta) : 0, FB = hasB ? L::fb_width(jb.tb) : 0;
+    const int ablk = hasA ? L::blk_bytes(jb.ta) : 0, bblk = hasB ? L::blk_bytes(jb.tb) : 0;
+    const uint32_t ones = tc::smem_u32(sOnes);
+    int ia = 0, ib = 0, blk_i = 0;
+    bool ok = true;
+    for (int c = c_lo; c < c_hi && ok; ++c)
+      for (int k = 0; k < a.rounds[c] && ok; ++k, ++blk_i) {
+        uint32_t aA = 0;
+        if (hasA) {
+          const int s = ia % NA;
+          ok = tc::mbar_wait(&fullA[s], (ia / NA) & 1u);
+          if (!ok) break;
+          aA = tc::smem_u32(sA + s * SLOT);
+        }
+        for (int u = 0; u < nbp && ok; ++u) {
+          uint32_t aB = 0;
+          if (hasB) {
+            const int s = ib % NB;
+            ok = tc::mbar_wait(&fullB[s], (ib / NB) & 1u);
+            if (!ok) break;
+            aB = tc::smem_u32(sB + s * SLOT);
+          }
+          const uint32_t dcol = tbase + (uint32_t)(jb.kind == 0 ? u * jb.bw : 0);
+          for (int ks = 0; ks < 4; ++ks) {  // 16 staged rows per K step
+            const bool acc0 = blk_i > 0 || ks > 0;
+            if (jb.kind == 0) {
+              const uint32_t idesc = tc::idesc_bf16_f32(128, jb.bw, true, true);
+              const uint64_t ah = tc::smem_desc_mn(aA + ks * 2 * FA * 16, FA * 16);
+              const uint64_t al = tc::smem_desc_mn(aA + ablk + ks * 2 * FA * 16, FA * 16);
+              const uint64_t bh = tc::smem_desc_mn(aB + ks * 2 * FB * 16, FB * 16);
+              const uint64_t bl = tc::smem_desc_mn(aB + bblk + ks * 2 * FB * 16, FB * 16);
+              tc::mma_bf16(dcol, ah, bh, idesc, acc0);
+              tc::mma_bf16(dcol, al, bh, idesc, true);
+              tc::mma_bf16(dcol, ah, bl, idesc, true);
+            } else if (jb.kind == 1) {  // column sums: A^T times a ones operand (N = 16)
+              const uint32_t idesc = tc::idesc_bf16_f32(128, 16, true, false);
+              const uint64_t ah = tc::smem_desc_mn(aA + ks * 2 * FA * 16, FA * 16);
+              const uint64_t al = tc::smem_desc_mn(aA + ablk + ks * 2 * FA * 16, FA * 16);
+              const uint64_t b1 = tc::smem_desc(ones, 128, 256);
+              tc::mma_bf16(dcol, ah, b1, idesc, acc0);
+              tc::mma_bf16(dcol, al, b1, idesc, true);
+            } else {  // a ones operand (M = 128) times B: every row holds B's column sums
+              const uint32_t idesc = tc::idesc_bf16_f32(128, FB, false, true);
+              const uint64_t a1 = tc::smem_desc(ones, 128, 256);
+              const uint64_t bh = tc::smem_desc_mn(aB + ks * 2 * FB * 16, FB * 16);
+              const uint64_t bl = tc::smem_desc_mn(aB + bblk + ks * 2 * FB * 16, FB * 16);
+              tc::mma_bf16(dcol, a1, bh, idesc, acc0);
+              tc::mma_bf16(dcol, a1, bl, idesc, true);
+            }
+          }
+          if (hasB) {
+            tc::mma_commit(&emptyB[ib % NB]);
+            ++ib;
+          }
+        }
+        if (hasA && ok) {
+          tc::mma_commit(&emptyA[ia % NA]);
+          ++ia;
+        }
+      }
+    if (!ok) atomicExch(&abort_s, 1);
+    tc::mma_commit(&done);
+  }
+  __syncwarp();
+  if (!tc::mbar_wait_sleep(&done, 0)) atomicExch(&abort_s, 1);
+  tc::fence_after_sync();
+  // add the accumulator to this item's partial (rows = lanes, one per thread)
+  const int ncols = jb.kind == 0 ? jb.nb * jb.bw : jb.kind == 1 ? 16 : L::fb_width(jb.tb);
+  if (nblk > 0 && !abort_s) {
+    float* dst = a.part + (size_t)item * DW_PART_FLOATS + (size_t)tid * 512;
+    const uint32_t lanes = (uint32_t)(32 * warp) << 16;
+    for (int c0 = 0; c0 < ncols; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tbase + lanes + c0, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        if (c0 + e < ncols) dst[c0 + e] += v[e];
+    }
+  }
+  if (abort_s && tid == 0) atomicExch(a.err, 3);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+// Gradients from the work items' partials, summed part by part in order:
+// gW0 [512][65] and gb0 (dW1's constant column), gW1, gW2 [512][512],
+// gW3 [64][512] (staged transposed), gb1, gb2, gb3.
+struct DwReduceArgs {
+  const float* part;
+  int item0[DW_MAX_JOBS + 1];
+  int jW[4], jb[4];  // first job of each gradient (4 consecutive row-block jobs; gb3: one)
+  float* gW[4];
+  float* gb[4];
+};
+__global__ void k_mlp_dw_reduce(DwReduceArgs a) {
+  constexpr int H = 512, D = 64, IN0 = D + 1;
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  auto sum = [&](int job, int m, int nn) {
+    float s = 0.0f;
+    for (int it = a.item0[job]; it < a.item0[job + 1]; ++it)
+      s += a.part[(size_t)it * DW_PART_FLOATS + (size_t)m * 512 + nn];
+    return s;
+  };
+  if (e < (long long)H * IN0) {  // gW0 [o][i], i < 65
+    const int o = (int)(e / IN0), i = (int)(e % IN0);
+    a.gW[0][e] = sum(a.jW[0] + o / 128, o % 128, i);
+    return;
+  }
+  e -= (long long)H * IN0;
+  if (e < H) {
+    if (a.gb[0]) a.gb[0][e] = sum(a.jW[0] + (int)e / 128, (int)e % 128, IN0);
+    return;
+  }
+  e -= H;
+  for (int l = 1; l <= 2; ++l) {
+    if (e < (long long)H * H) {
+      const int o = (int)(e / H), i = (int)(e % H);
+      a.gW[l][e] = sum(a.jW[l] + o / 128, o % 128, i);
+      return;
+    }
+    e -= (long long)H * H;
+    if (e < H) {
+      if (a.gb[l]) a.gb[l][e] = sum(a.jb[l] + (int)e / 128, (int)e % 128, 0);
+      return;
+    }
+    e -= H;
+  }
+  if (e < (long long)D * H) {  // gW3 [o][i] from dW3^T [i][o]
+    const int o = (int)(e / H), i = (int)(e % H);
+    a.gW[3][e] = sum(a.jW[3] + i / 128, i % 128, o);
+    return;
+  }
+  e -= (long long)D * H;
+  if (e < D && a.gb[3]) a.gb[3][e] = sum(a.jb[3], 0, (int)e);
+}
+
+// Queue of instances, most accepted steps first, and by index within equal
+// counts (stable: the same order on every call, so the weight-gradient sums
+// run in a fixed order).  One CTA: per 1024-instance chunk every warp ranks
+// its lanes per bin, the warps' bin counts are prefixed in warp order.
+__global__ void __launch_bounds__(1024) k_order_steps_stable(int B, StepsBin bin_of,
+                                                             int32_t* order) {
+  __shared__ int cnt[32][ORDER_BINS];
+  __shared__ int base[ORDER_BINS];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t < ORDER_BINS) base[t] = 0;
+  __syncthreads();
+  for (int i = t; i < B; i += 1024) atomicAdd(&base[bin_of(i)], 1);
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int b = 0; b < ORDER_BINS; ++b) {
+      const int v = base[b];
+      base[b] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < B; c0 += 1024) {
+    const int i = c0 + t;
+    const int b = i < B ? bin_of(i) : -1;
+#pragma unroll
+    for (int k = 0; k < ORDER_BINS / 32; ++k) cnt[w][lane + 32 * k] = 0;
+    __syncwarp();
+    const unsigned m = __match_any_sync(0xffffffffu, b);
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    if (b >= 0 && rank == 0) cnt[w][b] = __popc(m);
+    __syncthreads();
+    if (t < ORDER_BINS) {
+      int run = base[t];
+      for (int k = 0; k < 32; ++k) {
+        const int v = cnt[k][t];
+        cnt[k][t] = run;
+        run += v;
+      }
+      base[t] = run;
+    }
+    __syncthreads();
+    if (b >= 0) order[cnt[w][b] + rank] = i;
+    __syncthreads();
+  }
 }
 
 
@@ -2525,7 +2717,6 @@ static tode_err smem_optin(const void* fn, int bytes, std::atomic<uint64_t>& don
 
 using Cfg32 = MlpCfg<32, 128, 3, false>;
 using Cfg32s = MlpCfg<32, 128, 3, true>;
-using Cfg64w = MlpBigCfg<64, 512, 4>;
 using Cfg64s = MlpWideCfg<64, 512, 4>;  // the wide network's solver (stacked M = 128 tiles)
 
 // the two networks the MLP field is built for
@@ -2544,7 +2735,7 @@ bool mlp_supported(const tode_field_desc* f) {
 }
 
 size_t mlp_workspace_bytes(const tode_field_desc* f, const tode_options* o) {
-  const size_t img = is_d64_h512(f) ? (size_t)Cfg64w::WREP * Cfg64w::WIMG_STRIDE
+  const size_t img = is_d64_h512(f) ? (size_t)Cfg64s::WREP * Cfg64s::WIMG_STRIDE
                                     : (size_t)Cfg32::WREP * Cfg32::WIMG_STRIDE;
   size_t b = align256(256) + img;
   if (o->form == TODE_PLAIN) {  // parked solver state (must match launch_mlp)
@@ -2689,34 +2880,72 @@ tode_err mlp_solve(const SolveReq& r, bool split) {
   return split ? launch_mlp<Cfg32s>(r) : launch_mlp<Cfg32>(r);
 }
 
-// ---- wide network: scratch plan of the staged adjoint
+// ---- wide network: the staged adjoint's scratch and work items
 struct WidePlan {
-  int grid, cap;       // CTAs, reverse rounds per CTA per slice
-  size_t rows;         // staged rows per slice
-  size_t off_timg, off_stage[8], off_dw0, off_ones, off_cublas, total;
+  int grid, cap, items;
+  size_t off_img, off_timg, off_order, off_rounds, off_plane[32], off_part, total;
 };
-static constexpr size_t WIDE_CUBLAS_WS = 32u << 20;
+// The dW/db jobs of the wide adjoint, in the order dW2, dW3, dW1 (with the
+// constant input's column: db1), dW4^T, db2, db3, db4 -- four 128-row blocks
+// each (db4: one) -- with their work items (the chain CTAs split in parts:
+// eight for the 512 x 512 products, four otherwise).  jW[l] / jb[l]: the
+// first job of gradient l.  Returns the number of work items.
+static int wide_dw_jobs(DwArgs* a, int (&jW)[4], int (&jb)[4]) {
+  using L = WideAdj<MlpWideCfg<64, 512, 4>>;
+  int nj = 0, it = 0;
+  auto add = [&](DwJob j, int parts) {
+    if (a) {
+      a->job[nj] = j;
+      a->item0[nj] = it;
+    }
+    it += parts;
+    ++nj;
+  };
+  jW[1] = nj;
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D2, mb, L::T_H1, 4, 128}, 8);
+  jW[2] = nj;
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D3, mb, L::T_H2, 4, 128}, 8);
+  jW[0] = jb[0] = nj;
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D1, mb, L::T_X, 1, 80}, 4);
+  jW[3] = nj;
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_H3, mb, L::T_K, 1, 64}, 4);
+  jb[1] = nj;
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{1, L::T_D2, mb, 0, 0, 16}, 4);
+  jb[2] = nj;
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{1, L::T_D3, mb, 0, 0, 16}, 4);
+  jb[3] = nj;
+  add(DwJob{2, 0, 0, L::T_K, 1, 64}, 4);
+  if (a) {
+    a->njobs = nj;
+    a->item0[nj] = it;
+  }
+  return it;
+}
 static WidePlan wide_plan(int B, int slots, int num_sms) {
-  using Cfg = Cfg64w;
-  using L = WideAdjLayout<Cfg>;
+  using Cfg = Cfg64s;
+  using L = WideAdj<Cfg>;
   WidePlan p{};
   p.grid = (int)std::min<long long>((B + 63) / 64, num_sms);
   p.cap = 7 * std::max(slots, 1);  // one instance per row per slice
-  p.rows = (size_t)p.grid * p.cap * 64;
-  size_t o = align256(256) + (size_t)Cfg::WREP * Cfg::WIMG_STRIDE;
+  const size_t nblk = (size_t)std::max(p.grid, 1) * p.cap;
+  size_t o = align256(256);
+  p.off_img = o;
+  o += (size_t)Cfg::WREP * Cfg::WIMG_STRIDE;
   p.off_timg = o;
-  o += (size_t)Cfg::WREP * L::TIMG_STRIDE;
-  const int width[8] = {Cfg::K0, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::D};
-  for (int q = 0; q < 8; ++q) {  // sa[0..3], sg[0..3]; hi then lo planes
-    p.off_stage[q] = o;
-    o += 2 * align256(p.rows * width[q] * 2);
-  }
-  p.off_dw0 = o;
-  o += align256((size_t)Cfg::H * Cfg::K0 * 4);
-  p.off_ones = o;
-  o += align256(p.rows * 2);
-  p.off_cublas = o;
-  o += WIDE_CUBLAS_WS;
+  o += (size_t)Cfg::WREP * Cfg::WIMG_STRIDE;
+  p.off_order = o;
+  o += align256((size_t)std::max(B, 1) * 4);
+  p.off_rounds = o;
+  o += align256((size_t)std::max(p.grid, 1) * 4);
+  for (int t = 0; t < L::NTEN; ++t)
+    for (int fb = 0; fb < L::t_fb(t); ++fb) {
+      p.off_plane[L::plane_first(t) + fb] = o;
+      o += align256(nblk * 2 * (size_t)L::blk_bytes(t));
+    }
+  int jW[4], jb[4];
+  p.items = wide_dw_jobs(nullptr, jW, jb);
+  p.off_part = o;
+  o += (size_t)p.items * DW_PART_FLOATS * 4;
   p.total = o;
   return p;
 }
@@ -2730,50 +2959,28 @@ size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, int slots, int num_sm
          align256((size_t)grid * L::P_FLOATS * 4);
 }
 
-__global__ void k_fill_bf16_one(uint16_t* p, size_t n) {
-  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (e < n) p[e] = 0x3F80;  // BF16 1.0
-}
-// gW0 [H][65] from the padded [H][80] accumulator
-__global__ void k_copy_cols(const float* src, int rows, int ld, int cols, float* dst) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < rows * cols) dst[e] = src[(size_t)(e / cols) * ld + e % cols];
-}
-
-// one cuBLAS handle per device, created on first use
-static cublasHandle_t cublas_for_device(int dev) {
-  static std::mutex mu;
-  static cublasHandle_t handles[64] = {};
-  std::lock_guard<std::mutex> g(mu);
-  if (dev < 0 || dev >= 64) return nullptr;
-  if (!handles[dev] && cublasCreate(&handles[dev]) != CUBLAS_STATUS_SUCCESS) handles[dev] = nullptr;
-  return handles[dev];
-}
+static constexpr int DW_SMEM = 5 * 32768 + 4096;  // two A slots, three B slots, the ones tile
 
 static tode_err mlp_wide_adjoint(const AdjReq& r) {
-  using Cfg = Cfg64w;
-  using L = WideAdjLayout<Cfg>;
+  using Cfg = Cfg64s;
+  using L = WideAdj<Cfg>;
   const cudaStream_t st = r.stream;
   const WidePlan p = wide_plan(r.B, r.tape->slots, r.num_sms);
   if (r.scratch_bytes < p.total) return TODE_EWORKSPACE;
-  int dev = 0;
-  TODE_CUDA_TRY(cudaGetDevice(&dev));
-  cublasHandle_t hb = cublas_for_device(dev);
-  if (!hb) return TODE_ECUDA;
   char* base = r.scratch;
   WideAdjArgs a{};
   a.K = r.K;
+  a.order = (const int32_t*)(base + p.off_order);
   a.t0 = r.t0;
   a.t1 = r.t1;
   a.te = r.te;
   a.n_acc = r.n_acc;
   a.status = r.status;
   a.slots = r.tape->slots;
-  a.Btot = r.B;
   a.tp_y = (const float*)r.tape->y;
-  a.tp_k1 = (const float*)r.tape->k1;
   a.tp_t = r.tape->t;
   a.tp_h = (const float*)r.tape->h_acc;
+  a.tp_ys = (const float*)r.tape->y_stage;
   a.gye = (const float*)r.gye;
   a.gyf = (const float*)r.gyf;
   a.gy0 = (float*)r.gy0;
@@ -2781,87 +2988,64 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   a.err = (int32_t*)(base + 128);
   a.overflow = r.overflow;
   a.cap = p.cap;
-  a.tp_ys = (const float*)r.tape->y_stage;
-  unsigned char* img = (unsigned char*)base + align256(256);
+  a.rounds = (int32_t*)(base + p.off_rounds);
+  unsigned char* img = (unsigned char*)base + p.off_img;
   unsigned char* timg = (unsigned char*)base + p.off_timg;
   a.wimg = img;
   a.timg = timg;
-  const int width[8] = {Cfg::K0, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::H, Cfg::D};
-  uint16_t* planes[8][2];
-  for (int q = 0; q < 8; ++q) {
-    planes[q][0] = (uint16_t*)(base + p.off_stage[q]);
-    planes[q][1] = (uint16_t*)(base + p.off_stage[q] + align256(p.rows * width[q] * 2));
-  }
-  for (int j = 0; j < 4; ++j)
-    for (int k = 0; k < 2; ++k) {
-      a.sa[j][k] = planes[j][k];
-      a.sg[j][k] = planes[4 + j][k];
-    }
-  float* dw0 = (float*)(base + p.off_dw0);
-  uint16_t* ones = (uint16_t*)(base + p.off_ones);
+  for (int q = 0; q < L::NPLANES; ++q) a.plane[q] = (unsigned char*)base + p.off_plane[q];
+  DwArgs d{};
+  int jW[4], jb[4];
+  wide_dw_jobs(&d, jW, jb);
+  d.cap = p.cap;
+  d.rounds = a.rounds;
+  for (int q = 0; q < L::NPLANES; ++q) d.plane[q] = a.plane[q];
+  d.part = (float*)(base + p.off_part);
+  d.err = a.err;
   // weight images (forward chunks and transposed chunks, WREP copies each)
   {
-    size_t woff[MLP_MAX_LAYERS] = {}, toff[MLP_MAX_LAYERS] = {};
-    for (int l = 0; l < Cfg::NL; ++l) {
-      woff[l] = Cfg::W_off(l);
-      toff[l] = L::T_off(l);
-    }
+    size_t woff[MLP_MAX_LAYERS] = {};
+    for (int l = 0; l < Cfg::NL; ++l) woff[l] = Cfg::W_off(l);
     tode_err e = build_images<Cfg>(r.f, img, IMG_CHUNKS, Cfg::WREP, Cfg::WIMG_STRIDE, woff, st);
     if (e == TODE_OK)
-      e = build_images<Cfg>(r.f, timg, IMG_TCHUNKS, Cfg::WREP, L::TIMG_STRIDE, toff, st);
+      e = build_images<Cfg>(r.f, timg, IMG_TCHUNKS, Cfg::WREP, Cfg::WIMG_STRIDE, woff, st);
     if (e != TODE_OK) return e;
   }
-  k_fill_bf16_one<<<(unsigned)((p.rows + 255) / 256), 256, 0, st>>>(ones, p.rows);
-  TODE_CUDA_TRY(cudaGetLastError());
   TODE_CUDA_TRY(cudaMemsetAsync(base, 0, 256, st));
-  TODE_CUDA_TRY(cudaMemsetAsync(dw0, 0, (size_t)Cfg::H * Cfg::K0 * 4, st));
-  for (int l = 1; l < 4; ++l)
-    TODE_CUDA_TRY(cudaMemsetAsync(r.gW[l], 0, (size_t)Cfg::N_of(l) * Cfg::K_of(l) * 4, st));
-  if (r.gb)
-    for (int l = 0; l < 4; ++l)
-      if (r.gb[l]) TODE_CUDA_TRY(cudaMemsetAsync(r.gb[l], 0, (size_t)Cfg::N_of(l) * 4, st));
+  TODE_CUDA_TRY(cudaMemsetAsync(d.part, 0, (size_t)p.items * DW_PART_FLOATS * 4, st));
+  // the queue: most accepted steps first, so the rows of a tile reverse
+  // instances of similar length (stable: a fixed order every call)
+  k_order_steps_stable<<<1, 1024, 0, st>>>(r.B, StepsBin{r.n_acc, r.status},
+                                           (int32_t*)(base + p.off_order));
+  TODE_CUDA_TRY(cudaGetLastError());
   {
-    static std::atomic<uint64_t> done{0};
-    const tode_err e = smem_optin((const void*)k_mlp_adjoint_wide<Cfg>, L::S_END, done);
+    static std::atomic<uint64_t> d0{0}, d1{0};
+    tode_err e = smem_optin((const void*)k_mlp_adjoint_wide<Cfg>, L::S_END, d0);
+    if (e == TODE_OK) e = smem_optin((const void*)k_mlp_dw<Cfg>, DW_SMEM, d1);
     if (e != TODE_OK) return e;
   }
-  if (cublasSetStream(hb, st) != CUBLAS_STATUS_SUCCESS ||
-      cublasSetWorkspace(hb, base + p.off_cublas, WIDE_CUBLAS_WS) != CUBLAS_STATUS_SUCCESS)
-    return TODE_ECUDA;
-  const float one = 1.0f;
-  // dW_l (row-major [out][in]) += delta_l^T act_l: in cuBLAS's column-major
-  // terms C[in x out] += act[in x R] * delta[out x R]^T
-  auto gemm = [&](const uint16_t* act_p, int in, const uint16_t* del_p, int out, float* C) {
-    return cublasGemmEx(hb, CUBLAS_OP_N, CUBLAS_OP_T, in, out, (int)p.rows, &one, act_p,
-                        CUDA_R_16BF, in, del_p, CUDA_R_16BF, out, &one, C, CUDA_R_32F, in,
-                        CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) == CUBLAS_STATUS_SUCCESS;
-  };
-  auto colsum = [&](const uint16_t* del_p, int out, float* C) {  // db += delta^T 1
-    return cublasGemmEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, out, 1, (int)p.rows, &one, del_p,
-                        CUDA_R_16BF, out, ones, CUDA_R_16BF, (int)p.rows, &one, C, CUDA_R_32F,
-                        out, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) == CUBLAS_STATUS_SUCCESS;
-  };
   const int slice = p.grid * 64;
   for (int i0 = 0; i0 < r.B; i0 += slice) {
-    for (int q = 0; q < 8; ++q)
-      TODE_CUDA_TRY(cudaMemsetAsync(planes[q][0], 0, 2 * align256(p.rows * width[q] * 2), st));
     a.i0 = i0;
     a.B = std::min(slice, r.B - i0);
-    k_mlp_adjoint_wide<Cfg><<<p.grid, 256, L::S_END, st>>>(a);
+    const int cg = (a.B + 63) / 64;
+    k_mlp_adjoint_wide<Cfg><<<cg, 256, L::S_END, st>>>(a);
     TODE_CUDA_TRY(cudaGetLastError());
-    for (int l = 0; l < 4; ++l) {
-      const int in = Cfg::K_of(l), out = Cfg::N_of(l);
-      float* C = l == 0 ? dw0 : r.gW[l];
-      bool ok = gemm(planes[l][0], in, planes[4 + l][0], out, C) &&  // hi * hi
-                gemm(planes[l][1], in, planes[4 + l][0], out, C) &&  // lo * hi
-                gemm(planes[l][0], in, planes[4 + l][1], out, C);    // hi * lo
-      if (ok && r.gb && r.gb[l])
-        ok = colsum(planes[4 + l][0], out, r.gb[l]) && colsum(planes[4 + l][1], out, r.gb[l]);
-      if (!ok) return TODE_ECUDA;
-    }
+    d.chain_grid = cg;
+    k_mlp_dw<Cfg><<<p.items, 128, DW_SMEM, st>>>(d);
+    TODE_CUDA_TRY(cudaGetLastError());
   }
-  k_copy_cols<<<(Cfg::H * (Cfg::D + 1) + 255) / 256, 256, 0, st>>>(dw0, Cfg::H, Cfg::K0, Cfg::D + 1,
-                                                                   r.gW[0]);
+  DwReduceArgs ra{};
+  ra.part = d.part;
+  for (int j = 0; j <= d.njobs; ++j) ra.item0[j] = d.item0[j];
+  for (int l = 0; l < 4; ++l) {
+    ra.jW[l] = jW[l];
+    ra.jb[l] = jb[l];
+    ra.gW[l] = r.gW[l];
+    ra.gb[l] = r.gb ? r.gb[l] : nullptr;
+  }
+  const long long total = 512LL * 65 + 512 + 2 * (512LL * 512 + 512) + 64LL * 512 + 64;
+  k_mlp_dw_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ra);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
 }

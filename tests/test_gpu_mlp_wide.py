@@ -1,6 +1,7 @@
 """The wide MLP field (D = 64, three tanh layers of 512; 1.2 MB of BF16
-weights streamed through shared memory in K chunks, 64-row tiles with M = 64
-tcgen05 MMAs) against the FP64 oracle with the same BF16 weights.
+weights streamed through shared memory in 32 KB stages, 64-instance tiles
+whose hi and lo activation rows stack into M = 128 tcgen05 MMAs) against the
+FP64 oracle with the same BF16 weights.
 Tolerance: 10 (atol + rtol |y|) of a 1e-12-tolerance oracle solution."""
 import numpy as np
 import pytest

@@ -2,7 +2,8 @@
 App. A) against the FP64 oracle adjoint on the GPU's own mesh with the same
 BF16 weights: gy0 and every weight and bias gradient within 2e-3 relative
 l2.  The weight gradients come from the staged rows of every reverse round
-through split BF16 GEMMs (hi*hi + lo*hi + hi*lo)."""
+through the library's own tensor-core products over the split operands
+(hi*hi + lo*hi + hi*lo)."""
 import numpy as np
 import pytest
 import torch
