@@ -333,6 +333,30 @@ tode_err tode_t_eval_grad(int B, int K, int D, tode_prec prec, const void* gy_ev
 tode_err tode_tc_gemm(const void* A, const void* B, float* C, int M, int N, int K, int flags,
                       int32_t* err, void* stream);
 
+/* Micro-benchmark kernels for the rooflines' denominators on the running
+ * GPU (no paper counterpart: measurement infrastructure).  kind selects the
+ * kernel: each thread of the grid x block launch runs iters iterations of 8
+ * independent chains of one operation --
+ *   TODE_PEAK_FMA32  FP32 fused multiply-add (2 FLOP each)
+ *   TODE_PEAK_FFMA2  paired FP32 FMA, two lanes per instruction (4 FLOP)
+ *   TODE_PEAK_FMA64  FP64 fused multiply-add (2 FLOP)
+ *   TODE_PEAK_EX2    ex2.approx (one MUFU operation)
+ *   TODE_PEAK_TANH   tanh.approx (one MUFU operation)
+ * -- so one launch performs grid * block * iters * 8 operations;
+ * TODE_PEAK_EMPTY launches an empty kernel (launch and graph-replay rates;
+ * sink may be NULL).  sink (device, >= block floats) receives nothing in
+ * practice: it only keeps the chains alive.  The caller times the launch
+ * on `stream`.  TODE_EINVAL for a bad kind or shape. */
+enum {
+  TODE_PEAK_FMA32 = 0,
+  TODE_PEAK_FFMA2 = 1,
+  TODE_PEAK_FMA64 = 2,
+  TODE_PEAK_EX2 = 3,
+  TODE_PEAK_TANH = 4,
+  TODE_PEAK_EMPTY = 5
+};
+tode_err tode_peak_kernel(int kind, int grid, int block, int iters, float* sink, void* stream);
+
 /* Static text for an error code. */
 const char* tode_strerror(tode_err e);
 

@@ -15,12 +15,14 @@ TODE_OK, TODE_EINVAL, TODE_EWORKSPACE, TODE_ECUDA, TODE_EUNSUPPORTED, TODE_ETIME
 TODE_VDP, TODE_LINEAR, TODE_MLP = 1, 2, 3
 TODE_F64, TODE_F32, TODE_BF16W, TODE_BF16W_SPLIT = 0, 1, 2, 3
 TODE_PLAIN, TODE_FUSED = 0, 1
+(TODE_PEAK_FMA32, TODE_PEAK_FFMA2, TODE_PEAK_FMA64, TODE_PEAK_EX2, TODE_PEAK_TANH,
+ TODE_PEAK_EMPTY) = range(6)
 STATUS = {"SUCCESS": 0, "MAX_STEPS": 1, "DT_UNDERFLOW": 2, "NONFINITE": 3, "INVALID_INPUT": 4}
 
 # entry points include/tode.h declares
 EXPORTS = ("tode_version", "tode_strerror", "tode_default_options", "tode_workspace_size",
            "tode_solve", "tode_adjoint_scratch_size", "tode_adjoint", "tode_adjoint_static",
-           "tode_tc_gemm", "tode_t_eval_grad")
+           "tode_tc_gemm", "tode_t_eval_grad", "tode_peak_kernel")
 TODE_STATIC_ADJOINT_SCRATCH_BYTES = 32 << 20
 
 _vp = C.c_void_p
@@ -136,6 +138,8 @@ def load(path: str = LIB_PATH):
     lib.tode_adjoint_static.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), _vp, _vp, _vp,
                                         C.c_int, _vp, _vp, C.POINTER(Tape), _vp, _vp, _vp, _vp,
                                         C.POINTER(_vp), C.POINTER(_vp), _vp, _vp]
+    lib.tode_peak_kernel.restype = C.c_int
+    lib.tode_peak_kernel.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp]
     lib.tode_tc_gemm.restype = C.c_int
     lib.tode_tc_gemm.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp]
     _lib = lib

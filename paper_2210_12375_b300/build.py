@@ -29,6 +29,7 @@ UNITS = {
     "tode_static.cu": [],
     "tode_tc_gemm.cu": [],
     "tode_mlp.cu": ["-fmad=false"],
+    "tode_peak.cu": [],
 }
 
 
