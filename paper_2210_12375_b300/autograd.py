@@ -19,6 +19,8 @@ import torch
 from . import api
 
 DEFAULT_BUDGET_BYTES = 40 << 30
+# the most accepted steps the last solve of a problem shape needed
+_LAST_N: dict = {}
 
 
 def _tape_budget(dev, budget: Optional[int]) -> int:
@@ -28,25 +30,47 @@ def _tape_budget(dev, budget: Optional[int]) -> int:
     return int(min(DEFAULT_BUDGET_BYTES, free // 2))
 
 
+def _shape_key(field, y0, opt):
+    return (type(field).__name__, tuple(y0.shape), y0.dtype, str(y0.device),
+            bool(opt.get("joint")))
+
+
 def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint, want_yp=False):
+    """(solution, tape or None, most accepted steps, MLP chunk size or 0)."""
     B, D = y0.shape
     dev, dtype = y0.device, y0.dtype
     mlp = isinstance(field, api.MLP)
+    key = _shape_key(field, y0, opt)
     per_slot = api.TapeBuffers.bytes_per_slot(B, D, y0.element_size(), stages=mlp,
                                               minimal=True)
     max_slots = max(1, budget // max(per_slot, 1))
+    if key in _LAST_N:
+        hint = max(1, int(_LAST_N[key] * 1.25) + 1)
     slots = max(1, min(max_slots, hint))
     tape = api.TapeBuffers.allocate(B, D, dtype, slots, 1, dev, stages=mlp, minimal=True)
     sol = api.solve(field, y0, t0, t1, t_eval, tape=tape, form="fused", want_yp=want_yp, **opt)
     N = int(sol.n_acc.max().item()) if B > 0 else 0
+    _LAST_N[key] = N
+    chunk = 0
     if N > slots:
         full_slot = api.TapeBuffers.bytes_per_slot(B, D, y0.element_size(), stages=mlp)
         if N <= max_slots:
             stride = 1
-        elif mlp or opt.get("joint"):
-            what = "the MLP adjoint" if mlp else "the adjoint of a joint solve"
-            raise RuntimeError(f"{what} keeps every accepted step: {N} slots of "
-                               f"{per_slot} bytes exceed the tape budget of {budget} bytes")
+        elif opt.get("joint"):
+            raise RuntimeError(f"the adjoint of a joint solve keeps every accepted step: {N} "
+                               f"slots of {per_slot} bytes exceed the tape budget of "
+                               f"{budget} bytes")
+        elif mlp:
+            # the batch's tape does not fit: the backward recomputes it chunk
+            # by chunk (instances are independent); the forward needs no tape
+            one = api.TapeBuffers.bytes_per_slot(1, D, y0.element_size(), stages=True,
+                                                 minimal=True)
+            chunk = int(budget // max(one * N, 1))
+            if chunk < 1:
+                raise RuntimeError(f"the MLP adjoint keeps every accepted step of an instance: "
+                                   f"{N} steps of {one} bytes exceed the tape budget of "
+                                   f"{budget} bytes")
+            return sol, None, N, chunk
         else:  # strided segments are re-run: the tape keeps the whole state
             stride = math.ceil(N / max(1, budget // max(full_slot, 1)))
         slots = math.ceil(N / stride)
@@ -55,7 +79,38 @@ def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint, want_yp=False
         # the solve is deterministic: the re-run fills the tape on the same mesh
         sol = api.solve(field, y0, t0, t1, t_eval, tape=tape, form="fused", want_yp=want_yp,
                         **opt)
-    return sol, tape, N
+    return sol, tape, N, chunk
+
+
+def _mlp_adjoint_chunked(field, y0, t0, t1, t_eval, sol, gye, gyf, opt, chunk, N):
+    """The MLP adjoint of a solve whose tape did not fit: every chunk of
+    `chunk` instances is re-solved with a stride-1 stage tape (its meshes and
+    stage inputs are the forward's, bit for bit) and reversed; dL/dy0 per
+    chunk, the weight gradients summed over the chunks in order."""
+    B, D = y0.shape
+    gy0 = torch.empty_like(y0)
+    gW = gb = None
+    for c0 in range(0, B, chunk):
+        c1 = min(B, c0 + chunk)
+        n_c = int(sol.n_acc[c0:c1].max().item())
+        tape = api.TapeBuffers.allocate(c1 - c0, D, y0.dtype, max(1, n_c), 1, y0.device,
+                                        stages=True, minimal=True)
+        te = t_eval[c0:c1].contiguous() if t_eval is not None else None
+        s = api.solve(field, y0[c0:c1].contiguous(), t0[c0:c1].contiguous(),
+                      t1[c0:c1].contiguous(), te, tape=tape, form="fused", **opt)
+        g_e = gye[c0:c1].contiguous() if gye is not None else None
+        g_f = gyf[c0:c1].contiguous() if gyf is not None else None
+        g0, (w_c, b_c), ovf = api.adjoint(field, t0[c0:c1].contiguous(), t1[c0:c1].contiguous(),
+                                          te, s, tape, g_e, g_f, **opt)
+        if int(ovf.item()) != 0:
+            raise RuntimeError("tode_adjoint: the checkpoint tape overflowed")
+        gy0[c0:c1] = g0
+        if gW is None:
+            gW, gb = list(w_c), list(b_c)
+        else:
+            gW = [a + b for a, b in zip(gW, w_c)]
+            gb = [a + b for a, b in zip(gb, b_c)]
+    return gy0, (gW, gb)
 
 
 class _Odeint(torch.autograd.Function):
@@ -64,24 +119,31 @@ class _Odeint(torch.autograd.Function):
         field = spec["field"].with_tensors(list(tensors))
         # dL/dt_eval = <dL/dy_eval, dy/dt>: the forward also writes dy/dt there
         want_yp = t_eval is not None and ctx.needs_input_grad[4]
-        sol, tape, N = _solve_with_tape(field, y0, t0, t1, t_eval, spec["opt"],
-                                        spec["budget"], spec["hint"], want_yp)
+        sol, tape, N, chunk = _solve_with_tape(field, y0, t0, t1, t_eval, spec["opt"],
+                                               spec["budget"], spec["hint"], want_yp)
         spec["last_n_acc_max"] = N
+        spec["mlp_chunk"] = chunk
         ctx.field, ctx.sol, ctx.tape, ctx.opt = field, sol, tape, spec["opt"]
-        ctx.save_for_backward(t0, t1, t_eval)
+        ctx.chunk, ctx.N = chunk, N
+        ctx.save_for_backward(y0, t0, t1, t_eval)
         ctx.mark_non_differentiable(sol.n_acc, sol.n_rej, sol.status)
         return sol.y_eval, sol.y_final, sol.n_acc, sol.n_rej, sol.status
 
     @staticmethod
     def backward(ctx, g_eval, g_final, *_):
-        t0, t1, t_eval = ctx.saved_tensors
+        y0, t0, t1, t_eval = ctx.saved_tensors
         sol, field = ctx.sol, ctx.field
         dtype = sol.y_final.dtype
         gye = g_eval.to(dtype).contiguous() if g_eval is not None and t_eval is not None else None
         gyf = g_final.to(dtype).contiguous() if g_final is not None else None
-        gy0, gp, ovf = api.adjoint(field, t0, t1, t_eval, sol, ctx.tape, gye, gyf, **ctx.opt)
-        if int(ovf.item()) != 0:
-            raise RuntimeError("tode_adjoint: the checkpoint tape overflowed")
+        if ctx.chunk > 0:
+            gy0, gp = _mlp_adjoint_chunked(field, y0.detach(), t0, t1, t_eval, sol, gye, gyf,
+                                           ctx.opt, ctx.chunk, ctx.N)
+        else:
+            gy0, gp, ovf = api.adjoint(field, t0, t1, t_eval, sol, ctx.tape, gye, gyf,
+                                       **ctx.opt)
+            if int(ovf.item()) != 0:
+                raise RuntimeError("tode_adjoint: the checkpoint tape overflowed")
         if isinstance(field, api.MLP):
             gW, gb = gp
             grads = [g.to(w.dtype) for g, w in zip(gW + gb, field.W + field.b)]

@@ -223,3 +223,15 @@ def test_derivative_output_and_t_eval_grad_checked_before_launch():
     assert g(4, 5, 2, _abi.TODE_F64, None, p, p, None) == _abi.TODE_EINVAL
     assert g(4, 5, 0, _abi.TODE_F64, p, p, p, None) == _abi.TODE_EINVAL
     assert g(4, 5, 2, _abi.TODE_BF16W, p, p, p, None) == _abi.TODE_EUNSUPPORTED
+
+
+def test_peak_kernel_rejects_bad_shapes_before_launch():
+    """The micro-benchmark entry validates kind, grid, block and iters
+    before any CUDA call (no GPU needed)."""
+    lib = _abi.load()
+    bad = [(99, 1, 32, 1), (_abi.TODE_PEAK_FMA32, 0, 32, 1), (_abi.TODE_PEAK_FMA32, 1, 0, 1),
+           (_abi.TODE_PEAK_FMA32, 1, 2048, 1), (_abi.TODE_PEAK_FMA32, 1, 32, -1)]
+    for kind, grid, block, iters in bad:
+        assert lib.tode_peak_kernel(kind, grid, block, iters, None, None) == _abi.TODE_EINVAL
+    # the arithmetic kernels need a sink
+    assert lib.tode_peak_kernel(_abi.TODE_PEAK_EX2, 1, 32, 1, None, None) == _abi.TODE_EINVAL

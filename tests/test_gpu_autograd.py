@@ -91,11 +91,31 @@ def test_autograd_mlp_matches_direct_adjoint_call():
         assert np.array_equal(a, b.double().cpu().numpy())
 
 
-def test_autograd_mlp_over_budget_raises():
-    w = dict(make(4, B=128), split=True)
+@pytest.mark.parametrize("cfg,B", [(4, 300), (5, 150)])
+def test_autograd_mlp_budget_recomputes_chunks(cfg, B):
+    """A tape budget below the batch's stage tape: the backward re-solves
+    the batch chunk by chunk with tapes that fit and reverses each chunk.
+    dL/dy0 equals the full tape's bit for bit (an instance's solve and
+    reversal do not depend on its batch); the weight and bias gradients are
+    the same per-row products summed chunk by chunk, so they differ only by
+    FP32 summation order: measured 3.3e-5 relative on the D = 32 field,
+    where the per-CTA partials of a few hundred instances cancel heavily
+    (a dropped or doubled chunk would differ at O(1)); a budget below one
+    instance's tape is refused."""
+    w = dict(make(cfg, B=B), split=True)
     field = device_field(w, torch.float32)
+    full = _loss_and_grads(w, torch.float32, field)
+    n_max = int(full[2].max())
+    D = w["y0"].shape[1]
+    one = tode.TapeBuffers.bytes_per_slot(1, D, 4, stages=True, minimal=True)
+    budget = one * n_max * (B // 3 + 1)  # three or four chunks
+    small = _loss_and_grads(w, torch.float32, field, hbm_budget_bytes=budget)
+    assert np.array_equal(full[0].cpu().numpy(), small[0].cpu().numpy())
+    assert np.array_equal(full[3][0], small[3][0])  # dL/dy0
+    for a, b in zip(full[3][1:], small[3][1:]):
+        assert np.linalg.norm(a - b) <= 2e-4 * max(np.linalg.norm(a), 1e-30)
     with pytest.raises(RuntimeError):
-        _loss_and_grads(w, torch.float32, field, hbm_budget_bytes=1, slots_hint=1)
+        _loss_and_grads(w, torch.float32, field, hbm_budget_bytes=one)
 
 
 def test_autograd_joint_solve_vs_oracle_adjoint_on_the_shared_mesh():
