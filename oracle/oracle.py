@@ -99,6 +99,7 @@ def _load():
         lib.orc_solve_yp.restype = C.c_int
         lib.orc_replay.restype = C.c_int
         lib.orc_adjoint.restype = C.c_int
+        lib.orc_adjoint_t.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -348,11 +349,14 @@ def replay(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None,
 
 
 def adjoint(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None, gy_eval=None,
-            gy_final=None, nthreads: int = 0) -> dict:
+            gy_final=None, nthreads: int = 0, want_t_bounds: bool = False) -> dict:
     """Discrete adjoint of the fixed-mesh map (App. A, backprop through the
     solver).  Returns gy0 [B,D] and the parameter cotangents: ``gmu`` [B]
     (VdP), ``gA`` [B,D,D] (linear) or ``gW``/``gb`` lists summed over the
-    batch (MLP)."""
+    batch (MLP).  With ``want_t_bounds``, also ``gt0`` and ``gt1`` [B]: the
+    gradients with respect to t0 and t1 of the same frozen map (every step
+    size but the last and every evaluation point's step held, the last step
+    ending at t1)."""
     lib = _load()
     y0 = np.asarray(y0, dtype=np.float64)
     B = y0.shape[0]
@@ -387,10 +391,14 @@ def adjoint(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None, gy_eva
         gb_ptrs = (_dp * len(gb))(*[_ptr(b) for b in gb])
         out["gW"] = gW
         out["gb"] = gb
-    lib.orc_adjoint(C.byref(fh.f), C.c_int(B), _ptr(y0), _ptr(_f64(t0, (B,))),
-                    _ptr(_f64(t1, (B,))), _ptr(mesh_t), _ptr(mesh_h), _iptr(mesh_n),
-                    C.c_int(cap), _ptr(t_eval), C.c_int(K), _ptr(gye), _ptr(gyf), _ptr(gy0),
-                    _ptr(gparam), gW_ptrs, gb_ptrs, C.c_int(nthreads))
+    gt0 = np.zeros(B) if want_t_bounds else None
+    gt1 = np.zeros(B) if want_t_bounds else None
+    lib.orc_adjoint_t(C.byref(fh.f), C.c_int(B), _ptr(y0), _ptr(_f64(t0, (B,))),
+                      _ptr(_f64(t1, (B,))), _ptr(mesh_t), _ptr(mesh_h), _iptr(mesh_n),
+                      C.c_int(cap), _ptr(t_eval), C.c_int(K), _ptr(gye), _ptr(gyf), _ptr(gy0),
+                      _ptr(gparam), gW_ptrs, gb_ptrs, _ptr(gt0), _ptr(gt1), C.c_int(nthreads))
+    if want_t_bounds:
+        out["gt0"], out["gt1"] = gt0, gt1
     out["gy0"] = gy0
     return out
 

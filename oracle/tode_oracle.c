@@ -474,6 +474,7 @@ typedef struct {
   int mesh_cap;
   const double *gy_eval, *gy_final;
   double *gy0, *gparam; /* gparam: VdP [B], linear [B][D][D] */
+  double *gt0, *gt1;    /* optional: dL/dt0, dL/dt1 [B] */
   double **gW_part, **gb_part; /* MLP per-thread partial sums */
   /* threading */
   int nthreads;
@@ -681,7 +682,8 @@ static void replay_one(const job *J, int i, double *work, double *act, double *y
 /* parameter cotangents.                                                     */
 /* ------------------------------------------------------------------------ */
 static void vjp(const job *J, int i, double t, const double *y, const double *v, double *gy,
-                double *gparam_i, double *gW, double *gb, double *act, double *dscr) {
+                double *gparam_i, double *gW, double *gb, double *act, double *dscr,
+                double *gt) {
   const orc_field *F = J->F;
   const int D = F->D;
   if (F->kind == ORC_VDP) {
@@ -738,7 +740,8 @@ static void vjp(const job *J, int i, double t, const double *y, const double *v,
       if (l > 0) {
         for (int cidx = 0; cidx < nin; ++cidx) delta[cidx] = ga[cidx] * (1.0 - a[cidx] * a[cidx]);
       } else {
-        for (int r = 0; r < D; ++r) gy[r] = gy[r] + ga[r]; /* drop the t input */
+        for (int r = 0; r < D; ++r) gy[r] = gy[r] + ga[r];
+        if (gt) *gt = *gt + ga[D]; /* the t input: df/dt^T v */
       }
     }
   }
@@ -748,7 +751,23 @@ static void vjp(const job *J, int i, double t, const double *y, const double *v,
  * replay_one).  For step n with stages Y_i, k_i = f(t_n + c_i h, Y_i):
  *   kbar_i = h b_i ybar_{n+1} + sum_{tau in step} h b_i(theta_tau) ybar_tau
  *   for i = 7..1: g_i = J_f(Y_i)^T kbar_i, kbar_j += h a_ij g_i (j < i)
- *   ybar_n = ybar_{n+1} + sum_tau ybar_tau + sum_i g_i. */
+ *   ybar_n = ybar_{n+1} + sum_tau ybar_tau + sum_i g_i.
+ * With gt0 / gt1, also the gradients with respect to the integration bounds
+ * of the same frozen map, read this way: every accepted step size but the
+ * last and every evaluation point's step are constants, t_n = t0 + sum_{j<n}
+ * h_j for n < N, and the last step h_{N-1} = t1 - t_{N-1} absorbs the rest.
+ * A step's size enters through y_{n+1} = y_n + h sum b_i k_i, the stage
+ * inputs Y_i = y_n + h sum_j a_ij k_j at times t_n + c_i h, and the dense
+ * outputs y_n + h sum b_i(theta) k_i with theta = (tau - t_n) / h:
+ *   hbar_n = <ybar_{n+1}, sum_i b_i k_i>
+ *          + sum_tau <ybar_tau, sum_i (b_i(theta) - theta b_i'(theta)) k_i>
+ *          + sum_i <g_i, sum_j a_ij k_j> + sum_i c_i gt_i
+ * and its start time through the abscissae and the field's time argument:
+ *   tbar_n = -sum_tau <ybar_tau, sum_i b_i'(theta) k_i> + sum_i gt_i,
+ * gt_i = (df/dt at stage i)^T kbar_i (0 for autonomous fields).  A point at
+ * a step's end counts as theta = 1 of that step, a point at t0 as theta = 0
+ * of the first.  Then dL/dt1 = hbar_{N-1} and dL/dt0 = sum_n tbar_n -
+ * hbar_{N-1}. */
 static void adjoint_one(const job *J, int i, double *work, double *act, double *dscr,
                         double *gW, double *gb) {
   const orc_field *F = J->F;
@@ -760,6 +779,9 @@ static void adjoint_one(const job *J, int i, double *work, double *act, double *
   double *ys = (double *)malloc(sizeof(double) * (size_t)(N + 1) * D);
   double *yb = work, *k = yb + D, *Y = k + NS * D, *kb = Y + NS * D, *g = kb + NS * D;
   double *scratch = g + D;
+  double *tv = (double *)malloc(sizeof(double) * (size_t)2 * D); /* sum_i w_i k_i, scratch */
+  const int want_t = J->gt0 != NULL || J->gt1 != NULL;
+  double tbar = 0.0, hbar_last = 0.0;
   double *gp = NULL;
   if (F->kind == ORC_VDP) gp = J->gparam + i;
   if (F->kind == ORC_LINEAR) gp = J->gparam + (size_t)i * D * D;
@@ -781,41 +803,83 @@ static void adjoint_one(const job *J, int i, double *work, double *act, double *
     const double *y = ys + (size_t)n * D;
     feval(&c, t, y, k);
     dp_stages(&c, t, h, y, D, k, Y);
+    double hbar = 0.0;
+    if (want_t) { /* <ybar_{n+1}, sum b_i k_i> (dp_stages left k_7 = f(t_{n+1}, y_{n+1})) */
+      for (int j = 0; j < D; ++j) {
+        double s = 0.0;
+        for (int q = 0; q < NS; ++q) s = s + DP_B[q] * k[q * D + j];
+        hbar = hbar + yb[j] * s;
+      }
+    }
     /* cotangents of the stage values */
     for (int s = 0; s < NS; ++s)
       for (int j = 0; j < D; ++j) kb[s * D + j] = h * DP_B[s] * yb[j];
     while (cur >= 0 && dir * te[cur] > dir * t) {
       if (gye) {
         const double *gq = gye + (size_t)cur * D;
+        double bt[NS];
         if (te[cur] == t_next) {
           /* this output is y_{n+1} itself: y_{n+1} = y_n + h sum b_i k_i */
-          for (int s = 0; s < NS; ++s)
-            for (int j = 0; j < D; ++j) kb[s * D + j] = kb[s * D + j] + h * DP_B[s] * gq[j];
+          for (int s = 0; s < NS; ++s) bt[s] = DP_B[s];
         } else {
-          double bt[NS];
           orc_dense_weights((te[cur] - t) / h, bt);
-          for (int s = 0; s < NS; ++s)
-            for (int j = 0; j < D; ++j) kb[s * D + j] = kb[s * D + j] + h * bt[s] * gq[j];
         }
+        for (int s = 0; s < NS; ++s)
+          for (int j = 0; j < D; ++j) kb[s * D + j] = kb[s * D + j] + h * bt[s] * gq[j];
         for (int j = 0; j < D; ++j) yb[j] = yb[j] + gq[j];
+        if (want_t) {
+          const double th = te[cur] == t_next ? 1.0 : (te[cur] - t) / h;
+          dp_dense_deriv(th, k, D, tv); /* sum_i b_i'(theta) k_i */
+          for (int j = 0; j < D; ++j) {
+            double s = 0.0;
+            for (int q = 0; q < NS; ++q) s = s + bt[q] * k[q * D + j];
+            hbar = hbar + gq[j] * (s - th * tv[j]);
+            tbar = tbar - gq[j] * tv[j];
+          }
+        }
       }
       cur--;
     }
     for (int s = NS - 1; s >= 0; --s) {
+      double gts = 0.0;
       for (int j = 0; j < D; ++j) g[j] = 0.0;
-      vjp(J, i, t + DP_C[s] * h, Y + s * D, kb + s * D, g, gp, gW, gb, act, dscr);
+      vjp(J, i, t + DP_C[s] * h, Y + s * D, kb + s * D, g, gp, gW, gb, act, dscr,
+          want_t ? &gts : NULL);
+      if (want_t) {
+        for (int j = 0; j < D; ++j) {
+          double s2 = 0.0;
+          for (int l = 0; l < s; ++l) s2 = s2 + DP_A[s][l] * k[l * D + j];
+          hbar = hbar + g[j] * s2;
+        }
+        hbar = hbar + DP_C[s] * gts;
+        tbar = tbar + gts;
+      }
       for (int l = 0; l < s; ++l)
         for (int j = 0; j < D; ++j) kb[l * D + j] = kb[l * D + j] + h * DP_A[s][l] * g[j];
       for (int j = 0; j < D; ++j) yb[j] = yb[j] + g[j];
     }
+    if (n == N - 1) hbar_last = hbar;
   }
-  /* evaluation points at t0 are y0 itself */
+  /* evaluation points at t0 are y0 itself (theta = 0 of the first step:
+   * the abscissa's derivative is f(t0, y0)) */
+  double *f0 = NULL;
   while (cur >= 0) {
-    if (gye && te[cur] == t0)
+    if (gye && te[cur] == t0) {
       for (int j = 0; j < D; ++j) yb[j] = yb[j] + gye[(size_t)cur * D + j];
+      if (want_t) {
+        if (!f0) {
+          f0 = tv + D;
+          feval(&c, t0, ys, f0);
+        }
+        for (int j = 0; j < D; ++j) tbar = tbar - gye[(size_t)cur * D + j] * f0[j];
+      }
+    }
     cur--;
   }
   for (int j = 0; j < D; ++j) J->gy0[(size_t)i * D + j] = yb[j];
+  if (J->gt1) J->gt1[i] = hbar_last;
+  if (J->gt0) J->gt0[i] = tbar - hbar_last;
+  free(tv);
   free(ys);
 }
 
@@ -962,11 +1026,26 @@ int orc_replay(const orc_field *F, int B, const double *y0, const double *t0, co
 
 /* gparam: VdP [B] (d/dmu), linear [B][D][D] (d/dA); MLP: gW[l], gb[l] summed
  * over the batch (per-thread partials added in thread order). */
+int orc_adjoint_t(const orc_field *F, int B, const double *y0, const double *t0,
+                  const double *t1, const double *mesh_t, const double *mesh_h,
+                  const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
+                  const double *gy_eval, const double *gy_final, double *gy0, double *gparam,
+                  double *const *gW, double *const *gb, double *gt0, double *gt1, int nthreads);
 int orc_adjoint(const orc_field *F, int B, const double *y0, const double *t0, const double *t1,
                 const double *mesh_t, const double *mesh_h, const int32_t *mesh_n, int mesh_cap,
                 const double *t_eval, int K, const double *gy_eval, const double *gy_final,
                 double *gy0, double *gparam, double *const *gW, double *const *gb,
                 int nthreads) {
+  return orc_adjoint_t(F, B, y0, t0, t1, mesh_t, mesh_h, mesh_n, mesh_cap, t_eval, K, gy_eval,
+                       gy_final, gy0, gparam, gW, gb, NULL, NULL, nthreads);
+}
+/* orc_adjoint, plus dL/dt0 and dL/dt1 of the frozen map when gt0 / gt1 are
+ * not NULL ([B]; see adjoint_one). */
+int orc_adjoint_t(const orc_field *F, int B, const double *y0, const double *t0,
+                  const double *t1, const double *mesh_t, const double *mesh_h,
+                  const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
+                  const double *gy_eval, const double *gy_final, double *gy0, double *gparam,
+                  double *const *gW, double *const *gb, double *gt0, double *gt1, int nthreads) {
   /* the adjoint of a stacked problem is the per-instance adjoint on the
    * shared mesh (every block's Jacobian is its own); call it that way */
   if (F->kind == ORC_STACKED) return -1;
@@ -987,6 +1066,8 @@ int orc_adjoint(const orc_field *F, int B, const double *y0, const double *t0, c
   J.gy_final = gy_final;
   J.gy0 = gy0;
   J.gparam = gparam;
+  J.gt0 = gt0;
+  J.gt1 = gt1;
   double *ye_dummy = (double *)malloc(sizeof(double) * ((size_t)B * K * F->D + 1));
   double *yf_dummy = (double *)malloc(sizeof(double) * ((size_t)B * F->D + 1));
   J.y_eval = ye_dummy;

@@ -717,3 +717,95 @@ def test_starting_step_van_der_pol_exact(direction):
     got = r["trace_h"][0, 0]
     assert math.copysign(1.0, got) == direction
     assert abs(abs(got) / expect - 1.0) < 1e-11, (got, expect)
+
+
+# ---------------------------------------------------------------- t0, t1 gradients
+def _interior_t_eval(mt, mn, t0, t1, K, rng):
+    """K evaluation points per instance strictly inside (t0, t1), none within
+    1e-3 of the interval's length of a mesh point (so a small move of the
+    mesh leaves every point in its step)."""
+    B = len(t0)
+    te = np.zeros((B, K))
+    for i in range(B):
+        pts = np.concatenate([mt[i, :mn[i]], [t1[i]]])
+        span = abs(t1[i] - t0[i])
+        got = []
+        while len(got) < K:
+            x = t0[i] + (t1[i] - t0[i]) * rng.uniform(0.02, 0.98)
+            if np.min(np.abs(pts - x)) > 1e-3 * span:
+                got.append(x)
+        got = np.array(sorted(got, key=lambda v: (v - t0[i]) * np.sign(t1[i] - t0[i])))
+        te[i] = got
+    return te
+
+
+def _loss_replay(field, y0, t0, t1, mt, mh, mn, te, gye, gyf):
+    r = oracle.replay(field, y0, t0, t1, mt, mh, mn, te)
+    return (gye * r["y_eval"]).sum(axis=(1, 2)) + (gyf * r["y_final"]).sum(axis=1)
+
+
+@pytest.mark.parametrize("case", ["vdp", "vdp_backward", "linear", "mlp"])
+def test_t_bounds_gradient_matches_frozen_mesh_differences(case):
+    """dL/dt0 and dL/dt1 of the frozen map (every step size but the last and
+    every point's step held; t0 moves every mesh point before t1, the last
+    step absorbs the change) against central differences of the fixed-mesh
+    replay moved that way; for the autonomous fields also the time-translation
+    identity dL/dt0 + dL/dt1 = -sum_tau <ybar_tau, dy/dt(tau)>.  The MLP field
+    takes t as an input, so its stage times enter too."""
+    rng = np.random.default_rng(7)
+    cfg = {"vdp": 1, "vdp_backward": 1, "linear": 2, "mlp": 4}[case]
+    B = 3 if case == "mlp" else 5
+    w = workloads.make(cfg, B=B)
+    t0, t1 = w["t0"].copy(), w["t1"].copy()
+    if case == "vdp_backward":
+        t0, t1 = t1.copy(), t0.copy() + 2.0  # integrate from t1 down to below 0
+        t1 = np.full(B, -1.0)
+    rt = dict(rtol=1e-6, atol=1e-6)
+    K = 5
+    te0 = np.linspace(0, 1, K)[None, :] * (t1 - t0)[:, None] + t0[:, None]
+    r = oracle.solve(w["field"], w["y0"], t0, t1, te0, rt, trace_cap=4000)
+    assert (r["status"] == 0).all()
+    mt, mh, mn = mesh_from_trace(r)
+    te = _interior_t_eval(mt, mn, t0, t1, K, rng)
+    D = w["y0"].shape[1]
+    gye = rng.standard_normal((B, K, D))
+    gyf = rng.standard_normal((B, D))
+    adj = oracle.adjoint(w["field"], w["y0"], t0, t1, mt, mh, mn, te, gye, gyf,
+                         want_t_bounds=True)
+    fd0, fd1 = np.zeros(B), np.zeros(B)
+    for i in range(B):
+        eps = 1e-6 * max(1.0, abs(t1[i]), abs(t0[i]))
+        N = mn[i]
+        sl = slice(i, i + 1)
+        for which in (0, 1):
+            vals = []
+            for sgn in (1.0, -1.0):
+                a0, a1 = t0[sl].copy(), t1[sl].copy()
+                m_t, m_h = mt[sl].copy(), mh[sl].copy()
+                if which == 1:
+                    a1 += sgn * eps
+                    m_h[0, N - 1] += sgn * eps
+                else:
+                    a0 += sgn * eps
+                    m_t[0, :N] += sgn * eps
+                    m_h[0, N - 1] -= sgn * eps
+                f = dict(w["field"])
+                for k in ("mu", "A", "Q", "lam"):
+                    if k in f:
+                        f[k] = f[k][sl]
+                vals.append(_loss_replay(f, w["y0"][sl], a0, a1, m_t, m_h, mn[sl], te[sl],
+                                         gye[sl], gyf[sl])[0])
+            (fd1 if which == 1 else fd0)[i] = (vals[0] - vals[1]) / (2 * eps)
+    for g, fd in ((adj["gt0"], fd0), (adj["gt1"], fd1)):
+        scale = np.maximum(np.abs(fd), 1e-3)
+        assert (np.abs(g - fd) <= 1e-5 * scale).all(), (case, g, fd)
+    if case != "mlp":
+        # with interior points, and with points at t0 and t1 themselves (the
+        # first counts as theta = 0 of the first step, the last as theta = 1
+        # of the last; finite differences cannot move them, the identity can)
+        for pts in (te, te0):
+            yp = oracle.solve(w["field"], w["y0"], t0, t1, pts, rt, want_yp=True)["yp_eval"]
+            a = oracle.adjoint(w["field"], w["y0"], t0, t1, mt, mh, mn, pts, gye, gyf,
+                               want_t_bounds=True)
+            ident = -(gye * yp).sum(axis=(1, 2))
+            assert np.allclose(a["gt0"] + a["gt1"], ident, rtol=1e-9, atol=1e-9)
