@@ -313,6 +313,31 @@ tode_err tode_adjoint_static(const tode_field_desc* f, const tode_options* o, co
 tode_err tode_t_eval_grad(int B, int K, int D, tode_prec prec, const void* gy_eval,
                           const void* yp_eval, double* g_t_eval, void* stream);
 
+/* Gradients with respect to the integration bounds t0 and t1 of a solve's
+ * frozen map (the discrete-adjoint reading of App. A, extended to the two
+ * boundary times): every accepted step size but the last and every
+ * evaluation point's step are held, t0 moves every mesh point before t1, and
+ * the last step h = t1 - t_{N-1} absorbs the change.  Van der Pol and linear
+ * fields (autonomous: the bounds enter through the dense-output abscissae
+ * and the last step), independent solving, a stride-1 tape with h_acc filled
+ * by the solve; TODE_EUNSUPPORTED for the MLP field or a joint solve,
+ * TODE_EINVAL for a strided tape.
+ *  g_t1 [B] (double, required) = dL/dt1: the last step size's cotangent.
+ *  g_t0 [B] (double, may be NULL) = dL/dt0 = -sum_q <gy_eval[q], yp_eval[q]>
+ *  - dL/dt1 (translating both bounds shifts every output by -dy/dt); needs
+ *  yp_eval [B][K][D] from the same solve (tode_solve's dy/dt output) when
+ *  gy_eval is given.
+ * gy_eval [B][K][D] and gy_final [B][D] (state dtype, NULL = 0) as for
+ * tode_adjoint; instances whose status is not TODE_S_SUCCESS (or that needed
+ * more tape slots than the tape has) get NaN; an instance with t1 = t0 gets
+ * g_t1 = 0.  Backward instances (t1 < t0) are handled in their own
+ * direction.  Enqueued on stream; allocates nothing. */
+tode_err tode_t_bounds_grad(const tode_field_desc* f, const tode_options* o, const double* t0,
+                            const double* t1, const double* t_eval, int K, const int32_t* n_acc,
+                            const int32_t* status, const tode_tape* tape, const void* gy_eval,
+                            const void* gy_final, const void* yp_eval, double* g_t0,
+                            double* g_t1, void* stream);
+
 /* The MLP field's tensor-core building block on its own, for checking the
  * operand layouts and tensor-memory conventions against a plain product:
  * C[M][N] = sum_k A(m,k) B(n,k) with A, B BF16 (uint16 bit patterns) and C

@@ -22,7 +22,8 @@ STATUS = {"SUCCESS": 0, "MAX_STEPS": 1, "DT_UNDERFLOW": 2, "NONFINITE": 3, "INVA
 # entry points include/tode.h declares
 EXPORTS = ("tode_version", "tode_strerror", "tode_default_options", "tode_workspace_size",
            "tode_solve", "tode_adjoint_scratch_size", "tode_adjoint", "tode_adjoint_static",
-           "tode_tc_gemm", "tode_t_eval_grad", "tode_peak_kernel")
+           "tode_tc_gemm", "tode_t_eval_grad", "tode_peak_kernel",
+           "tode_t_bounds_grad")
 TODE_STATIC_ADJOINT_SCRATCH_BYTES = 32 << 20
 
 _vp = C.c_void_p
@@ -138,6 +139,10 @@ def load(path: str = LIB_PATH):
     lib.tode_adjoint_static.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), _vp, _vp, _vp,
                                         C.c_int, _vp, _vp, C.POINTER(Tape), _vp, _vp, _vp, _vp,
                                         C.POINTER(_vp), C.POINTER(_vp), _vp, _vp]
+    lib.tode_t_bounds_grad.restype = C.c_int
+    lib.tode_t_bounds_grad.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), _vp, _vp, _vp,
+                                       C.c_int, _vp, _vp, C.POINTER(Tape), _vp, _vp, _vp, _vp,
+                                       _vp, _vp]
     lib.tode_peak_kernel.restype = C.c_int
     lib.tode_peak_kernel.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp]
     lib.tode_tc_gemm.restype = C.c_int

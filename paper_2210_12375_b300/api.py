@@ -343,3 +343,29 @@ def adjoint(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=Non
         _ptr(overflow), _ptr(scratch), C.c_size_t(scratch.numel()), _stream_handle(stream))
     _abi.check(code, "tode_adjoint")
     return gy0, gparam, overflow
+
+
+def t_bounds_grad(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=None,
+                  gy_final=None, *, stream=None, want_t0: bool = True, **opt_kw):
+    """(dL/dt0, dL/dt1) [B] float64 of the forward solve that filled
+    ``tape`` (stride 1 with the accepted step sizes): the frozen map with
+    every step size but the last held and the last ending at t1.  dL/dt0
+    needs the solve's dy/dt at the points (``want_yp=True``) when gy_eval is
+    given.  Van der Pol and linear fields."""
+    lib = _abi.load()
+    B, D = sol.y_final.shape
+    K = 0 if t_eval is None else t_eval.shape[1]
+    dev = sol.y_final.device
+    opts = make_options(prec=_prec_of(field, sol.y_final), **opt_kw)
+    keep = []
+    fd = field.desc(B, D, keep)
+    tape_c = tape.c()
+    g1 = torch.empty(B, dtype=torch.float64, device=dev)
+    g0 = torch.empty(B, dtype=torch.float64, device=dev) if want_t0 else None
+    yp = sol.yp_eval if (want_t0 and K > 0 and gy_eval is not None) else None
+    code = lib.tode_t_bounds_grad(
+        C.byref(fd), C.byref(opts), _ptr(t0), _ptr(t1), _ptr(t_eval) if K > 0 else None,
+        int(K), _ptr(sol.n_acc), _ptr(sol.status), C.byref(tape_c), _ptr(gy_eval),
+        _ptr(gy_final), _ptr(yp), _ptr(g0), _ptr(g1), _stream_handle(stream))
+    _abi.check(code, "tode_t_bounds_grad")
+    return g0, g1

@@ -117,14 +117,23 @@ class _Odeint(torch.autograd.Function):
     @staticmethod
     def forward(ctx, spec, y0, t0, t1, t_eval, *tensors):
         field = spec["field"].with_tensors(list(tensors))
-        # dL/dt_eval = <dL/dy_eval, dy/dt>: the forward also writes dy/dt there
-        want_yp = t_eval is not None and ctx.needs_input_grad[4]
+        # dL/dt_eval = <dL/dy_eval, dy/dt> and dL/dt0 (which sums those):
+        # the forward also writes dy/dt there
+        want_t = ctx.needs_input_grad[2] or ctx.needs_input_grad[3]
+        want_yp = t_eval is not None and (ctx.needs_input_grad[4] or ctx.needs_input_grad[2])
+        if want_t and (isinstance(spec["field"], api.MLP) or spec["opt"].get("joint")):
+            raise RuntimeError("gradients with respect to t0 and t1 are built for the Van der "
+                               "Pol and linear fields, solved independently")
         sol, tape, N, chunk = _solve_with_tape(field, y0, t0, t1, t_eval, spec["opt"],
                                                spec["budget"], spec["hint"], want_yp)
         spec["last_n_acc_max"] = N
         spec["mlp_chunk"] = chunk
         ctx.field, ctx.sol, ctx.tape, ctx.opt = field, sol, tape, spec["opt"]
         ctx.chunk, ctx.N = chunk, N
+        if want_t and tape is not None and tape.stride != 1:
+            raise RuntimeError("gradients with respect to t0 and t1 need one tape slot per "
+                               "accepted step: raise hbm_budget_bytes")
+        ctx.want_t = want_t
         ctx.save_for_backward(y0, t0, t1, t_eval)
         ctx.mark_non_differentiable(sol.n_acc, sol.n_rej, sol.status)
         return sol.y_eval, sol.y_final, sol.n_acc, sol.n_rej, sol.status
@@ -150,9 +159,15 @@ class _Odeint(torch.autograd.Function):
         else:
             grads = [gp]
         g_te = None
-        if sol.yp_eval is not None and gye is not None:
+        if sol.yp_eval is not None and gye is not None and ctx.needs_input_grad[4]:
             g_te = api.t_eval_grad(gye, sol.yp_eval).to(t_eval.dtype)
-        return (None, gy0, None, None, g_te, *grads)
+        g_t0 = g_t1 = None
+        if ctx.want_t:
+            g_t0, g_t1 = api.t_bounds_grad(field, t0, t1, t_eval, sol, ctx.tape, gye, gyf,
+                                           want_t0=ctx.needs_input_grad[2], **ctx.opt)
+            g_t0 = g_t0.to(t0.dtype) if g_t0 is not None and ctx.needs_input_grad[2] else None
+            g_t1 = g_t1.to(t1.dtype) if ctx.needs_input_grad[3] else None
+        return (None, gy0, g_t0, g_t1, g_te, *grads)
 
 
 def odeint_adjoint(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
@@ -165,8 +180,10 @@ def odeint_adjoint(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
 
     Returns (y_eval [B,K,D], y_final [B,D], n_acc, n_rej, status); the counters
     and the status carry no gradient.  A t_eval that requires grad receives
-    dL/dt_eval through dy/dt of the dense output (Van der Pol and linear).  Keyword options as in
-    ``make_options`` (the fused form is used).
+    dL/dt_eval through dy/dt of the dense output; t0 and t1 that require grad
+    receive the gradients of the frozen map with respect to the integration
+    bounds (Van der Pol and linear fields; one tape slot per accepted step).
+    Keyword options as in ``make_options`` (the fused form is used).
     """
     opt = {k: v for k, v in opt_kw.items() if k != "form"}
     spec = {"field": field, "opt": opt, "budget": _tape_budget(y0.device, hbm_budget_bytes),

@@ -263,6 +263,41 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
   return o->prec == TODE_F64 ? simt_adjoint_f64(r) : simt_adjoint_f32(r);
 }
 
+tode_err tode_t_bounds_grad(const tode_field_desc* f, const tode_options* o, const double* t0,
+                            const double* t1, const double* t_eval, int K, const int32_t* n_acc,
+                            const int32_t* status, const tode_tape* tape, const void* gy_eval,
+                            const void* gy_final, const void* yp_eval, double* g_t0,
+                            double* g_t1, void* stream) {
+  if (!opts_ok(o) || K < 0) return TODE_EINVAL;
+  tode_err e = field_ok(f, o);
+  if (e != TODE_OK) return e;
+  if (f->kind == TODE_MLP || o->joint) return TODE_EUNSUPPORTED;
+  if (f->B == 0) return TODE_OK;
+  if (!t0 || !t1 || !n_acc || !status || !tape || !g_t1) return TODE_EINVAL;
+  if (K > 0 && !t_eval) return TODE_EINVAL;
+  if (g_t0 && K > 0 && gy_eval && !yp_eval) return TODE_EINVAL;
+  if (!tape_ok(tape, o, f) || tape->stride != 1 || !tape->h_acc) return TODE_EINVAL;
+  AdjReq r{};
+  r.f = f;
+  r.o = o;
+  r.B = f->B;
+  r.D = f->D;
+  r.K = K;
+  r.t0 = t0;
+  r.t1 = t1;
+  r.te = t_eval;
+  r.n_acc = n_acc;
+  r.status = status;
+  r.tape = tape;
+  r.gye = gy_eval;
+  r.gyf = gy_final;
+  r.stream = (cudaStream_t)stream;
+  e = device_sms(&r.num_sms);
+  if (e != TODE_OK) return e;
+  return o->prec == TODE_F64 ? simt_t_bounds_f64(r, yp_eval, g_t0, g_t1)
+                             : simt_t_bounds_f32(r, yp_eval, g_t0, g_t1);
+}
+
 }  // extern "C"
 
 namespace tode {

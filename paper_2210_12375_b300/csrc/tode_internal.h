@@ -118,6 +118,8 @@ tode_err simt_solve_f64(const SolveReq& r);  // both: independent or joint (o->j
 tode_err simt_solve_f32(const SolveReq& r);
 tode_err simt_adjoint_f64(const AdjReq& r);
 tode_err simt_adjoint_f32(const AdjReq& r);
+tode_err simt_t_bounds_f64(const AdjReq& r, const void* yp, double* gt0, double* gt1);
+tode_err simt_t_bounds_f32(const AdjReq& r, const void* yp, double* gt0, double* gt1);
 
 bool simt_supported(int kind, int D);
 

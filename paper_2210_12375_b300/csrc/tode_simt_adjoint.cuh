@@ -644,4 +644,222 @@ template <typename T> tode_err simt_adjoint(const AdjReq& r) {
   }
 }
 
+// ---------------------------------------------------------------- t0, t1
+// Gradients with respect to the integration bounds of the frozen map (every
+// accepted step size but the last and every evaluation point's step held;
+// t0 moves every mesh point before t1, the last step h = t1 - t_{N-1}
+// absorbs the change).  For these autonomous fields the bounds enter only
+// through the dense-output abscissae and the last step size, so
+//   dL/dt1 = hbar = dL/dh of the last step (y_{N-1} held), and
+//   dL/dt0 = -sum_tau <ybar_tau, dy/dt(tau)> - dL/dt1
+// (translating t0 and t1 together shifts every output by -dy/dt).  The last
+// step's hbar: with its stages Y_i, k_i and the reverse sweep's g_i,
+//   hbar = <ybar_N, sum_i b_i k_i>
+//        + sum_tau <ybar_tau, sum_i (b_i(theta) - theta b_i'(theta)) k_i>
+//        + sum_i <g_i, sum_j a_ij k_j>.
+// Backward instances run in tau = -t: hbar is dL/dtau1 there, and
+// dL/dt1 = -hbar.  One lane group per instance; the last step comes from a
+// stride-1 tape with the accepted step sizes.
+template <typename T> struct TBoundsArgs {
+  AdjArgs<T> a;
+  const T* yp;   // [B][K][D] dy/dt at the points (the forward's yp_eval), or NULL
+  double* gt0;   // [B] or NULL
+  double* gt1;   // [B]
+};
+
+template <int G> __device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(Grp<G>::mask(), v, o, G);
+  return v;
+}
+
+template <class AF, typename T, bool YS>
+__global__ void __launch_bounds__(128) k_t_bounds(TBoundsArgs<T> ta) {
+  using C = DP5;
+  constexpr int R = AF::R, G = AF::G;
+  const AdjArgs<T>& a = ta.a;
+  const int D = a.D;
+  const int g = Grp<G>::rank();
+  const long long groups = (long long)gridDim.x * blockDim.x / G;
+  for (long long gi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G; gi < a.B;
+       gi += groups) {
+    const int i = (int)gi;
+    const int N = a.n_acc[i];
+    const bool bad = a.status[i] != ST_SUCCESS || N > a.tape.slots;
+    const bool rev = reversed_at(a.t0, a.t1, i);
+    // -sum_tau <ybar_tau, dy/dt(tau)> over every point (the forward's dy/dt)
+    double tsum = 0.0;
+    if (ta.gt0 && a.gye && ta.yp) {
+      for (int q = 0; q < a.K; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const size_t o = ((size_t)i * a.K + q) * D + g * R + r;
+          tsum += (double)a.gye[o] * (double)ta.yp[o];
+        }
+      tsum = group_sum<G>(tsum);
+    }
+    double hbar = 0.0;
+    if (!bad && N > 0) {
+      AF F;
+      F.load(a.fparam, i, rev ? T(-1) : T(1));
+      AdjSlot<T, R> sl;
+      adj_load_slot<YS, T, R, G>(a, i, D, N - 1, sl);
+      const double t = sl.t;
+      const T h = sl.h;
+      const double hd = (double)h;
+      // the stage inputs (recorded, or recomputed from y and k1) and k_i = f(Y_i)
+      T Y[7][R], k[7][R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) Y[0][r] = sl.y[r];
+      if constexpr (YS) {
+#pragma unroll
+        for (int q6 = 0; q6 < 6; ++q6)
+#pragma unroll
+          for (int r = 0; r < R; ++r) Y[q6 + 1][r] = sl.ys[q6][r];
+      }
+      const T A[7][6] = {{T(0), T(0), T(0), T(0), T(0), T(0)},
+                         {T(C::a21), T(0), T(0), T(0), T(0), T(0)},
+                         {T(C::a31), T(C::a32), T(0), T(0), T(0), T(0)},
+                         {T(C::a41), T(C::a42), T(C::a43), T(0), T(0), T(0)},
+                         {T(C::a51), T(C::a52), T(C::a53), T(C::a54), T(0), T(0)},
+                         {T(C::a61), T(C::a62), T(C::a63), T(C::a64), T(C::a65), T(0)},
+                         {T(C::b1), T(0), T(C::b3), T(C::b4), T(C::b5), T(C::b6)}};
+      const double cs[7] = {0.0, C::c2, C::c3, C::c4, C::c5, 1.0, 1.0};
+#pragma unroll
+      for (int s = 0; s < 7; ++s) {
+        if constexpr (!YS) {
+          if (s > 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              T acc = T(0);
+#pragma unroll
+              for (int l = 0; l < s; ++l) acc = madd(A[s][l], k[l][r], acc);
+              Y[s][r] = madd(h, acc, sl.y[r]);
+            }
+          }
+        }
+        F.eval(t + cs[s] * hd, Y[s], k[s]);
+      }
+      const T bw[7] = {T(C::b1), T(0), T(C::b3), T(C::b4), T(C::b5), T(C::b6), T(0)};
+      T yb[R], kb[7][R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
+      double part = 0.0;  // this lane's share of hbar
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        T sb = T(0);
+#pragma unroll
+        for (int s = 0; s < 7; ++s) sb = madd(bw[s], k[s][r], sb);
+        part += (double)yb[r] * (double)sb;
+      }
+#pragma unroll
+      for (int s = 0; s < 7; ++s)
+#pragma unroll
+        for (int r = 0; r < R; ++r) kb[s][r] = h * bw[s] * yb[r];
+      // the points in the last step, from the last backwards
+      AdjCursor<T, R> c;
+      adj_cursor_start<T, R, G>(c, a, i, D);
+      const long long kt = tkey(t), kn = tkey(flip(a.t1[i], c.m));
+      while (true) {
+        const double tq = c.tq;
+        const long long kq = tkey(tq);
+        if (!(kq > kt)) break;
+        if (a.gye) {
+          T w[7], dv[R];
+          T th;
+          if (kq == kn) {
+            th = T(1);
+#pragma unroll
+            for (int s = 0; s < 7; ++s) w[s] = bw[s];
+          } else {
+            if constexpr (Comp<T>::on) th = T(tq - t) / h;
+            else th = T((tq - t) / hd);
+            dense_weights<T>(th, w);
+          }
+          dense_deriv<T, R>(th, T(1), k[0], k[2], k[3], k[4], k[5], k[6], dv);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            T sw = T(0);
+#pragma unroll
+            for (int s = 0; s < 7; ++s) sw = madd(w[s], k[s][r], sw);
+            part += (double)c.gq[r] * ((double)sw - (double)th * (double)dv[r]);
+          }
+#pragma unroll
+          for (int s = 0; s < 7; ++s)
+#pragma unroll
+            for (int r = 0; r < R; ++r) kb[s][r] = madd(h * w[s], c.gq[r], kb[s][r]);
+        }
+        adj_cursor_next<T, R, G>(c, a, i, D);
+      }
+      // reverse stage sweep: g_i, and <g_i, sum_j a_ij k_j>
+#pragma unroll
+      for (int s = 6; s >= 1; --s) {
+        T gs[R];
+        F.vjp(Y[s], kb[s], gs);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          T sa = T(0);
+#pragma unroll
+          for (int l = 0; l < s; ++l) sa = madd(A[s][l], k[l][r], sa);
+          part += (double)gs[r] * (double)sa;
+        }
+#pragma unroll
+        for (int l = 0; l < s; ++l)
+#pragma unroll
+          for (int r = 0; r < R; ++r) kb[l][r] = madd(h * A[s][l], gs[r], kb[l][r]);
+      }
+      hbar = group_sum<G>(part);
+    }
+    if (g == 0) {
+      const double nan = __longlong_as_double(0x7ff8000000000000LL);
+      const double g1 = bad ? nan : (N > 0 ? (rev ? -hbar : hbar) : 0.0);
+      ta.gt1[i] = g1;
+      if (ta.gt0) ta.gt0[i] = bad ? nan : -tsum - g1;
+    }
+  }
+}
+
+template <class AF, typename T> tode_err launch_t_bounds(const AdjReq& r, const void* yp,
+                                                         double* gt0, double* gt1) {
+  TBoundsArgs<T> ta{};
+  AdjArgs<T>& a = ta.a;
+  a.B = r.B;
+  a.D = r.D;
+  a.K = r.K;
+  a.t0 = r.t0;
+  a.t1 = r.t1;
+  a.te = r.te;
+  a.n_acc = r.n_acc;
+  a.status = r.status;
+  a.tape = make_tape<T>(r.tape, r.B, r.D);
+  a.gye = (const T*)r.gye;
+  a.gyf = (const T*)r.gyf;
+  a.fparam = (const T*)(r.f->kind == TODE_VDP ? r.f->mu : r.f->A);
+  ta.yp = (const T*)yp;
+  ta.gt0 = gt0;
+  ta.gt1 = gt1;
+  const long long threads = (long long)r.B * AF::G;
+  long long grid = (threads + 127) / 128;
+  if (grid > (long long)r.num_sms * 16) grid = (long long)r.num_sms * 16;
+  if (grid == 0) return TODE_OK;
+  if (r.tape->y_stage) k_t_bounds<AF, T, true><<<(int)grid, 128, 0, r.stream>>>(ta);
+  else k_t_bounds<AF, T, false><<<(int)grid, 128, 0, r.stream>>>(ta);
+  TODE_CUDA_TRY(cudaGetLastError());
+  return TODE_OK;
+}
+
+template <typename T> tode_err simt_t_bounds(const AdjReq& r, const void* yp, double* gt0,
+                                            double* gt1) {
+  if (r.f->kind == TODE_VDP) return launch_t_bounds<VdpAdj<T>, T>(r, yp, gt0, gt1);
+  switch (r.D) {  // one column of A per lane, as the direct adjoint takes it
+    case 1: return launch_t_bounds<LinearAdj<T, 1, 1>, T>(r, yp, gt0, gt1);
+    case 2: return launch_t_bounds<LinearAdj<T, 1, 2>, T>(r, yp, gt0, gt1);
+    case 4: return launch_t_bounds<LinearAdj<T, 1, 4>, T>(r, yp, gt0, gt1);
+    case 8: return launch_t_bounds<LinearAdj<T, 1, 8>, T>(r, yp, gt0, gt1);
+    case 16: return launch_t_bounds<LinearAdj<T, 1, 16>, T>(r, yp, gt0, gt1);
+    case 32: return launch_t_bounds<LinearAdj<T, 2, 16>, T>(r, yp, gt0, gt1);
+    default: return TODE_EUNSUPPORTED;
+  }
+}
+
 }  // namespace tode

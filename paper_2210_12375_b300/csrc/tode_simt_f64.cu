@@ -9,4 +9,7 @@ tode_err simt_solve_f64(const SolveReq& r) {
   return r.o->joint ? simt_joint<double>(r) : simt_solve<double>(r);
 }
 tode_err simt_adjoint_f64(const AdjReq& r) { return simt_adjoint<double>(r); }
+tode_err simt_t_bounds_f64(const AdjReq& r, const void* yp, double* gt0, double* gt1) {
+  return simt_t_bounds<double>(r, yp, gt0, gt1);
+}
 }  // namespace tode

@@ -739,7 +739,7 @@ def _interior_t_eval(mt, mn, t0, t1, K, rng):
     return te
 
 
-def _loss_replay(field, y0, t0, t1, mt, mh, mn, te, gye, gyf):
+def _loss_replay_t(field, y0, t0, t1, mt, mh, mn, te, gye, gyf):
     r = oracle.replay(field, y0, t0, t1, mt, mh, mn, te)
     return (gye * r["y_eval"]).sum(axis=(1, 2)) + (gyf * r["y_final"]).sum(axis=1)
 
@@ -793,7 +793,7 @@ def test_t_bounds_gradient_matches_frozen_mesh_differences(case):
                 for k in ("mu", "A", "Q", "lam"):
                     if k in f:
                         f[k] = f[k][sl]
-                vals.append(_loss_replay(f, w["y0"][sl], a0, a1, m_t, m_h, mn[sl], te[sl],
+                vals.append(_loss_replay_t(f, w["y0"][sl], a0, a1, m_t, m_h, mn[sl], te[sl],
                                          gye[sl], gyf[sl])[0])
             (fd1 if which == 1 else fd0)[i] = (vals[0] - vals[1]) / (2 * eps)
     for g, fd in ((adj["gt0"], fd0), (adj["gt1"], fd1)):
