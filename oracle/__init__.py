@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for batched adaptive Dormand-Prince 5(4).
+"""FP64 CPU oracle for batched adaptive explicit Runge-Kutta 5(4) solving:
+Dormand-Prince (dopri5) and Tsitouras (tsit5) pairs.
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 bench's CPU-baseline leg use it.  The product path never imports it.
@@ -13,5 +14,8 @@ from .oracle import (  # noqa: F401
     replay,
     adjoint,
     tableau_doubles,
+    tableau_m,
+    dense_weights_m,
+    METHODS,
     STATUS,
 )

@@ -28,6 +28,9 @@ _lib = None
 
 STATUS = {"SUCCESS": 0, "MAX_STEPS": 1, "DT_UNDERFLOW": 2, "NONFINITE": 3, "INVALID_INPUT": 4}
 _KIND = {"vdp": 1, "linear": 2, "mlp": 3}
+# the Runge-Kutta pair: dopri5 (Dormand & Prince 1980) or tsit5 (Tsitouras
+# 2011), both named in App. A
+METHODS = {"dopri5": 0, "tsit5": 1}
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -62,6 +65,7 @@ class _Opts(C.Structure):
         ("h0", C.c_double),
         ("max_steps", C.c_int),
         ("beta3", C.c_double),
+        ("method", C.c_int),
     ]
 
 
@@ -100,6 +104,8 @@ def _load():
         lib.orc_replay.restype = C.c_int
         lib.orc_adjoint.restype = C.c_int
         lib.orc_adjoint_t.restype = C.c_int
+        lib.orc_adjoint_tm.restype = C.c_int
+        lib.orc_replay_m.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -115,7 +121,8 @@ def _iptr(a):
 def default_opts(**kw) -> dict:
     """Integral controller defaults (App. A uses an I controller everywhere)."""
     o = dict(rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, fac_min=0.2,
-             fac_max=10.0, beta1=0.2, beta2=0.0, beta3=0.0, h0=0.0, max_steps=100000)
+             fac_max=10.0, beta1=0.2, beta2=0.0, beta3=0.0, h0=0.0, max_steps=100000,
+             method="dopri5")
     o.update(kw)
     return o
 
@@ -168,6 +175,7 @@ def _opts_struct(opts: dict, B: int, keep: list):
     for k in ("rtol", "atol", "safety", "fac_min", "fac_max", "beta1", "beta2", "beta3", "h0"):
         setattr(o, k, float(opts[k]))
     o.max_steps = int(opts["max_steps"])
+    o.method = METHODS[opts.get("method", "dopri5")]
     for k in ("rtol_b", "atol_b"):
         v = opts.get(k)
         if v is not None:
@@ -194,6 +202,25 @@ def dense_weights(theta: float) -> np.ndarray:
     lib = _load()
     out = np.zeros(7)
     lib.orc_dense_weights(C.c_double(theta), _ptr(out))
+    return out
+
+
+def tableau_m(method: str):
+    """The pair's coefficients as the oracle uses them: (c [7], A [7,7],
+    b [7], e = b - bhat [7], q [7,4] with b_i(theta) = theta*(q0 + theta*(q1 +
+    theta*(q2 + theta*q3))))."""
+    lib = _load()
+    c, b, e = np.zeros(7), np.zeros(7), np.zeros(7)
+    a, q = np.zeros((7, 7)), np.zeros((7, 4))
+    lib.orc_tableau_m(C.c_int(METHODS[method]), _ptr(c), _ptr(a), _ptr(b), _ptr(e), _ptr(q))
+    return c, a, b, e, q
+
+
+def dense_weights_m(method: str, theta: float) -> np.ndarray:
+    """b_i(theta) of the pair ``method``."""
+    lib = _load()
+    out = np.zeros(7)
+    lib.orc_dense_weights_m(C.c_int(METHODS[method]), C.c_double(theta), _ptr(out))
     return out
 
 
@@ -323,9 +350,10 @@ def solve_joint(field: dict, y0, t0: float, t1: float, t_eval=None, opts: dict |
 
 
 def replay(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None,
-           nthreads: int = 0) -> dict:
-    """Fixed-mesh dopri5 (no controller).  mesh_t/mesh_h [B,cap], mesh_n [B]
-    accepted steps; the last step of instance i ends at t1[i]."""
+           nthreads: int = 0, method: str = "dopri5") -> dict:
+    """Fixed-mesh steps of the pair ``method`` (no controller).  mesh_t/mesh_h
+    [B,cap], mesh_n [B] accepted steps; the last step of instance i ends at
+    t1[i]."""
     lib = _load()
     y0 = np.asarray(y0, dtype=np.float64)
     B = y0.shape[0]
@@ -342,21 +370,23 @@ def replay(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None,
     K = t_eval.shape[1]
     y_eval = np.zeros((B, K, D))
     y_final = np.zeros((B, D))
-    lib.orc_replay(C.byref(fh.f), C.c_int(B), _ptr(y0), _ptr(_f64(t0, (B,))),
-                   _ptr(_f64(t1, (B,))), _ptr(mesh_t), _ptr(mesh_h), _iptr(mesh_n), C.c_int(cap),
-                   _ptr(t_eval), C.c_int(K), _ptr(y_eval), _ptr(y_final), C.c_int(nthreads))
+    lib.orc_replay_m(C.c_int(METHODS[method]), C.byref(fh.f), C.c_int(B), _ptr(y0),
+                     _ptr(_f64(t0, (B,))), _ptr(_f64(t1, (B,))), _ptr(mesh_t), _ptr(mesh_h),
+                     _iptr(mesh_n), C.c_int(cap), _ptr(t_eval), C.c_int(K), _ptr(y_eval),
+                     _ptr(y_final), C.c_int(nthreads))
     return dict(y_eval=y_eval, y_final=y_final)
 
 
 def adjoint(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None, gy_eval=None,
-            gy_final=None, nthreads: int = 0, want_t_bounds: bool = False) -> dict:
+            gy_final=None, nthreads: int = 0, want_t_bounds: bool = False,
+            method: str = "dopri5") -> dict:
     """Discrete adjoint of the fixed-mesh map (App. A, backprop through the
     solver).  Returns gy0 [B,D] and the parameter cotangents: ``gmu`` [B]
     (VdP), ``gA`` [B,D,D] (linear) or ``gW``/``gb`` lists summed over the
     batch (MLP).  With ``want_t_bounds``, also ``gt0`` and ``gt1`` [B]: the
     gradients with respect to t0 and t1 of the same frozen map (every step
     size but the last and every evaluation point's step held, the last step
-    ending at t1)."""
+    ending at t1).  ``method`` is the pair the mesh was made with."""
     lib = _load()
     y0 = np.asarray(y0, dtype=np.float64)
     B = y0.shape[0]
@@ -393,10 +423,11 @@ def adjoint(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None, gy_eva
         out["gb"] = gb
     gt0 = np.zeros(B) if want_t_bounds else None
     gt1 = np.zeros(B) if want_t_bounds else None
-    lib.orc_adjoint_t(C.byref(fh.f), C.c_int(B), _ptr(y0), _ptr(_f64(t0, (B,))),
-                      _ptr(_f64(t1, (B,))), _ptr(mesh_t), _ptr(mesh_h), _iptr(mesh_n),
-                      C.c_int(cap), _ptr(t_eval), C.c_int(K), _ptr(gye), _ptr(gyf), _ptr(gy0),
-                      _ptr(gparam), gW_ptrs, gb_ptrs, _ptr(gt0), _ptr(gt1), C.c_int(nthreads))
+    lib.orc_adjoint_tm(C.c_int(METHODS[method]), C.byref(fh.f), C.c_int(B), _ptr(y0),
+                       _ptr(_f64(t0, (B,))), _ptr(_f64(t1, (B,))), _ptr(mesh_t), _ptr(mesh_h),
+                       _iptr(mesh_n), C.c_int(cap), _ptr(t_eval), C.c_int(K), _ptr(gye),
+                       _ptr(gyf), _ptr(gy0), _ptr(gparam), gW_ptrs, gb_ptrs, _ptr(gt0),
+                       _ptr(gt1), C.c_int(nthreads))
     if want_t_bounds:
         out["gt0"], out["gt1"] = gt0, gt1
     out["gy0"] = gy0

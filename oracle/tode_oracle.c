@@ -1,6 +1,7 @@
 /*
- * tode_oracle.c -- plain, slow FP64 CPU oracle for batched adaptive
- * Dormand-Prince 5(4) with fully independent per-instance solver state.
+ * tode_oracle.c -- plain, slow FP64 CPU oracle for batched adaptive explicit
+ * Runge-Kutta 5(4) solving (Dormand-Prince, and Tsitouras as the second
+ * pair) with fully independent per-instance solver state.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
  * load this file; only the tests, the package's smoke check and the bench's
@@ -15,7 +16,9 @@
  *     values, dense output polynomials evaluated by Horner's rule.
  *   - Sec. 3, paragraph "What slows torchode down?": every instance passes its
  *     own evaluation points at its own pace.
- *   - App. A: dopri5 (Dormand & Prince 1980) with an integral controller.
+ *   - App. A: dopri5 (Dormand & Prince 1980) with an integral controller;
+ *     tsit5 (Tsitouras 2011), which App. A names as also available, as the
+ *     second pair, swapped in by tableau only (orc_opts.method).
  *   - App. C "Impact of PID Control": the controller is a filter over the
  *     last error estimates (Soderlind 2002/2003); the PI subset is used here.
  *   - App. A, FEN benchmark: gradients by backpropagation through the solver
@@ -32,7 +35,9 @@
  * Readings of passages the paper leaves open (it prints no tableau, norm,
  * controller constants, starting-step rule or interpolant):
  *   - tableau: Dormand & Prince 1980, "A family of embedded Runge-Kutta
- *     formulae", the 5(4) pair with FSAL;
+ *     formulae", the 5(4) pair with FSAL; for tsit5, the table and the
+ *     order-4 continuous extension published by Tsitouras (2011), decimals
+ *     as printed there (pinned by the order conditions to their rounding);
  *   - dense output: the 4th-order continuous extension of that pair given by
  *     Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.6, expanded into one
  *     quartic polynomial b_i(theta) per stage and evaluated by Horner's rule;
@@ -100,6 +105,118 @@ static const double DP_Q[NS][4] = {
      -1453857185.0 / 822651844.0},
     {0.0, 40617522.0 / 29380423.0, -110615467.0 / 29380423.0, 69997945.0 / 29380423.0}};
 
+/* ------------------------------------------------------------------------ */
+/* Tsitouras 5(4) pair ("tsit5", named in App. A as available in torchode   */
+/* and often recommended over dopri5): Ch. Tsitouras, Runge-Kutta pairs of   */
+/* order 5(4) satisfying only the first column simplifying assumption,       */
+/* Comput. Math. Appl. 62 (2011), the pair's table and its continuous        */
+/* extension of order 4.  The decimals as published; FSAL (a7 = b, b7 = 0).  */
+/* ------------------------------------------------------------------------ */
+static const double TS_C[NS] = {0.0, 0.161, 0.327, 0.9, 0.9800255409045097, 1.0, 1.0};
+
+static const double TS_A[NS][NS] = {
+    {0, 0, 0, 0, 0, 0, 0},
+    {0.161, 0, 0, 0, 0, 0, 0},
+    {-0.008480655492356989, 0.335480655492357, 0, 0, 0, 0, 0},
+    {2.897153057105493, -6.359448489975075, 4.3622954328695815, 0, 0, 0, 0},
+    {5.325864828439257, -11.748883564062828, 7.4955393428898365, -0.09249506636175525, 0, 0, 0},
+    {5.86145544294642, -12.92096931784711, 8.159367898576159, -0.071584973281401,
+     -0.028269050394068383, 0, 0},
+    {0.09646076681806523, 0.01, 0.4798896504144996, 1.379008574103742, -3.290069515436081,
+     2.324710524099774, 0}};
+
+/* error weights: the difference of the 5th- and 4th-order weight rows */
+static const double TS_E[NS] = {-0.00178001105222577714, -0.0008164344596567469,
+                                0.007880878010261995,    -0.1447110071732629,
+                                0.5823571654525552,      -0.45808210592918697,
+                                0.015151515151515152};
+
+/* Continuous extension, b_i(theta) = k_i theta^m_i * (product of the listed
+ * monic factors): m_1 = 1 with the factors (theta - r) and (theta^2 + p theta
+ * + s); m_i = 2 for i >= 2 with one quadratic or two linear factors.  Each
+ * factor is given by its coefficients, highest power first. */
+typedef struct {
+  double k;
+  int m;
+  int nf;
+  int deg[2];
+  double f[2][3];
+} ts_dense_factored;
+
+static const ts_dense_factored TS_BT[NS] = {
+    {-1.0530884977290216, 1, 2, {1, 2},
+     {{1.0, -1.3299890189751412, 0.0}, {1.0, -1.4364028541716351, 0.7139816917074209}}},
+    {0.1017, 2, 1, {2, 0}, {{1.0, -2.1966568338249754, 1.2949852507374631}, {0, 0, 0}}},
+    {2.490627285651252793, 2, 1, {2, 0}, {{1.0, -2.38535645472061657, 1.57803468208092486}, {0, 0, 0}}},
+    {-16.54810288924490272, 2, 2, {1, 1}, {{1.0, -1.21712927295533244, 0}, {1.0, -0.61620406037800089, 0}}},
+    {47.37952196281928122, 2, 2, {1, 1}, {{1.0, -1.203071208372362603, 0}, {1.0, -0.658047292653547382, 0}}},
+    {-34.87065786149660974, 2, 2, {1, 1}, {{1.0, -1.2, 0}, {1.0, -0.666666666666666667, 0}}},
+    {2.5, 2, 2, {1, 1}, {{1.0, -1.0, 0}, {1.0, -0.6, 0}}}};
+
+/* One method's coefficients as the solver uses them. */
+typedef struct {
+  double c[NS];
+  double a[NS][NS];
+  double b[NS];
+  double e[NS];    /* b_i - bhat_i */
+  double q[NS][4]; /* b_i(theta) = theta*(q0 + theta*(q1 + theta*(q2 + theta*q3))) */
+} rk_tab;
+
+static rk_tab TAB[2];
+static pthread_once_t TAB_ONCE = PTHREAD_ONCE_INIT;
+
+/* Multiplies out k theta^m prod(factors) into monomial coefficients
+ * (plain polynomial products, lowest power first). */
+static void ts_expand(const ts_dense_factored *d, double *out /*[5]: theta^0..theta^4*/) {
+  double p[5] = {0, 0, 0, 0, 0};
+  p[d->m] = d->k; /* k theta^m */
+  int deg = d->m;
+  for (int f = 0; f < d->nf; ++f) {
+    double r[5] = {0, 0, 0, 0, 0};
+    const int df = d->deg[f];
+    for (int u = 0; u <= deg; ++u)
+      for (int v = 0; v <= df; ++v) r[u + v] = r[u + v] + p[u] * d->f[f][df - v];
+    deg += df;
+    for (int u = 0; u < 5; ++u) p[u] = r[u];
+  }
+  for (int u = 0; u < 5; ++u) out[u] = p[u];
+}
+
+static void tab_init(void) {
+  for (int i = 0; i < NS; ++i) {
+    TAB[0].c[i] = DP_C[i];
+    TAB[0].b[i] = DP_B[i];
+    TAB[0].e[i] = DP_B[i] - DP_BHAT[i];
+    for (int j = 0; j < NS; ++j) TAB[0].a[i][j] = DP_A[i][j];
+    for (int j = 0; j < 4; ++j) TAB[0].q[i][j] = DP_Q[i][j];
+    TAB[1].c[i] = TS_C[i];
+    TAB[1].b[i] = TS_A[NS - 1][i];
+    TAB[1].e[i] = TS_E[i];
+    for (int j = 0; j < NS; ++j) TAB[1].a[i][j] = TS_A[i][j];
+    double m[5];
+    ts_expand(&TS_BT[i], m); /* m[0] = 0: every b_i(theta) has a factor theta */
+    for (int j = 0; j < 4; ++j) TAB[1].q[i][j] = m[j + 1];
+  }
+}
+
+/* ORC_DOPRI5 = 0, ORC_TSIT5 = 1 */
+static const rk_tab *tab_of(int method) {
+  pthread_once(&TAB_ONCE, tab_init);
+  return &TAB[method == 1 ? 1 : 0];
+}
+
+/* For the tests: one method's coefficients (e = b - bhat, q as above). */
+void orc_tableau_m(int method, double *c, double *a, double *b, double *e, double *q) {
+  const rk_tab *T = tab_of(method);
+  for (int i = 0; i < NS; ++i) {
+    c[i] = T->c[i];
+    b[i] = T->b[i];
+    e[i] = T->e[i];
+    for (int j = 0; j < NS; ++j) a[i * NS + j] = T->a[i][j];
+    for (int j = 0; j < 4; ++j) q[i * 4 + j] = T->q[i][j];
+  }
+}
+
 /* Lets tests compare these doubles with an exact rational table. */
 void orc_tableau(double *c, double *a, double *b, double *bhat, double *q) {
   for (int i = 0; i < NS; ++i) {
@@ -144,6 +261,7 @@ typedef struct {
   double h0;                     /* > 0: first step given; 0: starting-step heuristic */
   int max_steps;                 /* attempted steps per instance */
   double beta3;                  /* derivative term: exponent of err_prev2 (App. C) */
+  int method;                    /* 0 dopri5, 1 tsit5 (App. A) */
 } orc_opts;
 
 typedef struct {
@@ -371,30 +489,30 @@ static double starting_step(fctx *c, double t0, double t1, double dir, const dou
 }
 
 /* ------------------------------------------------------------------------ */
-/* One Dormand-Prince step from (t, y) with step h; k[0] holds f(t, y)       */
-/* on entry (FSAL).  Fills k[1..6], Y (stage inputs, Y[6] = y1 by SSAL).     */
+/* One step of the pair T from (t, y) with step h; k[0] holds f(t, y) on    */
+/* entry (FSAL).  Fills k[1..6], Y (stage inputs, Y[6] = y1 by SSAL).        */
 /* ------------------------------------------------------------------------ */
-static void dp_stages(fctx *c, double t, double h, const double *y, int D, double *k /*[7][D]*/,
-                      double *Y /*[7][D]*/) {
+static void dp_stages(const rk_tab *T, fctx *c, double t, double h, const double *y, int D,
+                      double *k /*[7][D]*/, double *Y /*[7][D]*/) {
   for (int j = 0; j < D; ++j) Y[j] = y[j];
   for (int i = 1; i < NS; ++i) {
     double *Yi = Y + i * D;
     for (int j = 0; j < D; ++j) {
       double s = 0.0;
-      for (int l = 0; l < i; ++l) s = s + DP_A[i][l] * k[l * D + j];
+      for (int l = 0; l < i; ++l) s = s + T->a[i][l] * k[l * D + j];
       Yi[j] = y[j] + h * s;
     }
-    feval(c, t + DP_C[i] * h, Yi, k + i * D);
+    feval(c, t + T->c[i] * h, Yi, k + i * D);
   }
 }
 
 /* Embedded error e = h * sum_i (b_i - bhat_i) k_i, then its weighted RMS norm
  * against sc = atol + rtol * max(|y|, |y1|). */
-static double dp_error(double h, const double *y, const double *y1, const double *k, int D,
-                       double rtol, double atol, double *e, double *sc) {
+static double dp_error(const rk_tab *T, double h, const double *y, const double *y1,
+                       const double *k, int D, double rtol, double atol, double *e, double *sc) {
   for (int j = 0; j < D; ++j) {
     double s = 0.0;
-    for (int i = 0; i < NS; ++i) s = s + (DP_B[i] - DP_BHAT[i]) * k[i * D + j];
+    for (int i = 0; i < NS; ++i) s = s + T->e[i] * k[i * D + j];
     e[j] = h * s;
     sc[j] = atol + rtol * dmax(fabs(y[j]), fabs(y1[j]));
   }
@@ -403,11 +521,11 @@ static double dp_error(double h, const double *y, const double *y1, const double
 
 /* Dense output at theta in [0,1): y + h * sum_i b_i(theta) k_i, each b_i by
  * Horner's rule (Sec. 3, "What makes torchode fast?"). */
-static void dp_dense(double theta, double h, const double *y, const double *k, int D,
-                     double *out) {
+static void dp_dense(const rk_tab *T, double theta, double h, const double *y, const double *k,
+                     int D, double *out) {
   double bt[NS];
   for (int i = 0; i < NS; ++i) {
-    const double *q = DP_Q[i];
+    const double *q = T->q[i];
     bt[i] = theta * (q[0] + theta * (q[1] + theta * (q[2] + theta * q[3])));
   }
   for (int j = 0; j < D; ++j) {
@@ -421,10 +539,10 @@ static void dp_dense(double theta, double h, const double *y, const double *k, i
 /* d/dt of the dense output y + hs sum_i b_i(theta) k_i with theta = (t -
  * t_n) / hs: sum_i b_i'(theta) k_i, b_i'(theta) = q0 + 2 q1 theta + 3 q2
  * theta^2 + 4 q3 theta^3 from the same quartics (the step's sign cancels). */
-static void dp_dense_deriv(double theta, const double *k, int D, double *out) {
+static void dp_dense_deriv(const rk_tab *T, double theta, const double *k, int D, double *out) {
   double bd[NS];
   for (int i = 0; i < NS; ++i) {
-    const double *q = DP_Q[i];
+    const double *q = T->q[i];
     bd[i] = q[0] + theta * (2.0 * q[1] + theta * (3.0 * q[2] + theta * (4.0 * q[3])));
   }
   for (int j = 0; j < D; ++j) {
@@ -434,12 +552,16 @@ static void dp_dense_deriv(double theta, const double *k, int D, double *out) {
   }
 }
 
-void orc_dense_weights(double theta, double *bt) {
+static void dense_weights(const rk_tab *T, double theta, double *bt) {
   for (int i = 0; i < NS; ++i) {
-    const double *q = DP_Q[i];
+    const double *q = T->q[i];
     bt[i] = theta * (q[0] + theta * (q[1] + theta * (q[2] + theta * q[3])));
   }
 }
+void orc_dense_weights_m(int method, double theta, double *bt) {
+  dense_weights(tab_of(method), theta, bt);
+}
+void orc_dense_weights(double theta, double *bt) { dense_weights(tab_of(0), theta, bt); }
 
 /* ------------------------------------------------------------------------ */
 /* Input checks (Sec. 3: per-instance bounds and evaluation points).         */
@@ -462,6 +584,7 @@ static int instance_inputs_valid(double t0, double t1, const double *te, int K) 
 typedef struct {
   const orc_field *F;
   const orc_opts *O;
+  const rk_tab *T; /* the pair (dopri5 or tsit5) */
   int B, K;
   const double *y0, *t0, *t1, *t_eval;
   double *y_eval, *y_final;
@@ -548,9 +671,9 @@ static void solve_one(const job *J, int i, double *work, double *act) {
       last = 1;
     }
     const double hs = dir * h;
-    dp_stages(&c, t, hs, y, D, k, Y);
+    dp_stages(J->T, &c, t, hs, y, D, k, Y);
     for (int j = 0; j < D; ++j) y1[j] = Y[6 * D + j]; /* SSAL: y1 is the last stage input */
-    double err = dp_error(hs, y, y1, k, D, rtol, atol, e, sc);
+    double err = dp_error(J->T, hs, y, y1, k, D, rtol, atol, e, sc);
     int finite = isfinite(err);
     for (int j = 0; j < D; ++j) finite = finite && isfinite(y1[j]);
     int accept = finite && err <= 1.0;
@@ -573,10 +696,10 @@ static void solve_one(const job *J, int i, double *work, double *act) {
         if (te[cur] == t_next) {
           for (int j = 0; j < D; ++j) o[j] = y1[j];
         } else {
-          dp_dense((te[cur] - t) / hs, hs, y, k, D, o);
+          dp_dense(J->T, (te[cur] - t) / hs, hs, y, k, D, o);
         }
         if (yp) /* the interpolant's derivative; theta = 1 at the step's end */
-          dp_dense_deriv(te[cur] == t_next ? 1.0 : (te[cur] - t) / hs, k, D,
+          dp_dense_deriv(J->T, te[cur] == t_next ? 1.0 : (te[cur] - t) / hs, k, D,
                          yp + (size_t)cur * D);
         cur++;
       }
@@ -659,14 +782,14 @@ static void replay_one(const job *J, int i, double *work, double *act, double *y
     const double h = J->mesh_h[(size_t)i * J->mesh_cap + n];
     const double t_next = mesh_end(J, i, n);
     feval(&c, t, y, k);
-    dp_stages(&c, t, h, y, D, k, Y);
+    dp_stages(J->T, &c, t, h, y, D, k, Y);
     const double *y1 = Y + 6 * D;
     while (cur < K && dir * te[cur] <= dir * t_next) {
       double *o = ye + (size_t)cur * D;
       if (te[cur] == t_next) {
         for (int j = 0; j < D; ++j) o[j] = y1[j];
       } else {
-        dp_dense((te[cur] - t) / h, h, y, k, D, o);
+        dp_dense(J->T, (te[cur] - t) / h, h, y, k, D, o);
       }
       cur++;
     }
@@ -802,34 +925,35 @@ static void adjoint_one(const job *J, int i, double *work, double *act, double *
     const double t_next = mesh_end(J, i, n);
     const double *y = ys + (size_t)n * D;
     feval(&c, t, y, k);
-    dp_stages(&c, t, h, y, D, k, Y);
+    dp_stages(J->T, &c, t, h, y, D, k, Y);
+    const rk_tab *T = J->T;
     double hbar = 0.0;
     if (want_t) { /* <ybar_{n+1}, sum b_i k_i> (dp_stages left k_7 = f(t_{n+1}, y_{n+1})) */
       for (int j = 0; j < D; ++j) {
         double s = 0.0;
-        for (int q = 0; q < NS; ++q) s = s + DP_B[q] * k[q * D + j];
+        for (int q = 0; q < NS; ++q) s = s + T->b[q] * k[q * D + j];
         hbar = hbar + yb[j] * s;
       }
     }
     /* cotangents of the stage values */
     for (int s = 0; s < NS; ++s)
-      for (int j = 0; j < D; ++j) kb[s * D + j] = h * DP_B[s] * yb[j];
+      for (int j = 0; j < D; ++j) kb[s * D + j] = h * T->b[s] * yb[j];
     while (cur >= 0 && dir * te[cur] > dir * t) {
       if (gye) {
         const double *gq = gye + (size_t)cur * D;
         double bt[NS];
         if (te[cur] == t_next) {
           /* this output is y_{n+1} itself: y_{n+1} = y_n + h sum b_i k_i */
-          for (int s = 0; s < NS; ++s) bt[s] = DP_B[s];
+          for (int s = 0; s < NS; ++s) bt[s] = T->b[s];
         } else {
-          orc_dense_weights((te[cur] - t) / h, bt);
+          dense_weights(T, (te[cur] - t) / h, bt);
         }
         for (int s = 0; s < NS; ++s)
           for (int j = 0; j < D; ++j) kb[s * D + j] = kb[s * D + j] + h * bt[s] * gq[j];
         for (int j = 0; j < D; ++j) yb[j] = yb[j] + gq[j];
         if (want_t) {
           const double th = te[cur] == t_next ? 1.0 : (te[cur] - t) / h;
-          dp_dense_deriv(th, k, D, tv); /* sum_i b_i'(theta) k_i */
+          dp_dense_deriv(T, th, k, D, tv); /* sum_i b_i'(theta) k_i */
           for (int j = 0; j < D; ++j) {
             double s = 0.0;
             for (int q = 0; q < NS; ++q) s = s + bt[q] * k[q * D + j];
@@ -843,19 +967,19 @@ static void adjoint_one(const job *J, int i, double *work, double *act, double *
     for (int s = NS - 1; s >= 0; --s) {
       double gts = 0.0;
       for (int j = 0; j < D; ++j) g[j] = 0.0;
-      vjp(J, i, t + DP_C[s] * h, Y + s * D, kb + s * D, g, gp, gW, gb, act, dscr,
+      vjp(J, i, t + T->c[s] * h, Y + s * D, kb + s * D, g, gp, gW, gb, act, dscr,
           want_t ? &gts : NULL);
       if (want_t) {
         for (int j = 0; j < D; ++j) {
           double s2 = 0.0;
-          for (int l = 0; l < s; ++l) s2 = s2 + DP_A[s][l] * k[l * D + j];
+          for (int l = 0; l < s; ++l) s2 = s2 + T->a[s][l] * k[l * D + j];
           hbar = hbar + g[j] * s2;
         }
-        hbar = hbar + DP_C[s] * gts;
+        hbar = hbar + T->c[s] * gts;
         tbar = tbar + gts;
       }
       for (int l = 0; l < s; ++l)
-        for (int j = 0; j < D; ++j) kb[l * D + j] = kb[l * D + j] + h * DP_A[s][l] * g[j];
+        for (int j = 0; j < D; ++j) kb[l * D + j] = kb[l * D + j] + h * T->a[s][l] * g[j];
       for (int j = 0; j < D; ++j) yb[j] = yb[j] + g[j];
     }
     if (n == N - 1) hbar_last = hbar;
@@ -986,6 +1110,7 @@ int orc_solve_yp(const orc_field *F, const orc_opts *O, int B, const double *y0,
   memset(&J, 0, sizeof(J));
   J.F = F;
   J.O = O;
+  J.T = tab_of(O->method);
   J.B = B;
   J.K = K;
   J.y0 = y0;
@@ -1003,12 +1128,15 @@ int orc_solve_yp(const orc_field *F, const orc_opts *O, int B, const double *y0,
   return run(&J, MODE_SOLVE, nthreads);
 }
 
-int orc_replay(const orc_field *F, int B, const double *y0, const double *t0, const double *t1,
-               const double *mesh_t, const double *mesh_h, const int32_t *mesh_n, int mesh_cap,
-               const double *t_eval, int K, double *y_eval, double *y_final, int nthreads) {
+/* The fixed-mesh replay with the pair `method` (0 dopri5, 1 tsit5). */
+int orc_replay_m(int method, const orc_field *F, int B, const double *y0, const double *t0,
+                 const double *t1, const double *mesh_t, const double *mesh_h,
+                 const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
+                 double *y_eval, double *y_final, int nthreads) {
   job J;
   memset(&J, 0, sizeof(J));
   J.F = F;
+  J.T = tab_of(method);
   J.B = B;
   J.K = K;
   J.y0 = y0;
@@ -1023,14 +1151,29 @@ int orc_replay(const orc_field *F, int B, const double *y0, const double *t0, co
   J.mesh_cap = mesh_cap;
   return run(&J, MODE_REPLAY, nthreads);
 }
+int orc_replay(const orc_field *F, int B, const double *y0, const double *t0, const double *t1,
+               const double *mesh_t, const double *mesh_h, const int32_t *mesh_n, int mesh_cap,
+               const double *t_eval, int K, double *y_eval, double *y_final, int nthreads) {
+  return orc_replay_m(0, F, B, y0, t0, t1, mesh_t, mesh_h, mesh_n, mesh_cap, t_eval, K, y_eval,
+                      y_final, nthreads);
+}
 
 /* gparam: VdP [B] (d/dmu), linear [B][D][D] (d/dA); MLP: gW[l], gb[l] summed
  * over the batch (per-thread partials added in thread order). */
+int orc_adjoint_tm(int method, const orc_field *F, int B, const double *y0, const double *t0,
+                   const double *t1, const double *mesh_t, const double *mesh_h,
+                   const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
+                   const double *gy_eval, const double *gy_final, double *gy0, double *gparam,
+                   double *const *gW, double *const *gb, double *gt0, double *gt1,
+                   int nthreads);
 int orc_adjoint_t(const orc_field *F, int B, const double *y0, const double *t0,
                   const double *t1, const double *mesh_t, const double *mesh_h,
                   const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
                   const double *gy_eval, const double *gy_final, double *gy0, double *gparam,
-                  double *const *gW, double *const *gb, double *gt0, double *gt1, int nthreads);
+                  double *const *gW, double *const *gb, double *gt0, double *gt1, int nthreads) {
+  return orc_adjoint_tm(0, F, B, y0, t0, t1, mesh_t, mesh_h, mesh_n, mesh_cap, t_eval, K,
+                        gy_eval, gy_final, gy0, gparam, gW, gb, gt0, gt1, nthreads);
+}
 int orc_adjoint(const orc_field *F, int B, const double *y0, const double *t0, const double *t1,
                 const double *mesh_t, const double *mesh_h, const int32_t *mesh_n, int mesh_cap,
                 const double *t_eval, int K, const double *gy_eval, const double *gy_final,
@@ -1040,18 +1183,20 @@ int orc_adjoint(const orc_field *F, int B, const double *y0, const double *t0, c
                        gy_final, gy0, gparam, gW, gb, NULL, NULL, nthreads);
 }
 /* orc_adjoint, plus dL/dt0 and dL/dt1 of the frozen map when gt0 / gt1 are
- * not NULL ([B]; see adjoint_one). */
-int orc_adjoint_t(const orc_field *F, int B, const double *y0, const double *t0,
-                  const double *t1, const double *mesh_t, const double *mesh_h,
-                  const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
-                  const double *gy_eval, const double *gy_final, double *gy0, double *gparam,
-                  double *const *gW, double *const *gb, double *gt0, double *gt1, int nthreads) {
+ * not NULL ([B]; see adjoint_one), for the pair `method` (0 dopri5, 1 tsit5). */
+int orc_adjoint_tm(int method, const orc_field *F, int B, const double *y0, const double *t0,
+                   const double *t1, const double *mesh_t, const double *mesh_h,
+                   const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
+                   const double *gy_eval, const double *gy_final, double *gy0, double *gparam,
+                   double *const *gW, double *const *gb, double *gt0, double *gt1,
+                   int nthreads) {
   /* the adjoint of a stacked problem is the per-instance adjoint on the
    * shared mesh (every block's Jacobian is its own); call it that way */
   if (F->kind == ORC_STACKED) return -1;
   job J;
   memset(&J, 0, sizeof(J));
   J.F = F;
+  J.T = tab_of(method);
   J.B = B;
   J.K = K;
   J.y0 = y0;

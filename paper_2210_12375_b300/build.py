@@ -1,7 +1,7 @@
 """Builds ``libtode.so`` in-tree with nvcc for sm_103a (B300).
 
-Every translation unit is compiled separately (the FP64 one with
-``-fmad=false``) and linked into one shared library with the CUDA runtime
+Every translation unit is compiled separately, side by side (the solver
+units with ``-fmad=false``), and linked into one shared library with the CUDA runtime
 linked statically; no other library is linked.  Rebuilds only what changed.
 """
 from __future__ import annotations
@@ -42,7 +42,7 @@ def _deps():
 def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     hdr_time = _deps()
-    objs = []
+    objs, cmds = [], []
     changed = force or not os.path.exists(LIB)
     for src, extra in UNITS.items():
         s = os.path.join(CSRC, src)
@@ -54,10 +54,19 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
         cmd = [NVCC, *ARCH, *COMMON, *extra, "-c", s, "-o", o]
         if ptxas_verbose:
             cmd += ["-Xptxas", "-v"]
+        cmds.append(cmd)
+    # the units are independent: compile them side by side
+    jobs = max(1, min(len(cmds), os.cpu_count() or 1))
+    running = []
+    for cmd in cmds:
         if verbose:
             print(" ".join(cmd), flush=True)
-        subprocess.run(cmd, check=True)
-        changed = True
+        running.append(subprocess.Popen(cmd))
+        while len(running) >= jobs:
+            _reap(running)
+    while running:
+        _reap(running)
+    changed = changed or bool(cmds)
     if changed or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs,]
@@ -66,6 +75,16 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB
+
+
+def _reap(running: list) -> None:
+    """Waits for the oldest compile of the list; a failed one raises (after
+    the others have finished, so that no object is left half written)."""
+    p = running.pop(0)
+    if p.wait() != 0:
+        for q in running:
+            q.wait()
+        raise subprocess.CalledProcessError(p.returncode, p.args)
 
 
 if __name__ == "__main__":

@@ -131,3 +131,32 @@ def linear_step_polys():
     E = z * sum(sp.Rational((b[i] - bh[i]).numerator, (b[i] - bh[i]).denominator) * stage[i]
                 for i in range(n))
     return z, sp.expand(R), sp.expand(E)
+
+
+# ---- tsit5 (decimals as published, read as exact rationals) ----
+def tsit5_tableau():
+    """(c, A, b, e) of the Tsitouras 5(4) pair as exact rationals of the
+    published decimals; b is the last stage row (FSAL), e = b - bhat."""
+    c = [F(0)] * 7
+    A = [[F(0)] * 7 for _ in range(7)]
+    e = [F(0)] * 7
+    for r in _read("tsit5_tableau.txt"):
+        if r[0] == "c":
+            c[int(r[1]) - 1] = F(r[2])
+        elif r[0] == "a":
+            A[int(r[1]) - 1][int(r[2]) - 1] = F(r[3])
+        elif r[0] == "e":
+            e[int(r[1]) - 1] = F(r[2])
+    return c, A, list(A[6]), e
+
+
+def tsit5_dense_polys():
+    """b_i(theta) of tsit5's continuous extension as sympy polynomials with
+    the published decimals read as exact rationals."""
+    th = sp.Symbol("theta")
+    out = [None] * 7
+    for r in _read("tsit5_tableau.txt"):
+        if r[0] == "bt":
+            expr = sp.sympify(r[2], locals={"theta": th}, rational=True)
+            out[int(r[1]) - 1] = sp.Poly(sp.expand(expr), th)
+    return th, out
