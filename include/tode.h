@@ -142,7 +142,17 @@ typedef struct {
    * 0 = the PI / I controller.  A strided tape needs err_prev2 when it is
    * not 0. */
   double beta3;
+  /* the Runge-Kutta pair: TODE_DOPRI5 (0, Dormand & Prince 1980, the
+   * paper's method throughout) or TODE_TSIT5 (1, Tsitouras 2011, which App.
+   * A names as also available); both are 5(4) pairs with FSAL and an order-4
+   * dense output, swapped by tableau only.  tsit5 covers the Van der Pol
+   * and linear fields, independent solving, tode_solve, tode_adjoint and
+   * tode_t_bounds_grad; the MLP field and joint solving return
+   * TODE_EUNSUPPORTED with it. */
+  int method;
 } tode_options;
+
+enum { TODE_DOPRI5 = 0, TODE_TSIT5 = 1 };
 
 /* Checkpoint tape written by tode_solve for tode_adjoint.  Slot j of
  * instance i holds the solver state at the start of accepted step j*stride
@@ -201,7 +211,8 @@ typedef struct {
 
 /* Fills *o with the defaults: rtol = atol = 1e-6, safety 0.9, fac_min 0.2,
  * fac_max 10, beta1 0.2, beta2 = beta3 = 0 (integral controller), h0 = 0 (heuristic),
- * max_steps 100000, TODE_F32, TODE_FUSED, tuning fields 0, order 0, joint 0. */
+ * max_steps 100000, TODE_F32, TODE_FUSED, tuning fields 0, order 0, joint 0,
+ * TODE_DOPRI5. */
 void tode_default_options(tode_options* o);
 
 /* Bytes of device workspace tode_solve needs for this problem (the base

@@ -15,6 +15,7 @@ TODE_OK, TODE_EINVAL, TODE_EWORKSPACE, TODE_ECUDA, TODE_EUNSUPPORTED, TODE_ETIME
 TODE_VDP, TODE_LINEAR, TODE_MLP = 1, 2, 3
 TODE_F64, TODE_F32, TODE_BF16W, TODE_BF16W_SPLIT = 0, 1, 2, 3
 TODE_PLAIN, TODE_FUSED = 0, 1
+TODE_DOPRI5, TODE_TSIT5 = 0, 1
 (TODE_PEAK_FMA32, TODE_PEAK_FFMA2, TODE_PEAK_FMA64, TODE_PEAK_EX2, TODE_PEAK_TANH,
  TODE_PEAK_EMPTY) = range(6)
 STATUS = {"SUCCESS": 0, "MAX_STEPS": 1, "DT_UNDERFLOW": 2, "NONFINITE": 3, "INVALID_INPUT": 4}
@@ -65,6 +66,7 @@ class Options(C.Structure):
         ("order", C.c_int),
         ("joint", C.c_int),
         ("beta3", C.c_double),
+        ("method", C.c_int),
     ]
 
 

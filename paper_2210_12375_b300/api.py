@@ -121,7 +121,9 @@ def _prec_of(field, y0: torch.Tensor) -> int:
 def make_options(*, rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, fac_min=0.2,
                  fac_max=10.0, beta1=0.2, beta2=0.0, beta3=0.0, h0=0.0, max_steps=100000,
                  prec=_abi.TODE_F32, form="fused", group=0, block=0, ctas_per_sm=0,
-                 poll_every=0, order=0, joint=False) -> _abi.Options:
+                 poll_every=0, order=0, joint=False, method="dopri5") -> _abi.Options:
+    """The C options struct.  ``method``: the Runge-Kutta pair, "dopri5"
+    (Dormand & Prince) or "tsit5" (Tsitouras; App. A names both)."""
     o = _abi.Options()
     o.rtol, o.atol = float(rtol), float(atol)
     o.rtol_b = rtol_b.data_ptr() if rtol_b is not None else None
@@ -137,6 +139,8 @@ def make_options(*, rtol=1e-6, atol=1e-6, rtol_b=None, atol_b=None, safety=0.9, 
     o.order = int(order)
     o.joint = int(bool(joint))
     o.beta3 = float(beta3)
+    o.method = {"dopri5": _abi.TODE_DOPRI5, "tsit5": _abi.TODE_TSIT5}[method] \
+        if isinstance(method, str) else int(method)
     return o
 
 

@@ -26,6 +26,8 @@ UNITS = {
     "tode_api.cu": [],
     "tode_simt_f64.cu": ["-fmad=false"],
     "tode_simt_f32.cu": ["-fmad=false"],
+    "tode_simt_ts5_f64.cu": ["-fmad=false"],
+    "tode_simt_ts5_f32.cu": ["-fmad=false"],
     "tode_static.cu": [],
     "tode_tc_gemm.cu": [],
     "tode_mlp.cu": ["-fmad=false"],

@@ -31,6 +31,7 @@ static bool opts_ok(const tode_options* o) {
   if (o->block < 0 || o->group < 0 || o->ctas_per_sm < 0 || o->poll_every < 0) return false;
   if (o->order != 0 && o->order != 1) return false;
   if (o->joint != 0 && o->joint != 1) return false;
+  if (o->method != TODE_DOPRI5 && o->method != TODE_TSIT5) return false;
   return true;
 }
 
@@ -48,6 +49,7 @@ static tode_err field_ok(const tode_field_desc* f, const tode_options* o) {
   }
   if (f->kind == TODE_MLP) {
     if (o->prec != TODE_BF16W && o->prec != TODE_BF16W_SPLIT) return TODE_EUNSUPPORTED;
+    if (o->method != TODE_DOPRI5) return TODE_EUNSUPPORTED;  // the MLP solver is dopri5
     if (!f->widths || !f->W || !f->b) return TODE_EINVAL;
     if (!mlp_supported(f)) return TODE_EUNSUPPORTED;
     if (f->B > 0)
@@ -140,6 +142,7 @@ void tode_default_options(tode_options* o) {
 // scalar tolerances (one problem has one norm).
 static tode_err joint_ok(const tode_field_desc* f, const tode_options* o) {
   if (!o->joint) return TODE_OK;
+  if (o->method != TODE_DOPRI5) return TODE_EUNSUPPORTED;  // the joint solve is dopri5
   if (f->kind == TODE_MLP) return TODE_EUNSUPPORTED;
   if (o->rtol_b || o->atol_b) return TODE_EINVAL;
   return TODE_OK;

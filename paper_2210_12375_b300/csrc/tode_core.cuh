@@ -60,6 +60,118 @@ struct DP5 {
                           q63 = -1453857185.0 / 822651844.0;
   static constexpr double q71 = 40617522.0 / 29380423.0, q72 = -110615467.0 / 29380423.0,
                           q73 = 69997945.0 / 29380423.0;
+
+  // The interface both pairs share (1-based indices as in the tableau; zero
+  // entries fold away in unrolled loops): c_i, a_ij (stage rows 2..7, row 7
+  // = b by FSAL), e_i = b_i - bhat_i, and the dense-output coefficients q_im
+  // with b_i(theta) = theta*(q_i0 + theta*(q_i1 + theta*(q_i2 + theta*q_i3))).
+  __host__ __device__ static constexpr double c(int i) {
+    return i == 2 ? c2 : i == 3 ? c3 : i == 4 ? c4 : i == 5 ? c5 : i >= 6 ? 1.0 : 0.0;
+  }
+  __host__ __device__ static constexpr double a(int i, int j) {
+    switch (i * 8 + j) {
+      case 17: return a21;
+      case 25: return a31; case 26: return a32;
+      case 33: return a41; case 34: return a42; case 35: return a43;
+      case 41: return a51; case 42: return a52; case 43: return a53; case 44: return a54;
+      case 49: return a61; case 50: return a62; case 51: return a63; case 52: return a64;
+      case 53: return a65;
+      case 57: return b1; case 59: return b3; case 60: return b4; case 61: return b5;
+      case 62: return b6;
+      default: return 0.0;
+    }
+  }
+  __host__ __device__ static constexpr double b(int i) { return a(7, i); }
+  __host__ __device__ static constexpr double e(int i) {
+    return i == 1 ? e1 : i == 3 ? e3 : i == 4 ? e4 : i == 5 ? e5 : i == 6 ? e6 : i == 7 ? e7
+                                                                                        : 0.0;
+  }
+  __host__ __device__ static constexpr double q(int i, int m) {
+    switch (i * 4 + m) {
+      case 4: return q10; case 5: return q11; case 6: return q12; case 7: return q13;
+      case 13: return q31; case 14: return q32; case 15: return q33;
+      case 17: return q41; case 18: return q42; case 19: return q43;
+      case 21: return q51; case 22: return q52; case 23: return q53;
+      case 25: return q61; case 26: return q62; case 27: return q63;
+      case 29: return q71; case 30: return q72; case 31: return q73;
+      default: return 0.0;
+    }
+  }
+};
+
+// Tsitouras 5(4) pair (tsit5; the torchode paper names it in App. A as
+// available beside dopri5): Ch. Tsitouras, Comput. Math. Appl. 62 (2011),
+// the table and its continuous extension of order 4, decimals as published.
+// FSAL: the 7th stage row is the 5th-order weight row and c7 = 1, b7 = 0.
+struct TS5 {
+  __host__ __device__ static constexpr double c(int i) {
+    return i == 2 ? 0.161 : i == 3 ? 0.327 : i == 4 ? 0.9 : i == 5 ? 0.9800255409045097
+                                                                   : i >= 6 ? 1.0 : 0.0;
+  }
+  __host__ __device__ static constexpr double a(int i, int j) {
+    switch (i * 8 + j) {
+      case 17: return 0.161;
+      case 25: return -0.008480655492356989; case 26: return 0.335480655492357;
+      case 33: return 2.897153057105493; case 34: return -6.359448489975075;
+      case 35: return 4.3622954328695815;
+      case 41: return 5.325864828439257; case 42: return -11.748883564062828;
+      case 43: return 7.4955393428898365; case 44: return -0.09249506636175525;
+      case 49: return 5.86145544294642; case 50: return -12.92096931784711;
+      case 51: return 8.159367898576159; case 52: return -0.071584973281401;
+      case 53: return -0.028269050394068383;
+      case 57: return 0.09646076681806523; case 58: return 0.01;
+      case 59: return 0.4798896504144996; case 60: return 1.379008574103742;
+      case 61: return -3.290069515436081; case 62: return 2.324710524099774;
+      default: return 0.0;
+    }
+  }
+  __host__ __device__ static constexpr double b(int i) { return a(7, i); }
+  __host__ __device__ static constexpr double e(int i) {
+    switch (i) {
+      case 1: return -0.00178001105222577714;
+      case 2: return -0.0008164344596567469;
+      case 3: return 0.007880878010261995;
+      case 4: return -0.1447110071732629;
+      case 5: return 0.5823571654525552;
+      case 6: return -0.45808210592918697;
+      case 7: return 0.015151515151515152;
+      default: return 0.0;
+    }
+  }
+  // The continuous extension as published, in factored form:
+  //   b_1 = k1 theta (theta - r1) (theta^2 + p1 theta + s1),
+  //   b_2, b_3 = k theta^2 (theta^2 + p theta + s),
+  //   b_4..b_7 = k theta^2 (theta - u) (theta - v),
+  // multiplied out here into the Horner coefficients q_i0..q_i3.
+  static constexpr double k1 = -1.0530884977290216, r1 = 1.3299890189751412,
+                          p1 = -1.4364028541716351, s1 = 0.7139816917074209;
+  __host__ __device__ static constexpr double kq(int i) {
+    return i == 2 ? 0.1017 : i == 3 ? 2.490627285651252793 : i == 4 ? -16.54810288924490272
+         : i == 5 ? 47.37952196281928122 : i == 6 ? -34.87065786149660974 : 2.5;
+  }
+  // b_2, b_3: theta^2 + p theta + s;  b_4..b_7: roots u, v
+  __host__ __device__ static constexpr double pq(int i) {
+    return i == 2 ? -2.1966568338249754 : i == 3 ? -2.38535645472061657
+         : i == 4 ? -(1.21712927295533244 + 0.61620406037800089)
+         : i == 5 ? -(1.203071208372362603 + 0.658047292653547382)
+         : i == 6 ? -(1.2 + 0.666666666666666667) : -(1.0 + 0.6);
+  }
+  __host__ __device__ static constexpr double sq(int i) {
+    return i == 2 ? 1.2949852507374631 : i == 3 ? 1.57803468208092486
+         : i == 4 ? 1.21712927295533244 * 0.61620406037800089
+         : i == 5 ? 1.203071208372362603 * 0.658047292653547382
+         : i == 6 ? 1.2 * 0.666666666666666667 : 1.0 * 0.6;
+  }
+  __host__ __device__ static constexpr double q(int i, int m) {
+    if (i == 1) {
+      // k1 theta (theta^3 + (p1 - r1) theta^2 + (s1 - r1 p1) theta - r1 s1)
+      return m == 0 ? -(k1 * r1 * s1) : m == 1 ? k1 * (s1 - r1 * p1) : m == 2 ? k1 * (p1 - r1)
+                                                                              : k1;
+    }
+    if (i < 2 || i > 7) return 0.0;
+    // k theta^2 (theta^2 + p theta + s) = theta (0 + theta (k s + theta (k p + theta k)))
+    return m == 0 ? 0.0 : m == 1 ? kq(i) * sq(i) : m == 2 ? kq(i) * pq(i) : kq(i);
+  }
 };
 
 enum : int { ST_SUCCESS = 0, ST_MAX_STEPS = 1, ST_DT_UNDERFLOW = 2, ST_NONFINITE = 3,
@@ -309,36 +421,39 @@ __device__ __forceinline__ void advance_cursor(Inst<T, R>& s, const InstOut<T>& 
   s.tq2 = te_at(out, s.cursor + 1, rev_mask(s.flags));
 }
 
-// Dense-output weights b_i(theta), each by Horner's rule (w[1] = 0).
-template <typename T> __device__ __forceinline__ void dense_weights(T th, T (&w)[7]) {
-  using C = DP5;
-  w[0] = th * madd(th, madd(th, madd(th, T(C::q13), T(C::q12)), T(C::q11)), T(C::q10));
-  w[1] = T(0);
-  w[2] = th * madd(th, madd(th, madd(th, T(C::q33), T(C::q32)), T(C::q31)), T(0));
-  w[3] = th * madd(th, madd(th, madd(th, T(C::q43), T(C::q42)), T(C::q41)), T(0));
-  w[4] = th * madd(th, madd(th, madd(th, T(C::q53), T(C::q52)), T(C::q51)), T(0));
-  w[5] = th * madd(th, madd(th, madd(th, T(C::q63), T(C::q62)), T(C::q61)), T(0));
-  w[6] = th * madd(th, madd(th, madd(th, T(C::q73), T(C::q72)), T(C::q71)), T(0));
+// True when b_i(theta) vanishes identically (dopri5's stage 2).
+template <class Tab> __host__ __device__ constexpr bool dense_zero(int i) {
+  return Tab::q(i, 0) == 0.0 && Tab::q(i, 1) == 0.0 && Tab::q(i, 2) == 0.0 &&
+         Tab::q(i, 3) == 0.0;
 }
+
+// Dense-output weights b_i(theta), each by Horner's rule.
+template <class Tab, typename T> __device__ __forceinline__ void dense_weights(T th, T (&w)[7]) {
+#pragma unroll
+  for (int i = 1; i <= 7; ++i)
+    w[i - 1] = th * madd(th, madd(th, madd(th, T(Tab::q(i, 3)), T(Tab::q(i, 2))),
+                                  T(Tab::q(i, 1))),
+                         T(Tab::q(i, 0)));
+}
+
+// The stage derivatives k_1..k_7 of one step, as one indexable set.
+template <typename T, int R> struct Stages {
+  T k[7][R];
+};
 
 // Dense output of one evaluation point:  y + h * sum_i b_i(theta) k_i
 // (+ the state's compensation term in FP32).
-template <typename T, int R>
+template <class Tab, typename T, int R>
 __device__ __forceinline__ void dense_point(T theta, T h, const T (&y)[R], const T (&ylo)[R],
-                                            const T (&k1)[R], const T (&k3)[R], const T (&k4)[R],
-                                            const T (&k5)[R], const T (&k6)[R], const T (&k7)[R],
-                                            T (&out)[R]) {
-  using C = DP5;
+                                            const Stages<T, R>& K, T (&out)[R]) {
   T w[7];
-  dense_weights<T>(theta, w);
+  dense_weights<Tab, T>(theta, w);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    T s = w[0] * k1[r];
-    s = madd(w[2], k3[r], s);
-    s = madd(w[3], k4[r], s);
-    s = madd(w[4], k5[r], s);
-    s = madd(w[5], k6[r], s);
-    s = madd(w[6], k7[r], s);
+    T s = w[0] * K.k[0][r];
+#pragma unroll
+    for (int i = 2; i <= 7; ++i)
+      if (!dense_zero<Tab>(i)) s = madd(w[i - 1], K.k[i - 1][r], s);
     if constexpr (Comp<T>::on) out[r] = y[r] + madd(h, s, ylo[r]);
     else out[r] = madd(h, s, y[r]);
   }
@@ -347,27 +462,25 @@ __device__ __forceinline__ void dense_point(T theta, T h, const T (&y)[R], const
 // d/dt of the dense output at theta: sum_i b_i'(theta) k_i with b_i' the
 // derivatives of the same quartics (the step size cancels), times dir to
 // turn the solver's tau = dir t back into t.
-template <typename T, int R>
-__device__ __forceinline__ void dense_deriv(T th, T dir, const T (&k1)[R], const T (&k3)[R],
-                                            const T (&k4)[R], const T (&k5)[R],
-                                            const T (&k6)[R], const T (&k7)[R], T (&out)[R]) {
-  using C = DP5;
+template <class Tab, typename T, int R>
+__device__ __forceinline__ void dense_deriv(T th, T dir, const Stages<T, R>& K, T (&out)[R]) {
   T w[7];
-  w[0] = madd(th, madd(th, madd(th, T(4) * T(C::q13), T(3) * T(C::q12)), T(2) * T(C::q11)),
-              T(C::q10));
-  w[2] = th * madd(th, madd(th, T(4) * T(C::q33), T(3) * T(C::q32)), T(2) * T(C::q31));
-  w[3] = th * madd(th, madd(th, T(4) * T(C::q43), T(3) * T(C::q42)), T(2) * T(C::q41));
-  w[4] = th * madd(th, madd(th, T(4) * T(C::q53), T(3) * T(C::q52)), T(2) * T(C::q51));
-  w[5] = th * madd(th, madd(th, T(4) * T(C::q63), T(3) * T(C::q62)), T(2) * T(C::q61));
-  w[6] = th * madd(th, madd(th, T(4) * T(C::q73), T(3) * T(C::q72)), T(2) * T(C::q71));
+#pragma unroll
+  for (int i = 1; i <= 7; ++i) {
+    if (Tab::q(i, 0) != 0.0)
+      w[i - 1] = madd(th, madd(th, madd(th, T(4) * T(Tab::q(i, 3)), T(3) * T(Tab::q(i, 2))),
+                               T(2) * T(Tab::q(i, 1))),
+                      T(Tab::q(i, 0)));
+    else
+      w[i - 1] = th * madd(th, madd(th, T(4) * T(Tab::q(i, 3)), T(3) * T(Tab::q(i, 2))),
+                           T(2) * T(Tab::q(i, 1)));
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    T v = w[0] * k1[r];
-    v = madd(w[2], k3[r], v);
-    v = madd(w[3], k4[r], v);
-    v = madd(w[4], k5[r], v);
-    v = madd(w[5], k6[r], v);
-    v = madd(w[6], k7[r], v);
+    T v = w[0] * K.k[0][r];
+#pragma unroll
+    for (int i = 2; i <= 7; ++i)
+      if (!dense_zero<Tab>(i)) v = madd(w[i - 1], K.k[i - 1][r], v);
     out[r] = dir * v;
   }
 }
@@ -583,97 +696,53 @@ __device__ bool inst_init(const Field& F, Inst<T, R>& s, const SolveOpts& o, int
 }
 
 // ---------------------------------------------------------------- stages (a3, a4)
-// The six new stages of one attempt from (t, y, k1) with step h: the stage
-// inputs Y_2..Y_7 into ys (Y_7 is the new solution y1, SSAL), k3..k7 (k2 is
-// used only inside), the increment inc = h sum_i b_i k_i and y1 = y + inc.
-template <class Field, typename T, int R>
+// The six new stages of one attempt of the pair Tab from (t, y, K.k[0] = k1)
+// with step h: the stage inputs Y_2..Y_7 into ys (Y_7 is the new solution
+// y1, SSAL), K.k[1..6] = k2..k7, the increment inc = h sum_i b_i k_i and
+// y1 = y + inc.  Each stage input is y + h (a_i1 k1 + a_i2 k2 + ...), the
+// sum taken left to right; zero coefficients are skipped.  LAST = false
+// leaves out the evaluation at y1 (k7, FSAL: the next step's k1).
+template <class Tab, class Field, typename T, int R, bool LAST = true>
 __device__ __forceinline__ void attempt_stages(const Field& F, double t, T h, const T (&y)[R],
-                                               const T (&k1)[R], T (&ys)[6][R], T (&k3)[R],
-                                               T (&k4)[R], T (&k5)[R], T (&k6)[R], T (&k7)[R],
-                                               T (&y1)[R], T (&inc)[R]) {
-  using C = DP5;
+                                               Stages<T, R>& K, T (&ys)[6][R], T (&y1)[R],
+                                               T (&inc)[R]) {
   const double hd = (double)h;
-  T k2[R], Y[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) Y[r] = madd(h, T(C::a21) * k1[r], y[r]);
+  for (int i = 2; i <= 7; ++i) {
+    T Y[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) ys[0][r] = Y[r];
-  F.eval(t + C::c2 * hd, Y, k2);
+    for (int r = 0; r < R; ++r) {
+      T a = T(Tab::a(i, 1)) * K.k[0][r];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::a31) * k1[r];
-    a = madd(T(C::a32), k2[r], a);
-    Y[r] = madd(h, a, y[r]);
+      for (int j = 2; j < i; ++j)
+        if (Tab::a(i, j) != 0.0) a = madd(T(Tab::a(i, j)), K.k[j - 1][r], a);
+      if (i < 7) {
+        Y[r] = madd(h, a, y[r]);
+      } else {
+        inc[r] = h * a;
+        Y[r] = y[r] + inc[r];  // SSAL: the 7th stage input is the new solution
+        y1[r] = Y[r];
+      }
+      ys[i - 2][r] = Y[r];
+    }
+    if (i < 7 || LAST) F.eval(t + Tab::c(i) * hd, Y, K.k[i - 1]);
   }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[1][r] = Y[r];
-  F.eval(t + C::c3 * hd, Y, k3);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::a41) * k1[r];
-    a = madd(T(C::a42), k2[r], a);
-    a = madd(T(C::a43), k3[r], a);
-    Y[r] = madd(h, a, y[r]);
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[2][r] = Y[r];
-  F.eval(t + C::c4 * hd, Y, k4);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::a51) * k1[r];
-    a = madd(T(C::a52), k2[r], a);
-    a = madd(T(C::a53), k3[r], a);
-    a = madd(T(C::a54), k4[r], a);
-    Y[r] = madd(h, a, y[r]);
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[3][r] = Y[r];
-  F.eval(t + C::c5 * hd, Y, k5);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::a61) * k1[r];
-    a = madd(T(C::a62), k2[r], a);
-    a = madd(T(C::a63), k3[r], a);
-    a = madd(T(C::a64), k4[r], a);
-    a = madd(T(C::a65), k5[r], a);
-    Y[r] = madd(h, a, y[r]);
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[4][r] = Y[r];
-  F.eval(t + hd, Y, k6);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    T a = T(C::b1) * k1[r];
-    a = madd(T(C::b3), k3[r], a);
-    a = madd(T(C::b4), k4[r], a);
-    a = madd(T(C::b5), k5[r], a);
-    a = madd(T(C::b6), k6[r], a);
-    inc[r] = h * a;
-    y1[r] = y[r] + inc[r];  // SSAL: the 7th stage input is the new solution
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) ys[5][r] = y1[r];
-  F.eval(t + hd, y1, k7);
 }
 
 // Embedded error estimate e = h sum_i (b_i - bhat_i) k_i and the norm's
 // weights atol + rtol max(|y|, |y1|) (a4, a5); returns whether this lane's
 // components of y1 are finite.
-template <typename T, int R>
+template <class Tab, typename T, int R>
 __device__ __forceinline__ bool error_terms(T h, const T (&y)[R], const T (&y1)[R],
-                                            const T (&k1)[R], const T (&k3)[R], const T (&k4)[R],
-                                            const T (&k5)[R], const T (&k6)[R], const T (&k7)[R],
-                                            T rtol, T atol, T (&ev)[R], T (&sc)[R]) {
-  using C = DP5;
+                                            const Stages<T, R>& K, T rtol, T atol, T (&ev)[R],
+                                            T (&sc)[R]) {
   bool fin = true;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    T a = T(C::e1) * k1[r];
-    a = madd(T(C::e3), k3[r], a);
-    a = madd(T(C::e4), k4[r], a);
-    a = madd(T(C::e5), k5[r], a);
-    a = madd(T(C::e6), k6[r], a);
-    a = madd(T(C::e7), k7[r], a);
+    T a = T(Tab::e(1)) * K.k[0][r];
+#pragma unroll
+    for (int i = 2; i <= 7; ++i)
+      if (Tab::e(i) != 0.0) a = madd(T(Tab::e(i)), K.k[i - 1][r], a);
     ev[r] = h * a;
     sc[r] = madd(rtol, T(tmax(fabs(y[r]), fabs(y1[r]))), atol);
     fin = fin && finite_(y1[r]);
@@ -685,10 +754,9 @@ __device__ __forceinline__ bool error_terms(T h, const T (&y)[R], const T (&y1)[
 // Returns true while the instance is still running.
 // YP: the solve also writes dy/dt at the points (out.yp); a separate
 // instantiation, so that solves without it keep the leaner kernel.
-template <class Field, typename T, int R, int G, bool YP = false>
+template <class Tab, class Field, typename T, int R, int G, bool YP = false>
 __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, int i, int D,
                              const InstOut<T>& out, const TraceDev& tr, T (&ys)[6][R]) {
-  using C = DP5;
   T h = s.h;
   bool last = false;
   if constexpr (Comp<T>::on) {
@@ -704,10 +772,12 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
   }
   s.h_last = h;
   const double hd = (double)h;
-  T k3[R], k4[R], k5[R], k6[R], k7[R], y1[R], inc[R], ev[R], sc[R];
-  attempt_stages<Field, T, R>(F, s.t, h, s.y, s.k1, ys, k3, k4, k5, k6, k7, y1, inc);
-  const bool fin_local = error_terms<T, R>(h, s.y, y1, s.k1, k3, k4, k5, k6, k7, s.rtol, s.atol,
-                                           ev, sc);
+  Stages<T, R> K;
+#pragma unroll
+  for (int r = 0; r < R; ++r) K.k[0][r] = s.k1[r];
+  T y1[R], inc[R], ev[R], sc[R];
+  attempt_stages<Tab, Field, T, R>(F, s.t, h, s.y, K, ys, y1, inc);
+  const bool fin_local = error_terms<Tab, T, R>(h, s.y, y1, K, s.rtol, s.atol, ev, sc);
   const T err = rms_norm<T, R, G>(ev, sc);
   bool finite = finite_(err);
   if constexpr (G > 1) finite = finite && (__all_sync(Grp<G>::mask(), fin_local) != 0);
@@ -759,13 +829,12 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
         if constexpr (Comp<T>::on) theta = T(tq - s.t) / h;
         else theta = T((tq - s.t) / hd);
         T v[R];
-        dense_point<T, R>(theta, h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
+        dense_point<Tab, T, R>(theta, h, s.y, s.ylo, K, v);
         store_point<T, R, G>(dst, v);
       }
       if constexpr (YP) {
         T v[R];
-        dense_deriv<T, R>(theta, (s.flags & FL_REVERSE) ? T(-1) : T(1), s.k1, k3, k4, k5, k6,
-                          k7, v);
+        dense_deriv<Tab, T, R>(theta, (s.flags & FL_REVERSE) ? T(-1) : T(1), K, v);
         store_point<T, R, G>(out.yp + (size_t)s.cursor * D, v);
       }
       advance_cursor(s, out);
@@ -793,7 +862,7 @@ __device__ bool inst_attempt(const Field& F, Inst<T, R>& s, const SolveOpts& o, 
     for (int r = 0; r < R; ++r) {
       s.y[r] = yn[r];
       s.ylo[r] = ylon[r];
-      s.k1[r] = k7[r];  // FSAL
+      s.k1[r] = K.k[6][r];  // FSAL
     }
     if (last) s.status = ST_SUCCESS;
   } else {

@@ -120,6 +120,14 @@ tode_err simt_adjoint_f64(const AdjReq& r);
 tode_err simt_adjoint_f32(const AdjReq& r);
 tode_err simt_t_bounds_f64(const AdjReq& r, const void* yp, double* gt0, double* gt1);
 tode_err simt_t_bounds_f32(const AdjReq& r, const void* yp, double* gt0, double* gt1);
+// the same for the tsit5 pair (tode_simt_ts5_f64.cu, tode_simt_ts5_f32.cu);
+// the functions above hand over to these when o->method is TODE_TSIT5
+tode_err simt_solve_ts5_f64(const SolveReq& r);
+tode_err simt_solve_ts5_f32(const SolveReq& r);
+tode_err simt_adjoint_ts5_f64(const AdjReq& r);
+tode_err simt_adjoint_ts5_f32(const AdjReq& r);
+tode_err simt_t_bounds_ts5_f64(const AdjReq& r, const void* yp, double* gt0, double* gt1);
+tode_err simt_t_bounds_ts5_f32(const AdjReq& r, const void* yp, double* gt0, double* gt1);
 
 bool simt_supported(int kind, int D);
 

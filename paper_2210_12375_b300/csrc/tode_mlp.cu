@@ -1067,7 +1067,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
           } else {
             const float th = float(tq - s.t) / h;
             float w[7];
-            dense_weights<float>(th, w);
+            dense_weights<DP5, float>(th, w);
 #pragma unroll
             for (int r = 0; r < C; ++r) {
               float acc = w[0] * k1[r];
@@ -1589,7 +1589,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 #pragma unroll
             for (int j = 0; j < 7; ++j) w[j] = bw[j];
           } else {
-            dense_weights<float>(float(tq - tn) / h, w);
+            dense_weights<DP5, float>(float(tq - tn) / h, w);
           }
 #pragma unroll
           for (int j = 0; j < 7; ++j)
@@ -2245,7 +2245,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
 #pragma unroll
             for (int j = 0; j < 7; ++j) w[j] = bw[j];
           } else {
-            dense_weights<float>(float(tq - tn) / h, w);
+            dense_weights<DP5, float>(float(tq - tn) / h, w);
           }
 #pragma unroll
           for (int j = 0; j < 7; ++j)

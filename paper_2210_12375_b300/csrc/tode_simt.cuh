@@ -148,7 +148,7 @@ __global__ void k_plain_init(SolveArgs<T> a) {
                            a.status, a.trace);
 }
 
-template <class Field, typename T, int R, int G, bool YP>
+template <class Tab, class Field, typename T, int R, int G, bool YP>
 __global__ void k_plain_step(SolveArgs<T> a) {
   const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G);
   if (j >= a.B) return;
@@ -161,7 +161,7 @@ __global__ void k_plain_step(SolveArgs<T> a) {
   const int acc_before = s.n_acc;
   T ys[6][R];
   const bool run =
-      inst_attempt<Field, T, R, G, YP>(F, s, a.o, i, a.D, inst_out(a, i), a.trace, ys);
+      inst_attempt<Tab, Field, T, R, G, YP>(F, s, a.o, i, a.D, inst_out(a, i), a.trace, ys);
   if (s.n_acc != acc_before) {
     tape_store_hacc<T, R, G>(a.tape, i, s, ys);
     if (run) tape_store<T, R, G>(a.tape, i, s);
@@ -179,7 +179,7 @@ __global__ void k_plain_step(SolveArgs<T> a) {
 // Persistent kernel: each group integrates one instance at a time to its end
 // and then steals the next; one loop iteration is one attempt, so a group
 // whose instance finished refills at once instead of waiting for its warp.
-template <class Field, typename T, int R, int G, bool YP>
+template <class Tab, class Field, typename T, int R, int G, bool YP>
 __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
   const int groups_total = (int)((gridDim.x * (size_t)blockDim.x) / G);
   int i = queued(a, (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / G));
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_fused(SolveArgs<T> a) {
     const int acc_before = s.n_acc;
     T ys[6][R];
     const bool run =
-        inst_attempt<Field, T, R, G, YP>(F, s, a.o, i, a.D, inst_out(a, i), a.trace, ys);
+        inst_attempt<Tab, Field, T, R, G, YP>(F, s, a.o, i, a.D, inst_out(a, i), a.trace, ys);
     if (s.n_acc != acc_before) tape_store_hacc<T, R, G>(a.tape, i, s, ys);
     if (run) {
       if (s.n_acc != acc_before) tape_store<T, R, G>(a.tape, i, s);
@@ -331,7 +331,7 @@ inline int default_block(long long threads, int num_sms) {
   return b;
 }
 
-template <class Field, typename T, int R, int G, bool YP>
+template <class Tab, class Field, typename T, int R, int G, bool YP>
 tode_err launch_solve_yp(const SolveReq& r) {
   SolveArgs<T> a = make_solve_args<T>(r);
   const cudaStream_t st = r.stream;
@@ -352,9 +352,9 @@ tode_err launch_solve_yp(const SolveReq& r) {
     const long long limit = (long long)r.o->max_steps + 2LL * poll + 2;
     while (true) {
       for (int c = 0; c < poll - 1; ++c)
-        k_plain_step<Field, T, R, G, YP><<<grid, block, 0, st>>>(a);
+        k_plain_step<Tab, Field, T, R, G, YP><<<grid, block, 0, st>>>(a);
       TODE_CUDA_TRY(cudaMemsetAsync(a.active, 0, sizeof(int32_t), st));
-      k_plain_step<Field, T, R, G, YP><<<grid, block, 0, st>>>(a);
+      k_plain_step<Tab, Field, T, R, G, YP><<<grid, block, 0, st>>>(a);
       TODE_CUDA_TRY(cudaGetLastError());
       launched += poll;
       int32_t any = 0;
@@ -371,7 +371,7 @@ tode_err launch_solve_yp(const SolveReq& r) {
   int per_sm = r.o->ctas_per_sm;
   if (per_sm <= 0) {
     TODE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, k_fused<Field, T, R, G, YP>, block, 0));
+        &per_sm, k_fused<Tab, Field, T, R, G, YP>, block, 0));
     if (per_sm < 1) per_sm = 1;
   }
   long long grid = (long long)r.num_sms * per_sm;
@@ -379,15 +379,15 @@ tode_err launch_solve_yp(const SolveReq& r) {
   if (grid > need) grid = need;
   if (grid == 0) return TODE_OK;
   TODE_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int32_t), st));
-  k_fused<Field, T, R, G, YP><<<(int)grid, block, 0, st>>>(a);
+  k_fused<Tab, Field, T, R, G, YP><<<(int)grid, block, 0, st>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
 }
 
-template <class Field, typename T, int R, int G>
+template <class Tab, class Field, typename T, int R, int G>
 tode_err launch_solve(const SolveReq& r) {
-  return r.yp ? launch_solve_yp<Field, T, R, G, true>(r)
-              : launch_solve_yp<Field, T, R, G, false>(r);
+  return r.yp ? launch_solve_yp<Tab, Field, T, R, G, true>(r)
+              : launch_solve_yp<Tab, Field, T, R, G, false>(r);
 }
 
 // Lanes per instance of the linear field (0 = unsupported combination).
@@ -404,18 +404,18 @@ inline int linear_group(int D, int requested) {
   }
 }
 
-// Field / group dispatch for one state dtype.
-template <typename T> tode_err simt_solve(const SolveReq& r) {
-  if (r.f->kind == TODE_VDP) return launch_solve<VdpField<T>, T, 2, 1>(r);
+// Field / group dispatch for one state dtype and pair.
+template <class Tab, typename T> tode_err simt_solve(const SolveReq& r) {
+  if (r.f->kind == TODE_VDP) return launch_solve<Tab, VdpField<T>, T, 2, 1>(r);
   switch (linear_group(r.D, r.o->group)) {
-    case 1: return launch_solve<LinearField<T, 1, 1>, T, 1, 1>(r);
-    case 2: return launch_solve<LinearField<T, 1, 2>, T, 1, 2>(r);
-    case 4: return r.D == 4 ? launch_solve<LinearField<T, 1, 4>, T, 1, 4>(r)
-                            : launch_solve<LinearField<T, 4, 4>, T, 4, 4>(r);
-    case 8: return r.D == 8 ? launch_solve<LinearField<T, 1, 8>, T, 1, 8>(r)
-                            : launch_solve<LinearField<T, 2, 8>, T, 2, 8>(r);
-    case 16: return r.D == 16 ? launch_solve<LinearField<T, 1, 16>, T, 1, 16>(r)
-                              : launch_solve<LinearField<T, 2, 16>, T, 2, 16>(r);
+    case 1: return launch_solve<Tab, LinearField<T, 1, 1>, T, 1, 1>(r);
+    case 2: return launch_solve<Tab, LinearField<T, 1, 2>, T, 1, 2>(r);
+    case 4: return r.D == 4 ? launch_solve<Tab, LinearField<T, 1, 4>, T, 1, 4>(r)
+                            : launch_solve<Tab, LinearField<T, 4, 4>, T, 4, 4>(r);
+    case 8: return r.D == 8 ? launch_solve<Tab, LinearField<T, 1, 8>, T, 1, 8>(r)
+                            : launch_solve<Tab, LinearField<T, 2, 8>, T, 2, 8>(r);
+    case 16: return r.D == 16 ? launch_solve<Tab, LinearField<T, 1, 16>, T, 1, 16>(r)
+                              : launch_solve<Tab, LinearField<T, 2, 16>, T, 2, 16>(r);
     default: return TODE_EUNSUPPORTED;
   }
 }

@@ -1,4 +1,4 @@
-// tode_simt_adjoint.cuh -- discrete adjoint of the fixed-mesh dopri5 map for
+// tode_simt_adjoint.cuh -- discrete adjoint of the fixed-mesh map of the pair (dopri5 or tsit5) for
 // the SIMT fields (torchode App. A: gradients by backpropagation through the
 // solver, i.e. discretize-then-optimize).
 //
@@ -233,15 +233,13 @@ __device__ __forceinline__ void adj_load_slot(const AdjArgs<T>& a, int i, int D,
 // Reverse one accepted step.  sl: the step (YS: with its recorded stage
 // inputs), yb: running cotangent, c: cursor over the instance's evaluation
 // points, from the last backwards.
-template <bool YS, class AF, typename T, int R, int G>
+template <class Tab, bool YS, class AF, typename T, int R, int G>
 __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, int D,
                                              const AdjSlot<T, R>& sl, double t_next, T (&yb)[R],
                                              AdjCursor<T, R>& c) {
-  using C = DP5;
   const double t = sl.t;
   const T h = sl.h;
   const T (&y)[R] = sl.y;
-  const T (&k1)[R] = sl.k1;
   T Y[7][R];
 #pragma unroll
   for (int r = 0; r < R; ++r) Y[0][r] = y[r];
@@ -252,61 +250,23 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
 #pragma unroll
       for (int r = 0; r < R; ++r) Y[q6 + 1][r] = sl.ys[q6][r];
   } else {
-    // recompute them with the forward's operations (bit for bit)
-    T k[6][R];
-    const double hd = (double)h;
+    // recompute them with the forward's own stage code (bit for bit), less
+    // the evaluation at y_{n+1}
+    Stages<T, R> K;
+    T ysr[6][R], y1[R], inc[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) k[0][r] = k1[r];
+    for (int r = 0; r < R; ++r) K.k[0][r] = sl.k1[r];
+    attempt_stages<Tab, AF, T, R, false>(F, t, h, y, K, ysr, y1, inc);
 #pragma unroll
-    for (int r = 0; r < R; ++r) Y[1][r] = madd(h, T(C::a21) * k[0][r], y[r]);
-    F.eval(t + C::c2 * hd, Y[1], k[1]);
+    for (int q6 = 0; q6 < 6; ++q6)
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      T s = T(C::a31) * k[0][r];
-      s = madd(T(C::a32), k[1][r], s);
-      Y[2][r] = madd(h, s, y[r]);
-    }
-    F.eval(t + C::c3 * hd, Y[2], k[2]);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      T s = T(C::a41) * k[0][r];
-      s = madd(T(C::a42), k[1][r], s);
-      s = madd(T(C::a43), k[2][r], s);
-      Y[3][r] = madd(h, s, y[r]);
-    }
-    F.eval(t + C::c4 * hd, Y[3], k[3]);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      T s = T(C::a51) * k[0][r];
-      s = madd(T(C::a52), k[1][r], s);
-      s = madd(T(C::a53), k[2][r], s);
-      s = madd(T(C::a54), k[3][r], s);
-      Y[4][r] = madd(h, s, y[r]);
-    }
-    F.eval(t + C::c5 * hd, Y[4], k[4]);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      T s = T(C::a61) * k[0][r];
-      s = madd(T(C::a62), k[1][r], s);
-      s = madd(T(C::a63), k[2][r], s);
-      s = madd(T(C::a64), k[3][r], s);
-      s = madd(T(C::a65), k[4][r], s);
-      Y[5][r] = madd(h, s, y[r]);
-    }
-    F.eval(t + hd, Y[5], k[5]);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      T s = T(C::b1) * k[0][r];
-      s = madd(T(C::b3), k[2][r], s);
-      s = madd(T(C::b4), k[3][r], s);
-      s = madd(T(C::b5), k[4][r], s);
-      s = madd(T(C::b6), k[5][r], s);
-      Y[6][r] = y[r] + h * s;  // the forward's new solution y + (h s)
-    }
+      for (int r = 0; r < R; ++r) Y[q6 + 1][r] = ysr[q6][r];
   }
 
   // cotangents of the stage derivatives
-  const T bw[7] = {T(C::b1), T(0), T(C::b3), T(C::b4), T(C::b5), T(C::b6), T(0)};
+  T bw[7];
+#pragma unroll
+  for (int s = 0; s < 7; ++s) bw[s] = T(Tab::b(s + 1));
   T kb[7][R];
 #pragma unroll
   for (int s = 0; s < 7; ++s)
@@ -328,7 +288,7 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
         T th;
         if constexpr (Comp<T>::on) th = T(tq - t) / h;
         else th = T((tq - t) / (double)h);
-        dense_weights<T>(th, w);
+        dense_weights<Tab, T>(th, w);
         dense7 = true;
       }
 #pragma unroll
@@ -340,23 +300,18 @@ __device__ __forceinline__ void reverse_step(AF& F, const AdjArgs<T>& a, int i, 
     }
     adj_cursor_next<T, R, G>(c, a, i, D);
   }
-  // reverse stage sweep
-  const T A[7][6] = {{T(0), T(0), T(0), T(0), T(0), T(0)},
-                     {T(C::a21), T(0), T(0), T(0), T(0), T(0)},
-                     {T(C::a31), T(C::a32), T(0), T(0), T(0), T(0)},
-                     {T(C::a41), T(C::a42), T(C::a43), T(0), T(0), T(0)},
-                     {T(C::a51), T(C::a52), T(C::a53), T(C::a54), T(0), T(0)},
-                     {T(C::a61), T(C::a62), T(C::a63), T(C::a64), T(C::a65), T(0)},
-                     {T(C::b1), T(0), T(C::b3), T(C::b4), T(C::b5), T(C::b6)}};
+  // reverse stage sweep (b_7 = 0: kbar_7 = 0 without interior dense points)
 #pragma unroll
   for (int s = 6; s >= 0; --s) {
-    if (s == 6 && !dense7) continue;  // kbar_7 = 0 without interior dense points
+    if (s == 6 && !dense7) continue;
     T gs[R];
     F.vjp(Y[s], kb[s], gs);
 #pragma unroll
     for (int l = 0; l < s; ++l)
+      if (Tab::a(s + 1, l + 1) != 0.0)
 #pragma unroll
-      for (int r = 0; r < R; ++r) kb[l][r] = madd(h * A[s][l], gs[r], kb[l][r]);
+        for (int r = 0; r < R; ++r)
+          kb[l][r] = madd(h * T(Tab::a(s + 1, l + 1)), gs[r], kb[l][r]);
 #pragma unroll
     for (int r = 0; r < R; ++r) yb[r] = yb[r] + gs[r];
   }
@@ -399,7 +354,7 @@ __device__ __forceinline__ void adjoint_finish(AF& F, const AdjArgs<T>& a, int i
 // iteration reverses one step straight from its slot, and a group whose
 // instance is done finishes it and steals the next at once, so the groups of
 // a warp stay on the common step body whatever their step counts.
-template <class AF, typename T, bool YS>
+template <class Tab, class AF, typename T, bool YS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(AdjArgs<T> a) {
   constexpr int R = AF::R, G = AF::G;
   const int D = a.D;
@@ -443,7 +398,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
     if (n > 0) adj_load_slot<YS, T, R, G>(a, i, D, n - 1, nxt);
     const double t_next = t_after;  // the forward's t + h, bit for bit
     t_after = cur.t;
-    reverse_step<YS, AF, T, R, G>(F, a, i, D, cur, t_next, yb, c);
+    reverse_step<Tab, YS, AF, T, R, G>(F, a, i, D, cur, t_next, yb, c);
     cur = nxt;
     --n;
   }
@@ -452,7 +407,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint_steps(A
 // Re-running form (strided tape, or no recorded step sizes): each segment
 // between slots is re-run with the forward routine from its slot, its
 // step-start states parked in scratch, then reversed.
-template <class AF, typename T>
+template <class Tab, class AF, typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs<T> a) {
   constexpr int R = AF::R, G = AF::G;
   const int D = a.D;
@@ -522,7 +477,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
           ks[r] = s.k1[r];
         }
         T ysd[6][R];
-        inst_attempt<AF, T, R, G>(F, s, ro, i, D, no_out, no_trace, ysd);
+        inst_attempt<Tab, AF, T, R, G>(F, s, ro, i, D, no_out, no_trace, ysd);
         const T hb = s.h_last;
         if (s.n_acc != before) {
           const size_t p = (size_t)(before - n0) * a.B + i;
@@ -553,7 +508,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
         sl.t = a.st[p];
         sl.h = a.sh[p];
         const double t_next = (n == N - 1) ? t1 : sl.t + (double)sl.h;
-        reverse_step<false, AF, T, R, G>(F, a, i, D, sl, t_next, yb, c);
+        reverse_step<Tab, false, AF, T, R, G>(F, a, i, D, sl, t_next, yb, c);
       }
       if constexpr (G > 1) __syncwarp(Grp<G>::mask());
     }
@@ -562,7 +517,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adjoint(AdjArgs
   }
 }
 
-template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
+template <class Tab, class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   const bool direct = r.tape->stride == 1 && r.tape->h_acc != nullptr;
   AdjArgs<T> a{};
   a.B = r.B;
@@ -604,8 +559,9 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
   const long long threads = (long long)r.B * AF::G;
   const int block = r.o->block > 0 ? r.o->block : default_block(threads, r.num_sms);
   if (block % 32 != 0 || block > 256) return TODE_EINVAL;
-  auto kern = !direct ? k_adjoint<AF, T>
-              : r.tape->y_stage ? k_adjoint_steps<AF, T, true> : k_adjoint_steps<AF, T, false>;
+  auto kern = !direct ? k_adjoint<Tab, AF, T>
+              : r.tape->y_stage ? k_adjoint_steps<Tab, AF, T, true>
+                                : k_adjoint_steps<Tab, AF, T, false>;
   int per_sm = 0;
   TODE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0));
   if (per_sm < 1) per_sm = 1;
@@ -627,19 +583,19 @@ template <class AF, typename T> tode_err launch_adjoint(const AdjReq& r) {
 // and reversing a step gives the same bits for every grouping (each lane
 // holds whole rows and columns), so D = 16 then takes 16 lanes with A's
 // column in registers (measured fastest for the adjoint).
-template <typename T> tode_err simt_adjoint(const AdjReq& r) {
-  if (r.f->kind == TODE_VDP) return launch_adjoint<VdpAdj<T>, T>(r);
+template <class Tab, typename T> tode_err simt_adjoint(const AdjReq& r) {
+  if (r.f->kind == TODE_VDP) return launch_adjoint<Tab, VdpAdj<T>, T>(r);
   const bool direct = r.tape->stride == 1 && r.tape->h_acc != nullptr;
-  if (direct && r.D == 16) return launch_adjoint<LinearAdj<T, 1, 16>, T>(r);
+  if (direct && r.D == 16) return launch_adjoint<Tab, LinearAdj<T, 1, 16>, T>(r);
   switch (linear_group(r.D, r.o->group)) {
-    case 1: return launch_adjoint<LinearAdj<T, 1, 1>, T>(r);
-    case 2: return launch_adjoint<LinearAdj<T, 1, 2>, T>(r);
-    case 4: return r.D == 4 ? launch_adjoint<LinearAdj<T, 1, 4>, T>(r)
-                            : launch_adjoint<LinearAdj<T, 4, 4>, T>(r);
-    case 8: return r.D == 8 ? launch_adjoint<LinearAdj<T, 1, 8>, T>(r)
-                            : launch_adjoint<LinearAdj<T, 2, 8>, T>(r);
-    case 16: return r.D == 16 ? launch_adjoint<LinearAdj<T, 1, 16>, T>(r)
-                              : launch_adjoint<LinearAdj<T, 2, 16>, T>(r);
+    case 1: return launch_adjoint<Tab, LinearAdj<T, 1, 1>, T>(r);
+    case 2: return launch_adjoint<Tab, LinearAdj<T, 1, 2>, T>(r);
+    case 4: return r.D == 4 ? launch_adjoint<Tab, LinearAdj<T, 1, 4>, T>(r)
+                            : launch_adjoint<Tab, LinearAdj<T, 4, 4>, T>(r);
+    case 8: return r.D == 8 ? launch_adjoint<Tab, LinearAdj<T, 1, 8>, T>(r)
+                            : launch_adjoint<Tab, LinearAdj<T, 2, 8>, T>(r);
+    case 16: return r.D == 16 ? launch_adjoint<Tab, LinearAdj<T, 1, 16>, T>(r)
+                              : launch_adjoint<Tab, LinearAdj<T, 2, 16>, T>(r);
     default: return TODE_EUNSUPPORTED;
   }
 }
@@ -673,9 +629,8 @@ template <int G> __device__ __forceinline__ double group_sum(double v) {
   return v;
 }
 
-template <class AF, typename T, bool YS>
+template <class Tab, class AF, typename T, bool YS>
 __global__ void __launch_bounds__(128) k_t_bounds(TBoundsArgs<T> ta) {
-  using C = DP5;
   constexpr int R = AF::R, G = AF::G;
   const AdjArgs<T>& a = ta.a;
   const int D = a.D;
@@ -708,7 +663,9 @@ __global__ void __launch_bounds__(128) k_t_bounds(TBoundsArgs<T> ta) {
       const T h = sl.h;
       const double hd = (double)h;
       // the stage inputs (recorded, or recomputed from y and k1) and k_i = f(Y_i)
-      T Y[7][R], k[7][R];
+      T Y[7][R];
+      Stages<T, R> KS;
+      T (&k)[7][R] = KS.k;
 #pragma unroll
       for (int r = 0; r < R; ++r) Y[0][r] = sl.y[r];
       if constexpr (YS) {
@@ -717,14 +674,15 @@ __global__ void __launch_bounds__(128) k_t_bounds(TBoundsArgs<T> ta) {
 #pragma unroll
           for (int r = 0; r < R; ++r) Y[q6 + 1][r] = sl.ys[q6][r];
       }
-      const T A[7][6] = {{T(0), T(0), T(0), T(0), T(0), T(0)},
-                         {T(C::a21), T(0), T(0), T(0), T(0), T(0)},
-                         {T(C::a31), T(C::a32), T(0), T(0), T(0), T(0)},
-                         {T(C::a41), T(C::a42), T(C::a43), T(0), T(0), T(0)},
-                         {T(C::a51), T(C::a52), T(C::a53), T(C::a54), T(0), T(0)},
-                         {T(C::a61), T(C::a62), T(C::a63), T(C::a64), T(C::a65), T(0)},
-                         {T(C::b1), T(0), T(C::b3), T(C::b4), T(C::b5), T(C::b6)}};
-      const double cs[7] = {0.0, C::c2, C::c3, C::c4, C::c5, 1.0, 1.0};
+      T A[7][6], bw[7];
+      double cs[7];
+#pragma unroll
+      for (int s = 0; s < 7; ++s) {
+        cs[s] = Tab::c(s + 1);
+        bw[s] = T(Tab::b(s + 1));
+#pragma unroll
+        for (int l = 0; l < 6; ++l) A[s][l] = T(Tab::a(s + 1, l + 1));
+      }
 #pragma unroll
       for (int s = 0; s < 7; ++s) {
         if constexpr (!YS) {
@@ -740,7 +698,6 @@ __global__ void __launch_bounds__(128) k_t_bounds(TBoundsArgs<T> ta) {
         }
         F.eval(t + cs[s] * hd, Y[s], k[s]);
       }
-      const T bw[7] = {T(C::b1), T(0), T(C::b3), T(C::b4), T(C::b5), T(C::b6), T(0)};
       T yb[R], kb[7][R];
 #pragma unroll
       for (int r = 0; r < R; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + g * R + r] : T(0);
@@ -774,9 +731,9 @@ __global__ void __launch_bounds__(128) k_t_bounds(TBoundsArgs<T> ta) {
           } else {
             if constexpr (Comp<T>::on) th = T(tq - t) / h;
             else th = T((tq - t) / hd);
-            dense_weights<T>(th, w);
+            dense_weights<Tab, T>(th, w);
           }
-          dense_deriv<T, R>(th, T(1), k[0], k[2], k[3], k[4], k[5], k[6], dv);
+          dense_deriv<Tab, T, R>(th, T(1), KS, dv);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             T sw = T(0);
@@ -819,7 +776,8 @@ __global__ void __launch_bounds__(128) k_t_bounds(TBoundsArgs<T> ta) {
   }
 }
 
-template <class AF, typename T> tode_err launch_t_bounds(const AdjReq& r, const void* yp,
+template <class Tab, class AF, typename T>
+tode_err launch_t_bounds(const AdjReq& r, const void* yp,
                                                          double* gt0, double* gt1) {
   TBoundsArgs<T> ta{};
   AdjArgs<T>& a = ta.a;
@@ -842,22 +800,23 @@ template <class AF, typename T> tode_err launch_t_bounds(const AdjReq& r, const 
   long long grid = (threads + 127) / 128;
   if (grid > (long long)r.num_sms * 16) grid = (long long)r.num_sms * 16;
   if (grid == 0) return TODE_OK;
-  if (r.tape->y_stage) k_t_bounds<AF, T, true><<<(int)grid, 128, 0, r.stream>>>(ta);
-  else k_t_bounds<AF, T, false><<<(int)grid, 128, 0, r.stream>>>(ta);
+  if (r.tape->y_stage) k_t_bounds<Tab, AF, T, true><<<(int)grid, 128, 0, r.stream>>>(ta);
+  else k_t_bounds<Tab, AF, T, false><<<(int)grid, 128, 0, r.stream>>>(ta);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
 }
 
-template <typename T> tode_err simt_t_bounds(const AdjReq& r, const void* yp, double* gt0,
+template <class Tab, typename T>
+tode_err simt_t_bounds(const AdjReq& r, const void* yp, double* gt0,
                                             double* gt1) {
-  if (r.f->kind == TODE_VDP) return launch_t_bounds<VdpAdj<T>, T>(r, yp, gt0, gt1);
+  if (r.f->kind == TODE_VDP) return launch_t_bounds<Tab, VdpAdj<T>, T>(r, yp, gt0, gt1);
   switch (r.D) {  // one column of A per lane, as the direct adjoint takes it
-    case 1: return launch_t_bounds<LinearAdj<T, 1, 1>, T>(r, yp, gt0, gt1);
-    case 2: return launch_t_bounds<LinearAdj<T, 1, 2>, T>(r, yp, gt0, gt1);
-    case 4: return launch_t_bounds<LinearAdj<T, 1, 4>, T>(r, yp, gt0, gt1);
-    case 8: return launch_t_bounds<LinearAdj<T, 1, 8>, T>(r, yp, gt0, gt1);
-    case 16: return launch_t_bounds<LinearAdj<T, 1, 16>, T>(r, yp, gt0, gt1);
-    case 32: return launch_t_bounds<LinearAdj<T, 2, 16>, T>(r, yp, gt0, gt1);
+    case 1: return launch_t_bounds<Tab, LinearAdj<T, 1, 1>, T>(r, yp, gt0, gt1);
+    case 2: return launch_t_bounds<Tab, LinearAdj<T, 1, 2>, T>(r, yp, gt0, gt1);
+    case 4: return launch_t_bounds<Tab, LinearAdj<T, 1, 4>, T>(r, yp, gt0, gt1);
+    case 8: return launch_t_bounds<Tab, LinearAdj<T, 1, 8>, T>(r, yp, gt0, gt1);
+    case 16: return launch_t_bounds<Tab, LinearAdj<T, 1, 16>, T>(r, yp, gt0, gt1);
+    case 32: return launch_t_bounds<Tab, LinearAdj<T, 2, 16>, T>(r, yp, gt0, gt1);
     default: return TODE_EUNSUPPORTED;
   }
 }

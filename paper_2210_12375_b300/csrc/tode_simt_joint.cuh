@@ -389,9 +389,13 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
       // ---- attempt n with the batch's step
       const T h = c.h_use;
       const double hd = (double)h;
-      T ys[6][R], k3[R], k4[R], k5[R], k6[R], k7[R], y1[R], inc[R], ev[R], sc[R], q2[R];
-      attempt_stages<Field, T, R>(F, c.t, h, s.y, s.k1, ys, k3, k4, k5, k6, k7, y1, inc);
-      bool fin = error_terms<T, R>(h, s.y, y1, s.k1, k3, k4, k5, k6, k7, s.rtol, s.atol, ev, sc);
+      T ys[6][R], y1[R], inc[R], ev[R], sc[R], q2[R];
+      Stages<T, R> K;  // the joint solve runs the dopri5 pair
+#pragma unroll
+      for (int r = 0; r < R; ++r) K.k[0][r] = s.k1[r];
+      attempt_stages<DP5, Field, T, R>(F, c.t, h, s.y, K, ys, y1, inc);
+      const T (&k7)[R] = K.k[6];
+      bool fin = error_terms<DP5, T, R>(h, s.y, y1, K, s.rtol, s.atol, ev, sc);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const T u = ev[r] / sc[r];
@@ -438,7 +442,7 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
           if constexpr (Comp<T>::on) theta = T(tq - c.t) / h;
           else theta = T((tq - c.t) / hd);
           T v[R];
-          dense_point<T, R>(theta, h, s.y, s.ylo, s.k1, k3, k4, k5, k6, k7, v);
+          dense_point<DP5, T, R>(theta, h, s.y, s.ylo, K, v);
           store_point<T, R, G>(dst, v);
         }
       }
