@@ -13,6 +13,7 @@ from .oracle import (  # noqa: F401
     solve_joint,
     replay,
     adjoint,
+    joint_adjoint,
     tableau_doubles,
     tableau_m,
     dense_weights_m,

@@ -48,6 +48,7 @@ class _Field(C.Structure):
         ("bias", C.POINTER(_dp)),
         ("inner", C.c_void_p),
         ("n_inner", C.c_int),
+        ("scr", _dp),
     ]
 
 
@@ -106,6 +107,7 @@ def _load():
         lib.orc_adjoint_t.restype = C.c_int
         lib.orc_adjoint_tm.restype = C.c_int
         lib.orc_replay_m.restype = C.c_int
+        lib.orc_joint_adjoint.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -432,6 +434,43 @@ def adjoint(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None, gy_eva
         out["gt0"], out["gt1"] = gt0, gt1
     out["gy0"] = gy0
     return out
+
+
+def joint_adjoint(field: dict, y1, t0: float, t1: float, t_eval=None, gy_eval=None,
+                  gy_final=None, opts: dict | None = None) -> dict:
+    """Joint continuous adjoint of B instances of an MLP field over a shared
+    time axis (App. A, the CNF benchmark's "torchode-joint" backward pass):
+    the augmented system [y; a; abar] of size 2BD + P solved backward from
+    t1 to t0 as one problem, stopping at every evaluation point to add its
+    cotangent.  y1 [B,D] = y(t1) of the forward solve; t_eval [K] shared;
+    gy_eval [B,K,D], gy_final [B,D].  Returns gy0 [B,D], gW / gb (lists,
+    like the MLP field's W / b), y0 [B,D] (the state integrated back to t0)
+    and n_acc, n_rej, n_feval, status over all segments."""
+    lib = _load()
+    y1 = np.asarray(y1, dtype=np.float64)
+    B, D = y1.shape
+    fh = _FieldHolder(field, B)
+    assert field["kind"] == "mlp" and fh.D == D
+    keep = []
+    o = _opts_struct(default_opts(**(opts or {})), B, keep)
+    te = np.ascontiguousarray(np.zeros(0) if t_eval is None else t_eval, dtype=np.float64).reshape(-1)
+    K = te.shape[0]
+    gye = _f64(gy_eval, (B, K, D)) if gy_eval is not None else None
+    gyf = _f64(gy_final, (B, D)) if gy_final is not None else None
+    gy0 = np.zeros((B, D))
+    y0 = np.zeros((B, D))
+    gW = [np.zeros_like(np.asarray(w, dtype=np.float64)) for w in field["W"]]
+    gb = [np.zeros_like(np.asarray(b, dtype=np.float64)) for b in field["b"]]
+    gW_ptrs = (_dp * len(gW))(*[_ptr(w) for w in gW])
+    gb_ptrs = (_dp * len(gb))(*[_ptr(b) for b in gb])
+    stats = np.zeros(4, np.int32)
+    rc = lib.orc_joint_adjoint(C.byref(fh.f), C.byref(o), C.c_int(B), _ptr(_f64(y1, (B, D))),
+                               C.c_double(t0), C.c_double(t1), _ptr(te), C.c_int(K), _ptr(gye),
+                               _ptr(gyf), _ptr(gy0), gW_ptrs, gb_ptrs, _ptr(y0), _iptr(stats))
+    if rc != 0:
+        raise ValueError("orc_joint_adjoint: invalid call")
+    return dict(gy0=gy0, gW=gW, gb=gb, y0=y0, n_acc=int(stats[0]), n_rej=int(stats[1]),
+                n_feval=int(stats[2]), status=int(stats[3]))
 
 
 def mesh_from_trace(res: dict):

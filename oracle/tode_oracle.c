@@ -23,6 +23,11 @@
  *     last error estimates (Soderlind 2002/2003); the PI subset is used here.
  *   - App. A, FEN benchmark: gradients by backpropagation through the solver
  *     (discretize-then-optimize) -> the discrete adjoint of the fixed-mesh map.
+ *   - App. A, CNF benchmark ("torchode-joint"): the continuous adjoint
+ *     equation of the whole batch solved jointly, one problem of size
+ *     2bf + p (the state integrated back, its adjoint, the shared
+ *     parameters' adjoint) -> orc_joint_adjoint over the augmented field
+ *     ORC_AUGADJ, with the same single-problem solver.
  *   - integration backward in time (t1 < t0): the same method with negative
  *     steps; the controller acts on |h|, evaluation points run from t0 down
  *     to t1 (a reading: the paper only uses forward integration).
@@ -231,7 +236,7 @@ void orc_tableau(double *c, double *a, double *b, double *bhat, double *q) {
 /* ------------------------------------------------------------------------ */
 /* Problem description.                                                      */
 /* ------------------------------------------------------------------------ */
-enum { ORC_VDP = 1, ORC_LINEAR = 2, ORC_MLP = 3, ORC_STACKED = 4 };
+enum { ORC_VDP = 1, ORC_LINEAR = 2, ORC_MLP = 3, ORC_STACKED = 4, ORC_AUGADJ = 5 };
 enum { ST_SUCCESS = 0, ST_MAX_STEPS = 1, ST_DT_UNDERFLOW = 2, ST_NONFINITE = 3,
        ST_INVALID_INPUT = 4, ST_RUNNING = -1 };
 
@@ -252,6 +257,9 @@ typedef struct orc_field_s {
    * instance b of the inner field. */
   const struct orc_field_s *inner;
   int n_inner;
+  /* ORC_AUGADJ: the augmented adjoint system of n_inner instances of the MLP
+   * field `inner` (orc_joint_adjoint builds it; scr is its scratch) */
+  double *scr;
 } orc_field;
 
 typedef struct {
@@ -327,10 +335,14 @@ typedef struct {
   long nfe;     /* evaluations */
 } fctx;
 
+static void aug_eval(const orc_field *F, double t, const double *z, double *out);
+
 static void feval(fctx *c, double t, const double *y, double *out) {
   const orc_field *F = c->F;
   c->nfe++;
-  if (F->kind == ORC_VDP) {
+  if (F->kind == ORC_AUGADJ) {
+    aug_eval(F, t, y, out);
+  } else if (F->kind == ORC_VDP) {
     f_vdp(F->mu[c->i], y, out);
   } else if (F->kind == ORC_LINEAR) {
     f_linear(F->A + (size_t)c->i * F->D * F->D, F->D, y, out);
@@ -1027,6 +1039,42 @@ static size_t mlp_params(const orc_field *F, size_t *nb) {
   return w;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Joint continuous adjoint (App. A, CNF benchmark: the "torchode-joint"    */
+/* backward pass, one adjoint equation of size bf + p for the whole batch). */
+/* ------------------------------------------------------------------------ */
+/* The augmented system of B instances of the MLP field M sharing its
+ * parameters theta: z = [y (B x D); a (B x D); abar (P)] with
+ *   dy/dt = f(t, y_b),  da_b/dt = -J_f(t, y_b)^T a_b,
+ *   dabar/dt = -sum_b (df/dtheta)(t, y_b)^T a_b,
+ * abar laid out as the weights then the biases, layer by layer (W[l] row
+ * major).  One problem of size 2BD + P. */
+static void aug_eval(const orc_field *F, double t, const double *z, double *out) {
+  const orc_field *M = F->inner;
+  const int B = F->n_inner, D = M->D;
+  size_t nb;
+  const size_t nw = mlp_params(M, &nb);
+  int acts = 0;
+  for (int l = 0; l < M->n_layers; ++l) acts += M->widths[l];
+  const int maxw = mlp_max_width(M);
+  double *act = F->scr, *dscr = act + acts + 8, *gy = dscr + 2 * maxw + 8;
+  const double *y = z, *a = z + (size_t)B * D;
+  double *oy = out, *oa = out + (size_t)B * D, *ow = out + 2 * (size_t)B * D, *ob = ow + nw;
+  for (size_t p = 0; p < nw + nb; ++p) ow[p] = 0.0;
+  job Jm;
+  memset(&Jm, 0, sizeof(Jm));
+  Jm.F = M;
+  for (int b = 0; b < B; ++b) {
+    const double *yb = y + (size_t)b * D, *ab = a + (size_t)b * D;
+    f_mlp(M, t, yb, oy + (size_t)b * D, act);
+    for (int j = 0; j < D; ++j) gy[j] = 0.0;
+    /* gy = J^T a_b; the parameter cotangents summed into ow, ob in b order */
+    vjp(&Jm, 0, t, yb, ab, gy, NULL, ow, ob, act, dscr, NULL);
+    for (int j = 0; j < D; ++j) oa[(size_t)b * D + j] = -gy[j];
+  }
+  for (size_t p = 0; p < nw + nb; ++p) ow[p] = -ow[p];
+}
+
 static void *worker(void *p) {
   worker_arg *a = (worker_arg *)p;
   const job *J = a->J;
@@ -1257,4 +1305,107 @@ int orc_adjoint_tm(int method, const orc_field *F, int B, const double *y0, cons
   free(ye_dummy);
   free(yf_dummy);
   return used;
+}
+
+/* Joint continuous adjoint of B instances of the MLP field M over a shared
+ * time axis (App. A, CNF benchmark): the augmented system of aug_eval
+ * integrated backward from t1 to t0 as ONE problem -- one step size, one
+ * RMS error norm over all 2BD + P components, one accept/reject decision
+ * (the joint semantics of Sec. 4.1), with the pair, controller and
+ * starting-step heuristic of orc_solve.  Start: y = y1 (the forward's
+ * y(t1)), a = gy_final plus the cotangents of evaluation points at t1,
+ * abar = 0.  The integration stops at every evaluation point strictly
+ * inside (t0, t1), adds that point's cotangent to a (the loss jumps there),
+ * and restarts (a new starting step); points at t0 add to a at the end.
+ * Outputs: gy0 = a(t0) (dL/dy0), gW/gb = abar(t0) (dL/dtheta), y0_rec =
+ * y(t0) (the state integrated back), stats = {accepted, rejected,
+ * augmented-field evaluations, status} over all segments (status: the
+ * first failure, else success).  t_eval [K] is shared and ordered from t0
+ * to t1 (t0 < t1).  Returns -1 for an invalid call. */
+int orc_joint_adjoint(const orc_field *M, const orc_opts *O, int B, const double *y1, double t0,
+                      double t1, const double *t_eval, int K, const double *gy_eval,
+                      const double *gy_final, double *gy0, double *const *gW, double *const *gb,
+                      double *y0_rec, int32_t *stats) {
+  if (!M || M->kind != ORC_MLP || B < 1 || !(t0 < t1) || K < 0) return -1;
+  for (int k = 0; k < K; ++k)
+    if (!(t_eval[k] >= t0 && t_eval[k] <= t1) || (k > 0 && t_eval[k] < t_eval[k - 1])) return -1;
+  const int D = M->D;
+  size_t nb;
+  const size_t nw = mlp_params(M, &nb);
+  const size_t BD = (size_t)B * D, N = 2 * BD + nw + nb;
+  int acts = 0;
+  for (int l = 0; l < M->n_layers; ++l) acts += M->widths[l];
+  orc_field A;
+  memset(&A, 0, sizeof(A));
+  A.kind = ORC_AUGADJ;
+  A.D = (int)N;
+  A.inner = M;
+  A.n_inner = B;
+  A.scr = (double *)malloc(sizeof(double) * (size_t)(acts + 3 * mlp_max_width(M) + D + 32));
+  double *z = (double *)malloc(sizeof(double) * N), *z2 = (double *)malloc(sizeof(double) * N);
+  for (size_t j = 0; j < BD; ++j) {
+    z[j] = y1[j];
+    z[BD + j] = gy_final ? gy_final[j] : 0.0;
+  }
+  for (size_t p = 2 * BD; p < N; ++p) z[p] = 0.0;
+  orc_opts o = *O;
+  o.rtol_b = o.atol_b = NULL;
+  /* cotangent of the points at index k added to a */
+  int k = K - 1;
+  while (k >= 0 && t_eval[k] == t1) {
+    if (gy_eval)
+      for (int b = 0; b < B; ++b)
+        for (int j = 0; j < D; ++j) z[BD + (size_t)b * D + j] += gy_eval[((size_t)b * K + k) * D + j];
+    k--;
+  }
+  int32_t n_acc = 0, n_rej = 0, n_fe = 0, status = ST_SUCCESS;
+  double start = t1;
+  while (1) {
+    const double end = (k >= 0 && t_eval[k] > t0) ? t_eval[k] : t0;
+    if (end != start) {
+      int32_t na = 0, nr = 0, nf = 0, st = 0;
+      orc_solve_yp(&A, &o, 1, z, &start, &end, NULL, 0, NULL, NULL, z2, &na, &nr, &nf, &st, NULL,
+                   1);
+      n_acc += na;
+      n_rej += nr;
+      n_fe += nf;
+      if (st != ST_SUCCESS) {
+        status = st;
+        memcpy(z, z2, sizeof(double) * N);
+        break;
+      }
+      memcpy(z, z2, sizeof(double) * N);
+    }
+    while (k >= 0 && t_eval[k] == end) {
+      if (gy_eval)
+        for (int b = 0; b < B; ++b)
+          for (int j = 0; j < D; ++j)
+            z[BD + (size_t)b * D + j] += gy_eval[((size_t)b * K + k) * D + j];
+      k--;
+    }
+    start = end;
+    if (end == t0) break;
+  }
+  for (size_t j = 0; j < BD; ++j) {
+    gy0[j] = z[BD + j];
+    if (y0_rec) y0_rec[j] = z[j];
+  }
+  size_t off = 2 * BD;
+  for (int l = 0; l < M->n_layers; ++l) {
+    const size_t n = (size_t)M->widths[l] * M->widths[l + 1];
+    for (size_t q = 0; q < n; ++q) gW[l][q] = z[off + q];
+    off += n;
+  }
+  for (int l = 0; l < M->n_layers; ++l) {
+    for (int q = 0; q < M->widths[l + 1]; ++q) gb[l][q] = z[off + q];
+    off += M->widths[l + 1];
+  }
+  stats[0] = n_acc;
+  stats[1] = n_rej;
+  stats[2] = n_fe;
+  stats[3] = status;
+  free(A.scr);
+  free(z);
+  free(z2);
+  return 0;
 }
