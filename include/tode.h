@@ -349,6 +349,42 @@ tode_err tode_t_bounds_grad(const tode_field_desc* f, const tode_options* o, con
                             const void* gy_final, const void* yp_eval, double* g_t0,
                             double* g_t1, void* stream);
 
+/* Joint continuous adjoint (App. A, the CNF benchmark's "torchode-joint"
+ * backward pass): the adjoint equation of the whole batch solved as ONE
+ * problem of size 2BD + P -- the state integrated back from y(t1), its
+ * adjoint a and the adjoint of the P shared network parameters,
+ *   dy/dt = f(t, y_b),  da_b/dt = -J_f(t, y_b)^T a_b,
+ *   dabar/dt = -sum_b (df/dtheta)(t, y_b)^T a_b,
+ * integrated backward from t1 to t0 by dopri5 with one step size, one RMS
+ * error norm over all 2BD + P components (scale atol + rtol max(|z|,
+ * |z1|)) and one accept/reject decision, the controller of tode_options and
+ * the starting-step heuristic with its norms over the whole system.  The
+ * integration stops at every evaluation point strictly inside (t0, t1) and
+ * adds that point's cotangent to a (the loss jumps there); points at t1
+ * start a, points at t0 add at the end.  The MLP field of the D = 32, H =
+ * 128 network (TODE_EUNSUPPORTED otherwise), prec TODE_BF16W_SPLIT, scalar
+ * tolerances, TODE_DOPRI5; t0 < t1 shared by the batch (host doubles),
+ * t_eval [K] host, shared, ordered from t0 to t1.
+ *   y1 [B][D] float (device): y(t1) from the forward solve.
+ *   gy_eval [B][K][D], gy_final [B][D] (device float, NULL = 0).
+ *   gy0 [B][D] (device float, written): dL/dy0 = a(t0).
+ *   gW[l], gb[l] (device float, written): dL/dtheta = abar(t0), shaped like
+ *     the field's W[l] ([out][in]) and b[l].
+ *   y0 [B][D] (device float, written; may be NULL): y integrated back to t0.
+ *   stats (host int32 [4], written): accepted and rejected steps and
+ *     augmented evaluations over all segments, and the status
+ *     (TODE_S_SUCCESS or the first failure).
+ * workspace: tode_joint_adjoint_workspace_size bytes, 256-byte aligned.
+ * Synchronous: the host reads the decision every few attempts; enqueued on
+ * stream, returns when the result is there.  TODE_ETIMEOUT if a tensor-core
+ * wait gave up. */
+size_t tode_joint_adjoint_workspace_size(const tode_field_desc* f, const tode_options* o);
+tode_err tode_joint_adjoint(const tode_field_desc* f, const tode_options* o, double t0, double t1,
+                            const double* t_eval, int K, const void* y1, const void* gy_eval,
+                            const void* gy_final, void* gy0, float* const* gW, float* const* gb,
+                            void* y0, int32_t* stats, void* workspace, size_t ws_bytes,
+                            void* stream);
+
 /* The MLP field's tensor-core building block on its own, for checking the
  * operand layouts and tensor-memory conventions against a plain product:
  * C[M][N] = sum_k A(m,k) B(n,k) with A, B BF16 (uint16 bit patterns) and C

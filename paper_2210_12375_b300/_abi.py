@@ -23,6 +23,7 @@ STATUS = {"SUCCESS": 0, "MAX_STEPS": 1, "DT_UNDERFLOW": 2, "NONFINITE": 3, "INVA
 # entry points include/tode.h declares
 EXPORTS = ("tode_version", "tode_strerror", "tode_default_options", "tode_workspace_size",
            "tode_solve", "tode_adjoint_scratch_size", "tode_adjoint", "tode_adjoint_static",
+           "tode_joint_adjoint_workspace_size", "tode_joint_adjoint",
            "tode_tc_gemm", "tode_t_eval_grad", "tode_peak_kernel",
            "tode_t_bounds_grad")
 TODE_STATIC_ADJOINT_SCRATCH_BYTES = 32 << 20
@@ -137,6 +138,13 @@ def load(path: str = LIB_PATH):
     lib.tode_adjoint.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), _vp, _vp, _vp, C.c_int,
                                  _vp, _vp, C.POINTER(Tape), _vp, _vp, _vp, _vp,
                                  C.POINTER(_vp), C.POINTER(_vp), _vp, _vp, C.c_size_t, _vp]
+    lib.tode_joint_adjoint_workspace_size.restype = C.c_size_t
+    lib.tode_joint_adjoint_workspace_size.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options)]
+    lib.tode_joint_adjoint.restype = C.c_int
+    lib.tode_joint_adjoint.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), C.c_double,
+                                       C.c_double, C.POINTER(C.c_double), C.c_int, _vp, _vp, _vp,
+                                       _vp, _vp, _vp, _vp, C.POINTER(C.c_int32), _vp, C.c_size_t,
+                                       _vp]
     lib.tode_adjoint_static.restype = C.c_int
     lib.tode_adjoint_static.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), _vp, _vp, _vp,
                                         C.c_int, _vp, _vp, C.POINTER(Tape), _vp, _vp, _vp, _vp,

@@ -11,6 +11,7 @@ import ctypes as C
 from dataclasses import dataclass, field as dc_field
 from typing import Optional
 
+import numpy as np
 import torch
 
 from . import _abi
@@ -347,6 +348,54 @@ def adjoint(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=Non
         _ptr(overflow), _ptr(scratch), C.c_size_t(scratch.numel()), _stream_handle(stream))
     _abi.check(code, "tode_adjoint")
     return gy0, gparam, overflow
+
+
+def joint_adjoint(field, y1: torch.Tensor, t0: float, t1: float, t_eval=None, gy_eval=None,
+                  gy_final=None, *, stream=None, workspace: Optional[torch.Tensor] = None,
+                  **opt_kw):
+    """Joint continuous adjoint (App. A, the CNF benchmark's "torchode-joint"
+    backward pass): the adjoint equation of the whole batch -- the state
+    integrated back from y1 = y(t1), its adjoint and the adjoint of the
+    shared parameters -- solved backward from t1 to t0 as one problem with
+    one step size and one error norm, stopping at every evaluation point for
+    its cotangent.  ``field``: the MLP field (D = 32, H = 128, split);
+    ``t0 < t1`` shared floats; ``t_eval`` a [K] sequence shared by the batch
+    (host values); ``gy_eval`` [B, K, D], ``gy_final`` [B, D] float on the
+    device.  Returns (gy0 [B, D], (gW, gb) lists, y0 [B, D] integrated back,
+    stats dict with n_acc, n_rej, n_feval, status)."""
+    lib = _abi.load()
+    if not isinstance(field, MLP):
+        raise _abi.TodeError(_abi.TODE_EUNSUPPORTED, "tode_joint_adjoint")
+    B, D = y1.shape
+    dev = y1.device
+    te = np.ascontiguousarray(np.zeros(0) if t_eval is None else
+                              (t_eval.detach().cpu().numpy() if torch.is_tensor(t_eval)
+                               else np.asarray(t_eval)), dtype=np.float64).reshape(-1)
+    K = te.shape[0]
+    opts = make_options(prec=_prec_of(field, y1), **opt_kw)
+    keep = []
+    fd = field.desc(B, D, keep)
+    nb = lib.tode_joint_adjoint_workspace_size(C.byref(fd), C.byref(opts))
+    if nb == 0 and B > 0:
+        raise _abi.TodeError(_abi.TODE_EUNSUPPORTED, "tode_joint_adjoint_workspace_size")
+    if workspace is None or workspace.numel() < nb:
+        workspace = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+    gy0 = torch.empty((B, D), dtype=torch.float32, device=dev)
+    y0 = torch.empty((B, D), dtype=torch.float32, device=dev)
+    gW = [torch.empty(w.shape, dtype=torch.float32, device=dev) for w in field.W]
+    gb = [torch.empty(b.shape, dtype=torch.float32, device=dev) for b in field.b]
+    gW_arr = (C.c_void_p * len(gW))(*[g.data_ptr() for g in gW])
+    gb_arr = (C.c_void_p * len(gb))(*[g.data_ptr() for g in gb])
+    stats = (C.c_int32 * 4)()
+    y1c = y1.contiguous()
+    code = lib.tode_joint_adjoint(
+        C.byref(fd), C.byref(opts), C.c_double(float(t0)), C.c_double(float(t1)),
+        te.ctypes.data_as(C.POINTER(C.c_double)) if K > 0 else None, int(K), _ptr(y1c),
+        _ptr(gy_eval), _ptr(gy_final), _ptr(gy0), gW_arr, gb_arr, _ptr(y0), stats,
+        _ptr(workspace), C.c_size_t(workspace.numel()), _stream_handle(stream))
+    _abi.check(code, "tode_joint_adjoint")
+    return gy0, (gW, gb), y0, dict(n_acc=stats[0], n_rej=stats[1], n_feval=stats[2],
+                                   status=stats[3])
 
 
 def t_bounds_grad(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=None,

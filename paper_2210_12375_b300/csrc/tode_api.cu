@@ -266,6 +266,59 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
   return o->prec == TODE_F64 ? simt_adjoint_f64(r) : simt_adjoint_f32(r);
 }
 
+static bool jadj_ok(const tode_field_desc* f, const tode_options* o) {
+  return f->kind == TODE_MLP && o->prec == TODE_BF16W_SPLIT && !o->rtol_b && !o->atol_b &&
+         !o->joint;
+}
+
+size_t tode_joint_adjoint_workspace_size(const tode_field_desc* f, const tode_options* o) {
+  if (!opts_ok(o) || field_ok(f, o) != TODE_OK || !jadj_ok(f, o)) return 0;
+  return mlp_jadj_workspace_bytes(f);
+}
+
+tode_err tode_joint_adjoint(const tode_field_desc* f, const tode_options* o, double t0, double t1,
+                            const double* t_eval, int K, const void* y1, const void* gy_eval,
+                            const void* gy_final, void* gy0, float* const* gW, float* const* gb,
+                            void* y0, int32_t* stats, void* workspace, size_t ws_bytes,
+                            void* stream) {
+  if (!opts_ok(o) || K < 0 || !stats) return TODE_EINVAL;
+  tode_err e = field_ok(f, o);
+  if (e != TODE_OK) return e;
+  if (f->kind != TODE_MLP || o->prec != TODE_BF16W_SPLIT || o->joint) return TODE_EUNSUPPORTED;
+  if (o->rtol_b || o->atol_b) return TODE_EINVAL;
+  if (!std::isfinite(t0) || !std::isfinite(t1) || !(t0 < t1)) return TODE_EINVAL;
+  if (K > 0 && !t_eval) return TODE_EINVAL;
+  for (int q = 0; q < K; ++q)
+    if (!(t_eval[q] >= t0 && t_eval[q] <= t1) || (q > 0 && t_eval[q] < t_eval[q - 1]))
+      return TODE_EINVAL;
+  stats[0] = stats[1] = stats[2] = 0;
+  stats[3] = TODE_S_SUCCESS;
+  if (f->B == 0) return TODE_OK;
+  if (!y1 || !gy0 || !gW || !gW[0] || !gW[1] || !gW[2]) return TODE_EINVAL;
+  const size_t need = mlp_jadj_workspace_bytes(f);
+  if (need == 0) return TODE_EUNSUPPORTED;
+  if (!workspace || !aligned256(workspace) || ws_bytes < need) return TODE_EWORKSPACE;
+  JadjReq r{};
+  r.f = f;
+  r.o = o;
+  r.B = f->B;
+  r.K = K;
+  r.t0 = t0;
+  r.t1 = t1;
+  r.te = t_eval;
+  r.y1 = (const float*)y1;
+  r.gye = (const float*)gy_eval;
+  r.gyf = (const float*)gy_final;
+  r.gy0 = (float*)gy0;
+  r.y0 = (float*)y0;
+  r.gW = gW;
+  r.gb = gb;
+  r.stats = stats;
+  r.ws = (char*)workspace;
+  r.stream = (cudaStream_t)stream;
+  return mlp_joint_adjoint(r);
+}
+
 tode_err tode_t_bounds_grad(const tode_field_desc* f, const tode_options* o, const double* t0,
                             const double* t1, const double* t_eval, int K, const int32_t* n_acc,
                             const int32_t* status, const tode_tape* tape, const void* gy_eval,

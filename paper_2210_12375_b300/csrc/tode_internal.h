@@ -122,6 +122,26 @@ tode_err simt_t_bounds_f64(const AdjReq& r, const void* yp, double* gt0, double*
 tode_err simt_t_bounds_f32(const AdjReq& r, const void* yp, double* gt0, double* gt1);
 // the same for the tsit5 pair (tode_simt_ts5_f64.cu, tode_simt_ts5_f32.cu);
 // the functions above hand over to these when o->method is TODE_TSIT5
+// the joint continuous adjoint of the MLP field (tode_mlp.cu)
+struct JadjReq {
+  const tode_field_desc* f;
+  const tode_options* o;
+  int B, K;
+  double t0, t1;
+  const double* te;  // host [K]
+  const float* y1;
+  const float* gye;
+  const float* gyf;
+  float* gy0;
+  float* y0;
+  float* const* gW;
+  float* const* gb;
+  int32_t* stats;  // host [4]
+  char* ws;
+  cudaStream_t stream;
+};
+size_t mlp_jadj_workspace_bytes(const tode_field_desc* f);
+tode_err mlp_joint_adjoint(const JadjReq& r);
 tode_err simt_solve_ts5_f64(const SolveReq& r);
 tode_err simt_solve_ts5_f32(const SolveReq& r);
 tode_err simt_adjoint_ts5_f64(const AdjReq& r);

@@ -2701,6 +2701,831 @@ __global__ void k_mlp_grad_reduce(const float* part, int grid, float* gW0, float
   if (k < D && gb2) gb2[k] = sum(L::P_B2 + k);
 }
 
+// ======================================================================
+// Joint continuous adjoint of the D = 32, H = 128 MLP field (App. A, the
+// CNF benchmark's "torchode-joint" backward pass): ONE adjoint equation for
+// the whole batch, of size 2BD + P -- the state integrated back, its
+// adjoint and the adjoint of the shared parameters -- solved backward from
+// t1 to t0 with one step size, one RMS error norm over all its components
+// and one accept/reject decision (the joint semantics of Sec. 4.1), by
+// dopri5 with the solver's controller and starting-step heuristic:
+//   dy/dt = f(t, y_b),  da_b/dt = -J_f(t, y_b)^T a_b,
+//   dabar/dt = -G,  G = sum_b (df/dtheta)(t, y_b)^T a_b.
+// A stage of a row is one augmented evaluation: the hidden layers and the
+// output layer at [Y; t] (k_y = f), then the transposed chain with the
+// cotangent A (k_a = -J^T A) and the tile's weight products, its part of G,
+// in tensor memory (the round of k_mlp_adjoint with a fresh accumulator per
+// stage).  A row owns its y and a; abar is one vector of P values.
+//
+// Per attempt two launches: k_mlp_jadj (128-row tiles; six stages; each
+// CTA adds its stages' parts of G, weighted by -h b_i and -h e_i, into its
+// own slots, and writes its rows' candidate and squared scaled errors) and
+// k_mlp_jadj_decide (per parameter: the CTAs' slots summed in CTA order,
+// abar's candidate and error; its last CTA -- a ticket, no CTA waits for
+// another -- sums every partial in order, decides and runs the controller).
+// The launches after an accepted attempt commit its candidate (rows: y, a,
+// k7 as the next k1; abar: the vector and its k7).  Two launch pairs before
+// the first attempt of a segment take the starting step.
+// ======================================================================
+enum : int { JA_EVAL = 0, JA_PROBE = 1, JA_STEP = 2 };
+
+struct JadjCtl {
+  double t, t_end;       // time (decreasing: backward) and the segment's end
+  double h, h_use;       // proposed step (> 0) and the next attempt's, clipped at t_end
+  double h0, d1;         // the starting-step heuristic between its launches
+  double err_prev, err_prev2;
+  int use_last, n_acc, n_rej, n_fe, status, pending, prev_rej;
+  unsigned int ticket;
+};
+
+struct JadjArgs {
+  int B;
+  const unsigned char* wimg;
+  const float* bias[3];
+  float *y, *a, *yc, *ac;  // [B][D]: state and the attempt's candidate
+  float* kst;              // [7][B][2D]: stage derivatives [k_y | k_a]; slot 0 = k1
+  float* gpart;            // [grid][3][P]: each CTA's slots U, E, F
+  double* epart;           // [grid][2]: the rows' squared scaled sums
+  double *th, *thc, *kth1, *fsum;  // [P]: abar, its candidate, its k1, the candidate's k7
+  double* dpart;           // [decide grid][2]
+  JadjCtl* ctl;
+  double rtol, atol, safety, fac_min, fac_max, beta1, beta2, beta3, nnorm;
+  int max_steps;
+  int32_t* err;
+};
+
+// The parameter vector's padding entries (input columns past [y; t; 1] of
+// the first layer) are not part of the problem: no norm term.
+template <class L> __host__ __device__ constexpr bool jadj_real(int p) {
+  return !(p < L::P_W1 && (p % L::K0) >= L::D + 2);
+}
+
+template <class Cfg>
+__global__ void __launch_bounds__(256, 1) k_mlp_jadj(JadjArgs a, int mode) {
+  using L = MlpAdjLayout<Cfg>;
+  using Tb = DP5;
+  constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, HC = Cfg::HC;
+  constexpr int P = L::P_FLOATS;
+  const JadjCtl c = *a.ctl;
+  if (c.status != ST_RUNNING) return;  // block-uniform: the segment is over
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar_mma, mbar_w;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  __shared__ double red[8];
+  unsigned char* sW = sm + L::S_W;
+  unsigned char* sXh = sm + L::S_XH;
+  unsigned char* sXl = sm + L::S_XL;
+  unsigned char* sH1h = sm + L::S_H1H;
+  unsigned char* sH1l = sm + L::S_H1L;
+  unsigned char* sH2h = sm + L::S_H2H;
+  unsigned char* sH2l = sm + L::S_H2L;
+  unsigned char* sD3h = sm + L::S_D3H;
+  unsigned char* sD3l = sm + L::S_D3L;
+  unsigned char* sOnes = sm + L::S_ONES;
+  float* sBias = reinterpret_cast<float*>(sm + L::S_BIAS);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & 127, half = tid >> 7;
+  const int coff = half * C;
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const int inst = blockIdx.x * 128 + row;
+  const bool live = inst < a.B;
+
+  if (tid == 0) {
+    tc::mbar_init(&mbar_mma, 1);
+    tc::mbar_init(&mbar_w, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    tc::mbar_expect_tx(&mbar_w, (uint32_t)Cfg::WIMG_BYTES);
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      tc::bulk_g2s(sW + Cfg::W_off(l), a.wimg + Cfg::W_off(l), (uint32_t)Cfg::W_bytes(l), &mbar_w);
+  }
+  {
+    int o = 0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const int n = Cfg::N_of(l);
+      for (int j = tid; j < n; j += 256) sBias[o + j] = a.bias[l] ? a.bias[l][j] : 0.0f;
+      o += n;
+    }
+  }
+  for (int j = tid; j < 128 * K0 * 2 / 16; j += 256) {
+    reinterpret_cast<uint4*>(sXh)[j] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(sXl)[j] = make_uint4(0, 0, 0, 0);
+  }
+  for (int j = tid; j < 128 * 16; j += 256) {
+    const int r = j / 16, cc = j % 16;
+    *reinterpret_cast<__nv_bfloat16*>(sOnes + tc::cm_offset(r, cc, 16)) =
+        __float2bfloat16_rn(cc == 0 ? 1.0f : 0.0f);
+  }
+  __syncthreads();
+  if (tid < 128)
+    *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(tid, D + 1, K0)) =
+        __float2bfloat16_rn(1.0f);
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base_s, L::T_COLS);
+    tc::tmem_relinquish();
+  }
+  if (!tc::mbar_wait(&mbar_w, 0)) atomicExch(&abort_s, 1);
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tmem_base_s;
+  const uint32_t tl = tbase + lane_base;
+  uint32_t parity = 0;
+
+  // ---- this thread's components of its row: commit, then load
+  const size_t BD = (size_t)a.B * D, KS = 2 * BD;  // KS: floats per stage slot
+  const size_t ro = (size_t)inst * D + coff;       // y / a offset
+  const size_t ko = (size_t)inst * 2 * D + coff;   // slot offset (y part; a part at +D)
+  auto ld16 = [&](const float* p, float (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 u = reinterpret_cast<const float4*>(p)[q];
+      v[4 * q] = u.x, v[4 * q + 1] = u.y, v[4 * q + 2] = u.z, v[4 * q + 3] = u.w;
+    }
+  };
+  auto st16 = [&](float* p, const float (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  };
+  float y[16], av[16];
+  if (live) {
+    if (mode == JA_STEP && c.pending) {  // the previous attempt was accepted
+      float v[16];
+      ld16(a.yc + ro, v);
+      st16(a.y + ro, v);
+      ld16(a.ac + ro, v);
+      st16(a.a + ro, v);
+      ld16(a.kst + 6 * KS + ko, v);
+      st16(a.kst + ko, v);
+      ld16(a.kst + 6 * KS + ko + D, v);
+      st16(a.kst + ko + D, v);
+    }
+    ld16(a.y + ro, y);
+    ld16(a.a + ro, av);
+  } else {
+#pragma unroll
+    for (int r = 0; r < C; ++r) y[r] = av[r] = 0.0f;
+  }
+
+  auto barrier = [&]() {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  auto wait_mma = [&]() {
+    if (!tc::mbar_wait(&mbar_mma, parity)) atomicExch(&abort_s, 1);
+    parity ^= 1u;
+    tc::fence_after_sync();
+  };
+  auto hidden_epi = [&](const float* bl, unsigned char* th, unsigned char* tlo) {
+#pragma unroll
+    for (int c0 = 0; c0 < HC; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tl + L::T_R + half * HC + c0, v);
+      tc::tmem_wait_ld();
+      const int col = half * HC + c0;
+      const float4* b4 = reinterpret_cast<const float4*>(bl + col);
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 bq = b4[q4];
+        const float2 t0 = tanh_acc2(__fadd2_rn(make_float2(v[4 * q4], v[4 * q4 + 1]),
+                                               make_float2(bq.x, bq.y)));
+        const float2 t1 = tanh_acc2(__fadd2_rn(make_float2(v[4 * q4 + 2], v[4 * q4 + 3]),
+                                               make_float2(bq.z, bq.w)));
+        v[4 * q4] = t0.x, v[4 * q4 + 1] = t0.y;
+        v[4 * q4 + 2] = t1.x, v[4 * q4 + 3] = t1.y;
+      }
+      store_row16<true>(th, tlo, row, col, H, v);
+    }
+  };
+  auto delta_epi = [&](unsigned char* th, unsigned char* tlo) {
+#pragma unroll
+    for (int c0 = 0; c0 < HC; c0 += 16) {
+      const int col = half * HC + c0;
+      float v[16];
+      tc::tmem_ld16(tl + L::T_R + col, v);
+#pragma unroll
+      for (int c8 = 0; c8 < 2; ++c8) {
+        const uint32_t off = tc::cm_offset(row, col + 8 * c8, H);
+        const uint4 hv = *reinterpret_cast<const uint4*>(th + off);
+        const uint4 lv = *reinterpret_cast<const uint4*>(tlo + off);
+        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hw[j]);
+          const __nv_bfloat162 l2 = *reinterpret_cast<const __nv_bfloat162*>(&lw[j]);
+          const float2 x = __fadd2_rn(make_float2(__low2float(h2), __high2float(h2)),
+                                      make_float2(__low2float(l2), __high2float(l2)));
+          const float2 g = __ffma2_rn(make_float2(-x.x, -x.y), x, make_float2(1.0f, 1.0f));
+          const float2 d = __fmul2_rn(make_float2(v[8 * c8 + 2 * j], v[8 * c8 + 2 * j + 1]), g);
+          v[8 * c8 + 2 * j] = d.x;
+          v[8 * c8 + 2 * j + 1] = d.y;
+        }
+      }
+      store_row16<true>(th, tlo, row, col, H, v);
+    }
+  };
+  const uint32_t idH = tc::idesc_bf16_f32(128, H);
+
+  // ---- the stages of this launch
+  float* S = a.gpart + (size_t)blockIdx.x * 3 * P;  // this CTA's slots U, E, F
+  bool u_init = false, e_init = false, f_init = false;
+  float Udb[16], Edb[16], Fdb[16];  // the output bias's part of G: sum over rows of A
+#pragma unroll
+  for (int r = 0; r < C; ++r) Udb[r] = Edb[r] = Fdb[r] = 0.0f;
+  const double hsd = mode == JA_STEP ? -c.h_use : -c.h0;  // negative: backward in time
+  const float hs = (float)hsd;
+  const int nst = mode == JA_STEP ? 6 : 1;
+  float sq0 = 0.0f, sq1 = 0.0f;  // this thread's squared scaled terms
+#pragma unroll 1
+  for (int st = 0; st < nst; ++st) {
+    const int i = mode == JA_STEP ? st + 2 : 1;  // the tableau's stage
+    const int slot = mode == JA_STEP ? i - 1 : (mode == JA_EVAL ? 0 : 1);
+    float Y[16], A[16];
+    double tin = c.t;
+    if (live && mode == JA_PROBE) {
+      float k0[16];
+      ld16(a.kst + ko, k0);
+#pragma unroll
+      for (int r = 0; r < C; ++r) Y[r] = madd(hs, k0[r], y[r]);
+      ld16(a.kst + ko + D, k0);
+#pragma unroll
+      for (int r = 0; r < C; ++r) A[r] = madd(hs, k0[r], av[r]);
+      tin = c.t + hsd;
+    } else if (live && mode == JA_STEP) {
+      // Y_i = y + h (a_i1 k_1 + ... + a_i,i-1 k_i-1), the same for A
+      float sy[16], sa[16], kk[16];
+#pragma unroll
+      for (int r = 0; r < C; ++r) sy[r] = sa[r] = 0.0f;
+      for (int l = 1; l < i; ++l) {
+        const float al = (float)Tb::a(i, l);
+        if (al == 0.0f) continue;
+        ld16(a.kst + (size_t)(l - 1) * KS + ko, kk);
+#pragma unroll
+        for (int r = 0; r < C; ++r) sy[r] = madd(al, kk[r], sy[r]);
+        ld16(a.kst + (size_t)(l - 1) * KS + ko + D, kk);
+#pragma unroll
+        for (int r = 0; r < C; ++r) sa[r] = madd(al, kk[r], sa[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        Y[r] = madd(hs, sy[r], y[r]);
+        A[r] = madd(hs, sa[r], av[r]);
+      }
+      tin = c.t + Tb::c(i) * hsd;
+      if (i == 7) {  // SSAL: the last stage input is the candidate
+        st16(a.yc + ro, Y);
+        st16(a.ac + ro, A);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        Y[r] = live ? y[r] : 0.0f;
+        A[r] = live ? av[r] : 0.0f;
+      }
+    }
+    store_row16<true>(sXh, sXl, row, coff, K0, Y);
+    store_row16<true>(sD3h, sD3l, row, coff, D, A);
+    if (half == 1) {
+      const float tf = live ? (float)tin : 0.0f;
+      const __nv_bfloat16 th = __float2bfloat16_rn(tf);
+      const __nv_bfloat16 tlo = __float2bfloat16_rn(tf - __bfloat162float(th));
+      *reinterpret_cast<__nv_bfloat16*>(sXh + tc::cm_offset(row, D, K0)) = th;
+      *reinterpret_cast<__nv_bfloat16*>(sXl + tc::cm_offset(row, D, K0)) = tlo;
+    }
+    barrier();
+
+    // F0, F1: the hidden layers at [Y; t]
+    if (tid == 0) {
+      const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(0));
+      for (int kk = 0; kk < K0 / 16; ++kk) {
+        const uint64_t db = tc::smem_desc(wa + kk * 256, 128, K0 * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sXh) + kk * 256, 128, K0 * 16), db,
+                     idH, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sXl) + kk * 256, 128, K0 * 16), db,
+                     idH, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    hidden_epi(sBias, sH1h, sH1l);
+    barrier();
+    if (tid == 0) {
+      const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(1));
+      for (int kk = 0; kk < H / 16; ++kk) {
+        const uint64_t db = tc::smem_desc(wa + kk * 256, 128, H * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH1h) + kk * 256, 128, H * 16), db,
+                     idH, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH1l) + kk * 256, 128, H * 16), db,
+                     idH, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    hidden_epi(sBias + H, sH2h, sH2l);
+    barrier();
+    // F2: the output layer, k_y = h2 W3^T + b3
+    float ky[16], ka[16];
+    if (tid == 0) {
+      const uint32_t wa = tc::smem_u32(sW + Cfg::W_off(2));
+      const uint32_t idD = tc::idesc_bf16_f32(128, D);
+      for (int kk = 0; kk < H / 16; ++kk) {
+        const uint64_t db = tc::smem_desc(wa + kk * 256, 128, H * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2h) + kk * 256, 128, H * 16), db,
+                     idD, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(tc::smem_u32(sH2l) + kk * 256, 128, H * 16), db,
+                     idD, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    tc::tmem_ld16(tl + L::T_R + coff, ky);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int r = 0; r < C; ++r) ky[r] += sBias[2 * H + coff + r];
+    barrier();  // every lane's output read before B2 overwrites the accumulator
+    // B2: acc = A W3;  G_W3^T = h2^T A  (split operands: hi*hi + lo*hi + hi*lo)
+    if (tid == 0) {
+      const uint32_t w3 = tc::smem_u32(sW + Cfg::W_off(2));
+      const uint32_t dh = tc::smem_u32(sD3h), dl = tc::smem_u32(sD3l);
+      const uint32_t idR = tc::idesc_bf16_f32(128, H, false, true);
+      for (int kk = 0; kk < D / 16; ++kk) {
+        const uint64_t db = tc::smem_desc_mn(w3 + kk * 2 * (H * 16), H * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, D * 16), db, idR, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, D * 16), db, idR, true);
+      }
+      const uint32_t idT = tc::idesc_bf16_f32(128, D, true, true);
+      const uint32_t hh = tc::smem_u32(sH2h), hl = tc::smem_u32(sH2l);
+      for (int kk = 0; kk < 128 / 16; ++kk) {
+        const uint64_t bh = tc::smem_desc_mn(dh + kk * 2 * (D * 16), D * 16);
+        const uint64_t bl = tc::smem_desc_mn(dl + kk * 2 * (D * 16), D * 16);
+        const uint64_t ah = tc::smem_desc_mn(hh + kk * 2 * (H * 16), H * 16);
+        const uint64_t al = tc::smem_desc_mn(hl + kk * 2 * (H * 16), H * 16);
+        tc::mma_bf16(tbase + L::T_D2, ah, bh, idT, kk > 0);
+        tc::mma_bf16(tbase + L::T_D2, al, bh, idT, true);
+        tc::mma_bf16(tbase + L::T_D2, ah, bl, idT, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    delta_epi(sH2h, sH2l);  // delta2 replaces h2
+    barrier();
+    // B1: acc = delta2 W2;  G_W2 = delta2^T h1;  G_b2 = delta2^T 1
+    if (tid == 0) {
+      const uint32_t w2 = tc::smem_u32(sW + Cfg::W_off(1));
+      const uint32_t dh = tc::smem_u32(sH2h), dl = tc::smem_u32(sH2l);
+      const uint32_t idR = tc::idesc_bf16_f32(128, H, false, true);
+      for (int kk = 0; kk < H / 16; ++kk) {
+        const uint64_t db = tc::smem_desc_mn(w2 + kk * 2 * (H * 16), H * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, H * 16), db, idR, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, H * 16), db, idR, true);
+      }
+      const uint32_t idT = tc::idesc_bf16_f32(128, H, true, true);
+      const uint32_t idB = tc::idesc_bf16_f32(128, 16, true, true);
+      const uint32_t hh = tc::smem_u32(sH1h), hl = tc::smem_u32(sH1l);
+      for (int kk = 0; kk < 128 / 16; ++kk) {
+        const uint64_t ah = tc::smem_desc_mn(dh + kk * 2 * (H * 16), H * 16);
+        const uint64_t al = tc::smem_desc_mn(dl + kk * 2 * (H * 16), H * 16);
+        const uint64_t bh = tc::smem_desc_mn(hh + kk * 2 * (H * 16), H * 16);
+        const uint64_t bl = tc::smem_desc_mn(hl + kk * 2 * (H * 16), H * 16);
+        const uint64_t b1 = tc::smem_desc_mn(tc::smem_u32(sOnes) + kk * 2 * (16 * 16), 16 * 16);
+        tc::mma_bf16(tbase + L::T_D1, ah, bh, idT, kk > 0);
+        tc::mma_bf16(tbase + L::T_D1, al, bh, idT, true);
+        tc::mma_bf16(tbase + L::T_D1, ah, bl, idT, true);
+        tc::mma_bf16(tbase + L::T_DB, ah, b1, idB, kk > 0);
+        tc::mma_bf16(tbase + L::T_DB, al, b1, idB, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    delta_epi(sH1h, sH1l);  // delta1 replaces h1
+    barrier();
+    // B0: acc = delta1 W1 (= J^T A, the t column too);  G_W1 = delta1^T [X | 1]
+    if (tid == 0) {
+      const uint32_t w1 = tc::smem_u32(sW + Cfg::W_off(0));
+      const uint32_t dh = tc::smem_u32(sH1h), dl = tc::smem_u32(sH1l);
+      const uint32_t idR = tc::idesc_bf16_f32(128, K0, false, true);
+      for (int kk = 0; kk < H / 16; ++kk) {
+        const uint64_t db = tc::smem_desc_mn(w1 + kk * 2 * (K0 * 16), K0 * 16);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dh + kk * 256, 128, H * 16), db, idR, kk > 0);
+        tc::mma_bf16(tbase + L::T_R, tc::smem_desc(dl + kk * 256, 128, H * 16), db, idR, true);
+      }
+      const uint32_t idT = tc::idesc_bf16_f32(128, K0, true, true);
+      const uint32_t xh = tc::smem_u32(sXh), xl = tc::smem_u32(sXl);
+      for (int kk = 0; kk < 128 / 16; ++kk) {
+        const uint64_t ah = tc::smem_desc_mn(dh + kk * 2 * (H * 16), H * 16);
+        const uint64_t al = tc::smem_desc_mn(dl + kk * 2 * (H * 16), H * 16);
+        const uint64_t bh = tc::smem_desc_mn(xh + kk * 2 * (K0 * 16), K0 * 16);
+        const uint64_t bl = tc::smem_desc_mn(xl + kk * 2 * (K0 * 16), K0 * 16);
+        tc::mma_bf16(tbase + L::T_D0, ah, bh, idT, kk > 0);
+        tc::mma_bf16(tbase + L::T_D0, al, bh, idT, true);
+        tc::mma_bf16(tbase + L::T_D0, ah, bl, idT, true);
+      }
+      tc::mma_commit(&mbar_mma);
+    }
+    wait_mma();
+    tc::tmem_ld16(tl + L::T_R + coff, ka);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int r = 0; r < C; ++r) ka[r] = -ka[r];  // k_a = -J^T A
+    if (live) {
+      st16(a.kst + (size_t)slot * KS + ko, ky);
+      st16(a.kst + (size_t)slot * KS + ko + D, ka);
+    }
+
+    // ---- this stage's part of G into the CTA's slots: U += (-h b_i) G,
+    // E += (-h e_i) G, F = -G (the stage whose k is a next k1 or a probe)
+    float wU = 0.0f, wE = 0.0f, wF = 0.0f;
+    if (mode == JA_STEP) {
+      wU = (float)(-hsd * Tb::b(i));
+      wE = (float)(-hsd * Tb::e(i));
+      if (i == 7) wF = -1.0f;
+    } else {
+      wF = -1.0f;
+    }
+    if (wU != 0.0f || wE != 0.0f || wF != 0.0f) {
+      auto rmw = [&](int idx, float v) {
+        if (wU != 0.0f) S[idx] = (u_init ? S[idx] : 0.0f) + wU * v;
+        if (wE != 0.0f) S[P + idx] = (e_init ? S[P + idx] : 0.0f) + wE * v;
+        if (wF != 0.0f) S[2 * P + idx] = wF * v;
+      };
+      float v[16];
+      // G_W1 (lane = hidden unit; its t and b1 columns included)
+      for (int cc = half * 32; cc < (half ? K0 : 32); cc += 16) {
+        tc::tmem_ld16(tl + L::T_D0 + cc, v);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) rmw(L::P_W0 + row * K0 + cc + j, v[j]);
+      }
+#pragma unroll 1
+      for (int cc = 0; cc < HC; cc += 16) {
+        const int col = half * HC + cc;
+        tc::tmem_ld16(tl + L::T_D1 + col, v);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) rmw(L::P_W1 + row * H + col + j, v[j]);
+      }
+      tc::tmem_ld16(tl + L::T_DB, v);
+      tc::tmem_wait_ld();
+      if (half == 0) rmw(L::P_B1 + row, v[0]);
+      tc::tmem_ld16(tl + L::T_D2 + coff, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) rmw(L::P_W2T + row * D + coff + j, v[j]);
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        Udb[r] = madd(wU, A[r], Udb[r]);
+        Edb[r] = madd(wE, A[r], Edb[r]);
+        if (wF != 0.0f) Fdb[r] = wF * A[r];
+      }
+      u_init = u_init || wU != 0.0f;
+      e_init = e_init || wE != 0.0f;
+      f_init = f_init || wF != 0.0f;
+    }
+    // the squared scaled terms of the starting-step norms
+    if (live && mode == JA_EVAL) {
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        const float sy = (float)a.atol + (float)a.rtol * fabsf(y[r]);
+        const float sa = (float)a.atol + (float)a.rtol * fabsf(av[r]);
+        sq0 += (y[r] / sy) * (y[r] / sy) + (av[r] / sa) * (av[r] / sa);
+        sq1 += (ky[r] / sy) * (ky[r] / sy) + (ka[r] / sa) * (ka[r] / sa);
+      }
+    } else if (live && mode == JA_PROBE) {
+      float k0[16];
+      ld16(a.kst + ko, k0);
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        const float sy = (float)a.atol + (float)a.rtol * fabsf(y[r]);
+        const float dy = (ky[r] - k0[r]) / sy;
+        sq0 += dy * dy;
+      }
+      ld16(a.kst + ko + D, k0);
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        const float sa = (float)a.atol + (float)a.rtol * fabsf(av[r]);
+        const float da = (ka[r] - k0[r]) / sa;
+        sq0 += da * da;
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (abort_s) break;
+  }
+
+  // ---- the attempt's error terms of this row: e = h sum_i e_i k_i,
+  // scaled by atol + rtol max(|z|, |z1|) (z1 = the candidate)
+  if (live && mode == JA_STEP && !abort_s) {
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      float e[16], kk[16], z1[16];
+#pragma unroll
+      for (int r = 0; r < C; ++r) e[r] = 0.0f;
+      for (int l = 1; l <= 7; ++l) {
+        const float el = (float)Tb::e(l);
+        if (el == 0.0f) continue;
+        ld16(a.kst + (size_t)(l - 1) * KS + ko + part * D, kk);
+#pragma unroll
+        for (int r = 0; r < C; ++r) e[r] = madd(el, kk[r], e[r]);
+      }
+      ld16((part ? a.ac : a.yc) + ro, z1);
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        const float z = part ? av[r] : y[r];
+        const float sc = madd((float)a.rtol, fmaxf(fabsf(z), fabsf(z1[r])), (float)a.atol);
+        const float q = (hs * e[r]) / sc;
+        sq0 += q * q;
+      }
+    }
+  }
+  // the output bias's part of G: the rows' sums, in row order (the h2 tile
+  // is free now)
+  float* sR = reinterpret_cast<float*>(sH2h);
+  auto row_sum = [&](const float (&v)[16], bool init, float* dst) {
+#pragma unroll
+    for (int r = 0; r < C; ++r) sR[row * D + coff + r] = v[r];
+    __syncthreads();
+    if (tid < D) {
+      float s = 0.0f;
+      for (int rr = 0; rr < 128; ++rr) s += sR[rr * D + tid];
+      dst[L::P_B2 + tid] = init ? s : 0.0f;
+    }
+    __syncthreads();
+  };
+  row_sum(Udb, u_init, S);
+  row_sum(Edb, e_init, S + P);
+  row_sum(Fdb, f_init, S + 2 * P);
+  // slots no stage wrote hold zeros (their decide launch reads them)
+  for (int p = tid; p < P; p += 256) {
+    if (p >= L::P_B2) break;
+    if (!u_init) S[p] = 0.0f;
+    if (!e_init) S[P + p] = 0.0f;
+    if (!f_init) S[2 * P + p] = 0.0f;
+  }
+  // this CTA's squared scaled sums, in a fixed order, in FP64
+  {
+    double v0 = sq0, v1 = sq1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+    }
+    if ((tid & 31) == 0) red[warp] = v0;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[w];
+      a.epart[2 * blockIdx.x] = s;
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) red[warp] = v1;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[w];
+      a.epart[2 * blockIdx.x + 1] = s;
+    }
+  }
+  if (abort_s && tid == 0) atomicExch(a.err, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, L::T_COLS);
+}
+
+// Decide launch of the joint continuous adjoint (see k_mlp_jadj): per
+// parameter the CTAs' slots in CTA order, abar's candidate and its squared
+// scaled error term; then the last CTA's decision and controller, exactly
+// the solver's (the oracle's orc_solve on the same augmented problem).
+template <class Cfg>
+__global__ void __launch_bounds__(256) k_mlp_jadj_decide(JadjArgs a, int mode, int grid1) {
+  using L = MlpAdjLayout<Cfg>;
+  using Tb = DP5;
+  constexpr int P = L::P_FLOATS;
+  __shared__ double red[8];
+  __shared__ int last_s;
+  const JadjCtl c = *a.ctl;
+  if (c.status != ST_RUNNING) return;
+  const int tid = threadIdx.x;
+  const double hs = -c.h_use;
+  double s0 = 0.0, s1 = 0.0;
+  for (int p = blockIdx.x * 256 + tid; p < P; p += gridDim.x * 256) {
+    if (mode == JA_STEP && c.pending) {  // commit the accepted candidate
+      a.th[p] = a.thc[p];
+      a.kth1[p] = a.fsum[p];
+    }
+    double U = 0.0, E = 0.0, Fs = 0.0;
+    for (int b = 0; b < grid1; ++b) {
+      const float* S = a.gpart + (size_t)b * 3 * P;
+      if (mode == JA_STEP) {
+        U += (double)__ldcg(S + p);
+        E += (double)__ldcg(S + P + p);
+      }
+      Fs += (double)__ldcg(S + 2 * P + p);
+    }
+    const double th = a.th[p];
+    if (!jadj_real<L>(p)) {
+      if (mode == JA_STEP) {
+        a.thc[p] = th;
+        a.fsum[p] = 0.0;
+      } else if (mode == JA_EVAL) {
+        a.kth1[p] = 0.0;
+      }
+      continue;
+    }
+    if (mode == JA_EVAL) {
+      a.kth1[p] = Fs;
+      const double sc = a.atol + a.rtol * fabs(th);
+      s0 += (th / sc) * (th / sc);
+      s1 += (Fs / sc) * (Fs / sc);
+    } else if (mode == JA_PROBE) {
+      const double sc = a.atol + a.rtol * fabs(th);
+      const double d = (Fs - a.kth1[p]) / sc;
+      s0 += d * d;
+    } else {
+      const double k1 = a.kth1[p];
+      const double thn = th + (U + hs * Tb::b(1) * k1);
+      const double e = E + hs * Tb::e(1) * k1;
+      a.thc[p] = thn;
+      a.fsum[p] = Fs;
+      const double sc = a.atol + a.rtol * fmax(fabs(th), fabs(thn));
+      s0 += (e / sc) * (e / sc);
+    }
+  }
+  // this CTA's partials in a fixed order
+  auto cta_total = [&](double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0)
+      for (int w = 0; w < 8; ++w) s += red[w];
+    __syncthreads();
+    return s;
+  };
+  const double p0 = cta_total(s0), p1 = cta_total(s1);
+  if (tid == 0) {
+    a.dpart[2 * blockIdx.x] = p0;
+    a.dpart[2 * blockIdx.x + 1] = p1;
+    __threadfence();
+    last_s = atomicAdd(&a.ctl->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last_s || tid != 0) return;
+  __threadfence();
+  // ---- the last CTA: every partial in order, then the decision
+  double t0 = 0.0, t1 = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) {
+    t0 += __ldcg(a.dpart + 2 * b);
+    t1 += __ldcg(a.dpart + 2 * b + 1);
+  }
+  for (int b = 0; b < grid1; ++b) {
+    t0 += __ldcg(a.epart + 2 * b);
+    t1 += __ldcg(a.epart + 2 * b + 1);
+  }
+  JadjCtl n = c;
+  n.ticket = 0;
+  const double N = a.nnorm;
+  auto clip = [&]() {
+    const double rem = n.t - n.t_end;
+    if (n.h >= rem) {
+      n.h_use = rem;
+      n.use_last = 1;
+    } else {
+      n.h_use = n.h;
+      n.use_last = 0;
+    }
+  };
+  if (mode == JA_EVAL) {
+    const double d0 = sqrt(t0 / N), d1 = sqrt(t1 / N);
+    n.h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * (d0 / d1);
+    n.d1 = d1;
+    n.n_fe += 1;
+  } else if (mode == JA_PROBE) {
+    const double d2 = sqrt(t0 / N) / c.h0;
+    const double m = fmax(c.d1, d2);
+    const double h1 = (m <= 1e-15) ? fmax(1e-6, c.h0 * 1e-3) : ctl_pow(0.01 / m, 1.0 / 5.0);
+    double h = fmin(100.0 * c.h0, h1);
+    h = fmin(h, c.t - c.t_end);
+    if (!(h > 0.0 && isfinite(h))) h = c.t - c.t_end;
+    n.h = h;
+    n.n_fe += 1;
+    clip();
+  } else {
+    const double err = sqrt(t0 / N);
+    const bool finite = isfinite(err);
+    const bool accept = finite && err <= 1.0;
+    double h_next;
+    n.n_fe += 6;
+    if (accept) {
+      n.t = c.use_last ? c.t_end : c.t + hs;
+      double fac;
+      if (err == 0.0) {
+        fac = a.fac_max;
+      } else {
+        fac = a.safety * ctl_pow(err, -a.beta1);
+        if (a.beta2 != 0.0) fac = fac * ctl_pow(c.err_prev, a.beta2);
+        if (a.beta3 != 0.0) fac = fac * ctl_pow(c.err_prev2, -a.beta3);
+      }
+      fac = fmin(fmax(fac, a.fac_min), a.fac_max);
+      if (c.prev_rej) fac = fmin(fac, 1.0);
+      h_next = c.h_use * fac;
+      n.err_prev2 = c.err_prev;
+      n.err_prev = fmax(err, 1e-4);
+      n.prev_rej = 0;
+      n.n_acc += 1;
+      n.pending = 1;
+      if (c.use_last) n.status = ST_SUCCESS;
+    } else {
+      const double fac =
+          finite ? fmin(fmax(a.safety * ctl_pow(err, -a.beta1), a.fac_min), 1.0) : a.fac_min;
+      h_next = c.h_use * fac;
+      n.prev_rej = 1;
+      n.n_rej += 1;
+      n.pending = 0;
+    }
+    n.h = h_next;
+    if (n.status == ST_RUNNING) {
+      const double scale = fmax(fabs(n.t), fabs(n.t_end));
+      if (n.t - h_next == n.t || h_next < 1e-14 * scale || !(h_next > 0.0))
+        n.status = finite ? ST_DT_UNDERFLOW : ST_NONFINITE;
+      else if (n.n_acc + n.n_rej >= a.max_steps)
+        n.status = ST_MAX_STEPS;
+    }
+    clip();
+  }
+  *a.ctl = n;
+}
+
+// Segment end: commit an accepted last candidate (rows and abar).
+__global__ void k_mlp_jadj_commit(JadjArgs a, int P) {
+  const JadjCtl c = *a.ctl;
+  if (!c.pending) return;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long BD = (long long)a.B * 32;
+  if (e < BD) {
+    a.y[e] = a.yc[e];
+    a.a[e] = a.ac[e];
+  }
+  if (e < P) a.th[e] = a.thc[e];
+}
+
+// a += the cotangent of evaluation point q (the loss jumps there).
+__global__ void k_mlp_jadj_jump(float* av, const float* gye, int B, int K, int D, int q) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)B * D) return;
+  const long long b = e / D, j = e % D;
+  av[e] += gye[(b * K + q) * D + j];
+}
+
+// abar (the parameters' layout of the adjoint partials) into the layers'
+// gradients, W[l] row-major [out][in] like the field's weights.
+template <class Cfg>
+__global__ void k_mlp_jadj_out(const double* th, float* gW0, float* gb0, float* gW1, float* gb1,
+                               float* gW2, float* gb2) {
+  using L = MlpAdjLayout<Cfg>;
+  constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, IN = D + 1;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < H * IN) {
+    gW0[k] = (float)th[L::P_W0 + (k / IN) * K0 + k % IN];
+    return;
+  }
+  k -= H * IN;
+  if (k < H) {
+    if (gb0) gb0[k] = (float)th[L::P_W0 + k * K0 + IN];
+    return;
+  }
+  k -= H;
+  if (k < H * H) {
+    gW1[k] = (float)th[L::P_W1 + k];
+    return;
+  }
+  k -= H * H;
+  if (k < H) {
+    if (gb1) gb1[k] = (float)th[L::P_B1 + k];
+    return;
+  }
+  k -= H;
+  if (k < D * H) {
+    gW2[k] = (float)th[L::P_W2T + (k % H) * D + k / H];
+    return;
+  }
+  k -= D * H;
+  if (k < D && gb2) gb2[k] = (float)th[L::P_B2 + k];
+}
+
 // ---------------------------------------------------------------- host side
 // Opts a kernel into its dynamic shared memory once per device: the
 // attribute is host-side state, and doing it once keeps later calls (for
@@ -3112,6 +3937,200 @@ tode_err mlp_adjoint(const AdjReq& r) {
       r.gW[2], r.gb ? r.gb[2] : nullptr);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
+}
+
+
+// ---------------------------------------------------------------- joint continuous adjoint
+// Workspace: control block, weight image, the rows' state and candidate,
+// the stage slots, the CTAs' parameter slots, abar and its companions.
+struct JadjWs {
+  JadjCtl* ctl;
+  int32_t* err;
+  unsigned char* img;
+  float *y, *a, *yc, *ac, *kst, *gpart;
+  double *epart, *th, *thc, *kth1, *fsum, *dpart;
+  size_t bytes;
+};
+static JadjWs jadj_carve(char* base, int B) {
+  using L = MlpAdjLayout<Cfg32s>;
+  constexpr int D = 32, P = L::P_FLOATS;
+  const size_t BD = (size_t)B * D;
+  const int grid1 = (B + 127) / 128, grid2 = (P + 255) / 256;
+  JadjWs w{};
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    char* q = base ? base + o : nullptr;
+    o += align256(n);
+    return q;
+  };
+  char* c = take(256);
+  w.ctl = (JadjCtl*)c;
+  w.err = c ? (int32_t*)(c + 128) : nullptr;
+  w.img = (unsigned char*)take((size_t)Cfg32s::WIMG_BYTES);
+  w.y = (float*)take(BD * 4);
+  w.a = (float*)take(BD * 4);
+  w.yc = (float*)take(BD * 4);
+  w.ac = (float*)take(BD * 4);
+  w.kst = (float*)take(7 * 2 * BD * 4);
+  w.gpart = (float*)take((size_t)grid1 * 3 * P * 4);
+  w.epart = (double*)take((size_t)grid1 * 2 * 8);
+  w.th = (double*)take((size_t)P * 8);
+  w.thc = (double*)take((size_t)P * 8);
+  w.kth1 = (double*)take((size_t)P * 8);
+  w.fsum = (double*)take((size_t)P * 8);
+  w.dpart = (double*)take((size_t)grid2 * 2 * 8);
+  w.bytes = o;
+  return w;
+}
+static_assert(sizeof(JadjCtl) <= 128, "joint adjoint control block");
+
+size_t mlp_jadj_workspace_bytes(const tode_field_desc* f) {
+  if (!is_d32_h128(f)) return 0;
+  return jadj_carve(nullptr, f->B).bytes;
+}
+
+tode_err mlp_joint_adjoint(const JadjReq& r) {
+  using Cfg = Cfg32s;
+  using L = MlpAdjLayout<Cfg>;
+  constexpr int D = 32, P = L::P_FLOATS;
+  if (!is_d32_h128(r.f)) return TODE_EUNSUPPORTED;
+  const cudaStream_t st = r.stream;
+  const int B = r.B, K = r.K;
+  const int grid1 = (B + 127) / 128, grid2 = (P + 255) / 256;
+  const JadjWs w = jadj_carve(r.ws, B);
+  JadjArgs a{};
+  a.B = B;
+  a.wimg = w.img;
+  for (int l = 0; l < 3; ++l) a.bias[l] = r.f->b[l];
+  a.y = w.y;
+  a.a = w.a;
+  a.yc = w.yc;
+  a.ac = w.ac;
+  a.kst = w.kst;
+  a.gpart = w.gpart;
+  a.epart = w.epart;
+  a.th = w.th;
+  a.thc = w.thc;
+  a.kth1 = w.kth1;
+  a.fsum = w.fsum;
+  a.dpart = w.dpart;
+  a.ctl = w.ctl;
+  a.err = w.err;
+  const tode_options* o = r.o;
+  a.rtol = o->rtol;
+  a.atol = o->atol;
+  a.safety = o->safety;
+  a.fac_min = o->fac_min;
+  a.fac_max = o->fac_max;
+  a.beta1 = o->beta1;
+  a.beta2 = o->beta2;
+  a.beta3 = o->beta3;
+  a.max_steps = o->max_steps;
+  // the norm's components: y and a of every row, the network's parameters
+  a.nnorm = 2.0 * B * D + (double)(Cfg::H * (D + 1) + Cfg::H + Cfg::H * Cfg::H + Cfg::H +
+                                   D * Cfg::H + D);
+  {
+    size_t loff[MLP_MAX_LAYERS] = {};
+    for (int l = 0; l < Cfg::NL; ++l) loff[l] = Cfg::W_off(l);
+    const tode_err e = build_images<Cfg>(r.f, w.img, IMG_TILE, 1, Cfg::WIMG_STRIDE, loff, st);
+    if (e != TODE_OK) return e;
+  }
+  {
+    static std::atomic<uint64_t> done{0};
+    const tode_err e = smem_optin((const void*)k_mlp_jadj<Cfg>, L::S_END, done);
+    if (e != TODE_OK) return e;
+  }
+  const size_t BD = (size_t)B * D;
+  TODE_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, 256, st));
+  TODE_CUDA_TRY(cudaMemsetAsync(w.th, 0, (size_t)P * 8, st));
+  TODE_CUDA_TRY(cudaMemcpyAsync(w.y, r.y1, BD * 4, cudaMemcpyDeviceToDevice, st));
+  if (r.gyf)
+    TODE_CUDA_TRY(cudaMemcpyAsync(w.a, r.gyf, BD * 4, cudaMemcpyDeviceToDevice, st));
+  else
+    TODE_CUDA_TRY(cudaMemsetAsync(w.a, 0, BD * 4, st));
+  const unsigned jb = (unsigned)((BD + 255) / 256);
+  auto jump = [&](int q) -> tode_err {
+    if (r.gye) {
+      k_mlp_jadj_jump<<<jb, 256, 0, st>>>(w.a, r.gye, B, K, D, q);
+      TODE_CUDA_TRY(cudaGetLastError());
+    }
+    return TODE_OK;
+  };
+  auto pair = [&](int mode) -> tode_err {
+    k_mlp_jadj<Cfg><<<grid1, 256, L::S_END, st>>>(a, mode);
+    TODE_CUDA_TRY(cudaGetLastError());
+    k_mlp_jadj_decide<Cfg><<<grid2, 256, 0, st>>>(a, mode, grid1);
+    TODE_CUDA_TRY(cudaGetLastError());
+    return TODE_OK;
+  };
+  // cotangents of the points at t1 start a
+  int k = K - 1;
+  while (k >= 0 && r.te[k] == r.t1) {
+    const tode_err e = jump(k--);
+    if (e != TODE_OK) return e;
+  }
+  int32_t n_acc = 0, n_rej = 0, n_fe = 0, status = ST_SUCCESS;
+  double start = r.t1;
+  const int poll = 8;
+  while (true) {
+    const double end = (k >= 0 && r.te[k] > r.t0) ? r.te[k] : r.t0;
+    if (end != start) {
+      JadjCtl h{};
+      h.t = start;
+      h.t_end = end;
+      h.err_prev = h.err_prev2 = 1.0;
+      h.status = ST_RUNNING;
+      TODE_CUDA_TRY(cudaMemcpyAsync(w.ctl, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+      TODE_CUDA_TRY(cudaStreamSynchronize(st));  // h is reused below
+      tode_err e = pair(JA_EVAL);
+      if (e == TODE_OK) e = pair(JA_PROBE);
+      if (e != TODE_OK) return e;
+      long long launched = 0;
+      const long long limit = (long long)o->max_steps + 2LL * poll + 2;
+      while (true) {
+        for (int q = 0; q < poll; ++q) {
+          e = pair(JA_STEP);
+          if (e != TODE_OK) return e;
+        }
+        launched += poll;
+        TODE_CUDA_TRY(cudaMemcpyAsync(&h, w.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+        TODE_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h.status != ST_RUNNING) break;
+        // one attempt per launch pair, so max_steps bounds the loop
+        if (launched > limit) return TODE_ETIMEOUT;
+      }
+      k_mlp_jadj_commit<<<(unsigned)((std::max<size_t>(BD, P) + 255) / 256), 256, 0, st>>>(a, P);
+      TODE_CUDA_TRY(cudaGetLastError());
+      n_acc += h.n_acc;
+      n_rej += h.n_rej;
+      n_fe += h.n_fe;
+      if (h.status != ST_SUCCESS) {
+        status = h.status;
+        break;
+      }
+    }
+    while (k >= 0 && r.te[k] == end) {
+      const tode_err e = jump(k--);
+      if (e != TODE_OK) return e;
+    }
+    start = end;
+    if (end == r.t0) break;
+  }
+  TODE_CUDA_TRY(cudaMemcpyAsync(r.gy0, w.a, BD * 4, cudaMemcpyDeviceToDevice, st));
+  if (r.y0) TODE_CUDA_TRY(cudaMemcpyAsync(r.y0, w.y, BD * 4, cudaMemcpyDeviceToDevice, st));
+  const int total = Cfg::H * (D + 1) + Cfg::H + Cfg::H * Cfg::H + Cfg::H + D * Cfg::H + D;
+  k_mlp_jadj_out<Cfg><<<(total + 255) / 256, 256, 0, st>>>(
+      w.th, r.gW[0], r.gb ? r.gb[0] : nullptr, r.gW[1], r.gb ? r.gb[1] : nullptr, r.gW[2],
+      r.gb ? r.gb[2] : nullptr);
+  TODE_CUDA_TRY(cudaGetLastError());
+  int32_t flag = 0;
+  TODE_CUDA_TRY(cudaMemcpyAsync(&flag, w.err, 4, cudaMemcpyDeviceToHost, st));
+  TODE_CUDA_TRY(cudaStreamSynchronize(st));
+  r.stats[0] = n_acc;
+  r.stats[1] = n_rej;
+  r.stats[2] = n_fe;
+  r.stats[3] = status;
+  return flag ? TODE_ETIMEOUT : TODE_OK;
 }
 
 }  // namespace tode

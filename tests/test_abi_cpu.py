@@ -258,3 +258,51 @@ def test_peak_kernel_rejects_bad_shapes_before_launch():
         assert lib.tode_peak_kernel(kind, grid, block, iters, None, None) == _abi.TODE_EINVAL
     # the arithmetic kernels need a sink
     assert lib.tode_peak_kernel(_abi.TODE_PEAK_EX2, 1, 32, 1, None, None) == _abi.TODE_EINVAL
+
+
+def _mlp_desc(B, widths=(33, 128, 128, 32)):
+    f = _abi.FieldDesc()
+    f.kind, f.B, f.D = _abi.TODE_MLP, B, widths[-1]
+    wa = (C.c_int * len(widths))(*widths)
+    ptrs = (C.c_void_p * (len(widths) - 1))(*([0x1000] * (len(widths) - 1)))
+    f.n_layers = len(widths) - 1
+    f.widths = wa
+    f.W = ptrs
+    f.b = ptrs
+    return f, (wa, ptrs)
+
+
+def test_joint_adjoint_rules_before_launch():
+    """The joint continuous adjoint covers the D = 32, H = 128 MLP field with
+    split activations and scalar tolerances; its workspace grows with the
+    batch; bad times, unordered points or other fields are refused before
+    anything runs."""
+    lib = _abi.load()
+    split = _opts(prec=_abi.TODE_BF16W_SPLIT)
+    f1, keep1 = _mlp_desc(128)
+    f2, keep2 = _mlp_desc(1024)
+    n1 = lib.tode_joint_adjoint_workspace_size(C.byref(f1), C.byref(split))
+    n2 = lib.tode_joint_adjoint_workspace_size(C.byref(f2), C.byref(split))
+    assert 0 < n1 < n2 and n1 % 256 == 0
+    assert lib.tode_joint_adjoint_workspace_size(C.byref(f1), C.byref(_opts(prec=_abi.TODE_BF16W))) == 0
+    wide, keep3 = _mlp_desc(128, (65, 512, 512, 512, 64))
+    assert lib.tode_joint_adjoint_workspace_size(C.byref(wide), C.byref(split)) == 0
+    assert lib.tode_joint_adjoint_workspace_size(C.byref(_desc(_abi.TODE_VDP, 10, 2)),
+                                                 C.byref(_opts())) == 0
+    stats = (C.c_int32 * 4)()
+    p = C.c_void_p(0x1000)
+    gw = (C.c_void_p * 3)(0x1000, 0x1000, 0x1000)
+    te = (C.c_double * 3)(0.0, 0.7, 0.5)  # not ordered
+
+    def call(f, o, t0, t1, tep, K):
+        return lib.tode_joint_adjoint(C.byref(f), C.byref(o), t0, t1, tep, K, p, None, None, p,
+                                      gw, None, None, stats, p, C.c_size_t(1 << 30), None)
+    assert call(f1, split, 1.0, 0.0, None, 0) == _abi.TODE_EINVAL       # t1 <= t0
+    assert call(f1, split, 0.0, 1.0, te, 3) == _abi.TODE_EINVAL         # unordered points
+    assert call(f1, _opts(prec=_abi.TODE_BF16W), 0.0, 1.0, None, 0) == _abi.TODE_EUNSUPPORTED
+    assert call(_desc(_abi.TODE_VDP, 4, 2), _opts(), 0.0, 1.0, None, 0) == _abi.TODE_EUNSUPPORTED
+    # a misaligned workspace is reported before any launch
+    rc = lib.tode_joint_adjoint(C.byref(f1), C.byref(split), 0.0, 1.0, None, 0, p, None, None, p,
+                                gw, None, None, stats, C.c_void_p(0x1001), C.c_size_t(1 << 30),
+                                None)
+    assert rc == _abi.TODE_EWORKSPACE
