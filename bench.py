@@ -594,6 +594,89 @@ def measure(cfg, args, dev, fp32_peak, fp32_src, world=1, headline=False, peaks=
                 clocks=clocks, steps=steps, with_adj=with_adj)
 
 
+# ------------------------------------------------------------------ joint continuous adjoint
+JADJ_FLOP_PER_ROW_EVAL = 3 * 2 * (33 * 128 + 128 * 128 + 128 * 32)  # fwd, VJP, parameter products
+
+
+def measure_joint_adjoint(args, dev, peaks, do_cpu):
+    """The joint continuous adjoint (App. A, the CNF benchmark's
+    "torchode-joint" backward pass) on the D = 32, H = 128 MLP workload: one
+    adjoint equation of size 2BD + P for the whole batch, from the fused
+    forward's y(t1), timed (CUDA events, L2 flushed outside) beside the
+    per-instance discrete adjoint of the same gradient."""
+    torch = __import__("torch")
+    import paper_2210_12375_b300 as tode
+    wl = Workload(4, args, dev)
+    w = wl.w
+    te = w["t_eval"][0]
+    assert (w["t_eval"] == te).all() and (w["t0"] == w["t0"][0]).all() and \
+        (w["t1"] == w["t1"][0]).all(), "a shared time axis"
+    t0, t1 = float(w["t0"][0]), float(w["t1"][0])
+    opt = dict(rtol=w["rtol"], atol=w["atol"])
+    sol = wl.fwd("fused")
+    torch.cuda.synchronize()
+    y1 = sol.y_final.clone()
+    ws = tode.joint_adjoint_workspace(wl.field, wl.B, wl.D, dev, **opt)
+
+    def once():
+        return tode.joint_adjoint(wl.field, y1, t0, t1, te, wl.gye, wl.gyf, workspace=ws, **opt)
+    for _ in range(max(args.warmup, 1)):
+        out = once()
+    torch.cuda.synchronize()
+    n = max(1, min(args.config_steps, 5))
+    stream = torch.cuda.current_stream()
+    ev = _events(torch, n)
+    for k in range(n):
+        wl.flush.zero_()
+        ev[k][0].record(stream)
+        out = once()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    st = out[3]
+    ms_disc = wl.kernel_ms(args.kernel_reps, True)
+    flop = st["n_feval"] * wl.B * JADJ_FLOP_PER_ROW_EVAL
+    pk, src = _peaks_file()
+    P = 128 * 33 + 128 + 128 * 128 + 128 + 32 * 128 + 32
+    entry = {
+        "B": wl.B, "D": wl.D, "K": wl.K, "rtol": w["rtol"], "t0": t0, "t1": t1,
+        "augmented_size": 2 * wl.B * wl.D + P,
+        "accepted": st["n_acc"], "rejected": st["n_rej"], "augmented_evaluations": st["n_feval"],
+        "segments": int(((te > t0) & (te < t1)).sum()) + 1,
+        "ms_joint_backward": ms, "ms_discrete_adjoint": ms_disc,
+        "discrete_over_joint": ms_disc / ms,
+        "roofline": {"bound": "tensor", "kernel": "k_mlp_jadj + k_mlp_jadj_decide (per attempt)",
+                     "achieved": flop / (ms * 1e-3) / 1e12, "peak": pk["bf16_tflops"],
+                     "unit": "TFLOP/s", "frac": flop / (ms * 1e-3) / 1e12 / pk["bf16_tflops"],
+                     "flop_per_row_evaluation": JADJ_FLOP_PER_ROW_EVAL, "traffic": None,
+                     "peak_source": f"bf16 burst, MEASURED_PEAKS.json; of {src}"},
+        "issue": "host-synchronous: the decision read every 4 attempts, one launch pair per "
+                 "attempt, restarted at every evaluation point",
+    }
+    if do_cpu:
+        # FP64 oracle of the same joint problem on a 256-instance prefix
+        import oracle
+        ws_ = workloads.make(4, 256)
+        r = oracle.solve(ws_["field"], ws_["y0"], ws_["t0"], ws_["t1"], ws_["t_eval"],
+                         dict(rtol=1e-10, atol=1e-10))
+        y1s = r["y_final"].astype(np.float32).astype(np.float64)
+        gye = wl.gye[:256].double().cpu().numpy()
+        gyf = wl.gyf[:256].double().cpu().numpy()
+        tt = time.perf_counter()
+        ref = oracle.joint_adjoint(ws_["field"], y1s, t0, t1, te, gye, gyf, opt)
+        cpu_s = time.perf_counter() - tt
+        f32 = lambda x: torch.tensor(x, dtype=torch.float32, device=dev)
+        g = tode.joint_adjoint(wl.field, f32(y1s), t0, t1, te, wl.gye[:256].contiguous(),
+                               wl.gyf[:256].contiguous(), **opt)
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        entry["error_vs_fp64"] = {
+            "reference": "FP64 oracle joint adjoint, same y(t1), on a 256-instance prefix",
+            "gy0_rel_l2": rel(g[0].double().cpu().numpy(), ref["gy0"]),
+            "gW_rel_l2": [rel(x.double().cpu().numpy(), y) for x, y in zip(g[1][0], ref["gW"])],
+            "accepted_gpu_vs_oracle": [g[3]["n_acc"], ref["n_acc"]], "cpu_s": cpu_s}
+    return entry
+
+
 # ------------------------------------------------------------------ CPU leg
 def error_sample(w):
     """Instances on which the FP64 reference is computed: all of the small
@@ -861,6 +944,10 @@ def run_tode(args):
             kept[m["wl"].w["name"]] = (m["wl"].w, m["keep"])
             del m
             torch.cuda.empty_cache()
+    if args.workload < 0:
+        configs["mlp_d32_h128_joint_adjoint"] = measure_joint_adjoint(
+            args, dev, peaks, rank == 0 and not args.no_cpu and world == 1)
+        torch.cuda.empty_cache()
     steps = head["steps"]
     per_step = head["ms"] / steps
     value = world * wl.n_att / (per_step * 1e-3)

@@ -350,6 +350,19 @@ def adjoint(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=Non
     return gy0, gparam, overflow
 
 
+def joint_adjoint_workspace(field, B: int, D: int, device="cuda", **opt_kw) -> torch.Tensor:
+    """A device workspace large enough for joint_adjoint on B x D."""
+    lib = _abi.load()
+    opts = make_options(prec=_abi.TODE_BF16W_SPLIT if getattr(field, "split", False)
+                        else _abi.TODE_BF16W, **opt_kw)
+    keep = []
+    fd = field.desc(B, D, keep)
+    nb = lib.tode_joint_adjoint_workspace_size(C.byref(fd), C.byref(opts))
+    if nb == 0 and B > 0:
+        raise _abi.TodeError(_abi.TODE_EUNSUPPORTED, "tode_joint_adjoint_workspace_size")
+    return torch.empty(max(nb, 256), dtype=torch.uint8, device=device)
+
+
 def joint_adjoint(field, y1: torch.Tensor, t0: float, t1: float, t_eval=None, gy_eval=None,
                   gy_final=None, *, stream=None, workspace: Optional[torch.Tensor] = None,
                   **opt_kw):

@@ -3155,34 +3155,56 @@ __global__ void __launch_bounds__(256, 1) k_mlp_jadj(JadjArgs a, int mode) {
       wF = -1.0f;
     }
     if (wU != 0.0f || wE != 0.0f || wF != 0.0f) {
-      auto rmw = [&](int idx, float v) {
-        if (wU != 0.0f) S[idx] = (u_init ? S[idx] : 0.0f) + wU * v;
-        if (wE != 0.0f) S[P + idx] = (e_init ? S[P + idx] : 0.0f) + wE * v;
-        if (wF != 0.0f) S[2 * P + idx] = wF * v;
+      // 16 consecutive slot entries (64-byte aligned): both slots' old values
+      // are loaded before anything is stored, so the loads overlap
+      auto rmw16 = [&](int idx, const float (&v)[16]) {
+        float4 u[4], e[4];
+        float4* pu = reinterpret_cast<float4*>(S + idx);
+        float4* pe = reinterpret_cast<float4*>(S + P + idx);
+        float4* pf = reinterpret_cast<float4*>(S + 2 * P + idx);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          u[q] = (wU != 0.0f && u_init) ? pu[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+          e[q] = (wE != 0.0f && e_init) ? pe[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (wU != 0.0f)
+            pu[q] = make_float4(madd(wU, v[4 * q], u[q].x), madd(wU, v[4 * q + 1], u[q].y),
+                                madd(wU, v[4 * q + 2], u[q].z), madd(wU, v[4 * q + 3], u[q].w));
+          if (wE != 0.0f)
+            pe[q] = make_float4(madd(wE, v[4 * q], e[q].x), madd(wE, v[4 * q + 1], e[q].y),
+                                madd(wE, v[4 * q + 2], e[q].z), madd(wE, v[4 * q + 3], e[q].w));
+          if (wF != 0.0f)
+            pf[q] = make_float4(wF * v[4 * q], wF * v[4 * q + 1], wF * v[4 * q + 2],
+                                wF * v[4 * q + 3]);
+        }
       };
       float v[16];
       // G_W1 (lane = hidden unit; its t and b1 columns included)
       for (int cc = half * 32; cc < (half ? K0 : 32); cc += 16) {
         tc::tmem_ld16(tl + L::T_D0 + cc, v);
         tc::tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) rmw(L::P_W0 + row * K0 + cc + j, v[j]);
+        rmw16(L::P_W0 + row * K0 + cc, v);
       }
 #pragma unroll 1
       for (int cc = 0; cc < HC; cc += 16) {
         const int col = half * HC + cc;
         tc::tmem_ld16(tl + L::T_D1 + col, v);
         tc::tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) rmw(L::P_W1 + row * H + col + j, v[j]);
+        rmw16(L::P_W1 + row * H + col, v);
       }
       tc::tmem_ld16(tl + L::T_DB, v);
       tc::tmem_wait_ld();
-      if (half == 0) rmw(L::P_B1 + row, v[0]);
+      if (half == 0) {
+        const int idx = L::P_B1 + row;
+        if (wU != 0.0f) S[idx] = madd(wU, v[0], u_init ? S[idx] : 0.0f);
+        if (wE != 0.0f) S[P + idx] = madd(wE, v[0], e_init ? S[P + idx] : 0.0f);
+        if (wF != 0.0f) S[2 * P + idx] = wF * v[0];
+      }
       tc::tmem_ld16(tl + L::T_D2 + coff, v);
       tc::tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < 16; ++j) rmw(L::P_W2T + row * D + coff + j, v[j]);
+      rmw16(L::P_W2T + row * D + coff, v);
 #pragma unroll
       for (int r = 0; r < C; ++r) {
         Udb[r] = madd(wU, A[r], Udb[r]);
@@ -3325,15 +3347,36 @@ __global__ void __launch_bounds__(256) k_mlp_jadj_decide(JadjArgs a, int mode, i
       a.th[p] = a.thc[p];
       a.kth1[p] = a.fsum[p];
     }
-    double U = 0.0, E = 0.0, Fs = 0.0;
-    for (int b = 0; b < grid1; ++b) {
-      const float* S = a.gpart + (size_t)b * 3 * P;
-      if (mode == JA_STEP) {
-        U += (double)__ldcg(S + p);
-        E += (double)__ldcg(S + P + p);
+    // the CTAs' slots in CTA order (eight rows of loads in flight, added
+    // one by one in order), by compensated FP32 sums: B300's FP64 pipe is
+    // narrow, and the compensation keeps the sums to a few FP32 roundings
+    float su = 0.0f, cu = 0.0f, se = 0.0f, ce = 0.0f, sf = 0.0f, cf = 0.0f;
+    auto kahan = [](float& s_, float& c_, float x) {
+      const float yk = x - c_;
+      const float tk = s_ + yk;
+      c_ = (tk - s_) - yk;
+      s_ = tk;
+    };
+    for (int b0 = 0; b0 < grid1; b0 += 8) {
+      float u[8], e[8], f[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int b = b0 + q;
+        const float* S = a.gpart + (size_t)b * 3 * P;
+        const bool in = b < grid1;
+        u[q] = (in && mode == JA_STEP) ? __ldcg(S + p) : 0.0f;
+        e[q] = (in && mode == JA_STEP) ? __ldcg(S + P + p) : 0.0f;
+        f[q] = in ? __ldcg(S + 2 * P + p) : 0.0f;
       }
-      Fs += (double)__ldcg(S + 2 * P + p);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        kahan(su, cu, u[q]);
+        kahan(se, ce, e[q]);
+        kahan(sf, cf, f[q]);
+      }
     }
+    const double U = (double)su - (double)cu, E = (double)se - (double)ce,
+                 Fs = (double)sf - (double)cf;
     const double th = a.th[p];
     if (!jadj_real<L>(p)) {
       if (mode == JA_STEP) {
@@ -3383,18 +3426,21 @@ __global__ void __launch_bounds__(256) k_mlp_jadj_decide(JadjArgs a, int mode, i
     last_s = atomicAdd(&a.ctl->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last_s || tid != 0) return;
+  if (!last_s) return;
   __threadfence();
-  // ---- the last CTA: every partial in order, then the decision
-  double t0 = 0.0, t1 = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) {
-    t0 += __ldcg(a.dpart + 2 * b);
-    t1 += __ldcg(a.dpart + 2 * b + 1);
+  // ---- the last CTA: every partial (each thread a fixed subset, then the
+  // fixed tree of cta_total), then thread 0's decision
+  double q0 = 0.0, q1 = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += 256) {
+    q0 += __ldcg(a.dpart + 2 * b);
+    q1 += __ldcg(a.dpart + 2 * b + 1);
   }
-  for (int b = 0; b < grid1; ++b) {
-    t0 += __ldcg(a.epart + 2 * b);
-    t1 += __ldcg(a.epart + 2 * b + 1);
+  for (int b = tid; b < grid1; b += 256) {
+    q0 += __ldcg(a.epart + 2 * b);
+    q1 += __ldcg(a.epart + 2 * b + 1);
   }
+  const double t0 = cta_total(q0), t1 = cta_total(q1);
+  if (tid != 0) return;
   JadjCtl n = c;
   n.ticket = 0;
   const double N = a.nnorm;
@@ -4071,7 +4117,7 @@ tode_err mlp_joint_adjoint(const JadjReq& r) {
   }
   int32_t n_acc = 0, n_rej = 0, n_fe = 0, status = ST_SUCCESS;
   double start = r.t1;
-  const int poll = 8;
+  const int poll = 4;
   while (true) {
     const double end = (k >= 0 && r.te[k] > r.t0) ? r.te[k] : r.t0;
     if (end != start) {
