@@ -72,7 +72,7 @@ enum {
   TODE_S_DT_UNDERFLOW = 2,  /* step size underflowed with finite errors */
   TODE_S_NONFINITE = 3,     /* step size underflowed while the state was non-finite */
   TODE_S_INVALID_INPUT = 4  /* t0/t1/t_eval not finite, t_eval not ordered from t0 towards t1
-                               or outside the range; MLP field: also t1 < t0 */
+                               or outside the range */
 };
 
 /* The vector field f(t, y) (built-in kinds only).
@@ -227,10 +227,11 @@ size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int 
 
 /* Solve all B instances (Sec. 3: independent parallel solving).
  *  y0 [B][D], t0 [B], t1 [B], t_eval [B][K] (K >= 0; NULL when K == 0).
- *  An instance with t1 < t0 (Van der Pol and linear fields) integrates
- *  backward in time with negative steps: its t_eval runs from t0 down to
- *  t1, its trace holds negative h, and its tape holds -t (the solver works
- *  in tau = -t with positive steps; tode_adjoint reads it that way).
+ *  An instance with t1 < t0 (every field; the MLP field's time input is the
+ *  caller's t) integrates backward in time with negative steps: its t_eval
+ *  runs from t0 down to t1, its trace holds negative h, and its tape holds
+ *  -t (the solver works in tau = -t with positive steps and the field -f;
+ *  tode_adjoint reads it that way).
  *  Outputs: y_eval [B][K][D] (NULL when K == 0), y_final [B][D] (state at
  *  the last accepted step), n_acc, n_rej, n_feval, status [B] int32.
  *  Evaluation points not reached (failed instance) are NaN; instances with

@@ -510,14 +510,17 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   auto start_instance = [&](const int i) {
     // load and validate the instance (Sec. 3: per-instance bounds / points)
     s.inst = i;
-    s.t0 = a.t0[i];
-    s.t1 = a.t1[i];
+    // backward in time (t1 < t0): the row runs in tau = -t with the field
+    // -f(-tau, y) (its times through a sign xor, see tode_core.cuh)
+    const unsigned long long m = (a.t1[i] < a.t0[i]) ? SIGN_BIT : 0ULL;
+    s.t0 = flip(a.t0[i], m);
+    s.t1 = flip(a.t1[i], m);
     s.t = s.t0;
     s.rtol = (float)(a.rtol_b ? a.rtol_b[i] : a.rtol);
     s.atol = (float)(a.atol_b ? a.atol_b[i] : a.atol);
     s.n_acc = s.n_rej = 0;
     s.cursor = 0;
-    s.flags = 0;
+    s.flags = m ? FL_REVERSE : 0;
     s.err_prev = 1.0f;
     s.err_prev2 = 1.0f;
     s.h = s.h0h = 0.0f;
@@ -533,7 +536,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     const long long k0 = tkey(s.t0), k1 = tkey(s.t1);
     long long kprev = k0;
     for (int q = 0; q < a.K && ok; ++q) {
-      const long long kv = tkey(te[q]);
+      const long long kv = tkey(flip(te[q], m));
       ok = tfinite(te[q]) && kv >= kprev && kv <= k1;
       kprev = kv;
     }
@@ -546,7 +549,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         for (int r = 0; r < C; ++r) ye[(size_t)q * D + r] = nan_(0.0f);
       done = true;
     } else {
-      while (s.cursor < a.K && tkey(te[s.cursor]) == k0) {
+      while (s.cursor < a.K && tkey(flip(te[s.cursor], m)) == k0) {
 #pragma unroll
         for (int r = 0; r < C; ++r) ye[(size_t)s.cursor * D + r] = y[r];
         s.cursor++;
@@ -601,15 +604,15 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   // plain form: resume a parked instance at the start of its next attempt
   auto resume = [&](const int i) {
     s.inst = i;
-    s.t0 = a.t0[i];
-    s.t1 = a.t1[i];
-    s.t = a.wt[i];
+    s.flags = a.wfl[i];
+    s.t0 = flip(a.t0[i], rev_mask(s.flags));
+    s.t1 = flip(a.t1[i], rev_mask(s.flags));
+    s.t = a.wt[i];  // parked in the row's own time
     s.rtol = (float)(a.rtol_b ? a.rtol_b[i] : a.rtol);
     s.atol = (float)(a.atol_b ? a.atol_b[i] : a.atol);
     s.n_acc = a.n_acc[i];
     s.n_rej = a.n_rej[i];
     s.cursor = a.wcur[i];
-    s.flags = a.wfl[i];
     s.err_prev = a.wep[i];
     s.err_prev2 = a.wep2[i];
     s.h = a.wh[i];
@@ -677,11 +680,11 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     if (s.phase == PH_INIT0 || s.phase == PH_IDLE) {
 #pragma unroll
       for (int r = 0; r < C; ++r) Y[r] = y[r];
-      tin = (float)s.t;
+      tin = (float)flip(s.t, rev_mask(s.flags));  // the network sees the caller's time
     } else if (s.phase == PH_INIT1) {
 #pragma unroll
       for (int r = 0; r < C; ++r) Y[r] = madd(s.h0h, k1[r], y[r]);
-      tin = (float)(s.t + (double)s.h0h);
+      tin = (float)flip(s.t + (double)s.h0h, rev_mask(s.flags));
     } else {
       if (stage == 2) {  // a new attempt starts: clip at t1
         float h = s.h;
@@ -717,7 +720,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         case 5: cs = Cc::c5; break;
         default: cs = 1.0; break;
       }
-      tin = (float)(s.t + cs * (double)h);
+      tin = (float)flip(s.t + cs * (double)h, rev_mask(s.flags));
     }
     if constexpr (Cfg::STACKED) store_row16_stk(sXh, row, coff, K0, Y);
     else store_row16<true>(sXh, sXl, row, coff, K0, Y);
@@ -918,6 +921,10 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
 #pragma unroll
       for (int r = 0; r < C; ++r) f[r] = v[r] + bo[coff + r];
     }
+    if (s.flags & FL_REVERSE) {  // the row's field in tau = -t is -f
+#pragma unroll
+      for (int r = 0; r < C; ++r) f[r] = -f[r];
+    }
 
     // ---- consume: partial sums of this thread's components
     float p0 = 0.0f, p1 = 0.0f;
@@ -1021,8 +1028,8 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       const int att = s.n_acc + s.n_rej;
       if (a.trace.cap > 0 && att < a.trace.cap && sub == 0) {
         const size_t q = (size_t)i * a.trace.cap + att;
-        a.trace.t[q] = s.t;
-        a.trace.h[q] = hd;
+        a.trace.t[q] = flip(s.t, rev_mask(s.flags));  // the caller's time and signed step
+        a.trace.h[q] = flip(hd, rev_mask(s.flags));
         a.trace.err[q] = (double)err;
         a.trace.acc[q] = accept ? 1 : 0;
       }
@@ -1057,7 +1064,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         const double* te = a.te + (size_t)i * a.K;
         float* ye = a.ye + (size_t)i * a.K * D + coff;
         while (s.cursor < a.K) {
-          const double tq = te[s.cursor];
+          const double tq = flip(te[s.cursor], rev_mask(s.flags));
           const long long kq = tkey(tq);
           if (kq > kn) break;
           float* dst = ye + (size_t)s.cursor * D;
@@ -1416,6 +1423,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   bool bad = false;
   double tn = 0.0, tnext = 0.0;
   float h = 0.0f;
+  unsigned long long rmask = 0;  // the instance runs backward in time: tau = -t, field -f
   float yb[16], db3[16], kb[7][16];
 #pragma unroll
   for (int r = 0; r < C; ++r) {
@@ -1430,7 +1438,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
     const size_t o = (size_t)i * a.slots + n;
     tn = a.tp_t[o];
     h = a.tp_h[o];
-    tnext = (n == N - 1) ? a.t1[i] : tn + (double)h;
+    tnext = (n == N - 1) ? flip(a.t1[i], rmask) : tn + (double)h;
     act = true;
   };
   // Y_s of the step being reversed: Y_1 = y_n, Y_2..Y_7 as the forward recorded
@@ -1452,9 +1460,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
       if (finishing) {
         const int i = inst;
         if (!bad && a.gye) {
-          const long long k0 = tkey(a.t0[i]);
+          const long long k0 = tkey(flip(a.t0[i], rmask));
           for (; q >= 0; --q)
-            if (tkey(a.te[(size_t)i * a.K + q]) == k0)
+            if (tkey(flip(a.te[(size_t)i * a.K + q], rmask)) == k0)
 #pragma unroll
               for (int r = 0; r < C; ++r) yb[r] += a.gye[((size_t)i * a.K + q) * D + coff + r];
         }
@@ -1470,6 +1478,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
       const int i = inst;
       N = a.n_acc[i];
       bad = a.status[i] != ST_SUCCESS;
+      rmask = (a.t1[i] < a.t0[i]) ? SIGN_BIT : 0ULL;
       if (!bad && N > a.slots) {
         bad = true;
         if (half == 0) atomicExch(a.overflow, 1);
@@ -1578,7 +1587,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
         for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
       const long long kt = tkey(tn), kn = tkey(tnext);
       while (q >= 0) {
-        const double tq = a.te[(size_t)i * a.K + q];
+        const double tq = flip(a.te[(size_t)i * a.K + q], rmask);
         const long long kq = tkey(tq);
         if (!(kq > kt)) break;
         if (a.gye) {
@@ -1603,8 +1612,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
     }
     if (act) {
       load_stage(s, Y);
-      tin = (float)(tn + dp_c(s) * (double)h);
+      tin = (float)flip(tn + dp_c(s) * (double)h, rmask);  // the caller's time
       pick7(kb, s - 1, d3);
+      if (rmask) {  // the field in tau is -f: its products take -kbar
+#pragma unroll
+        for (int r = 0; r < C; ++r) d3[r] = -d3[r];
+      }
     } else {
 #pragma unroll
       for (int r = 0; r < C; ++r) Y[r] = d3[r] = 0.0f;
@@ -1750,7 +1763,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
       float kbs[16];
       pick7(kb, s - 1, kbs);
 #pragma unroll
-      for (int r = 0; r < C; ++r) db3[r] += kbs[r];
+      for (int r = 0; r < C; ++r) db3[r] += rmask ? -kbs[r] : kbs[r];
 #pragma unroll
       for (int j = 0; j < 6; ++j) {  // kbar_j += h a_{s,j} g  (j < s)
         if (j + 1 >= s) continue;
@@ -2005,6 +2018,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
   // ---- this row's instance (one per row and slice) and its reverse state
   const int pos = a.i0 + (int)blockIdx.x * ROWS + row;
   const int inst = pos < a.i0 + a.B ? a.order[pos] : -1;
+  // backward in time: the row runs in tau = -t with the field -f
+  const unsigned long long rmask = (inst >= 0 && a.t1[inst] < a.t0[inst]) ? SIGN_BIT : 0ULL;
   bool act = false, bad = false;
   int n = -1, N = 0, q = -1;
   double tn = 0.0, tnext = 0.0;
@@ -2020,7 +2035,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     const size_t o = (size_t)inst * a.slots + n;
     tn = a.tp_t[o];
     h = a.tp_h[o];
-    tnext = (n == N - 1) ? a.t1[inst] : tn + (double)h;
+    tnext = (n == N - 1) ? flip(a.t1[inst], rmask) : tn + (double)h;
   };
   // Y_s of the step being reversed: Y_1 = y_n, Y_2..Y_7 as the forward recorded
   auto load_stage = [&](int s_, float (&Yo)[16]) {
@@ -2037,9 +2052,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
   // the instance is done: cotangents of points at t0, then dL/dy0
   auto finish = [&]() {
     if (!bad && a.gye) {
-      const long long k0 = tkey(a.t0[inst]);
+      const long long k0 = tkey(flip(a.t0[inst], rmask));
       for (; q >= 0; --q)
-        if (tkey(a.te[(size_t)inst * a.K + q]) == k0)
+        if (tkey(flip(a.te[(size_t)inst * a.K + q], rmask)) == k0)
 #pragma unroll
           for (int r = 0; r < C; ++r) yb[r] += a.gye[((size_t)inst * a.K + q) * D + coff + r];
     }
@@ -2234,7 +2249,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
         for (int r = 0; r < C; ++r) kb[j][r] = h * bw[j] * yb[r];
       const long long kt = tkey(tn), kn = tkey(tnext);
       while (q >= 0) {
-        const double tq = a.te[(size_t)inst * a.K + q];
+        const double tq = flip(a.te[(size_t)inst * a.K + q], rmask);
         const long long kk = tkey(tq);
         if (!(kk > kt)) break;
         if (a.gye) {
@@ -2259,8 +2274,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     }
     if (act) {
       load_stage(s, Y);
-      tin = (float)(tn + dp_c(s) * (double)h);
+      tin = (float)flip(tn + dp_c(s) * (double)h, rmask);  // the caller's time
       pick7(kb, s - 1, kq);
+      if (rmask) {  // the field in tau is -f: its products take -kbar
+#pragma unroll
+        for (int r = 0; r < C; ++r) kq[r] = -kq[r];
+      }
     } else {
 #pragma unroll
       for (int r = 0; r < C; ++r) Y[r] = kq[r] = 0.0f;

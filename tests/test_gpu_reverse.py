@@ -150,11 +150,3 @@ def test_backward_joint_matches_oracle():
     assert (g["trace_h"][0, :L] < 0).all()
     np.testing.assert_allclose(g["trace_h"][0, :L], o["trace_h"], rtol=1e-11, atol=1e-11)
     assert _rel_close(g["y_eval"], o["y_eval"], 1e-10).all()
-
-
-def test_backward_is_refused_per_instance_for_the_mlp():
-    w = dict(make(4, B=8), split=True)
-    t0, t1 = w["t1"].copy(), w["t0"].copy()
-    te = w["t_eval"][:, ::-1].copy()
-    g = gpu_solve(dict(w, t0=t0, t1=t1, t_eval=te), torch.float32, "fused")
-    assert (g["status"] == 4).all() and np.isnan(g["y_eval"]).all()

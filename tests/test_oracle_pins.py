@@ -809,3 +809,49 @@ def test_t_bounds_gradient_matches_frozen_mesh_differences(case):
                                want_t_bounds=True)
             ident = -(gye * yp).sum(axis=(1, 2))
             assert np.allclose(a["gt0"] + a["gt1"], ident, rtol=1e-9, atol=1e-9)
+
+
+def _negated_mlp(field):
+    """g(s, y) = -f(-s, y) as an MLP: the time column of the first layer and
+    the output layer (weights and bias) negated; IEEE negation is exact."""
+    W = [w.copy() for w in field["W"]]
+    b = [x.copy() for x in field["b"]]
+    D = W[-1].shape[0]
+    W[0][:, D] = -W[0][:, D]
+    W[-1] = -W[-1]
+    b[-1] = -b[-1]
+    return dict(field, W=W, b=b)
+
+
+def test_mlp_backward_in_time_is_forward_with_the_negated_network():
+    """The MLP field integrated backward (t1 < t0) is, bit for bit, the
+    negated network integrated forward in s = -t (the same method with
+    negative steps): outputs, statistics and the mesh; the adjoint on that
+    mesh likewise (the weight gradients of the negated layers negated)."""
+    w = workloads.make(4, B=4)
+    B = w["y0"].shape[0]
+    t0, t1 = w["t1"].copy(), w["t0"].copy()  # from 1 down to 0
+    te = np.ascontiguousarray(w["t_eval"][:, ::-1])
+    opts = dict(rtol=1e-6, atol=1e-6)
+    b = oracle.solve(w["field"], w["y0"], t0, t1, te, opts, trace_cap=2000)
+    g = _negated_mlp(w["field"])
+    f = oracle.solve(g, w["y0"], -t0, -t1, np.ascontiguousarray(-te), opts, trace_cap=2000)
+    assert (b["status"] == 0).all()
+    for k in ("y_eval", "y_final", "n_acc", "n_rej", "n_feval"):
+        assert np.array_equal(b[k], f[k]), k
+    L = b["trace_len"]
+    for i in range(B):
+        assert np.array_equal(b["trace_h"][i, :L[i]], -f["trace_h"][i, :L[i]])
+        assert np.array_equal(b["trace_t"][i, :L[i]], -f["trace_t"][i, :L[i]])
+    mt, mh, mn = mesh_from_trace(b)
+    rng = np.random.default_rng(3)
+    gye = rng.standard_normal(b["y_eval"].shape)
+    ab = oracle.adjoint(w["field"], w["y0"], t0, t1, mt, mh, mn, te, gye)
+    mt2, mh2, mn2 = mesh_from_trace(f)
+    af = oracle.adjoint(g, w["y0"], -t0, -t1, mt2, mh2, mn2, np.ascontiguousarray(-te), gye)
+    assert np.array_equal(ab["gy0"], af["gy0"])
+    D = w["y0"].shape[1]
+    assert np.array_equal(ab["gW"][1], af["gW"][1])
+    assert np.array_equal(ab["gW"][2], -af["gW"][2]) and np.array_equal(ab["gb"][2], -af["gb"][2])
+    assert np.array_equal(ab["gW"][0][:, :D], af["gW"][0][:, :D])
+    assert np.array_equal(ab["gW"][0][:, D], -af["gW"][0][:, D])
