@@ -345,10 +345,10 @@ class Workload:
             opt["order"] = args.order
         self.opt, self.opt_plain = dict(opt), dict(opt)
         self.tuned = self.tuned_plain = None
-        if args.launch and not self.mlp:
+        if args.launch:
             self.tuned = _launch_opts(args.launch)
             self.opt.update(self.tuned)
-        elif not args.no_autotune and not self.mlp:
+        elif not args.no_autotune:
             # the launch shape (lanes per instance, CTA size, resident CTAs,
             # work order; for the plain form its poll interval) the
             # autotuner picks for this batch, timed on it (fwd + adjoint)

@@ -116,13 +116,16 @@ typedef struct {
   int block;                  /* threads per block (multiple of 32, <= 256; 0 = 128, or
                                  fewer when the batch has under 128 threads per SM);
                                  Van der Pol and linear: tode_solve and tode_adjoint */
-  int ctas_per_sm;            /* fused form: resident CTAs per SM */
+  int ctas_per_sm;            /* fused form: resident CTAs per SM; MLP field, wide
+                                 network: tode_adjoint's slices of instances as
+                                 a multiple (1..4, 0 = 1) of one CTA per SM */
   int poll_every;             /* plain form: steps between host polls */
-  /* work order of the Van der Pol and linear solvers (both forms):
-   * 0 = index order, 1 = longest integration interval t1 - t0 first (lane
-   * groups that share a warp then tend to take similar step counts and long
-   * instances start early, but a warp's per-instance stores scatter).
-   * Results do not depend on it; the autotuner tries both. */
+  /* work order of the solvers (both forms, every field): 0 = index order,
+   * 1 = longest integration interval |t1 - t0| first (lane groups that
+   * share a warp then tend to take similar step counts, and long instances
+   * start early so the persistent grid's tail shortens; a warp's
+   * per-instance stores scatter).  Results do not depend on it; the
+   * autotuner tries both. */
   int order;
   /* 0 = every instance solved independently (Sec. 3).  1 = joint
    * ("stacked") solving, the semantics Sec. 4.1 compares against: the batch

@@ -216,7 +216,7 @@ size_t tode_adjoint_scratch_size(const tode_field_desc* f, const tode_options* o
     // sized for one CTA per SM of the current device (at least one SM)
     const int sms = sm_count_or_zero();
     return (tape->stride == 1 && o->prec == TODE_BF16W_SPLIT)
-               ? mlp_adjoint_scratch_bytes(f, tape->slots, sms > 0 ? sms : 1)
+               ? mlp_adjoint_scratch_bytes(f, o, tape->slots, sms > 0 ? sms : 1)
                : 0;
   }
   return simt_adjoint_scratch_bytes(f->B, f->D, state_size(o), tape->stride);

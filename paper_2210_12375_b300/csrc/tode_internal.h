@@ -154,7 +154,8 @@ bool simt_supported(int kind, int D);
 bool mlp_supported(const tode_field_desc* f);
 size_t mlp_workspace_bytes(const tode_field_desc* f, const tode_options* o);
 tode_err mlp_solve(const SolveReq& r, bool split);
-size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, int slots, int num_sms);
+size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, const tode_options* o, int slots,
+                                 int num_sms);
 tode_err mlp_adjoint(const AdjReq& r);
 
 }  // namespace tode

@@ -72,6 +72,8 @@ struct MlpArgs {
   int32_t* wcur;
   int32_t* wfl;
   int32_t* active;
+  // work order: the instance at queue position q (nullptr: q itself)
+  const int32_t* order;
 };
 
 // Kernel modes of the MLP solver body: the fused persistent form, and the
@@ -638,7 +640,8 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       __syncthreads();
       if (need_grab) {
         need_grab = false;
-        const int i = sNxt[row];
+        const int q = sNxt[row];
+        const int i = q >= a.B ? a.B : (a.order ? a.order[q] : q);
         if (i >= a.B) {
           s.phase = PH_IDLE;
           s.inst = -1;
@@ -648,7 +651,8 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       }
     } else if (need_load) {
       need_load = false;
-      const int i = tile * ROWS + row;
+      const int q = tile * ROWS + row;
+      const int i = q >= a.B ? a.B : (a.order ? a.order[q] : q);
       s.phase = PH_IDLE;
       s.inst = -1;
       if (i < a.B) {
@@ -3627,7 +3631,9 @@ bool mlp_supported(const tode_field_desc* f) {
 size_t mlp_workspace_bytes(const tode_field_desc* f, const tode_options* o) {
   const size_t img = is_d64_h512(f) ? (size_t)Cfg64s::WREP * Cfg64s::WIMG_STRIDE
                                     : (size_t)Cfg32::WREP * Cfg32::WIMG_STRIDE;
-  size_t b = align256(256) + img;
+  // counters, images, the work order and its sort's per-CTA counts
+  size_t b = align256(256) + img + align256((size_t)std::max(f->B, 1) * 4) +
+             order_part_bytes(f->B);
   if (o->form == TODE_PLAIN) {  // parked solver state (must match launch_mlp)
     const size_t B = (size_t)f->B, D = (size_t)f->D;
     b += 3 * align256(B * D * 4) + align256(B * 8) + 5 * align256(B * 4);
@@ -3691,6 +3697,17 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   unsigned char* img = (unsigned char*)p;
   a.wimg = img;
   p += (size_t)Cfg::WREP * Cfg::WIMG_STRIDE;
+  int32_t* order = (int32_t*)p;
+  p += align256((size_t)std::max(r.B, 1) * 4);
+  int* order_part = (int*)p;
+  p += order_part_bytes(r.B);
+  a.order = nullptr;
+  if (r.o->order == 1 && r.B > 0) {
+    // the longest integration intervals first (rows refill from the queue,
+    // so the long instances start early and the tail shortens)
+    TODE_CUDA_TRY(launch_order(r.B, IntervalBin{r.t0, r.t1}, order, order_part, r.stream));
+    a.order = order;
+  }
   if (r.o->form == TODE_PLAIN) {
     const size_t B = (size_t)r.B, D = (size_t)r.D;
     a.wy = (float*)p;
@@ -3840,9 +3857,18 @@ static WidePlan wide_plan(int B, int slots, int num_sms) {
   return p;
 }
 
-size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, int slots, int num_sms) {
+// The wide adjoint's slices hold mult x (SMs x 64) instances (tode_options
+// ctas_per_sm, 1..4; default 1): larger slices mean fewer, larger weight-
+// gradient passes and more staging memory; the chain CTAs past one per SM
+// queue for a free SM.  Results do not depend on it.
+static int wide_slice_mult(const tode_options* o) {
+  return (o && o->ctas_per_sm > 0) ? std::min(o->ctas_per_sm, 4) : 1;
+}
+
+size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, const tode_options* o, int slots,
+                                 int num_sms) {
   using L = MlpAdjLayout<Cfg32s>;
-  if (is_d64_h512(f)) return wide_plan(f->B, slots, num_sms).total;
+  if (is_d64_h512(f)) return wide_plan(f->B, slots, num_sms * wide_slice_mult(o)).total;
   if (!is_d32_h128(f)) return 0;
   const long long grid = std::min<long long>((f->B + 127) / 128, num_sms);
   return align256(256) + align256((size_t)Cfg32s::WIMG_BYTES) +
@@ -3855,7 +3881,7 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   using Cfg = Cfg64s;
   using L = WideAdj<Cfg>;
   const cudaStream_t st = r.stream;
-  const WidePlan p = wide_plan(r.B, r.tape->slots, r.num_sms);
+  const WidePlan p = wide_plan(r.B, r.tape->slots, r.num_sms * wide_slice_mult(r.o));
   if (r.scratch_bytes < p.total) return TODE_EWORKSPACE;
   char* base = r.scratch;
   WideAdjArgs a{};

@@ -1,4 +1,4 @@
-"""Launch-shape autotuner for the SIMT solver kernels.
+"""Launch-shape autotuner for the solver kernels.
 
 The fused persistent kernel and its adjoint take three launch knobs
 (``tode_options``): ``group`` (lanes per instance of the linear field),
@@ -18,7 +18,10 @@ Different ``group`` values change the FP32 summation order of the error
 norm, so results of different candidates agree to rounding, not bit for bit;
 the adjoint must run with the forward's options (it re-runs the forward's
 attempts when the tape is strided).  The MLP field's tiles are fixed by its
-network shape and have no knobs here.
+network shape (tensor-memory lanes, shared memory); its knobs are the work
+order of the persistent grid and, for the wide network's adjoint, the size
+of the slices the adjoint stages (``ctas_per_sm``: 1 or 2 CTAs' worth of
+instances per SM); its results do not depend on either.
 """
 from __future__ import annotations
 
@@ -77,10 +80,16 @@ def cache_key(kind: str, D: int, B: int, prec: str, form: str, with_adjoint: boo
     return f"{device_name}|{kind}|D{D}|B{b2}|{prec}|{form}|{'adj' if with_adjoint else 'fwd'}"
 
 
-def candidates(kind: str, D: int, form: str) -> List[dict]:
+def candidates(kind: str, D: int, form: str, with_adjoint: bool = False) -> List[dict]:
     """The launch shapes tried for a field (each a dict of tode_options keys)."""
     if kind == "mlp":
-        return [{}]
+        # the MLP tiles are fixed by the network (tensor-memory lanes, shared
+        # memory); what varies is the instances' order on the persistent
+        # grid and, for the wide network's adjoint, the size of its slices
+        out = [{"order": o} for o in (0, 1)]
+        if with_adjoint and D == 64:
+            out = [dict(x, ctas_per_sm=m) for x in out for m in (1, 2)]
+        return out
     groups = [0]
     if kind == "linear":
         groups = {16: [4, 8, 16], 32: [16]}.get(D, [D])
@@ -145,7 +154,7 @@ def autotune(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
             if key in disk:
                 _mem[key] = disk[key]
                 return dict(disk[key]["options"])
-        cands = candidates(kind, D, form)
+        cands = candidates(kind, D, form, with_adjoint)
         if timer is None:
             tape = None
             if with_adjoint:

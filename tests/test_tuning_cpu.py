@@ -24,7 +24,9 @@ def test_candidates_cover_the_knobs():
     assert {o["ctas_per_sm"] for o in c} == {0, 1, 2, 4}
     assert {o["order"] for o in c} == {0, 1}
     assert all("poll_every" in o for o in at.candidates("vdp", 2, "plain"))
-    assert at.candidates("mlp", 32, "fused") == [{}]
+    assert at.candidates("mlp", 32, "fused") == [{"order": 0}, {"order": 1}]
+    wide = at.candidates("mlp", 64, "fused", with_adjoint=True)
+    assert {(o["order"], o["ctas_per_sm"]) for o in wide} == {(0, 1), (0, 2), (1, 1), (1, 2)}
 
 
 def test_autotune_picks_fastest_and_caches(tmp_path):
