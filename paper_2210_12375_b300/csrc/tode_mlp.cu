@@ -298,20 +298,26 @@ __device__ __forceinline__ float tanh_fast(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-// tanh(x) = sign(x) (1 - e) / (1 + e), e = exp(-2|x|); absolute error ~1e-7
-__device__ __forceinline__ float tanh_acc(float x) {
-  const float e = __expf(-2.0f * fabsf(x));
-  return copysignf(__fdividef(1.0f - e, 1.0f + e), x);
+// tanh of two values as 1 - 2 / (1 + e^(2x)): one ex2 of 2x log2(e) and one
+// reciprocal (MUFU), the rest in FP32x2 pairs; no sign fix-up is needed
+// (e^(2x) -> inf gives 1, -> 0 gives -1, x = 0 gives 0 exactly).  Absolute
+// error ~2e-7, below the hi + lo split of the activation (~16 bits).
+__device__ __forceinline__ float ex2_mufu(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
-
-// tanh_acc of two values, the additions packed in pairs (FP32x2 operations
-// round each lane as the scalar ones: the same results, half the additions).
+__device__ __forceinline__ float rcp_mufu(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float2 tanh_acc2(float2 z) {
-  const float2 e = make_float2(__expf(-2.0f * fabsf(z.x)), __expf(-2.0f * fabsf(z.y)));
-  const float2 num = __ffma2_rn(e, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));  // 1 - e
-  const float2 den = __fadd2_rn(e, make_float2(1.0f, 1.0f));                           // 1 + e
-  return make_float2(copysignf(__fdividef(num.x, den.x), z.x),
-                     copysignf(__fdividef(num.y, den.y), z.y));
+  constexpr float k2log2e = 2.8853900817779268f;  // 2 / ln 2
+  const float2 s = __fmul2_rn(z, make_float2(k2log2e, k2log2e));
+  const float2 d = __fadd2_rn(make_float2(ex2_mufu(s.x), ex2_mufu(s.y)), make_float2(1.0f, 1.0f));
+  return __ffma2_rn(make_float2(rcp_mufu(d.x), rcp_mufu(d.y)), make_float2(-2.0f, -2.0f),
+                    make_float2(1.0f, 1.0f));
 }
 
 // Stores 16 consecutive values of a row as BF16 (hi, and lo = x - hi) into
