@@ -2198,12 +2198,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
   // replaces the tile and is staged
   auto epi_delta = [&](int t_h, bool h_in_tile, int t_del) {
     const int fw = L::fb_width(t_h);
-#pragma unroll 1
-    for (int c = 0; c < 256; c += 32) {
-      float v0[16], v1[16];
-      tc::tmem_ld16(tbase + lanes + 256 * hf + c, v0);
-      tc::tmem_ld16(tbase + lanes + 256 * hf + c + 16, v1);
-      uint4 hh[2], hl[2];
+    // h of columns [c, c + 32) of this lane: from the tile, or from its
+    // staged rows in global memory -- those are fetched one iteration ahead,
+    // so that their latency overlaps the previous columns' arithmetic
+    auto ld_h = [&](int c, uint4 (&hh)[2], uint4 (&hl)[2]) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int col = 256 * hf + c + 16 * u + 8 * odd;
@@ -2217,6 +2215,22 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
           hh[u] = *reinterpret_cast<const uint4*>(src);
           hl[u] = *reinterpret_cast<const uint4*>(src + L::blk_bytes(t_h));
         }
+      }
+    };
+    uint4 nh[2], nl[2];
+    if (!h_in_tile) ld_h(0, nh, nl);
+#pragma unroll 1
+    for (int c = 0; c < 256; c += 32) {
+      float v0[16], v1[16];
+      tc::tmem_ld16(tbase + lanes + 256 * hf + c, v0);
+      tc::tmem_ld16(tbase + lanes + 256 * hf + c + 16, v1);
+      uint4 hh[2], hl[2];
+      if (h_in_tile) {
+        ld_h(c, hh, hl);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) hh[u] = nh[u], hl[u] = nl[u];
+        if (c + 32 < 256) ld_h(c + 32, nh, nl);
       }
       tc::tmem_wait_ld();
 #pragma unroll
