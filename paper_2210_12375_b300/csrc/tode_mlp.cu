@@ -1195,19 +1195,34 @@ __global__ void __launch_bounds__(256, 1) k_mlp_plain_step(MlpArgs a) {
 
 // The BF16 weights W_l [N_l][K_in,l] (row-major) as core-matrix images with
 // K padded to K_l, for all layers and all copies in one launch.  Layouts:
-//   IMG_TILE    one [N_l][K_l] tile per layer (weights resident in shared memory)
-//   IMG_CHUNKS  K_l/16 consecutive [N_l][16] tiles (the streamed K chunks)
-//   IMG_TCHUNKS N_l/16 consecutive MN-major [16][K_l] tiles: W_l^T in K chunks
-//               along the layer's outputs (the transposed products)
-enum : int { IMG_TILE = 0, IMG_CHUNKS = 1, IMG_TCHUNKS = 2 };
+//   IMG_TILE     one [N_l][K_l] tile per layer (weights resident in shared memory)
+//   IMG_CHUNKS   K_l/16 consecutive [N_l][16] tiles (the streamed K chunks)
+//   IMG_CHUNKS2  IMG_CHUNKS split in two half images (`half` bytes apart) for
+//                a CTA pair: an M = 256 product of width NW = min(N_l, 256)
+//                takes columns [NW j, NW j + NW/2) from CTA 0 and the next
+//                NW/2 from CTA 1, so half r of chunk c holds those rows of
+//                every product j, as [N_l/2][16] (rows NW/2 j .. of product j)
+//   IMG_TCHUNKS2 W_l^T in K chunks along the layer's outputs for a CTA pair:
+//                half r of chunk c is an MN-major [16][K_l/2] tile of outputs
+//                16c .. 16c+15, its inputs split as in IMG_CHUNKS2
+enum : int { IMG_TILE = 0, IMG_CHUNKS = 1, IMG_CHUNKS2 = 2, IMG_TCHUNKS2 = 3 };
 struct ImageJob {
   const uint16_t* W[MLP_MAX_LAYERS];
   int N[MLP_MAX_LAYERS], Kin[MLP_MAX_LAYERS], Kp[MLP_MAX_LAYERS];
-  size_t off[MLP_MAX_LAYERS];      // layer offset inside one copy
+  size_t off[MLP_MAX_LAYERS];      // layer offset inside one copy (one half)
   long long start[MLP_MAX_LAYERS + 1];  // element ranges of the layers
   int nl, reps, mode;
   size_t stride;  // bytes between copies
+  size_t half;    // bytes between the two halves of a pair image
 };
+// (product, CTA, row inside the CTA's part) of index x along a pair
+// product's N of width n_total
+__device__ __forceinline__ void pair_split(int x, int n_total, int& r, int& xr) {
+  const int nw = n_total < 256 ? n_total : 256, hw = nw / 2;
+  const int j = x / nw, p = x - j * nw;
+  r = p / hw;
+  xr = j * hw + (p - r * hw);
+}
 __global__ void k_mlp_images(ImageJob j, unsigned char* img) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= j.start[j.nl]) return;
@@ -1217,10 +1232,20 @@ __global__ void k_mlp_images(ImageJob j, unsigned char* img) {
   const int Kp = j.Kp[l], N = j.N[l];
   const int n = (int)(x / Kp), k = (int)(x % Kp);
   const uint16_t v = k < j.Kin[l] ? j.W[l][(size_t)n * j.Kin[l] + k] : (uint16_t)0;
-  uint32_t off;
-  if (j.mode == IMG_TILE) off = tc::cm_offset(n, k, Kp);
-  else if (j.mode == IMG_CHUNKS) off = (uint32_t)(k / 16) * (uint32_t)N * 32u + tc::cm_offset(n, k % 16, 16);
-  else off = (uint32_t)(n / 16) * 16u * (uint32_t)Kp * 2u + tc::cm_offset(n % 16, k, Kp);
+  size_t off;
+  if (j.mode == IMG_TILE) {
+    off = tc::cm_offset(n, k, Kp);
+  } else if (j.mode == IMG_CHUNKS) {
+    off = (size_t)(k / 16) * (size_t)N * 32u + tc::cm_offset(n, k % 16, 16);
+  } else if (j.mode == IMG_CHUNKS2) {
+    int r, nr;
+    pair_split(n, N, r, nr);
+    off = (size_t)r * j.half + (size_t)(k / 16) * (size_t)N * 16u + tc::cm_offset(nr, k % 16, 16);
+  } else {
+    int r, kr;
+    pair_split(k, Kp, r, kr);
+    off = (size_t)r * j.half + (size_t)(n / 16) * 16u * (size_t)Kp + tc::cm_offset(n % 16, kr, Kp / 2);
+  }
   for (int r = 0; r < j.reps; ++r)
     *reinterpret_cast<uint16_t*>(img + (size_t)r * j.stride + j.off[l] + off) = v;
 }
@@ -1230,12 +1255,13 @@ __global__ void k_mlp_images(ImageJob j, unsigned char* img) {
 template <class Cfg>
 static tode_err build_images(const tode_field_desc* f, unsigned char* img, int mode, int reps,
                              size_t stride, const size_t (&layer_off)[MLP_MAX_LAYERS],
-                             cudaStream_t st) {
+                             cudaStream_t st, size_t half = 0) {
   ImageJob j{};
   j.nl = Cfg::NL;
   j.reps = reps;
   j.mode = mode;
   j.stride = stride;
+  j.half = half;
   j.start[0] = 0;
   for (int l = 0; l < Cfg::NL; ++l) {
     j.W[l] = (const uint16_t*)f->W[l];
@@ -1857,6 +1883,15 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 // features -- and k_mlp_dw forms the products from them afterwards.  A row
 // whose instance is done runs on zeros: its kbar and hence every delta is
 // 0, so its staged rows add nothing.
+//
+// The chain runs on CTA pairs (2-CTA clusters): the pair's MMAs are
+// M = 256 over both CTAs' stacked tiles, issued by CTA 0, and each CTA
+// streams only its half of every weight chunk (IMG_CHUNKS2 / IMG_TCHUNKS2),
+// so a stage carries twice the tensor work per byte an SM receives.  Per
+// stage CTA 1 forwards the arrival of its half to CTA 0; per product CTA 1
+// reports its tile written; CTA 0's commits arrive in both CTAs.  Both CTAs
+// run the same rounds: the pair stops when neither has a row left (the
+// shorter tile's rows run on zeros meanwhile).
 // ======================================================================
 template <class Cfg> struct WideAdj {
   static constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, ROWS = Cfg::ROWS;
@@ -1873,12 +1908,15 @@ template <class Cfg> struct WideAdj {
   static_assert(S_END <= 232448 - 1024, "shared memory");
   // the round's weight stream: segments 0-2 the forward chunks of layers
   // 0-2 ([N][16] K-major), segments 3-6 the transposed chunks of layers 3,
-  // 2, 1, 0 ([16 outputs][K] MN-major); both images hold layer l at W_off(l)
+  // 2, 1, 0 ([16 outputs][K] MN-major); a CTA streams its half of each
+  // chunk, from the half image that holds layer l at W_off(l) / 2
   static constexpr int NSEG = 7;
+  static constexpr size_t HALF_BYTES = Cfg::WIMG_BYTES / 2;
+  static_assert(HALF_BYTES % 16 == 0, "bulk copies");
   __host__ __device__ static constexpr int seg_layer(int q) { return q < 3 ? q : 6 - q; }
   __host__ __device__ static constexpr bool seg_tr(int q) { return q >= 3; }
-  __host__ __device__ static constexpr int seg_chunk_bytes(int q) {
-    return q < 3 ? Cfg::N_of(q) * 16 * 2 : 16 * Cfg::K_of(seg_layer(q)) * 2;
+  __host__ __device__ static constexpr int seg_chunk_bytes(int q) {  // one CTA's half
+    return q < 3 ? Cfg::N_of(q) * 16 : 16 * Cfg::K_of(seg_layer(q));
   }
   __host__ __device__ static constexpr int seg_chunks(int q) {
     return q < 3 ? Cfg::K_of(q) / 16 : Cfg::N_of(seg_layer(q)) / 16;
@@ -1901,7 +1939,7 @@ template <class Cfg> struct WideAdj {
     c0 = st * seg_per_stage(q);
     nc = seg_chunks(q) - c0 < seg_per_stage(q) ? seg_chunks(q) - c0 : seg_per_stage(q);
     bytes = nc * seg_chunk_bytes(q);
-    off = Cfg::W_off(seg_layer(q)) + c0 * seg_chunk_bytes(q);
+    off = Cfg::W_off(seg_layer(q)) / 2 + c0 * seg_chunk_bytes(q);
   }
   // staged tensors; each splits into planes of (up to) 128 features, and a
   // plane holds one block pair (hi, lo) per (chain CTA, reverse round)
@@ -1939,8 +1977,8 @@ struct WideAdjArgs {
   const float* gye;
   const float* gyf;
   float* gy0;
-  const unsigned char* wimg;     // forward chunk image (copies WIMG_STRIDE apart)
-  const unsigned char* timg;     // transposed chunk image (same strides)
+  const unsigned char* wimg;     // forward chunk pair image (copies WIMG_STRIDE apart)
+  const unsigned char* timg;     // transposed chunk pair image (same strides)
   const float* bias[MLP_MAX_LAYERS];
   unsigned char* plane[32];      // staging planes (WideAdj::NPLANES used)
   int cap;                       // reverse rounds per CTA the planes hold
@@ -1962,15 +2000,22 @@ __device__ __forceinline__ void unsplit8(const uint4& hi, const uint4& lo, float
 }
 
 template <class Cfg>
-__global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
+    k_mlp_adjoint_wide(WideAdjArgs a) {
   using L = WideAdj<Cfg>;
   using Cc = DP5;
   constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, ROWS = Cfg::ROWS;
   constexpr int NSL = L::NSL;
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mbar_mma, mbar_full[NSL], mbar_empty[NSL];
+  // mbar_full: this CTA's half of a stage landed; mbar_pfull (CTA 0): CTA 1's
+  // half landed; mbar_tile (CTA 0): CTA 1's tile is written for the next
+  // product; mbar_empty / mbar_mma: the pair's MMAs of a stage / a product
+  // are done (arrive in both CTAs); mbar_fin: CTA 0's last MMAs are done
+  __shared__ __align__(8) uint64_t mbar_mma, mbar_full[NSL], mbar_empty[NSL], mbar_pfull[NSL],
+      mbar_tile, mbar_fin;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
+  __shared__ int pair_flag[2];
   unsigned char* sX = sm + L::S_X;  // input tile, then the kbar tile
   unsigned char* sH = sm + L::S_H;
   unsigned char* sW = sm + L::S_W;
@@ -1980,9 +2025,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
   const int row = Cfg::row_of(tid), sub = Cfg::sub_of(tid);
   const int coff = sub * C;
   const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
-  const unsigned char* wimg = a.wimg + (size_t)(blockIdx.x % Cfg::WREP) * Cfg::WIMG_STRIDE;
-  const unsigned char* timg = a.timg + (size_t)(blockIdx.x % Cfg::WREP) * Cfg::WIMG_STRIDE;
+  const uint32_t rank = tc::cluster_rank();
+  const size_t rep = (size_t)((blockIdx.x >> 1) % Cfg::WREP) * Cfg::WIMG_STRIDE + rank * L::HALF_BYTES;
+  const unsigned char* wimg = a.wimg + rep;
+  const unsigned char* timg = a.timg + rep;
   uint32_t g_stage = 0;  // weight stages consumed so far
+  uint32_t tile_par = 0;  // products issued so far (parity of mbar_tile)
 
   auto issue_stage = [&](uint32_t g, int slot) {
     int q, c0, nc, off, bytes;
@@ -1996,7 +2044,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     for (int b = 0; b < NSL; ++b) {
       tc::mbar_init(&mbar_full[b], 1);
       tc::mbar_init(&mbar_empty[b], 1);
+      tc::mbar_init(&mbar_pfull[b], 1);
     }
+    tc::mbar_init(&mbar_tile, 1);
+    tc::mbar_init(&mbar_fin, 1);
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -2014,10 +2065,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
   }
   for (int j = tid; j < 2 * ROWS * K0 * 2 / 16; j += 256)
     reinterpret_cast<uint4*>(sX)[j] = make_uint4(0, 0, 0, 0);
-  if (warp == 0) {
-    tc::tmem_alloc(&tmem_base_s, 512);
-    tc::tmem_relinquish();
-  }
+  // both CTAs run and their barriers are initialised before any arrival
+  // crosses; the pair's tensor memory is allocated by a warp of each
+  tc::cluster_sync();
+  if (warp == 0) tc::tmem_alloc_pair(&tmem_base_s, 512);
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
@@ -2095,43 +2146,60 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     tc::fence_after_sync();
   };
   auto wait_mma = [&]() {
-    if (!tc::mbar_wait_sleep(&mbar_mma, parity)) atomicExch(&abort_s, 1);
+    if (!abort_s && !tc::mbar_wait_sleep(&mbar_mma, parity)) atomicExch(&abort_s, 1);
     parity ^= 1u;
     tc::fence_after_sync();
   };
-  // one GEMM of the round (segment qs): thread 0 issues M = 128 MMAs over
-  // the stacked A tile (K-major, Ka columns) as the stages arrive, thread 32
-  // refills each stage's slot with the stage NSL ahead once its MMAs are
-  // done.  N = 512 as two halves of 256, else one MMA of width Nl; the
-  // transposed chunks are MN-major [16][Nl] tiles.
+  // one product of the round (segment qs) on the pair.  CTA 0's thread 0
+  // waits for CTA 1's tile, then issues M = 256 MMAs over both stacked tiles
+  // (K-major, Ka columns) as both halves of each stage arrive; CTA 1's
+  // thread 0 reports its tile and forwards the arrival of each of its
+  // halves; thread 32 of each CTA refills its own slot with the stage NSL
+  // ahead once the pair's MMAs of the slot are done.  N > 256 runs as
+  // products of 256 (tensor-memory columns 256 j); a CTA's half of a chunk
+  // holds NW/2 columns of each (IMG_CHUNKS2 / IMG_TCHUNKS2).
   auto gemm = [&](int qs, uint32_t a_addr, int Ka, int Nl) {
     const bool tr = L::seg_tr(qs);
     if (tid == 0 && !abort_s) {
-      const int nh = Nl > 256 ? Nl / 256 : 1, nw = Nl > 256 ? 256 : Nl;
-      const uint32_t idesc = tc::idesc_bf16_f32(128, nw, false, tr);
-      const int cb = L::seg_chunk_bytes(qs);
       bool ok = true;
-      for (int st = 0; st < L::seg_stages(qs) && ok; ++st) {
-        const uint32_t g = g_stage + (uint32_t)st;
-        const int b = (int)(g % NSL);
-        ok = tc::mbar_wait(&mbar_full[b], (g / NSL) & 1u);
-        if (!ok) break;
-        int q_, c0, nc, off_, bytes_;
-        L::stage_of(g, q_, c0, nc, off_, bytes_);
-        const uint32_t wb = tc::smem_u32(sW + b * L::SLOT_BYTES);
-        for (int c = 0; c < nc; ++c) {
-          const int kc = c0 + c;
-          const uint64_t da = tc::smem_desc(a_addr + kc * 256, 128, Ka * 16);
-          for (int j = 0; j < nh; ++j) {
-            const uint64_t db = tr ? tc::smem_desc_mn(wb + c * cb + j * 4096, Nl * 16)
-                                   : tc::smem_desc(wb + c * cb + j * 8192, 128, 256);
-            tc::mma_bf16(tbase + 256 * j, da, db, idesc, kc > 0);
-          }
+      if (rank != 0) {
+        tc::mbar_arrive_peer(&mbar_tile, 0);
+        for (int st = 0; st < L::seg_stages(qs) && ok; ++st) {
+          const uint32_t g = g_stage + (uint32_t)st;
+          const int b = (int)(g % NSL);
+          ok = tc::mbar_wait(&mbar_full[b], (g / NSL) & 1u);
+          if (ok) tc::mbar_arrive_peer(&mbar_pfull[b], 0);
         }
-        tc::mma_commit(&mbar_empty[b]);
+      } else {
+        const int nh = Nl > 256 ? Nl / 256 : 1, nw = Nl > 256 ? 256 : Nl, hw = nw / 2;
+        const uint32_t idesc = tc::idesc_bf16_f32(256, nw, false, tr);
+        const int cb = L::seg_chunk_bytes(qs);
+        ok = tc::mbar_wait_cluster(&mbar_tile, tile_par);
+        tc::fence_after_sync();
+        for (int st = 0; st < L::seg_stages(qs) && ok; ++st) {
+          const uint32_t g = g_stage + (uint32_t)st;
+          const int b = (int)(g % NSL);
+          ok = tc::mbar_wait(&mbar_full[b], (g / NSL) & 1u) &&
+               tc::mbar_wait_cluster(&mbar_pfull[b], (g / NSL) & 1u);
+          if (!ok) break;
+          int q_, c0, nc, off_, bytes_;
+          L::stage_of(g, q_, c0, nc, off_, bytes_);
+          const uint32_t wb = tc::smem_u32(sW + b * L::SLOT_BYTES);
+          for (int c = 0; c < nc; ++c) {
+            const int kc = c0 + c;
+            const uint64_t da = tc::smem_desc(a_addr + kc * 256, 128, Ka * 16);
+            for (int j = 0; j < nh; ++j) {
+              const uint64_t db =
+                  tr ? tc::smem_desc_mn(wb + c * cb + j * (hw / 8) * 128, (Nl / 2) * 16)
+                     : tc::smem_desc(wb + c * cb + j * hw * 32, 128, 256);
+              tc::mma_bf16_pair(tbase + 256 * j, da, db, idesc, kc > 0);
+            }
+          }
+          tc::mma_commit_pair_both(&mbar_empty[b]);
+        }
+        tc::mma_commit_pair_both(&mbar_mma);
       }
       if (!ok) atomicExch(&abort_s, 1);
-      tc::mma_commit(&mbar_mma);
     } else if (tid == 32 && !abort_s) {
       bool ok = true;
       for (int st = 0; st < L::seg_stages(qs) && ok; ++st) {
@@ -2143,6 +2211,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
       if (!ok) atomicExch(&abort_s, 1);
     }
     g_stage += (uint32_t)L::seg_stages(qs);
+    tile_par ^= 1u;
     __syncwarp();
   };
   size_t blk = 0;  // this round's staging block
@@ -2251,15 +2320,29 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
 
   const float bw[7] = {float(Cc::b1), 0.0f, float(Cc::b3), float(Cc::b4), float(Cc::b5),
                        float(Cc::b6), 0.0f};
-  int k_round = 0;  // reverse rounds staged by this CTA
+  int k_round = 0;  // reverse rounds staged by this CTA (the same in both CTAs of the pair)
+  int n_check = 0;
   for (int rnd = 0;; ++rnd) {
     const int ph = rnd % ADJ_ROUNDS;
-    if (ph == 0 && __syncthreads_or(act) == 0) break;
-    if (abort_s) break;
-    const int s = 7 - ph;  // the stage reversed this round (block-uniform)
+    if (ph == 0) {
+      // the pair goes on while either CTA has a row left and neither gave up
+      // (abort_s is read after a barrier: block-uniform)
+      const int mine = __syncthreads_or(act) ? 1 : 0;
+      if (tid == 0) pair_flag[n_check & 1] = mine | (abort_s ? 2 : 0);
+      tc::cluster_sync();
+      const int f = pair_flag[n_check & 1] | tc::ld_peer_s32(&pair_flag[n_check & 1], rank ^ 1u);
+      ++n_check;
+      if (!(f & 1) || (f & 2)) break;
+    }
+    if (abort_s) continue;  // wind down to the pair's next check
+    const int s = 7 - ph;   // the stage reversed this round (block-uniform)
     if (k_round >= a.cap) {  // cannot happen: the planes hold 7 rounds per tape slot
-      if (tid == 0) atomicExch(a.err, 2);
-      break;
+      if (tid == 0) {
+        atomicExch(a.err, 2);
+        abort_s = 1;
+      }
+      __syncthreads();
+      continue;
     }
     blk = (size_t)blockIdx.x * a.cap + k_round;
 
@@ -2366,7 +2449,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (abort_s) break;
+    if (abort_s) continue;
 
     // ---- consume (row-local)
     if (!act) continue;
@@ -2390,11 +2473,17 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint_wide(WideAdjArgs a) {
     // the ring's copies still in flight (stages g .. g + NSL - 1) land before the CTA exits
     for (uint32_t x = g_stage; x < g_stage + NSL; ++x)
       if (!tc::mbar_wait(&mbar_full[x % NSL], (x / NSL) & 1u)) atomicExch(&abort_s, 1);
+    // and the pair's MMAs, which read both CTAs' shared memory, are done
+    if (rank == 0) {
+      tc::mma_commit_pair_local(&mbar_fin);
+      if (!tc::mbar_wait(&mbar_fin, 0)) atomicExch(&abort_s, 1);
+    }
+    if (abort_s) atomicExch(a.err, 1);
   }
-  if (abort_s && tid == 0) atomicExch(a.err, 1);
+  // neither CTA leaves while the other may still reach its shared memory
   tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+  tc::cluster_sync();
+  if (warp == 0) tc::tmem_dealloc_pair(tbase, 512);
 }
 
 // ---------------------------------------------------------------- dW, db
@@ -3853,6 +3942,7 @@ static WidePlan wide_plan(int B, int slots, int num_sms) {
   using L = WideAdj<Cfg>;
   WidePlan p{};
   p.grid = (int)std::min<long long>((B + 63) / 64, num_sms);
+  p.grid += p.grid & 1;  // CTA pairs
   p.cap = 7 * std::max(slots, 1);  // one instance per row per slice
   const size_t nblk = (size_t)std::max(p.grid, 1) * p.cap;
   size_t o = align256(256);
@@ -3938,13 +4028,16 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   for (int q = 0; q < L::NPLANES; ++q) d.plane[q] = a.plane[q];
   d.part = (float*)(base + p.off_part);
   d.err = a.err;
-  // weight images (forward chunks and transposed chunks, WREP copies each)
+  // weight images for the CTA pairs (forward and transposed chunks, two
+  // halves of WIMG_BYTES / 2 each, WREP copies)
   {
     size_t woff[MLP_MAX_LAYERS] = {};
-    for (int l = 0; l < Cfg::NL; ++l) woff[l] = Cfg::W_off(l);
-    tode_err e = build_images<Cfg>(r.f, img, IMG_CHUNKS, Cfg::WREP, Cfg::WIMG_STRIDE, woff, st);
+    for (int l = 0; l < Cfg::NL; ++l) woff[l] = Cfg::W_off(l) / 2;
+    tode_err e = build_images<Cfg>(r.f, img, IMG_CHUNKS2, Cfg::WREP, Cfg::WIMG_STRIDE, woff, st,
+                                   L::HALF_BYTES);
     if (e == TODE_OK)
-      e = build_images<Cfg>(r.f, timg, IMG_TCHUNKS, Cfg::WREP, Cfg::WIMG_STRIDE, woff, st);
+      e = build_images<Cfg>(r.f, timg, IMG_TCHUNKS2, Cfg::WREP, Cfg::WIMG_STRIDE, woff, st,
+                            L::HALF_BYTES);
     if (e != TODE_OK) return e;
   }
   TODE_CUDA_TRY(cudaMemsetAsync(base, 0, 256, st));
@@ -3960,11 +4053,30 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
     if (e == TODE_OK) e = smem_optin((const void*)k_mlp_dw<Cfg>, DW_SMEM, d1);
     if (e != TODE_OK) return e;
   }
-  const int slice = p.grid * 64;
+  // a slice's pairs all resident at once (one pair per two SMs the cluster
+  // scheduler can place, times the slice multiplier)
+  int grid = p.grid;
+  {
+    static std::atomic<int> pairs_cached{0};
+    int pairs = pairs_cached.load();
+    if (pairs <= 0) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(2);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = L::S_END;
+      TODE_CUDA_TRY(cudaOccupancyMaxActiveClusters(&pairs, (const void*)k_mlp_adjoint_wide<Cfg>,
+                                                   &cfg));
+      if (pairs <= 0) return TODE_ECUDA;
+      pairs_cached.store(pairs);
+    }
+    grid = std::min(grid, 2 * pairs * wide_slice_mult(r.o));
+  }
+  const int slice = grid * 64;
   for (int i0 = 0; i0 < r.B; i0 += slice) {
     a.i0 = i0;
     a.B = std::min(slice, r.B - i0);
-    const int cg = (a.B + 63) / 64;
+    int cg = (a.B + 63) / 64;
+    cg += cg & 1;  // CTA pairs: an odd tile count gets an idle partner
     k_mlp_adjoint_wide<Cfg><<<cg, 256, L::S_END, st>>>(a);
     TODE_CUDA_TRY(cudaGetLastError());
     d.chain_grid = cg;

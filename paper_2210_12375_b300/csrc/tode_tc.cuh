@@ -220,5 +220,98 @@ __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint3
       : "memory");
 }
 
+// ---------------------------------------------------------------- CTA pairs
+// A 2-CTA cluster whose M = 256 MMAs span both SMs (cta_group::2): CTA r
+// holds rows 128r .. 128r+127 of A and half of B's N columns at the same
+// shared-memory offsets, and its tensor memory receives its own 128 rows of
+// D.  One thread of CTA 0 issues the pair's MMAs.  Every tcgen05 operation of
+// a kernel that uses these takes the same cta_group, so the pair kernels
+// allocate, commit and free through the functions below.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// all threads of both CTAs; release / acquire at cluster scope
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::
+          : "memory");
+}
+// the same shared-memory variable in CTA `cta` of the cluster
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t cta) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(p)), "r"(cta));
+  return ra;
+}
+__device__ __forceinline__ int ld_peer_s32(const int* p, uint32_t cta) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(peer_addr(p, cta)) : "memory");
+  return v;
+}
+// one arrival on the mbarrier at this address in CTA `cta`, ordered after
+// this thread's earlier memory operations at cluster scope
+__device__ __forceinline__ void mbar_arrive_peer(uint64_t* mbar, uint32_t cta) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+                   peer_addr(mbar, cta))
+               : "memory");
+}
+// bounded wait with cluster-scope acquire (arrivals from the peer CTA)
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* mbar, uint32_t parity,
+                                                  long long budget = 2000000000LL) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > budget) return false;
+  }
+}
+// whole warp, in each CTA of the pair
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* smem_dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(smem_dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// D[tmem] (+)= A B^T over the pair (idesc with M = 256), from CTA 0
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t da, uint64_t db,
+                                              uint32_t idesc, bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"((uint32_t)accumulate)
+      : "memory");
+}
+// once the pair's earlier MMAs complete: one arrival on the mbarrier at this
+// offset in both CTAs ...
+__device__ __forceinline__ void mma_commit_pair_both(uint64_t* mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+      "[%0], %1;" ::"r"(smem_u32(mbar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+// ... or in the issuing CTA only
+__device__ __forceinline__ void mma_commit_pair_local(uint64_t* mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(mbar))
+      : "memory");
+}
+
 }  // namespace tc
 }  // namespace tode
