@@ -1896,15 +1896,19 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 template <class Cfg> struct WideAdj {
   static constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, ROWS = Cfg::ROWS;
   static_assert(Cfg::NL == 4 && D == 64 && H == 512 && K0 == 80 && ROWS == 64, "network");
-  static constexpr int NSL = 2, SLOT_BYTES = 32768;
-  // shared memory: the stacked input tile [128][K0] (after the first layer
-  // the stacked kbar tile [128][D] in the same place), the stacked hidden /
-  // delta tile [128][H], the weight ring, the biases
-  static constexpr int S_X = 0;
-  static constexpr int S_H = S_X + 2 * ROWS * K0 * 2;
+  // Three 32 KB slots: a slot's refill is requested when the pair's MMAs of
+  // the stage before are done, and its copy plus the hand-off to CTA 0 must
+  // land within the two stages of MMAs still queued (with two slots the
+  // tensor pipe drained at every stage).
+  static constexpr int NSL = 3, SLOT_BYTES = 32768;
+  // shared memory: one stacked tile, [128][K0] input X, then h1, h2
+  // ([128][H]), then the kbar tile [128][D], then delta3 .. delta1
+  // ([128][H]); the weight ring; one hidden layer's biases (loaded while
+  // that layer's product runs).  h3 lives only in its staged rows.
+  static constexpr int S_H = 0;
   static constexpr int S_W = S_H + 2 * ROWS * H * 2;
   static constexpr int S_BIAS = S_W + NSL * SLOT_BYTES;
-  static constexpr int S_END = S_BIAS + Cfg::BIAS_FLOATS * 4;
+  static constexpr int S_END = S_BIAS + H * 4;
   static_assert(S_END <= 232448 - 1024, "shared memory");
   // the round's weight stream: segments 0-2 the forward chunks of layers
   // 0-2 ([N][16] K-major), segments 3-6 the transposed chunks of layers 3,
@@ -1979,7 +1983,7 @@ struct WideAdjArgs {
   float* gy0;
   const unsigned char* wimg;     // forward chunk pair image (copies WIMG_STRIDE apart)
   const unsigned char* timg;     // transposed chunk pair image (same strides)
-  const float* bias[MLP_MAX_LAYERS];
+  const float* bias;             // layers 0-2's biases at l*H (16-byte aligned copy)
   unsigned char* plane[32];      // staging planes (WideAdj::NPLANES used)
   int cap;                       // reverse rounds per CTA the planes hold
   int32_t* rounds;               // [grid]: reverse rounds staged by each CTA
@@ -2016,8 +2020,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
   __shared__ int pair_flag[2];
-  unsigned char* sX = sm + L::S_X;  // input tile, then the kbar tile
-  unsigned char* sH = sm + L::S_H;
+  unsigned char* sH = sm + L::S_H;  // the stacked tile (also the input and kbar tiles)
   unsigned char* sW = sm + L::S_W;
   float* sBias = reinterpret_cast<float*>(sm + L::S_BIAS);
 
@@ -2054,17 +2057,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
   __syncthreads();
   if (tid == 0)
     for (int b = 0; b < NSL; ++b) issue_stage((uint32_t)b, b);
-  {
-    int o = 0;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int nn = Cfg::N_of(l);
-      for (int j = tid; j < nn; j += 256) sBias[o + j] = a.bias[l] ? a.bias[l][j] : 0.0f;
-      o += nn;
-    }
-  }
-  for (int j = tid; j < 2 * ROWS * K0 * 2 / 16; j += 256)
-    reinterpret_cast<uint4*>(sX)[j] = make_uint4(0, 0, 0, 0);
   // both CTAs run and their barriers are initialised before any arrival
   // crosses; the pair's tensor memory is allocated by a warp of each
   tc::cluster_sync();
@@ -2235,8 +2227,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
       stage8(t, col + 8 * u, hi, lo);
     }
   };
-  // hidden epilogue: h = tanh(acc + b) into the stacked tile, staged as act
-  auto epi_hidden = [&](const float* bl, int t_act) {
+  // hidden epilogue: h = tanh(acc + b), staged as act and (to_tile) written
+  // into the stacked tile as the next product's A
+  auto epi_hidden = [&](int t_act, bool to_tile) {
 #pragma unroll 1
     for (int c = 0; c < 256; c += 32) {
       float v0[16], v1[16];
@@ -2248,8 +2241,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
         float z[8];
         combine_pair8(u == 0 ? v0 : v1, odd, z);
         const int col = 256 * hf + c + 16 * u + 8 * odd;
-        const float4 b0 = *reinterpret_cast<const float4*>(bl + col);
-        const float4 b1 = *reinterpret_cast<const float4*>(bl + col + 4);
+        const float4 b0 = *reinterpret_cast<const float4*>(sBias + col);
+        const float4 b1 = *reinterpret_cast<const float4*>(sBias + col + 4);
         const float2 t0 = tanh_acc2(__fadd2_rn(make_float2(z[0], z[1]), make_float2(b0.x, b0.y)));
         const float2 t1 = tanh_acc2(__fadd2_rn(make_float2(z[2], z[3]), make_float2(b0.z, b0.w)));
         const float2 t2 = tanh_acc2(__fadd2_rn(make_float2(z[4], z[5]), make_float2(b1.x, b1.y)));
@@ -2257,50 +2250,39 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
         const float hv[8] = {t0.x, t0.y, t1.x, t1.y, t2.x, t2.y, t3.x, t3.y};
         uint4 hi, lo;
         split8(hv, hi, lo);
-        store_pair8(sH, row, col, H, odd, hi, lo);
+        if (to_tile) store_pair8(sH, row, col, H, odd, hi, lo);
         stage8(t_act, col, hi, lo);
       }
     }
   };
-  // delta epilogue: delta = acc (1 - h^2), h from the tile (its own layer,
-  // read before it is overwritten) or from its staged rows; the split delta
-  // replaces the tile and is staged
-  auto epi_delta = [&](int t_h, bool h_in_tile, int t_del) {
+  // delta epilogue: delta = acc (1 - h^2), h from its staged rows in global
+  // memory (fetched one iteration ahead, so that their latency overlaps the
+  // previous columns' arithmetic); the split delta replaces the tile and is
+  // staged
+  auto epi_delta = [&](int t_h, int t_del) {
     const int fw = L::fb_width(t_h);
-    // h of columns [c, c + 32) of this lane: from the tile, or from its
-    // staged rows in global memory -- those are fetched one iteration ahead,
-    // so that their latency overlaps the previous columns' arithmetic
     auto ld_h = [&](int c, uint4 (&hh)[2], uint4 (&hl)[2]) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int col = 256 * hf + c + 16 * u + 8 * odd;
-        if (h_in_tile) {
-          hh[u] = *reinterpret_cast<const uint4*>(sH + tc::cm_offset(2 * row, col, H));
-          hl[u] = *reinterpret_cast<const uint4*>(sH + tc::cm_offset(2 * row + 1, col, H));
-        } else {
-          const int fb = col / fw, m = col - fb * fw;
-          const unsigned char* src = a.plane[L::plane_first(t_h) + fb] +
-                                     blk * 2 * (size_t)L::blk_bytes(t_h) + L::blk_off(row, m, fw);
-          hh[u] = *reinterpret_cast<const uint4*>(src);
-          hl[u] = *reinterpret_cast<const uint4*>(src + L::blk_bytes(t_h));
-        }
+        const int fb = col / fw, m = col - fb * fw;
+        const unsigned char* src = a.plane[L::plane_first(t_h) + fb] +
+                                   blk * 2 * (size_t)L::blk_bytes(t_h) + L::blk_off(row, m, fw);
+        hh[u] = *reinterpret_cast<const uint4*>(src);
+        hl[u] = *reinterpret_cast<const uint4*>(src + L::blk_bytes(t_h));
       }
     };
     uint4 nh[2], nl[2];
-    if (!h_in_tile) ld_h(0, nh, nl);
+    ld_h(0, nh, nl);
 #pragma unroll 1
     for (int c = 0; c < 256; c += 32) {
       float v0[16], v1[16];
       tc::tmem_ld16(tbase + lanes + 256 * hf + c, v0);
       tc::tmem_ld16(tbase + lanes + 256 * hf + c + 16, v1);
       uint4 hh[2], hl[2];
-      if (h_in_tile) {
-        ld_h(c, hh, hl);
-      } else {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) hh[u] = nh[u], hl[u] = nl[u];
-        if (c + 32 < 256) ld_h(c + 32, nh, nl);
-      }
+      for (int u = 0; u < 2; ++u) hh[u] = nh[u], hl[u] = nl[u];
+      if (c + 32 < 256) ld_h(c + 32, nh, nl);
       tc::tmem_wait_ld();
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -2318,6 +2300,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     }
   };
 
+  // layer l's biases into shared memory, by threads that neither issue nor
+  // refill (the previous epilogue's reads ended at the barrier before the product)
+  auto load_bias = [&](int l) {
+    if (tid >= 64 && tid < 64 + H / 4)
+      reinterpret_cast<float4*>(sBias)[tid - 64] =
+          __ldg(reinterpret_cast<const float4*>(a.bias + (size_t)l * H) + (tid - 64));
+  };
   const float bw[7] = {float(Cc::b1), 0.0f, float(Cc::b3), float(Cc::b4), float(Cc::b5),
                        float(Cc::b6), 0.0f};
   int k_round = 0;  // reverse rounds staged by this CTA (the same in both CTAs of the pair)
@@ -2391,7 +2380,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
 #pragma unroll
       for (int r = 0; r < C; ++r) Y[r] = kq[r] = 0.0f;
     }
-    store_row16_stk(sX, row, coff, K0, Y);
+    store_row16_stk(sH, row, coff, K0, Y);  // the input tile [128][K0]
     stage16(L::T_X, coff, Y);
     stage16(L::T_K, coff, kq);
     if (sub == Cfg::TPR - 1) {
@@ -2402,38 +2391,44 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
 #pragma unroll
       for (int j = 0; j < 16; ++j) tail[j] = 0.0f;
       tail[0] = tin;
-      store_row16_stk(sX, row, D, K0, tail);
+      store_row16_stk(sH, row, D, K0, tail);
       tail[1] = 1.0f;
       stage16(L::T_X, D, tail);
     }
     barrier();
 
     // ---- forward layers at Y_s
-    gemm(0, tc::smem_u32(sX), K0, H);
+    gemm(0, tc::smem_u32(sH), K0, H);
+    load_bias(0);
     wait_mma();
-    epi_hidden(sBias, L::T_H1);
-    store_row16_stk(sX, row, coff, D, kq);  // the kbar tile, now that X is read
+    __syncthreads();
+    epi_hidden(L::T_H1, true);
     barrier();
     gemm(1, tc::smem_u32(sH), H, H);
+    load_bias(1);
     wait_mma();
-    epi_hidden(sBias + H, L::T_H2);
+    __syncthreads();
+    epi_hidden(L::T_H2, true);
     barrier();
     gemm(2, tc::smem_u32(sH), H, H);
+    load_bias(2);
     wait_mma();
-    epi_hidden(sBias + 2 * H, L::T_H3);
+    __syncthreads();
+    epi_hidden(L::T_H3, false);  // h3: staged only
+    store_row16_stk(sH, row, coff, D, kq);       // the kbar tile [128][D]
     barrier();
     // ---- backward chain
-    gemm(3, tc::smem_u32(sX), D, H);  // gh3 = kbar W4
+    gemm(3, tc::smem_u32(sH), D, H);  // gh3 = kbar W4
     wait_mma();
-    epi_delta(L::T_H3, true, L::T_D3);
+    epi_delta(L::T_H3, L::T_D3);
     barrier();
     gemm(4, tc::smem_u32(sH), H, H);  // gh2 = delta3 W3
     wait_mma();
-    epi_delta(L::T_H2, false, L::T_D2);
+    epi_delta(L::T_H2, L::T_D2);
     barrier();
     gemm(5, tc::smem_u32(sH), H, H);  // gh1 = delta2 W2
     wait_mma();
-    epi_delta(L::T_H1, false, L::T_D1);
+    epi_delta(L::T_H1, L::T_D1);
     barrier();
     gemm(6, tc::smem_u32(sH), H, K0);  // gx = delta1 W1
     wait_mma();
@@ -3899,7 +3894,7 @@ tode_err mlp_solve(const SolveReq& r, bool split) {
 // ---- wide network: the staged adjoint's scratch and work items
 struct WidePlan {
   int grid, cap, items;
-  size_t off_img, off_timg, off_order, off_rounds, off_plane[32], off_part, total;
+  size_t off_img, off_timg, off_bias, off_order, off_rounds, off_plane[32], off_part, total;
 };
 // The dW/db jobs of the wide adjoint, in the order dW2, dW3, dW1 (with the
 // constant input's column: db1), dW4^T, db2, db3, db4 -- four 128-row blocks
@@ -3950,6 +3945,8 @@ static WidePlan wide_plan(int B, int slots, int num_sms) {
   o += (size_t)Cfg::WREP * Cfg::WIMG_STRIDE;
   p.off_timg = o;
   o += (size_t)Cfg::WREP * Cfg::WIMG_STRIDE;
+  p.off_bias = o;
+  o += align256((size_t)3 * Cfg::H * 4);
   p.off_order = o;
   o += align256((size_t)std::max(B, 1) * 4);
   p.off_rounds = o;
@@ -4010,7 +4007,7 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   a.gye = (const float*)r.gye;
   a.gyf = (const float*)r.gyf;
   a.gy0 = (float*)r.gy0;
-  for (int l = 0; l < MLP_MAX_LAYERS; ++l) a.bias[l] = r.f->b[l];
+  a.bias = (const float*)(base + p.off_bias);
   a.err = (int32_t*)(base + 128);
   a.overflow = r.overflow;
   a.cap = p.cap;
@@ -4042,6 +4039,12 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   }
   TODE_CUDA_TRY(cudaMemsetAsync(base, 0, 256, st));
   TODE_CUDA_TRY(cudaMemsetAsync(d.part, 0, (size_t)p.items * DW_PART_FLOATS * 4, st));
+  // the hidden layers' biases, contiguous and aligned for vector loads (none: 0)
+  TODE_CUDA_TRY(cudaMemsetAsync(base + p.off_bias, 0, (size_t)3 * Cfg::H * 4, st));
+  for (int l = 0; l < 3; ++l)
+    if (r.f->b[l])
+      TODE_CUDA_TRY(cudaMemcpyAsync(base + p.off_bias + (size_t)l * Cfg::H * 4, r.f->b[l],
+                                    (size_t)Cfg::H * 4, cudaMemcpyDeviceToDevice, st));
   // the queue: most accepted steps first, so the rows of a tile reverse
   // instances of similar length (stable: a fixed order every call)
   k_order_steps_stable<<<1, 1024, 0, st>>>(r.B, StepsBin{r.n_acc, r.status},
