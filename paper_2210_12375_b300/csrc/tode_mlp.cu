@@ -1945,13 +1945,16 @@ template <class Cfg> struct WideAdj {
     bytes = nc * seg_chunk_bytes(q);
     off = Cfg::W_off(seg_layer(q)) / 2 + c0 * seg_chunk_bytes(q);
   }
-  // staged tensors; each splits into planes of (up to) 128 features, and a
-  // plane holds one block pair (hi, lo) per (chain CTA, reverse round)
+  // staged tensors; each splits into planes of (up to) 128 features -- 256
+  // for h1 and h2, the N = 256 operands of dW2 and dW3 -- and a plane holds
+  // one block pair (hi, lo) per (chain CTA, reverse round)
   enum { T_X = 0, T_H1 = 1, T_H2 = 2, T_H3 = 3, T_D1 = 4, T_D2 = 5, T_D3 = 6, T_K = 7, NTEN = 8 };
   __host__ __device__ static constexpr int fb_width(int t) {
-    return t == T_X ? K0 : t == T_K ? D : 128;
+    return t == T_X ? K0 : t == T_K ? D : (t == T_H1 || t == T_H2) ? 256 : 128;
   }
-  __host__ __device__ static constexpr int t_fb(int t) { return t == T_X || t == T_K ? 1 : H / 128; }
+  __host__ __device__ static constexpr int t_fb(int t) {
+    return t == T_X || t == T_K ? 1 : H / fb_width(t);
+  }
   __host__ __device__ static constexpr int blk_bytes(int t) { return ROWS * fb_width(t) * 2; }
   __host__ __device__ static constexpr int plane_first(int t) {
     int p = 0;
@@ -2512,14 +2515,14 @@ struct DwArgs {
 template <class Cfg>
 __global__ void __launch_bounds__(128, 1) k_mlp_dw(DwArgs a) {
   using L = WideAdj<Cfg>;
-  constexpr int NA = 2, NB = 3, SLOT = 32768;
+  constexpr int NA = 2, NB = 2, SLOT_A = 32768, SLOT_B = 65536;
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t fullA[NA], emptyA[NA], fullB[NB], emptyB[NB], done;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
   unsigned char* sA = sm;
-  unsigned char* sB = sm + NA * SLOT;
-  unsigned char* sOnes = sm + (NA + NB) * SLOT;  // [128][16] K-major BF16 ones
+  unsigned char* sB = sm + NA * SLOT_A;
+  unsigned char* sOnes = sm + NA * SLOT_A + NB * SLOT_B;  // [128][16] K-major BF16 ones
   const int tid = threadIdx.x, warp = tid >> 5;
   const int item = blockIdx.x;
   int j = 0;
@@ -2576,7 +2579,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_dw(DwArgs a) {
           if (ia >= NA) ok = tc::mbar_wait(&emptyA[s], ((ia - NA) / NA) & 1u);
           if (!ok) break;
           tc::mbar_expect_tx(&fullA[s], (uint32_t)abytes);
-          tc::bulk_g2s(sA + s * SLOT, pa + bk * abytes, (uint32_t)abytes, &fullA[s]);
+          tc::bulk_g2s(sA + s * SLOT_A, pa + bk * abytes, (uint32_t)abytes, &fullA[s]);
           ++ia;
         }
         if (hasB)
@@ -2586,7 +2589,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_dw(DwArgs a) {
             if (!ok) break;
             const unsigned char* pb = a.plane[L::plane_first(jb.tb) + u];
             tc::mbar_expect_tx(&fullB[s], (uint32_t)bbytes);
-            tc::bulk_g2s(sB + s * SLOT, pb + bk * bbytes, (uint32_t)bbytes, &fullB[s]);
+            tc::bulk_g2s(sB + s * SLOT_B, pb + bk * bbytes, (uint32_t)bbytes, &fullB[s]);
             ++ib;
           }
       }
@@ -2604,7 +2607,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_dw(DwArgs a) {
           const int s = ia % NA;
           ok = tc::mbar_wait(&fullA[s], (ia / NA) & 1u);
           if (!ok) break;
-          aA = tc::smem_u32(sA + s * SLOT);
+          aA = tc::smem_u32(sA + s * SLOT_A);
         }
         for (int u = 0; u < nbp && ok; ++u) {
           uint32_t aB = 0;
@@ -2612,7 +2615,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_dw(DwArgs a) {
             const int s = ib % NB;
             ok = tc::mbar_wait(&fullB[s], (ib / NB) & 1u);
             if (!ok) break;
-            aB = tc::smem_u32(sB + s * SLOT);
+            aB = tc::smem_u32(sB + s * SLOT_B);
           }
           const uint32_t dcol = tbase + (uint32_t)(jb.kind == 0 ? u * jb.bw : 0);
           for (int ks = 0; ks < 4; ++ks) {  // 16 staged rows per K step
@@ -3913,9 +3916,9 @@ static int wide_dw_jobs(DwArgs* a, int (&jW)[4], int (&jb)[4]) {
     ++nj;
   };
   jW[1] = nj;
-  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D2, mb, L::T_H1, 4, 128}, 8);
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D2, mb, L::T_H1, 2, 256}, 8);
   jW[2] = nj;
-  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D3, mb, L::T_H2, 4, 128}, 8);
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D3, mb, L::T_H2, 2, 256}, 8);
   jW[0] = jb[0] = nj;
   for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D1, mb, L::T_X, 1, 80}, 4);
   jW[3] = nj;
@@ -3982,7 +3985,7 @@ size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, const tode_options* o
          align256((size_t)grid * L::P_FLOATS * 4);
 }
 
-static constexpr int DW_SMEM = 5 * 32768 + 4096;  // two A slots, three B slots, the ones tile
+static constexpr int DW_SMEM = 2 * 32768 + 2 * 65536 + 4096;  // two A, two B slots, the ones tile
 
 static tode_err mlp_wide_adjoint(const AdjReq& r) {
   using Cfg = Cfg64s;
