@@ -157,18 +157,18 @@ TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum per launch, from the
     # captures summarised under profiles/ (launch shapes as given there)
     ("vdp_f64_b256", "k_fused<VdpField<double>>"): 0.141e6,
-    ("linear_d16_b8192", "k_fused<LinearField<float,1,16>>"): 28.38e6,
-    ("linear_d16_b8192", "k_adjoint_steps<LinearAdj<float,1,16>>"): 86.81e6,
+    ("linear_d16_b8192", "k_fused<LinearField<float,1,16>>"): 28.11e6,
+    ("linear_d16_b8192", "k_adjoint_steps<LinearAdj<float,1,16>>"): 86.32e6,
     # captured on the first 32,768 instances, x8 (the tape grows with the steps)
-    ("vdp_mix_b262144", "k_fused<VdpField<float>>"): 8 * 93.77e6,
-    ("vdp_mix_b262144", "k_adjoint_steps<VdpAdj<float>>"): 8 * 123.79e6,
-    ("mlp_d32_h128", "k_mlp_fused"): 13.28e6,
-    ("mlp_d32_h128", "k_mlp_adjoint"): 67.33e6,
+    ("vdp_mix_b262144", "k_fused<VdpField<float>>"): 8 * 93.10e6,
+    ("vdp_mix_b262144", "k_adjoint_steps<VdpAdj<float>>"): 8 * 123.80e6,
+    ("mlp_d32_h128", "k_mlp_fused"): 14.15e6,
+    ("mlp_d32_h128", "k_mlp_adjoint"): 49.46e6,
     # full size (B = 65,536), one pass per launch: the forward launch, and the
     # sum over the 16 launches of one adjoint call (the call is the entry)
-    ("mlp_d64_h512", "k_mlp_fused"): 1115.20e6,
-    ("mlp_d64_h512", "k_mlp_adjoint"): 66.208e9,
-    ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 69.53e6,
+    ("mlp_d64_h512", "k_mlp_fused"): 1121.63e6,
+    ("mlp_d64_h512", "k_mlp_adjoint"): 65.126e9,
+    ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 69.76e6,
 }
 
 
