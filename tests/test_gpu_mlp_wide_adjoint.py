@@ -94,3 +94,14 @@ def test_wide_mlp_adjoint_several_slices_and_deterministic():
     assert np.array_equal(a["gy0"], b["gy0"])
     for l in range(4):
         assert np.array_equal(a["gW"][l], b["gW"][l]) and np.array_equal(a["gb"][l], b["gb"][l])
+
+
+def test_wide_mlp_adjoint_odd_tile_count():
+    """Three 64-row tiles (the last ragged): the reverse chain runs on CTA
+    pairs, so the second pair's CTA 1 holds no instance and runs the pair's
+    rounds on zeros; its staged rows add nothing to the weight gradients."""
+    w = dict(make(5, B=130), split=True)
+    r = _run(w, seed=3)
+    o = r["out"][0]
+    assert o["ovf"] == 0
+    _check(o, _oracle_adj(w, r["probe"], r["gye"], r["gyf"]))
