@@ -26,6 +26,8 @@
 #include "tode_internal.h"
 #include "tode_tc.cuh"
 
+#include <cuda.h>  // CUtensorMap and its encoder type (through the runtime entry point)
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -1887,9 +1889,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 // The chain runs on CTA pairs (2-CTA clusters): the pair's MMAs are
 // M = 256 over both CTAs' stacked tiles, issued by CTA 0, and each CTA
 // streams only its half of every weight chunk (IMG_CHUNKS2 / IMG_TCHUNKS2),
-// so a stage carries twice the tensor work per byte an SM receives.  Per
-// stage CTA 1 forwards the arrival of its half to CTA 0; per product CTA 1
-// reports its tile written; CTA 0's commits arrive in both CTAs.  Both CTAs
+// so a stage carries twice the tensor work per byte an SM receives.  The
+// halves come in as 2-D tensor-map copies of the cta_group::2 form: CTA 1's
+// copy completes on CTA 0's barrier, which expects both halves' bytes; per
+// product CTA 1 reports its tile written; CTA 0's commits arrive in both
+// CTAs' barriers (a CTA refills its own slot).  Both CTAs
 // run the same rounds: the pair stops when neither has a row left (the
 // shorter tile's rows run on zeros meanwhile).
 // ======================================================================
@@ -1936,7 +1940,8 @@ template <class Cfg> struct WideAdj {
     for (int q = 0; q < NSEG; ++q) s += seg_stages(q);
     return s;
   }
-  __device__ static void stage_of(uint32_t g, int& q, int& c0, int& nc, int& off, int& bytes) {
+  __host__ __device__ static void stage_of(uint32_t g, int& q, int& c0, int& nc, int& off,
+                                           int& bytes) {
     int st = (int)(g % (uint32_t)stages());
     q = 0;
     while (st >= seg_stages(q)) st -= seg_stages(q++);
@@ -1968,7 +1973,13 @@ template <class Cfg> struct WideAdj {
   }
 };
 
+// the chain's weight stages as 2-D tensor-map boxes: both pair images (the
+// forward chunks', then the transposed chunks', WREP copies each) as one
+// [rows][64] BF16 tensor of 128-byte rows, one map per stage size
+constexpr int WIDE_TMAPS = 4;
 struct WideAdjArgs {
+  CUtensorMap tmap[WIDE_TMAPS];  // boxes of tmap_rows[k] rows
+  int tmap_rows[WIDE_TMAPS];
   int i0, B, K;                  // the slice: queue positions i0 .. i0+B-1
   const int32_t* order;          // queue position -> instance (most accepted steps first)
   const double* t0;
@@ -1984,8 +1995,6 @@ struct WideAdjArgs {
   const float* gye;
   const float* gyf;
   float* gy0;
-  const unsigned char* wimg;     // forward chunk pair image (copies WIMG_STRIDE apart)
-  const unsigned char* timg;     // transposed chunk pair image (same strides)
   const float* bias;             // layers 0-2's biases at l*H (16-byte aligned copy)
   unsigned char* plane[32];      // staging planes (WideAdj::NPLANES used)
   int cap;                       // reverse rounds per CTA the planes hold
@@ -2008,18 +2017,18 @@ __device__ __forceinline__ void unsplit8(const uint4& hi, const uint4& lo, float
 
 template <class Cfg>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
-    k_mlp_adjoint_wide(WideAdjArgs a) {
+    k_mlp_adjoint_wide(const __grid_constant__ WideAdjArgs a) {
   using L = WideAdj<Cfg>;
   using Cc = DP5;
   constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, ROWS = Cfg::ROWS;
   constexpr int NSL = L::NSL;
   extern __shared__ __align__(1024) unsigned char sm[];
-  // mbar_full: this CTA's half of a stage landed; mbar_pfull (CTA 0): CTA 1's
-  // half landed; mbar_tile (CTA 0): CTA 1's tile is written for the next
-  // product; mbar_empty / mbar_mma: the pair's MMAs of a stage / a product
-  // are done (arrive in both CTAs); mbar_fin: CTA 0's last MMAs are done
-  __shared__ __align__(8) uint64_t mbar_mma, mbar_full[NSL], mbar_empty[NSL], mbar_pfull[NSL],
-      mbar_tile, mbar_fin;
+  // mbar_full (CTA 0): both halves of a stage landed (CTA 1's copies
+  // complete on CTA 0's barrier); mbar_tile (CTA 0): CTA 1's tile is written
+  // for the next product; mbar_empty / mbar_mma: the pair's MMAs of a stage /
+  // a product are done (arrive in both CTAs); mbar_fin: CTA 0's last MMAs
+  // are done
+  __shared__ __align__(8) uint64_t mbar_mma, mbar_full[NSL], mbar_empty[NSL], mbar_tile, mbar_fin;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
   __shared__ int pair_flag[2];
@@ -2032,25 +2041,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
   const int coff = sub * C;
   const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
   const uint32_t rank = tc::cluster_rank();
+  // this CTA's half image: byte offsets in the tensor-map rows (the
+  // transposed image follows the forward one)
   const size_t rep = (size_t)((blockIdx.x >> 1) % Cfg::WREP) * Cfg::WIMG_STRIDE + rank * L::HALF_BYTES;
-  const unsigned char* wimg = a.wimg + rep;
-  const unsigned char* timg = a.timg + rep;
+  const size_t timg_off = (size_t)Cfg::WREP * Cfg::WIMG_STRIDE;
   uint32_t g_stage = 0;  // weight stages consumed so far
   uint32_t tile_par = 0;  // products issued so far (parity of mbar_tile)
 
+  // this CTA's half of stage g into the slot; CTA 0 expects both halves
   auto issue_stage = [&](uint32_t g, int slot) {
     int q, c0, nc, off, bytes;
     L::stage_of(g, q, c0, nc, off, bytes);
-    tc::mbar_expect_tx(&mbar_full[slot], (uint32_t)bytes);
-    tc::bulk_g2s(sW + slot * L::SLOT_BYTES, (L::seg_tr(q) ? timg : wimg) + off, (uint32_t)bytes,
-                 &mbar_full[slot]);
+    const int rows = bytes / 128;
+    int m = 0;
+    while (m + 1 < WIDE_TMAPS && a.tmap_rows[m] != rows) ++m;
+    const size_t boff = (L::seg_tr(q) ? timg_off : 0) + rep + (size_t)off;
+    uint32_t mb;
+    if (rank == 0) {
+      tc::mbar_expect_tx(&mbar_full[slot], 2u * (uint32_t)bytes);
+      mb = tc::smem_u32(&mbar_full[slot]);
+    } else {
+      mb = tc::peer_addr(&mbar_full[slot], 0);
+    }
+    tc::tensor_g2s_pair(sW + slot * L::SLOT_BYTES, &a.tmap[m], 0, (int)(boff / 128), mb);
   };
   if (tid == 0) {
     tc::mbar_init(&mbar_mma, 1);
     for (int b = 0; b < NSL; ++b) {
       tc::mbar_init(&mbar_full[b], 1);
       tc::mbar_init(&mbar_empty[b], 1);
-      tc::mbar_init(&mbar_pfull[b], 1);
     }
     tc::mbar_init(&mbar_tile, 1);
     tc::mbar_init(&mbar_fin, 1);
@@ -2058,11 +2077,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // both CTAs run and their barriers are initialised before any arrival or
+  // copy crosses; the pair's tensor memory is allocated by a warp of each
+  tc::cluster_sync();
   if (tid == 0)
     for (int b = 0; b < NSL; ++b) issue_stage((uint32_t)b, b);
-  // both CTAs run and their barriers are initialised before any arrival
-  // crosses; the pair's tensor memory is allocated by a warp of each
-  tc::cluster_sync();
   if (warp == 0) tc::tmem_alloc_pair(&tmem_base_s, 512);
   tc::fence_proxy_async();
   tc::fence_before_sync();
@@ -2147,10 +2166,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
   };
   // one product of the round (segment qs) on the pair.  CTA 0's thread 0
   // waits for CTA 1's tile, then issues M = 256 MMAs over both stacked tiles
-  // (K-major, Ka columns) as both halves of each stage arrive; CTA 1's
-  // thread 0 reports its tile and forwards the arrival of each of its
-  // halves; thread 32 of each CTA refills its own slot with the stage NSL
-  // ahead once the pair's MMAs of the slot are done.  N > 256 runs as
+  // (K-major, Ka columns) as both halves of each stage arrive (on CTA 0's
+  // barrier); CTA 1's thread 0 reports its tile; thread 32 of each CTA
+  // refills its own slot with the stage NSL ahead once the pair's MMAs of
+  // the slot are done.  N > 256 runs as
   // products of 256 (tensor-memory columns 256 j); a CTA's half of a chunk
   // holds NW/2 columns of each (IMG_CHUNKS2 / IMG_TCHUNKS2).
   auto gemm = [&](int qs, uint32_t a_addr, int Ka, int Nl) {
@@ -2159,12 +2178,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
       bool ok = true;
       if (rank != 0) {
         tc::mbar_arrive_peer(&mbar_tile, 0);
-        for (int st = 0; st < L::seg_stages(qs) && ok; ++st) {
-          const uint32_t g = g_stage + (uint32_t)st;
-          const int b = (int)(g % NSL);
-          ok = tc::mbar_wait(&mbar_full[b], (g / NSL) & 1u);
-          if (ok) tc::mbar_arrive_peer(&mbar_pfull[b], 0);
-        }
       } else {
         const int nh = Nl > 256 ? Nl / 256 : 1, nw = Nl > 256 ? 256 : Nl, hw = nw / 2;
         const uint32_t idesc = tc::idesc_bf16_f32(256, nw, false, tr);
@@ -2174,8 +2187,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
         for (int st = 0; st < L::seg_stages(qs) && ok; ++st) {
           const uint32_t g = g_stage + (uint32_t)st;
           const int b = (int)(g % NSL);
-          ok = tc::mbar_wait(&mbar_full[b], (g / NSL) & 1u) &&
-               tc::mbar_wait_cluster(&mbar_pfull[b], (g / NSL) & 1u);
+          ok = tc::mbar_wait_cluster(&mbar_full[b], (g / NSL) & 1u);
           if (!ok) break;
           int q_, c0, nc, off_, bytes_;
           L::stage_of(g, q_, c0, nc, off_, bytes_);
@@ -2468,11 +2480,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
   }
   if (tid == 0) {
     a.rounds[blockIdx.x] = k_round;
-    // the ring's copies still in flight (stages g .. g + NSL - 1) land before the CTA exits
-    for (uint32_t x = g_stage; x < g_stage + NSL; ++x)
-      if (!tc::mbar_wait(&mbar_full[x % NSL], (x / NSL) & 1u)) atomicExch(&abort_s, 1);
-    // and the pair's MMAs, which read both CTAs' shared memory, are done
     if (rank == 0) {
+      // the ring's copies still in flight (stages g .. g + NSL - 1, both
+      // CTAs' halves: they complete on CTA 0's barriers) land before either
+      // CTA exits, and the pair's MMAs, which read both CTAs' shared memory,
+      // are done
+      for (uint32_t x = g_stage; x < g_stage + NSL; ++x)
+        if (!tc::mbar_wait_cluster(&mbar_full[x % NSL], (x / NSL) & 1u)) atomicExch(&abort_s, 1);
       tc::mma_commit_pair_local(&mbar_fin);
       if (!tc::mbar_wait(&mbar_fin, 0)) atomicExch(&abort_s, 1);
     }
@@ -3987,6 +4001,54 @@ size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, const tode_options* o
 
 static constexpr int DW_SMEM = 2 * 32768 + 2 * 65536 + 4096;  // two A, two B slots, the ones tile
 
+// The tensor maps of the chain's weight stream: the distinct stage sizes of
+// a round (in 128-byte rows, at most WIDE_TMAPS), each a box of that many
+// rows over both pair images.  The encoder comes from the driver through the
+// runtime's entry-point query (the library links only the runtime).
+template <class Cfg>
+static tode_err wide_tensor_maps(const unsigned char* img, WideAdjArgs& a) {
+  using L = WideAdj<Cfg>;
+  static std::atomic<void*> encoder{nullptr};
+  void* fn = encoder.load();
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return TODE_ECUDA;
+    }
+    encoder.store(fn);
+  }
+  int n = 0;
+  for (int g = 0; g < L::stages(); ++g) {
+    int q, c0, nc, off, bytes;
+    L::stage_of((uint32_t)g, q, c0, nc, off, bytes);
+    if (bytes % 128 != 0 || off % 128 != 0) return TODE_EINVAL;
+    const int rows = bytes / 128;
+    int m = 0;
+    while (m < n && a.tmap_rows[m] != rows) ++m;
+    if (m == n) {
+      if (n == WIDE_TMAPS || rows > 256) return TODE_EINVAL;
+      a.tmap_rows[n++] = rows;
+    }
+  }
+  for (int m = n; m < WIDE_TMAPS; ++m) a.tmap_rows[m] = a.tmap_rows[0];
+  static_assert(Cfg::WIMG_STRIDE % 128 == 0 && L::HALF_BYTES % 128 == 0, "128-byte rows");
+  const cuuint64_t dims[2] = {64, (cuuint64_t)2 * Cfg::WREP * Cfg::WIMG_STRIDE / 128};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t estr[2] = {1, 1};
+  for (int m = 0; m < WIDE_TMAPS; ++m) {
+    const cuuint32_t box[2] = {64, (cuuint32_t)a.tmap_rows[m]};
+    const CUresult r = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)(
+        &a.tmap[m], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<unsigned char*>(img), dims,
+        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return TODE_ECUDA;
+  }
+  return TODE_OK;
+}
+
 static tode_err mlp_wide_adjoint(const AdjReq& r) {
   using Cfg = Cfg64s;
   using L = WideAdj<Cfg>;
@@ -4017,8 +4079,10 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   a.rounds = (int32_t*)(base + p.off_rounds);
   unsigned char* img = (unsigned char*)base + p.off_img;
   unsigned char* timg = (unsigned char*)base + p.off_timg;
-  a.wimg = img;
-  a.timg = timg;
+  {
+    const tode_err e = wide_tensor_maps<Cfg>(img, a);
+    if (e != TODE_OK) return e;
+  }
   for (int q = 0; q < L::NPLANES; ++q) a.plane[q] = (unsigned char*)base + p.off_plane[q];
   DwArgs d{};
   int jW[4], jb[4];

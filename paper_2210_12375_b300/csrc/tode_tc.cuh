@@ -305,6 +305,18 @@ __device__ __forceinline__ void mma_commit_pair_both(uint64_t* mbar) {
       "h"((uint16_t)3)
       : "memory");
 }
+// 2-D tensor-map copy of one box at (x, y) into this CTA's shared memory,
+// completing on the mbarrier at shared::cluster address `mbar` -- this CTA's
+// or, for CTA 1 of a pair, CTA 0's (the pair's cta_group::2 form).  x times
+// the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tensor_g2s_pair(void* smem_dst, const void* tmap, int x, int y,
+                                                uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
 // ... or in the issuing CTA only
 __device__ __forceinline__ void mma_commit_pair_local(uint64_t* mbar) {
   asm volatile(
