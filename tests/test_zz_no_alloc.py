@@ -159,6 +159,20 @@ def _static_code(w, g, tp, gye, gyf):
     return code, need
 
 
+def test_static_scratch_refuses_the_wide_mlp():
+    """The wide network's adjoint (D = 64, three layers of 512) keeps its
+    pair weight images and the staged rows of every reverse round in
+    scratch, far beyond the array even for one small slice: the call is
+    refused with TODE_EWORKSPACE before any device work (the outputs keep
+    their NaN fill)."""
+    w, g, tape, gye, gyf = _prepare(5, 64, torch.float32, seed=30)
+    lib = _abi.load()
+    code, gy0, gp, ovf = _static_adjoint(w, g, tape, gye, gyf)
+    assert code == _abi.TODE_EWORKSPACE, lib.tode_strerror(code)
+    assert torch.isnan(gy0).all()
+    assert all(torch.isnan(x).all() for x in gp[0])
+
+
 def test_static_scratch_rejects_problems_beyond_its_size():
     # a valid strided tape (every field a re-run needs) whose segments of
     # 20000 steps per instance need more scratch than the array holds
