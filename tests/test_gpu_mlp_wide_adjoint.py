@@ -10,7 +10,7 @@ import torch
 
 import oracle
 import paper_2210_12375_b300 as tode
-from gpu_helpers import gpu_solve, make, subset
+from gpu_helpers import gpu_solve, make, oracle_solve, subset
 from oracle.oracle import mesh_from_trace
 
 pytestmark = pytest.mark.gpu
@@ -105,3 +105,28 @@ def test_wide_mlp_adjoint_odd_tile_count():
     o = r["out"][0]
     assert o["ovf"] == 0
     _check(o, _oracle_adj(w, r["probe"], r["gye"], r["gyf"]))
+
+
+def test_wide_mlp_full_size_sampled():
+    """The bench's workload at full size (65,536 instances: 1024 tiles, the
+    reverse chain on 74 CTA pairs in several slices): the forward on a
+    stratified sample within the FP32 band of a 1e-12 oracle solution, and
+    the adjoint with cotangents only on that sample, whose summed gradients
+    equal the oracle's over it."""
+    w = dict(make(5), split=True)
+    B = w["B"]
+    assert B == 65536
+    idx = np.unique(np.concatenate([np.arange(0, B, 2731), np.arange(B - 64, B, 21), [B - 1]]))
+    mask = np.zeros(B, bool)
+    mask[idx] = True
+    r = _run(w, mask=mask, seed=5)
+    o = r["out"][0]
+    assert o["ovf"] == 0
+    assert (r["probe"]["status"] == 0).all()
+    ws = subset(w, idx)
+    ref = oracle_solve(ws, rtol=1e-12, atol=1e-12)
+    band = 10 * (w["atol"] + w["rtol"] * np.abs(ref["y_eval"]))
+    ratio = np.abs(r["probe"]["y_eval"][idx] - ref["y_eval"]) / band
+    assert np.isfinite(ratio).all() and ratio.max() <= 1.0, ratio.max()
+    assert (o["gy0"][~mask] == 0.0).all()
+    _check(o, _oracle_adj(w, r["probe"], r["gye"], r["gyf"], idx), idx)
