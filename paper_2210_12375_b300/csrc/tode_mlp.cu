@@ -3916,8 +3916,10 @@ struct WidePlan {
 // The dW/db jobs of the wide adjoint, in the order dW2, dW3, dW1 (with the
 // constant input's column: db1), dW4^T, db2, db3, db4 -- four 128-row blocks
 // each (db4: one) -- with their work items (the chain CTAs split in parts:
-// eight for the 512 x 512 products, four otherwise).  jW[l] / jb[l]: the
-// first job of gradient l.  Returns the number of work items.
+// ten for the 512 x 512 products, four otherwise: 148 items, one wave of
+// one CTA per SM on a 148-SM B300, the heavy items' bytes close to the
+// others').  jW[l] / jb[l]: the first job of gradient l.  Returns the
+// number of work items.
 static int wide_dw_jobs(DwArgs* a, int (&jW)[4], int (&jb)[4]) {
   using L = WideAdj<MlpWideCfg<64, 512, 4>>;
   int nj = 0, it = 0;
@@ -3930,9 +3932,9 @@ static int wide_dw_jobs(DwArgs* a, int (&jW)[4], int (&jb)[4]) {
     ++nj;
   };
   jW[1] = nj;
-  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D2, mb, L::T_H1, 2, 256}, 8);
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D2, mb, L::T_H1, 2, 256}, 10);
   jW[2] = nj;
-  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D3, mb, L::T_H2, 2, 256}, 8);
+  for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D3, mb, L::T_H2, 2, 256}, 10);
   jW[0] = jb[0] = nj;
   for (int mb = 0; mb < 4; ++mb) add(DwJob{0, L::T_D1, mb, L::T_X, 1, 80}, 4);
   jW[3] = nj;
