@@ -2506,7 +2506,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
 // tensor memory.  A job is one 128-feature block of the output's rows
 // (M = 128); its work items split the chain CTAs (the K dimension) into
 // parts, each accumulating its own partial in a fixed order, which
-// k_mlp_dw_reduce sums part by part: deterministic.
+// k_mlp_dw_reduce sums part by part: deterministic.  A work item's copies
+// stream through two A and two B slots (more slots for the jobs with small
+// blocks measured slower: their extra bytes in flight evicted the blocks
+// that the N = 256 jobs share through L2).  A partial is column-major
+// ([column][128 output rows]), so that the accumulator's rows, one per
+// thread, go out coalesced.
 //   kind 0: D[o][i] += A^T B over nb operand blocks of width bw (dW)
 //   kind 1: D[o][0] += A^T 1 (a bias: the delta's column sums)
 //   kind 2: D[*][i] += 1^T B (the output bias from the kbar rows)
@@ -2515,6 +2520,8 @@ struct DwJob {
 };
 constexpr int DW_MAX_JOBS = 32;
 constexpr int DW_PART_FLOATS = 128 * 512;
+constexpr int DW_NA = 2, DW_NB = 2, DW_SLOT_A = 32768, DW_SLOT_B = 65536;
+constexpr int DW_RING = DW_NA * DW_SLOT_A + DW_NB * DW_SLOT_B;
 struct DwArgs {
   int njobs;
   DwJob job[DW_MAX_JOBS];
@@ -2529,19 +2536,19 @@ struct DwArgs {
 template <class Cfg>
 __global__ void __launch_bounds__(128, 1) k_mlp_dw(DwArgs a) {
   using L = WideAdj<Cfg>;
-  constexpr int NA = 2, NB = 2, SLOT_A = 32768, SLOT_B = 65536;
   extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr int NA = DW_NA, NB = DW_NB, SLOT_A = DW_SLOT_A, SLOT_B = DW_SLOT_B;
   __shared__ __align__(8) uint64_t fullA[NA], emptyA[NA], fullB[NB], emptyB[NB], done;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
-  unsigned char* sA = sm;
-  unsigned char* sB = sm + NA * SLOT_A;
-  unsigned char* sOnes = sm + NA * SLOT_A + NB * SLOT_B;  // [128][16] K-major BF16 ones
   const int tid = threadIdx.x, warp = tid >> 5;
   const int item = blockIdx.x;
   int j = 0;
   while (j + 1 < a.njobs && item >= a.item0[j + 1]) ++j;
   const DwJob jb = a.job[j];
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + NA * SLOT_A;
+  unsigned char* sOnes = sm + DW_RING;  // [128][16] K-major BF16 ones
   const int P = a.item0[j + 1] - a.item0[j], p = item - a.item0[j];
   const int c_lo = (int)((long long)a.chain_grid * p / P);
   const int c_hi = (int)((long long)a.chain_grid * (p + 1) / P);
@@ -2675,18 +2682,23 @@ __global__ void __launch_bounds__(128, 1) k_mlp_dw(DwArgs a) {
   __syncwarp();
   if (!tc::mbar_wait_sleep(&done, 0)) atomicExch(&abort_s, 1);
   tc::fence_after_sync();
-  // add the accumulator to this item's partial (rows = lanes, one per thread)
+  // add the accumulator to this item's partial (rows = lanes, one per
+  // thread; column-major, so a warp's 32 rows of a column are contiguous)
   const int ncols = jb.kind == 0 ? jb.nb * jb.bw : jb.kind == 1 ? 16 : L::fb_width(jb.tb);
   if (nblk > 0 && !abort_s) {
-    float* dst = a.part + (size_t)item * DW_PART_FLOATS + (size_t)tid * 512;
+    float* dst = a.part + (size_t)item * DW_PART_FLOATS + tid;
     const uint32_t lanes = (uint32_t)(32 * warp) << 16;
     for (int c0 = 0; c0 < ncols; c0 += 16) {
       float v[16];
       tc::tmem_ld16(tbase + lanes + c0, v);
       tc::tmem_wait_ld();
+      float o[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e)
-        if (c0 + e < ncols) dst[c0 + e] += v[e];
+        if (c0 + e < ncols) o[e] = dst[(size_t)(c0 + e) * 128];
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        if (c0 + e < ncols) dst[(size_t)(c0 + e) * 128] = o[e] + v[e];
     }
   }
   if (abort_s && tid == 0) atomicExch(a.err, 3);
@@ -2708,15 +2720,18 @@ struct DwReduceArgs {
 __global__ void k_mlp_dw_reduce(DwReduceArgs a) {
   constexpr int H = 512, D = 64, IN0 = D + 1;
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // partial element (row m, column nn) of each item of a job, in item order;
+  // consecutive threads take consecutive rows m where the partial's rows are
+  // the gradient's (the column-major partials read coalesced)
   auto sum = [&](int job, int m, int nn) {
     float s = 0.0f;
     for (int it = a.item0[job]; it < a.item0[job + 1]; ++it)
-      s += a.part[(size_t)it * DW_PART_FLOATS + (size_t)m * 512 + nn];
+      s += a.part[(size_t)it * DW_PART_FLOATS + (size_t)nn * 128 + m];
     return s;
   };
   if (e < (long long)H * IN0) {  // gW0 [o][i], i < 65
-    const int o = (int)(e / IN0), i = (int)(e % IN0);
-    a.gW[0][e] = sum(a.jW[0] + o / 128, o % 128, i);
+    const int i = (int)(e / H), o = (int)(e % H);
+    a.gW[0][(size_t)o * IN0 + i] = sum(a.jW[0] + o / 128, o % 128, i);
     return;
   }
   e -= (long long)H * IN0;
@@ -2727,8 +2742,8 @@ __global__ void k_mlp_dw_reduce(DwReduceArgs a) {
   e -= H;
   for (int l = 1; l <= 2; ++l) {
     if (e < (long long)H * H) {
-      const int o = (int)(e / H), i = (int)(e % H);
-      a.gW[l][e] = sum(a.jW[l] + o / 128, o % 128, i);
+      const int i = (int)(e / H), o = (int)(e % H);
+      a.gW[l][(size_t)o * H + i] = sum(a.jW[l] + o / 128, o % 128, i);
       return;
     }
     e -= (long long)H * H;
@@ -4001,7 +4016,7 @@ size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, const tode_options* o
          align256((size_t)grid * L::P_FLOATS * 4);
 }
 
-static constexpr int DW_SMEM = 2 * 32768 + 2 * 65536 + 4096;  // two A, two B slots, the ones tile
+static constexpr int DW_SMEM = DW_RING + 4096;  // the copy ring, the ones tile
 
 // The tensor maps of the chain's weight stream: the distinct stage sizes of
 // a round (in 128-byte rows, at most WIDE_TMAPS), each a box of that many
