@@ -242,8 +242,11 @@ size_t tode_workspace_size(const tode_field_desc* f, const tode_options* o, int 
  *  tape: NULL or a checkpoint tape to fill for tode_adjoint.
  *  yp_eval: NULL or [B][K][D] state dtype: dy/dt at every evaluation point,
  *  the derivative of the dense-output interpolant there (f(t0, y0) at points
- *  equal to t0; NaN where y_eval is NaN).  Van der Pol and linear fields,
- *  independent solving; otherwise TODE_EUNSUPPORTED.  With it, the gradient
+ *  equal to t0; NaN where y_eval is NaN).  Every field, independent solving
+ *  (TODE_EUNSUPPORTED for a joint solve); for the MLP field the derivative
+ *  is formed from the tensor-core stage values k_i in FP32, and an instance
+ *  with t1 = t0 and points spends one evaluation round on f(t0, y0) (its
+ *  counters stay 0).  With it, the gradient
  *  of a loss with respect to t_eval is <dL/dy_eval, yp_eval> per point
  *  (tode_t_eval_grad).
  *  trace: NULL or a per-attempt trace to fill.

@@ -107,6 +107,7 @@ def _load():
         lib.orc_adjoint_t.restype = C.c_int
         lib.orc_adjoint_tm.restype = C.c_int
         lib.orc_replay_m.restype = C.c_int
+        lib.orc_replay_yp.restype = C.c_int
         lib.orc_joint_adjoint.restype = C.c_int
         _lib = lib
     return _lib
@@ -352,10 +353,11 @@ def solve_joint(field: dict, y0, t0: float, t1: float, t_eval=None, opts: dict |
 
 
 def replay(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None,
-           nthreads: int = 0, method: str = "dopri5") -> dict:
+           nthreads: int = 0, method: str = "dopri5", want_yp: bool = False) -> dict:
     """Fixed-mesh steps of the pair ``method`` (no controller).  mesh_t/mesh_h
     [B,cap], mesh_n [B] accepted steps; the last step of instance i ends at
-    t1[i]."""
+    t1[i].  With ``want_yp``, also yp_eval [B,K,D]: dy/dt of the dense output
+    of the replayed steps at the points (f(t0, y0) at points equal to t0)."""
     lib = _load()
     y0 = np.asarray(y0, dtype=np.float64)
     B = y0.shape[0]
@@ -372,11 +374,15 @@ def replay(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None,
     K = t_eval.shape[1]
     y_eval = np.zeros((B, K, D))
     y_final = np.zeros((B, D))
-    lib.orc_replay_m(C.c_int(METHODS[method]), C.byref(fh.f), C.c_int(B), _ptr(y0),
-                     _ptr(_f64(t0, (B,))), _ptr(_f64(t1, (B,))), _ptr(mesh_t), _ptr(mesh_h),
-                     _iptr(mesh_n), C.c_int(cap), _ptr(t_eval), C.c_int(K), _ptr(y_eval),
-                     _ptr(y_final), C.c_int(nthreads))
-    return dict(y_eval=y_eval, y_final=y_final)
+    yp = np.zeros((B, K, D)) if want_yp else None
+    lib.orc_replay_yp(C.c_int(METHODS[method]), C.byref(fh.f), C.c_int(B), _ptr(y0),
+                      _ptr(_f64(t0, (B,))), _ptr(_f64(t1, (B,))), _ptr(mesh_t), _ptr(mesh_h),
+                      _iptr(mesh_n), C.c_int(cap), _ptr(t_eval), C.c_int(K), _ptr(y_eval),
+                      _ptr(yp) if yp is not None else None, _ptr(y_final), C.c_int(nthreads))
+    out = dict(y_eval=y_eval, y_final=y_final)
+    if yp is not None:
+        out["yp_eval"] = yp
+    return out
 
 
 def adjoint(field: dict, y0, t0, t1, mesh_t, mesh_h, mesh_n, t_eval=None, gy_eval=None,

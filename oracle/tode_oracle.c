@@ -778,14 +778,21 @@ static void replay_one(const job *J, int i, double *work, double *act, double *y
   const double dir = (J->t1[i] < t0) ? -1.0 : 1.0; /* mesh steps carry this sign */
   const double *te = J->t_eval + (size_t)i * K;
   double *ye = J->y_eval + (size_t)i * K * D;
+  double *yp = J->yp_eval ? J->yp_eval + (size_t)i * K * D : NULL;
   double *y = work, *k = y + D, *Y = k + NS * D;
   fctx c = {F, i, act, 0};
   for (int j = 0; j < D; ++j) y[j] = J->y0[(size_t)i * D + j];
   fill_nan(ye, (size_t)K * D);
+  if (yp) fill_nan(yp, (size_t)K * D);
   int cur = 0;
   while (cur < K && te[cur] == t0) {
     for (int j = 0; j < D; ++j) ye[(size_t)cur * D + j] = y[j];
     cur++;
+  }
+  if (yp && cur > 0) { /* the derivative at t0 is f(t0, y0) */
+    feval(&c, t0, y, k);
+    for (int q = 0; q < cur; ++q)
+      for (int j = 0; j < D; ++j) yp[(size_t)q * D + j] = k[j];
   }
   if (ys)
     for (int j = 0; j < D; ++j) ys[j] = y[j];
@@ -803,6 +810,9 @@ static void replay_one(const job *J, int i, double *work, double *act, double *y
       } else {
         dp_dense(J->T, (te[cur] - t) / h, h, y, k, D, o);
       }
+      if (yp) /* the interpolant's derivative; theta = 1 at the step's end */
+        dp_dense_deriv(J->T, te[cur] == t_next ? 1.0 : (te[cur] - t) / h, k, D,
+                       yp + (size_t)cur * D);
       cur++;
     }
     for (int j = 0; j < D; ++j) y[j] = y1[j];
@@ -1176,11 +1186,23 @@ int orc_solve_yp(const orc_field *F, const orc_opts *O, int B, const double *y0,
   return run(&J, MODE_SOLVE, nthreads);
 }
 
-/* The fixed-mesh replay with the pair `method` (0 dopri5, 1 tsit5). */
+/* The fixed-mesh replay with the pair `method` (0 dopri5, 1 tsit5); yp_eval
+ * (optional, [B][K][D]) receives dy/dt of the dense output at the points. */
+int orc_replay_yp(int method, const orc_field *F, int B, const double *y0, const double *t0,
+                  const double *t1, const double *mesh_t, const double *mesh_h,
+                  const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
+                  double *y_eval, double *yp_eval, double *y_final, int nthreads);
 int orc_replay_m(int method, const orc_field *F, int B, const double *y0, const double *t0,
                  const double *t1, const double *mesh_t, const double *mesh_h,
                  const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
                  double *y_eval, double *y_final, int nthreads) {
+  return orc_replay_yp(method, F, B, y0, t0, t1, mesh_t, mesh_h, mesh_n, mesh_cap, t_eval, K,
+                       y_eval, NULL, y_final, nthreads);
+}
+int orc_replay_yp(int method, const orc_field *F, int B, const double *y0, const double *t0,
+                  const double *t1, const double *mesh_t, const double *mesh_h,
+                  const int32_t *mesh_n, int mesh_cap, const double *t_eval, int K,
+                  double *y_eval, double *yp_eval, double *y_final, int nthreads) {
   job J;
   memset(&J, 0, sizeof(J));
   J.F = F;
@@ -1192,6 +1214,7 @@ int orc_replay_m(int method, const orc_field *F, int B, const double *y0, const 
   J.t1 = t1;
   J.t_eval = t_eval;
   J.y_eval = y_eval;
+  J.yp_eval = yp_eval;
   J.y_final = y_final;
   J.mesh_t = mesh_t;
   J.mesh_h = mesh_h;

@@ -246,7 +246,7 @@ def solve(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
     y0 [B, D] (float64 or float32; MLP: float32), t0/t1 [B] float64,
     t_eval [B, K] float64.  Keyword options as in ``make_options``.  With
     ``want_yp`` the solution also carries yp_eval [B, K, D], dy/dt of the
-    dense output at every evaluation point (Van der Pol and linear fields).
+    dense output at every evaluation point (every field, solved independently).
     """
     lib = _abi.load()
     B, D = y0.shape

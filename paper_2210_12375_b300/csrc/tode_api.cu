@@ -168,8 +168,8 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
   if (!y0 || !t0 || !t1 || !y_final || !n_acc || !n_rej || !n_feval || !status)
     return TODE_EINVAL;
   if (K > 0 && (!t_eval || !y_eval)) return TODE_EINVAL;
-  // the derivative at the points: the SIMT fields, solved independently
-  if (K > 0 && yp_eval && (f->kind == TODE_MLP || o->joint)) return TODE_EUNSUPPORTED;
+  // the derivative at the points: every field, solved independently
+  if (K > 0 && yp_eval && o->joint) return TODE_EUNSUPPORTED;
   if (tape && !tape_ok(tape, o, f)) return TODE_EINVAL;
   // a joint mesh is reversed from the tape, never re-run per instance
   if (tape && o->joint && !(tape->stride == 1 && tape->h_acc)) return TODE_EINVAL;

@@ -436,6 +436,15 @@ template <class Tab, typename T> __device__ __forceinline__ void dense_weights(T
                          T(Tab::q(i, 0)));
 }
 
+// Derivatives b_i'(theta) of the dense-output weights, each by Horner's rule.
+template <class Tab, typename T> __device__ __forceinline__ void dense_dweights(T th, T (&w)[7]) {
+#pragma unroll
+  for (int i = 1; i <= 7; ++i)
+    w[i - 1] = madd(th, madd(th, madd(th, T(4) * T(Tab::q(i, 3)), T(3) * T(Tab::q(i, 2))),
+                             T(2) * T(Tab::q(i, 1))),
+                    T(Tab::q(i, 0)));
+}
+
 // The stage derivatives k_1..k_7 of one step, as one indexable set.
 template <typename T, int R> struct Stages {
   T k[7][R];

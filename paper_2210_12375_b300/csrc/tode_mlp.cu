@@ -47,6 +47,7 @@ struct MlpArgs {
   const double* atol_b;
   double rtol, atol;
   float* ye;
+  float* yp;  // [B][K][D] dy/dt at the points, or NULL
   float* yf;
   int32_t *n_acc, *n_rej, *n_fe, *status;
   SolveOpts o;
@@ -294,6 +295,9 @@ __device__ __forceinline__ void store_pair8(unsigned char* t, int r, int col, in
 }
 
 enum : int { PH_IDLE = 0, PH_INIT0 = 1, PH_INIT1 = 2, PH_STAGE = 3 };  // PH_STAGE + s - 2
+// row flag beside FL_PREV_REJ / FL_REVERSE: an instance with t1 = t0 whose
+// points need dy/dt = f(t0, y0) runs one evaluation round and ends there
+constexpr int FL_YP_ONLY = 4;
 
 __device__ __forceinline__ float tanh_fast(float x) {
   float y;
@@ -557,6 +561,10 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       for (int q = 0; q < a.K; ++q)
 #pragma unroll
         for (int r = 0; r < C; ++r) ye[(size_t)q * D + r] = nan_(0.0f);
+      if (a.yp)
+        for (int q = 0; q < a.K; ++q)
+#pragma unroll
+          for (int r = 0; r < C; ++r) a.yp[((size_t)i * a.K + q) * D + coff + r] = nan_(0.0f);
       done = true;
     } else {
       while (s.cursor < a.K && tkey(flip(te[s.cursor], m)) == k0) {
@@ -564,7 +572,12 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         for (int r = 0; r < C; ++r) ye[(size_t)s.cursor * D + r] = y[r];
         s.cursor++;
       }
-      if (k1 == k0) {
+      if (k1 == k0 && a.yp && s.cursor > 0) {
+        // no step, but the points' dy/dt = f(t0, y0) takes one evaluation
+        s.status = ST_SUCCESS;
+        s.flags |= FL_YP_ONLY;
+        s.phase = PH_INIT0;
+      } else if (k1 == k0) {
         s.status = ST_SUCCESS;
         done = true;
       } else {
@@ -952,6 +965,13 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         p0 = madd(q0, q0, p0);
         p1 = madd(q1, q1, p1);
       }
+      if (a.yp) {  // points at t0: dy/dt = f(t0, y0) in the caller's time
+        const float dir = (s.flags & FL_REVERSE) ? -1.0f : 1.0f;
+        for (int q = 0; q < s.cursor; ++q)
+#pragma unroll
+          for (int r = 0; r < C; ++r)
+            a.yp[((size_t)s.inst * a.K + q) * D + coff + r] = dir * k1[r];
+      }
     } else if (s.phase == PH_INIT1) {
 #pragma unroll
       for (int r = 0; r < C; ++r) {
@@ -1003,7 +1023,18 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     }
 
     const int i = s.inst;
-    if (s.phase == PH_INIT0) {
+    if (s.phase == PH_INIT0 && (s.flags & FL_YP_ONLY)) {
+      // t1 = t0: the evaluation was for dy/dt only; the instance ends here
+#pragma unroll
+      for (int r = 0; r < C; ++r) a.yf[(size_t)i * D + coff + r] = y[r];
+      if (sub == 0) {
+        a.n_acc[i] = a.n_rej[i] = a.n_fe[i] = 0;
+        a.status[i] = ST_SUCCESS;
+        if (a.trace.cap > 0) a.trace.len[i] = 0;
+      }
+      s.phase = PH_IDLE;
+      if (MODE == MLP_FUSED) need_grab = true;
+    } else if (s.phase == PH_INIT0) {
       if (a.o.h0 > 0.0) {
         s.h = (float)a.o.h0;
         s.phase = PH_STAGE;
@@ -1080,11 +1111,11 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
           const long long kq = tkey(tq);
           if (kq > kn) break;
           float* dst = ye + (size_t)s.cursor * D;
+          const float th = kq == kn ? 1.0f : float(tq - s.t) / h;
           if (kq == kn) {
 #pragma unroll
             for (int r = 0; r < C; ++r) dst[r] = yn[r];
           } else {
-            const float th = float(tq - s.t) / h;
             float w[7];
             dense_weights<DP5, float>(th, w);
 #pragma unroll
@@ -1096,6 +1127,22 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
               acc = madd(w[5], k6[r], acc);
               acc = madd(w[6], f[r], acc);
               dst[r] = y[r] + madd(h, acc, ylo[r]);
+            }
+          }
+          if (a.yp) {  // dy/dt = sum_i b_i'(theta) k_i (the step size cancels)
+            float w[7];
+            dense_dweights<DP5, float>(th, w);
+            const float dir = (s.flags & FL_REVERSE) ? -1.0f : 1.0f;
+            float* dp = a.yp + ((size_t)i * a.K + s.cursor) * D + coff;
+#pragma unroll
+            for (int r = 0; r < C; ++r) {
+              float acc = w[0] * k1[r];
+              acc = madd(w[2], k3[r], acc);
+              acc = madd(w[3], k4[r], acc);
+              acc = madd(w[4], k5[r], acc);
+              acc = madd(w[5], k6[r], acc);
+              acc = madd(w[6], f[r], acc);
+              dp[r] = dir * acc;
             }
           }
           s.cursor++;
@@ -1150,6 +1197,11 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
           for (int q = s.cursor; q < a.K; ++q)
 #pragma unroll
             for (int r = 0; r < C; ++r) ye[(size_t)q * D + r] = nan_(0.0f);
+          if (a.yp)
+            for (int q = s.cursor; q < a.K; ++q)
+#pragma unroll
+              for (int r = 0; r < C; ++r)
+                a.yp[((size_t)i * a.K + q) * D + coff + r] = nan_(0.0f);
         }
 #pragma unroll
         for (int r = 0; r < C; ++r) a.yf[(size_t)i * D + coff + r] = y[r];
@@ -3790,6 +3842,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   a.rtol = r.o->rtol;
   a.atol = r.o->atol;
   a.ye = (float*)r.ye;
+  a.yp = (float*)r.yp;
   a.yf = (float*)r.yf;
   a.n_acc = r.n_acc;
   a.n_rej = r.n_rej;

@@ -602,6 +602,28 @@ def test_dense_output_derivative_pins():
     assert np.abs(rl["yp_eval"] - dex).max() <= 1e-6 * max(1.0, np.abs(dex).max())
 
 
+def test_replay_dense_derivative_equals_the_solve_on_its_own_mesh():
+    """The replay's dy/dt at the points (o9 with the interpolant's derivative)
+    on the mesh a solve recorded is the solve's own dy/dt, bit for bit: the
+    same steps from the same states (Van der Pol with instances in both
+    directions, and the MLP field, non-autonomous, with points at t0)."""
+    v = workloads.make(1, B=6)
+    t0, t1, te = v["t0"].copy(), v["t1"].copy(), v["t_eval"].copy()
+    t0[::2], t1[::2] = v["t1"][::2], v["t0"][::2]
+    te[::2] = te[::2, ::-1]
+    m = workloads.make(4, B=5)
+    for w in (dict(v, t0=t0, t1=t1, t_eval=te), m):
+        r = oracle.solve(w["field"], w["y0"], w["t0"], w["t1"], w["t_eval"],
+                         dict(rtol=w["rtol"], atol=w["atol"]), trace_cap=4000, want_yp=True)
+        assert (r["status"] == 0).all()
+        mt, mh, mn = mesh_from_trace(r)
+        p = oracle.replay(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"],
+                          want_yp=True)
+        assert np.array_equal(p["y_eval"], r["y_eval"])
+        assert np.array_equal(p["yp_eval"], r["yp_eval"])
+        assert (w["t_eval"][:, 0] == w["t0"]).any()
+
+
 # ---------------------------------------------------------------- starting step
 def _hnw_starting_step(lams, y0, rtol, atol, span):
     """The starting-step heuristic of Hairer-Norsett-Wanner Sec. II.4 for
