@@ -275,7 +275,13 @@ size_t tode_adjoint_scratch_size(const tode_field_desc* f, const tode_options* o
  * otherwise recomputing the stages from the checkpoints -- and writes
  *   gy0 [B][D]       = dL/dy0
  *   gparam           = VDP: dL/dmu [B]; LINEAR: dL/dA [B][D][D] (state
- *                      dtype, per instance); MLP: unused (NULL)
+ *                      dtype, per instance); MLP: NULL, or [B] double that
+ *                      receives each instance's time-translation sum S_t,
+ *                      the sum over its reversed stages of the cotangent of
+ *                      the network's time input = dL/d(delta) when t0, t1
+ *                      and the instance's evaluation points all move by
+ *                      delta (NaN where the gradients are NaN); the input
+ *                      tode_t_bounds_grad takes for dL/dt0 of this field
  *   gW, gb           = MLP only (host arrays of device pointers): dL/dW_l
  *                      [widths[l+1]][widths[l]] and dL/db_l [widths[l+1]],
  *                      float, summed over the batch in a fixed order
@@ -335,16 +341,20 @@ tode_err tode_t_eval_grad(int B, int K, int D, tode_prec prec, const void* gy_ev
  * frozen map (the discrete-adjoint reading of App. A, extended to the two
  * boundary times): every accepted step size but the last and every
  * evaluation point's step are held, t0 moves every mesh point before t1, and
- * the last step h = t1 - t_{N-1} absorbs the change.  Van der Pol and linear
- * fields (autonomous: the bounds enter through the dense-output abscissae
- * and the last step), independent solving, a stride-1 tape with h_acc filled
- * by the solve; TODE_EUNSUPPORTED for the MLP field or a joint solve,
- * TODE_EINVAL for a strided tape.
- *  g_t1 [B] (double, required) = dL/dt1: the last step size's cotangent.
- *  g_t0 [B] (double, may be NULL) = dL/dt0 = -sum_q <gy_eval[q], yp_eval[q]>
- *  - dL/dt1 (translating both bounds shifts every output by -dy/dt); needs
- *  yp_eval [B][K][D] from the same solve (tode_solve's dy/dt output) when
- *  gy_eval is given.
+ * the last step h = t1 - t_{N-1} absorbs the change.  Every field solved
+ * independently (TODE_EUNSUPPORTED for a joint solve; the MLP field with
+ * prec TODE_BF16W_SPLIT), a stride-1 tape with h_acc filled by the solve
+ * (TODE_EINVAL for a strided tape).
+ *  g_t1 [B] (double, required) = dL/dt1: the last step size's cotangent
+ *  (for the MLP field, whose stage times t_n + c_i h move with h, through
+ *  its time input too; that step is re-run in FP32 on the CUDA cores).
+ *  g_t0 [B] (double, may be NULL) = dL/dt0 = S_t - sum_q <gy_eval[q],
+ *  yp_eval[q]> - dL/dt1: translating both bounds and every point by delta
+ *  changes L by S_t delta, S_t = 0 for the autonomous Van der Pol and linear
+ *  fields; for the MLP field g_t0 must hold S_t on entry (tode_adjoint's
+ *  gparam of the same cotangents) and is overwritten.  Needs yp_eval
+ *  [B][K][D] from the same solve (tode_solve's dy/dt output) when gy_eval is
+ *  given.
  * gy_eval [B][K][D] and gy_final [B][D] (state dtype, NULL = 0) as for
  * tode_adjoint; instances whose status is not TODE_S_SUCCESS (or that needed
  * more tape slots than the tape has) get NaN; an instance with t1 = t0 gets

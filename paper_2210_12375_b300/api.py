@@ -310,10 +310,14 @@ def t_eval_grad(gy_eval: torch.Tensor, yp_eval: torch.Tensor,
 
 
 def adjoint(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=None,
-            gy_final=None, *, stream=None, scratch: Optional[torch.Tensor] = None, **opt_kw):
+            gy_final=None, *, stream=None, scratch: Optional[torch.Tensor] = None,
+            want_tshift: bool = False, **opt_kw):
     """Discrete adjoint of the forward solve that filled ``tape`` (App. A:
     backpropagation through the solver on the frozen mesh).  Returns
-    (gy0, gparam, overflow)."""
+    (gy0, gparam, overflow); for the MLP field gparam is (gW, gb), and with
+    ``want_tshift`` (gW, gb, tshift): tshift [B] float64, the derivative of L
+    when every time of an instance (t0, t1, its evaluation points) moves
+    together, which ``t_bounds_grad`` needs for dL/dt0 of this field."""
     lib = _abi.load()
     B, D = sol.y_final.shape
     K = 0 if t_eval is None else t_eval.shape[1]
@@ -340,11 +344,16 @@ def adjoint(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=Non
         gW_arr = (C.c_void_p * len(gW))(*[g.data_ptr() for g in gW])
         gb_arr = (C.c_void_p * len(gb))(*[g.data_ptr() for g in gb])
         gparam = (gW, gb)
+    gp_ptr = _ptr(gparam) if params is not None else None
+    if isinstance(field, MLP) and want_tshift:  # the MLP field's gparam: the time sums
+        ts = torch.empty(B, dtype=torch.float64, device=dev)
+        gparam = (gW, gb, ts)
+        gp_ptr = _ptr(ts)
     overflow = torch.zeros(1, dtype=torch.int32, device=dev)
     code = lib.tode_adjoint(
         C.byref(fd), C.byref(opts), _ptr(t0), _ptr(t1), _ptr(t_eval) if K > 0 else None,
         int(K), _ptr(sol.n_acc), _ptr(sol.status), C.byref(tape_c), _ptr(gy_eval),
-        _ptr(gy_final), _ptr(gy0), _ptr(gparam) if params is not None else None, gW_arr, gb_arr,
+        _ptr(gy_final), _ptr(gy0), gp_ptr, gW_arr, gb_arr,
         _ptr(overflow), _ptr(scratch), C.c_size_t(scratch.numel()), _stream_handle(stream))
     _abi.check(code, "tode_adjoint")
     return gy0, gparam, overflow
@@ -412,12 +421,14 @@ def joint_adjoint(field, y1: torch.Tensor, t0: float, t1: float, t_eval=None, gy
 
 
 def t_bounds_grad(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_eval=None,
-                  gy_final=None, *, stream=None, want_t0: bool = True, **opt_kw):
+                  gy_final=None, *, stream=None, want_t0: bool = True,
+                  tshift: Optional[torch.Tensor] = None, **opt_kw):
     """(dL/dt0, dL/dt1) [B] float64 of the forward solve that filled
     ``tape`` (stride 1 with the accepted step sizes): the frozen map with
     every step size but the last held and the last ending at t1.  dL/dt0
     needs the solve's dy/dt at the points (``want_yp=True``) when gy_eval is
-    given.  Van der Pol and linear fields."""
+    given, and for the MLP field (time-dependent) the adjoint's ``tshift``
+    (``adjoint(..., want_tshift=True)``) of the same cotangents."""
     lib = _abi.load()
     B, D = sol.y_final.shape
     K = 0 if t_eval is None else t_eval.shape[1]
@@ -427,7 +438,14 @@ def t_bounds_grad(field, t0, t1, t_eval, sol: Solution, tape: TapeBuffers, gy_ev
     fd = field.desc(B, D, keep)
     tape_c = tape.c()
     g1 = torch.empty(B, dtype=torch.float64, device=dev)
-    g0 = torch.empty(B, dtype=torch.float64, device=dev) if want_t0 else None
+    g0 = None
+    if want_t0:
+        if isinstance(field, MLP):  # dL/dt0 starts from the translation sums
+            if tshift is None:
+                raise ValueError("dL/dt0 of the MLP field needs the adjoint's tshift")
+            g0 = tshift.to(torch.float64).clone()
+        else:
+            g0 = torch.empty(B, dtype=torch.float64, device=dev)
     yp = sol.yp_eval if (want_t0 and K > 0 and gy_eval is not None) else None
     code = lib.tode_t_bounds_grad(
         C.byref(fd), C.byref(opts), _ptr(t0), _ptr(t1), _ptr(t_eval) if K > 0 else None,

@@ -121,16 +121,16 @@ class _Odeint(torch.autograd.Function):
         # the forward also writes dy/dt there
         want_t = ctx.needs_input_grad[2] or ctx.needs_input_grad[3]
         want_yp = t_eval is not None and (ctx.needs_input_grad[4] or ctx.needs_input_grad[2])
-        if want_t and (isinstance(spec["field"], api.MLP) or spec["opt"].get("joint")):
-            raise RuntimeError("gradients with respect to t0 and t1 are built for the Van der "
-                               "Pol and linear fields, solved independently")
+        if want_t and spec["opt"].get("joint"):
+            raise RuntimeError("gradients with respect to t0 and t1 are built for independent "
+                               "solves")
         sol, tape, N, chunk = _solve_with_tape(field, y0, t0, t1, t_eval, spec["opt"],
                                                spec["budget"], spec["hint"], want_yp)
         spec["last_n_acc_max"] = N
         spec["mlp_chunk"] = chunk
         ctx.field, ctx.sol, ctx.tape, ctx.opt = field, sol, tape, spec["opt"]
         ctx.chunk, ctx.N = chunk, N
-        if want_t and tape is not None and tape.stride != 1:
+        if want_t and (tape is None or tape.stride != 1):
             raise RuntimeError("gradients with respect to t0 and t1 need one tape slot per "
                                "accepted step: raise hbm_budget_bytes")
         ctx.want_t = want_t
@@ -149,12 +149,15 @@ class _Odeint(torch.autograd.Function):
             gy0, gp = _mlp_adjoint_chunked(field, y0.detach(), t0, t1, t_eval, sol, gye, gyf,
                                            ctx.opt, ctx.chunk, ctx.N)
         else:
+            mlp_t = ctx.want_t and isinstance(field, api.MLP)
             gy0, gp, ovf = api.adjoint(field, t0, t1, t_eval, sol, ctx.tape, gye, gyf,
-                                       **ctx.opt)
+                                       want_tshift=mlp_t, **ctx.opt)
             if int(ovf.item()) != 0:
                 raise RuntimeError("tode_adjoint: the checkpoint tape overflowed")
+        tshift = None
         if isinstance(field, api.MLP):
-            gW, gb = gp
+            gW, gb = gp[0], gp[1]
+            tshift = gp[2] if len(gp) > 2 else None
             grads = [g.to(w.dtype) for g, w in zip(gW + gb, field.W + field.b)]
         else:
             grads = [gp]
@@ -164,7 +167,8 @@ class _Odeint(torch.autograd.Function):
         g_t0 = g_t1 = None
         if ctx.want_t:
             g_t0, g_t1 = api.t_bounds_grad(field, t0, t1, t_eval, sol, ctx.tape, gye, gyf,
-                                           want_t0=ctx.needs_input_grad[2], **ctx.opt)
+                                           want_t0=ctx.needs_input_grad[2], tshift=tshift,
+                                           **ctx.opt)
             g_t0 = g_t0.to(t0.dtype) if g_t0 is not None and ctx.needs_input_grad[2] else None
             g_t1 = g_t1.to(t1.dtype) if ctx.needs_input_grad[3] else None
         return (None, gy0, g_t0, g_t1, g_te, *grads)
@@ -182,7 +186,8 @@ def odeint_adjoint(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
     and the status carry no gradient.  A t_eval that requires grad receives
     dL/dt_eval through dy/dt of the dense output; t0 and t1 that require grad
     receive the gradients of the frozen map with respect to the integration
-    bounds (Van der Pol and linear fields; one tape slot per accepted step).
+    bounds (every field, solved independently; one tape slot per accepted
+    step).
     Keyword options as in ``make_options`` (the fused form is used).
     """
     opt = {k: v for k, v in opt_kw.items() if k != "form"}

@@ -31,6 +31,7 @@ UNITS = {
     "tode_static.cu": [],
     "tode_tc_gemm.cu": [],
     "tode_mlp.cu": ["-fmad=false"],
+    "tode_mlp_tb.cu": [],
     "tode_peak.cu": [],
 }
 

@@ -327,7 +327,8 @@ tode_err tode_t_bounds_grad(const tode_field_desc* f, const tode_options* o, con
   if (!opts_ok(o) || K < 0) return TODE_EINVAL;
   tode_err e = field_ok(f, o);
   if (e != TODE_OK) return e;
-  if (f->kind == TODE_MLP || o->joint) return TODE_EUNSUPPORTED;
+  if (o->joint) return TODE_EUNSUPPORTED;
+  if (f->kind == TODE_MLP && o->prec != TODE_BF16W_SPLIT) return TODE_EUNSUPPORTED;
   if (f->B == 0) return TODE_OK;
   if (!t0 || !t1 || !n_acc || !status || !tape || !g_t1) return TODE_EINVAL;
   if (K > 0 && !t_eval) return TODE_EINVAL;
@@ -350,6 +351,7 @@ tode_err tode_t_bounds_grad(const tode_field_desc* f, const tode_options* o, con
   r.stream = (cudaStream_t)stream;
   e = device_sms(&r.num_sms);
   if (e != TODE_OK) return e;
+  if (f->kind == TODE_MLP) return mlp_t_bounds(r, yp_eval, g_t0, g_t1);
   return o->prec == TODE_F64 ? simt_t_bounds_f64(r, yp_eval, g_t0, g_t1)
                              : simt_t_bounds_f32(r, yp_eval, g_t0, g_t1);
 }

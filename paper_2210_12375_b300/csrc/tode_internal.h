@@ -151,11 +151,14 @@ tode_err simt_t_bounds_ts5_f32(const AdjReq& r, const void* yp, double* gt0, dou
 
 bool simt_supported(int kind, int D);
 
+// the MLP field's most weight layers
+constexpr int MLP_MAX_LAYERS = 4;
 bool mlp_supported(const tode_field_desc* f);
 size_t mlp_workspace_bytes(const tode_field_desc* f, const tode_options* o);
 tode_err mlp_solve(const SolveReq& r, bool split);
 size_t mlp_adjoint_scratch_bytes(const tode_field_desc* f, const tode_options* o, int slots,
                                  int num_sms);
 tode_err mlp_adjoint(const AdjReq& r);
+tode_err mlp_t_bounds(const AdjReq& r, const void* yp, double* gt0, double* gt1);
 
 }  // namespace tode

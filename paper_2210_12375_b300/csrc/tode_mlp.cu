@@ -35,7 +35,6 @@
 
 namespace tode {
 
-constexpr int MLP_MAX_LAYERS = 4;
 
 struct MlpArgs {
   int B, K;
@@ -1404,6 +1403,7 @@ struct MlpAdjArgs {
   float* part;   // [grid][P_FLOATS]
   int32_t* overflow;
   int32_t* err;
+  double* gts;   // [B] or NULL: each instance's time-translation sum (see tode.h)
 };
 
 constexpr int ADJ_ROUNDS = 7;  // one reverse round per stage, 7..1
@@ -1514,6 +1514,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   double tn = 0.0, tnext = 0.0;
   float h = 0.0f;
   unsigned long long rmask = 0;  // the instance runs backward in time: tau = -t, field -f
+  float tsum = 0.0f;  // the time inputs' cotangents of the instance's stages (a.gts)
   float yb[16], db3[16], kb[7][16];
 #pragma unroll
   for (int r = 0; r < C; ++r) {
@@ -1558,6 +1559,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
         }
 #pragma unroll
         for (int r = 0; r < C; ++r) a.gy0[(size_t)i * D + coff + r] = bad ? nan_(0.0f) : yb[r];
+        if (a.gts && half == 0) a.gts[i] = bad ? (double)nan_(0.0f) : (double)tsum;
         inst += grid * 128;
         finishing = false;
       }
@@ -1575,6 +1577,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
       }
 #pragma unroll
       for (int r = 0; r < C; ++r) yb[r] = a.gyf ? a.gyf[(size_t)i * D + coff + r] : 0.0f;
+      tsum = 0.0f;
       q = a.K - 1;
       n = N - 1;
       if (bad || n < 0) {
@@ -1754,6 +1757,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
     barrier();
 
     float fg[16];  // g = J_f(Y_s)^T kbar_s
+    float tcot = 0.0f;  // and the time input's cotangent (a.gts only)
     {
       const bool acc0 = !dw_first;
       // B2: acc = kbar W3;  dW3^T += h2^T kbar  (split: hi*hi + lo*hi + hi*lo)
@@ -1839,6 +1843,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
       }
       wait_mma();
       tc::tmem_ld16(tl + L::T_R + coff, fg);
+      // column D of the product: the cotangent of the field's time input
+      if (a.gts) tcot = tc::tmem_ld1(tl + L::T_R + D);
       tc::tmem_wait_ld();
       dw_first = false;
     }
@@ -1863,6 +1869,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
       }
 #pragma unroll
       for (int r = 0; r < C; ++r) yb[r] += fg[r];
+      tsum += tcot;
       if (s == 1) {  // step n reversed
         n -= 1;
         if (n >= 0) load_step(inst);
@@ -2053,6 +2060,7 @@ struct WideAdjArgs {
   int32_t* rounds;               // [grid]: reverse rounds staged by each CTA
   int32_t* overflow;
   int32_t* err;
+  double* gts;  // [B] or NULL: each instance's time-translation sum
 };
 
 // 8 floats from a BF16 hi + lo pair of 16-byte rows
@@ -2151,6 +2159,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
   int n = -1, N = 0, q = -1;
   double tn = 0.0, tnext = 0.0;
   float h = 0.0f;
+  float tsum = 0.0f;  // the time inputs' cotangents of the instance's stages (a.gts)
   float yb[16], kb[7][16];
 #pragma unroll
   for (int r = 0; r < C; ++r) {
@@ -2187,6 +2196,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     }
 #pragma unroll
     for (int r = 0; r < C; ++r) a.gy0[(size_t)inst * D + coff + r] = bad ? nan_(0.0f) : yb[r];
+    if (a.gts && sub == 0) a.gts[inst] = bad ? (double)nan_(0.0f) : (double)tsum;
     act = false;
   };
   if (inst >= 0) {
@@ -2500,12 +2510,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     gemm(6, tc::smem_u32(sH), H, K0);  // gx = delta1 W1
     wait_mma();
     float fg[16];
+    float tcot = 0.0f;  // the time input's cotangent (column D), hi + lo rows
     {
       float v0[16], v1[16];
       tc::tmem_ld16(tbase + lanes + 32 * hf, v0);
       tc::tmem_ld16(tbase + lanes + 32 * hf + 16, v1);
+      if (a.gts) tcot = tc::tmem_ld1(tbase + lanes + D);
       tc::tmem_wait_ld();
       combine_pair16(v0, v1, odd, fg);
+      if (a.gts) tcot += __shfl_xor_sync(0xffffffffu, tcot, 1);
     }
     k_round++;
     tc::fence_before_sync();
@@ -2524,6 +2537,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     }
 #pragma unroll
     for (int r = 0; r < C; ++r) yb[r] += fg[r];
+    tsum += tcot;
     if (s == 1) {
       n -= 1;
       if (n >= 0) load_step();
@@ -4145,6 +4159,7 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   a.bias = (const float*)(base + p.off_bias);
   a.err = (int32_t*)(base + 128);
   a.overflow = r.overflow;
+  a.gts = (double*)r.gparam;  // MLP field: the time-translation sums, or NULL
   a.cap = p.cap;
   a.rounds = (int32_t*)(base + p.off_rounds);
   unsigned char* img = (unsigned char*)base + p.off_img;
@@ -4279,6 +4294,7 @@ tode_err mlp_adjoint(const AdjReq& r) {
   p += align256((size_t)Cfg::WIMG_BYTES);
   a.part = (float*)p;
   a.overflow = r.overflow;
+  a.gts = (double*)r.gparam;  // MLP field: the time-translation sums, or NULL
   {
     size_t loff[MLP_MAX_LAYERS] = {};
     for (int l = 0; l < Cfg::NL; ++l) loff[l] = Cfg::W_off(l);

@@ -124,3 +124,98 @@ def test_t_bounds_through_autograd_and_edge_cases():
     failed = (sol.status != 0).cpu().numpy()
     assert failed.any()
     assert np.isnan(g1.cpu().numpy()[failed]).all() and np.isnan(g0.cpu().numpy()[failed]).all()
+
+
+def _mlp_case(cfg, B, mixed):
+    w = dict(make(cfg, B=B), split=True)
+    if mixed:  # every other instance backward over the same interval
+        t0, t1, te = w["t0"].copy(), w["t1"].copy(), w["t_eval"].copy()
+        t0[::2], t1[::2] = w["t1"][::2], w["t0"][::2]
+        te[::2] = te[::2, ::-1]
+        w = dict(w, t0=t0, t1=t1, t_eval=np.ascontiguousarray(te))
+    return w
+
+
+@pytest.mark.parametrize("cfg,B,mixed", [(4, 256, False), (4, 256, True), (5, 96, True)])
+def test_t_bounds_grad_mlp_vs_oracle_on_the_gpu_mesh(cfg, B, mixed):
+    """The MLP field (time-dependent: its stage times move with the last
+    step and with the translation of every time): dL/dt1 from the last step
+    re-run on the CUDA cores, dL/dt0 from the tensor-core adjoint's
+    translation sums, against the FP64 oracle's adjoint of the GPU's mesh
+    (same BF16 weights) within the BF16-weight gradient tolerance 2e-3,
+    relative l2 over the batch, both directions of integration."""
+    w = _mlp_case(cfg, B, mixed)
+    D = w["y0"].shape[1]
+    probe = gpu_solve(w, torch.float32, "fused", trace_cap=64)
+    assert (probe["status"] == 0).all()
+    tape = tode.TapeBuffers.allocate(B, D, torch.float32, int(probe["n_acc"].max()), 1, "cuda",
+                                     stages=True, minimal=True)
+    g = gpu_solve(w, torch.float32, "fused", tape=tape, want_yp=True)
+    assert np.array_equal(g["n_acc"], probe["n_acc"])
+    rng = np.random.default_rng(5)
+    gye = rng.standard_normal(g["y_eval"].shape)
+    gyf = rng.standard_normal(g["y_final"].shape)
+    dev = g["_dev"]
+    gye_t = torch.tensor(gye, dtype=torch.float32, device="cuda")
+    gyf_t = torch.tensor(gyf, dtype=torch.float32, device="cuda")
+    opt = dict(rtol=w["rtol"], atol=w["atol"])
+    gy0, (gW, gb, ts), ovf = tode.adjoint(dev["field"], dev["t0"], dev["t1"], dev["te"],
+                                          g["_sol"], tape, gye_t, gyf_t, want_tshift=True, **opt)
+    gy0_plain, _, _ = tode.adjoint(dev["field"], dev["t0"], dev["t1"], dev["te"], g["_sol"],
+                                   tape, gye_t, gyf_t, **opt)
+    g0, g1 = tode.t_bounds_grad(dev["field"], dev["t0"], dev["t1"], dev["te"], g["_sol"], tape,
+                                gye_t, gyf_t, tshift=ts, **opt)
+    torch.cuda.synchronize()
+    assert int(ovf.item()) == 0
+    # the translation sums change nothing else
+    assert torch.equal(gy0, gy0_plain)
+    mt, mh, mn = mesh_from_trace(probe)
+    ref = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"], gye, gyf,
+                         want_t_bounds=True)
+    g0, g1 = g0.cpu().numpy(), g1.cpu().numpy()
+    assert np.isfinite(g0).all() and np.isfinite(g1).all()
+    assert _rel(g1, ref["gt1"]) <= 2e-3, _rel(g1, ref["gt1"])
+    assert _rel(g0, ref["gt0"]) <= 2e-3, _rel(g0, ref["gt0"])
+
+
+def test_t_bounds_mlp_through_autograd_and_edge_cases():
+    """odeint_adjoint with t0 and t1 requiring grad for the MLP field gives
+    the direct calls' numbers; an empty interval gets dL/dt1 = 0 and a
+    failed instance NaN."""
+    w = dict(make(4, B=160), split=True)
+    w["t1"][3] = w["t0"][3]  # an empty interval
+    w["t_eval"][3] = w["t0"][3]
+    dev = "cuda"
+    from gpu_helpers import device_field
+    f = device_field(w, torch.float32)
+    y0 = torch.tensor(w["y0"], dtype=torch.float32, device=dev)
+    t0 = torch.tensor(w["t0"], device=dev, requires_grad=True)
+    t1 = torch.tensor(w["t1"], device=dev, requires_grad=True)
+    te = torch.tensor(w["t_eval"], device=dev)
+    ye, yf, n_acc, n_rej, st = tode.odeint_adjoint(f, y0, t0, t1, te, rtol=w["rtol"],
+                                                   atol=w["atol"])
+    loss = (ye.double() ** 2).sum() + yf.double().sum()
+    gt0, gt1 = torch.autograd.grad(loss, [t0, t1])
+    g = gpu_solve(w, torch.float32, "fused", trace_cap=64)
+    mt, mh, mn = mesh_from_trace(g)
+    gye = 2.0 * ye.detach().double().cpu().numpy()
+    gyf = np.ones(yf.shape)
+    ref = oracle.adjoint(w["field"], w["y0"], w["t0"], w["t1"], mt, mh, mn, w["t_eval"], gye, gyf,
+                         want_t_bounds=True)
+    assert _rel(gt1.cpu().numpy(), ref["gt1"]) <= 2e-3
+    assert _rel(gt0.cpu().numpy(), ref["gt0"]) <= 2e-3
+    assert gt1[3].item() == 0.0
+    B, D = w["y0"].shape
+    tape = tode.TapeBuffers.allocate(B, D, torch.float32, 8, 1, dev, stages=True, minimal=True)
+    sol = tode.solve(f, y0, t0.detach(), t1.detach(), te, tape=tape, want_yp=True,
+                     rtol=w["rtol"], atol=w["atol"], max_steps=2)
+    gye_t = torch.ones_like(sol.y_eval)
+    _, (_, _, ts), _ = tode.adjoint(f, t0.detach(), t1.detach(), te, sol, tape, gye_t, None,
+                                    want_tshift=True, rtol=w["rtol"], atol=w["atol"],
+                                    max_steps=2)
+    g0, g1 = tode.t_bounds_grad(f, t0.detach(), t1.detach(), te, sol, tape, gye_t, None,
+                                tshift=ts, rtol=w["rtol"], atol=w["atol"], max_steps=2)
+    failed = (sol.status != 0).cpu().numpy()
+    assert failed.any()
+    assert np.isnan(g1.cpu().numpy()[failed]).all() and np.isnan(g0.cpu().numpy()[failed]).all()
+    assert np.isfinite(g1.cpu().numpy()[~failed]).all()
