@@ -162,11 +162,11 @@ TRAFFIC = {
     # captured on the first 32,768 instances, x8 (the tape grows with the steps)
     ("vdp_mix_b262144", "k_fused<VdpField<float>>"): 8 * 93.10e6,
     ("vdp_mix_b262144", "k_adjoint_steps<VdpAdj<float>>"): 8 * 123.80e6,
-    ("mlp_d32_h128", "k_mlp_fused"): 14.15e6,
-    ("mlp_d32_h128", "k_mlp_adjoint"): 49.46e6,
+    ("mlp_d32_h128", "k_mlp_fused"): 11.17e6,
+    ("mlp_d32_h128", "k_mlp_adjoint"): 48.45e6,
     # full size (B = 65,536), one pass per launch: the forward launch, and the
     # sum over the 16 launches of one adjoint call (the call is the entry)
-    ("mlp_d64_h512", "k_mlp_fused"): 1121.63e6,
+    ("mlp_d64_h512", "k_mlp_fused"): 1118.73e6,
     ("mlp_d64_h512", "k_mlp_adjoint"): 65.204e9,
     ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 69.76e6,
 }

@@ -314,7 +314,10 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
  *    library-owned device array of TODE_STATIC_ADJOINT_SCRATCH_BYTES; a
  *    valid problem whose tode_adjoint_scratch_size exceeds it is rejected
  *    with TODE_EWORKSPACE before any device work (a strided tape: lower
- *    tape->stride; otherwise split the batch).
+ *    tape->stride; otherwise split the batch).  The wide MLP network
+ *    (D = 64, hidden 512) stages gigabytes of layer rows for its weight
+ *    gradients and is always rejected this way; the D = 32, hidden 128
+ *    network fits.
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  *  - The first call on each device looks up the array's device address with
  *    that device current (cudaGetSymbolAddress) and caches it; make that
