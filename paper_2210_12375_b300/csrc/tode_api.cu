@@ -49,7 +49,8 @@ static tode_err field_ok(const tode_field_desc* f, const tode_options* o) {
   }
   if (f->kind == TODE_MLP) {
     if (o->prec != TODE_BF16W && o->prec != TODE_BF16W_SPLIT) return TODE_EUNSUPPORTED;
-    if (o->method != TODE_DOPRI5) return TODE_EUNSUPPORTED;  // the MLP solver is dopri5
+    // tsit5 on the split form only (the adjoints and the reported form)
+    if (o->method == TODE_TSIT5 && o->prec != TODE_BF16W_SPLIT) return TODE_EUNSUPPORTED;
     if (!f->widths || !f->W || !f->b) return TODE_EINVAL;
     if (!mlp_supported(f)) return TODE_EUNSUPPORTED;
     if (f->B > 0)
@@ -268,7 +269,7 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
 
 static bool jadj_ok(const tode_field_desc* f, const tode_options* o) {
   return f->kind == TODE_MLP && o->prec == TODE_BF16W_SPLIT && !o->rtol_b && !o->atol_b &&
-         !o->joint;
+         !o->joint && o->method == TODE_DOPRI5;
 }
 
 size_t tode_joint_adjoint_workspace_size(const tode_field_desc* f, const tode_options* o) {

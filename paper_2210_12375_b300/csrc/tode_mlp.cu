@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 namespace tode {
 
@@ -379,6 +380,31 @@ __device__ __forceinline__ float dp_a(int s, int j) {
     default: return 0.0f;
   }
 }
+// a_{s,j} of the pair Tab as float (dopri5: dp_a, the same values)
+template <class Tab> __device__ __forceinline__ float tab_a(int s, int j) {
+  if constexpr (std::is_same<Tab, DP5>::value) {
+    return dp_a(s, j);
+  } else {
+#define TODE_TA(S, J) \
+  case S * 8 + J: return float(Tab::a(S, J));
+    switch (s * 8 + j) {
+      TODE_TA(2, 1)
+      TODE_TA(3, 1) TODE_TA(3, 2)
+      TODE_TA(4, 1) TODE_TA(4, 2) TODE_TA(4, 3)
+      TODE_TA(5, 1) TODE_TA(5, 2) TODE_TA(5, 3) TODE_TA(5, 4)
+      TODE_TA(6, 1) TODE_TA(6, 2) TODE_TA(6, 3) TODE_TA(6, 4) TODE_TA(6, 5)
+      TODE_TA(7, 1) TODE_TA(7, 2) TODE_TA(7, 3) TODE_TA(7, 4) TODE_TA(7, 5) TODE_TA(7, 6)
+      default: return 0.0f;
+    }
+#undef TODE_TA
+  }
+}
+// the pair keeps k_2 in its solution, error or dense output (tsit5; dopri5
+// drops it)
+template <class Tab> __host__ __device__ constexpr bool tab_k2() {
+  return Tab::b(2) != 0.0 || Tab::e(2) != 0.0 || Tab::q(2, 0) != 0.0 || Tab::q(2, 1) != 0.0 ||
+         Tab::q(2, 2) != 0.0 || Tab::q(2, 3) != 0.0;
+}
 // Per-row solver state (identical scalars in both threads of the row).
 struct MlpRow {
   int inst, phase, cursor, status, flags, n_acc, n_rej;
@@ -392,8 +418,9 @@ struct MlpRow {
 // integrates them to their end.  Plain: tile c of ROWS instances belongs to
 // CTA c mod grid; the initialising launch runs the starting-step rounds, every
 // later launch one attempt (six stage rounds) per running instance, with the
-// state parked in the workspace in between.
-template <class Cfg, int MODE>
+// state parked in the workspace in between.  Tab: the Runge-Kutta pair
+// (dopri5 or tsit5; the same seven-stage FSAL structure).
+template <class Cfg, int MODE, class Tab>
 __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   constexpr int D = Cfg::D, H = Cfg::H, NL = Cfg::NL, K0 = Cfg::K0, C = Cfg::C;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -697,7 +724,6 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     }
 
     // ---- this row's field input [Y; t] for the round
-    using Cc = DP5;
     float Y[16];
     float tin = 0.0f;
     const int stage = s.phase - PH_STAGE + 2;  // 2..7 in stage phases
@@ -722,27 +748,38 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       const float h = s.h;
       double cs = 0.0;
       // Y_s = y + h sum_j a_sj k_j, the terms in the order j = 1, 2, ...
-      // (the stage-7 row is b, which has no k2 term)
+      // (dopri5's stage-7 row is b, which has no k2 term)
       float acc[16];
-      const float a1 = dp_a(stage, 1);
+      const float a1 = tab_a<Tab>(stage, 1);
 #pragma unroll
       for (int r = 0; r < C; ++r) acc[r] = a1 * k1[r];
       for (int j = 2; j < stage && j <= 6; ++j) {
-        if (stage == 7 && j == 2) continue;
+        if (stage == 7 && j == 2 && Tab::a(7, 2) == 0.0) continue;
         float kj[16];
         kget(j, kj);
-        const float c = dp_a(stage, j);
+        const float c = tab_a<Tab>(stage, j);
 #pragma unroll
         for (int r = 0; r < C; ++r) acc[r] = madd(c, kj[r], acc[r]);
       }
 #pragma unroll
       for (int r = 0; r < C; ++r) Y[r] = (stage == 7) ? y[r] + h * acc[r] : madd(h, acc[r], y[r]);
-      switch (stage) {
-        case 2: cs = Cc::c2; break;
-        case 3: cs = Cc::c3; break;
-        case 4: cs = Cc::c4; break;
-        case 5: cs = Cc::c5; break;
-        default: cs = 1.0; break;
+      if constexpr (std::is_same<Tab, DP5>::value) {
+        switch (stage) {
+          case 2: cs = DP5::c2; break;
+          case 3: cs = DP5::c3; break;
+          case 4: cs = DP5::c4; break;
+          case 5: cs = DP5::c5; break;
+          default: cs = 1.0; break;
+        }
+      } else {
+        switch (stage) {
+          case 2: cs = Tab::c(2); break;
+          case 3: cs = Tab::c(3); break;
+          case 4: cs = Tab::c(4); break;
+          case 5: cs = Tab::c(5); break;
+          case 6: cs = Tab::c(6); break;
+          default: cs = Tab::c(7); break;
+        }
       }
       tin = (float)flip(s.t + cs * (double)h, rev_mask(s.flags));
     }
@@ -955,6 +992,8 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     int fin = 1;
     float inc[16];
     float k3[16], k4[16], k5[16], k6[16];  // stage 7: the attempt's k3..k6
+    constexpr bool K2 = tab_k2<Tab>();
+    float k2[K2 ? 16 : 1];  // and k2 where the pair uses it
     if (s.phase == PH_INIT0) {
 #pragma unroll
       for (int r = 0; r < C; ++r) {
@@ -981,25 +1020,28 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
     } else if (s.phase >= PH_STAGE) {
       if (stage < 7) kput(stage, f);
       if (stage == 7) {
+        if constexpr (K2) kget(2, k2);
         kget(3, k3);
         kget(4, k4);
         kget(5, k5);
         kget(6, k6);
 #pragma unroll
         for (int r = 0; r < C; ++r) {
-          float acc = float(Cc::b1) * k1[r];
-          acc = madd(float(Cc::b3), k3[r], acc);
-          acc = madd(float(Cc::b4), k4[r], acc);
-          acc = madd(float(Cc::b5), k5[r], acc);
-          acc = madd(float(Cc::b6), k6[r], acc);
+          float acc = float(Tab::b(1)) * k1[r];
+          if constexpr (K2) acc = madd(float(Tab::b(2)), k2[r], acc);
+          acc = madd(float(Tab::b(3)), k3[r], acc);
+          acc = madd(float(Tab::b(4)), k4[r], acc);
+          acc = madd(float(Tab::b(5)), k5[r], acc);
+          acc = madd(float(Tab::b(6)), k6[r], acc);
           inc[r] = s.h * acc;
           const float y1 = y[r] + inc[r];
-          float e = float(Cc::e1) * k1[r];
-          e = madd(float(Cc::e3), k3[r], e);
-          e = madd(float(Cc::e4), k4[r], e);
-          e = madd(float(Cc::e5), k5[r], e);
-          e = madd(float(Cc::e6), k6[r], e);
-          e = madd(float(Cc::e7), f[r], e);
+          float e = float(Tab::e(1)) * k1[r];
+          if constexpr (K2) e = madd(float(Tab::e(2)), k2[r], e);
+          e = madd(float(Tab::e(3)), k3[r], e);
+          e = madd(float(Tab::e(4)), k4[r], e);
+          e = madd(float(Tab::e(5)), k5[r], e);
+          e = madd(float(Tab::e(6)), k6[r], e);
+          e = madd(float(Tab::e(7)), f[r], e);
           e = s.h * e;
           const float sc = madd(s.rtol, tmax(fabsf(y[r]), fabsf(y1)), s.atol);
           const float q = e / sc;
@@ -1116,10 +1158,11 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
             for (int r = 0; r < C; ++r) dst[r] = yn[r];
           } else {
             float w[7];
-            dense_weights<DP5, float>(th, w);
+            dense_weights<Tab, float>(th, w);
 #pragma unroll
             for (int r = 0; r < C; ++r) {
               float acc = w[0] * k1[r];
+              if constexpr (K2) acc = madd(w[1], k2[r], acc);
               acc = madd(w[2], k3[r], acc);
               acc = madd(w[3], k4[r], acc);
               acc = madd(w[4], k5[r], acc);
@@ -1130,12 +1173,13 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
           }
           if (a.yp) {  // dy/dt = sum_i b_i'(theta) k_i (the step size cancels)
             float w[7];
-            dense_dweights<DP5, float>(th, w);
+            dense_dweights<Tab, float>(th, w);
             const float dir = (s.flags & FL_REVERSE) ? -1.0f : 1.0f;
             float* dp = a.yp + ((size_t)i * a.K + s.cursor) * D + coff;
 #pragma unroll
             for (int r = 0; r < C; ++r) {
               float acc = w[0] * k1[r];
+              if constexpr (K2) acc = madd(w[1], k2[r], acc);
               acc = madd(w[2], k3[r], acc);
               acc = madd(w[3], k4[r], acc);
               acc = madd(w[4], k5[r], acc);
@@ -1233,17 +1277,17 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   if (warp == 0) tc::tmem_dealloc(tbase, Cfg::TMEM_COLS);
 }
 
-template <class Cfg>
+template <class Cfg, class Tab = DP5>
 __global__ void __launch_bounds__(256, 1) k_mlp_fused(MlpArgs a) {
-  mlp_solver<Cfg, MLP_FUSED>(a);
+  mlp_solver<Cfg, MLP_FUSED, Tab>(a);
 }
-template <class Cfg>
+template <class Cfg, class Tab = DP5>
 __global__ void __launch_bounds__(256, 1) k_mlp_plain_init(MlpArgs a) {
-  mlp_solver<Cfg, MLP_PLAIN_INIT>(a);
+  mlp_solver<Cfg, MLP_PLAIN_INIT, Tab>(a);
 }
-template <class Cfg>
+template <class Cfg, class Tab = DP5>
 __global__ void __launch_bounds__(256, 1) k_mlp_plain_step(MlpArgs a) {
-  mlp_solver<Cfg, MLP_PLAIN_STEP>(a);
+  mlp_solver<Cfg, MLP_PLAIN_STEP, Tab>(a);
 }
 
 // The BF16 weights W_l [N_l][K_in,l] (row-major) as core-matrix images with
@@ -1412,6 +1456,15 @@ __device__ __forceinline__ double dp_c(int s) {
   using C = DP5;
   return s == 2 ? C::c2 : s == 3 ? C::c3 : s == 4 ? C::c4 : s == 5 ? C::c5 : s >= 6 ? 1.0 : 0.0;
 }
+// c_s of the pair Tab (dopri5: dp_c)
+template <class Tab> __device__ __forceinline__ double tab_c(int s) {
+  if constexpr (std::is_same<Tab, DP5>::value) {
+    return dp_c(s);
+  } else {
+    return s == 2 ? Tab::c(2) : s == 3 ? Tab::c(3) : s == 4 ? Tab::c(4) : s == 5 ? Tab::c(5)
+         : s == 6 ? Tab::c(6) : s == 7 ? Tab::c(7) : 0.0;
+  }
+}
 // o = k[j] for a runtime j (selects; keeps k in registers)
 __device__ __forceinline__ void pick7(const float (&k)[7][16], int j, float (&o)[16]) {
 #pragma unroll
@@ -1424,10 +1477,9 @@ __device__ __forceinline__ void pick7(const float (&k)[7][16], int j, float (&o)
     }
 }
 
-template <class Cfg>
+template <class Cfg, class Tab = DP5>
 __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
   using L = MlpAdjLayout<Cfg>;
-  using Cc = DP5;
   constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, HC = Cfg::HC;
   static_assert(C == 16, "16 state components per thread");
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -1659,8 +1711,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
       store_row16<true>(th, tlo, row, col, H, v);
     }
   };
-  const float bw[7] = {float(Cc::b1), 0.0f, float(Cc::b3), float(Cc::b4), float(Cc::b5),
-                       float(Cc::b6), 0.0f};
+  const float bw[7] = {float(Tab::b(1)), float(Tab::b(2)), float(Tab::b(3)), float(Tab::b(4)),
+                       float(Tab::b(5)), float(Tab::b(6)), float(Tab::b(7))};
   const uint32_t idH = tc::idesc_bf16_f32(128, H);
 
   for (int rnd = 0;; ++rnd) {
@@ -1691,7 +1743,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 #pragma unroll
             for (int j = 0; j < 7; ++j) w[j] = bw[j];
           } else {
-            dense_weights<DP5, float>(float(tq - tn) / h, w);
+            dense_weights<Tab, float>(float(tq - tn) / h, w);
           }
 #pragma unroll
           for (int j = 0; j < 7; ++j)
@@ -1705,7 +1757,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
     }
     if (act) {
       load_stage(s, Y);
-      tin = (float)flip(tn + dp_c(s) * (double)h, rmask);  // the caller's time
+      tin = (float)flip(tn + tab_c<Tab>(s) * (double)h, rmask);  // the caller's time
       pick7(kb, s - 1, d3);
       if (rmask) {  // the field in tau is -f: its products take -kbar
 #pragma unroll
@@ -1863,7 +1915,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_adjoint(MlpAdjArgs a) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) {  // kbar_j += h a_{s,j} g  (j < s)
         if (j + 1 >= s) continue;
-        const float c = h * dp_a(s, j + 1);
+        const float c = h * tab_a<Tab>(s, j + 1);
 #pragma unroll
         for (int r = 0; r < C; ++r) kb[j][r] = madd(c, fg[r], kb[j][r]);
       }
@@ -2075,11 +2127,10 @@ __device__ __forceinline__ void unsplit8(const uint4& hi, const uint4& lo, float
   }
 }
 
-template <class Cfg>
+template <class Cfg, class Tab = DP5>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     k_mlp_adjoint_wide(const __grid_constant__ WideAdjArgs a) {
   using L = WideAdj<Cfg>;
-  using Cc = DP5;
   constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, ROWS = Cfg::ROWS;
   constexpr int NSL = L::NSL;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -2384,8 +2435,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
       reinterpret_cast<float4*>(sBias)[tid - 64] =
           __ldg(reinterpret_cast<const float4*>(a.bias + (size_t)l * H) + (tid - 64));
   };
-  const float bw[7] = {float(Cc::b1), 0.0f, float(Cc::b3), float(Cc::b4), float(Cc::b5),
-                       float(Cc::b6), 0.0f};
+  const float bw[7] = {float(Tab::b(1)), float(Tab::b(2)), float(Tab::b(3)), float(Tab::b(4)),
+                       float(Tab::b(5)), float(Tab::b(6)), float(Tab::b(7))};
   int k_round = 0;  // reverse rounds staged by this CTA (the same in both CTAs of the pair)
   int n_check = 0;
   for (int rnd = 0;; ++rnd) {
@@ -2433,7 +2484,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
 #pragma unroll
             for (int j = 0; j < 7; ++j) w[j] = bw[j];
           } else {
-            dense_weights<DP5, float>(float(tq - tn) / h, w);
+            dense_weights<Tab, float>(float(tq - tn) / h, w);
           }
 #pragma unroll
           for (int j = 0; j < 7; ++j)
@@ -2447,7 +2498,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     }
     if (act) {
       load_stage(s, Y);
-      tin = (float)flip(tn + dp_c(s) * (double)h, rmask);  // the caller's time
+      tin = (float)flip(tn + tab_c<Tab>(s) * (double)h, rmask);  // the caller's time
       pick7(kb, s - 1, kq);
       if (rmask) {  // the field in tau is -f: its products take -kbar
 #pragma unroll
@@ -2531,7 +2582,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       if (j + 1 >= s) continue;
-      const float cc = h * dp_a(s, j + 1);
+      const float cc = h * tab_a<Tab>(s, j + 1);
 #pragma unroll
       for (int r = 0; r < C; ++r) kb[j][r] = madd(cc, fg[r], kb[j][r]);
     }
@@ -3843,7 +3894,7 @@ size_t mlp_workspace_bytes(const tode_field_desc* f, const tode_options* o) {
   return b;
 }
 
-template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
+template <class Cfg, class Tab = DP5> static tode_err launch_mlp(const SolveReq& r) {
   MlpArgs a{};
   a.B = r.B;
   a.K = r.K;
@@ -3943,7 +3994,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   TODE_CUDA_TRY(cudaMemsetAsync(r.ws, 0, 256, st));  // queue counter and error flag
   {
     static std::atomic<uint64_t> done{0};
-    const tode_err e = smem_optin((const void*)k_mlp_fused<Cfg>, Cfg::S_END, done);
+    const tode_err e = smem_optin((const void*)k_mlp_fused<Cfg, Tab>, Cfg::S_END, done);
     if (e != TODE_OK) return e;
   }
   long long grid = (r.B + Cfg::ROWS - 1) / Cfg::ROWS;
@@ -3952,20 +4003,20 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
   if (r.o->form == TODE_PLAIN) {
     {
       static std::atomic<uint64_t> d0{0}, d1{0};
-      tode_err e = smem_optin((const void*)k_mlp_plain_init<Cfg>, Cfg::S_END, d0);
-      if (e == TODE_OK) e = smem_optin((const void*)k_mlp_plain_step<Cfg>, Cfg::S_END, d1);
+      tode_err e = smem_optin((const void*)k_mlp_plain_init<Cfg, Tab>, Cfg::S_END, d0);
+      if (e == TODE_OK) e = smem_optin((const void*)k_mlp_plain_step<Cfg, Tab>, Cfg::S_END, d1);
       if (e != TODE_OK) return e;
     }
-    k_mlp_plain_init<Cfg><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
+    k_mlp_plain_init<Cfg, Tab><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
     TODE_CUDA_TRY(cudaGetLastError());
     const int poll = r.o->poll_every > 0 ? r.o->poll_every : 16;
     long long launched = 0;
     const long long limit = (long long)r.o->max_steps + 2LL * poll + 2;
     while (true) {
       for (int c = 0; c < poll - 1; ++c)
-        k_mlp_plain_step<Cfg><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
+        k_mlp_plain_step<Cfg, Tab><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
       TODE_CUDA_TRY(cudaMemsetAsync(a.active, 0, sizeof(int32_t), st));
-      k_mlp_plain_step<Cfg><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
+      k_mlp_plain_step<Cfg, Tab><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
       TODE_CUDA_TRY(cudaGetLastError());
       launched += poll;
       int32_t any = 0;
@@ -3978,7 +4029,7 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
     }
     return TODE_OK;
   }
-  k_mlp_fused<Cfg><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
+  k_mlp_fused<Cfg, Tab><<<(int)grid, Cfg::NT, Cfg::S_END, st>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
 }
@@ -3986,6 +4037,10 @@ template <class Cfg> static tode_err launch_mlp(const SolveReq& r) {
 tode_err mlp_solve(const SolveReq& r, bool split) {
   if (r.o->form != TODE_FUSED && r.o->form != TODE_PLAIN) return TODE_EUNSUPPORTED;
   if (r.tape && r.tape->stride != 1) return TODE_EUNSUPPORTED;
+  if (r.o->method == TODE_TSIT5) {  // the Tsitouras pair, split form
+    if (!split) return TODE_EUNSUPPORTED;
+    return is_d64_h512(r.f) ? launch_mlp<Cfg64s, TS5>(r) : launch_mlp<Cfg32s, TS5>(r);
+  }
   if (is_d64_h512(r.f)) return split ? launch_mlp<Cfg64s>(r) : TODE_EUNSUPPORTED;
   return split ? launch_mlp<Cfg32s>(r) : launch_mlp<Cfg32>(r);
 }
@@ -4133,7 +4188,7 @@ static tode_err wide_tensor_maps(const unsigned char* img, WideAdjArgs& a) {
   return TODE_OK;
 }
 
-static tode_err mlp_wide_adjoint(const AdjReq& r) {
+template <class Tab> static tode_err mlp_wide_adjoint(const AdjReq& r) {
   using Cfg = Cfg64s;
   using L = WideAdj<Cfg>;
   const cudaStream_t st = r.stream;
@@ -4204,7 +4259,7 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   TODE_CUDA_TRY(cudaGetLastError());
   {
     static std::atomic<uint64_t> d0{0}, d1{0};
-    tode_err e = smem_optin((const void*)k_mlp_adjoint_wide<Cfg>, L::S_END, d0);
+    tode_err e = smem_optin((const void*)k_mlp_adjoint_wide<Cfg, Tab>, L::S_END, d0);
     if (e == TODE_OK) e = smem_optin((const void*)k_mlp_dw<Cfg>, DW_SMEM, d1);
     if (e != TODE_OK) return e;
   }
@@ -4219,7 +4274,7 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
       cfg.gridDim = dim3(2);
       cfg.blockDim = dim3(256);
       cfg.dynamicSmemBytes = L::S_END;
-      TODE_CUDA_TRY(cudaOccupancyMaxActiveClusters(&pairs, (const void*)k_mlp_adjoint_wide<Cfg>,
+      TODE_CUDA_TRY(cudaOccupancyMaxActiveClusters(&pairs, (const void*)k_mlp_adjoint_wide<Cfg, Tab>,
                                                    &cfg));
       if (pairs <= 0) return TODE_ECUDA;
       pairs_cached.store(pairs);
@@ -4232,7 +4287,7 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
     a.B = std::min(slice, r.B - i0);
     int cg = (a.B + 63) / 64;
     cg += cg & 1;  // CTA pairs: an odd tile count gets an idle partner
-    k_mlp_adjoint_wide<Cfg><<<cg, 256, L::S_END, st>>>(a);
+    k_mlp_adjoint_wide<Cfg, Tab><<<cg, 256, L::S_END, st>>>(a);
     TODE_CUDA_TRY(cudaGetLastError());
     d.chain_grid = cg;
     k_mlp_dw<Cfg><<<p.items, 128, DW_SMEM, st>>>(d);
@@ -4253,14 +4308,14 @@ static tode_err mlp_wide_adjoint(const AdjReq& r) {
   return TODE_OK;
 }
 
-tode_err mlp_adjoint(const AdjReq& r) {
+template <class Tab> static tode_err mlp_adjoint_tab(const AdjReq& r) {
   using Cfg = Cfg32s;
   using L = MlpAdjLayout<Cfg>;
   if (is_d64_h512(r.f)) {
     if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->y || !r.tape->t || !r.tape->y_stage)
       return TODE_EINVAL;
     if (!r.gW || !r.gW[0] || !r.gW[1] || !r.gW[2] || !r.gW[3]) return TODE_EINVAL;
-    return mlp_wide_adjoint(r);
+    return mlp_wide_adjoint<Tab>(r);
   }
   if (!is_d32_h128(r.f)) return TODE_EUNSUPPORTED;
   if (r.tape->stride != 1 || !r.tape->h_acc || !r.tape->y || !r.tape->t || !r.tape->y_stage)
@@ -4304,10 +4359,10 @@ tode_err mlp_adjoint(const AdjReq& r) {
   TODE_CUDA_TRY(cudaMemsetAsync(r.scratch, 0, 256, st));
   {
     static std::atomic<uint64_t> done{0};
-    const tode_err e = smem_optin((const void*)k_mlp_adjoint<Cfg>, L::S_END, done);
+    const tode_err e = smem_optin((const void*)k_mlp_adjoint<Cfg, Tab>, L::S_END, done);
     if (e != TODE_OK) return e;
   }
-  k_mlp_adjoint<Cfg><<<(int)grid, 256, L::S_END, st>>>(a);
+  k_mlp_adjoint<Cfg, Tab><<<(int)grid, 256, L::S_END, st>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   const int total = Cfg::H * (Cfg::D + 1) + Cfg::H + Cfg::H * Cfg::H + Cfg::H +
                     Cfg::D * Cfg::H + Cfg::D;
@@ -4316,6 +4371,10 @@ tode_err mlp_adjoint(const AdjReq& r) {
       r.gW[2], r.gb ? r.gb[2] : nullptr);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
+}
+
+tode_err mlp_adjoint(const AdjReq& r) {
+  return r.o->method == TODE_TSIT5 ? mlp_adjoint_tab<TS5>(r) : mlp_adjoint_tab<DP5>(r);
 }
 
 

@@ -19,7 +19,8 @@
 // and thread-per-input column sums (backward) over the BF16 weights read
 // from global memory, the stage activations kept in shared memory.
 // Backward instances run in tau = -t with the field -f(-tau, y) as the
-// solver ran them: hbar is dL/dtau1 there, and dL/dt1 = -hbar.
+// solver ran them: hbar is dL/dtau1 there, and dL/dt1 = -hbar.  The pair
+// (dopri5 or tsit5) is the one the solve used.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -75,9 +76,9 @@ __device__ double block_sum(double v, double* red) {
 
 // Shared memory (floats): Y[7][D], k[7][D], kb[7][D], x[Hmax + D + 1],
 // g0[Hmax + D + 1], g1[Hmax + D + 1], act[7][NL-1][Hmax], then 8 doubles.
+template <class Tab>
 __global__ void __launch_bounds__(TB_THREADS) k_mlp_t_last(MlpTbArgs a) {
   extern __shared__ __align__(16) float sm[];
-  using Tab = DP5;
   const int D = a.D, NL = a.NL, Hm = a.Hmax, XW = a.Hmax + a.D + 1;
   float* sY = sm;
   float* sk = sY + 7 * D;
@@ -266,10 +267,14 @@ tode_err mlp_t_bounds(const AdjReq& r, const void* yp, double* gt0, double* gt1)
   a.gt1 = gt1;
   const size_t smem = mlp_t_bounds_smem(f);
   if (smem > 227 * 1024) return TODE_EUNSUPPORTED;
-  TODE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_mlp_t_last,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const void* kern = r.o->method == TODE_TSIT5 ? (const void*)k_mlp_t_last<TS5>
+                                                : (const void*)k_mlp_t_last<DP5>;
+  TODE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::min(r.B, std::max(1, r.num_sms) * 4);
-  k_mlp_t_last<<<grid, TB_THREADS, smem, r.stream>>>(a);
+  if (r.o->method == TODE_TSIT5)
+    k_mlp_t_last<TS5><<<grid, TB_THREADS, smem, r.stream>>>(a);
+  else
+    k_mlp_t_last<DP5><<<grid, TB_THREADS, smem, r.stream>>>(a);
   TODE_CUDA_TRY(cudaGetLastError());
   return TODE_OK;
 }

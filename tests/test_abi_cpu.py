@@ -97,9 +97,9 @@ def test_workspace_size_rules():
 
 
 def test_method_rules():
-    """tsit5 (method 1) covers the Van der Pol and linear fields solved
-    independently; the MLP field and joint solving refuse it, and an
-    unknown method is invalid."""
+    """tsit5 (method 1) covers every field solved independently (the MLP
+    field in its split form); joint solving refuses it, and an unknown
+    method is invalid."""
     lib = _abi.load()
     assert _opts().method == _abi.TODE_DOPRI5
     vdp = C.byref(_desc(_abi.TODE_VDP, 100, 2))
