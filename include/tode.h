@@ -168,8 +168,11 @@ enum { TODE_DOPRI5 = 0, TODE_TSIT5 = 1 };
  * With stride 1 and h_acc given (the same tape struct for both calls), every
  * accepted step is on the tape with its size and tode_adjoint reverses it
  * directly, without re-running the forward's attempts.
- * MLP field: stride must be 1; y, t, h_acc and y_stage are used (the
- * adjoint reverses every step from its recorded stage inputs).
+ * MLP field: the adjoint reverses every step from its recorded stage
+ * inputs, so it takes a stride-1 tape with y, t, h_acc and y_stage; a solve
+ * given a tape with stride > 1 records checkpoints for tode_mlp_resolve
+ * instead (y, y_lo, k1, t, h, err_prev, flags and, when beta3 != 0,
+ * err_prev2).
  * Every array is instance-major ([B][slots]...): the slots of one instance
  * are contiguous, so a lane group's successive checkpoint stores (and the
  * adjoint's loads) stay within the same cache lines.  Every array must be
@@ -257,6 +260,31 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
                     void* y_eval, void* yp_eval, void* y_final, int32_t* n_acc, int32_t* n_rej,
                     int32_t* n_feval, int32_t* status, const tode_tape* tape,
                     const tode_trace* trace, void* workspace, size_t ws_bytes, void* stream);
+
+/* Re-solve one checkpointed segment of an MLP-field solve (the budgeted
+ * adjoint of App. A's backpropagation through the solver: the stages are
+ * recomputed from checkpointed step-start states and step sizes).  A
+ * tode_solve of the MLP field given a tape with stride m > 1 writes no stage
+ * inputs; it records, at the start of every m-th accepted step, the whole
+ * solver state (y, y_lo, k1, t, h = the step proposed for the first attempt,
+ * err_prev, err_prev2 when beta3 != 0, flags).  This call runs, for every
+ * instance, the accepted steps seg*m .. seg*m + m - 1 of that solve again from
+ * checkpoint slot seg -- bit for bit the same attempts -- and fills seg_tape
+ * (stride 1, slots >= m, h_acc and y_stage) with them, writing nothing else
+ * of the solve.  Outputs per instance: seg_n [B] int32, the segment's accepted
+ * steps (0 past the instance's last step); seg_t0, seg_t1 [B] double, its
+ * bounds in the caller's time (both t1 when seg_n = 0).  tode_adjoint with t0
+ * = seg_t0, t1 = seg_t1, n_acc = seg_n, the forward's status, seg_tape,
+ * gy_final = the cotangent at seg_t1 and gy_eval zero outside (seg_t0,
+ * seg_t1] (for seg > 0; [t0, seg_t1] for seg 0) reverses the segment and
+ * returns the cotangent at seg_t0 in gy0.  n_acc: the solve's accepted-step
+ * counts.  The fused form, prec TODE_BF16W_SPLIT (TODE_EUNSUPPORTED
+ * otherwise); workspace as for tode_solve with K = 0.  Enqueued on stream;
+ * allocates nothing. */
+tode_err tode_mlp_resolve(const tode_field_desc* f, const tode_options* o, const double* t0,
+                          const double* t1, const int32_t* n_acc, const tode_tape* ckpt, int seg,
+                          const tode_tape* seg_tape, int32_t* seg_n, double* seg_t0,
+                          double* seg_t1, void* workspace, size_t ws_bytes, void* stream);
 
 /* Bytes of device scratch tode_adjoint needs (256-byte aligned base).  For
  * the MLP field it depends on the current device's SM count and, for the

@@ -7,11 +7,12 @@ this package only marshals torch tensors into it.
 """
 from . import _abi  # noqa: F401
 from .api import (MLP, Linear, Solution, TapeBuffers, VdP, adjoint, make_options,  # noqa: F401
-                  solve, t_bounds_grad, t_eval_grad, joint_adjoint, joint_adjoint_workspace)
+                  solve, t_bounds_grad, t_eval_grad, joint_adjoint, joint_adjoint_workspace,
+                  mlp_resolve)
 from .autograd import odeint_adjoint  # noqa: F401
 from .tuning import autotune, set_cache_path  # noqa: F401
 
 __all__ = ["VdP", "Linear", "MLP", "solve", "adjoint", "TapeBuffers", "Solution",
            "make_options", "odeint_adjoint", "autotune", "set_cache_path", "t_bounds_grad",
            "joint_adjoint", "joint_adjoint_workspace",
-           "t_eval_grad"]
+           "t_eval_grad", "mlp_resolve"]

@@ -25,7 +25,7 @@ EXPORTS = ("tode_version", "tode_strerror", "tode_default_options", "tode_worksp
            "tode_solve", "tode_adjoint_scratch_size", "tode_adjoint", "tode_adjoint_static",
            "tode_joint_adjoint_workspace_size", "tode_joint_adjoint",
            "tode_tc_gemm", "tode_t_eval_grad", "tode_peak_kernel",
-           "tode_t_bounds_grad")
+           "tode_t_bounds_grad", "tode_mlp_resolve")
 TODE_STATIC_ADJOINT_SCRATCH_BYTES = 32 << 20
 
 _vp = C.c_void_p
@@ -153,6 +153,10 @@ def load(path: str = LIB_PATH):
     lib.tode_t_bounds_grad.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), _vp, _vp, _vp,
                                        C.c_int, _vp, _vp, C.POINTER(Tape), _vp, _vp, _vp, _vp,
                                        _vp, _vp]
+    lib.tode_mlp_resolve.restype = C.c_int
+    lib.tode_mlp_resolve.argtypes = [C.POINTER(FieldDesc), C.POINTER(Options), _vp, _vp, _vp,
+                                     C.POINTER(Tape), C.c_int, C.POINTER(Tape), _vp, _vp, _vp,
+                                     _vp, C.c_size_t, _vp]
     lib.tode_peak_kernel.restype = C.c_int
     lib.tode_peak_kernel.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp]
     lib.tode_tc_gemm.restype = C.c_int

@@ -295,6 +295,39 @@ def solve(field, y0: torch.Tensor, t0: torch.Tensor, t1: torch.Tensor,
     return out
 
 
+def mlp_resolve(field, t0, t1, n_acc: torch.Tensor, ckpt: TapeBuffers, seg: int,
+                seg_tape: TapeBuffers, *, stream=None,
+                workspace: Optional[torch.Tensor] = None, **opt_kw):
+    """Re-run segment ``seg`` of an MLP-field solve that filled the
+    checkpoint tape ``ckpt`` (stride m > 1): accepted steps seg*m .. of every
+    instance, bit for bit, into the stride-1 stage tape ``seg_tape`` (m
+    slots).  Returns (seg_n [B] int32, seg_t0 [B], seg_t1 [B] float64): the
+    segment's accepted steps and its bounds in the caller's time, the
+    arguments ``adjoint`` takes to reverse the segment.  ``n_acc``: the
+    solve's accepted-step counts."""
+    lib = _abi.load()
+    B, D = ckpt.y.shape[0], ckpt.y.shape[2]
+    dev = ckpt.y.device
+    opts = make_options(prec=_abi.TODE_BF16W_SPLIT, **opt_kw)
+    keep = []
+    fd = field.desc(B, D, keep)
+    ws_bytes = lib.tode_workspace_size(C.byref(fd), C.byref(opts), 0)
+    if ws_bytes == 0 and B > 0:
+        raise _abi.TodeError(_abi.TODE_EUNSUPPORTED, "tode_workspace_size")
+    if workspace is None or workspace.numel() < ws_bytes:
+        workspace = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
+    seg_n = torch.empty(B, dtype=torch.int32, device=dev)
+    seg_t0 = torch.empty(B, dtype=torch.float64, device=dev)
+    seg_t1 = torch.empty(B, dtype=torch.float64, device=dev)
+    ck_c, st_c = ckpt.c(), seg_tape.c()
+    code = lib.tode_mlp_resolve(C.byref(fd), C.byref(opts), _ptr(t0), _ptr(t1), _ptr(n_acc),
+                                C.byref(ck_c), int(seg), C.byref(st_c), _ptr(seg_n),
+                                _ptr(seg_t0), _ptr(seg_t1), _ptr(workspace),
+                                C.c_size_t(workspace.numel()), _stream_handle(stream))
+    _abi.check(code, "tode_mlp_resolve")
+    return seg_n, seg_t0, seg_t1
+
+
 def t_eval_grad(gy_eval: torch.Tensor, yp_eval: torch.Tensor,
                 stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
     """dL/dt_eval [B, K] (float64) = <dL/dy_eval, dy/dt> per evaluation point,

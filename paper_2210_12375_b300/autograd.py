@@ -6,8 +6,11 @@ backpropagation through the solver, on the forward's frozen mesh).
 The tape is sized from the forward's accepted-step counts under an HBM
 budget: one slot per accepted step when it fits, otherwise one slot every m
 steps with the segments recomputed in the backward pass (gradients bitwise
-equal to m = 1).  The MLP field and joint solves (Sec. 4.1, ``joint=True``:
-one shared mesh, reversed per instance) keep every step (m = 1).
+equal to m = 1).  For the MLP field a slot every m steps holds the whole
+solver state, and the backward re-solves one segment at a time into an
+m-slot stage tape (tode_mlp_resolve) before reversing it.  Joint solves
+(Sec. 4.1, ``joint=True``: one shared mesh, reversed per instance) keep
+every step (m = 1).
 """
 from __future__ import annotations
 
@@ -60,9 +63,13 @@ def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint, want_yp=False
             raise RuntimeError(f"the adjoint of a joint solve keeps every accepted step: {N} "
                                f"slots of {per_slot} bytes exceed the tape budget of "
                                f"{budget} bytes")
+        elif mlp and _mlp_segment_stride(B, D, N, budget) > 1:
+            # checkpoints every m accepted steps; the backward re-solves one
+            # segment at a time into an m-slot stage tape and reverses it
+            stride = _mlp_segment_stride(B, D, N, budget)
         elif mlp:
-            # the batch's tape does not fit: the backward recomputes it chunk
-            # by chunk (instances are independent); the forward needs no tape
+            # not even that fits: the backward recomputes the batch chunk by
+            # chunk (instances are independent); the forward needs no tape
             one = api.TapeBuffers.bytes_per_slot(1, D, y0.element_size(), stages=True,
                                                  minimal=True)
             chunk = int(budget // max(one * N, 1))
@@ -74,12 +81,69 @@ def _solve_with_tape(field, y0, t0, t1, t_eval, opt, budget, hint, want_yp=False
         else:  # strided segments are re-run: the tape keeps the whole state
             stride = math.ceil(N / max(1, budget // max(full_slot, 1)))
         slots = math.ceil(N / stride)
-        tape = api.TapeBuffers.allocate(B, D, dtype, slots, stride, dev, stages=mlp,
-                                        minimal=stride == 1)
+        tape = api.TapeBuffers.allocate(B, D, dtype, slots, stride, dev,
+                                        stages=mlp and stride == 1, minimal=stride == 1)
         # the solve is deterministic: the re-run fills the tape on the same mesh
         sol = api.solve(field, y0, t0, t1, t_eval, tape=tape, form="fused", want_yp=want_yp,
                         **opt)
     return sol, tape, N, chunk
+
+
+def _mlp_segment_stride(B, D, N, budget):
+    """The largest m (2..N) whose checkpoint tape (ceil(N/m) slots of the
+    whole solver state) plus one m-slot stage tape fits the budget; 0 if
+    none does."""
+    ck = api.TapeBuffers.bytes_per_slot(B, D, 4)
+    st = api.TapeBuffers.bytes_per_slot(B, D, 4, stages=True, minimal=True)
+    best = 0
+    for m in range(2, max(N, 2) + 1):
+        if math.ceil(N / m) * ck + m * st <= budget:
+            best = m
+    return best
+
+
+def _mlp_adjoint_segments(field, t0, t1, t_eval, sol, ckpt, gye, gyf, opt, N, want_ts=False):
+    """The MLP adjoint of a solve that recorded checkpoints every m accepted
+    steps: segment by segment from the last, the segment is re-solved from
+    its checkpoint into an m-slot stage tape (the same attempts, bit for bit)
+    and reversed as a solve of its own -- from its end's cotangent, with the
+    points inside it (the first segment also takes those at t0) -- and its
+    start's cotangent carried to the segment before.  Weight gradients (and
+    the time-translation sums) are summed over the segments."""
+    B, D = sol.y_final.shape
+    m = ckpt.stride
+    dev = sol.y_final.device
+    seg_tape = api.TapeBuffers.allocate(B, D, sol.y_final.dtype, m, 1, dev, stages=True,
+                                        minimal=True)
+    carry = gyf if gyf is not None else torch.zeros_like(sol.y_final)
+    dirn = torch.where(t1 < t0, -1.0, 1.0).to(torch.float64)
+    gW = gb = ts = None
+    ws = None
+    for j in reversed(range(math.ceil(N / m))):
+        seg_n, s0, s1 = api.mlp_resolve(field, t0, t1, sol.n_acc, ckpt, j, seg_tape,
+                                        workspace=ws, **opt)
+        g_e = None
+        if gye is not None and t_eval is not None:
+            tq = dirn[:, None] * t_eval
+            lo, hi = (dirn * s0)[:, None], (dirn * s1)[:, None]
+            inside = (tq <= hi) & ((tq > lo) if j > 0 else (tq >= lo))
+            g_e = (gye * inside[..., None].to(gye.dtype)).contiguous()
+        seg = api.Solution(y_eval=sol.y_eval, y_final=sol.y_final, n_acc=seg_n,
+                           n_rej=sol.n_rej, n_feval=sol.n_feval, status=sol.status)
+        g0, gp, ovf = api.adjoint(field, s0, s1, t_eval, seg, seg_tape, g_e,
+                                  carry.contiguous(), want_tshift=want_ts, **opt)
+        if int(ovf.item()) != 0:
+            raise RuntimeError("tode_adjoint: a segment overflowed its stage tape")
+        carry = g0
+        if gW is None:
+            gW, gb = list(gp[0]), list(gp[1])
+            ts = gp[2] if want_ts else None
+        else:
+            gW = [a + b for a, b in zip(gW, gp[0])]
+            gb = [a + b for a, b in zip(gb, gp[1])]
+            if want_ts:
+                ts = ts + gp[2]
+    return carry, (gW, gb) if not want_ts else (gW, gb, ts)
 
 
 def _mlp_adjoint_chunked(field, y0, t0, t1, t_eval, sol, gye, gyf, opt, chunk, N):
@@ -148,6 +212,9 @@ class _Odeint(torch.autograd.Function):
         if ctx.chunk > 0:
             gy0, gp = _mlp_adjoint_chunked(field, y0.detach(), t0, t1, t_eval, sol, gye, gyf,
                                            ctx.opt, ctx.chunk, ctx.N)
+        elif isinstance(field, api.MLP) and ctx.tape.stride > 1:
+            gy0, gp = _mlp_adjoint_segments(field, t0, t1, t_eval, sol, ctx.tape, gye, gyf,
+                                            ctx.opt, ctx.N)
         else:
             mlp_t = ctx.want_t and isinstance(field, api.MLP)
             gy0, gp, ovf = api.adjoint(field, t0, t1, t_eval, sol, ctx.tape, gye, gyf,

@@ -69,7 +69,12 @@ static bool tape_ok(const tode_tape* tp, const tode_options* o, const tode_field
   for (const void* p : arrays)
     if (!aligned16(p)) return false;  // NULL passes
   if (tp->slots < 1 || tp->stride < 1 || !tp->y || !tp->t) return false;
-  if (f->kind == TODE_MLP) return tp->stride == 1 && tp->h_acc && tp->y_stage;
+  if (f->kind == TODE_MLP) {
+    if (tp->stride == 1) return tp->h_acc && tp->y_stage;
+    // checkpoints of a budgeted solve: the whole solver state at each one
+    return tp->k1 && tp->y_lo && tp->h && tp->err_prev && tp->flags &&
+           (o->beta3 == 0.0 || tp->err_prev2);
+  }
   // stride 1 with the accepted step sizes: reversed straight from the slots,
   // which need the FSAL stage only when the stage inputs are not recorded
   if (tp->stride == 1 && tp->h_acc) return tp->k1 || tp->y_stage;
@@ -208,6 +213,47 @@ tode_err tode_solve(const tode_field_desc* f, const tode_options* o, const void*
   if (e != TODE_OK) return e;
   if (f->kind == TODE_MLP) return mlp_solve(r, o->prec == TODE_BF16W_SPLIT);
   return o->prec == TODE_F64 ? simt_solve_f64(r) : simt_solve_f32(r);
+}
+
+tode_err tode_mlp_resolve(const tode_field_desc* f, const tode_options* o, const double* t0,
+                          const double* t1, const int32_t* n_acc, const tode_tape* ckpt, int seg,
+                          const tode_tape* seg_tape, int32_t* seg_n, double* seg_t0,
+                          double* seg_t1, void* workspace, size_t ws_bytes, void* stream) {
+  if (!opts_ok(o) || seg < 0) return TODE_EINVAL;
+  tode_err e = field_ok(f, o);
+  if (e != TODE_OK) return e;
+  if (f->kind != TODE_MLP || o->prec != TODE_BF16W_SPLIT || o->joint || o->form != TODE_FUSED)
+    return TODE_EUNSUPPORTED;
+  if (f->B == 0) return TODE_OK;
+  if (!t0 || !t1 || !n_acc || !ckpt || !seg_tape || !seg_n || !seg_t0 || !seg_t1)
+    return TODE_EINVAL;
+  if (!tape_ok(ckpt, o, f) || ckpt->stride < 2) return TODE_EINVAL;
+  if (!tape_ok(seg_tape, o, f) || seg_tape->stride != 1 || seg_tape->slots < ckpt->stride)
+    return TODE_EINVAL;
+  const size_t need = tode_workspace_size(f, o, 0);
+  if (!workspace || !aligned256(workspace) || ws_bytes < need) return TODE_EWORKSPACE;
+  SolveReq r{};
+  r.f = f;
+  r.o = o;
+  r.B = f->B;
+  r.D = f->D;
+  r.K = 0;
+  r.t0 = t0;
+  r.t1 = t1;
+  r.n_acc = const_cast<int32_t*>(n_acc);
+  r.tape = seg_tape;
+  r.ws = (char*)workspace;
+  r.ws_bytes = ws_bytes;
+  r.stream = (cudaStream_t)stream;
+  r.resolve = true;
+  r.rs_seg = seg;
+  r.ck = ckpt;
+  r.rs_n = seg_n;
+  r.rs_t0 = seg_t0;
+  r.rs_t1 = seg_t1;
+  e = device_sms(&r.num_sms);
+  if (e != TODE_OK) return e;
+  return mlp_solve(r, true);
 }
 
 size_t tode_adjoint_scratch_size(const tode_field_desc* f, const tode_options* o,

@@ -28,6 +28,13 @@ struct SolveReq {
   size_t ws_bytes;
   cudaStream_t stream;
   int num_sms;
+  // MLP field, re-solve of one checkpointed segment (tode_mlp_resolve)
+  bool resolve;
+  int rs_seg;
+  const tode_tape* ck;
+  int32_t* rs_n;
+  double* rs_t0;
+  double* rs_t1;
 };
 
 struct AdjReq {

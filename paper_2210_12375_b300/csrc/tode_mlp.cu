@@ -77,6 +77,28 @@ struct MlpArgs {
   int32_t* active;
   // work order: the instance at queue position q (nullptr: q itself)
   const int32_t* order;
+  // checkpoint tape of a budgeted solve (ck_stride > 1; the stage tape is
+  // then off): slot j = the solver state at the start of accepted step
+  // j * ck_stride (y, its compensation term, FSAL k1, t, the proposed step,
+  // the controller's error history, the flags)
+  int ck_stride, ck_slots;
+  float* ck_y;
+  float* ck_ylo;
+  float* ck_k1;
+  double* ck_t;
+  float* ck_h;
+  float* ck_ep;
+  float* ck_ep2;
+  int32_t* ck_fl;
+  // re-solve of segment rs_seg (>= 0) of every instance from the checkpoint
+  // tape: accepted steps rs_seg * ck_stride .. of the first solve (rs_nacc)
+  // into the stage tape, no outputs; per instance the segment's steps and
+  // its bounds in the caller's time (rs_n, rs_t0, rs_t1)
+  int rs_seg;
+  const int32_t* rs_nacc;
+  int32_t* rs_n;
+  double* rs_t0;
+  double* rs_t1;
 };
 
 // Kernel modes of the MLP solver body: the fused persistent form, and the
@@ -407,7 +429,7 @@ template <class Tab> __host__ __device__ constexpr bool tab_k2() {
 }
 // Per-row solver state (identical scalars in both threads of the row).
 struct MlpRow {
-  int inst, phase, cursor, status, flags, n_acc, n_rej;
+  int inst, phase, cursor, status, flags, n_acc, n_rej, target;
   double t, t0, t1;
   float h, h0h, err_prev, err_prev2, rtol, atol, rem, hmin;
   bool last;
@@ -512,6 +534,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
 
   MlpRow s;
   s.inst = -1;
+  s.target = -1;
   s.phase = PH_IDLE;
   // k1 (FSAL) in registers; k2..k6 of the attempt in shared memory when the
   // config has room (else in the thread's local array); k7 is the last f
@@ -550,9 +573,55 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   auto start_instance = [&](const int i) {
     // load and validate the instance (Sec. 3: per-instance bounds / points)
     s.inst = i;
+    s.target = -1;
     // backward in time (t1 < t0): the row runs in tau = -t with the field
     // -f(-tau, y) (its times through a sign xor, see tode_core.cuh)
     const unsigned long long m = (a.t1[i] < a.t0[i]) ? SIGN_BIT : 0ULL;
+    if (a.rs_seg >= 0) {
+      // re-solve: the segment's first accepted step from its checkpoint,
+      // the same state the first solve had there (bit for bit)
+      const int first = a.rs_seg * a.ck_stride, N = a.rs_nacc[i];
+      const int n_seg = N - first < a.ck_stride ? N - first : a.ck_stride;
+      if (n_seg <= 0 || a.rs_seg >= a.ck_slots) {
+        if (sub == 0) {
+          a.rs_n[i] = 0;
+          a.rs_t0[i] = a.rs_t1[i] = a.t1[i];
+        }
+        s.phase = PH_IDLE;
+        if (MODE == MLP_FUSED) need_grab = true;
+        return;
+      }
+      const size_t o = (size_t)i * a.ck_slots + a.rs_seg;
+      s.t0 = flip(a.t0[i], m);
+      s.t1 = flip(a.t1[i], m);
+      s.t = a.ck_t[o];
+      s.rtol = (float)(a.rtol_b ? a.rtol_b[i] : a.rtol);
+      s.atol = (float)(a.atol_b ? a.atol_b[i] : a.atol);
+      s.n_acc = s.n_rej = 0;
+      s.cursor = 0;
+      s.flags = a.ck_fl[o];
+      s.err_prev = a.ck_ep[o];
+      s.err_prev2 = a.ck_ep2 ? a.ck_ep2[o] : 1.0f;
+      s.h = a.ck_h[o];
+      s.h0h = 0.0f;
+      s.last = false;
+      s.status = ST_RUNNING;
+      s.target = n_seg;
+      s.rem = __double2float_rd(s.t1 - s.t);
+      s.hmin = (float)(1e-14 * tmax(fabs(s.t0), fabs(s.t1)));
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        y[r] = a.ck_y[o * D + coff + r];
+        ylo[r] = a.ck_ylo[o * D + coff + r];
+        k1[r] = a.ck_k1[o * D + coff + r];
+      }
+      if (sub == 0) {
+        a.rs_n[i] = n_seg;
+        a.rs_t0[i] = flip(s.t, m);
+      }
+      s.phase = PH_STAGE;
+      return;
+    }
     s.t0 = flip(a.t0[i], m);
     s.t1 = flip(a.t1[i], m);
     s.t = s.t0;
@@ -653,6 +722,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
   // plain form: resume a parked instance at the start of its next attempt
   auto resume = [&](const int i) {
     s.inst = i;
+    s.target = -1;
     s.flags = a.wfl[i];
     s.t0 = flip(a.t0[i], rev_mask(s.flags));
     s.t1 = flip(a.t1[i], rev_mask(s.flags));
@@ -737,6 +807,24 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       tin = (float)flip(s.t + (double)s.h0h, rev_mask(s.flags));
     } else {
       if (stage == 2) {  // a new attempt starts: clip at t1
+        if (a.ck_stride > 1 && !(s.flags & FL_PREV_REJ) && s.n_acc % a.ck_stride == 0 &&
+            s.n_acc / a.ck_stride < a.ck_slots && a.rs_seg < 0) {
+          // checkpoint: the state the first attempt of this step starts from
+          const size_t o = (size_t)s.inst * a.ck_slots + s.n_acc / a.ck_stride;
+#pragma unroll
+          for (int r = 0; r < C; ++r) {
+            a.ck_y[o * D + coff + r] = y[r];
+            a.ck_ylo[o * D + coff + r] = ylo[r];
+            a.ck_k1[o * D + coff + r] = k1[r];
+          }
+          if (sub == 0) {
+            a.ck_t[o] = s.t;
+            a.ck_h[o] = s.h;
+            a.ck_ep[o] = s.err_prev;
+            if (a.ck_ep2) a.ck_ep2[o] = s.err_prev2;
+            a.ck_fl[o] = s.flags;
+          }
+        }
         float h = s.h;
         s.last = false;
         if (h >= s.rem) {
@@ -1214,6 +1302,7 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
         }
         if (last) s.status = ST_SUCCESS;
         else s.rem = __double2float_rd(s.t1 - s.t);
+        if (s.target >= 0 && s.n_acc >= s.target) s.status = ST_SUCCESS;  // segment re-solved
       } else {
         const float fac =
             finite ? tmin(tmax(a.o.safety_f * ctl_pow(err, -a.o.beta1_f),
@@ -1234,6 +1323,10 @@ __device__ __forceinline__ void mlp_solver(const MlpArgs a) {
       if (s.status == ST_RUNNING) {
         s.phase = PH_STAGE;  // next attempt, FSAL k1 in hand
         if (MODE == MLP_PLAIN_STEP) park();
+      } else if (s.target >= 0) {  // a re-solved segment: its end, no outputs
+        if (sub == 0) a.rs_t1[i] = flip(s.t, rev_mask(s.flags));
+        s.phase = PH_IDLE;
+        if (MODE == MLP_FUSED) need_grab = true;
       } else {
         if (s.status != ST_SUCCESS) {  // points the failed instance never reached
           float* ye = a.ye + (size_t)i * a.K * D + coff;
@@ -3922,7 +4015,23 @@ template <class Cfg, class Tab = DP5> static tode_err launch_mlp(const SolveReq&
   a.o.h0 = r.o->h0;
   a.o.max_steps = r.o->max_steps;
   opts_round_f32(a.o);
-  if (r.tape) {
+  a.rs_seg = -1;
+  auto set_ck = [&](const tode_tape* tp) {
+    a.ck_stride = tp->stride;
+    a.ck_slots = tp->slots;
+    a.ck_y = (float*)tp->y;
+    a.ck_ylo = (float*)tp->y_lo;
+    a.ck_k1 = (float*)tp->k1;
+    a.ck_t = tp->t;
+    a.ck_h = (float*)tp->h;
+    a.ck_ep = (float*)tp->err_prev;
+    a.ck_ep2 = (float*)tp->err_prev2;
+    a.ck_fl = tp->flags;
+  };
+  if (r.tape && r.tape->stride > 1) {  // checkpoints every stride steps, no stage tape
+    a.slots = 0;
+    set_ck(r.tape);
+  } else if (r.tape) {
     a.slots = r.tape->slots;
     a.tp_y = (float*)r.tape->y;
     a.tp_k1 = (float*)r.tape->k1;
@@ -3931,6 +4040,16 @@ template <class Cfg, class Tab = DP5> static tode_err launch_mlp(const SolveReq&
     a.tp_ys = (float*)r.tape->y_stage;
   } else {
     a.slots = 0;
+  }
+  if (r.resolve) {  // one segment from the checkpoints into the stage tape
+    set_ck(r.ck);
+    a.rs_seg = r.rs_seg;
+    a.rs_nacc = r.n_acc;
+    a.rs_n = r.rs_n;
+    a.rs_t0 = r.rs_t0;
+    a.rs_t1 = r.rs_t1;
+    a.K = 0;
+    a.ye = a.yp = nullptr;
   }
   if (r.trace) {
     a.trace.cap = r.trace->cap;
@@ -4036,7 +4155,7 @@ template <class Cfg, class Tab = DP5> static tode_err launch_mlp(const SolveReq&
 
 tode_err mlp_solve(const SolveReq& r, bool split) {
   if (r.o->form != TODE_FUSED && r.o->form != TODE_PLAIN) return TODE_EUNSUPPORTED;
-  if (r.tape && r.tape->stride != 1) return TODE_EUNSUPPORTED;
+  if (r.resolve && (r.o->form != TODE_FUSED || !split)) return TODE_EUNSUPPORTED;
   if (r.o->method == TODE_TSIT5) {  // the Tsitouras pair, split form
     if (!split) return TODE_EUNSUPPORTED;
     return is_d64_h512(r.f) ? launch_mlp<Cfg64s, TS5>(r) : launch_mlp<Cfg32s, TS5>(r);

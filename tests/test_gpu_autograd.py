@@ -141,3 +141,77 @@ def test_autograd_joint_solve_vs_oracle_adjoint_on_the_shared_mesh():
     with pytest.raises(RuntimeError):
         _loss_and_grads(w, torch.float64, field, joint=True, hbm_budget_bytes=40 * 40,
                         slots_hint=1)
+
+
+@pytest.mark.parametrize("cfg,B", [(4, 300), (5, 150)])
+def test_mlp_resolve_reproduces_the_stage_tape_bitwise(cfg, B):
+    """A solve with a checkpoint tape (every m-th accepted step) and
+    tode_mlp_resolve of each segment give, slot for slot, the stage inputs,
+    times and step sizes a stride-1 tape records in one solve -- the same
+    attempts from the same states -- and the segment counts and bounds."""
+    w = dict(make(cfg, B=B), split=True)
+    field = device_field(w, torch.float32)
+    y0, t0, t1, te = _inputs(w, torch.float32)
+    y0 = y0.detach()
+    opt = dict(rtol=w["rtol"], atol=w["atol"])
+    probe = tode.solve(field, y0, t0, t1, te, **opt)
+    N = int(probe.n_acc.max().item())
+    D = w["y0"].shape[1]
+    full = tode.TapeBuffers.allocate(B, D, torch.float32, N, 1, "cuda", stages=True, minimal=True)
+    ref = tode.solve(field, y0, t0, t1, te, tape=full, **opt)
+    m = 2
+    ck = tode.TapeBuffers.allocate(B, D, torch.float32, -(-N // m), m, "cuda")
+    sol = tode.solve(field, y0, t0, t1, te, tape=ck, **opt)
+    for k in ("y_eval", "y_final", "n_acc", "n_rej", "status"):
+        assert torch.equal(getattr(sol, k), getattr(ref, k)), k
+    seg_tape = tode.TapeBuffers.allocate(B, D, torch.float32, m, 1, "cuda", stages=True,
+                                         minimal=True)
+    n_acc = sol.n_acc.cpu().numpy()
+    for j in range(-(-N // m)):
+        seg_n, s0, s1 = tode.mlp_resolve(field, t0, t1, sol.n_acc, ck, j, seg_tape, **opt)
+        torch.cuda.synchronize()
+        want = np.clip(n_acc - j * m, 0, m)
+        assert np.array_equal(seg_n.cpu().numpy(), want)
+        for i in range(B):
+            n = int(want[i])
+            if n == 0:
+                assert s0[i].item() == s1[i].item() == w["t1"][i]
+                continue
+            sl = slice(j * m, j * m + n)
+            assert torch.equal(seg_tape.y_stage[i, :n], full.y_stage[i, sl]), (j, i)
+            assert torch.equal(seg_tape.y[i, :n], full.y[i, sl]), (j, i)
+            assert torch.equal(seg_tape.t[i, :n], full.t[i, sl]), (j, i)
+            assert torch.equal(seg_tape.h_acc[i, :n], full.h_acc[i, sl]), (j, i)
+            assert s0[i].item() == full.t[i, j * m].item()
+            end = w["t1"][i] if j * m + n == n_acc[i] else full.t[i, j * m + n].item()
+            assert s1[i].item() == end
+
+
+@pytest.mark.parametrize("cfg,B", [(4, 300), (5, 150)])
+def test_autograd_mlp_budget_checkpoints_segments(cfg, B, monkeypatch):
+    """A tape budget just below the stride-1 stage tape: the forward keeps
+    the solver state every m accepted steps, the backward re-solves each
+    segment into an m-slot stage tape and reverses it from the cotangent the
+    later segment handed over.  dL/dy0 equals the full tape's bit for bit
+    (the same stage inputs, the same per-row reversal); the weight and bias
+    gradients are summed segment by segment (FP32 summation order, as for
+    chunks)."""
+    w = dict(make(cfg, B=B), split=True)
+    field = device_field(w, torch.float32)
+    full = _loss_and_grads(w, torch.float32, field)
+    n_max = int(full[2].max())
+    D = w["y0"].shape[1]
+    st = tode.TapeBuffers.bytes_per_slot(B, D, 4, stages=True, minimal=True)
+    calls = []
+    real = tode.api.mlp_resolve
+
+    def counting(*a, **k):
+        calls.append(a[5])
+        return real(*a, **k)
+    monkeypatch.setattr(tode.api, "mlp_resolve", counting)
+    small = _loss_and_grads(w, torch.float32, field, hbm_budget_bytes=n_max * st - 1)
+    assert len(calls) >= 2 and calls == sorted(calls, reverse=True)
+    assert np.array_equal(full[0].cpu().numpy(), small[0].cpu().numpy())
+    assert np.array_equal(full[3][0], small[3][0])  # dL/dy0
+    for a, b in zip(full[3][1:], small[3][1:]):
+        assert np.linalg.norm(a - b) <= 2e-4 * max(np.linalg.norm(a), 1e-30)

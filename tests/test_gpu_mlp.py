@@ -89,12 +89,23 @@ def test_mlp_max_steps_leaves_unreached_points_nan(form):
 
 
 def test_mlp_unsupported_requests_fail_loudly():
-    """The MLP tape keeps every accepted step: a checkpoint stride is refused."""
+    """The MLP adjoint reverses recorded stage inputs: a checkpoint tape
+    (stride 2) is accepted by the solve, which records checkpoints there,
+    but refused by the adjoint (it is the re-solve's input), and a stride-2
+    tape without the solver state is refused by the solve."""
     import paper_2210_12375_b300 as tode
     w = dict(make(4, B=64), split=True)
-    tape = tode.TapeBuffers.allocate(64, 32, torch.float32, 8, 2, "cuda", stages=True)
+    tape = tode.TapeBuffers.allocate(64, 32, torch.float32, 8, 2, "cuda")
+    g = gpu_solve(w, torch.float32, "fused", tape=tape)
+    dev = g["_dev"]
     with pytest.raises(tode._abi.TodeError):
-        gpu_solve(w, torch.float32, "fused", tape=tape)
+        tode.adjoint(dev["field"], dev["t0"], dev["t1"], dev["te"], g["_sol"], tape,
+                     torch.ones_like(g["_sol"].y_eval), None, rtol=w["rtol"], atol=w["atol"])
+    bare = tode.TapeBuffers.allocate(64, 32, torch.float32, 8, 1, "cuda", stages=True,
+                                     minimal=True)
+    bare.stride = 2
+    with pytest.raises(tode._abi.TodeError):
+        gpu_solve(w, torch.float32, "fused", tape=bare)
 
 
 @pytest.mark.parametrize("B", [300, 148 * 128 + 256])
