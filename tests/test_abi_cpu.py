@@ -306,3 +306,44 @@ def test_joint_adjoint_rules_before_launch():
                                 gw, None, None, stats, C.c_void_p(0x1001), C.c_size_t(1 << 30),
                                 None)
     assert rc == _abi.TODE_EWORKSPACE
+
+
+def test_mlp_resolve_rules_before_launch():
+    """tode_mlp_resolve (the MLP field's checkpointed segment re-solve)
+    takes the split MLP field in the fused form, a checkpoint tape with
+    stride > 1 that holds the whole solver state and a stride-1 stage tape
+    with at least `stride` slots; anything else is refused before anything
+    runs, and an empty batch is a no-op."""
+    lib = _abi.load()
+    split = _opts(prec=_abi.TODE_BF16W_SPLIT)
+    f, keep = _mlp_desc(64)
+    p = 0x1000  # 16-byte aligned stand-ins: nothing is dereferenced
+
+    def tape(stride, slots, full=True, stages=False):
+        t = _abi.Tape()
+        t.slots, t.stride = slots, stride
+        t.y = t.t = p
+        if full:
+            t.y_lo = t.k1 = t.h = t.err_prev = t.flags = p
+        if stages:
+            t.h_acc = t.y_stage = p
+        return t
+    ck, st = tape(4, 8), tape(1, 4, full=False, stages=True)
+    out = C.c_void_p(p)
+
+    def call(fd, o, ckt, seg, stt, ws_bytes=1 << 30):
+        return lib.tode_mlp_resolve(C.byref(fd), C.byref(o), out, out, out, C.byref(ckt), seg,
+                                    C.byref(stt), out, out, out, out, C.c_size_t(ws_bytes), None)
+    assert call(f, split, ck, -1, st) == _abi.TODE_EINVAL                      # segment
+    assert call(f, split, tape(1, 8, stages=True), 0, st) == _abi.TODE_EINVAL  # not strided
+    assert call(f, split, tape(4, 8, full=False), 0, st) == _abi.TODE_EINVAL   # no state
+    assert call(f, split, ck, 0, tape(1, 2, full=False, stages=True)) == _abi.TODE_EINVAL
+    assert call(f, split, ck, 0, tape(2, 4, stages=True)) == _abi.TODE_EINVAL  # stage stride
+    assert call(f, _opts(prec=_abi.TODE_BF16W), ck, 0, st) == _abi.TODE_EUNSUPPORTED
+    assert call(f, _opts(prec=_abi.TODE_BF16W_SPLIT, form=_abi.TODE_PLAIN), ck, 0, st) == \
+        _abi.TODE_EUNSUPPORTED
+    assert call(_desc(_abi.TODE_VDP, 64, 2), _opts(prec=_abi.TODE_F32), ck, 0, st) == \
+        _abi.TODE_EUNSUPPORTED
+    assert call(f, split, ck, 0, st, ws_bytes=16) == _abi.TODE_EWORKSPACE
+    f0, keep0 = _mlp_desc(0)
+    assert call(f0, split, ck, 0, st) == _abi.TODE_OK
