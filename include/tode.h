@@ -148,11 +148,10 @@ typedef struct {
   /* the Runge-Kutta pair: TODE_DOPRI5 (0, Dormand & Prince 1980, the
    * paper's method throughout) or TODE_TSIT5 (1, Tsitouras 2011, which App.
    * A names as also available); both are 5(4) pairs with FSAL and an order-4
-   * dense output, swapped by tableau only.  tsit5 covers every field solved
-   * independently (the MLP field with prec TODE_BF16W_SPLIT): tode_solve,
-   * tode_adjoint and tode_t_bounds_grad; joint solving, the joint
-   * continuous adjoint and the MLP field's TODE_BF16W form return
-   * TODE_EUNSUPPORTED with it. */
+   * dense output, swapped by tableau only.  tsit5 covers every field (the
+   * MLP field with prec TODE_BF16W_SPLIT) and joint solving: tode_solve,
+   * tode_adjoint and tode_t_bounds_grad; the joint continuous adjoint and
+   * the MLP field's TODE_BF16W form return TODE_EUNSUPPORTED with it. */
   int method;
 } tode_options;
 

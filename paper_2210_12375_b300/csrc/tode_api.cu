@@ -148,7 +148,6 @@ void tode_default_options(tode_options* o) {
 // scalar tolerances (one problem has one norm).
 static tode_err joint_ok(const tode_field_desc* f, const tode_options* o) {
   if (!o->joint) return TODE_OK;
-  if (o->method != TODE_DOPRI5) return TODE_EUNSUPPORTED;  // the joint solve is dopri5
   if (f->kind == TODE_MLP) return TODE_EUNSUPPORTED;
   if (o->rtol_b || o->atol_b) return TODE_EINVAL;
   return TODE_OK;

@@ -308,7 +308,7 @@ __device__ __forceinline__ void joint_tape_state(const TapeDev<T>& tp, int i, in
   if (g == 0) tp.t[o] = t;
 }
 
-template <class Field, typename T, int R, int G>
+template <class Field, typename T, int R, int G, class Tab = DP5>
 __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
   const SolveArgs<T>& a = ja.a;
   const JointCtl<T> c = *ja.ctl;
@@ -390,12 +390,12 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
       const T h = c.h_use;
       const double hd = (double)h;
       T ys[6][R], y1[R], inc[R], ev[R], sc[R], q2[R];
-      Stages<T, R> K;  // the joint solve runs the dopri5 pair
+      Stages<T, R> K;  // the pair Tab (dopri5 or tsit5)
 #pragma unroll
       for (int r = 0; r < R; ++r) K.k[0][r] = s.k1[r];
-      attempt_stages<DP5, Field, T, R>(F, c.t, h, s.y, K, ys, y1, inc);
+      attempt_stages<Tab, Field, T, R>(F, c.t, h, s.y, K, ys, y1, inc);
       const T (&k7)[R] = K.k[6];
-      bool fin = error_terms<DP5, T, R>(h, s.y, y1, K, s.rtol, s.atol, ev, sc);
+      bool fin = error_terms<Tab, T, R>(h, s.y, y1, K, s.rtol, s.atol, ev, sc);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const T u = ev[r] / sc[r];
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(256) k_joint_step(JointArgs<T> ja) {
           if constexpr (Comp<T>::on) theta = T(tq - c.t) / h;
           else theta = T((tq - c.t) / hd);
           T v[R];
-          dense_point<DP5, T, R>(theta, h, s.y, s.ylo, K, v);
+          dense_point<Tab, T, R>(theta, h, s.y, s.ylo, K, v);
           store_point<T, R, G>(dst, v);
         }
       }
@@ -570,7 +570,7 @@ template <typename T> JointArgs<T> make_joint_args(const SolveReq& r) {
   return j;
 }
 
-template <class Field, typename T, int R, int G>
+template <class Field, typename T, int R, int G, class Tab>
 tode_err launch_joint(const SolveReq& r) {
   if (r.B == 0) return TODE_OK;
   JointArgs<T> ja = make_joint_args<T>(r);
@@ -583,7 +583,7 @@ tode_err launch_joint(const SolveReq& r) {
   int per_sm = r.o->ctas_per_sm;
   if (per_sm <= 0) {
     TODE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, k_joint_step<Field, T, R, G>, block, 0));
+        &per_sm, k_joint_step<Field, T, R, G, Tab>, block, 0));
     if (per_sm < 1) per_sm = 1;
   }
   long long grid_ll = (threads + block - 1) / block;
@@ -598,7 +598,7 @@ tode_err launch_joint(const SolveReq& r) {
   const long long limit = (long long)r.o->max_steps + 2LL * poll + 2;
   long long launched = 0;
   while (true) {
-    for (int k = 0; k < poll; ++k) k_joint_step<Field, T, R, G><<<grid, block, 0, st>>>(ja);
+    for (int k = 0; k < poll; ++k) k_joint_step<Field, T, R, G, Tab><<<grid, block, 0, st>>>(ja);
     TODE_CUDA_TRY(cudaGetLastError());
     launched += poll;
     int phase = 0;
@@ -613,17 +613,17 @@ tode_err launch_joint(const SolveReq& r) {
 
 // Field / group dispatch of the joint solve (the same lane groups as the
 // independent solver).
-template <typename T> tode_err simt_joint(const SolveReq& r) {
-  if (r.f->kind == TODE_VDP) return launch_joint<VdpField<T>, T, 2, 1>(r);
+template <typename T, class Tab = DP5> tode_err simt_joint(const SolveReq& r) {
+  if (r.f->kind == TODE_VDP) return launch_joint<VdpField<T>, T, 2, 1, Tab>(r);
   switch (linear_group(r.D, r.o->group)) {
-    case 1: return launch_joint<LinearField<T, 1, 1>, T, 1, 1>(r);
-    case 2: return launch_joint<LinearField<T, 1, 2>, T, 1, 2>(r);
-    case 4: return r.D == 4 ? launch_joint<LinearField<T, 1, 4>, T, 1, 4>(r)
-                            : launch_joint<LinearField<T, 4, 4>, T, 4, 4>(r);
-    case 8: return r.D == 8 ? launch_joint<LinearField<T, 1, 8>, T, 1, 8>(r)
-                            : launch_joint<LinearField<T, 2, 8>, T, 2, 8>(r);
-    case 16: return r.D == 16 ? launch_joint<LinearField<T, 1, 16>, T, 1, 16>(r)
-                              : launch_joint<LinearField<T, 2, 16>, T, 2, 16>(r);
+    case 1: return launch_joint<LinearField<T, 1, 1>, T, 1, 1, Tab>(r);
+    case 2: return launch_joint<LinearField<T, 1, 2>, T, 1, 2, Tab>(r);
+    case 4: return r.D == 4 ? launch_joint<LinearField<T, 1, 4>, T, 1, 4, Tab>(r)
+                            : launch_joint<LinearField<T, 4, 4>, T, 4, 4, Tab>(r);
+    case 8: return r.D == 8 ? launch_joint<LinearField<T, 1, 8>, T, 1, 8, Tab>(r)
+                            : launch_joint<LinearField<T, 2, 8>, T, 2, 8, Tab>(r);
+    case 16: return r.D == 16 ? launch_joint<LinearField<T, 1, 16>, T, 1, 16, Tab>(r)
+                              : launch_joint<LinearField<T, 2, 16>, T, 2, 16, Tab>(r);
     default: return TODE_EUNSUPPORTED;
   }
 }

@@ -5,8 +5,9 @@ of a 1e-12 oracle solution; dy/dt at the points; the discrete adjoint and
 the t0/t1 gradients within the adjoint tolerances (1e-10 FP64, 1e-4 FP32),
 the re-run (strided) tape bitwise equal to the direct one; the MLP field
 (split form, both networks) within the band, its adjoints and t0/t1
-gradients within the BF16-weight tolerance; joint solving and the unsplit
-MLP form refuse the pair."""
+gradients within the BF16-weight tolerance; the unsplit MLP form refuses
+the pair; joint solving with it matches the oracle's stacked tsit5
+solve."""
 import numpy as np
 import pytest
 import torch
@@ -154,11 +155,35 @@ def test_tsit5_adjoint_f32_linear_vs_oracle():
     assert _rel(r["gt1"], ref["gt1"]) <= 1e-4
 
 
-def test_tsit5_refused_for_joint_and_the_unsplit_mlp():
-    w = make(2, B=16)
-    with pytest.raises(tode._abi.TodeError) as e:
-        gpu_solve(w, torch.float64, "fused", joint=True, **TS)
-    assert e.value.code == tode._abi.TODE_EUNSUPPORTED
+def test_tsit5_joint_f64_vdp_matches_oracle():
+    """Joint solving (Sec. 4.1) with tsit5 against the oracle's stacked
+    solve with tsit5, at the joint solve's FP64 bar: identical
+    accept/reject sequences, mesh within 1e-11 (the norms' summation orders
+    differ), outputs within 1e-10; and not dopri5's mesh."""
+    B, T = 64, 10.0
+    w = make(1, B=B)
+    te = np.linspace(0.0, T, 16)
+    w = dict(w, t0=np.zeros(B), t1=np.full(B, T), t_eval=np.tile(te, (B, 1)))
+    g = gpu_solve(w, torch.float64, "plain", trace_cap=4000, joint=True, **TS)
+    o = oracle.solve_joint(w["field"], w["y0"], 0.0, T, te,
+                           dict(rtol=w["rtol"], atol=w["atol"], **TS), trace_cap=4000)
+    assert o["status"] == 0 and (g["status"] == 0).all()
+    assert (g["n_acc"] == o["n_acc"]).all() and (g["n_rej"] == o["n_rej"]).all()
+    L = o["trace_len"]
+    assert (g["trace_len"] == L).all()
+    for i in (0, 33, 63):
+        assert np.array_equal(g["trace_accepted"][i, :L], o["trace_accepted"])
+        np.testing.assert_allclose(g["trace_t"][i, :L], o["trace_t"], rtol=1e-11, atol=0)
+        np.testing.assert_allclose(g["trace_h"][i, :L], o["trace_h"], rtol=1e-11, atol=1e-11)
+    assert _rel_close(g["y_eval"], o["y_eval"], 1e-10).all()
+    gf = gpu_solve(w, torch.float64, "fused", joint=True, **TS)
+    assert np.array_equal(gf["y_eval"], g["y_eval"])
+    d = oracle.solve_joint(w["field"], w["y0"], 0.0, T, te,
+                           dict(rtol=w["rtol"], atol=w["atol"]))
+    assert d["n_acc"] + d["n_rej"] != o["n_acc"] + o["n_rej"]
+
+
+def test_tsit5_refused_for_the_unsplit_mlp():
     wm = dict(make(4, B=64), split=False)
     with pytest.raises(tode._abi.TodeError) as e:
         gpu_solve(wm, torch.float32, "fused", **TS)
