@@ -149,9 +149,10 @@ typedef struct {
    * paper's method throughout) or TODE_TSIT5 (1, Tsitouras 2011, which App.
    * A names as also available); both are 5(4) pairs with FSAL and an order-4
    * dense output, swapped by tableau only.  tsit5 covers every field (the
-   * MLP field with prec TODE_BF16W_SPLIT) and joint solving: tode_solve,
-   * tode_adjoint and tode_t_bounds_grad; the joint continuous adjoint and
-   * the MLP field's TODE_BF16W form return TODE_EUNSUPPORTED with it. */
+   * MLP field with prec TODE_BF16W_SPLIT), joint solving and the joint
+   * continuous adjoint: tode_solve, tode_adjoint, tode_t_bounds_grad and
+   * tode_joint_adjoint; the MLP field's TODE_BF16W form returns
+   * TODE_EUNSUPPORTED with it. */
   int method;
 } tode_options;
 
@@ -411,7 +412,7 @@ tode_err tode_t_bounds_grad(const tode_field_desc* f, const tode_options* o, con
  * adds that point's cotangent to a (the loss jumps there); points at t1
  * start a, points at t0 add at the end.  The MLP field of the D = 32, H =
  * 128 network (TODE_EUNSUPPORTED otherwise), prec TODE_BF16W_SPLIT, scalar
- * tolerances, TODE_DOPRI5; t0 < t1 shared by the batch (host doubles),
+ * tolerances, either pair; t0 < t1 shared by the batch (host doubles),
  * t_eval [K] host, shared, ordered from t0 to t1.
  *   y1 [B][D] float (device): y(t1) from the forward solve.
  *   gy_eval [B][K][D], gy_final [B][D] (device float, NULL = 0).

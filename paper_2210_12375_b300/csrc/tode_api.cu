@@ -314,7 +314,7 @@ tode_err tode_adjoint(const tode_field_desc* f, const tode_options* o, const dou
 
 static bool jadj_ok(const tode_field_desc* f, const tode_options* o) {
   return f->kind == TODE_MLP && o->prec == TODE_BF16W_SPLIT && !o->rtol_b && !o->atol_b &&
-         !o->joint && o->method == TODE_DOPRI5;
+         !o->joint;
 }
 
 size_t tode_joint_adjoint_workspace_size(const tode_field_desc* f, const tode_options* o) {

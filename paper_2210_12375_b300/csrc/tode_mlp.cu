@@ -3129,10 +3129,9 @@ template <class L> __host__ __device__ constexpr bool jadj_real(int p) {
   return !(p < L::P_W1 && (p % L::K0) >= L::D + 2);
 }
 
-template <class Cfg>
+template <class Cfg, class Tb = DP5>
 __global__ void __launch_bounds__(256, 1) k_mlp_jadj(JadjArgs a, int mode) {
   using L = MlpAdjLayout<Cfg>;
-  using Tb = DP5;
   constexpr int D = Cfg::D, H = Cfg::H, K0 = Cfg::K0, C = Cfg::C, HC = Cfg::HC;
   constexpr int P = L::P_FLOATS;
   const JadjCtl c = *a.ctl;
@@ -3699,10 +3698,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_jadj(JadjArgs a, int mode) {
 // parameter the CTAs' slots in CTA order, abar's candidate and its squared
 // scaled error term; then the last CTA's decision and controller, exactly
 // the solver's (the oracle's orc_solve on the same augmented problem).
-template <class Cfg>
+template <class Cfg, class Tb = DP5>
 __global__ void __launch_bounds__(256) k_mlp_jadj_decide(JadjArgs a, int mode, int grid1) {
   using L = MlpAdjLayout<Cfg>;
-  using Tb = DP5;
   constexpr int P = L::P_FLOATS;
   __shared__ double red[8];
   __shared__ int last_s;
@@ -4546,7 +4544,7 @@ size_t mlp_jadj_workspace_bytes(const tode_field_desc* f) {
   return jadj_carve(nullptr, f->B).bytes;
 }
 
-tode_err mlp_joint_adjoint(const JadjReq& r) {
+template <class Tb> static tode_err mlp_joint_adjoint_tab(const JadjReq& r) {
   using Cfg = Cfg32s;
   using L = MlpAdjLayout<Cfg>;
   constexpr int D = 32, P = L::P_FLOATS;
@@ -4594,7 +4592,7 @@ tode_err mlp_joint_adjoint(const JadjReq& r) {
   }
   {
     static std::atomic<uint64_t> done{0};
-    const tode_err e = smem_optin((const void*)k_mlp_jadj<Cfg>, L::S_END, done);
+    const tode_err e = smem_optin((const void*)k_mlp_jadj<Cfg, Tb>, L::S_END, done);
     if (e != TODE_OK) return e;
   }
   const size_t BD = (size_t)B * D;
@@ -4614,9 +4612,9 @@ tode_err mlp_joint_adjoint(const JadjReq& r) {
     return TODE_OK;
   };
   auto pair = [&](int mode) -> tode_err {
-    k_mlp_jadj<Cfg><<<grid1, 256, L::S_END, st>>>(a, mode);
+    k_mlp_jadj<Cfg, Tb><<<grid1, 256, L::S_END, st>>>(a, mode);
     TODE_CUDA_TRY(cudaGetLastError());
-    k_mlp_jadj_decide<Cfg><<<grid2, 256, 0, st>>>(a, mode, grid1);
+    k_mlp_jadj_decide<Cfg, Tb><<<grid2, 256, 0, st>>>(a, mode, grid1);
     TODE_CUDA_TRY(cudaGetLastError());
     return TODE_OK;
   };
@@ -4688,6 +4686,11 @@ tode_err mlp_joint_adjoint(const JadjReq& r) {
   r.stats[2] = n_fe;
   r.stats[3] = status;
   return flag ? TODE_ETIMEOUT : TODE_OK;
+}
+
+// the pair of the joint continuous adjoint's steps (dopri5 or tsit5)
+tode_err mlp_joint_adjoint(const JadjReq& r) {
+  return r.o->method == TODE_TSIT5 ? mlp_joint_adjoint_tab<TS5>(r) : mlp_joint_adjoint_tab<DP5>(r);
 }
 
 }  // namespace tode
