@@ -215,3 +215,40 @@ def test_autograd_mlp_budget_checkpoints_segments(cfg, B, monkeypatch):
     assert np.array_equal(full[3][0], small[3][0])  # dL/dy0
     for a, b in zip(full[3][1:], small[3][1:]):
         assert np.linalg.norm(a - b) <= 2e-4 * max(np.linalg.norm(a), 1e-30)
+
+
+def test_autograd_mlp_budget_segments_pid_mixed_directions_tsit5(monkeypatch):
+    """The checkpoints carry the whole controller state: with the PID
+    controller (beta2, beta3 != 0, so err_prev and err_prev2 steer the
+    steps), every other instance integrated backward, and the tsit5 pair,
+    the budgeted backward's dL/dy0 still equals the full tape's bit for
+    bit, and the (BF16) weight gradients agree to the BF16 unit roundoff."""
+    B = 300
+    w = dict(make(4, B=B), split=True)
+    t0, t1, te = w["t0"].copy(), w["t1"].copy(), w["t_eval"].copy()
+    t0[::2], t1[::2] = w["t1"][::2], w["t0"][::2]
+    te[::2] = te[::2, ::-1]
+    w = dict(w, t0=t0, t1=t1, t_eval=np.ascontiguousarray(te), rtol=1e-6, atol=1e-6)
+    field = device_field(w, torch.float32)
+    opt = dict(beta1=0.7 / 5, beta2=0.5 / 5, beta3=0.1 / 5, method="tsit5")
+    full = _loss_and_grads(w, torch.float32, field, **opt)
+    n_max = int(full[2].max())
+    assert n_max >= 4
+    D = w["y0"].shape[1]
+    st = tode.TapeBuffers.bytes_per_slot(B, D, 4, stages=True, minimal=True)
+    calls = []
+    real = tode.api.mlp_resolve
+
+    def counting(*a, **k):
+        calls.append(a[5])
+        return real(*a, **k)
+    monkeypatch.setattr(tode.api, "mlp_resolve", counting)
+    small = _loss_and_grads(w, torch.float32, field, hbm_budget_bytes=n_max * st - 1, **opt)
+    assert len(calls) >= 2
+    assert np.array_equal(full[0].cpu().numpy(), small[0].cpu().numpy())
+    assert np.array_equal(full[3][0], small[3][0])  # dL/dy0
+    # the weight gradients come back in the weights' BF16: sums that differ
+    # in FP32 summation order round to the same BF16 value or to a
+    # neighbour, so the tensors agree to the BF16 unit roundoff (2^-8)
+    for a, b in zip(full[3][1:], small[3][1:]):
+        assert np.linalg.norm(a - b) <= 2.0 ** -8 * max(np.linalg.norm(a), 1e-30)
