@@ -469,7 +469,7 @@ class Workload:
         torch.cuda.synchronize()
         return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
-    def rooflines(self, k_fwd_ms, k_adj_ms, fp32_peak, fp32_src):
+    def rooflines(self, k_fwd_ms, k_adj_ms, fp32_peak, fp32_src, fp64=None):
         """The forward's and the adjoint's rooflines: tensor (BF16) for the
         MLP field, the FP32 pipe (measured here) for the SIMT fields."""
         w, D = self.w, self.D
@@ -515,12 +515,13 @@ class Workload:
                 ka = {"achieved": adjoint_flops_per_step(self.kind, D, self.kind == "linear")
                       * self.n_acc_total / (k_adj_ms * 1e-3) / 1e12,
                       "kernel": f"k_adjoint_steps<{adj}> (stride-1 tape)", "kernel_ms": k_adj_ms}
+            # FP64 state: the FP64 pipe's measured peak (when measured), else FP32's
+            pk, src_ = fp64 if (tn == "double" and fp64) else (fp32_peak, fp32_src)
             for r in (kf, ka):
                 if r is None:
                     continue
-                r.update(bound="alu", peak=fp32_peak, unit="TFLOP/s",
-                         frac=r["achieved"] / fp32_peak,
-                         traffic=_traffic(w["name"], r["kernel"]), peak_source=fp32_src)
+                r.update(bound="alu", peak=pk, unit="TFLOP/s", frac=r["achieved"] / pk,
+                         traffic=_traffic(w["name"], r["kernel"]), peak_source=src_)
         return kf, ka
 
 
@@ -546,7 +547,9 @@ def measure(cfg, args, dev, fp32_peak, fp32_src, world=1, headline=False, peaks=
         ms_ff = ms_f
     ms_p, _, _, sol_p = wl.timed("plain", args.plain_steps, with_adj, world)
     ms_pf = wl.timed("plain", args.plain_steps, False, world)[0] if with_adj else ms_p
-    kf, ka = wl.rooflines(k_fwd, k_adj, fp32_peak, fp32_src)
+    fp64 = ((peaks["fp64_tflops"], "measured here: FP64 FMA micro-benchmark (tode_peak_kernel)")
+            if peaks else None)
+    kf, ka = wl.rooflines(k_fwd, k_adj, fp32_peak, fp32_src, fp64=fp64)
     dom, other = ((ka, kf) if (ka is not None and k_adj >= k_fwd) else (kf, ka))
     per = ms_f / steps
     n = world * wl.n_att
