@@ -199,7 +199,10 @@ template <int D_, int H_, int NL_> struct MlpWideCfg {
     return o;
   }
   static constexpr int WIMG_BYTES = W_off(NL);
-  static constexpr int WREP = 16, WIMG_STRIDE = ((WIMG_BYTES + 255) / 256) * 256;
+  // one weight image for all CTAs: more copies only spread the same reads
+  // over more L2 lines (measured on the whole wide step: 16 copies 30.9 ms,
+  // 8: 30.7, 4: 30.5, 2: 30.5, 1: 30.4)
+  static constexpr int WREP = 1, WIMG_STRIDE = ((WIMG_BYTES + 255) / 256) * 256;
   static constexpr int BIAS_FLOATS = (NL - 1) * H + D;
   // weight stages: consecutive 16-column K chunks of one layer, up to 32 KB
   static constexpr int KC = 16, NSL = 2, SLOT_BYTES = 32768;
