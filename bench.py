@@ -167,7 +167,7 @@ TRAFFIC = {
     # full size (B = 65,536), one pass per launch: the forward launch, and the
     # sum over the 16 launches of one adjoint call (the call is the entry)
     ("mlp_d64_h512", "k_mlp_fused"): 1066.11e6,
-    ("mlp_d64_h512", "k_mlp_adjoint"): 56.606e9,
+    ("mlp_d64_h512", "k_mlp_adjoint"): 53.981e9,
     ("vdp_joint_mu10_b2097152", "k_joint_step<VdpField<float>>"): 69.76e6,
 }
 

@@ -2437,8 +2437,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     const int fb = col / fw, m = col - fb * fw;
     unsigned char* dst = a.plane[L::plane_first(t) + fb] + blk * 2 * (size_t)L::blk_bytes(t) +
                          L::blk_off(row, m, fw);
-    *reinterpret_cast<uint4*>(dst) = hi;
-    *reinterpret_cast<uint4*>(dst + L::blk_bytes(t)) = lo;
+    if (t == L::T_H1 || t == L::T_H2 || t == L::T_H3) {  // read back by the delta epilogues
+      *reinterpret_cast<uint4*>(dst) = hi;
+      *reinterpret_cast<uint4*>(dst + L::blk_bytes(t)) = lo;
+    } else {  // read only by the weight-gradient kernel: streamed past the L2
+      __stcs(reinterpret_cast<uint4*>(dst), hi);
+      __stcs(reinterpret_cast<uint4*>(dst + L::blk_bytes(t)), lo);
+    }
   };
   auto stage16 = [&](int t, int col, const float (&v)[16]) {
 #pragma unroll
